@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""Benchmark of the SANS Fourier-sum hot path on GB300.
+
+One step = one pass of the whole hot path over the workload: rotation and
+weights, the four Fourier sums (tensor-core split-FP16 GEMM on the separable
+detector grid, or the FP32 direct sum), the Hermitian products, the
+unpolarized and spin-flip cross sections, their azimuthal averages and the
+correlation functions.  Metric: cell x q-point terms per second (one term =
+one (cell, pixel) pair, all four channels, real and imaginary part).
+
+Default workload: the micromagnetic-style box, 256 x 256 x 64 cells at 2 nm
+(4.19M cells, smooth random M from 64 Fourier modes, 200 pores), 512 x 512
+detector on [-2, 2]^2 nm^-1: 1.10e12 terms per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nms|reference]
+                  [--precision auto|tc|direct|naive] [--workload box|sphere]
+
+With --gpus N > 1 (torchrun) every rank evaluates its own replica of the
+workload (weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell·q-point terms/s of SANS Fourier sum: tensor-core split vs FP32 at 1e-6 err"
+
+# FP32-pipe operations per term of the compensated direct-sum kernel counted
+# from its source (phase 22, sincospif ~20, 8 FMA, two-float fold 7).
+DIRECT_OPS_PER_TERM = 57
+# Executed tensor flops per term of the split-FP16 GEMM: 3 products x 32 flops.
+TC_FLOPS_PER_TERM = 96
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+# ----------------------------------------------------------------- workloads
+def make_workload(name):
+    from paper_2601_18444_gb300 import inputs as I
+    if name == "box":
+        f = I.box_field(256, 256, 64, a=2.0, n_modes=64, kmax=0.2, n_pores=200, seed=1)
+        grid = dict(kind="cartesian", n0=512, n1=512, lo0=-2.0, hi0=2.0, lo1=-2.0, hi1=2.0)
+        edges = np.linspace(0.0, 2.0, 129)
+        r = np.linspace(0.0, 600.0, 64)
+        desc = "box 256x256x64 cells a=2nm (4.19M), 64 modes k<=0.2, 200 pores; 512x512 detector [-2,2]^2 nm^-1"
+    elif name == "box64":
+        # small case of the same kernels for profiler captures (262k cells)
+        f = I.box_field(64, 64, 64, a=2.0, n_modes=64, kmax=0.2, n_pores=20, seed=1)
+        grid = dict(kind="cartesian", n0=512, n1=512, lo0=-2.0, hi0=2.0, lo1=-2.0, hi1=2.0)
+        edges = np.linspace(0.0, 2.0, 129)
+        r = np.linspace(0.0, 200.0, 64)
+        desc = "box 64x64x64 cells a=2nm (262k), 512x512 detector [-2,2]^2 nm^-1 (profiling case)"
+    elif name == "sphere":
+        f = I.sphere_vortex(16.0, 2.0, seed=0)
+        grid = dict(kind="cartesian", n0=128, n1=128, lo0=-1.0, hi0=1.0, lo1=-1.0, hi1=1.0)
+        edges = np.linspace(0.0, 1.0, 65)
+        r = np.linspace(0.0, 40.0, 64)
+        desc = "sphere R=16nm a=2nm (2109 cells) seeded vortex; 128x128 detector [-1,1]^2 nm^-1"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return f, grid, edges, r, desc
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, max_mhz):
+        sm = []
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+                max_mhz = mx
+            except (ValueError, IndexError):
+                continue
+            for k, v in zip(names, r[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(k)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max_mhz,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- oracle timing
+def oracle_sample_rate(field, grid_kw, target_s=12.0, seed=0):
+    """Oracle terms/s on a random sample of pixels (all cells); returns (rate, sample, F_ref, idx)."""
+    from oracle import sans as S
+    kw = dict(grid_kw)
+    kind = kw.pop("kind")
+    g = S.q_grid(kind, **kw)
+    rng = np.random.default_rng(seed)
+    w = S.cell_weights(field.vol, field.nuc, field.mag, np.eye(3))
+    Y, Z = field.pos[:, 1].copy(), field.pos[:, 2].copy()
+    npix = g[0].shape[0]
+    probe = rng.choice(npix, size=min(8, npix), replace=False)
+    t0 = time.perf_counter()
+    S.dsft(Y, Z, w, g[0][probe], g[1][probe])
+    dt = max(time.perf_counter() - t0, 1e-4)
+    per_pix = dt / len(probe)
+    n_s = int(max(8, min(npix, target_s / per_pix)))
+    idx = np.sort(rng.choice(npix, size=n_s, replace=False))
+    t0 = time.perf_counter()
+    F = S.dsft(Y, Z, w, g[0][idx], g[1][idx])
+    dt = time.perf_counter() - t0
+    terms = float(n_s) * field.n
+    return terms / dt, f"{n_s} random pixels x {field.n} cells (seed {seed}), {dt:.1f} s", F, idx, S.oracle_threads()
+
+
+# ----------------------------------------------------------------- dist helpers
+def dist_setup(n_gpus):
+    rank, world = 0, 1
+    if n_gpus > 1 or "RANK" in os.environ:
+        import torch.distributed as dist
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        if world > 1:
+            import torch
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            dist.init_process_group(backend=backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world = dist_setup(args.gpus)
+    if rank != 0:
+        return 0
+    field, grid_kw, edges, r, desc = make_workload(args.workload)
+    from oracle import sans as S
+    kw = dict(grid_kw)
+    kind = kw.pop("kind")
+    g = S.q_grid(kind, **kw)
+    w = S.cell_weights(field.vol, field.nuc, field.mag, np.eye(3))
+    Y, Z = field.pos[:, 1].copy(), field.pos[:, 2].copy()
+    rng = np.random.default_rng(1)
+    npix = g[0].shape[0]
+    n_s = min(npix, 48 if field.n > 1e6 else npix)
+    times = []
+    for it in range(args.warmup + args.steps):
+        idx = rng.choice(npix, size=n_s, replace=False)
+        t0 = time.perf_counter()
+        S.dsft(Y, Z, w, g[0][idx], g[1][idx])
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    terms = float(n_s) * field.n
+    rate = terms * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "terms/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "sample": f"{n_s} random pixels x {field.n} cells per step"},
+            "cpu_baseline": {"value": rate, "unit": "terms/s", "cores": S.oracle_threads(), "kind": "oracle",
+                             "sample": f"{n_s} random pixels x {field.n} cells per step"},
+            "e2e": {"value": rate, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- main arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="nms", choices=["nms", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "tc", "direct", "naive"])
+    ap.add_argument("--workload", default="box", choices=["box", "box64", "sphere"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kc", type=int, default=0, help="cells per TMEM accumulation chunk (0: library default)")
+    ap.add_argument("--workspace-gb", type=float, default=0.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2601_18444_gb300 import nms
+
+    rank, world = dist_setup(args.gpus)
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    nms.load()
+    field, grid_kw, edges, r, desc = make_workload(args.workload)
+    prec = {"auto": nms.PREC_AUTO, "tc": nms.PREC_TC_F16X3, "direct": nms.PREC_FP32_DIRECT,
+            "naive": nms.PREC_FP32_NAIVE}[args.precision]
+    stream = torch.cuda.current_stream()
+    g = nms.make_grid(**grid_kw)
+    opt = nms.nms_options_default(precision=prec, timing=1, kc_cells=args.kc,
+                                  workspace_bytes=int(args.workspace_gb * (1 << 30)))
+    plan = nms.plan_from_field(field, g, opt, stream=stream.cuda_stream)
+    npix = plan.npix
+    terms = float(field.n) * npix
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    img_u = torch.empty(npix, dtype=torch.float64, device="cuda")
+    img_s = torch.empty(npix, dtype=torch.float64, device="cuda")
+    r_dev = torch.tensor(r, dtype=torch.float64, device="cuda")
+
+    def step():
+        nms.nms_amplitudes(plan)
+        nms.nms_response(plan, "UNPOL", out=img_u)
+        nms.nms_response(plan, "SF", out=img_s)
+        out = []
+        for img in (img_u, img_s):
+            I, c, qm = nms.nms_azimuthal_average(plan, img, edges)
+            cc, pp = nms.nms_correlation(qm, I, r, stream=stream.cuda_stream)
+            out.append((I, cc, pp))
+        return out
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    nms.nms_plan_stage_ms(plan, reset=True)
+    peaks, peak_src = load_peaks()
+    times = []
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)                       # L2 flush between timed steps (256 MB > 129 MB L2)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier(world)
+    stage = nms.nms_plan_stage_ms(plan)
+    ms_step = max_over_ranks(float(np.mean(times)), world)
+    value = world * terms / (ms_step * 1e-3)
+    launches_per_step = sum(v[1] for v in stage.values()) / args.steps + 2 + 2 + 4
+    clocks = clk.summary(peaks.get("sm_max_mhz", 2070.0))
+
+    # dominant kernel roofline
+    if plan_path_is_tc(stage):
+        k_ms = stage["gemm"][0] / args.steps
+        achieved = terms * TC_FLOPS_PER_TERM / (k_ms * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops", 1900.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_gemm_f16x3",
+                "peak_source": f"{peak_src} bf16 dense (f16 same rate)"}
+    else:
+        k_ms = stage["direct"][0] / args.steps
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+        peak = sms * 128 * mhz * 1e6 / 1e12
+        achieved = terms * DIRECT_OPS_PER_TERM / (k_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_direct<compensated>",
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz (median SM clock under load)"}
+
+    # error on a sample of pixels vs the oracle, and the oracle's own rate
+    cpu = None
+    err = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, sample, F_ref, idx, cores = oracle_sample_rate(field, grid_kw, args.cpu_seconds)
+        F = nms.nms_get_amplitudes(plan)
+        from oracle import sans as S
+        wsum = np.abs(S.cell_weights(field.vol, field.nuc, field.mag, np.eye(3))).sum(1)
+        err = [float(np.max(np.abs(F[c][idx] - F_ref[c])) / wsum[c]) if wsum[c] > 0 else 0.0 for c in range(4)]
+        cpu = {"value": rate, "unit": "terms/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if args.steps > 0 and not args.no_e2e:
+        pin = {}
+        for k in ("pos", "vol", "nuc", "mag"):
+            a = getattr(field, k)
+            t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+            t.numpy()[...] = a
+            pin[k] = t.numpy()
+        out_u = torch.empty(npix, dtype=torch.float64, pin_memory=True).numpy()
+        out_s = torch.empty(npix, dtype=torch.float64, pin_memory=True).numpy()
+        e2e_times = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p2 = nms.nms_plan_create(pin["pos"], pin["vol"], pin["nuc"], pin["mag"], grid=g, opt=opt,
+                                     stream=stream.cuda_stream)
+            nms.nms_amplitudes(p2)
+            nms.nms_response(p2, "UNPOL", out=out_u)
+            nms.nms_response(p2, "SF", out=out_s)
+            for img in (out_u, out_s):
+                I, c, qm = nms.nms_azimuthal_average(p2, img, edges)
+                nms.nms_correlation(qm, I, r)
+            p2.close()
+            torch.cuda.synchronize()
+            e2e_times.append(time.perf_counter() - t0)
+        t_e2e = max_over_ranks(min(e2e_times), world)
+        h2d = sum(pin[k].nbytes for k in pin)
+        d2h = 2 * npix * 8
+        e2e = {"value": world * terms / t_e2e, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "s_per_step": t_e2e}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f16x3->f32(two-float)" if plan_path_is_tc(stage) else "f32(two-float)",
+                "data": "synthetic",
+                "config": {"workload": desc, "parallelism": f"replicas x{world}", "l2": "flushed between steps",
+                           "precision": args.precision, "terms_per_step": terms,
+                           "stage_ms_per_step": {k: v[0] / args.steps for k, v in stage.items() if v[1]}},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(round(launches_per_step
+                                                                                           * args.steps)),
+                "clocks": clocks, "amp_err_vs_oracle": err}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def plan_path_is_tc(stage):
+    return stage.get("gemm", (0, 0))[1] > 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

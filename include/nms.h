@@ -1,0 +1,233 @@
+/*
+ * nms.h -- C ABI of the GB300 SANS Fourier-sum library (libnms.so).
+ *
+ * The library evaluates, on one NVIDIA GB300 (sm_103a), the hot path of the
+ * NuMagSANS method: the discrete Fourier sums of the nuclear scattering-length
+ * density and of the magnetization over every (rotated) cell, on a 2D
+ * detector q-grid, the Halpern-Johnson projection, the nuclear, magnetic,
+ * interference, polarised and unpolarized cross sections, their azimuthal
+ * average and the Fourier-Bessel correlation functions.
+ *
+ * Conventions used by every entry point:
+ *  - Lengths in the caller's unit (nm in the examples), q in the inverse
+ *    unit.  The scattering geometry is fixed as in the paper: beam along x,
+ *    detector in the y-z plane, q = (0, q_y, q_z), qhat = (0, sin t, cos t).
+ *  - Amplitudes are RAW sums F_c(q) = sum_j w_cj exp(-i q.r'_j) with
+ *    w_cj = V_j (N_j, M'_xj, M'_yj, M'_zj): the (2 pi)^{-3/2} of the DSFT and
+ *    the 8 pi^3 of the cross sections cancel, so every cross section is the
+ *    raw quadratic form times 1/V (and b_H, b_H^2 for magnetic terms).
+ *  - Row-major arrays.  "host or device" pointers are told apart by the
+ *    *_is_device flag next to them; nothing is inferred.
+ *  - Status codes only: no exception or abort crosses the ABI.  On failure
+ *    nms_last_error() returns a thread-local message.  Failed creates leave
+ *    *out == NULL.
+ *  - Thread safety: one plan per host thread (a plan owns one CUDA stream).
+ *  - Memory: the plan deep-copies its inputs to the device at create time and
+ *    owns all device memory it allocates until nms_plan_destroy().  Caller
+ *    buffers are never retained after a call returns.
+ *  - No CPU fallback: without a usable sm_103a device every call that would
+ *    compute returns NMS_ERR_CUDA.
+ */
+#ifndef NMS_H
+#define NMS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nms_plan_s* nms_plan_t;
+
+typedef enum {
+    NMS_OK = 0,
+    NMS_ERR_INVALID_ARG = 1,   /* a size, pointer, id or option is out of range   */
+    NMS_ERR_OUT_OF_MEMORY = 2, /* a device or host allocation failed              */
+    NMS_ERR_CUDA = 3,          /* a CUDA call failed (no device, launch failure)  */
+    NMS_ERR_UNSUPPORTED = 4,   /* valid request the chosen path cannot serve      */
+    NMS_ERR_TIMEOUT = 5,       /* a bounded device wait gave up (kernel returned) */
+    NMS_ERR_BAD_STATE = 6      /* call out of order (e.g. response before sums)   */
+} nms_status;
+
+/* Detector grids (paper, Sec. "Configuration file" and Eq. qdef).
+ *  CARTESIAN: q_y[a] = lo0 + (hi0-lo0) a/(n0-1), a < n0 (n0 == 1 gives lo0),
+ *             q_z[b] likewise with (n1, lo1, hi1); pixel p = a*n1 + b.
+ *             Separable: served by the tensor-core path.
+ *  POLAR:     q_i = lo0 + (hi0-lo0) i/(n0-1), theta_j = 2 pi j/n1,
+ *             q_y = q sin theta, q_z = q cos theta; pixel p = i*n1 + j.
+ *             This is the paper's (q, theta) grid; served by the direct sum.
+ *  LIST:      n0 arbitrary points, qlist[2p] = q_y, qlist[2p+1] = q_z (host).
+ *             Served by the direct sum.
+ * qhat = q/|q|; where |q| == 0 qhat = e_z (CARTESIAN, LIST) or uses theta_j
+ * (POLAR). */
+typedef enum { NMS_QGRID_CARTESIAN = 0, NMS_QGRID_POLAR = 1, NMS_QGRID_LIST = 2 } nms_qgrid_kind;
+
+typedef struct {
+    int32_t kind;            /* nms_qgrid_kind */
+    int32_t n0, n1;          /* CARTESIAN: n_y, n_z; POLAR: n_q, n_theta; LIST: n, ignored */
+    double lo0, hi0;         /* CARTESIAN: q_y range; POLAR: |q| range */
+    double lo1, hi1;         /* CARTESIAN: q_z range; unused otherwise */
+    const double* qlist;     /* LIST only: host [n0][2] */
+} nms_qgrid;
+
+/* How the Fourier sums are evaluated. */
+typedef enum {
+    NMS_PREC_AUTO = 0,          /* TC_F16X3 on CARTESIAN grids, FP32_DIRECT otherwise   */
+    NMS_PREC_TC_F16X3 = 1,      /* split-FP16 (hi/lo, 3 products) tcgen05 GEMM, FP32
+                                   TMEM accumulation promoted to two-float every
+                                   kc_cells cells; CARTESIAN grids only               */
+    NMS_PREC_FP32_DIRECT = 2,   /* compensated FP32 direct sum (two-float phase in
+                                   turns, exact reduction, sincospif)                  */
+    NMS_PREC_FP32_NAIVE = 3     /* plain FP32 phase + sincosf: fast, inaccurate at
+                                   large |q.r|; reported for comparison only           */
+} nms_precision;
+
+typedef struct {
+    int32_t precision;       /* nms_precision */
+    int32_t want_dilute;     /* 1: also accumulate sum_k G_k over objects (form
+                                factors without interparticle interference)     */
+    double volume_V;         /* scattering volume V of the 1/V prefactor; 0 -> 1 */
+    double b_H;              /* magnetic scattering length b_H; 0 -> 1           */
+    double P[3];             /* polarisation unit vector; all 0 -> e_z           */
+    int32_t kc_cells;        /* tensor path: cells per FP32 TMEM chunk; 0 -> auto */
+    int32_t split_k;         /* tensor path: K splits across CTAs; 0 -> auto     */
+    int64_t max_spin;        /* bounded device waits: poll iterations before the
+                                kernel gives up with NMS_ERR_TIMEOUT; 0 -> default */
+    int64_t workspace_bytes; /* cap on tensor-path table workspace; 0 -> default */
+    int32_t timing;          /* 1: record CUDA events around each stage (see
+                                nms_plan_stage_ms)                               */
+    int32_t reserved[7];
+} nms_options;
+
+/* Fill *opt with the defaults above. */
+nms_status nms_options_default(nms_options* opt);
+
+/* Create a plan: validate inputs, copy them to the device (H2D), build the
+ * q-grid.  Paper: Sec. "Real-space input data" (cells x^{kl}, objects k with
+ * centres r^k, indexing W = sum N_k), Sec. "Configuration file" (rotation
+ * R = R_z(beta) R_y(alpha), generalised here to any R), Sec. "Summation
+ * approach".
+ *   n_cells         W >= 1 total cells.
+ *   pos             host [n_cells][3] local cell coordinates x^{kl}.
+ *   cell_vol        host [n_cells] cell volumes V_j, or NULL for all 1.
+ *   nuc             host [n_cells] nuclear density N_j, or NULL (channel off).
+ *   mag             host [n_cells][3] magnetization M_j, or NULL (off).
+ *   n_objects       K >= 1.
+ *   object_offsets  host [K+1], 0 = off_0 <= ... <= off_K = n_cells (empty
+ *                   objects allowed), or NULL when K == 1.
+ *   object_centers  host [K][3] centres r^k, or NULL (all 0: dilute system).
+ *   n_rot           >= 1 sample orientations; results are averaged over them.
+ *   rot             host [n_rot][9] row-major rotation matrices, or NULL for
+ *                   the identity (n_rot must then be 1).  Positions AND
+ *                   magnetizations are rotated: r' = R (x + r^k), M' = R M.
+ *   grid            detector grid (copied).
+ *   opt             options (copied), or NULL for defaults.
+ *   cuda_stream     cudaStream_t every launch of this plan goes to (NULL: the
+ *                   legacy default stream).
+ * Errors: INVALID_ARG (sizes, offsets not monotone, TC precision on a
+ * non-CARTESIAN grid), OUT_OF_MEMORY, CUDA. */
+nms_status nms_plan_create(nms_plan_t* out, int64_t n_cells, const double* pos,
+                           const double* cell_vol, const double* nuc, const double* mag,
+                           int64_t n_objects, const int64_t* object_offsets,
+                           const double* object_centers, int32_t n_rot, const double* rot,
+                           const nms_qgrid* grid, const nms_options* opt, void* cuda_stream);
+
+/* Evaluate the Fourier sums for every rotation and accumulate the Hermitian
+ * products G = F F^dagger (16 reals per pixel) that every response is a
+ * linear function of: G_total from the full amplitude sum_k F_k e^{-iq.r^k}
+ * and, with want_dilute, G_dilute = sum_k F_k F_k^dagger (paper, Sec.
+ * "Summation approach": interparticle decomposition).  Both are averaged over
+ * the rotations.  Asynchronous on the plan's stream; errors from the device
+ * (e.g. TIMEOUT) surface here or at the next synchronising call. */
+nms_status nms_amplitudes(nms_plan_t plan);
+
+/* Copy the total amplitudes of the LAST rotation evaluated:
+ * out[c][p][2] = (Re, Im) F_c(q_p), c = N, Mx, My, Mz (rotated frame),
+ * n_pixels = n0*n1 (n0 for LIST).  out is host or device memory of
+ * 8*n_pixels doubles.  Synchronises the plan's stream. */
+nms_status nms_get_amplitudes(nms_plan_t plan, double* out, int32_t out_is_device);
+
+/* Response ids (paper, Sec. "SANS observables"):
+ *  N   = |F_N|^2 / V                                    Eq. NuclearSANS
+ *  M   = b^2 |Q|^2 / V, Q = qhat x (qhat x F_M)          Eqs. MagneticSANS, HJdef
+ *  P   = b^2 |P.Q|^2 / V                                 Eq. PSANSdef
+ *  NM  = b (F_N (P.Q)^* + F_N^* P.Q) / V                 Eq. NMdef
+ *  CHI = -i b^2 P.(Q x Q^*) / V                          Eq. ChiralSANS
+ *  SF  = M - P                                           Eq. sfdef
+ *  PM, MP = SF +- CHI  (+-, -+)      PP, MM = N +- NM + P  (++, --)
+ *  SANSPOL_P = PP + PM,  SANSPOL_M = MM + MP             SANSPOL section
+ *  UNPOL = (PP + MM + PM + MP)/2 = N + M                 unpolarized section
+ *  G_ab_RE/IM = Re/Im F_Ma F_Mb^* / V (a, b in x, y, z)  Fourier cross spectra
+ *  QX2, QY2, QZ2 = |Q_x|^2/V, |Q_y|^2/V, |Q_z|^2/V */
+enum {
+    NMS_RESP_N = 0, NMS_RESP_M, NMS_RESP_P, NMS_RESP_NM, NMS_RESP_CHI, NMS_RESP_SF,
+    NMS_RESP_PM, NMS_RESP_MP, NMS_RESP_PP, NMS_RESP_MM, NMS_RESP_SANSPOL_P,
+    NMS_RESP_SANSPOL_M, NMS_RESP_UNPOL,
+    NMS_RESP_G_XX_RE, NMS_RESP_G_XX_IM, NMS_RESP_G_XY_RE, NMS_RESP_G_XY_IM,
+    NMS_RESP_G_XZ_RE, NMS_RESP_G_XZ_IM, NMS_RESP_G_YX_RE, NMS_RESP_G_YX_IM,
+    NMS_RESP_G_YY_RE, NMS_RESP_G_YY_IM, NMS_RESP_G_YZ_RE, NMS_RESP_G_YZ_IM,
+    NMS_RESP_G_ZX_RE, NMS_RESP_G_ZX_IM, NMS_RESP_G_ZY_RE, NMS_RESP_G_ZY_IM,
+    NMS_RESP_G_ZZ_RE, NMS_RESP_G_ZZ_IM,
+    NMS_RESP_QX2, NMS_RESP_QY2, NMS_RESP_QZ2,
+    NMS_RESP_COUNT
+};
+
+/* Which part of the object decomposition a response is taken from. */
+enum { NMS_PART_TOTAL = 0, NMS_PART_DILUTE = 1, NMS_PART_INTERFERENCE = 2 };
+
+/* Evaluate one response on every pixel from the accumulated G (FP64).
+ * out: host or device [n_pixels] doubles, layout as the grid.  DILUTE and
+ * INTERFERENCE (= TOTAL - DILUTE) need want_dilute.  Errors: INVALID_ARG
+ * (id, part), BAD_STATE (no nms_amplitudes yet), UNSUPPORTED (dilute part
+ * without want_dilute). */
+nms_status nms_response(nms_plan_t plan, int32_t response_id, int32_t part,
+                        double* out, int32_t out_is_device);
+
+/* Azimuthal average of a per-pixel image of this plan's grid (paper,
+ * Eq. iqazi, trapezoidal rule).
+ *  POLAR grid:  nbins must equal n0 and bin_edges may be NULL; Iq[i] is the
+ *               mean over theta_j (the periodic trapezoid), counts[i] = n1,
+ *               qmean[i] = q_i.
+ *  CARTESIAN/LIST: bin b collects pixels with edges[b] <= |q| < edges[b+1]
+ *               (bin_edges host [nbins+1], increasing); Iq[b] = their mean,
+ *               counts[b] = their number, qmean[b] = their mean |q|; empty
+ *               bins give NaN in Iq and qmean.
+ * img: [n_pixels] doubles, host or device per img_is_device.  Iq, counts,
+ * qmean (qmean may be NULL): host or device per out_is_device.  Synchronous. */
+nms_status nms_azimuthal_average(nms_plan_t plan, const double* img, int32_t img_is_device,
+                                 int32_t nbins, const double* bin_edges,
+                                 double* Iq, int64_t* counts, double* qmean,
+                                 int32_t out_is_device);
+
+/* Correlation and pair-distance distribution functions (paper, Eqs. crrad
+ * and prrad): c(r_m) = prefactor * trapz_i [ I(q_i) j0(q_i r_m) q_i^2 ],
+ * p(r_m) = r_m^2 c(r_m), trapezoid over the nodes in the given order with
+ * non-finite (q_i, I_i) nodes dropped; j0(0) = 1.  The printed prefactor is
+ * 1/(2 pi^2); pass 0 to get it.  All arrays host or device per is_device
+ * (c_r or p_r may be NULL).  cuda_stream as in nms_plan_create.
+ * Synchronous. */
+nms_status nms_correlation(int32_t nq, const double* q, const double* Iq, int32_t nr,
+                           const double* r, double prefactor, double* c_r, double* p_r,
+                           int32_t is_device, void* cuda_stream);
+
+/* Per-stage device times in milliseconds, summed over all nms_amplitudes
+ * calls since the plan was created or the last reset (needs opt.timing=1):
+ * stage 0 = rotation/weights, 1 = phase tables, 2 = tensor-core GEMM,
+ * 3 = direct sum, 4 = promotion/reduction of partials, 5 = G accumulation.
+ * launches[s] counts the kernel launches of stage s.  Synchronises. */
+nms_status nms_plan_stage_ms(nms_plan_t plan, double ms[8], int64_t launches[8], int32_t reset);
+
+/* Release every device resource of the plan.  NULL is accepted. */
+nms_status nms_plan_destroy(nms_plan_t plan);
+
+/* Thread-local text of the last failure in this thread ("" if none). */
+const char* nms_last_error(void);
+
+/* Library version, e.g. "nms 0.1.0 sm_103a". */
+const char* nms_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NMS_H */

@@ -19,7 +19,8 @@ Steps and the passages they follow (paper section / equation):
                     ChiralSANS, NMdef, POLARIS and SANSPOL definitions, the
                     unpolarized average (Sec. "Unpolarized SANS cross
                     sections") and the cross spectra G_ab of Sec. "Fourier and
-                    real-space output data".  Prefactor 8 pi^3/V times the
+                    real-space output data" (reported with the same 1/V
+                    prefactor as the cross sections, like |Q_a|^2).  Prefactor 8 pi^3/V times the
                     (2 pi)^{-3} of the DSFT gives 1/V on the raw sums.
   dilute/total      Sec. "Summation approach", the interparticle
                     decomposition (form factor sum vs full amplitude).
@@ -228,11 +229,11 @@ def responses(F, hy, hz, P=(0.0, 0.0, 1.0), b_H=1.0, V=1.0):
     names = "XYZ"
     for a in range(3):
         for b in range(3):
-            g = FM[a] * np.conj(FM[b])
+            g = s * FM[a] * np.conj(FM[b])
             out[f"G_{names[a]}{names[b]}_RE"] = np.real(g)
             out[f"G_{names[a]}{names[b]}_IM"] = np.imag(g)
     for a in range(3):
-        out[f"Q{names[a]}2"] = np.abs(Q[a]) ** 2
+        out[f"Q{names[a]}2"] = s * np.abs(Q[a]) ** 2
     return out
 
 

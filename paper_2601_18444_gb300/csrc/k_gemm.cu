@@ -1,0 +1,717 @@
+// Tensor-core path: the Fourier sum on a separable (Cartesian) detector grid
+// as a split-FP16 complex GEMM on tcgen05 (sm_103a).
+//
+// Paper, Sec. "Summation approach": F_c(q) = sum_j w_cj exp(-i q.r_j).  On the
+// detector plane q = (0, q_y, q_z) the phase separates,
+//   exp(-i (q_y Y + q_z Z)) = exp(-i q_y Y) exp(-i q_z Z),
+// so with m = 4a + c (q_y index a, channel c), n = 2b + r (q_z index b,
+// r = Re/Im) and k = 2j + p (cell j, p = cos/sin part)
+//   A[m, 2j]   = w_cj cos(q_y,a Y_j)      A[m, 2j+1]   = w_cj sin(q_y,a Y_j)
+//   B[2b, 2j]  = cos(q_z,b Z_j)           B[2b, 2j+1]  = -sin(q_z,b Z_j)
+//   B[2b+1,2j] = -sin(q_z,b Z_j)          B[2b+1,2j+1] = -cos(q_z,b Z_j)
+//   D = A B^T:  D[4a+c, 2b] = Re F_c(a, b),  D[4a+c, 2b+1] = Im F_c(a, b).
+//
+// Precision (GB300-specific choice): each operand x (scaled by a power of two
+// to |x| <= 2^12) is split x = hi + lo with hi = fp16(x), lo = fp16(x - hi);
+// three kind::f16 MMAs per K step give hi*hi (accumulator D0) and
+// hi*lo + lo*hi (accumulator D1), a per-product error of ~3 * 2^-22 -- the
+// precision of TF32x3 at the FP16 tensor rate.  FP32 accumulation in TMEM is
+// limited to kc cells at a time: the accumulators are double-buffered and
+// drained by 16 epilogue warps into two-float (hi, lo) registers.
+//
+// Phase tables use the two-float phase in turns t = q'.r (q' = q/2 pi) with
+// the exact reduction t - rint(t), then sincospif.  Tables are written in the
+// canonical K-major 128-byte-swizzled UMMA layout, 16 KB per (tile, k-block),
+// so the GEMM moves them with plain 1D bulk copies (cp.async.bulk).
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "nms_internal.h"
+
+namespace nms {
+
+constexpr int TC_BM = 128;          // rows of A per tile (32 q_y values x 4 channels)
+constexpr int TC_BN = 128;          // rows of B per tile (64 q_z values x Re/Im)
+constexpr int TC_BK = 64;           // k per block (32 cells), one 128-byte swizzle row
+constexpr int TC_BLOCK_BYTES = TC_BM * TC_BK * 2;   // 16 KB
+constexpr int TC_STAGES = 3;
+constexpr int TC_STAGE_BYTES = 4 * TC_BLOCK_BYTES;  // A_hi, A_lo, B_hi, B_lo
+constexpr int TC_THREADS = 576;     // warp 0 producer, warp 1 MMA, warps 2..17 epilogue
+constexpr int TC_EPI_WARPS = 16;    // 4 per TMEM lane quadrant, 32 accumulator columns each
+constexpr float TC_SCALE = 4096.0f; // operand scale 2^12
+
+// ------------------------------------------------------------------ tables
+__device__ __forceinline__ uint32_t swz_offset(int row, int k)
+{
+    // byte offset of element (row, k) of a 128 x 64 fp16 block, 128B swizzle
+    return (uint32_t)row * 128u + ((uint32_t)(((k >> 3) ^ (row & 7))) << 4) + (uint32_t)(k & 7) * 2u;
+}
+
+__device__ __forceinline__ void split_h(float x, __half& h, __half& l)
+{
+    h = __float2half_rn(x);
+    l = __float2half_rn(x - __half2float(h));
+}
+
+__device__ __forceinline__ float turns_reduced(float2 q, float4 c, bool use_z)
+{
+    // two-float product q' * coordinate (turns) reduced to [-1/2, 1/2]
+    float xh = use_z ? c.z : c.x;
+    float xl = use_z ? c.w : c.y;
+    float p = q.x * xh;
+    float e = fmaf(q.x, xh, -p) + fmaf(q.x, xl, q.y * xh);
+    float n = rintf(p);
+    return (p - n) + e;
+}
+
+union H8 {
+    uint4 v;
+    __half h[8];
+};
+
+// A tables: block (mt, kb) holds rows m = mt*128 + 4*a_loc + c, a_loc < 32,
+// and k = 64 kb + 2 j_loc + p.  Thread (a_loc, chunk): 4 cells x 4 channels.
+__global__ void __launch_bounds__(256)
+k_tables_a(const float4* __restrict__ cpos, const float4* __restrict__ cw, int64_t j0, int64_t ncell,
+           const float2* __restrict__ qy, int ny, float4 wscale, int64_t nkb, uint8_t* __restrict__ A_hi,
+           uint8_t* __restrict__ A_lo)
+{
+    const int kb = blockIdx.x;
+    const int mt = blockIdx.y;
+    const int a_loc = threadIdx.x >> 3;
+    const int chunk = threadIdx.x & 7;
+    const int a = mt * 32 + a_loc;
+    H8 hi[4], lo[4];
+    const bool arow = a < ny;
+    const float2 q = arow ? qy[a] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t jl = (int64_t)kb * 32 + chunk * 4 + u;
+        float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+        float sn = 0.f, cs = 0.f;
+        if (arow && jl < ncell) {
+            const float4 c = cpos[j0 + jl];
+            w = cw[j0 + jl];
+            float t = turns_reduced(q, c, false);
+            sincospif(2.0f * t, &sn, &cs);
+        }
+        const float wv[4] = {w.x * wscale.x, w.y * wscale.y, w.z * wscale.z, w.w * wscale.w};
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) {
+            split_h(wv[ch] * cs, hi[ch].h[2 * u], lo[ch].h[2 * u]);
+            split_h(wv[ch] * sn, hi[ch].h[2 * u + 1], lo[ch].h[2 * u + 1]);
+        }
+    }
+    const size_t blk = ((size_t)mt * nkb + kb) * TC_BLOCK_BYTES;
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+        const int row = 4 * a_loc + ch;
+        const uint32_t off = swz_offset(row, chunk * 8);
+        *reinterpret_cast<uint4*>(A_hi + blk + off) = hi[ch].v;
+        *reinterpret_cast<uint4*>(A_lo + blk + off) = lo[ch].v;
+    }
+}
+
+// B tables: block (nt, kb) holds rows n = nt*128 + 2*b_loc + r, b_loc < 64.
+__global__ void __launch_bounds__(512)
+k_tables_b(const float4* __restrict__ cpos, int64_t j0, int64_t ncell, const float2* __restrict__ qz, int nz,
+           int64_t nkb, uint8_t* __restrict__ B_hi, uint8_t* __restrict__ B_lo)
+{
+    const int kb = blockIdx.x;
+    const int nt = blockIdx.y;
+    const int b_loc = threadIdx.x >> 3;
+    const int chunk = threadIdx.x & 7;
+    const int b = nt * 64 + b_loc;
+    const bool brow = b < nz;
+    const float2 q = brow ? qz[b] : make_float2(0.f, 0.f);
+    H8 hr, lr, hi_, li_;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int64_t jl = (int64_t)kb * 32 + chunk * 4 + u;
+        float sn = 0.f, cs = 0.f;
+        if (brow && jl < ncell) {
+            const float4 c = cpos[j0 + jl];
+            float t = turns_reduced(q, c, true);
+            sincospif(2.0f * t, &sn, &cs);
+        }
+        cs *= TC_SCALE;
+        sn *= TC_SCALE;
+        split_h(cs, hr.h[2 * u], lr.h[2 * u]);          // Re row: ( cos, -sin)
+        split_h(-sn, hr.h[2 * u + 1], lr.h[2 * u + 1]);
+        split_h(-sn, hi_.h[2 * u], li_.h[2 * u]);       // Im row: (-sin, -cos)
+        split_h(-cs, hi_.h[2 * u + 1], li_.h[2 * u + 1]);
+    }
+    const size_t blk = ((size_t)nt * nkb + kb) * TC_BLOCK_BYTES;
+    const uint32_t o0 = swz_offset(2 * b_loc, chunk * 8);
+    const uint32_t o1 = swz_offset(2 * b_loc + 1, chunk * 8);
+    *reinterpret_cast<uint4*>(B_hi + blk + o0) = hr.v;
+    *reinterpret_cast<uint4*>(B_lo + blk + o0) = lr.v;
+    *reinterpret_cast<uint4*>(B_hi + blk + o1) = hi_.v;
+    *reinterpret_cast<uint4*>(B_lo + blk + o1) = li_.v;
+}
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after limit_ns or when another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
+                                          volatile int* abort_flag)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                           uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v)
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v)
+{
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Packed FP32x2 arithmetic (sm_100+): two lanes of a 64-bit register, RN.
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ uint64_t f2_pack(float lo_lane, float hi_lane)
+{
+    return ((uint64_t)__float_as_uint(hi_lane) << 32) | (uint64_t)__float_as_uint(lo_lane);
+}
+
+__device__ __forceinline__ float f2_lane0(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float f2_lane1(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// K-major, 128B-swizzled shared-memory matrix descriptor (tcgen05 format):
+// start >> 4 in [0,14), leading byte offset >> 4 in [16,30) (unused for
+// swizzled K-major), stride byte offset >> 4 in [32,46) = 1024 B between
+// 8-row groups, fixed 0b01 in [46,48), swizzle mode 2 (128B) in [61,64).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1u << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)2u << 61;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: D F32 (bits 4-5 = 1), A and B F16
+// (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0), N >> 3 in bits
+// 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ------------------------------------------------------------------ GEMM
+struct GemmArgs {
+    const uint8_t* A_hi;
+    const uint8_t* A_lo;
+    const uint8_t* B_hi;
+    const uint8_t* B_lo;
+    int64_t nkb;          // k-blocks in the tables of this launch
+    int mtiles, ntiles;
+    int splits;           // K splits (gridDim.z)
+    int kcb;              // k-blocks per TMEM chunk (drain interval)
+    double* P;            // [splits][mtiles*128][ntiles*128] partial sums (FP64)
+    int32_t* err;
+    uint64_t limit_ns;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bar_full[TC_STAGES];
+    __shared__ __align__(8) uint64_t bar_empty[TC_STAGES];
+    __shared__ __align__(8) uint64_t bar_acc_full[2];
+    __shared__ __align__(8) uint64_t bar_acc_empty[2];
+    __shared__ __align__(8) uint64_t bar_final;
+    __shared__ uint32_t s_taddr;
+    __shared__ volatile int s_abort;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nt = blockIdx.x, mt = blockIdx.y, sp = blockIdx.z;
+    // this CTA's k-block range
+    const int64_t kb0 = (g.nkb * sp) / g.splits;
+    const int64_t kb1 = (g.nkb * (sp + 1)) / g.splits;
+    const int nkb_me = (int)(kb1 - kb0);
+    const int nchunks = (nkb_me + g.kcb - 1) / g.kcb;
+
+    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&bar_full[s], 1);
+            mbar_init(&bar_empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bar_acc_full[b], 1);
+            mbar_init(&bar_acc_empty[b], TC_EPI_WARPS);
+        }
+        mbar_init(&bar_final, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = s_taddr;
+
+    if (warp == 0) {
+        // ---------------- producer: bulk copies of the four operand blocks
+        if (lane == 0) {
+            int64_t issued = 0;
+            for (int64_t i = 0; i < nkb_me; ++i) {
+                const int s = (int)(i % TC_STAGES);
+                const uint32_t par = (uint32_t)((i / TC_STAGES) & 1) ^ 1u;
+                if (!mbar_wait(&bar_empty[s], par, g.limit_ns, &s_abort)) {
+                    s_abort = 1;
+                    atomicExch(g.err, 1);
+                    break;
+                }
+                const int64_t kb = kb0 + i;
+                const uint32_t st = sbase + (uint32_t)s * TC_STAGE_BYTES;
+                mbar_arrive_expect_tx(&bar_full[s], TC_STAGE_BYTES);
+                const size_t ao = ((size_t)mt * g.nkb + kb) * TC_BLOCK_BYTES;
+                const size_t bo = ((size_t)nt * g.nkb + kb) * TC_BLOCK_BYTES;
+                bulk_g2s(st, g.A_hi + ao, TC_BLOCK_BYTES, &bar_full[s]);
+                bulk_g2s(st + TC_BLOCK_BYTES, g.A_lo + ao, TC_BLOCK_BYTES, &bar_full[s]);
+                bulk_g2s(st + 2 * TC_BLOCK_BYTES, g.B_hi + bo, TC_BLOCK_BYTES, &bar_full[s]);
+                bulk_g2s(st + 3 * TC_BLOCK_BYTES, g.B_lo + bo, TC_BLOCK_BYTES, &bar_full[s]);
+                ++issued;
+            }
+            // copies in flight must land before the CTA exits (bounded): only
+            // the last TC_STAGES issued stages can still be pending
+            for (int64_t i = (issued > TC_STAGES ? issued - TC_STAGES : 0); i < issued; ++i) {
+                const int s = (int)(i % TC_STAGES);
+                const uint32_t par = (uint32_t)((i / TC_STAGES) & 1);
+                mbar_wait(&bar_full[s], par, g.limit_ns, &s_abort);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16_f32(TC_BM, TC_BN);
+            int i = 0;
+            bool ok = true;
+            for (int c = 0; c < nchunks && ok; ++c) {
+                const int b = (int)(c & 1);
+                const uint32_t apar = (uint32_t)((c >> 1) & 1) ^ 1u;
+                if (!mbar_wait(&bar_acc_empty[b], apar, g.limit_ns, &s_abort)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d0 = taddr + (uint32_t)b * 256u;
+                const uint32_t d1 = d0 + 128u;
+                const int kend = (c + 1) * g.kcb < nkb_me ? (c + 1) * g.kcb : nkb_me;
+                bool first = true;
+                for (; i < kend; ++i) {
+                    const int s = (int)(i % TC_STAGES);
+                    const uint32_t par = (uint32_t)((i / TC_STAGES) & 1);
+                    if (!mbar_wait(&bar_full[s], par, g.limit_ns, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = sbase + (uint32_t)s * TC_STAGE_BYTES;
+#pragma unroll
+                    for (int k16 = 0; k16 < 4; ++k16) {
+                        const uint64_t ah = sw128_desc(st + k16 * 32);
+                        const uint64_t al = sw128_desc(st + TC_BLOCK_BYTES + k16 * 32);
+                        const uint64_t bh = sw128_desc(st + 2 * TC_BLOCK_BYTES + k16 * 32);
+                        const uint64_t bl = sw128_desc(st + 3 * TC_BLOCK_BYTES + k16 * 32);
+                        const uint32_t acc = first ? 0u : 1u;
+                        tc_mma_f16(d0, ah, bh, idesc, acc);
+                        tc_mma_f16(d1, ah, bl, idesc, acc);
+                        tc_mma_f16(d1, al, bh, idesc, 1u);
+                        first = false;
+                    }
+                    tc_commit(&bar_empty[s]);
+                }
+                if (!ok) break;
+                tc_commit(&bar_acc_full[b]);
+            }
+            if (!ok) {
+                s_abort = 1;
+                atomicExch(g.err, 2);
+            }
+            // all MMAs issued by this thread complete before TMEM is freed
+            tc_commit(&bar_final);
+            mbar_wait(&bar_final, 0, g.limit_ns, &s_abort);
+        }
+    } else {
+        // ---------------- epilogue: drain TMEM chunks into two-float sums
+        const int e = warp - 2;
+        const int quad = warp & 3;                 // TMEM lane quadrant of this warp
+        const int colh = (e >> 2) * 32;            // column quarter
+        // two-float running sums, two columns per 64-bit register
+        uint64_t hi[16], lo[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) { hi[i] = 0ull; lo[i] = 0ull; }
+        for (int c = 0; c < nchunks; ++c) {
+            const int b = (int)(c & 1);
+            const uint32_t par = (uint32_t)((c >> 1) & 1);
+            int okw = 0;
+            if (lane == 0) okw = mbar_wait(&bar_acc_full[b], par, g.limit_ns, &s_abort) ? 1 : 0;
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            if (!okw) {
+                if (lane == 0) {
+                    s_abort = 1;
+                    atomicExch(g.err, 3);
+                }
+                break;
+            }
+            tc_fence_after();
+            const uint32_t base = taddr + ((uint32_t)(quad * 32) << 16) + (uint32_t)b * 256u + (uint32_t)colh;
+#pragma unroll
+            for (int cb = 0; cb < 8; ++cb) {
+                float v0[4], v1[4];
+                tmem_ld4(base + cb * 4, v0);
+                tmem_ld4(base + 128 + cb * 4, v1);
+                tmem_wait_ld();
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int idx = cb * 2 + u;
+                    // x = D0 + D1; TwoSum(hi, x) -> (s, er); hi = s; lo += er
+                    const uint64_t x = f2_add(f2_pack(v0[2 * u], v0[2 * u + 1]), f2_pack(v1[2 * u], v1[2 * u + 1]));
+                    const uint64_t sm = f2_add(hi[idx], x);
+                    const uint64_t bb = f2_sub(sm, hi[idx]);
+                    const uint64_t er = f2_add(f2_sub(hi[idx], f2_sub(sm, bb)), f2_sub(x, bb));
+                    hi[idx] = sm;
+                    lo[idx] = f2_add(lo[idx], er);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_acc_empty[b]);
+        }
+        // partial sums of this split, unscaled, FP64
+        const int64_t ldn = (int64_t)g.ntiles * TC_BN;
+        const int64_t row = (int64_t)mt * TC_BM + quad * 32 + lane;
+        double* out = g.P + ((int64_t)sp * g.mtiles * TC_BM + row) * ldn + (int64_t)nt * TC_BN + colh;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            double2 v = make_double2((double)f2_lane0(hi[i]) + (double)f2_lane0(lo[i]),
+                                     (double)f2_lane1(hi[i]) + (double)f2_lane1(lo[i]));
+            reinterpret_cast<double2*>(out)[i] = v;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(512) : "memory");
+    }
+}
+
+// F[c][p][r] += scale_c * sum_s P[s][4a + c][2b + r], p = a*nz + b
+struct Scale4 {
+    double v[4];
+};
+
+__global__ void k_gemm_reduce(const double* __restrict__ P, int splits, int64_t ldm, int64_t ldn, int ny, int nz,
+                              Scale4 scale, double* __restrict__ F)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t npix = (int64_t)ny * nz;
+    if (idx >= npix * 4) return;
+    const int c = (int)(idx / npix);
+    const int64_t p = idx % npix;
+    const int a = (int)(p / nz), b = (int)(p % nz);
+    const int64_t m = 4 * a + c;
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < splits; ++s) {
+        const double2 v = *reinterpret_cast<const double2*>(P + ((int64_t)s * ldm + m) * ldn + 2 * b);
+        re += v.x;
+        im += v.y;
+    }
+    const double sc = scale.v[c];
+    double2* o = reinterpret_cast<double2*>(F) + (int64_t)c * npix + p;
+    double2 t = *o;
+    t.x += sc * re;
+    t.y += sc * im;
+    *o = t;
+}
+
+// ------------------------------------------------------------------ host side
+struct TcState {
+    int ny = 0, nz = 0, mtiles = 0, ntiles = 0;
+    int64_t kt_cells = 0;     // cells per table chunk
+    int64_t nkb_max = 0;
+    float2* d_qy = nullptr;
+    float2* d_qz = nullptr;
+    double* d_P = nullptr;
+    int max_splits = 1;
+    double W[4] = {1, 1, 1, 1};   // power-of-two weight bounds per channel
+    bool attr_set = false;
+};
+
+static double pow2_ceil(double x)
+{
+    if (!(x > 0)) return 1.0;
+    int e;
+    frexp(x, &e);          // x = f 2^e, f in [0.5, 1)
+    double r = ldexp(1.0, e);
+    if (r / 2 >= x) r /= 2;
+    return r;
+}
+
+nms_status tc_setup(Plan& p)
+{
+    if (p.grid.kind != NMS_QGRID_CARTESIAN) {
+        set_error("tensor-core path needs a CARTESIAN grid");
+        return NMS_ERR_INVALID_ARG;
+    }
+    TcState* t = new TcState();
+    p.tc_state = t;
+    t->ny = p.grid.n0;
+    t->nz = p.grid.n1;
+    t->mtiles = (4 * t->ny + TC_BM - 1) / TC_BM;
+    t->ntiles = (2 * t->nz + TC_BN - 1) / TC_BN;
+    // q' = q / 2 pi as two-float, per axis
+    std::vector<float2> qy(t->ny), qz(t->nz);
+    const double two_pi = 2.0 * M_PI;
+    auto lin = [](int64_t a, int64_t n, double lo, double hi) {
+        return n == 1 ? lo : lo + ((hi - lo) * (double)a) / (double)(n - 1);
+    };
+    for (int a = 0; a < t->ny; ++a) {
+        double v = lin(a, t->ny, p.grid.lo0, p.grid.hi0) / two_pi;
+        float h = (float)v;
+        qy[a] = make_float2(h, (float)(v - (double)h));
+    }
+    for (int b = 0; b < t->nz; ++b) {
+        double v = lin(b, t->nz, p.grid.lo1, p.grid.hi1) / two_pi;
+        float h = (float)v;
+        qz[b] = make_float2(h, (float)(v - (double)h));
+    }
+    NMS_CUDA_TRY(cudaMalloc(&t->d_qy, t->ny * sizeof(float2)));
+    NMS_CUDA_TRY(cudaMalloc(&t->d_qz, t->nz * sizeof(float2)));
+    NMS_CUDA_TRY(cudaMemcpy(t->d_qy, qy.data(), t->ny * sizeof(float2), cudaMemcpyHostToDevice));
+    NMS_CUDA_TRY(cudaMemcpy(t->d_qz, qz.data(), t->nz * sizeof(float2), cudaMemcpyHostToDevice));
+    // weight bounds: rotation-invariant max_j V_j |N_j| and max_j V_j |M_j|
+    t->W[0] = pow2_ceil(p.h_wmax[0]);
+    t->W[1] = t->W[2] = t->W[3] = pow2_ceil(p.h_wmax[1]);
+    // table chunk: as many cells as the workspace allows (largest object if objects are summed separately)
+    const int64_t per_cell = (int64_t)(t->mtiles * TC_BM + t->ntiles * TC_BN) * 2 * 2 * 2;
+    int64_t need_cells = p.max_sum_cells;
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    int64_t budget = p.opt.workspace_bytes > 0 ? p.opt.workspace_bytes : (int64_t)std::min<size_t>(free_b / 3, (size_t)48 << 30);
+    int64_t cells = std::max<int64_t>(32, std::min<int64_t>(need_cells, budget / per_cell));
+    cells = (cells + 31) / 32 * 32;
+    t->kt_cells = cells;
+    t->nkb_max = cells / 32;
+    const size_t tab = (size_t)t->nkb_max * (t->mtiles + t->ntiles) * 2 * TC_BLOCK_BYTES;
+    NMS_CUDA_TRY(cudaMalloc(&p.d_tab, tab));
+    p.tab_bytes = tab;
+    // split partials: up to 512 MB
+    const int64_t tile_elems = (int64_t)t->mtiles * TC_BM * t->ntiles * TC_BN;
+    t->max_splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, (512ll << 20) / (tile_elems * 8)));
+    NMS_CUDA_TRY(cudaMalloc(&t->d_P, (size_t)t->max_splits * tile_elems * 8));
+    const int smem = TC_STAGES * TC_STAGE_BYTES + 1024;
+    NMS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    return NMS_OK;
+}
+
+void tc_release(Plan& p)
+{
+    TcState* t = (TcState*)p.tc_state;
+    if (!t) return;
+    if (t->d_qy) cudaFree(t->d_qy);
+    if (t->d_qz) cudaFree(t->d_qz);
+    if (t->d_P) cudaFree(t->d_P);
+    delete t;
+    p.tc_state = nullptr;
+}
+
+nms_status tc_run(Plan& p, const float4* cpos, int64_t c0, int64_t c1, double* Fout, cudaStream_t s)
+{
+    TcState* t = (TcState*)p.tc_state;
+    NMS_CUDA_TRY(cudaMemsetAsync(Fout, 0, 8 * p.npix * sizeof(double), s));
+    const int sms = device_sm_count();
+    const int tiles = t->mtiles * t->ntiles;
+    int kcb = p.opt.kc_cells > 0 ? std::max(1, p.opt.kc_cells / 32) : 2;
+    const float4 wscale = make_float4((float)(TC_SCALE / t->W[0]), (float)(TC_SCALE / t->W[1]),
+                                      (float)(TC_SCALE / t->W[2]), (float)(TC_SCALE / t->W[3]));
+    const double inv = 1.0 / ((double)TC_SCALE * (double)TC_SCALE);
+    Scale4 scale;
+    for (int c = 0; c < 4; ++c) scale.v[c] = t->W[c] * inv;
+    const uint64_t limit = p.opt.max_spin > 0 ? (uint64_t)p.opt.max_spin * 1000ull : 4000000000ull;
+    for (int64_t j0 = c0; j0 < c1; j0 += t->kt_cells) {
+        const int64_t nc = std::min<int64_t>(t->kt_cells, c1 - j0);
+        const int64_t nkb = (nc + 31) / 32;
+        uint8_t* base = (uint8_t*)p.d_tab;
+        const size_t asz = (size_t)t->mtiles * nkb * TC_BLOCK_BYTES;
+        const size_t bsz = (size_t)t->ntiles * nkb * TC_BLOCK_BYTES;
+        uint8_t* A_hi = base;
+        uint8_t* A_lo = A_hi + asz;
+        uint8_t* B_hi = A_lo + asz;
+        uint8_t* B_lo = B_hi + bsz;
+        p.timer.begin(ST_TABLES);
+        k_tables_a<<<dim3((unsigned)nkb, (unsigned)t->mtiles), 256, 0, s>>>(cpos, p.d_cw, j0, nc, t->d_qy, t->ny,
+                                                                              wscale, nkb, A_hi, A_lo);
+        k_tables_b<<<dim3((unsigned)nkb, (unsigned)t->ntiles), 512, 0, s>>>(cpos, j0, nc, t->d_qz, t->nz, nkb,
+                                                                              B_hi, B_lo);
+        NMS_CUDA_TRY(cudaGetLastError());
+        p.timer.end(ST_TABLES, 2);
+        int splits = p.opt.split_k;
+        if (splits <= 0) {
+            // fewest K splits whose CTA count fills whole waves of the SMs
+            auto eff = [&](int sp) {
+                const int64_t n = (int64_t)tiles * sp;
+                const int64_t w = (n + sms - 1) / sms;
+                return (double)n / (double)(w * sms);
+            };
+            const int lim = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)t->max_splits, nkb));
+            splits = 1;
+            double be = eff(1);
+            for (int sp = 2; sp <= lim && be < 0.97; ++sp) {
+                const double e = eff(sp);
+                if (e > be + 1e-9) { be = e; splits = sp; }
+            }
+        }
+        splits = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)splits, (int64_t)t->max_splits, nkb}));
+        GemmArgs ga;
+        ga.A_hi = A_hi; ga.A_lo = A_lo; ga.B_hi = B_hi; ga.B_lo = B_lo;
+        ga.nkb = nkb; ga.mtiles = t->mtiles; ga.ntiles = t->ntiles; ga.splits = splits; ga.kcb = kcb;
+        ga.P = t->d_P; ga.err = p.d_err; ga.limit_ns = limit;
+        p.timer.begin(ST_GEMM);
+        k_gemm_f16x3<<<dim3(t->ntiles, t->mtiles, splits), TC_THREADS, TC_STAGES * TC_STAGE_BYTES + 1024, s>>>(ga);
+        NMS_CUDA_TRY(cudaGetLastError());
+        p.timer.end(ST_GEMM, 1);
+        p.timer.begin(ST_REDUCE);
+        const int64_t n = 4 * p.npix;
+        k_gemm_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t->d_P, splits, (int64_t)t->mtiles * TC_BM,
+                                                                  (int64_t)t->ntiles * TC_BN, t->ny, t->nz, scale,
+                                                                  Fout);
+        NMS_CUDA_TRY(cudaGetLastError());
+        p.timer.end(ST_REDUCE, 1);
+    }
+    return NMS_OK;
+}
+
+}  // namespace nms

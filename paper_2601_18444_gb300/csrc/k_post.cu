@@ -1,0 +1,177 @@
+// Azimuthal averages (paper, Eq. iqazi) and correlation functions
+// (Eqs. crrad, prrad).  Both are small, HBM-bound reductions over the
+// detector image; the kernels read each pixel once.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "nms_internal.h"
+
+namespace nms {
+
+// ------------------------------------------------------------ cartesian rings
+// Bin b holds pixels with edges[b] <= |q| < edges[b+1].  Each block bins its
+// pixels in shared memory first, then adds its per-bin totals to global
+// memory once (FP64 atomics), so contention scales with blocks, not pixels.
+constexpr int AZI_THREADS = 256;
+constexpr int AZI_SMEM_BINS = 1024;
+
+__device__ __forceinline__ int find_bin(const double* __restrict__ e, int nb, double x)
+{
+    if (!(x >= e[0]) || !(x < e[nb])) return -1;
+    int lo = 0, hi = nb;  // e[lo] <= x < e[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (x >= e[mid]) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_azimuthal_cart(const double* __restrict__ img, const double* __restrict__ qa, int64_t npix,
+                                 const double* __restrict__ edges, int nbins, double* __restrict__ sum,
+                                 unsigned long long* __restrict__ cnt, double* __restrict__ qsum)
+{
+    __shared__ double s_sum[AZI_SMEM_BINS];
+    __shared__ double s_q[AZI_SMEM_BINS];
+    __shared__ unsigned int s_cnt[AZI_SMEM_BINS];
+    const bool local = nbins <= AZI_SMEM_BINS;
+    if (local) {
+        for (int b = threadIdx.x; b < nbins; b += blockDim.x) { s_sum[b] = 0.0; s_q[b] = 0.0; s_cnt[b] = 0u; }
+        __syncthreads();
+    }
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+        double x = qa[p];
+        int b = find_bin(edges, nbins, x);
+        if (b < 0) continue;
+        if (local) {
+            atomicAdd(&s_sum[b], img[p]);
+            atomicAdd(&s_q[b], x);
+            atomicAdd(&s_cnt[b], 1u);
+        } else {
+            atomicAdd(&sum[b], img[p]);
+            atomicAdd(&qsum[b], x);
+            atomicAdd(&cnt[b], 1ull);
+        }
+    }
+    if (local) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+            if (s_cnt[b]) {
+                atomicAdd(&sum[b], s_sum[b]);
+                atomicAdd(&qsum[b], s_q[b]);
+                atomicAdd(&cnt[b], (unsigned long long)s_cnt[b]);
+            }
+    }
+}
+
+cudaError_t launch_azimuthal_cart(const Plan& p, const double* img, int nbins, const double* d_edges, double* d_sum,
+                                  unsigned long long* d_cnt, double* d_qsum, cudaStream_t s)
+{
+    int64_t blocks = (p.npix + AZI_THREADS * 8 - 1) / (AZI_THREADS * 8);
+    int cap = 4 * device_sm_count();
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_azimuthal_cart<<<(unsigned)blocks, AZI_THREADS, 0, s>>>(img, p.d_qa, p.npix, d_edges, nbins, d_sum, d_cnt,
+                                                              d_qsum);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ polar grid
+// Periodic trapezoid over theta_j = 2 pi j / n_theta equals the mean over j.
+__global__ void k_azimuthal_polar(const double* __restrict__ img, int n0, int n1, double* __restrict__ Iq)
+{
+    __shared__ double red[256];
+    int i = blockIdx.x;
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < n1; j += blockDim.x) acc += img[(int64_t)i * n1 + j];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) Iq[i] = red[0] / (double)n1;
+}
+
+cudaError_t launch_azimuthal_polar(const Plan& p, const double* img, double* Iq, cudaStream_t s)
+{
+    k_azimuthal_polar<<<p.grid.n0, 256, 0, s>>>(img, p.grid.n0, p.grid.n1, Iq);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ correlation
+// Compaction of the finite nodes (one block, order preserving), then one
+// block per r_m sums the trapezoids I j0(q r) q^2.
+__global__ void k_corr_compact(int nq, const double* __restrict__ q, const double* __restrict__ I,
+                               double* __restrict__ qo, double* __restrict__ Io, int* __restrict__ nout)
+{
+    __shared__ int s_base;
+    __shared__ int s_scan[1024];
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    for (int start = 0; start < nq; start += blockDim.x) {
+        int i = start + threadIdx.x;
+        int ok = (i < nq) && isfinite(q[i]) && isfinite(I[i]);
+        s_scan[threadIdx.x] = ok;
+        __syncthreads();
+        // inclusive Hillis-Steele scan
+        for (int off = 1; off < blockDim.x; off <<= 1) {
+            int v = (threadIdx.x >= off) ? s_scan[threadIdx.x - off] : 0;
+            __syncthreads();
+            s_scan[threadIdx.x] += v;
+            __syncthreads();
+        }
+        if (ok) {
+            int dst = s_base + s_scan[threadIdx.x] - 1;
+            qo[dst] = q[i];
+            Io[dst] = I[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_base += s_scan[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *nout = s_base;
+}
+
+__device__ __forceinline__ double j0_sph(double x)
+{
+    return x == 0.0 ? 1.0 : sin(x) / x;
+}
+
+__global__ void k_corr(const double* __restrict__ q, const double* __restrict__ I, const int* __restrict__ nvalid,
+                       const double* __restrict__ r, double pref, double* __restrict__ c, double* __restrict__ pr)
+{
+    __shared__ double red[256];
+    const int m = blockIdx.x;
+    const int n = *nvalid;
+    const double rm = r[m];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i + 1 < n; i += blockDim.x) {
+        double q0 = q[i], q1 = q[i + 1];
+        double f0 = I[i] * j0_sph(q0 * rm) * q0 * q0;
+        double f1 = I[i + 1] * j0_sph(q1 * rm) * q1 * q1;
+        acc += 0.5 * (f0 + f1) * (q1 - q0);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double v = pref * red[0];
+        if (c) c[m] = v;
+        if (pr) pr[m] = rm * rm * v;
+    }
+}
+
+cudaError_t launch_correlation(int nq, const double* q, const double* Iq, int nr, const double* r, double pref,
+                               double* c, double* pr, double* sq, double* sf, int* sn, cudaStream_t s)
+{
+    k_corr_compact<<<1, 1024, 0, s>>>(nq, q, Iq, sq, sf, sn);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (nr > 0) k_corr<<<nr, 256, 0, s>>>(sq, sf, sn, r, pref, c, pr);
+    return cudaGetLastError();
+}
+
+}  // namespace nms

@@ -1,0 +1,654 @@
+// C ABI of libnms: plan creation, orchestration of the kernels, results.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "nms.h"
+#include "nms_internal.h"
+
+namespace nms {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+nms_status cuda_fail(cudaError_t e, const char* what)
+{
+    set_error(std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return NMS_ERR_OUT_OF_MEMORY;
+    return NMS_ERR_CUDA;
+}
+
+static nms_status fail(nms_status st, const std::string& msg)
+{
+    set_error(msg);
+    return st;
+}
+
+int device_sm_count()
+{
+    static thread_local int cached = 0;
+    if (!cached) {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+            cached = n;
+        else
+            cached = 148;
+    }
+    return cached;
+}
+
+// ------------------------------------------------------------ stage timer
+cudaEvent_t StageTimer::get_event()
+{
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void StageTimer::begin(int stage)
+{
+    if (!on) return;
+    open_stage = stage;
+    open_ev = get_event();
+    cudaEventRecord(open_ev, stream);
+}
+
+void StageTimer::end(int stage, int n_launch)
+{
+    launches[stage] += n_launch;
+    if (!on || open_stage != stage) return;
+    cudaEvent_t b = get_event();
+    cudaEventRecord(b, stream);
+    pending.push_back({stage, open_ev, b});
+    open_stage = -1;
+    open_ev = nullptr;
+    if (pending.size() > 4096) collect();
+}
+
+nms_status StageTimer::collect()
+{
+    for (auto& pe : pending) {
+        cudaError_t e = cudaEventSynchronize(pe.b);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        float t = 0.f;
+        cudaEventElapsedTime(&t, pe.a, pe.b);
+        ms[pe.stage] += t;
+        pool.push_back(pe.a);
+        pool.push_back(pe.b);
+    }
+    pending.clear();
+    return NMS_OK;
+}
+
+void StageTimer::release()
+{
+    for (auto& pe : pending) {
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+    }
+    pending.clear();
+    for (auto e : pool) cudaEventDestroy(e);
+    pool.clear();
+    if (open_ev) cudaEventDestroy(open_ev);
+    open_ev = nullptr;
+}
+
+// ------------------------------------------------------------ helpers
+template <class T>
+static nms_status dalloc(T** p, size_t count, const char* what)
+{
+    *p = nullptr;
+    if (count == 0) return NMS_OK;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? NMS_ERR_OUT_OF_MEMORY : NMS_ERR_CUDA,
+                    std::string("cudaMalloc failed for ") + what + ": " + cudaGetErrorString(e));
+    }
+    return NMS_OK;
+}
+
+static void dfree(void* p)
+{
+    if (p) cudaFree(p);
+}
+
+static void free_plan(nms_plan_s* p)
+{
+    if (!p) return;
+    void* bufs[] = {p->d_pos, p->d_vol, p->d_nuc, p->d_mag, p->d_cen_cell, p->d_qy, p->d_qz, p->d_hy,
+                    p->d_hz, p->d_qa, p->d_qturn, p->d_cpos, p->d_w64, p->d_cw, p->d_yz, p->d_F,
+                    p->d_Ftot, p->d_Fpart, p->d_Gtot, p->d_Gdil, p->d_err, p->d_tab, p->d_wscale};
+    for (void* b : bufs) dfree(b);
+    tc_release(*p);
+    if (p->d_cposl && p->d_cposl != p->d_cpos) dfree(p->d_cposl);
+    if (p->d_yzl && p->d_yzl != p->d_yz) dfree(p->d_yzl);
+    p->timer.release();
+    delete p;
+}
+
+// q-grid on the host in FP64.  The expression order of the linear spacing is
+// lo + ((hi - lo) * a) / (n - 1).
+static double lin_node(int64_t a, int64_t n, double lo, double hi)
+{
+    if (n == 1) return lo;
+    return lo + ((hi - lo) * (double)a) / (double)(n - 1);
+}
+
+static nms_status build_grid(Plan& p, const nms_qgrid& g)
+{
+    int64_t np = 0;
+    if (g.kind == NMS_QGRID_CARTESIAN || g.kind == NMS_QGRID_POLAR) {
+        if (g.n0 < 1 || g.n1 < 1) return fail(NMS_ERR_INVALID_ARG, "grid: n0 and n1 must be >= 1");
+        np = (int64_t)g.n0 * g.n1;
+    } else if (g.kind == NMS_QGRID_LIST) {
+        if (g.n0 < 1 || !g.qlist) return fail(NMS_ERR_INVALID_ARG, "grid: LIST needs n0 >= 1 and qlist");
+        np = g.n0;
+    } else {
+        return fail(NMS_ERR_INVALID_ARG, "grid: unknown kind");
+    }
+    std::vector<double> qy(np), qz(np), hy(np), hz(np), qa(np);
+    std::vector<float4> qt(np);
+    const double two_pi = 2.0 * M_PI;
+    for (int64_t i = 0; i < np; ++i) {
+        double y, z, h1, h2, a;
+        if (g.kind == NMS_QGRID_CARTESIAN) {
+            y = lin_node(i / g.n1, g.n0, g.lo0, g.hi0);
+            z = lin_node(i % g.n1, g.n1, g.lo1, g.hi1);
+        } else if (g.kind == NMS_QGRID_POLAR) {
+            double qm = lin_node(i / g.n1, g.n0, g.lo0, g.hi0);
+            double th = (two_pi * (double)(i % g.n1)) / (double)g.n1;
+            double st = sin(th), ct = cos(th);
+            y = qm * st;
+            z = qm * ct;
+            h1 = st;
+            h2 = ct;
+            a = qm;
+        } else {
+            y = g.qlist[2 * i];
+            z = g.qlist[2 * i + 1];
+        }
+        if (!std::isfinite(y) || !std::isfinite(z)) return fail(NMS_ERR_INVALID_ARG, "grid: non-finite q");
+        if (g.kind != NMS_QGRID_POLAR) {
+            a = hypot(y, z);
+            if (a > 0.0) { h1 = y / a; h2 = z / a; } else { h1 = 0.0; h2 = 1.0; }
+        }
+        qy[i] = y; qz[i] = z; hy[i] = h1; hz[i] = h2; qa[i] = a;
+        double ty = y / two_pi, tz = z / two_pi;
+        float tyh = (float)ty, tzh = (float)tz;
+        qt[i] = make_float4(tyh, (float)(ty - (double)tyh), tzh, (float)(tz - (double)tzh));
+    }
+    p.npix = np;
+    p.h_qa = qa;
+    nms_status st;
+    if ((st = dalloc(&p.d_qy, np, "qy")) || (st = dalloc(&p.d_qz, np, "qz")) || (st = dalloc(&p.d_hy, np, "hy")) ||
+        (st = dalloc(&p.d_hz, np, "hz")) || (st = dalloc(&p.d_qa, np, "qa")) || (st = dalloc(&p.d_qturn, np, "qturn")))
+        return st;
+    NMS_CUDA_TRY(cudaMemcpy(p.d_qy, qy.data(), np * 8, cudaMemcpyHostToDevice));
+    NMS_CUDA_TRY(cudaMemcpy(p.d_qz, qz.data(), np * 8, cudaMemcpyHostToDevice));
+    NMS_CUDA_TRY(cudaMemcpy(p.d_hy, hy.data(), np * 8, cudaMemcpyHostToDevice));
+    NMS_CUDA_TRY(cudaMemcpy(p.d_hz, hz.data(), np * 8, cudaMemcpyHostToDevice));
+    NMS_CUDA_TRY(cudaMemcpy(p.d_qa, qa.data(), np * 8, cudaMemcpyHostToDevice));
+    NMS_CUDA_TRY(cudaMemcpy(p.d_qturn, qt.data(), np * sizeof(float4), cudaMemcpyHostToDevice));
+    return NMS_OK;
+}
+
+static int direct_splits(const Plan& p, int64_t ncell)
+{
+    const int64_t per_block = 256 * 2;
+    int64_t pix_blocks = (p.npix + per_block - 1) / per_block;
+    int64_t target = (int64_t)device_sm_count() * 8;
+    int64_t s = (target + pix_blocks - 1) / pix_blocks;
+    int64_t by_cells = std::max<int64_t>(1, ncell / 2048);
+    s = std::min(s, by_cells);
+    s = std::min(s, p.fpart_splits);
+    return (int)std::max<int64_t>(1, s);
+}
+
+// Direct sum of cells [c0, c1) with positions cpos into out [4][npix][2].
+static nms_status direct_sum(Plan& p, const float4* cpos, int64_t c0, int64_t c1, double* out)
+{
+    cudaStream_t s = p.stream;
+    int splits = direct_splits(p, c1 - c0);
+    p.timer.begin(ST_DIRECT);
+    NMS_CUDA_TRY(launch_direct(p, cpos, c0, c1, p.path != NMS_PREC_FP32_NAIVE, splits, s));
+    p.timer.end(ST_DIRECT, 1);
+    p.timer.begin(ST_REDUCE);
+    NMS_CUDA_TRY(launch_reduce_splits(p, splits, out, s));
+    p.timer.end(ST_REDUCE, 1);
+    return NMS_OK;
+}
+
+static nms_status check_device_error(Plan& p)
+{
+    int32_t herr = 0;
+    NMS_CUDA_TRY(cudaMemcpyAsync(&herr, p.d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, p.stream));
+    NMS_CUDA_TRY(cudaStreamSynchronize(p.stream));
+    if (herr != 0) {
+        cudaMemsetAsync(p.d_err, 0, sizeof(int32_t), p.stream);
+        return fail(NMS_ERR_TIMEOUT, "a bounded device wait gave up (code " + std::to_string(herr) + ")");
+    }
+    return NMS_OK;
+}
+
+}  // namespace nms
+
+using namespace nms;
+
+extern "C" {
+
+const char* nms_last_error(void) { return g_last_error.c_str(); }
+
+const char* nms_version(void) { return "nms 0.1.0 sm_103a"; }
+
+nms_status nms_options_default(nms_options* opt)
+{
+    if (!opt) return fail(NMS_ERR_INVALID_ARG, "opt is NULL");
+    memset(opt, 0, sizeof(*opt));
+    opt->precision = NMS_PREC_AUTO;
+    opt->volume_V = 1.0;
+    opt->b_H = 1.0;
+    opt->P[2] = 1.0;
+    return NMS_OK;
+}
+
+nms_status nms_plan_create(nms_plan_t* out, int64_t n_cells, const double* pos, const double* cell_vol,
+                           const double* nuc, const double* mag, int64_t n_objects, const int64_t* object_offsets,
+                           const double* object_centers, int32_t n_rot, const double* rot, const nms_qgrid* grid,
+                           const nms_options* opt, void* cuda_stream)
+{
+    set_error("");
+    if (!out) return fail(NMS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_cells < 1 || !pos) return fail(NMS_ERR_INVALID_ARG, "need n_cells >= 1 and pos");
+    if (n_objects < 1) return fail(NMS_ERR_INVALID_ARG, "n_objects must be >= 1");
+    if (n_objects > 1 && !object_offsets) return fail(NMS_ERR_INVALID_ARG, "object_offsets required for K > 1");
+    if (n_rot < 1) return fail(NMS_ERR_INVALID_ARG, "n_rot must be >= 1");
+    if (!rot && n_rot != 1) return fail(NMS_ERR_INVALID_ARG, "rot == NULL requires n_rot == 1");
+    if (!grid) return fail(NMS_ERR_INVALID_ARG, "grid is NULL");
+    int dev_count = 0;
+    cudaError_t ce = cudaGetDeviceCount(&dev_count);
+    if (ce != cudaSuccess || dev_count < 1) {
+        cudaGetLastError();
+        return fail(NMS_ERR_CUDA, "no CUDA device available (libnms has no CPU fallback)");
+    }
+
+    nms_plan_s* p = new (std::nothrow) nms_plan_s();
+    if (!p) return fail(NMS_ERR_OUT_OF_MEMORY, "host allocation failed");
+    if (opt) p->opt = *opt; else nms_options_default(&p->opt);
+    p->grid = *grid;
+    p->grid.qlist = nullptr;
+    p->stream = (cudaStream_t)cuda_stream;
+    p->timer.stream = p->stream;
+    p->timer.on = p->opt.timing != 0;
+    p->n_cells = n_cells;
+    p->n_objects = n_objects;
+    p->n_rot = n_rot;
+    p->V = p->opt.volume_V > 0 ? p->opt.volume_V : 1.0;
+    p->bH = p->opt.b_H != 0 ? p->opt.b_H : 1.0;
+    double pn = sqrt(p->opt.P[0] * p->opt.P[0] + p->opt.P[1] * p->opt.P[1] + p->opt.P[2] * p->opt.P[2]);
+    if (pn == 0.0) { p->P[0] = 0; p->P[1] = 0; p->P[2] = 1; }
+    else for (int a = 0; a < 3; ++a) p->P[a] = p->opt.P[a] / pn;
+    p->has_nuc = nuc != nullptr;
+    p->has_mag = mag != nullptr;
+    p->has_centers = object_centers != nullptr;
+
+    auto bail = [&](nms_status st) { free_plan(p); return st; };
+
+    // precision / path
+    int prec = p->opt.precision;
+    if (prec < NMS_PREC_AUTO || prec > NMS_PREC_FP32_NAIVE) return bail(fail(NMS_ERR_INVALID_ARG, "bad precision"));
+    if (prec == NMS_PREC_TC_F16X3 && grid->kind != NMS_QGRID_CARTESIAN)
+        return bail(fail(NMS_ERR_INVALID_ARG, "the tensor-core path needs a CARTESIAN (separable) grid"));
+    if (prec == NMS_PREC_AUTO) prec = grid->kind == NMS_QGRID_CARTESIAN ? NMS_PREC_TC_F16X3 : NMS_PREC_FP32_DIRECT;
+    p->path = prec;
+
+    // offsets
+    p->h_off.resize(n_objects + 1);
+    if (object_offsets) {
+        for (int64_t k = 0; k <= n_objects; ++k) p->h_off[k] = object_offsets[k];
+        if (p->h_off[0] != 0 || p->h_off[n_objects] != n_cells)
+            return bail(fail(NMS_ERR_INVALID_ARG, "object_offsets must start at 0 and end at n_cells"));
+        for (int64_t k = 0; k < n_objects; ++k)
+            if (p->h_off[k + 1] < p->h_off[k]) return bail(fail(NMS_ERR_INVALID_ARG, "object_offsets not monotone"));
+    } else {
+        p->h_off[0] = 0;
+        p->h_off[1] = n_cells;
+    }
+    // rotations
+    p->h_rot.resize((size_t)9 * n_rot);
+    for (int32_t r = 0; r < n_rot; ++r)
+        for (int a = 0; a < 9; ++a) p->h_rot[9 * r + a] = rot ? rot[9 * r + a] : (a % 4 == 0 ? 1.0 : 0.0);
+    for (double v : p->h_rot)
+        if (!std::isfinite(v)) return bail(fail(NMS_ERR_INVALID_ARG, "non-finite rotation entry"));
+    if (object_centers) p->h_cen.assign(object_centers, object_centers + 3 * n_objects);
+
+    nms_status st;
+    if ((st = build_grid(*p, *grid))) return bail(st);
+
+    // inputs to the device
+    const int64_t n = n_cells;
+    if ((st = dalloc(&p->d_pos, 3 * n, "pos"))) return bail(st);
+    NMS_CUDA_TRY(cudaMemcpy(p->d_pos, pos, 3 * n * 8, cudaMemcpyHostToDevice));
+    if (cell_vol) {
+        if ((st = dalloc(&p->d_vol, n, "vol"))) return bail(st);
+        NMS_CUDA_TRY(cudaMemcpy(p->d_vol, cell_vol, n * 8, cudaMemcpyHostToDevice));
+    }
+    if (nuc) {
+        if ((st = dalloc(&p->d_nuc, n, "nuc"))) return bail(st);
+        NMS_CUDA_TRY(cudaMemcpy(p->d_nuc, nuc, n * 8, cudaMemcpyHostToDevice));
+    }
+    if (mag) {
+        if ((st = dalloc(&p->d_mag, 3 * n, "mag"))) return bail(st);
+        NMS_CUDA_TRY(cudaMemcpy(p->d_mag, mag, 3 * n * 8, cudaMemcpyHostToDevice));
+    }
+    if (object_centers) {
+        std::vector<double> cc((size_t)3 * n);
+        for (int64_t k = 0; k < n_objects; ++k)
+            for (int64_t j = p->h_off[k]; j < p->h_off[k + 1]; ++j)
+                for (int a = 0; a < 3; ++a) cc[3 * j + a] = object_centers[3 * k + a];
+        if ((st = dalloc(&p->d_cen_cell, 3 * n, "centres"))) return bail(st);
+        NMS_CUDA_TRY(cudaMemcpy(p->d_cen_cell, cc.data(), 3 * n * 8, cudaMemcpyHostToDevice));
+    }
+    // per-rotation work arrays
+    if ((st = dalloc(&p->d_cpos, n, "cpos")) || (st = dalloc(&p->d_cw, n, "cw"))) return bail(st);
+    bool need_local = p->opt.want_dilute && n_objects > 1 && object_centers;
+    if (need_local) {
+        if ((st = dalloc(&p->d_cposl, n, "cposl"))) return bail(st);
+    } else {
+        p->d_cposl = p->d_cpos;
+    }
+    const int64_t np = p->npix;
+    p->fpart_splits = std::max<int64_t>(1, std::min<int64_t>(64, (int64_t)(256ll << 20) / (64 * np)));
+    if ((st = dalloc(&p->d_F, 8 * np, "F")) || (st = dalloc(&p->d_Fpart, 8 * np * p->fpart_splits, "Fpart")) ||
+        (st = dalloc(&p->d_Gtot, 16 * np, "Gtot")) || (st = dalloc(&p->d_err, 1, "err")))
+        return bail(st);
+    if (p->opt.want_dilute) {
+        if ((st = dalloc(&p->d_Gdil, 16 * np, "Gdil"))) return bail(st);
+    }
+    if (n_objects > 1 && p->opt.want_dilute) {
+        if ((st = dalloc(&p->d_Ftot, 8 * np, "Ftot"))) return bail(st);
+    }
+    NMS_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int32_t)));
+    for (int64_t j = 0; j < n; ++j) {
+        double v = cell_vol ? fabs(cell_vol[j]) : 1.0;
+        if (nuc) p->h_wmax[0] = std::max(p->h_wmax[0], v * fabs(nuc[j]));
+        if (mag) {
+            double m2 = mag[3 * j] * mag[3 * j] + mag[3 * j + 1] * mag[3 * j + 1] + mag[3 * j + 2] * mag[3 * j + 2];
+            p->h_wmax[1] = std::max(p->h_wmax[1], v * sqrt(m2));
+        }
+    }
+    p->max_sum_cells = n_cells;
+    if (n_objects > 1 && p->opt.want_dilute) {
+        p->max_sum_cells = 0;
+        for (int64_t k = 0; k < n_objects; ++k) p->max_sum_cells = std::max(p->max_sum_cells, p->h_off[k + 1] - p->h_off[k]);
+    }
+    if (p->path == NMS_PREC_TC_F16X3) {
+        if ((st = tc_setup(*p))) return bail(st);
+    }
+    *out = p;
+    return NMS_OK;
+}
+
+nms_status nms_amplitudes(nms_plan_t plan)
+{
+    set_error("");
+    if (!plan) return fail(NMS_ERR_INVALID_ARG, "plan is NULL");
+    Plan& p = *plan;
+    cudaStream_t s = p.stream;
+    const int64_t np = p.npix;
+    NMS_CUDA_TRY(cudaMemsetAsync(p.d_Gtot, 0, 16 * np * 8, s));
+    if (p.d_Gdil) NMS_CUDA_TRY(cudaMemsetAsync(p.d_Gdil, 0, 16 * np * 8, s));
+    const bool objects = p.n_objects > 1 && p.opt.want_dilute;
+    const bool tc = p.path == NMS_PREC_TC_F16X3;
+    for (int32_t r = 0; r < p.n_rot; ++r) {
+        const double* R = &p.h_rot[9 * r];
+        p.timer.begin(ST_PREP);
+        NMS_CUDA_TRY(launch_prep(p, R, s));
+        p.timer.end(ST_PREP, 1);
+        if (!objects) {
+            nms_status st = tc ? tc_run(p, p.d_cpos, 0, p.n_cells, p.d_F, s) : direct_sum(p, p.d_cpos, 0, p.n_cells, p.d_F);
+            if (st) return st;
+            p.timer.begin(ST_GACC);
+            NMS_CUDA_TRY(launch_gacc(p, p.d_F, p.d_Gtot, s));
+            if (p.d_Gdil) NMS_CUDA_TRY(launch_gacc(p, p.d_F, p.d_Gdil, s));
+            p.timer.end(ST_GACC, p.d_Gdil ? 2 : 1);
+        } else {
+            // per object: local amplitude F_k -> G_dil, and shifted into F_tot
+            NMS_CUDA_TRY(cudaMemsetAsync(p.d_Ftot, 0, 8 * np * 8, s));
+            for (int64_t k = 0; k < p.n_objects; ++k) {
+                int64_t a = p.h_off[k], b = p.h_off[k + 1];
+                if (b == a) continue;
+                nms_status st = tc ? tc_run(p, p.d_cposl, a, b, p.d_F, s) : direct_sum(p, p.d_cposl, a, b, p.d_F);
+                if (st) return st;
+                double cy = 0.0, cz = 0.0;
+                if (!p.h_cen.empty()) {
+                    const double* c = &p.h_cen[3 * k];
+                    cy = R[3] * c[0] + R[4] * c[1] + R[5] * c[2];
+                    cz = R[6] * c[0] + R[7] * c[1] + R[8] * c[2];
+                }
+                p.timer.begin(ST_GACC);
+                NMS_CUDA_TRY(launch_gacc(p, p.d_F, p.d_Gdil, s));
+                NMS_CUDA_TRY(launch_shift_add(p, p.d_F, cy, cz, p.d_Ftot, s));
+                p.timer.end(ST_GACC, 2);
+            }
+            p.timer.begin(ST_GACC);
+            NMS_CUDA_TRY(launch_gacc(p, p.d_Ftot, p.d_Gtot, s));
+            p.timer.end(ST_GACC, 1);
+        }
+    }
+    p.rot_done = p.n_rot;
+    p.have_G = true;
+    return NMS_OK;
+}
+
+nms_status nms_get_amplitudes(nms_plan_t plan, double* out, int32_t out_is_device)
+{
+    set_error("");
+    if (!plan || !out) return fail(NMS_ERR_INVALID_ARG, "plan/out is NULL");
+    Plan& p = *plan;
+    if (!p.have_G) return fail(NMS_ERR_BAD_STATE, "nms_amplitudes has not run");
+    nms_status st = check_device_error(p);
+    if (st) return st;
+    const double* src = (p.n_objects > 1 && p.opt.want_dilute) ? p.d_Ftot : p.d_F;
+    NMS_CUDA_TRY(cudaMemcpyAsync(out, src, 8 * p.npix * 8,
+                                 out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p.stream));
+    NMS_CUDA_TRY(cudaStreamSynchronize(p.stream));
+    return NMS_OK;
+}
+
+nms_status nms_response(nms_plan_t plan, int32_t id, int32_t part, double* out, int32_t out_is_device)
+{
+    set_error("");
+    if (!plan || !out) return fail(NMS_ERR_INVALID_ARG, "plan/out is NULL");
+    Plan& p = *plan;
+    if (id < 0 || id >= NMS_RESP_COUNT) return fail(NMS_ERR_INVALID_ARG, "response id out of range");
+    if (part < NMS_PART_TOTAL || part > NMS_PART_INTERFERENCE) return fail(NMS_ERR_INVALID_ARG, "bad part");
+    if (!p.have_G) return fail(NMS_ERR_BAD_STATE, "nms_amplitudes has not run");
+    if (part != NMS_PART_TOTAL && !p.d_Gdil) return fail(NMS_ERR_UNSUPPORTED, "dilute part needs want_dilute");
+    const double* Ga = part == NMS_PART_DILUTE ? p.d_Gdil : p.d_Gtot;
+    const double* Gb = part == NMS_PART_INTERFERENCE ? p.d_Gdil : nullptr;
+    double norm = 1.0 / (double)(p.rot_done > 0 ? p.rot_done : 1);
+    double* dst = out;
+    if (!out_is_device) {
+        NMS_CUDA_TRY(cudaMallocAsync((void**)&dst, p.npix * 8, p.stream));
+    }
+    cudaError_t e = launch_response(p, id, Ga, Gb, norm, dst, p.stream);
+    if (e == cudaSuccess && !out_is_device)
+        e = cudaMemcpyAsync(out, dst, p.npix * 8, cudaMemcpyDeviceToHost, p.stream);
+    if (!out_is_device) cudaFreeAsync(dst, p.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "response");
+    return check_device_error(p);
+}
+
+nms_status nms_azimuthal_average(nms_plan_t plan, const double* img, int32_t img_is_device, int32_t nbins,
+                                 const double* bin_edges, double* Iq, int64_t* counts, double* qmean,
+                                 int32_t out_is_device)
+{
+    set_error("");
+    if (!plan || !img || !Iq || !counts) return fail(NMS_ERR_INVALID_ARG, "NULL argument");
+    Plan& p = *plan;
+    cudaStream_t s = p.stream;
+    const int64_t np = p.npix;
+    const double* d_img = img;
+    double* tmp_img = nullptr;
+    if (!img_is_device) {
+        NMS_CUDA_TRY(cudaMallocAsync((void**)&tmp_img, np * 8, s));
+        NMS_CUDA_TRY(cudaMemcpyAsync(tmp_img, img, np * 8, cudaMemcpyHostToDevice, s));
+        d_img = tmp_img;
+    }
+    std::vector<double> hI(std::max(nbins, 0)), hq(std::max(nbins, 0));
+    std::vector<int64_t> hc(std::max(nbins, 0));
+    nms_status result = NMS_OK;
+    if (p.grid.kind == NMS_QGRID_POLAR) {
+        if (nbins != p.grid.n0) {
+            result = fail(NMS_ERR_INVALID_ARG, "POLAR grid: nbins must equal n0");
+        } else {
+            double* d_I = nullptr;
+            NMS_CUDA_TRY(cudaMallocAsync((void**)&d_I, nbins * 8, s));
+            cudaError_t e = launch_azimuthal_polar(p, d_img, d_I, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hI.data(), d_I, nbins * 8, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            cudaFreeAsync(d_I, s);
+            if (e != cudaSuccess) result = cuda_fail(e, "azimuthal (polar)");
+            for (int i = 0; i < nbins; ++i) {
+                hc[i] = p.grid.n1;
+                hq[i] = lin_node(i, p.grid.n0, p.grid.lo0, p.grid.hi0);
+            }
+        }
+    } else {
+        if (nbins < 1 || !bin_edges) {
+            result = fail(NMS_ERR_INVALID_ARG, "need nbins >= 1 and bin_edges");
+        } else {
+            for (int b = 0; b < nbins; ++b)
+                if (!(bin_edges[b + 1] > bin_edges[b])) { result = fail(NMS_ERR_INVALID_ARG, "bin_edges not increasing"); break; }
+        }
+        if (result == NMS_OK) {
+            double *d_e = nullptr, *d_sum = nullptr, *d_qs = nullptr;
+            unsigned long long* d_cnt = nullptr;
+            NMS_CUDA_TRY(cudaMallocAsync((void**)&d_e, (nbins + 1) * 8, s));
+            NMS_CUDA_TRY(cudaMallocAsync((void**)&d_sum, nbins * 8, s));
+            NMS_CUDA_TRY(cudaMallocAsync((void**)&d_qs, nbins * 8, s));
+            NMS_CUDA_TRY(cudaMallocAsync((void**)&d_cnt, nbins * 8, s));
+            cudaError_t e = cudaMemcpyAsync(d_e, bin_edges, (nbins + 1) * 8, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(d_sum, 0, nbins * 8, s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(d_qs, 0, nbins * 8, s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, nbins * 8, s);
+            if (e == cudaSuccess) e = launch_azimuthal_cart(p, d_img, nbins, d_e, d_sum, d_cnt, d_qs, s);
+            std::vector<unsigned long long> cnt(nbins);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hI.data(), d_sum, nbins * 8, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hq.data(), d_qs, nbins * 8, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), d_cnt, nbins * 8, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            cudaFreeAsync(d_e, s);
+            cudaFreeAsync(d_sum, s);
+            cudaFreeAsync(d_qs, s);
+            cudaFreeAsync(d_cnt, s);
+            if (e != cudaSuccess) result = cuda_fail(e, "azimuthal (cartesian)");
+            for (int b = 0; b < nbins; ++b) {
+                hc[b] = (int64_t)cnt[b];
+                if (cnt[b]) { hI[b] /= (double)cnt[b]; hq[b] /= (double)cnt[b]; }
+                else { hI[b] = NAN; hq[b] = NAN; }
+            }
+        }
+    }
+    if (tmp_img) cudaFreeAsync(tmp_img, s);
+    if (result != NMS_OK) return result;
+    cudaMemcpyKind k = out_is_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    NMS_CUDA_TRY(cudaMemcpyAsync(Iq, hI.data(), nbins * 8, k, s));
+    NMS_CUDA_TRY(cudaMemcpyAsync(counts, hc.data(), nbins * 8, k, s));
+    if (qmean) NMS_CUDA_TRY(cudaMemcpyAsync(qmean, hq.data(), nbins * 8, k, s));
+    NMS_CUDA_TRY(cudaStreamSynchronize(s));
+    return NMS_OK;
+}
+
+nms_status nms_correlation(int32_t nq, const double* q, const double* Iq, int32_t nr, const double* r,
+                           double prefactor, double* c_r, double* p_r, int32_t is_device, void* cuda_stream)
+{
+    set_error("");
+    if (nq < 0 || nr < 0 || (nq > 0 && (!q || !Iq)) || (nr > 0 && !r)) return fail(NMS_ERR_INVALID_ARG, "bad sizes or NULL");
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) {
+        cudaGetLastError();
+        return fail(NMS_ERR_CUDA, "no CUDA device available (libnms has no CPU fallback)");
+    }
+    if (nr == 0) return NMS_OK;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    double pref = prefactor != 0.0 ? prefactor : 1.0 / (2.0 * M_PI * M_PI);
+    int nqa = std::max(nq, 1);
+    double *dq = nullptr, *dI = nullptr, *dr = nullptr, *dc = nullptr, *dp = nullptr, *sq = nullptr, *sf = nullptr;
+    int* sn = nullptr;
+    NMS_CUDA_TRY(cudaMallocAsync((void**)&sq, nqa * 8, s));
+    NMS_CUDA_TRY(cudaMallocAsync((void**)&sf, nqa * 8, s));
+    NMS_CUDA_TRY(cudaMallocAsync((void**)&sn, sizeof(int), s));
+    if (is_device) {
+        dq = (double*)q; dI = (double*)Iq; dr = (double*)r; dc = c_r; dp = p_r;
+    } else {
+        NMS_CUDA_TRY(cudaMallocAsync((void**)&dq, nqa * 8, s));
+        NMS_CUDA_TRY(cudaMallocAsync((void**)&dI, nqa * 8, s));
+        NMS_CUDA_TRY(cudaMallocAsync((void**)&dr, nr * 8, s));
+        NMS_CUDA_TRY(cudaMallocAsync((void**)&dc, nr * 8, s));
+        NMS_CUDA_TRY(cudaMallocAsync((void**)&dp, nr * 8, s));
+        if (nq) NMS_CUDA_TRY(cudaMemcpyAsync(dq, q, nq * 8, cudaMemcpyHostToDevice, s));
+        if (nq) NMS_CUDA_TRY(cudaMemcpyAsync(dI, Iq, nq * 8, cudaMemcpyHostToDevice, s));
+        NMS_CUDA_TRY(cudaMemcpyAsync(dr, r, nr * 8, cudaMemcpyHostToDevice, s));
+    }
+    cudaError_t e = launch_correlation(nq, dq, dI, nr, dr, pref, dc, dp, sq, sf, sn, s);
+    if (e == cudaSuccess && !is_device) {
+        if (c_r) e = cudaMemcpyAsync(c_r, dc, nr * 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && p_r) e = cudaMemcpyAsync(p_r, dp, nr * 8, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(sq, s);
+    cudaFreeAsync(sf, s);
+    cudaFreeAsync(sn, s);
+    if (!is_device) {
+        cudaFreeAsync(dq, s);
+        cudaFreeAsync(dI, s);
+        cudaFreeAsync(dr, s);
+        cudaFreeAsync(dc, s);
+        cudaFreeAsync(dp, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "correlation");
+    return NMS_OK;
+}
+
+nms_status nms_plan_stage_ms(nms_plan_t plan, double ms[8], int64_t launches[8], int32_t reset)
+{
+    set_error("");
+    if (!plan) return fail(NMS_ERR_INVALID_ARG, "plan is NULL");
+    Plan& p = *plan;
+    nms_status st = p.timer.collect();
+    if (st) return st;
+    for (int i = 0; i < ST_COUNT; ++i) {
+        if (ms) ms[i] = p.timer.ms[i];
+        if (launches) launches[i] = p.timer.launches[i];
+    }
+    if (reset) {
+        for (int i = 0; i < ST_COUNT; ++i) { p.timer.ms[i] = 0; p.timer.launches[i] = 0; }
+    }
+    return NMS_OK;
+}
+
+nms_status nms_plan_destroy(nms_plan_t plan)
+{
+    if (!plan) return NMS_OK;
+    cudaStreamSynchronize(plan->stream);
+    free_plan(plan);
+    return NMS_OK;
+}
+
+}  // extern "C"

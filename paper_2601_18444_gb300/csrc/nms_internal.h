@@ -1,0 +1,134 @@
+// Internal declarations of libnms (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "nms.h"
+
+namespace nms {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+nms_status cuda_fail(cudaError_t e, const char* what);
+
+#define NMS_CUDA_TRY(expr)                                        \
+    do {                                                          \
+        cudaError_t _e = (expr);                                  \
+        if (_e != cudaSuccess) return ::nms::cuda_fail(_e, #expr); \
+    } while (0)
+
+// ---------------------------------------------------------------- stages
+enum Stage { ST_PREP = 0, ST_TABLES = 1, ST_GEMM = 2, ST_DIRECT = 3, ST_REDUCE = 4, ST_GACC = 5, ST_COUNT = 8 };
+
+struct StageTimer {
+    bool on = false;
+    cudaStream_t stream = nullptr;
+    struct Pending { int stage; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    double ms[ST_COUNT] = {0};
+    int64_t launches[ST_COUNT] = {0};
+    int open_stage = -1;
+    cudaEvent_t open_ev = nullptr;
+    cudaEvent_t get_event();
+    void begin(int stage);
+    void end(int stage, int n_launch);
+    nms_status collect();
+    void release();
+};
+
+// ---------------------------------------------------------------- plan
+struct Plan {
+    cudaStream_t stream = nullptr;
+    nms_options opt{};
+    nms_qgrid grid{};
+    int path = 0;                 // nms_precision actually used
+    int64_t n_cells = 0, n_objects = 1, npix = 0;
+    int32_t n_rot = 1;
+    double V = 1.0, bH = 1.0, P[3] = {0, 0, 1};
+    bool has_nuc = false, has_mag = false, has_centers = false;
+    std::vector<int64_t> h_off;   // [K+1]
+    std::vector<double> h_rot;    // [n_rot][9]
+    std::vector<double> h_cen;    // [K][3]
+
+    // device inputs (FP64)
+    double* d_pos = nullptr;      // [n][3]
+    double* d_vol = nullptr;      // [n]
+    double* d_nuc = nullptr;      // [n] or null
+    double* d_mag = nullptr;      // [n][3] or null
+    double* d_cen_cell = nullptr; // [n][3] object centre of each cell, or null
+    // q-grid (FP64) and the turns form used by the kernels
+    double* d_qy = nullptr; double* d_qz = nullptr;
+    double* d_hy = nullptr; double* d_hz = nullptr; double* d_qa = nullptr;
+    float4* d_qturn = nullptr;    // per pixel (qy/2pi hi, lo, qz/2pi hi, lo)
+    std::vector<double> h_qa;     // |q| per pixel (host copy, binning)
+    // per-rotation cell data
+    float4* d_cpos = nullptr;     // global positions R(x + r^k): (Yh, Yl, Zh, Zl)
+    float4* d_cposl = nullptr;    // local positions R x (dilute), may alias d_cpos
+    float4* d_cw = nullptr;       // weights (wN, wMx', wMy', wMz') FP32
+    double* d_yz = nullptr;       // FP64 (Y, Z) global, [2][n] (tensor-path tables)
+    double* d_yzl = nullptr;      // FP64 (Y, Z) local
+    double* d_w64 = nullptr;      // FP64 weights [4][n]
+    // results
+    double* d_F = nullptr;        // [4][npix][2] amplitudes of the current sum
+    double* d_Ftot = nullptr;     // [4][npix][2] total amplitude (object path)
+    double* d_Fpart = nullptr;    // split partials [splits][4][npix][2]
+    int64_t fpart_splits = 0;
+    double* d_Gtot = nullptr;     // [16][npix]
+    double* d_Gdil = nullptr;     // [16][npix] (want_dilute)
+    int32_t* d_err = nullptr;     // device error word (timeouts)
+    bool have_G = false;
+    int32_t rot_done = 0;
+
+    // tensor path workspace
+    void* d_tab = nullptr;        // split-FP16 operand tables
+    size_t tab_bytes = 0;
+    int64_t tab_cells = 0;        // cells per table chunk
+    double* d_wscale = nullptr;   // per-channel power-of-two weight scales [4]
+    void* tc_state = nullptr;     // tensor-path state (k_gemm.cu)
+    double h_wmax[2] = {0, 0};    // max_j V_j |N_j|, max_j V_j |M_j| (rotation invariant)
+    int64_t max_sum_cells = 0;    // largest cell range summed in one call
+
+    StageTimer timer;
+};
+
+// ---------------------------------------------------------------- kernels (launchers)
+// Rotation and weights for cells [0, n): FP64 positions -> two-float, FP32 weights.
+cudaError_t launch_prep(Plan& p, const double* R9, cudaStream_t s);
+// Direct sum over cells [c0, c1) of the given position array into split partials.
+cudaError_t launch_direct(const Plan& p, const float4* cpos, int64_t c0, int64_t c1,
+                          bool compensated, int splits, cudaStream_t s);
+// Sum split partials into out [4][npix][2] (assign).
+cudaError_t launch_reduce_splits(const Plan& p, int splits, double* out, cudaStream_t s);
+// G += F F^dagger for every pixel (F: [4][npix][2]).
+cudaError_t launch_gacc(const Plan& p, const double* F, double* G, cudaStream_t s);
+// out[p] = factor * F_tot accumulate with object phase (total from objects).
+cudaError_t launch_shift_add(const Plan& p, const double* Fk, double cy, double cz, double* Ftot,
+                             cudaStream_t s);
+// Response id from G (FP64), divided by norm (number of rotations).
+cudaError_t launch_response(const Plan& p, int id, const double* Ga, const double* Gb, double norm,
+                            double* out, cudaStream_t s);
+// Azimuthal averages.
+cudaError_t launch_azimuthal_cart(const Plan& p, const double* img, int nbins, const double* d_edges,
+                                  double* d_sum, unsigned long long* d_cnt, double* d_qsum,
+                                  cudaStream_t s);
+cudaError_t launch_azimuthal_polar(const Plan& p, const double* img, double* Iq, cudaStream_t s);
+cudaError_t launch_correlation(int nq, const double* q, const double* Iq, int nr, const double* r,
+                               double pref, double* c, double* pr, double* scratch_q, double* scratch_f,
+                               int* scratch_n, cudaStream_t s);
+
+// Tensor-core path (split-FP16 tcgen05 GEMM).
+nms_status tc_setup(Plan& p);
+nms_status tc_run(Plan& p, const float4* cpos, int64_t c0, int64_t c1, double* Fout, cudaStream_t s);
+void tc_release(Plan& p);
+
+int device_sm_count();
+
+}  // namespace nms
+
+// The opaque handle of the C ABI is the plan itself.
+struct nms_plan_s : public nms::Plan {};

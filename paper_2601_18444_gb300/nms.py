@@ -1,0 +1,282 @@
+"""Python binding of libnms (ctypes): the C ABI of include/nms.h, same names.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Host arrays are numpy float64; device arrays are torch CUDA tensors
+(passed by ``data_ptr()``).  There is no CPU fallback: if libnms.so is not
+built or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+NMS_OK = 0
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "UNSUPPORTED", 5: "TIMEOUT",
+          6: "BAD_STATE"}
+
+QGRID_CARTESIAN, QGRID_POLAR, QGRID_LIST = 0, 1, 2
+PREC_AUTO, PREC_TC_F16X3, PREC_FP32_DIRECT, PREC_FP32_NAIVE = 0, 1, 2, 3
+PART_TOTAL, PART_DILUTE, PART_INTERFERENCE = 0, 1, 2
+
+RESPONSE_NAMES = ["N", "M", "P", "NM", "CHI", "SF", "PM", "MP", "PP", "MM", "SANSPOL_P", "SANSPOL_M", "UNPOL"] + \
+    [f"G_{a}{b}_{p}" for a in "XYZ" for b in "XYZ" for p in ("RE", "IM")] + ["QX2", "QY2", "QZ2"]
+RESPONSE_ID = {n: i for i, n in enumerate(RESPONSE_NAMES)}
+
+STAGES = ["prep", "tables", "gemm", "direct", "reduce", "gacc", "s6", "s7"]
+
+
+class NmsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"nms {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class nms_qgrid(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n0", ctypes.c_int32), ("n1", ctypes.c_int32),
+                ("lo0", ctypes.c_double), ("hi0", ctypes.c_double), ("lo1", ctypes.c_double),
+                ("hi1", ctypes.c_double), ("qlist", ctypes.POINTER(ctypes.c_double))]
+
+
+class nms_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("want_dilute", ctypes.c_int32), ("volume_V", ctypes.c_double),
+                ("b_H", ctypes.c_double), ("P", ctypes.c_double * 3), ("kc_cells", ctypes.c_int32),
+                ("split_k", ctypes.c_int32), ("max_spin", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+_V = ctypes.c_void_p
+
+# name -> (restype, argtypes); the full C ABI of include/nms.h
+SIGNATURES = {
+    "nms_options_default": (ctypes.c_int, [ctypes.POINTER(nms_options)]),
+    "nms_plan_create": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int64, _D, _D, _D, _D, ctypes.c_int64, _I64, _D,
+                                       ctypes.c_int32, _D, ctypes.POINTER(nms_qgrid), ctypes.POINTER(nms_options),
+                                       _V]),
+    "nms_amplitudes": (ctypes.c_int, [_V]),
+    "nms_get_amplitudes": (ctypes.c_int, [_V, _V, ctypes.c_int32]),
+    "nms_response": (ctypes.c_int, [_V, ctypes.c_int32, ctypes.c_int32, _V, ctypes.c_int32]),
+    "nms_azimuthal_average": (ctypes.c_int, [_V, _V, ctypes.c_int32, ctypes.c_int32, _D, _V, _V, _V,
+                                             ctypes.c_int32]),
+    "nms_correlation": (ctypes.c_int, [ctypes.c_int32, _V, _V, ctypes.c_int32, _V, ctypes.c_double, _V, _V,
+                                       ctypes.c_int32, _V]),
+    "nms_plan_stage_ms": (ctypes.c_int, [_V, _D, _I64, ctypes.c_int32]),
+    "nms_plan_destroy": (ctypes.c_int, [_V]),
+    "nms_last_error": (ctypes.c_char_p, []),
+    "nms_version": (ctypes.c_char_p, []),
+}
+
+
+def lib_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libnms.so (building it in-tree if needed); raises if it cannot."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if build_if_missing and _build.needs_build():
+        _build.build()
+    if not os.path.exists(path):
+        raise NmsError(3, f"libnms.so not built at {path}")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(st):
+    if st != NMS_OK:
+        raise NmsError(st, nms_last_error())
+
+
+def nms_last_error():
+    return load().nms_last_error().decode()
+
+
+def nms_version():
+    return load().nms_version().decode()
+
+
+def _host(a, shape_last=None):
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_D)
+
+
+def _is_dev(t):
+    return hasattr(t, "is_cuda") and t.is_cuda
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr() if _is_dev(t) else t.ctypes.data)
+
+
+def nms_options_default(**kw):
+    o = nms_options()
+    _check(load().nms_options_default(ctypes.byref(o)))
+    for k, v in kw.items():
+        if k == "P":
+            for i in range(3):
+                o.P[i] = float(v[i])
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def make_grid(kind, n0, n1=1, lo0=0.0, hi0=0.0, lo1=0.0, hi1=0.0, qlist=None):
+    g = nms_qgrid()
+    g.kind = {"cartesian": 0, "polar": 1, "list": 2}.get(kind, kind)
+    g.n0, g.n1 = int(n0), int(n1)
+    g.lo0, g.hi0, g.lo1, g.hi1 = float(lo0), float(hi0), float(lo1), float(hi1)
+    keep = None
+    if qlist is not None:
+        keep = np.ascontiguousarray(qlist, dtype=np.float64).reshape(-1)
+        g.qlist = keep.ctypes.data_as(_D)
+    g._keep = keep
+    return g
+
+
+class Plan:
+    """Owning wrapper of an nms_plan_t (destroyed on close/garbage collection)."""
+
+    def __init__(self, handle, npix, grid):
+        self.handle = handle
+        self.npix = npix
+        self.grid = grid
+
+    def close(self):
+        if self.handle:
+            load().nms_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def nms_plan_create(pos, cell_vol=None, nuc=None, mag=None, object_offsets=None, object_centers=None, rot=None,
+                    grid=None, opt=None, stream=None):
+    lib = load()
+    pos, p_pos = _host(pos)
+    n = pos.shape[0]
+    vol, p_vol = _host(cell_vol)
+    nuc, p_nuc = _host(nuc)
+    mag, p_mag = _host(mag)
+    cen, p_cen = _host(object_centers)
+    off = None
+    p_off = None
+    K = 1
+    if object_offsets is not None:
+        off = np.ascontiguousarray(object_offsets, dtype=np.int64)
+        p_off = off.ctypes.data_as(_I64)
+        K = len(off) - 1
+    nrot = 1
+    R, p_R = None, None
+    if rot is not None:
+        R = np.ascontiguousarray(rot, dtype=np.float64).reshape(-1, 9)
+        nrot = R.shape[0]
+        p_R = R.ctypes.data_as(_D)
+    h = ctypes.c_void_p()
+    _check(lib.nms_plan_create(ctypes.byref(h), n, p_pos, p_vol, p_nuc, p_mag, K, p_off, p_cen, nrot, p_R,
+                               ctypes.byref(grid), ctypes.byref(opt) if opt is not None else None,
+                               ctypes.c_void_p(stream or 0)))
+    npix = grid.n0 * grid.n1 if grid.kind != QGRID_LIST else grid.n0
+    return Plan(h, npix, grid)
+
+
+def nms_amplitudes(plan):
+    _check(load().nms_amplitudes(plan.handle))
+
+
+def nms_get_amplitudes(plan, out=None):
+    """Total amplitudes of the last rotation: complex128 [4, npix] (host) or into a device tensor."""
+    if out is None:
+        buf = np.empty(8 * plan.npix, dtype=np.float64)
+        _check(load().nms_get_amplitudes(plan.handle, _ptr(buf), 0))
+        b = buf.reshape(4, plan.npix, 2)
+        return b[..., 0] + 1j * b[..., 1]
+    _check(load().nms_get_amplitudes(plan.handle, _ptr(out), 1 if _is_dev(out) else 0))
+    return out
+
+
+def nms_response(plan, response, part=PART_TOTAL, out=None):
+    rid = RESPONSE_ID[response] if isinstance(response, str) else int(response)
+    if out is None:
+        out = np.empty(plan.npix, dtype=np.float64)
+    _check(load().nms_response(plan.handle, rid, part, _ptr(out), 1 if _is_dev(out) else 0))
+    return out
+
+
+def nms_azimuthal_average(plan, img, bin_edges=None, nbins=None):
+    """Returns (I, counts, qmean) as host numpy arrays."""
+    if bin_edges is not None:
+        edges = np.ascontiguousarray(bin_edges, dtype=np.float64)
+        nb = len(edges) - 1
+        p_e = edges.ctypes.data_as(_D)
+    else:
+        edges, p_e, nb = None, None, int(nbins)
+    if not _is_dev(img):
+        img = np.ascontiguousarray(img, dtype=np.float64)
+    I = np.empty(nb, dtype=np.float64)
+    c = np.empty(nb, dtype=np.int64)
+    qm = np.empty(nb, dtype=np.float64)
+    _check(load().nms_azimuthal_average(plan.handle, _ptr(img), 1 if _is_dev(img) else 0, nb, p_e, _ptr(I),
+                                        _ptr(c), _ptr(qm), 0))
+    return I, c, qm
+
+
+def nms_correlation(q, Iq, r, prefactor=0.0, stream=None):
+    """c(r), p(r) by the library's trapezoid kernel; host numpy in and out."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    Iq = np.ascontiguousarray(Iq, dtype=np.float64)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    c = np.empty(len(r))
+    p = np.empty(len(r))
+    _check(load().nms_correlation(len(q), _ptr(q), _ptr(Iq), len(r), _ptr(r), float(prefactor), _ptr(c), _ptr(p),
+                                  0, ctypes.c_void_p(stream or 0)))
+    return c, p
+
+
+def nms_correlation_device(q, Iq, r, c, p, prefactor=0.0, stream=None):
+    """Device variant: all five arguments are CUDA tensors (float64)."""
+    _check(load().nms_correlation(q.numel(), _ptr(q), _ptr(Iq), r.numel(), _ptr(r), float(prefactor), _ptr(c),
+                                  _ptr(p), 1, ctypes.c_void_p(stream or 0)))
+
+
+def nms_plan_stage_ms(plan, reset=False):
+    ms = (ctypes.c_double * 8)()
+    ln = (ctypes.c_int64 * 8)()
+    _check(load().nms_plan_stage_ms(plan.handle, ms, ln, 1 if reset else 0))
+    return {STAGES[i]: (ms[i], ln[i]) for i in range(8)}
+
+
+def nms_plan_destroy(plan):
+    plan.close()
+
+
+def plan_from_field(field, grid, opt=None, rot=None, stream=None):
+    """Convenience: nms_plan_create from an inputs.Field."""
+    return nms_plan_create(field.pos, field.vol, field.nuc, field.mag, field.offsets, field.centers, rot, grid, opt,
+                           stream)

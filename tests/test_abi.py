@@ -1,0 +1,89 @@
+"""The C-ABI library builds, loads and exports every symbol include/nms.h declares.
+
+CPU-only: no compute call is made except those that must fail cleanly
+without a GPU (no CPU fallback exists).
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2601_18444_gb300 import nms
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nms.h")
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(nms_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for n in ["nms_plan_create", "nms_amplitudes", "nms_response", "nms_azimuthal_average", "nms_correlation",
+              "nms_plan_destroy", "nms_last_error", "nms_get_amplitudes", "nms_options_default"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    path = nms.lib_path()
+    nms.load()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (nms_[a-z_0-9]+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    assert sorted(nms.SIGNATURES) == declared_functions()
+
+
+def test_struct_layouts_match_c(tmp_path):
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "nms.h"\n'
+                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(nms_options), sizeof(nms_qgrid),'
+                   ' offsetof(nms_options, timing), offsetof(nms_qgrid, qlist));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    a, b, c, d = map(int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split())
+    assert a == ctypes.sizeof(nms.nms_options)
+    assert b == ctypes.sizeof(nms.nms_qgrid)
+    assert c == nms.nms_options.timing.offset
+    assert d == nms.nms_qgrid.qlist.offset
+
+
+def test_response_ids_match_header():
+    txt = open(HEADER).read()
+    body = txt[txt.index("NMS_RESP_N = 0"):txt.index("NMS_RESP_COUNT")]
+    ids = [m.replace("NMS_RESP_", "") for m in re.findall(r"NMS_RESP_[A-Z_0-9]+", body)]
+    assert ids == nms.RESPONSE_NAMES
+
+
+def test_defaults_and_version():
+    o = nms.nms_options_default()
+    assert o.precision == nms.PREC_AUTO and o.volume_V == 1.0 and o.b_H == 1.0 and tuple(o.P) == (0.0, 0.0, 1.0)
+    assert "sm_103a" in nms.nms_version()
+
+
+def test_invalid_arguments_are_reported_without_gpu():
+    g = nms.make_grid("cartesian", 4, 4, -1, 1, -1, 1)
+    with pytest.raises(nms.NmsError) as e:
+        nms.nms_plan_create(np.zeros((0, 3)), grid=g)
+    assert e.value.status == 1
+    # with valid arguments and no GPU the library refuses: no CPU fallback
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if not has_gpu:
+        with pytest.raises(nms.NmsError) as e:
+            nms.nms_plan_create(np.zeros((3, 3)), grid=g)
+        assert e.value.status == 3
+        with pytest.raises(nms.NmsError):
+            nms.nms_correlation([0.0, 1.0], [1.0, 1.0], [1.0])

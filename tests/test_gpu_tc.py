@@ -1,0 +1,135 @@
+"""GPU parity of the tensor-core path (split-FP16 tcgen05 GEMM) against the oracle.
+
+Same bars as the direct path: max_p |dF|/sum_j|w_cj| <= 1e-6 per channel,
+responses within the bound that implies, I(q) within 1e-5.  Shapes cover
+several tiles with ragged tails in every GEMM dimension (q_y rows, q_z
+columns, cells), a single cell, objects with the dilute/interference split,
+rotation averages, the coherent q = 0 pixel, and the full-size box workload
+on sampled pixels.
+"""
+import numpy as np
+import pytest
+
+from oracle import sans as S
+from paper_2601_18444_gb300 import inputs as I
+from paper_2601_18444_gb300 import nms
+from parity_util import AMP_TOL, IQ_TOL, amp_error, iq_rel_error, resp_tol, weight_sums
+
+pytestmark = pytest.mark.gpu
+
+TC = nms.PREC_TC_F16X3
+
+
+def run(field, grid_kw, rot=None, **optkw):
+    g = nms.make_grid(**grid_kw)
+    opt = nms.nms_options_default(precision=TC, **optkw)
+    plan = nms.plan_from_field(field, g, opt, rot=rot)
+    nms.nms_amplitudes(plan)
+    return plan
+
+
+def og(grid_kw):
+    kw = dict(grid_kw)
+    kind = kw.pop("kind")
+    return S.q_grid(kind, **kw)
+
+
+def test_tc_single_tile_small():
+    f = I.sphere_vortex(6.0, 2.0, seed=3)
+    kw = dict(kind="cartesian", n0=8, n1=8, lo0=-1.0, hi0=1.0, lo1=-1.0, hi1=1.0)
+    plan = run(f, kw)
+    g = og(kw)
+    F_ref = S.amplitudes(f, np.eye(3), g[0], g[1])
+    err = amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f))
+    assert np.all(err <= AMP_TOL), err
+
+
+def test_tc_config1_all_responses():
+    f = I.sphere_vortex(16.0, 2.0, seed=0)
+    kw = dict(kind="cartesian", n0=128, n1=128, lo0=-1.0, hi0=1.0, lo1=-1.0, hi1=1.0)
+    plan = run(f, kw)
+    g = og(kw)
+    F_ref = S.amplitudes(f, np.eye(3), g[0], g[1])
+    err = amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f))
+    assert np.all(err <= AMP_TOL), err
+    ref = S.responses(F_ref, g[2], g[3])
+    for name in nms.RESPONSE_NAMES:
+        assert np.max(np.abs(nms.nms_response(plan, name) - ref[name])) <= resp_tol(f), name
+    edges = np.linspace(0, 1, 65)
+    for name in ("UNPOL", "SF"):
+        Ig, cg, _ = nms.nms_azimuthal_average(plan, nms.nms_response(plan, name), edges)
+        Ir, cr, _ = S.azimuthal_average_cartesian(ref[name], g[4], edges)
+        assert np.array_equal(cg, cr)
+        assert iq_rel_error(Ig, Ir) <= IQ_TOL
+
+
+@pytest.mark.parametrize("ny,nz,n", [(33, 65, 1), (1, 1, 31), (97, 130, 1001), (200, 7, 4129)])
+def test_tc_ragged_shapes(ny, nz, n):
+    f = I.small_random_field(n, seed=ny + nz + n, extent=12.0)
+    kw = dict(kind="cartesian", n0=ny, n1=nz, lo0=-1.7, hi0=1.3, lo1=-0.6, hi1=2.1)
+    plan = run(f, kw)
+    g = og(kw)
+    F_ref = S.amplitudes(f, np.eye(3), g[0], g[1])
+    err = amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f))
+    assert np.all(err <= AMP_TOL), err
+
+
+@pytest.mark.parametrize("kc", [0, 32, 64, 128])
+def test_tc_coherent_q0_pixel(kc):
+    # all-positive constant weights, pixels at and near q = 0: the partial sums
+    # in the FP32 tensor accumulators are as coherent as they can be
+    f = I.box_field(40, 40, 40, a=1.0, n_modes=4, seed=2, pores=False)
+    kw = dict(kind="cartesian", n0=9, n1=9, lo0=-0.02, hi0=0.02, lo1=-0.02, hi1=0.02)
+    plan = run(f, kw, kc_cells=kc)
+    g = og(kw)
+    F_ref = S.amplitudes(f, np.eye(3), g[0], g[1])
+    err = amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f))
+    assert np.all(err <= AMP_TOL), err
+
+
+def test_tc_objects_and_rotation():
+    f = I.small_random_field(1500, seed=5, extent=5.0, n_objects=6)
+    kw = dict(kind="cartesian", n0=40, n1=36, lo0=-1.0, hi0=1.2, lo1=-1.1, hi1=0.9)
+    Rs = I.random_rotations(2, seed=4)
+    plan = run(f, kw, rot=Rs, want_dilute=1)
+    g = og(kw)
+    ids = ("N", "M", "SF", "CHI", "UNPOL")
+    acc = {k: [0, 0, 0] for k in ids}
+    for R in Rs:
+        parts = S.response_parts(f, R, g, ids=ids)
+        for k in ids:
+            for i in range(3):
+                acc[k][i] = acc[k][i] + parts[k][i] / len(Rs)
+    tol = 2 * resp_tol(f, rotations=Rs)
+    for k in ids:
+        for i, part in enumerate((nms.PART_TOTAL, nms.PART_DILUTE, nms.PART_INTERFERENCE)):
+            assert np.max(np.abs(nms.nms_response(plan, k, part) - acc[k][i])) <= tol, (k, part)
+
+
+def test_tc_matches_direct_path():
+    f = I.box_field(48, 40, 24, a=2.0, n_modes=8, n_pores=5, seed=6)
+    kw = dict(kind="cartesian", n0=96, n1=80, lo0=-2.0, hi0=2.0, lo1=-2.0, hi1=2.0)
+    F_tc = nms.nms_get_amplitudes(run(f, kw))
+    g = nms.make_grid(**kw)
+    pd = nms.plan_from_field(f, g, nms.nms_options_default(precision=nms.PREC_FP32_DIRECT))
+    nms.nms_amplitudes(pd)
+    F_d = nms.nms_get_amplitudes(pd)
+    err = amp_error(F_tc, F_d, weight_sums(f))
+    assert np.all(err <= 2 * AMP_TOL), err
+
+
+def test_tc_full_box_sampled_pixels():
+    # the default benchmark workload at full size (4.19M cells, 512^2 pixels),
+    # checked on a random sample of pixels the oracle evaluates one by one
+    f = I.box_field(256, 256, 64, a=2.0, n_modes=64, kmax=0.2, n_pores=200, seed=1)
+    kw = dict(kind="cartesian", n0=512, n1=512, lo0=-2.0, hi0=2.0, lo1=-2.0, hi1=2.0)
+    plan = run(f, kw)
+    F = nms.nms_get_amplitudes(plan)
+    g = og(kw)
+    rng = np.random.default_rng(0)
+    centre = [255 * 512 + 255, 255 * 512 + 256, 256 * 512 + 255, 256 * 512 + 256]   # most coherent pixels
+    idx = np.unique(np.concatenate([rng.choice(512 * 512, 24, replace=False), centre]))
+    w = S.cell_weights(f.vol, f.nuc, f.mag, np.eye(3))
+    F_ref = S.dsft(f.pos[:, 1], f.pos[:, 2], w, g[0][idx], g[1][idx])
+    err = amp_error(F[:, idx], F_ref, np.abs(w).sum(1))
+    assert np.all(err <= AMP_TOL), err

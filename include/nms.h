@@ -217,6 +217,32 @@ nms_status nms_correlation(int32_t nq, const double* q, const double* Iq, int32_
  * launches[s] counts the kernel launches of stage s.  Synchronises. */
 nms_status nms_plan_stage_ms(nms_plan_t plan, double ms[8], int64_t launches[8], int32_t reset);
 
+/* Direct Fourier sums with no device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot let a library
+ * allocate GPU memory -- applications whose device memory is owned by their
+ * own allocator or budget, and latency-sensitive loops in which a
+ * cudaMalloc/cudaFree pair would stall or synchronise the device.
+ * It computes the same sums as the FP32_DIRECT path of a plan with identity
+ * rotation and a LIST grid:
+ *   F[c][p] = sum_j w[c][j] exp(-i (qy[p] Y[j] + qz[p] Z[j])),
+ *   out F[c][p][2] = (Re, Im), c = 0..3.
+ *   Y, Z    device [n_cells] FP64 (already rotated) coordinates.
+ *   w       device [4][n_cells] FP64 weights (V N, V M_x, V M_y, V M_z).
+ *   qy, qz  device [n_q] FP64 detector points.
+ *   F       device [4][n_q][2] FP64 output (overwritten).
+ * The only scratch is a 16 MiB array inside the library image (resident on
+ * every GPU that loads libnms until the process exits), so n_q is limited to
+ * 262144 points (a 512 x 512 detector); larger n_q returns
+ * NMS_ERR_INVALID_ARG.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) and caches it: make that first call
+ * before any stream capture.  All calls share the array, so calls whose
+ * kernels can overlap on the GPU (different streams without ordering) race.
+ * Asynchronous on cuda_stream; no cudaMalloc, cudaFree or other allocating
+ * call is made. */
+nms_status nms_dsft_direct_noalloc(int64_t n_cells, const double* Y, const double* Z, const double* w,
+                                   int64_t n_q, const double* qy, const double* qz, double* F,
+                                   void* cuda_stream);
+
 /* Release every device resource of the plan.  NULL is accepted. */
 nms_status nms_plan_destroy(nms_plan_t plan);
 

@@ -68,6 +68,7 @@ SIGNATURES = {
     "nms_correlation": (ctypes.c_int, [ctypes.c_int32, _V, _V, ctypes.c_int32, _V, ctypes.c_double, _V, _V,
                                        ctypes.c_int32, _V]),
     "nms_plan_stage_ms": (ctypes.c_int, [_V, _D, _I64, ctypes.c_int32]),
+    "nms_dsft_direct_noalloc": (ctypes.c_int, [ctypes.c_int64, _V, _V, _V, ctypes.c_int64, _V, _V, _V, _V]),
     "nms_plan_destroy": (ctypes.c_int, [_V]),
     "nms_last_error": (ctypes.c_char_p, []),
     "nms_version": (ctypes.c_char_p, []),
@@ -270,6 +271,14 @@ def nms_plan_stage_ms(plan, reset=False):
     ln = (ctypes.c_int64 * 8)()
     _check(load().nms_plan_stage_ms(plan.handle, ms, ln, 1 if reset else 0))
     return {STAGES[i]: (ms[i], ln[i]) for i in range(8)}
+
+
+def nms_dsft_direct_noalloc(Y, Z, w, qy, qz, F, stream=None):
+    """Direct sums into a caller-owned device tensor F [4, n_q, 2] without any
+    device allocation by the library (all arguments are float64 CUDA tensors)."""
+    _check(load().nms_dsft_direct_noalloc(Y.numel(), _ptr(Y), _ptr(Z), _ptr(w), qy.numel(), _ptr(qy), _ptr(qz),
+                                          _ptr(F), ctypes.c_void_p(stream or 0)))
+    return F
 
 
 def nms_plan_destroy(plan):

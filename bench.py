@@ -74,9 +74,26 @@ def make_workload(name):
         edges = np.linspace(0.0, 1.0, 65)
         r = np.linspace(0.0, 40.0, 64)
         desc = "sphere R=16nm a=2nm (2109 cells) seeded vortex; 128x128 detector [-1,1]^2 nm^-1"
+    elif name == "ensemble":
+        f = I.sphere_ensemble(n_spheres=10000, median=8.0, sigma=0.35, clip=(5.0, 20.0), a=1.0, cube=2000.0, seed=3)
+        grid = dict(kind="cartesian", n0=256, n1=256, lo0=-1.0, hi0=1.0, lo1=-1.0, hi1=1.0)
+        edges = np.linspace(0.0, 1.0, 129)
+        r = np.linspace(0.0, 60.0, 64)
+        desc = (f"ensemble of 10000 spheres, lognormal R (median 8nm, sigma 0.35, 5-20nm) a=1nm ({f.n} cells), "
+                "Neel-like canting, 2um cube; 256x256 detector [-1,1]^2 nm^-1; dilute + total + interference")
+        return f, grid, edges, r, desc, None, True
+    elif name == "rotations":
+        f = I.ellipsoid_uniform((40.0, 25.0, 25.0), a=0.8, seed=4)
+        rot = I.random_rotations(4096, seed=5)
+        grid = dict(kind="cartesian", n0=256, n1=256, lo0=-2.0, hi0=2.0, lo1=-2.0, hi1=2.0)
+        edges = np.geomspace(0.01, 2.0, 129)
+        r = np.linspace(0.0, 120.0, 64)
+        desc = (f"ellipsoid 40/25/25nm a=0.8nm ({f.n} cells) uniform M, 4096 random orientations (Shoemake); "
+                "256x256 detector [-2,2]^2 nm^-1; 128 log bins 0.01-2 nm^-1")
+        return f, grid, edges, r, desc, rot, False
     else:
         raise SystemExit(f"unknown workload {name}")
-    return f, grid, edges, r, desc
+    return f, grid, edges, r, desc, None, False
 
 
 # ----------------------------------------------------------------- clocks
@@ -132,15 +149,19 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- oracle timing
-def oracle_sample_rate(field, grid_kw, target_s=12.0, seed=0):
-    """Oracle terms/s on a random sample of pixels (all cells); returns (rate, sample, F_ref, idx)."""
+def oracle_sample_rate(field, grid_kw, target_s=12.0, seed=0, R=None):
+    """Oracle terms/s on a random sample of pixels (all cells, rotation R, object
+    centres applied); returns (rate, sample, F_ref, idx, threads)."""
     from oracle import sans as S
     kw = dict(grid_kw)
     kind = kw.pop("kind")
     g = S.q_grid(kind, **kw)
     rng = np.random.default_rng(seed)
-    w = S.cell_weights(field.vol, field.nuc, field.mag, np.eye(3))
-    Y, Z = field.pos[:, 1].copy(), field.pos[:, 2].copy()
+    R = np.eye(3) if R is None else R
+    w = S.cell_weights(field.vol, field.nuc, field.mag, R)
+    pr = S.rotate_cells(field.pos, R, field.offsets, field.centers)
+    Y, Z = pr[:, 1].copy(), pr[:, 2].copy()
+    del pr
     npix = g[0].shape[0]
     probe = rng.choice(npix, size=min(8, npix), replace=False)
     t0 = time.perf_counter()
@@ -193,7 +214,7 @@ def run_reference(args):
     rank, world = dist_setup(args.gpus)
     if rank != 0:
         return 0
-    field, grid_kw, edges, r, desc = make_workload(args.workload)
+    field, grid_kw, edges, r, desc, rot, dilute = make_workload(args.workload)
     from oracle import sans as S
     kw = dict(grid_kw)
     kind = kw.pop("kind")
@@ -232,7 +253,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nms", choices=["nms", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "tc", "direct", "naive"])
-    ap.add_argument("--workload", default="box", choices=["box", "box64", "sphere"])
+    ap.add_argument("--workload", default="box", choices=["box", "box64", "sphere", "ensemble", "rotations"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kc", type=int, default=0, help="cells per TMEM accumulation chunk (0: library default)")
     ap.add_argument("--workspace-gb", type=float, default=0.0)
@@ -249,16 +270,18 @@ def main():
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     nms.load()
-    field, grid_kw, edges, r, desc = make_workload(args.workload)
+    field, grid_kw, edges, r, desc, rot, dilute = make_workload(args.workload)
     prec = {"auto": nms.PREC_AUTO, "tc": nms.PREC_TC_F16X3, "direct": nms.PREC_FP32_DIRECT,
             "naive": nms.PREC_FP32_NAIVE}[args.precision]
     stream = torch.cuda.current_stream()
     g = nms.make_grid(**grid_kw)
-    opt = nms.nms_options_default(precision=prec, timing=1, kc_cells=args.kc,
+    opt = nms.nms_options_default(precision=prec, timing=1, kc_cells=args.kc, want_dilute=1 if dilute else 0,
                                   workspace_bytes=int(args.workspace_gb * (1 << 30)))
-    plan = nms.plan_from_field(field, g, opt, stream=stream.cuda_stream)
+    plan = nms.plan_from_field(field, g, opt, rot=rot, stream=stream.cuda_stream)
     npix = plan.npix
-    terms = float(field.n) * npix
+    n_rot = 1 if rot is None else len(rot)
+    # with the dilute split the per-object form factors are the summed terms
+    terms = float(field.n) * npix * n_rot
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     img_u = torch.empty(npix, dtype=torch.float64, device="cuda")
     img_s = torch.empty(npix, dtype=torch.float64, device="cuda")
@@ -323,10 +346,11 @@ def main():
     cpu = None
     err = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, sample, F_ref, idx, cores = oracle_sample_rate(field, grid_kw, args.cpu_seconds)
+        R_last = np.eye(3) if rot is None else rot[-1]
+        rate, sample, F_ref, idx, cores = oracle_sample_rate(field, grid_kw, args.cpu_seconds, R=R_last)
         F = nms.nms_get_amplitudes(plan)
         from oracle import sans as S
-        wsum = np.abs(S.cell_weights(field.vol, field.nuc, field.mag, np.eye(3))).sum(1)
+        wsum = np.abs(S.cell_weights(field.vol, field.nuc, field.mag, R_last)).sum(1)
         err = [float(np.max(np.abs(F[c][idx] - F_ref[c])) / wsum[c]) if wsum[c] > 0 else 0.0 for c in range(4)]
         cpu = {"value": rate, "unit": "terms/s", "cores": cores, "kind": "oracle", "sample": sample}
 
@@ -345,8 +369,8 @@ def main():
         for _ in range(2):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            p2 = nms.nms_plan_create(pin["pos"], pin["vol"], pin["nuc"], pin["mag"], grid=g, opt=opt,
-                                     stream=stream.cuda_stream)
+            p2 = nms.nms_plan_create(pin["pos"], pin["vol"], pin["nuc"], pin["mag"], field.offsets, field.centers,
+                                     rot, grid=g, opt=opt, stream=stream.cuda_stream)
             nms.nms_amplitudes(p2)
             nms.nms_response(p2, "UNPOL", out=out_u)
             nms.nms_response(p2, "SF", out=out_s)

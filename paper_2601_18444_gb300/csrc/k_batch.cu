@@ -1,0 +1,195 @@
+// Batch kernels of the tensor path: per-rotation preparation into stacked
+// arrays, and the accumulation of many amplitudes F_o (objects and/or
+// rotations) into the Hermitian products G and the total amplitude.
+//
+// Paper, Sec. "Summation approach", interparticle decomposition:
+//   |sum_k F_k e^{-iq.r^k}|^2 = sum_k |F_k|^2 + cross terms;
+// the dilute part is G_dil = sum_k F_k F_k^dagger, the total amplitude is
+// F_tot = sum_k F_k exp(-i q.(R r^k)) (object k moved to its rotated centre),
+// and orientation averages add G over rotations.
+//
+// GB300: FP64 is slow on this part, so the products are formed in FP32 from
+// the FP64 amplitudes and accumulated in two-float (hi, lo) registers; the
+// FP64 arrays in HBM are touched once per batch.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "nms_internal.h"
+
+namespace nms {
+
+__device__ __forceinline__ float4 split_pos(double y, double z)
+{
+    const float yh = (float)y, zh = (float)z;
+    return make_float4(yh, (float)(y - (double)yh), zh, (float)(z - (double)zh));
+}
+
+// Rotated positions (global R(x + r^k) or local R x) and rotated weights of
+// one rotation, written at the given offset of the stacked arrays.
+__global__ void k_prep_rot(int64_t n, const double* __restrict__ pos, const double* __restrict__ vol,
+                           const double* __restrict__ nuc, const double* __restrict__ mag,
+                           const double* __restrict__ cen_cell, RotMat R, float4* __restrict__ cpos,
+                           float4* __restrict__ cw)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double x = pos[3 * j], y = pos[3 * j + 1], z = pos[3 * j + 2];
+    if (cen_cell) {
+        x += cen_cell[3 * j];
+        y += cen_cell[3 * j + 1];
+        z += cen_cell[3 * j + 2];
+    }
+    const double* r = R.m;
+    cpos[j] = split_pos(r[3] * x + r[4] * y + r[5] * z, r[6] * x + r[7] * y + r[8] * z);
+    const double v = vol ? vol[j] : 1.0;
+    const double wn = nuc ? v * nuc[j] : 0.0;
+    double wx = 0.0, wy = 0.0, wz = 0.0;
+    if (mag) {
+        const double mx = mag[3 * j], my = mag[3 * j + 1], mz = mag[3 * j + 2];
+        wx = v * (r[0] * mx + r[1] * my + r[2] * mz);
+        wy = v * (r[3] * mx + r[4] * my + r[5] * mz);
+        wz = v * (r[6] * mx + r[7] * my + r[8] * mz);
+    }
+    cw[j] = make_float4((float)wn, (float)wx, (float)wy, (float)wz);
+}
+
+cudaError_t launch_prep_rot(const Plan& p, const RotMat& R, bool global, float4* cpos, float4* cw, cudaStream_t s)
+{
+    const int64_t n = p.n_cells;
+    k_prep_rot<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, p.d_pos, p.d_vol, p.d_nuc, p.d_mag,
+                                                           global ? p.d_cen_cell : nullptr, R, cpos, cw);
+    return cudaGetLastError();
+}
+
+// Rotated centre of each output: (Y, Z) rows of R_rot r^obj, as two-float.
+__global__ void k_centres(int n_out, const int32_t* __restrict__ out_obj, const int32_t* __restrict__ out_rot,
+                          int rot0, const double* __restrict__ rot, const double* __restrict__ cen,
+                          float4* __restrict__ cyz)
+{
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n_out) return;
+    const double* r = rot + 9 * (int64_t)(rot0 + out_rot[o]);
+    const double* c = cen + 3 * (int64_t)out_obj[o];
+    cyz[o] = split_pos(r[3] * c[0] + r[4] * c[1] + r[5] * c[2], r[6] * c[0] + r[7] * c[1] + r[8] * c[2]);
+}
+
+cudaError_t launch_centres(int n_out, const int32_t* out_obj, const int32_t* out_rot, int rot0, const double* rot,
+                           const double* cen, float4* cyz, cudaStream_t s)
+{
+    k_centres<<<(n_out + 127) / 128, 128, 0, s>>>(n_out, out_obj, out_rot, rot0, rot, cen, cyz);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ void ts_acc(float& hi, float& lo, float x)
+{
+    const float s = hi + x;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (x - bb);
+    hi = s;
+}
+
+__device__ __forceinline__ int pair_idx(int a, int b)  // a < b
+{
+    return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
+}
+
+// G[16][npix] += sum_o F_o F_o^dagger (F: [n_out][4][npix] complex FP64).
+__global__ void k_gacc_batch(const double2* __restrict__ F, int n_out, int64_t npix, double* __restrict__ G)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    float hi[16], lo[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) { hi[k] = 0.f; lo[k] = 0.f; }
+    for (int o = 0; o < n_out; ++o) {
+        float2 f[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const double2 v = F[((int64_t)o * 4 + c) * npix + p];
+            f[c] = make_float2((float)v.x, (float)v.y);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) ts_acc(hi[a], lo[a], fmaf(f[a].x, f[a].x, f[a].y * f[a].y));
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = a + 1; b < 4; ++b) {
+                const int k = pair_idx(a, b);
+                ts_acc(hi[4 + 2 * k], lo[4 + 2 * k], fmaf(f[a].x, f[b].x, f[a].y * f[b].y));
+                ts_acc(hi[5 + 2 * k], lo[5 + 2 * k], fmaf(f[a].y, f[b].x, -f[a].x * f[b].y));
+            }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) G[(int64_t)k * npix + p] += (double)hi[k] + (double)lo[k];
+}
+
+cudaError_t launch_gacc_batch(const double* F, int n_out, int64_t npix, double* G, cudaStream_t s)
+{
+    if (n_out <= 0) return cudaSuccess;
+    k_gacc_batch<<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(reinterpret_cast<const double2*>(F), n_out, npix, G);
+    return cudaGetLastError();
+}
+
+// Ftot[out_rot[o]][c][p] += F_o[c][p] exp(-i (q_y cy_o + q_z cz_o)); the
+// phase is a two-float product in turns reduced exactly (as in the direct
+// sum).  Outputs are ordered by rotation, so each thread flushes its
+// two-float sums to FP64 once per rotation.
+__global__ void k_shift_batch(const double2* __restrict__ F, int n_out, const float4* __restrict__ cyz,
+                              const int32_t* __restrict__ out_rot, const float4* __restrict__ qturn, int64_t npix,
+                              double2* __restrict__ Ftot)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    const float4 q = qturn[p];
+    float hi[8], lo[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { hi[k] = 0.f; lo[k] = 0.f; }
+    int cur = n_out > 0 ? out_rot[0] : 0;
+    for (int o = 0; o <= n_out; ++o) {
+        const int r = o < n_out ? out_rot[o] : -1;
+        if (r != cur) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                double2* t = Ftot + ((int64_t)cur * 4 + c) * npix + p;
+                double2 v = *t;
+                v.x += (double)hi[2 * c] + (double)lo[2 * c];
+                v.y += (double)hi[2 * c + 1] + (double)lo[2 * c + 1];
+                *t = v;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) { hi[k] = 0.f; lo[k] = 0.f; }
+            cur = r;
+        }
+        if (o == n_out) break;
+        const float4 cc = cyz[o];
+        const float py = q.x * cc.x;
+        const float ey = fmaf(q.x, cc.x, -py) + fmaf(q.x, cc.y, q.y * cc.x);
+        const float pz = q.z * cc.z;
+        const float ez = fmaf(q.z, cc.z, -pz) + fmaf(q.z, cc.w, q.w * cc.z);
+        const float sm = py + pz;
+        const float bb = sm - py;
+        const float es = (py - (sm - bb)) + (pz - bb);
+        const float t = (sm - rintf(sm)) + (es + ey + ez);
+        float sn, cs;
+        sincospif(2.0f * t, &sn, &cs);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const double2 v = F[((int64_t)o * 4 + c) * npix + p];
+            const float fr = (float)v.x, fi = (float)v.y;
+            ts_acc(hi[2 * c], lo[2 * c], fmaf(fr, cs, fi * sn));
+            ts_acc(hi[2 * c + 1], lo[2 * c + 1], fmaf(fi, cs, -fr * sn));
+        }
+    }
+}
+
+cudaError_t launch_shift_batch(const double* F, int n_out, const float4* cyz, const int32_t* out_rot,
+                               const float4* qturn, int64_t npix, double* Ftot, cudaStream_t s)
+{
+    if (n_out <= 0) return cudaSuccess;
+    k_shift_batch<<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(reinterpret_cast<const double2*>(F), n_out, cyz,
+                                                                 out_rot, qturn, npix,
+                                                                 reinterpret_cast<double2*>(Ftot));
+    return cudaGetLastError();
+}
+
+}  // namespace nms

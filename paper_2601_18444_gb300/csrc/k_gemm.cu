@@ -46,6 +46,9 @@ constexpr int TC_EPI_WARPS = 16;    // 4 per TMEM lane quadrant, 32 accumulator 
 constexpr float TC_SCALE = 4096.0f; // operand scale 2^12
 
 // ------------------------------------------------------------------ tables
+// Tables cover a list of k-blocks; k-block kb holds the cells
+// [kb_cell0[kb], kb_cell0[kb] + kb_ncell[kb]) (kb_ncell <= 32) of the stacked
+// per-rotation cell arrays, the rest of the block is zero padding.
 __device__ __forceinline__ uint32_t swz_offset(int row, int k)
 {
     // byte offset of element (row, k) of a 128 x 64 fp16 block, 128B swizzle
@@ -58,11 +61,9 @@ __device__ __forceinline__ void split_h(float x, __half& h, __half& l)
     l = __float2half_rn(x - __half2float(h));
 }
 
-__device__ __forceinline__ float turns_reduced(float2 q, float4 c, bool use_z)
+__device__ __forceinline__ float turns_reduced(float2 q, float xh, float xl)
 {
     // two-float product q' * coordinate (turns) reduced to [-1/2, 1/2]
-    float xh = use_z ? c.z : c.x;
-    float xl = use_z ? c.w : c.y;
     float p = q.x * xh;
     float e = fmaf(q.x, xh, -p) + fmaf(q.x, xl, q.y * xh);
     float n = rintf(p);
@@ -75,29 +76,31 @@ union H8 {
 };
 
 // A tables: block (mt, kb) holds rows m = mt*128 + 4*a_loc + c, a_loc < 32,
-// and k = 64 kb + 2 j_loc + p.  Thread (a_loc, chunk): 4 cells x 4 channels.
+// and k = 2 j_loc + p.  Thread (a_loc, chunk): 4 cells x 4 channels.
 __global__ void __launch_bounds__(256)
-k_tables_a(const float4* __restrict__ cpos, const float4* __restrict__ cw, int64_t j0, int64_t ncell,
-           const float2* __restrict__ qy, int ny, float4 wscale, int64_t nkb, uint8_t* __restrict__ A_hi,
-           uint8_t* __restrict__ A_lo)
+k_tables_a(const float4* __restrict__ cpos, const float4* __restrict__ cw, const int64_t* __restrict__ kb_cell0,
+           const int32_t* __restrict__ kb_ncell, const float2* __restrict__ qy, int ny, float4 wscale, int64_t nkb,
+           uint8_t* __restrict__ A_hi, uint8_t* __restrict__ A_lo)
 {
-    const int kb = blockIdx.x;
+    const int64_t kb = blockIdx.x;
     const int mt = blockIdx.y;
     const int a_loc = threadIdx.x >> 3;
     const int chunk = threadIdx.x & 7;
     const int a = mt * 32 + a_loc;
+    const int64_t c0 = kb_cell0[kb];
+    const int nc = kb_ncell[kb];
     H8 hi[4], lo[4];
     const bool arow = a < ny;
     const float2 q = arow ? qy[a] : make_float2(0.f, 0.f);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        const int64_t jl = (int64_t)kb * 32 + chunk * 4 + u;
+        const int jl = chunk * 4 + u;
         float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
         float sn = 0.f, cs = 0.f;
-        if (arow && jl < ncell) {
-            const float4 c = cpos[j0 + jl];
-            w = cw[j0 + jl];
-            float t = turns_reduced(q, c, false);
+        if (arow && jl < nc) {
+            const float4 c = cpos[c0 + jl];
+            w = cw[c0 + jl];
+            float t = turns_reduced(q, c.x, c.y);
             sincospif(2.0f * t, &sn, &cs);
         }
         const float wv[4] = {w.x * wscale.x, w.y * wscale.y, w.z * wscale.z, w.w * wscale.w};
@@ -119,24 +122,26 @@ k_tables_a(const float4* __restrict__ cpos, const float4* __restrict__ cw, int64
 
 // B tables: block (nt, kb) holds rows n = nt*128 + 2*b_loc + r, b_loc < 64.
 __global__ void __launch_bounds__(512)
-k_tables_b(const float4* __restrict__ cpos, int64_t j0, int64_t ncell, const float2* __restrict__ qz, int nz,
-           int64_t nkb, uint8_t* __restrict__ B_hi, uint8_t* __restrict__ B_lo)
+k_tables_b(const float4* __restrict__ cpos, const int64_t* __restrict__ kb_cell0, const int32_t* __restrict__ kb_ncell,
+           const float2* __restrict__ qz, int nz, int64_t nkb, uint8_t* __restrict__ B_hi, uint8_t* __restrict__ B_lo)
 {
-    const int kb = blockIdx.x;
+    const int64_t kb = blockIdx.x;
     const int nt = blockIdx.y;
     const int b_loc = threadIdx.x >> 3;
     const int chunk = threadIdx.x & 7;
     const int b = nt * 64 + b_loc;
+    const int64_t c0 = kb_cell0[kb];
+    const int nc = kb_ncell[kb];
     const bool brow = b < nz;
     const float2 q = brow ? qz[b] : make_float2(0.f, 0.f);
     H8 hr, lr, hi_, li_;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        const int64_t jl = (int64_t)kb * 32 + chunk * 4 + u;
+        const int jl = chunk * 4 + u;
         float sn = 0.f, cs = 0.f;
-        if (brow && jl < ncell) {
-            const float4 c = cpos[j0 + jl];
-            float t = turns_reduced(q, c, true);
+        if (brow && jl < nc) {
+            const float4 c = cpos[c0 + jl];
+            float t = turns_reduced(q, c.z, c.w);
             sincospif(2.0f * t, &sn, &cs);
         }
         cs *= TC_SCALE;
@@ -183,13 +188,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
 {
+    // the waiting thread is suspended (up to the hint, in ns) until the phase
+    // completes instead of spinning on the issue slots
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(200000u)
         : "memory");
     return ok != 0;
 }
@@ -320,16 +327,27 @@ __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N)
 }
 
 // ------------------------------------------------------------------ GEMM
+// Persistent: gridDim.x CTAs (one per SM) walk the work list round-robin;
+// TMEM, barriers and the stage ring stay live across items.  An item is one
+// 128 x 128 output tile over a k-block range of the chunk's tables; its
+// unscaled FP64 result goes to P[slot] (128 x 128, row-major).
+struct GemmItem {
+    int32_t mt, nt;       // A / B tile rows
+    int32_t kb0, kb1;     // k-block range (within this chunk's tables)
+    int32_t slot;         // output slot in P
+    int32_t pad;
+};
+
 struct GemmArgs {
     const uint8_t* A_hi;
     const uint8_t* A_lo;
     const uint8_t* B_hi;
     const uint8_t* B_lo;
-    int64_t nkb;          // k-blocks in the tables of this launch
-    int mtiles, ntiles;
-    int splits;           // K splits (gridDim.z)
+    int64_t nkb;          // k-blocks in the tables of this launch (block stride)
+    const GemmItem* items;
+    int n_items;
     int kcb;              // k-blocks per TMEM chunk (drain interval)
-    double* P;            // [splits][mtiles*128][ntiles*128] partial sums (FP64)
+    double* P;            // [slots][128][128]
     int32_t* err;
     uint64_t limit_ns;
 };
@@ -347,13 +365,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int nt = blockIdx.x, mt = blockIdx.y, sp = blockIdx.z;
-    // this CTA's k-block range
-    const int64_t kb0 = (g.nkb * sp) / g.splits;
-    const int64_t kb1 = (g.nkb * (sp + 1)) / g.splits;
-    const int nkb_me = (int)(kb1 - kb0);
-    const int nchunks = (nkb_me + g.kcb - 1) / g.kcb;
-
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
 
     if (threadIdx.x == 0) {
@@ -383,83 +394,91 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
     if (warp == 0) {
         // ---------------- producer: bulk copies of the four operand blocks
         if (lane == 0) {
-            int64_t issued = 0;
-            for (int64_t i = 0; i < nkb_me; ++i) {
-                const int s = (int)(i % TC_STAGES);
-                const uint32_t par = (uint32_t)((i / TC_STAGES) & 1) ^ 1u;
-                if (!mbar_wait(&bar_empty[s], par, g.limit_ns, &s_abort)) {
-                    s_abort = 1;
-                    atomicExch(g.err, 1);
-                    break;
+            int64_t i = 0;              // stage sequence number across items
+            bool ok = true;
+            for (int it = blockIdx.x; it < g.n_items && ok; it += gridDim.x) {
+                const GemmItem item = g.items[it];
+                for (int kb = item.kb0; kb < item.kb1; ++kb) {
+                    const int s = (int)(i % TC_STAGES);
+                    const uint32_t par = (uint32_t)((i / TC_STAGES) & 1) ^ 1u;
+                    if (!mbar_wait(&bar_empty[s], par, g.limit_ns, &s_abort)) {
+                        s_abort = 1;
+                        atomicExch(g.err, 1);
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t st = sbase + (uint32_t)s * TC_STAGE_BYTES;
+                    mbar_arrive_expect_tx(&bar_full[s], TC_STAGE_BYTES);
+                    const size_t ao = ((size_t)item.mt * g.nkb + kb) * TC_BLOCK_BYTES;
+                    const size_t bo = ((size_t)item.nt * g.nkb + kb) * TC_BLOCK_BYTES;
+                    bulk_g2s(st, g.A_hi + ao, TC_BLOCK_BYTES, &bar_full[s]);
+                    bulk_g2s(st + TC_BLOCK_BYTES, g.A_lo + ao, TC_BLOCK_BYTES, &bar_full[s]);
+                    bulk_g2s(st + 2 * TC_BLOCK_BYTES, g.B_hi + bo, TC_BLOCK_BYTES, &bar_full[s]);
+                    bulk_g2s(st + 3 * TC_BLOCK_BYTES, g.B_lo + bo, TC_BLOCK_BYTES, &bar_full[s]);
+                    ++i;
                 }
-                const int64_t kb = kb0 + i;
-                const uint32_t st = sbase + (uint32_t)s * TC_STAGE_BYTES;
-                mbar_arrive_expect_tx(&bar_full[s], TC_STAGE_BYTES);
-                const size_t ao = ((size_t)mt * g.nkb + kb) * TC_BLOCK_BYTES;
-                const size_t bo = ((size_t)nt * g.nkb + kb) * TC_BLOCK_BYTES;
-                bulk_g2s(st, g.A_hi + ao, TC_BLOCK_BYTES, &bar_full[s]);
-                bulk_g2s(st + TC_BLOCK_BYTES, g.A_lo + ao, TC_BLOCK_BYTES, &bar_full[s]);
-                bulk_g2s(st + 2 * TC_BLOCK_BYTES, g.B_hi + bo, TC_BLOCK_BYTES, &bar_full[s]);
-                bulk_g2s(st + 3 * TC_BLOCK_BYTES, g.B_lo + bo, TC_BLOCK_BYTES, &bar_full[s]);
-                ++issued;
             }
             // copies in flight must land before the CTA exits (bounded): only
             // the last TC_STAGES issued stages can still be pending
-            for (int64_t i = (issued > TC_STAGES ? issued - TC_STAGES : 0); i < issued; ++i) {
-                const int s = (int)(i % TC_STAGES);
-                const uint32_t par = (uint32_t)((i / TC_STAGES) & 1);
+            for (int64_t k = (i > TC_STAGES ? i - TC_STAGES : 0); k < i; ++k) {
+                const int s = (int)(k % TC_STAGES);
+                const uint32_t par = (uint32_t)((k / TC_STAGES) & 1);
                 mbar_wait(&bar_full[s], par, g.limit_ns, &s_abort);
             }
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer
+        // ---------------- MMA issuer (one thread)
         if (lane == 0) {
             const uint32_t idesc = idesc_f16_f32(TC_BM, TC_BN);
-            int i = 0;
+            int64_t i = 0;              // stage sequence number
+            int64_t c = 0;              // TMEM chunk sequence number
             bool ok = true;
-            for (int c = 0; c < nchunks && ok; ++c) {
-                const int b = (int)(c & 1);
-                const uint32_t apar = (uint32_t)((c >> 1) & 1) ^ 1u;
-                if (!mbar_wait(&bar_acc_empty[b], apar, g.limit_ns, &s_abort)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t d0 = taddr + (uint32_t)b * 256u;
-                const uint32_t d1 = d0 + 128u;
-                const int kend = (c + 1) * g.kcb < nkb_me ? (c + 1) * g.kcb : nkb_me;
-                bool first = true;
-                for (; i < kend; ++i) {
-                    const int s = (int)(i % TC_STAGES);
-                    const uint32_t par = (uint32_t)((i / TC_STAGES) & 1);
-                    if (!mbar_wait(&bar_full[s], par, g.limit_ns, &s_abort)) {
+            for (int it = blockIdx.x; it < g.n_items && ok; it += gridDim.x) {
+                const GemmItem item = g.items[it];
+                for (int k0 = item.kb0; k0 < item.kb1 && ok; k0 += g.kcb, ++c) {
+                    const int b = (int)(c & 1);
+                    const uint32_t apar = (uint32_t)((c >> 1) & 1) ^ 1u;
+                    if (!mbar_wait(&bar_acc_empty[b], apar, g.limit_ns, &s_abort)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t st = sbase + (uint32_t)s * TC_STAGE_BYTES;
+                    const uint32_t d0 = taddr + (uint32_t)b * 256u;
+                    const uint32_t d1 = d0 + 128u;
+                    const int k1 = min(item.kb1, k0 + g.kcb);
+                    bool first = true;
+                    for (int kb = k0; kb < k1; ++kb, ++i) {
+                        const int s = (int)(i % TC_STAGES);
+                        const uint32_t par = (uint32_t)((i / TC_STAGES) & 1);
+                        if (!mbar_wait(&bar_full[s], par, g.limit_ns, &s_abort)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t st = sbase + (uint32_t)s * TC_STAGE_BYTES;
 #pragma unroll
-                    for (int k16 = 0; k16 < 4; ++k16) {
-                        const uint64_t ah = sw128_desc(st + k16 * 32);
-                        const uint64_t al = sw128_desc(st + TC_BLOCK_BYTES + k16 * 32);
-                        const uint64_t bh = sw128_desc(st + 2 * TC_BLOCK_BYTES + k16 * 32);
-                        const uint64_t bl = sw128_desc(st + 3 * TC_BLOCK_BYTES + k16 * 32);
-                        const uint32_t acc = first ? 0u : 1u;
-                        tc_mma_f16(d0, ah, bh, idesc, acc);
-                        tc_mma_f16(d1, ah, bl, idesc, acc);
-                        tc_mma_f16(d1, al, bh, idesc, 1u);
-                        first = false;
+                        for (int k16 = 0; k16 < 4; ++k16) {
+                            const uint64_t ah = sw128_desc(st + k16 * 32);
+                            const uint64_t al = sw128_desc(st + TC_BLOCK_BYTES + k16 * 32);
+                            const uint64_t bh = sw128_desc(st + 2 * TC_BLOCK_BYTES + k16 * 32);
+                            const uint64_t bl = sw128_desc(st + 3 * TC_BLOCK_BYTES + k16 * 32);
+                            const uint32_t acc = first ? 0u : 1u;
+                            tc_mma_f16(d0, ah, bh, idesc, acc);
+                            tc_mma_f16(d1, ah, bl, idesc, acc);
+                            tc_mma_f16(d1, al, bh, idesc, 1u);
+                            first = false;
+                        }
+                        tc_commit(&bar_empty[s]);
                     }
-                    tc_commit(&bar_empty[s]);
+                    if (!ok) break;
+                    tc_commit(&bar_acc_full[b]);
                 }
-                if (!ok) break;
-                tc_commit(&bar_acc_full[b]);
             }
             if (!ok) {
                 s_abort = 1;
                 atomicExch(g.err, 2);
             }
-            // all MMAs issued by this thread complete before TMEM is freed
+            // every MMA issued by this thread completes before TMEM is freed
             tc_commit(&bar_final);
             mbar_wait(&bar_final, 0, g.limit_ns, &s_abort);
         }
@@ -468,56 +487,62 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
         const int e = warp - 2;
         const int quad = warp & 3;                 // TMEM lane quadrant of this warp
         const int colh = (e >> 2) * 32;            // column quarter
-        // two-float running sums, two columns per 64-bit register
-        uint64_t hi[16], lo[16];
+        int64_t c = 0;
+        bool ok = true;
+        for (int it = blockIdx.x; it < g.n_items && ok; it += gridDim.x) {
+            const GemmItem item = g.items[it];
+            // two-float running sums, two columns per 64-bit register
+            uint64_t hi[16], lo[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) { hi[i] = 0ull; lo[i] = 0ull; }
-        for (int c = 0; c < nchunks; ++c) {
-            const int b = (int)(c & 1);
-            const uint32_t par = (uint32_t)((c >> 1) & 1);
-            int okw = 0;
-            if (lane == 0) okw = mbar_wait(&bar_acc_full[b], par, g.limit_ns, &s_abort) ? 1 : 0;
-            okw = __shfl_sync(0xffffffffu, okw, 0);
-            if (!okw) {
-                if (lane == 0) {
-                    s_abort = 1;
-                    atomicExch(g.err, 3);
+            for (int i = 0; i < 16; ++i) { hi[i] = 0ull; lo[i] = 0ull; }
+            for (int k0 = item.kb0; k0 < item.kb1; k0 += g.kcb, ++c) {
+                const int b = (int)(c & 1);
+                const uint32_t par = (uint32_t)((c >> 1) & 1);
+                int okw = 0;
+                if (lane == 0) okw = mbar_wait(&bar_acc_full[b], par, g.limit_ns, &s_abort) ? 1 : 0;
+                okw = __shfl_sync(0xffffffffu, okw, 0);
+                if (!okw) {
+                    if (lane == 0) {
+                        s_abort = 1;
+                        atomicExch(g.err, 3);
+                    }
+                    ok = false;
+                    break;
                 }
-                break;
-            }
-            tc_fence_after();
-            const uint32_t base = taddr + ((uint32_t)(quad * 32) << 16) + (uint32_t)b * 256u + (uint32_t)colh;
+                tc_fence_after();
+                const uint32_t base = taddr + ((uint32_t)(quad * 32) << 16) + (uint32_t)b * 256u + (uint32_t)colh;
 #pragma unroll
-            for (int cb = 0; cb < 8; ++cb) {
-                float v0[4], v1[4];
-                tmem_ld4(base + cb * 4, v0);
-                tmem_ld4(base + 128 + cb * 4, v1);
-                tmem_wait_ld();
+                for (int cb = 0; cb < 8; ++cb) {
+                    float v0[4], v1[4];
+                    tmem_ld4(base + cb * 4, v0);
+                    tmem_ld4(base + 128 + cb * 4, v1);
+                    tmem_wait_ld();
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int idx = cb * 2 + u;
-                    // x = D0 + D1; TwoSum(hi, x) -> (s, er); hi = s; lo += er
-                    const uint64_t x = f2_add(f2_pack(v0[2 * u], v0[2 * u + 1]), f2_pack(v1[2 * u], v1[2 * u + 1]));
-                    const uint64_t sm = f2_add(hi[idx], x);
-                    const uint64_t bb = f2_sub(sm, hi[idx]);
-                    const uint64_t er = f2_add(f2_sub(hi[idx], f2_sub(sm, bb)), f2_sub(x, bb));
-                    hi[idx] = sm;
-                    lo[idx] = f2_add(lo[idx], er);
+                    for (int u = 0; u < 2; ++u) {
+                        const int idx = cb * 2 + u;
+                        // x = D0 + D1; TwoSum(hi, x) -> (s, er); hi = s; lo += er
+                        const uint64_t x =
+                            f2_add(f2_pack(v0[2 * u], v0[2 * u + 1]), f2_pack(v1[2 * u], v1[2 * u + 1]));
+                        const uint64_t sm = f2_add(hi[idx], x);
+                        const uint64_t bb = f2_sub(sm, hi[idx]);
+                        const uint64_t er = f2_add(f2_sub(hi[idx], f2_sub(sm, bb)), f2_sub(x, bb));
+                        hi[idx] = sm;
+                        lo[idx] = f2_add(lo[idx], er);
+                    }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar_acc_empty[b]);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&bar_acc_empty[b]);
-        }
-        // partial sums of this split, unscaled, FP64
-        const int64_t ldn = (int64_t)g.ntiles * TC_BN;
-        const int64_t row = (int64_t)mt * TC_BM + quad * 32 + lane;
-        double* out = g.P + ((int64_t)sp * g.mtiles * TC_BM + row) * ldn + (int64_t)nt * TC_BN + colh;
+            if (!ok) break;
+            // this item's tile, unscaled, FP64
+            double* out = g.P + (int64_t)item.slot * (TC_BM * TC_BN) + (int64_t)(quad * 32 + lane) * TC_BN + colh;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            double2 v = make_double2((double)f2_lane0(hi[i]) + (double)f2_lane0(lo[i]),
-                                     (double)f2_lane1(hi[i]) + (double)f2_lane1(lo[i]));
-            reinterpret_cast<double2*>(out)[i] = v;
+            for (int i = 0; i < 16; ++i) {
+                double2 v = make_double2((double)f2_lane0(hi[i]) + (double)f2_lane0(lo[i]),
+                                         (double)f2_lane1(hi[i]) + (double)f2_lane1(lo[i]));
+                reinterpret_cast<double2*>(out)[i] = v;
+            }
         }
     }
     tc_fence_before();
@@ -528,190 +553,103 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
     }
 }
 
-// F[c][p][r] += scale_c * sum_s P[s][4a + c][2b + r], p = a*nz + b
+// Reduction of item tiles into per-output amplitudes:
+//   F[out][c][p][r] += scale_c * sum_{s < splits} P[slot_base + (mt*ntiles + nt)*splits + s][row][col]
+// with m = 4a + c = mt*128 + row, n = 2b + r = nt*128 + col, p = a*nz + b.
+struct RedDesc {
+    int32_t slot_base;
+    int32_t splits;
+    int32_t out;
+    int32_t pad;
+};
+
 struct Scale4 {
     double v[4];
 };
 
-__global__ void k_gemm_reduce(const double* __restrict__ P, int splits, int64_t ldm, int64_t ldn, int ny, int nz,
-                              Scale4 scale, double* __restrict__ F)
+__global__ void k_gemm_reduce(const double* __restrict__ P, const RedDesc* __restrict__ reds, int n_red, int ny,
+                              int nz, int ntiles, Scale4 scale, double* __restrict__ F)
 {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t npix = (int64_t)ny * nz;
-    if (idx >= npix * 4) return;
-    const int c = (int)(idx / npix);
-    const int64_t p = idx % npix;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n_red * 4 * npix) return;
+    const int r = (int)(idx / (4 * npix));
+    const int64_t rem = idx % (4 * npix);
+    const int c = (int)(rem / npix);
+    const int64_t p = rem % npix;
     const int a = (int)(p / nz), b = (int)(p % nz);
-    const int64_t m = 4 * a + c;
+    const int m = 4 * a + c, n = 2 * b;
+    const int mt = m >> 7, row = m & 127, nt = n >> 7, col = n & 127;
+    const RedDesc d = reds[r];
+    const int64_t base = (int64_t)d.slot_base + (int64_t)(mt * ntiles + nt) * d.splits;
     double re = 0.0, im = 0.0;
-    for (int s = 0; s < splits; ++s) {
-        const double2 v = *reinterpret_cast<const double2*>(P + ((int64_t)s * ldm + m) * ldn + 2 * b);
+    for (int s = 0; s < d.splits; ++s) {
+        const double2 v = *reinterpret_cast<const double2*>(P + (base + s) * (TC_BM * TC_BN) + row * TC_BN + col);
         re += v.x;
         im += v.y;
     }
-    const double sc = scale.v[c];
-    double2* o = reinterpret_cast<double2*>(F) + (int64_t)c * npix + p;
+    double2* o = reinterpret_cast<double2*>(F) + ((int64_t)d.out * 4 + c) * npix + p;
     double2 t = *o;
-    t.x += sc * re;
-    t.y += sc * im;
+    t.x += scale.v[c] * re;
+    t.y += scale.v[c] * im;
     *o = t;
 }
 
-// ------------------------------------------------------------------ host side
-struct TcState {
-    int ny = 0, nz = 0, mtiles = 0, ntiles = 0;
-    int64_t kt_cells = 0;     // cells per table chunk
-    int64_t nkb_max = 0;
-    float2* d_qy = nullptr;
-    float2* d_qz = nullptr;
-    double* d_P = nullptr;
-    int max_splits = 1;
-    double W[4] = {1, 1, 1, 1};   // power-of-two weight bounds per channel
-    bool attr_set = false;
-};
-
-static double pow2_ceil(double x)
+// ------------------------------------------------------------------ launchers
+cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, const int64_t* kb_cell0, const int32_t* kb_ncell,
+                             int64_t nkb, const float2* qy, int ny, const float2* qz, int nz, int mtiles, int ntiles,
+                             const float wscale[4], void* tab, cudaStream_t s)
 {
-    if (!(x > 0)) return 1.0;
-    int e;
-    frexp(x, &e);          // x = f 2^e, f in [0.5, 1)
-    double r = ldexp(1.0, e);
-    if (r / 2 >= x) r /= 2;
-    return r;
+    uint8_t* A_hi = (uint8_t*)tab;
+    uint8_t* A_lo = A_hi + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
+    uint8_t* B_hi = A_lo + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
+    uint8_t* B_lo = B_hi + (size_t)ntiles * nkb * TC_BLOCK_BYTES;
+    k_tables_a<<<dim3((unsigned)nkb, (unsigned)mtiles), 256, 0, s>>>(
+        cpos, cw, kb_cell0, kb_ncell, qy, ny, make_float4(wscale[0], wscale[1], wscale[2], wscale[3]), nkb, A_hi, A_lo);
+    k_tables_b<<<dim3((unsigned)nkb, (unsigned)ntiles), 512, 0, s>>>(cpos, kb_cell0, kb_ncell, qz, nz, nkb, B_hi,
+                                                                     B_lo);
+    return cudaGetLastError();
 }
 
-nms_status tc_setup(Plan& p)
+cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
+                           int grid, int kcb, double* P, int32_t* err, uint64_t limit_ns, cudaStream_t s)
 {
-    if (p.grid.kind != NMS_QGRID_CARTESIAN) {
-        set_error("tensor-core path needs a CARTESIAN grid");
-        return NMS_ERR_INVALID_ARG;
-    }
-    TcState* t = new TcState();
-    p.tc_state = t;
-    t->ny = p.grid.n0;
-    t->nz = p.grid.n1;
-    t->mtiles = (4 * t->ny + TC_BM - 1) / TC_BM;
-    t->ntiles = (2 * t->nz + TC_BN - 1) / TC_BN;
-    // q' = q / 2 pi as two-float, per axis
-    std::vector<float2> qy(t->ny), qz(t->nz);
-    const double two_pi = 2.0 * M_PI;
-    auto lin = [](int64_t a, int64_t n, double lo, double hi) {
-        return n == 1 ? lo : lo + ((hi - lo) * (double)a) / (double)(n - 1);
-    };
-    for (int a = 0; a < t->ny; ++a) {
-        double v = lin(a, t->ny, p.grid.lo0, p.grid.hi0) / two_pi;
-        float h = (float)v;
-        qy[a] = make_float2(h, (float)(v - (double)h));
-    }
-    for (int b = 0; b < t->nz; ++b) {
-        double v = lin(b, t->nz, p.grid.lo1, p.grid.hi1) / two_pi;
-        float h = (float)v;
-        qz[b] = make_float2(h, (float)(v - (double)h));
-    }
-    NMS_CUDA_TRY(cudaMalloc(&t->d_qy, t->ny * sizeof(float2)));
-    NMS_CUDA_TRY(cudaMalloc(&t->d_qz, t->nz * sizeof(float2)));
-    NMS_CUDA_TRY(cudaMemcpy(t->d_qy, qy.data(), t->ny * sizeof(float2), cudaMemcpyHostToDevice));
-    NMS_CUDA_TRY(cudaMemcpy(t->d_qz, qz.data(), t->nz * sizeof(float2), cudaMemcpyHostToDevice));
-    // weight bounds: rotation-invariant max_j V_j |N_j| and max_j V_j |M_j|
-    t->W[0] = pow2_ceil(p.h_wmax[0]);
-    t->W[1] = t->W[2] = t->W[3] = pow2_ceil(p.h_wmax[1]);
-    // table chunk: as many cells as the workspace allows (largest object if objects are summed separately)
-    const int64_t per_cell = (int64_t)(t->mtiles * TC_BM + t->ntiles * TC_BN) * 2 * 2 * 2;
-    int64_t need_cells = p.max_sum_cells;
-    size_t free_b = 0, total_b = 0;
-    cudaMemGetInfo(&free_b, &total_b);
-    int64_t budget = p.opt.workspace_bytes > 0 ? p.opt.workspace_bytes : (int64_t)std::min<size_t>(free_b / 3, (size_t)48 << 30);
-    int64_t cells = std::max<int64_t>(32, std::min<int64_t>(need_cells, budget / per_cell));
-    cells = (cells + 31) / 32 * 32;
-    t->kt_cells = cells;
-    t->nkb_max = cells / 32;
-    const size_t tab = (size_t)t->nkb_max * (t->mtiles + t->ntiles) * 2 * TC_BLOCK_BYTES;
-    NMS_CUDA_TRY(cudaMalloc(&p.d_tab, tab));
-    p.tab_bytes = tab;
-    // split partials: up to 512 MB
-    const int64_t tile_elems = (int64_t)t->mtiles * TC_BM * t->ntiles * TC_BN;
-    t->max_splits = (int)std::max<int64_t>(1, std::min<int64_t>(64, (512ll << 20) / (tile_elems * 8)));
-    NMS_CUDA_TRY(cudaMalloc(&t->d_P, (size_t)t->max_splits * tile_elems * 8));
+    static bool attr = false;
     const int smem = TC_STAGES * TC_STAGE_BYTES + 1024;
-    NMS_CUDA_TRY(cudaFuncSetAttribute(k_gemm_f16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    return NMS_OK;
-}
-
-void tc_release(Plan& p)
-{
-    TcState* t = (TcState*)p.tc_state;
-    if (!t) return;
-    if (t->d_qy) cudaFree(t->d_qy);
-    if (t->d_qz) cudaFree(t->d_qz);
-    if (t->d_P) cudaFree(t->d_P);
-    delete t;
-    p.tc_state = nullptr;
-}
-
-nms_status tc_run(Plan& p, const float4* cpos, int64_t c0, int64_t c1, double* Fout, cudaStream_t s)
-{
-    TcState* t = (TcState*)p.tc_state;
-    NMS_CUDA_TRY(cudaMemsetAsync(Fout, 0, 8 * p.npix * sizeof(double), s));
-    const int sms = device_sm_count();
-    const int tiles = t->mtiles * t->ntiles;
-    int kcb = p.opt.kc_cells > 0 ? std::max(1, p.opt.kc_cells / 32) : 2;
-    const float4 wscale = make_float4((float)(TC_SCALE / t->W[0]), (float)(TC_SCALE / t->W[1]),
-                                      (float)(TC_SCALE / t->W[2]), (float)(TC_SCALE / t->W[3]));
-    const double inv = 1.0 / ((double)TC_SCALE * (double)TC_SCALE);
-    Scale4 scale;
-    for (int c = 0; c < 4; ++c) scale.v[c] = t->W[c] * inv;
-    const uint64_t limit = p.opt.max_spin > 0 ? (uint64_t)p.opt.max_spin * 1000ull : 4000000000ull;
-    for (int64_t j0 = c0; j0 < c1; j0 += t->kt_cells) {
-        const int64_t nc = std::min<int64_t>(t->kt_cells, c1 - j0);
-        const int64_t nkb = (nc + 31) / 32;
-        uint8_t* base = (uint8_t*)p.d_tab;
-        const size_t asz = (size_t)t->mtiles * nkb * TC_BLOCK_BYTES;
-        const size_t bsz = (size_t)t->ntiles * nkb * TC_BLOCK_BYTES;
-        uint8_t* A_hi = base;
-        uint8_t* A_lo = A_hi + asz;
-        uint8_t* B_hi = A_lo + asz;
-        uint8_t* B_lo = B_hi + bsz;
-        p.timer.begin(ST_TABLES);
-        k_tables_a<<<dim3((unsigned)nkb, (unsigned)t->mtiles), 256, 0, s>>>(cpos, p.d_cw, j0, nc, t->d_qy, t->ny,
-                                                                              wscale, nkb, A_hi, A_lo);
-        k_tables_b<<<dim3((unsigned)nkb, (unsigned)t->ntiles), 512, 0, s>>>(cpos, j0, nc, t->d_qz, t->nz, nkb,
-                                                                              B_hi, B_lo);
-        NMS_CUDA_TRY(cudaGetLastError());
-        p.timer.end(ST_TABLES, 2);
-        int splits = p.opt.split_k;
-        if (splits <= 0) {
-            // fewest K splits whose CTA count fills whole waves of the SMs
-            auto eff = [&](int sp) {
-                const int64_t n = (int64_t)tiles * sp;
-                const int64_t w = (n + sms - 1) / sms;
-                return (double)n / (double)(w * sms);
-            };
-            const int lim = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)t->max_splits, nkb));
-            splits = 1;
-            double be = eff(1);
-            for (int sp = 2; sp <= lim && be < 0.97; ++sp) {
-                const double e = eff(sp);
-                if (e > be + 1e-9) { be = e; splits = sp; }
-            }
-        }
-        splits = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)splits, (int64_t)t->max_splits, nkb}));
-        GemmArgs ga;
-        ga.A_hi = A_hi; ga.A_lo = A_lo; ga.B_hi = B_hi; ga.B_lo = B_lo;
-        ga.nkb = nkb; ga.mtiles = t->mtiles; ga.ntiles = t->ntiles; ga.splits = splits; ga.kcb = kcb;
-        ga.P = t->d_P; ga.err = p.d_err; ga.limit_ns = limit;
-        p.timer.begin(ST_GEMM);
-        k_gemm_f16x3<<<dim3(t->ntiles, t->mtiles, splits), TC_THREADS, TC_STAGES * TC_STAGE_BYTES + 1024, s>>>(ga);
-        NMS_CUDA_TRY(cudaGetLastError());
-        p.timer.end(ST_GEMM, 1);
-        p.timer.begin(ST_REDUCE);
-        const int64_t n = 4 * p.npix;
-        k_gemm_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t->d_P, splits, (int64_t)t->mtiles * TC_BM,
-                                                                  (int64_t)t->ntiles * TC_BN, t->ny, t->nz, scale,
-                                                                  Fout);
-        NMS_CUDA_TRY(cudaGetLastError());
-        p.timer.end(ST_REDUCE, 1);
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_f16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
     }
-    return NMS_OK;
+    GemmArgs ga;
+    ga.A_hi = (const uint8_t*)tab;
+    ga.A_lo = ga.A_hi + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
+    ga.B_hi = ga.A_lo + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
+    ga.B_lo = ga.B_hi + (size_t)ntiles * nkb * TC_BLOCK_BYTES;
+    ga.nkb = nkb;
+    ga.items = (const GemmItem*)items;
+    ga.n_items = n_items;
+    ga.kcb = kcb;
+    ga.P = P;
+    ga.err = err;
+    ga.limit_ns = limit_ns;
+    k_gemm_f16x3<<<grid, TC_THREADS, smem, s>>>(ga);
+    return cudaGetLastError();
 }
+
+cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, int ny, int nz, int ntiles,
+                             const double scale[4], double* F, cudaStream_t s)
+{
+    Scale4 sc;
+    for (int c = 0; c < 4; ++c) sc.v[c] = scale[c];
+    const int64_t n = (int64_t)n_red * 4 * ny * nz;
+    k_gemm_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, (const RedDesc*)reds, n_red, ny, nz, ntiles, sc, F);
+    return cudaGetLastError();
+}
+
+size_t tc_item_bytes() { return sizeof(GemmItem); }
+size_t tc_red_bytes() { return sizeof(RedDesc); }
+size_t tc_block_bytes() { return TC_BLOCK_BYTES; }
+float tc_operand_scale() { return TC_SCALE; }
 
 }  // namespace nms

@@ -412,15 +412,21 @@ nms_status nms_amplitudes(nms_plan_t plan)
     const int64_t np = p.npix;
     NMS_CUDA_TRY(cudaMemsetAsync(p.d_Gtot, 0, 16 * np * 8, s));
     if (p.d_Gdil) NMS_CUDA_TRY(cudaMemsetAsync(p.d_Gdil, 0, 16 * np * 8, s));
+    if (p.path == NMS_PREC_TC_F16X3) {
+        nms_status st = tc_amplitudes(p, s);
+        if (st) return st;
+        p.rot_done = p.n_rot;
+        p.have_G = true;
+        return NMS_OK;
+    }
     const bool objects = p.n_objects > 1 && p.opt.want_dilute;
-    const bool tc = p.path == NMS_PREC_TC_F16X3;
     for (int32_t r = 0; r < p.n_rot; ++r) {
         const double* R = &p.h_rot[9 * r];
         p.timer.begin(ST_PREP);
         NMS_CUDA_TRY(launch_prep(p, R, s));
         p.timer.end(ST_PREP, 1);
         if (!objects) {
-            nms_status st = tc ? tc_run(p, p.d_cpos, 0, p.n_cells, p.d_F, s) : direct_sum(p, p.d_cpos, 0, p.n_cells, p.d_F);
+            nms_status st = direct_sum(p, p.d_cpos, 0, p.n_cells, p.d_F);
             if (st) return st;
             p.timer.begin(ST_GACC);
             NMS_CUDA_TRY(launch_gacc(p, p.d_F, p.d_Gtot, s));
@@ -432,7 +438,7 @@ nms_status nms_amplitudes(nms_plan_t plan)
             for (int64_t k = 0; k < p.n_objects; ++k) {
                 int64_t a = p.h_off[k], b = p.h_off[k + 1];
                 if (b == a) continue;
-                nms_status st = tc ? tc_run(p, p.d_cposl, a, b, p.d_F, s) : direct_sum(p, p.d_cposl, a, b, p.d_F);
+                nms_status st = direct_sum(p, p.d_cposl, a, b, p.d_F);
                 if (st) return st;
                 double cy = 0.0, cz = 0.0;
                 if (!p.h_cen.empty()) {

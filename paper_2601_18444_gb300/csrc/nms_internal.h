@@ -41,6 +41,11 @@ struct StageTimer {
     void release();
 };
 
+// A row-major 3x3 rotation passed to kernels by value.
+struct RotMat {
+    double m[9];
+};
+
 // ---------------------------------------------------------------- plan
 struct Plan {
     cudaStream_t stream = nullptr;
@@ -121,9 +126,10 @@ cudaError_t launch_correlation(int nq, const double* q, const double* Iq, int nr
                                double pref, double* c, double* pr, double* scratch_q, double* scratch_f,
                                int* scratch_n, cudaStream_t s);
 
-// Tensor-core path (split-FP16 tcgen05 GEMM).
+// Tensor-core path (split-FP16 tcgen05 GEMM): schedule at plan creation,
+// all rotations/objects of one nms_amplitudes call, release.
 nms_status tc_setup(Plan& p);
-nms_status tc_run(Plan& p, const float4* cpos, int64_t c0, int64_t c1, double* Fout, cudaStream_t s);
+nms_status tc_amplitudes(Plan& p, cudaStream_t s);
 void tc_release(Plan& p);
 
 int device_sm_count();

@@ -1,0 +1,425 @@
+// Host side of the tensor-core path: the work schedule and its launches.
+//
+// Every amplitude the plan needs is a "summand": the cells of one object (or
+// all cells) under one rotation.  Summands are grouped into output batches
+// (amplitude buffers F_b in HBM) and, within a batch, packed into table
+// chunks that fit the table workspace (a large object is cut into several
+// pieces that add into the same output).  For each chunk the phase tables
+// are generated and one persistent GEMM launch walks a work list of
+// (tile, k-range) items, longest first; a reduction adds the item tiles into
+// F_b.  Batches then feed the Hermitian-product and shift kernels.
+//
+// The whole schedule is built and uploaded when the plan is created, so
+// nms_amplitudes only launches kernels: no host synchronisation and no host
+// to device copy happen inside it.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "nms_internal.h"
+
+namespace nms {
+
+// launchers in k_gemm.cu / k_batch.cu
+cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, const int64_t* kb_cell0, const int32_t* kb_ncell,
+                             int64_t nkb, const float2* qy, int ny, const float2* qz, int nz, int mtiles, int ntiles,
+                             const float wscale[4], void* tab, cudaStream_t s);
+cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
+                           int grid, int kcb, double* P, int32_t* err, uint64_t limit_ns, cudaStream_t s);
+cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, int ny, int nz, int ntiles,
+                             const double scale[4], double* F, cudaStream_t s);
+size_t tc_item_bytes();
+size_t tc_red_bytes();
+size_t tc_block_bytes();
+float tc_operand_scale();
+cudaError_t launch_prep_rot(const Plan& p, const RotMat& R, bool global, float4* cpos, float4* cw, cudaStream_t s);
+cudaError_t launch_centres(int n_out, const int32_t* out_obj, const int32_t* out_rot, int rot0, const double* rot,
+                           const double* cen, float4* cyz, cudaStream_t s);
+cudaError_t launch_gacc_batch(const double* F, int n_out, int64_t npix, double* G, cudaStream_t s);
+cudaError_t launch_shift_batch(const double* F, int n_out, const float4* cyz, const int32_t* out_rot,
+                               const float4* qturn, int64_t npix, double* Ftot, cudaStream_t s);
+
+namespace {
+
+struct HostItem {
+    int32_t mt, nt, kb0, kb1, slot, pad;
+};
+struct HostRed {
+    int32_t slot_base, splits, out, pad;
+};
+
+struct Chunk {
+    int64_t kb_off = 0, nkb = 0;    // into the k-block arrays
+    int64_t item_off = 0;
+    int n_items = 0, grid = 0;
+    int64_t red_off = 0;
+    int n_red = 0;
+};
+
+struct OutBatch {
+    int out0 = 0, n_out = 0;        // outputs [out0, out0 + n_out) of the schedule
+    std::vector<Chunk> chunks;
+};
+
+struct Schedule {
+    int n_rot_local = 0;
+    int n_out = 0;
+    std::vector<OutBatch> batches;
+    // device arrays
+    int64_t* d_kb_cell0 = nullptr;
+    int32_t* d_kb_ncell = nullptr;
+    void* d_items = nullptr;
+    void* d_reds = nullptr;
+    int32_t* d_out_obj = nullptr;
+    int32_t* d_out_rot = nullptr;
+    int64_t max_items = 0;
+    int max_batch_out = 0;
+};
+
+}  // namespace
+
+struct TcState {
+    int ny = 0, nz = 0, mtiles = 0, ntiles = 0;
+    float2* d_qy = nullptr;
+    float2* d_qz = nullptr;
+    double W[4] = {1, 1, 1, 1};
+    int kcb = 2;
+    bool objects = false;        // per-object amplitudes (dilute split) with shifts
+    int R_b = 1;                 // rotations prepared per rotation batch
+    int64_t tab_kb = 0;          // table capacity in k-blocks
+    float4* d_cpos_b = nullptr;  // [R_b][n]
+    float4* d_cw_b = nullptr;
+    double* d_Fb = nullptr;      // [out_cap][4][npix][2]
+    double* d_Ftot_b = nullptr;  // [R_b][4][npix][2] (objects)
+    float4* d_cyz = nullptr;     // [out_cap]
+    double* d_rot = nullptr;     // [n_rot][9]
+    double* d_cen = nullptr;     // [K][3]
+    double* d_P = nullptr;       // item tiles
+    Schedule full, last;
+};
+
+static double pow2_ceil(double x)
+{
+    if (!(x > 0)) return 1.0;
+    int e;
+    frexp(x, &e);
+    double r = ldexp(1.0, e);
+    if (r / 2 >= x) r /= 2;
+    return r;
+}
+
+template <class T>
+static nms_status upload(T** d, const std::vector<T>& h)
+{
+    *d = nullptr;
+    if (h.empty()) return NMS_OK;
+    NMS_CUDA_TRY(cudaMalloc((void**)d, h.size() * sizeof(T)));
+    NMS_CUDA_TRY(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return NMS_OK;
+}
+
+static void free_schedule(Schedule& s)
+{
+    void* b[] = {s.d_kb_cell0, s.d_kb_ncell, s.d_items, s.d_reds, s.d_out_obj, s.d_out_rot};
+    for (void* x : b)
+        if (x) cudaFree(x);
+    s = Schedule();
+}
+
+// Build the schedule of one rotation batch of n_rl rotations.
+static nms_status build_schedule(const Plan& p, const TcState& t, int n_rl, int out_cap, Schedule& S)
+{
+    struct Summand {
+        int rl, obj;
+        int64_t c0, c1;
+    };
+    std::vector<Summand> sums;
+    for (int rl = 0; rl < n_rl; ++rl) {
+        if (t.objects) {
+            for (int64_t k = 0; k < p.n_objects; ++k)
+                if (p.h_off[k + 1] > p.h_off[k]) sums.push_back({rl, (int)k, p.h_off[k], p.h_off[k + 1]});
+        } else {
+            sums.push_back({rl, 0, 0, p.n_cells});
+        }
+    }
+    S.n_rot_local = n_rl;
+    S.n_out = (int)sums.size();
+    const int sms = device_sm_count();
+    const int tiles = t.mtiles * t.ntiles;
+    std::vector<int64_t> kb_cell0;
+    std::vector<int32_t> kb_ncell;
+    std::vector<HostItem> items;
+    std::vector<HostRed> reds;
+    std::vector<int32_t> out_obj(sums.size()), out_rot(sums.size());
+    for (size_t o = 0; o < sums.size(); ++o) {
+        out_obj[o] = sums[o].obj;
+        out_rot[o] = sums[o].rl;
+    }
+    for (int o0 = 0; o0 < S.n_out; o0 += out_cap) {
+        OutBatch ob;
+        ob.out0 = o0;
+        ob.n_out = std::min(out_cap, S.n_out - o0);
+        S.max_batch_out = std::max(S.max_batch_out, ob.n_out);
+        // pieces: (out_local, first cell in the stacked arrays, cells)
+        struct Piece {
+            int out;
+            int64_t g0, n;
+        };
+        std::vector<std::vector<Piece>> chunk_pieces(1);
+        int64_t cur_kb = 0;
+        for (int o = o0; o < o0 + ob.n_out; ++o) {
+            const Summand& sm = sums[o];
+            int64_t c = sm.c0;
+            while (c < sm.c1) {
+                int64_t room = (t.tab_kb - cur_kb) * 32;
+                if (room <= 0) {
+                    chunk_pieces.emplace_back();
+                    cur_kb = 0;
+                    room = t.tab_kb * 32;
+                }
+                const int64_t take = std::min(room, sm.c1 - c);
+                chunk_pieces.back().push_back({o - o0, (int64_t)sm.rl * p.n_cells + c, take});
+                cur_kb += (take + 31) / 32;
+                c += take;
+            }
+        }
+        for (auto& pieces : chunk_pieces) {
+            if (pieces.empty()) continue;
+            Chunk ch;
+            ch.kb_off = (int64_t)kb_cell0.size();
+            int64_t nkb_chunk = 0;
+            for (const Piece& pc : pieces) nkb_chunk += (pc.n + 31) / 32;
+            ch.nkb = nkb_chunk;
+            // work items: about 8 per SM, never shorter than 2 TMEM chunks
+            const int64_t kb_per_item =
+                std::max<int64_t>(2 * t.kcb, (nkb_chunk * tiles + 8LL * sms - 1) / (8LL * sms));
+            std::vector<HostItem> its;
+            ch.red_off = (int64_t)reds.size();
+            int slot = 0;
+            int64_t kb = 0;
+            for (const Piece& pc : pieces) {
+                const int64_t nkb_p = (pc.n + 31) / 32;
+                for (int64_t i = 0; i < nkb_p; ++i) {
+                    kb_cell0.push_back(pc.g0 + 32 * i);
+                    kb_ncell.push_back((int32_t)std::min<int64_t>(32, pc.n - 32 * i));
+                }
+                const int splits = (int)((nkb_p + kb_per_item - 1) / kb_per_item);
+                reds.push_back({slot, splits, pc.out, 0});
+                for (int mt = 0; mt < t.mtiles; ++mt)
+                    for (int nt = 0; nt < t.ntiles; ++nt)
+                        for (int sp = 0; sp < splits; ++sp) {
+                            const int64_t a = kb + (nkb_p * sp) / splits;
+                            const int64_t b = kb + (nkb_p * (sp + 1)) / splits;
+                            its.push_back({mt, nt, (int32_t)a, (int32_t)b, slot + (mt * t.ntiles + nt) * splits + sp,
+                                           0});
+                        }
+                slot += tiles * splits;
+                kb += nkb_p;
+            }
+            ch.n_red = (int)(reds.size() - ch.red_off);
+            // longest items first, dealt round-robin to the persistent CTAs
+            std::stable_sort(its.begin(), its.end(),
+                             [](const HostItem& x, const HostItem& y) { return (x.kb1 - x.kb0) > (y.kb1 - y.kb0); });
+            ch.item_off = (int64_t)items.size();
+            ch.n_items = (int)its.size();
+            ch.grid = std::min(ch.n_items, sms);
+            items.insert(items.end(), its.begin(), its.end());
+            S.max_items = std::max<int64_t>(S.max_items, slot);
+            ob.chunks.push_back(ch);
+        }
+        S.batches.push_back(ob);
+    }
+    nms_status st;
+    if ((st = upload(&S.d_kb_cell0, kb_cell0)) || (st = upload(&S.d_kb_ncell, kb_ncell)) ||
+        (st = upload(&S.d_out_obj, out_obj)) || (st = upload(&S.d_out_rot, out_rot)))
+        return st;
+    if (!items.empty()) {
+        NMS_CUDA_TRY(cudaMalloc(&S.d_items, items.size() * sizeof(HostItem)));
+        NMS_CUDA_TRY(cudaMemcpy(S.d_items, items.data(), items.size() * sizeof(HostItem), cudaMemcpyHostToDevice));
+    }
+    if (!reds.empty()) {
+        NMS_CUDA_TRY(cudaMalloc(&S.d_reds, reds.size() * sizeof(HostRed)));
+        NMS_CUDA_TRY(cudaMemcpy(S.d_reds, reds.data(), reds.size() * sizeof(HostRed), cudaMemcpyHostToDevice));
+    }
+    return NMS_OK;
+}
+
+nms_status tc_setup(Plan& p)
+{
+    if (p.grid.kind != NMS_QGRID_CARTESIAN) {
+        set_error("tensor-core path needs a CARTESIAN grid");
+        return NMS_ERR_INVALID_ARG;
+    }
+    if (tc_item_bytes() != sizeof(HostItem) || tc_red_bytes() != sizeof(HostRed)) {
+        set_error("internal: work-list record size mismatch");
+        return NMS_ERR_UNSUPPORTED;
+    }
+    TcState* t = new TcState();
+    p.tc_state = t;
+    t->ny = p.grid.n0;
+    t->nz = p.grid.n1;
+    t->mtiles = (4 * t->ny + 127) / 128;
+    t->ntiles = (2 * t->nz + 127) / 128;
+    t->kcb = p.opt.kc_cells > 0 ? std::max(1, p.opt.kc_cells / 32) : 2;
+    t->objects = p.n_objects > 1 && p.opt.want_dilute;
+    const int64_t n = p.n_cells;
+    const int64_t np = p.npix;
+
+    std::vector<float2> qy(t->ny), qz(t->nz);
+    const double two_pi = 2.0 * M_PI;
+    auto lin = [](int64_t a, int64_t nn, double lo, double hi) {
+        return nn == 1 ? lo : lo + ((hi - lo) * (double)a) / (double)(nn - 1);
+    };
+    for (int a = 0; a < t->ny; ++a) {
+        double v = lin(a, t->ny, p.grid.lo0, p.grid.hi0) / two_pi;
+        float h = (float)v;
+        qy[a] = make_float2(h, (float)(v - (double)h));
+    }
+    for (int b = 0; b < t->nz; ++b) {
+        double v = lin(b, t->nz, p.grid.lo1, p.grid.hi1) / two_pi;
+        float h = (float)v;
+        qz[b] = make_float2(h, (float)(v - (double)h));
+    }
+    nms_status st;
+    if ((st = upload(&t->d_qy, qy)) || (st = upload(&t->d_qz, qz))) return st;
+    t->W[0] = pow2_ceil(p.h_wmax[0]);
+    t->W[1] = t->W[2] = t->W[3] = pow2_ceil(p.h_wmax[1]);
+    if ((st = upload(&t->d_rot, p.h_rot))) return st;
+    if (t->objects && !p.h_cen.empty()) {
+        if ((st = upload(&t->d_cen, p.h_cen))) return st;
+    } else if (t->objects) {
+        std::vector<double> z((size_t)3 * p.n_objects, 0.0);
+        if ((st = upload(&t->d_cen, z))) return st;
+    }
+
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    // rotations prepared per batch: stacked positions and weights up to 2 GB
+    const int64_t per_rot = n * 32;
+    t->R_b = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)p.n_rot, 64, (2ll << 30) / std::max<int64_t>(1, per_rot)}));
+    NMS_CUDA_TRY(cudaMalloc(&t->d_cpos_b, (size_t)t->R_b * n * sizeof(float4)));
+    NMS_CUDA_TRY(cudaMalloc(&t->d_cw_b, (size_t)t->R_b * n * sizeof(float4)));
+    // output amplitude batch: up to 1 GB
+    const int64_t outs_per_rb = t->objects ? (int64_t)t->R_b * p.n_objects : t->R_b;
+    const int out_cap = (int)std::max<int64_t>(1, std::min<int64_t>(outs_per_rb, (1ll << 30) / (64 * np)));
+    NMS_CUDA_TRY(cudaMalloc(&t->d_Fb, (size_t)out_cap * 8 * np * sizeof(double)));
+    NMS_CUDA_TRY(cudaMalloc(&t->d_cyz, (size_t)out_cap * sizeof(float4)));
+    if (t->objects) NMS_CUDA_TRY(cudaMalloc(&t->d_Ftot_b, (size_t)t->R_b * 8 * np * sizeof(double)));
+    // phase tables: as many k-blocks as the workspace allows
+    const int64_t per_kb = (int64_t)(t->mtiles + t->ntiles) * 2 * (int64_t)tc_block_bytes();
+    const int64_t budget = p.opt.workspace_bytes > 0 ? p.opt.workspace_bytes
+                                                     : (int64_t)std::min<size_t>(free_b / 3, (size_t)48 << 30);
+    int64_t total_kb = 0;
+    if (t->objects) {
+        for (int64_t k = 0; k < p.n_objects; ++k) total_kb += (p.h_off[k + 1] - p.h_off[k] + 31) / 32;
+    } else {
+        total_kb = (n + 31) / 32;
+    }
+    total_kb *= t->R_b;
+    t->tab_kb = std::max<int64_t>(1, std::min<int64_t>(total_kb, budget / per_kb));
+    p.tab_bytes = (size_t)t->tab_kb * per_kb;
+    NMS_CUDA_TRY(cudaMalloc(&p.d_tab, p.tab_bytes));
+    // schedules: a full rotation batch and the remainder
+    if ((st = build_schedule(p, *t, t->R_b, out_cap, t->full))) return st;
+    const int rem = p.n_rot % t->R_b;
+    if (rem) {
+        if ((st = build_schedule(p, *t, rem, out_cap, t->last))) return st;
+    }
+    const int64_t slots = std::max(t->full.max_items, t->last.max_items);
+    NMS_CUDA_TRY(cudaMalloc(&t->d_P, (size_t)std::max<int64_t>(1, slots) * 128 * 128 * sizeof(double)));
+    return NMS_OK;
+}
+
+void tc_release(Plan& p)
+{
+    TcState* t = (TcState*)p.tc_state;
+    if (!t) return;
+    void* b[] = {t->d_qy, t->d_qz, t->d_cpos_b, t->d_cw_b, t->d_Fb, t->d_Ftot_b, t->d_cyz, t->d_rot, t->d_cen, t->d_P};
+    for (void* x : b)
+        if (x) cudaFree(x);
+    free_schedule(t->full);
+    free_schedule(t->last);
+    delete t;
+    p.tc_state = nullptr;
+}
+
+nms_status tc_amplitudes(Plan& p, cudaStream_t s)
+{
+    TcState& t = *(TcState*)p.tc_state;
+    const int64_t n = p.n_cells;
+    const int64_t np = p.npix;
+    const float sc = tc_operand_scale();
+    const float wscale[4] = {(float)(sc / t.W[0]), (float)(sc / t.W[1]), (float)(sc / t.W[2]), (float)(sc / t.W[3])};
+    double scale[4];
+    for (int c = 0; c < 4; ++c) scale[c] = t.W[c] / ((double)sc * (double)sc);
+    const uint64_t limit = p.opt.max_spin > 0 ? (uint64_t)p.opt.max_spin * 1000ull : 4000000000ull;
+    double* last_F = nullptr;
+    for (int rb0 = 0; rb0 < p.n_rot; rb0 += t.R_b) {
+        const int nrl = std::min(t.R_b, p.n_rot - rb0);
+        const Schedule& S = nrl == t.R_b ? t.full : t.last;
+        p.timer.begin(ST_PREP);
+        for (int rl = 0; rl < nrl; ++rl) {
+            RotMat R;
+            memcpy(R.m, &p.h_rot[9 * (size_t)(rb0 + rl)], sizeof(R.m));
+            NMS_CUDA_TRY(launch_prep_rot(p, R, !t.objects, t.d_cpos_b + (size_t)rl * n, t.d_cw_b + (size_t)rl * n, s));
+        }
+        p.timer.end(ST_PREP, nrl);
+        if (t.objects) NMS_CUDA_TRY(cudaMemsetAsync(t.d_Ftot_b, 0, (size_t)nrl * 8 * np * sizeof(double), s));
+        for (const OutBatch& ob : S.batches) {
+            NMS_CUDA_TRY(cudaMemsetAsync(t.d_Fb, 0, (size_t)ob.n_out * 8 * np * sizeof(double), s));
+            for (const Chunk& ch : ob.chunks) {
+                p.timer.begin(ST_TABLES);
+                NMS_CUDA_TRY(tc_launch_tables(t.d_cpos_b, t.d_cw_b, S.d_kb_cell0 + ch.kb_off, S.d_kb_ncell + ch.kb_off,
+                                              ch.nkb, t.d_qy, t.ny, t.d_qz, t.nz, t.mtiles, t.ntiles, wscale, p.d_tab,
+                                              s));
+                p.timer.end(ST_TABLES, 2);
+                p.timer.begin(ST_GEMM);
+                NMS_CUDA_TRY(tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles,
+                                            (const char*)S.d_items + ch.item_off * tc_item_bytes(), ch.n_items, ch.grid,
+                                            t.kcb, t.d_P, p.d_err, limit, s));
+                p.timer.end(ST_GEMM, 1);
+                p.timer.begin(ST_REDUCE);
+                NMS_CUDA_TRY(tc_launch_reduce(t.d_P, (const char*)S.d_reds + ch.red_off * tc_red_bytes(), ch.n_red, t.ny,
+                                              t.nz, t.ntiles, scale, t.d_Fb, s));
+                p.timer.end(ST_REDUCE, 1);
+            }
+            p.timer.begin(ST_GACC);
+            int nl = 0;
+            if (t.objects) {
+                NMS_CUDA_TRY(launch_centres(ob.n_out, S.d_out_obj + ob.out0, S.d_out_rot + ob.out0, rb0, t.d_rot, t.d_cen,
+                                            t.d_cyz, s));
+                NMS_CUDA_TRY(launch_gacc_batch(t.d_Fb, ob.n_out, np, p.d_Gdil, s));
+                NMS_CUDA_TRY(launch_shift_batch(t.d_Fb, ob.n_out, t.d_cyz, S.d_out_rot + ob.out0, p.d_qturn, np,
+                                                t.d_Ftot_b, s));
+                nl = 3;
+            } else {
+                NMS_CUDA_TRY(launch_gacc_batch(t.d_Fb, ob.n_out, np, p.d_Gtot, s));
+                nl = 1;
+                if (p.d_Gdil) {
+                    NMS_CUDA_TRY(launch_gacc_batch(t.d_Fb, ob.n_out, np, p.d_Gdil, s));
+                    nl = 2;
+                }
+                last_F = t.d_Fb + (size_t)(ob.n_out - 1) * 8 * np;
+                if (rb0 + nrl == p.n_rot && &ob == &S.batches.back())
+                    NMS_CUDA_TRY(cudaMemcpyAsync(p.d_F, last_F, 8 * np * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            }
+            p.timer.end(ST_GACC, nl);
+        }
+        if (t.objects) {
+            p.timer.begin(ST_GACC);
+            NMS_CUDA_TRY(launch_gacc_batch(t.d_Ftot_b, nrl, np, p.d_Gtot, s));
+            p.timer.end(ST_GACC, 1);
+            if (rb0 + nrl == p.n_rot)
+                NMS_CUDA_TRY(cudaMemcpyAsync(p.d_Ftot, t.d_Ftot_b + (size_t)(nrl - 1) * 8 * np, 8 * np * sizeof(double),
+                                             cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    (void)last_F;
+    return NMS_OK;
+}
+
+}  // namespace nms

@@ -133,3 +133,62 @@ def test_tc_full_box_sampled_pixels():
     F_ref = S.dsft(f.pos[:, 1], f.pos[:, 2], w, g[0][idx], g[1][idx])
     err = amp_error(F[:, idx], F_ref, np.abs(w).sum(1))
     assert np.all(err <= AMP_TOL), err
+
+
+def test_tc_ensemble_many_chunks_dilute_interference():
+    # ~1500 small spheres, table workspace forced small so objects are cut
+    # into pieces across many table chunks; dilute, total and interference
+    f = I.sphere_ensemble(n_spheres=1500, median=2.5, sigma=0.35, clip=(1.5, 4.0), a=1.0, cube=300.0, seed=7)
+    kw = dict(kind="cartesian", n0=40, n1=56, lo0=-1.5, hi0=1.5, lo1=-1.5, hi1=1.5)
+    plan = run(f, kw, want_dilute=1, workspace_bytes=8 << 20)
+    g = og(kw)
+    ids = ("N", "M", "SF", "CHI", "NM", "UNPOL")
+    parts = S.response_parts(f, np.eye(3), g, ids=ids)
+    tol = 2 * resp_tol(f)
+    # the dilute part scales with the number of objects, not with (sum |w|)^2
+    wk = [np.abs(S.cell_weights(f.vol[a:b], f.nuc[a:b], f.mag[a:b], np.eye(3))).sum(1)
+          for a, b in zip(f.offsets[:-1], f.offsets[1:])]
+    tol_dil = 4e-6 * sum((w[0] + w[1] + w[2] + w[3]) ** 2 for w in wk)
+    for k in ids:
+        assert np.max(np.abs(nms.nms_response(plan, k, nms.PART_TOTAL) - parts[k][0])) <= tol, k
+        assert np.max(np.abs(nms.nms_response(plan, k, nms.PART_DILUTE) - parts[k][1])) <= tol_dil, k
+        assert np.max(np.abs(nms.nms_response(plan, k, nms.PART_INTERFERENCE) - parts[k][2])) <= tol + tol_dil, k
+
+
+def test_tc_rotation_batches_full_and_remainder():
+    # 70 rotations: one batch of 64 prepared rotations and a remainder of 6
+    f = I.ellipsoid_uniform((8.0, 5.0, 5.0), a=1.0, seed=2)
+    Rs = I.random_rotations(70, seed=13)
+    kw = dict(kind="cartesian", n0=24, n1=20, lo0=-1.0, hi0=1.0, lo1=-1.0, hi1=1.0)
+    plan = run(f, kw, rot=Rs)
+    g = og(kw)
+    acc = None
+    for R in Rs:
+        r = S.responses(S.amplitudes(f, R, g[0], g[1]), g[2], g[3])
+        acc = r if acc is None else {k: acc[k] + r[k] for k in acc}
+    for name in ("UNPOL", "SF", "M", "P", "CHI"):
+        assert np.max(np.abs(nms.nms_response(plan, name) - acc[name] / len(Rs))) <= resp_tol(f, rotations=Rs), name
+    F_ref = S.amplitudes(f, Rs[-1], g[0], g[1])
+    assert np.all(amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f, Rs[-1])) <= AMP_TOL)
+
+
+def test_tc_amplitudes_capture_in_cuda_graph():
+    torch = pytest.importorskip("torch")
+    f = I.small_random_field(3000, seed=31, extent=8.0, n_objects=5)
+    kw = dict(kind="cartesian", n0=48, n1=40, lo0=-1.0, hi0=1.0, lo1=-1.0, hi1=1.0)
+    side = torch.cuda.Stream()
+    opt = nms.nms_options_default(precision=TC, want_dilute=1)
+    plan = nms.plan_from_field(f, nms.make_grid(**kw), opt, rot=I.random_rotations(3, seed=2),
+                               stream=side.cuda_stream)
+    nms.nms_amplitudes(plan)                     # first call outside capture
+    ref = nms.nms_response(plan, "UNPOL", nms.PART_INTERFERENCE).copy()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        graph.capture_begin()
+        nms.nms_amplitudes(plan)
+        graph.capture_end()
+    for _ in range(2):
+        graph.replay()
+        side.synchronize()
+        got = nms.nms_response(plan, "UNPOL", nms.PART_INTERFERENCE)
+        assert np.array_equal(got, ref)

@@ -210,12 +210,78 @@ nms_status nms_correlation(int32_t nq, const double* q, const double* Iq, int32_
                            const double* r, double prefactor, double* c_r, double* p_r,
                            int32_t is_device, void* cuda_stream);
 
+/* Per-object, orientation-averaged azimuthal averages (paper, Eq. iqazi on
+ * ring bins, averaged over the plan's rotations; Sec. "Summation approach"
+ * form factors of the objects without interparticle interference).  Call
+ * after nms_plan_create and before nms_amplitudes: every following
+ * nms_amplitudes then also bins, for each object k (or for the whole sample
+ * when the plan has one object or want_dilute = 0), the response
+ * response_id (N, M, P, SF or UNPOL) of its own amplitude F_k over the ring
+ * bins edges[b] <= |q| < edges[b+1] (bin_edges host [nbins+1], increasing,
+ * nbins <= 8192).  This is how surrogate training data are generated in one
+ * batched pass.  Tensor-core path only (UNSUPPORTED otherwise). */
+nms_status nms_plan_object_iq(nms_plan_t plan, int32_t response_id, int32_t nbins, const double* bin_edges);
+
+/* Results of nms_plan_object_iq after nms_amplitudes: Iq[k][b] = mean over
+ * the bin's pixels and over the rotations (NaN for empty bins), counts[b] =
+ * pixels in bin b, qmean[b] = their mean |q| (counts, qmean may be NULL).
+ * Host or device per out_is_device.  Synchronous. */
+nms_status nms_get_object_iq(nms_plan_t plan, double* Iq, int64_t* counts, double* qmean, int32_t out_is_device);
+
 /* Per-stage device times in milliseconds, summed over all nms_amplitudes
  * calls since the plan was created or the last reset (needs opt.timing=1):
  * stage 0 = rotation/weights, 1 = phase tables, 2 = tensor-core GEMM,
  * 3 = direct sum, 4 = promotion/reduction of partials, 5 = G accumulation.
  * launches[s] counts the kernel launches of stage s.  Synchronises. */
 nms_status nms_plan_stage_ms(nms_plan_t plan, double ms[8], int64_t launches[8], int32_t reset);
+
+/* ---------------------------------------------------------------------
+ * Learned surrogate.  The paper has no learned component: this MLP maps the
+ * parameters of a magnetization family to its orientation-averaged
+ * log10 I(q), trained on curves the batched transform computes
+ * (nms_plan_object_iq); the exact transform stays the reference for its
+ * error.  Architecture n_in -> H -> H -> n_out with SiLU, FP32 master
+ * weights, BF16 weights/activations in the GEMMs with FP32 accumulation,
+ * mean-squared error on standardised targets, Adam.  Parameters are one
+ * flat FP32 vector: W1[H][n_in] b1[H] W2[H][H] b2[H] W3[n_out][H] b3[n_out].
+ * Inputs are scaled to [-1, 1] with the per-input bounds given at create.
+ * --------------------------------------------------------------------- */
+typedef struct nms_surrogate_s* nms_surrogate_t;
+
+/* x_lo, x_hi: host [n_in] input bounds; weights He-uniform from seed. */
+nms_status nms_surrogate_create(nms_surrogate_t* out, int32_t n_in, int32_t n_hidden, int32_t n_out,
+                                const float* x_lo, const float* x_hi, uint64_t seed, void* cuda_stream);
+
+/* Target standardisation (host [n_out] each, y_std > 0).  When not set, the
+ * first nms_surrogate_train computes them from its targets. */
+nms_status nms_surrogate_set_target_stats(nms_surrogate_t s, const float* y_mean, const float* y_std);
+
+/* Mini-batch Adam over device data X [n][n_in], Y [n][n_out] (FP32,
+ * unnormalised targets), epochs passes with a seeded shuffle per epoch;
+ * final_loss (host, may be NULL) = mean 0.5 (y_n - t_n)^2 of the last epoch
+ * on standardised targets. */
+nms_status nms_surrogate_train(nms_surrogate_t s, const float* X, const float* Y, int64_t n, int32_t batch,
+                               int32_t epochs, float lr, uint64_t shuffle_seed, float* final_loss);
+
+/* One forward + backward over device rows X [n][n_in], Y [n][n_out] without
+ * an update: grad (host [n_params]) = d loss / d params, loss (host) = mean
+ * 0.5 (y_n - t_n)^2.  For gradient checks. */
+nms_status nms_surrogate_gradients(nms_surrogate_t s, const float* X, const float* Y, int32_t n, float* grad,
+                                   double* loss);
+
+/* Y [n][n_out] (device, FP32, de-standardised log10 I) for device X [n][n_in].
+ * Asynchronous on the surrogate's stream. */
+nms_status nms_surrogate_infer(nms_surrogate_t s, const float* X, int64_t n, float* Y);
+
+/* Master parameters to/from host (count = number of parameters). */
+nms_status nms_surrogate_get_params(nms_surrogate_t s, float* host, int64_t* count);
+nms_status nms_surrogate_set_params(nms_surrogate_t s, const float* host, int64_t count);
+
+/* Checkpoint (weights, Adam state, step, standardisation, bounds) to a file,
+ * and back into a surrogate of the same shape. */
+nms_status nms_surrogate_save(nms_surrogate_t s, const char* path);
+nms_status nms_surrogate_load(nms_surrogate_t s, const char* path);
+nms_status nms_surrogate_destroy(nms_surrogate_t s);
 
 /* Direct Fourier sums with no device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot let a library

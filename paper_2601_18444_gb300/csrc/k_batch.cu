@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "nms_internal.h"
 
 namespace nms {
@@ -189,6 +191,76 @@ cudaError_t launch_shift_batch(const double* F, int n_out, const float4* cyz, co
     k_shift_batch<<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(reinterpret_cast<const double2*>(F), n_out, cyz,
                                                                  out_rot, qturn, npix,
                                                                  reinterpret_cast<double2*>(Ftot));
+    return cudaGetLastError();
+}
+
+}  // namespace nms
+
+namespace nms {
+
+// Per-object azimuthal binning of one response evaluated from a batch of
+// amplitudes: Iobj[obj[o]][bin(p)] += resp(F_o, p) over the pixels of each
+// bin (Eq. iqazi on the ring bins of the detector).  The response is formed
+// in FP32 from the FP64 amplitudes:
+//   N  = s |F_N|^2,  M = s b^2 (|F_M|^2 - |qhat.F_M|^2)   (|Q|^2, Eq. HJdef)
+//   P  = s b^2 |u.F_M|^2, u = P - qhat (qhat.P)            (Eq. PSANSdef)
+//   SF = M - P,  UNPOL = N + M.
+__global__ void k_obj_bin(const double2* __restrict__ F, int n_out, const int32_t* __restrict__ out_obj,
+                          const double* __restrict__ hy, const double* __restrict__ hz,
+                          const int32_t* __restrict__ bin_of, int64_t npix, int nbins, int id, float s, float b,
+                          float Px, float Py, float Pz, double* __restrict__ Iobj)
+{
+    extern __shared__ float s_bins[];
+    const int o = blockIdx.y;
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x) s_bins[k] = 0.f;
+    __syncthreads();
+    const double2* Fo = F + (int64_t)o * 4 * npix;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+        const int bin = bin_of[p];
+        if (bin < 0) continue;
+        float2 f[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const double2 v = Fo[(int64_t)c * npix + p];
+            f[c] = make_float2((float)v.x, (float)v.y);
+        }
+        const float y = (float)hy[p], z = (float)hz[p];
+        const float nn = f[0].x * f[0].x + f[0].y * f[0].y;
+        const float mm = f[1].x * f[1].x + f[1].y * f[1].y + f[2].x * f[2].x + f[2].y * f[2].y + f[3].x * f[3].x +
+                         f[3].y * f[3].y;
+        const float pr = y * f[2].x + z * f[3].x, pi = y * f[2].y + z * f[3].y;
+        const float vM = s * b * b * (mm - (pr * pr + pi * pi));
+        float v;
+        if (id == NMS_RESP_N) {
+            v = s * nn;
+        } else if (id == NMS_RESP_M) {
+            v = vM;
+        } else if (id == NMS_RESP_UNPOL) {
+            v = s * nn + vM;
+        } else {
+            const float qp = y * Py + z * Pz;
+            const float ux = Px, uy = Py - y * qp, uz = Pz - z * qp;
+            const float ur = ux * f[1].x + uy * f[2].x + uz * f[3].x, ui = ux * f[1].y + uy * f[2].y + uz * f[3].y;
+            const float vP = s * b * b * (ur * ur + ui * ui);
+            v = id == NMS_RESP_P ? vP : vM - vP;
+        }
+        atomicAdd(&s_bins[bin], v);
+    }
+    __syncthreads();
+    double* dst = Iobj + (int64_t)out_obj[o] * nbins;
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x)
+        if (s_bins[k] != 0.f) atomicAdd(&dst[k], (double)s_bins[k]);
+}
+
+cudaError_t launch_obj_bin(const double* F, int n_out, const int32_t* out_obj, const Plan& p, const int32_t* bin_of,
+                           int nbins, int id, double* Iobj, cudaStream_t s)
+{
+    if (n_out <= 0) return cudaSuccess;
+    const int64_t pix_blocks = std::min<int64_t>((p.npix + 1023) / 1024, 64);
+    dim3 grid((unsigned)pix_blocks, (unsigned)n_out);
+    k_obj_bin<<<grid, 256, nbins * sizeof(float), s>>>(reinterpret_cast<const double2*>(F), n_out, out_obj, p.d_hy,
+                                                       p.d_hz, bin_of, p.npix, nbins, id, (float)(1.0 / p.V),
+                                                       (float)p.bH, (float)p.P[0], (float)p.P[1], (float)p.P[2], Iobj);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,690 @@
+// Learned surrogate: an MLP n_in -> H -> H -> n_out (SiLU) that maps the
+// parameters of a magnetization family to its orientation-averaged log10 I(q),
+// trained on data produced by the batched transform, with hand-written BF16
+// kernels (FP32 accumulation, FP32 master weights, Adam).
+//
+// The paper has no learned component; this follows the surrogate of the
+// build's scope: the exact transform generates the targets and judges the
+// network's error.
+//
+// Kernels: a BF16 tensor-core GEMM (mma.sync m16n8k16, FP32 accumulate) with
+// the transposes the forward and backward passes need, plus element-wise
+// SiLU / SiLU', MSE gradient, column sums for bias gradients, and Adam.
+// The MLP GEMMs are small (B x 256 x 256); this path is not the Fourier sum.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "nms.h"
+#include "nms_internal.h"
+
+namespace nms {
+
+// ------------------------------------------------------------------ GEMM
+// C[m][n] (FP32, ldc) = sum_k A(m,k) B(n,k), A(m,k) = TA ? A[k*lda + m] :
+// A[m*lda + k], B(n,k) = TB ? B[k*ldb + n] : B[n*ldb + k]; BF16 operands.
+constexpr int MG_BM = 64, MG_BN = 64, MG_BK = 32, MG_LD = MG_BK + 8;
+
+__device__ __forceinline__ void mma_bf16_16816(float* c, const uint32_t* a, const uint32_t* b)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(128) k_mlp_gemm(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda,
+                                                  const __nv_bfloat16* __restrict__ B, int ldb, float* __restrict__ C,
+                                                  int ldc)
+{
+    __shared__ __align__(16) __nv_bfloat16 As[MG_BM][MG_LD];
+    __shared__ __align__(16) __nv_bfloat16 Bs[MG_BN][MG_LD];
+    const int m0 = blockIdx.y * MG_BM, n0 = blockIdx.x * MG_BN;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int gid = lane >> 2, tig = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+    const __nv_bfloat16 zero = __float2bfloat16(0.f);
+    for (int k0 = 0; k0 < K; k0 += MG_BK) {
+        for (int idx = threadIdx.x; idx < MG_BM * MG_BK; idx += blockDim.x) {
+            int r, kk;
+            if (TA) { kk = idx / MG_BM; r = idx % MG_BM; } else { r = idx / MG_BK; kk = idx % MG_BK; }
+            const int m = m0 + r, k = k0 + kk;
+            As[r][kk] = (m < M && k < K) ? (TA ? A[(int64_t)k * lda + m] : A[(int64_t)m * lda + k]) : zero;
+        }
+        for (int idx = threadIdx.x; idx < MG_BN * MG_BK; idx += blockDim.x) {
+            int r, kk;
+            if (TB) { kk = idx / MG_BN; r = idx % MG_BN; } else { r = idx / MG_BK; kk = idx % MG_BK; }
+            const int n = n0 + r, k = k0 + kk;
+            Bs[r][kk] = (n < N && k < K) ? (TB ? B[(int64_t)k * ldb + n] : B[(int64_t)n * ldb + k]) : zero;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < MG_BK; ks += 16) {
+            uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm + i * 16 + gid;
+                af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + tig * 2]);
+                af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + tig * 2]);
+                af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + tig * 2 + 8]);
+                af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + tig * 2 + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int r = wn + j * 8 + gid;
+                bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[r][ks + tig * 2]);
+                bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[r][ks + tig * 2 + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16_16816(acc[i][j], af[i], bfr[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = m0 + wm + i * 16 + gid;
+            const int c = n0 + wn + j * 8 + tig * 2;
+            if (r < M && c < N) C[(int64_t)r * ldc + c] = acc[i][j][0];
+            if (r < M && c + 1 < N) C[(int64_t)r * ldc + c + 1] = acc[i][j][1];
+            if (r + 8 < M && c < N) C[(int64_t)(r + 8) * ldc + c] = acc[i][j][2];
+            if (r + 8 < M && c + 1 < N) C[(int64_t)(r + 8) * ldc + c + 1] = acc[i][j][3];
+        }
+}
+
+static cudaError_t mlp_gemm(bool ta, bool tb, int M, int N, int K, const __nv_bfloat16* A, int lda,
+                            const __nv_bfloat16* B, int ldb, float* C, int ldc, cudaStream_t s)
+{
+    dim3 grid((N + MG_BN - 1) / MG_BN, (M + MG_BM - 1) / MG_BM);
+    if (!ta && !tb) k_mlp_gemm<false, false><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
+    else if (!ta && tb) k_mlp_gemm<false, true><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
+    else if (ta && !tb) k_mlp_gemm<true, false><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
+    else k_mlp_gemm<true, true><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ element-wise
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + expf(-z)); }
+__device__ __forceinline__ float silu_grad(float z)
+{
+    const float s = 1.0f / (1.0f + expf(-z));
+    return s * (1.0f + z * (1.0f - s));
+}
+
+// rows of X (FP32, raw) -> normalised input; layer 1 in FP32 (K = n_in is tiny)
+__global__ void k_layer1(int B, int nin, int H, const float* __restrict__ X, const int32_t* __restrict__ perm,
+                         const float* __restrict__ xlo, const float* __restrict__ xhi, const float* __restrict__ W1,
+                         const float* __restrict__ b1, float* __restrict__ Xn, float* __restrict__ Z1,
+                         __nv_bfloat16* __restrict__ H1)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)B * H) return;
+    const int r = (int)(idx / H), h = (int)(idx % H);
+    const int64_t src = perm ? perm[r] : r;
+    float z = b1[h];
+    for (int i = 0; i < nin; ++i) {
+        const float xn = 2.0f * (X[src * nin + i] - xlo[i]) / (xhi[i] - xlo[i]) - 1.0f;
+        if (h == 0) Xn[(int64_t)r * nin + i] = xn;
+        z = fmaf(W1[h * nin + i], xn, z);
+    }
+    Z1[idx] = z;
+    H1[idx] = __float2bfloat16(silu(z));
+}
+
+// Z = C + b (row-wise), H = bf16(silu(Z)) (act) or Y = Z (no act)
+__global__ void k_bias_act(int B, int N, const float* __restrict__ C, const float* __restrict__ b, int act,
+                           float* __restrict__ Z, __nv_bfloat16* __restrict__ H)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)B * N) return;
+    const float z = C[idx] + b[idx % N];
+    Z[idx] = z;
+    if (act) H[idx] = __float2bfloat16(silu(z));
+}
+
+// dY = (Yn - Tn) / (B N) with Tn the standardised target; loss partial sums
+__global__ void k_mse_grad(int B, int N, const float* __restrict__ Y, const float* __restrict__ T,
+                           const int32_t* __restrict__ perm, const float* __restrict__ ymean,
+                           const float* __restrict__ ystd, __nv_bfloat16* __restrict__ dY, float* __restrict__ dYf,
+                           double* __restrict__ loss)
+{
+    __shared__ double red[256];
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (idx < (int64_t)B * N) {
+        const int r = (int)(idx / N), o = (int)(idx % N);
+        const int64_t src = perm ? perm[r] : r;
+        const float t = (T[src * N + o] - ymean[o]) / ystd[o];
+        const float d = Y[idx] - t;
+        l = 0.5 * (double)d * (double)d;
+        const float g = d / ((float)B * (float)N);
+        dY[idx] = __float2bfloat16(g);
+        dYf[idx] = g;
+    }
+    red[threadIdx.x] = l;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, red[0]);
+}
+
+// dZ = dH * silu'(Z): BF16 copy for the next GEMM, FP32 copy for sums
+__global__ void k_act_grad(int64_t n, const float* __restrict__ dH, const float* __restrict__ Z,
+                           __nv_bfloat16* __restrict__ dZ, float* __restrict__ dZf)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    const float g = dH[idx] * silu_grad(Z[idx]);
+    if (dZ) dZ[idx] = __float2bfloat16(g);
+    dZf[idx] = g;
+}
+
+// column sums: db[n] = sum_r G[r][n]
+__global__ void k_col_sum(int B, int N, const float* __restrict__ G, float* __restrict__ db)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float acc = 0.f;
+    for (int r = 0; r < B; ++r) acc += G[(int64_t)r * N + n];
+    db[n] = acc;
+}
+
+// dW1[h][i] = sum_r dZ1[r][h] Xn[r][i] (FP32; K = batch)
+__global__ void k_dw1(int B, int nin, int H, const float* __restrict__ dZ1, const float* __restrict__ Xn,
+                      float* __restrict__ dW1)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= H * nin) return;
+    const int h = idx / nin, i = idx % nin;
+    float acc = 0.f;
+    for (int r = 0; r < B; ++r) acc = fmaf(dZ1[(int64_t)r * H + h], Xn[(int64_t)r * nin + i], acc);
+    dW1[idx] = acc;
+}
+
+__global__ void k_adam(int64_t n, float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void k_to_bf16(int64_t n, const float* __restrict__ a, __nv_bfloat16* __restrict__ b)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = __float2bfloat16(a[i]);
+}
+
+// de-normalise outputs: y = Yn * ystd + ymean
+__global__ void k_denorm(int64_t n, int N, const float* __restrict__ Yn, const float* __restrict__ ymean,
+                         const float* __restrict__ ystd, float* __restrict__ Y)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) Y[i] = Yn[i] * ystd[i % N] + ymean[i % N];
+}
+
+// per-output mean and standard deviation of the targets (FP64 sums)
+__global__ void k_target_stats(int64_t n, int N, const float* __restrict__ T, float* __restrict__ mean,
+                               float* __restrict__ stdv)
+{
+    const int o = blockIdx.x;
+    __shared__ double s1[256], s2[256];
+    double a = 0.0, b = 0.0;
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
+        const double t = T[r * N + o];
+        a += t;
+        b += t * t;
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            s1[threadIdx.x] += s1[threadIdx.x + w];
+            s2[threadIdx.x] += s2[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double mu = s1[0] / (double)n;
+        const double var = fmax(s2[0] / (double)n - mu * mu, 1e-12);
+        mean[o] = (float)mu;
+        stdv[o] = (float)sqrt(var);
+    }
+}
+
+}  // namespace nms
+
+// ------------------------------------------------------------------ surrogate object
+struct nms_surrogate_s {
+    int nin = 0, H = 0, nout = 0;
+    cudaStream_t stream = nullptr;
+    int64_t nparam = 0;
+    float* d_w = nullptr;      // master FP32: W1[H][nin] b1[H] W2[H][H] b2[H] W3[nout][H] b3[nout]
+    float* d_g = nullptr;      // gradients, same layout
+    float* d_m = nullptr;      // Adam moments
+    float* d_v = nullptr;
+    __nv_bfloat16* d_W2h = nullptr;
+    __nv_bfloat16* d_W3h = nullptr;
+    float* d_xlo = nullptr;
+    float* d_xhi = nullptr;
+    float* d_ymean = nullptr;
+    float* d_ystd = nullptr;
+    int64_t step = 0;
+    // activations for a batch of capacity bcap
+    int bcap = 0;
+    float *d_Xn = nullptr, *d_Z1 = nullptr, *d_Z2 = nullptr, *d_Y = nullptr, *d_C = nullptr;
+    float *d_dYf = nullptr, *d_dH = nullptr, *d_dZf = nullptr;
+    __nv_bfloat16 *d_H1 = nullptr, *d_H2 = nullptr, *d_dY = nullptr, *d_dZ = nullptr;
+    int32_t* d_perm = nullptr;
+    int64_t perm_cap = 0;
+    double* d_loss = nullptr;
+    bool stats_set = false;
+};
+
+using namespace nms;
+
+namespace {
+
+float* W1p(nms_surrogate_s* s) { return s->d_w; }
+float* b1p(nms_surrogate_s* s) { return s->d_w + (int64_t)s->H * s->nin; }
+float* W2p(nms_surrogate_s* s) { return b1p(s) + s->H; }
+float* b2p(nms_surrogate_s* s) { return W2p(s) + (int64_t)s->H * s->H; }
+float* W3p(nms_surrogate_s* s) { return b2p(s) + s->H; }
+float* b3p(nms_surrogate_s* s) { return W3p(s) + (int64_t)s->nout * s->H; }
+int64_t off_b1(const nms_surrogate_s* s) { return (int64_t)s->H * s->nin; }
+int64_t off_W2(const nms_surrogate_s* s) { return off_b1(s) + s->H; }
+int64_t off_b2(const nms_surrogate_s* s) { return off_W2(s) + (int64_t)s->H * s->H; }
+int64_t off_W3(const nms_surrogate_s* s) { return off_b2(s) + s->H; }
+int64_t off_b3(const nms_surrogate_s* s) { return off_W3(s) + (int64_t)s->nout * s->H; }
+
+unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+nms_status ensure_batch(nms_surrogate_s* s, int B)
+{
+    if (B <= s->bcap) return NMS_OK;
+    void* bufs[] = {s->d_Xn, s->d_Z1, s->d_Z2, s->d_Y, s->d_C, s->d_dYf, s->d_dH, s->d_dZf, s->d_H1, s->d_H2, s->d_dY,
+                    s->d_dZ};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    const int64_t w = std::max(s->H, s->nout);
+    NMS_CUDA_TRY(cudaMalloc(&s->d_Xn, (size_t)B * s->nin * 4));
+    NMS_CUDA_TRY(cudaMalloc(&s->d_Z1, (size_t)B * s->H * 4));
+    NMS_CUDA_TRY(cudaMalloc(&s->d_Z2, (size_t)B * s->H * 4));
+    NMS_CUDA_TRY(cudaMalloc(&s->d_Y, (size_t)B * s->nout * 4));
+    NMS_CUDA_TRY(cudaMalloc(&s->d_C, (size_t)B * w * 4));
+    NMS_CUDA_TRY(cudaMalloc(&s->d_dYf, (size_t)B * s->nout * 4));
+    NMS_CUDA_TRY(cudaMalloc(&s->d_dH, (size_t)B * s->H * 4));
+    NMS_CUDA_TRY(cudaMalloc(&s->d_dZf, (size_t)B * s->H * 4));
+    NMS_CUDA_TRY(cudaMalloc(&s->d_H1, (size_t)B * s->H * 2));
+    NMS_CUDA_TRY(cudaMalloc(&s->d_H2, (size_t)B * s->H * 2));
+    NMS_CUDA_TRY(cudaMalloc(&s->d_dY, (size_t)B * s->nout * 2));
+    NMS_CUDA_TRY(cudaMalloc(&s->d_dZ, (size_t)B * s->H * 2));
+    s->bcap = B;
+    return NMS_OK;
+}
+
+nms_status refresh_bf16(nms_surrogate_s* s)
+{
+    const int64_t n2 = (int64_t)s->H * s->H, n3 = (int64_t)s->nout * s->H;
+    k_to_bf16<<<nb(n2), 256, 0, s->stream>>>(n2, W2p(s), s->d_W2h);
+    k_to_bf16<<<nb(n3), 256, 0, s->stream>>>(n3, W3p(s), s->d_W3h);
+    NMS_CUDA_TRY(cudaGetLastError());
+    return NMS_OK;
+}
+
+// forward on rows perm[0..B) (or 0..B) of X; output normalised Y in d_Y
+nms_status forward(nms_surrogate_s* s, const float* X, const int32_t* perm, int B)
+{
+    cudaStream_t st = s->stream;
+    const int H = s->H, O = s->nout;
+    k_layer1<<<nb((int64_t)B * H), 256, 0, st>>>(B, s->nin, H, X, perm, s->d_xlo, s->d_xhi, W1p(s), b1p(s), s->d_Xn,
+                                                 s->d_Z1, s->d_H1);
+    NMS_CUDA_TRY(cudaGetLastError());
+    NMS_CUDA_TRY(mlp_gemm(false, false, B, H, H, s->d_H1, H, s->d_W2h, H, s->d_C, H, st));
+    k_bias_act<<<nb((int64_t)B * H), 256, 0, st>>>(B, H, s->d_C, b2p(s), 1, s->d_Z2, s->d_H2);
+    NMS_CUDA_TRY(cudaGetLastError());
+    NMS_CUDA_TRY(mlp_gemm(false, false, B, O, H, s->d_H2, H, s->d_W3h, H, s->d_C, O, st));
+    k_bias_act<<<nb((int64_t)B * O), 256, 0, st>>>(B, O, s->d_C, b3p(s), 0, s->d_Y, nullptr);
+    NMS_CUDA_TRY(cudaGetLastError());
+    return NMS_OK;
+}
+
+// backward after forward: gradients into d_g (overwritten), loss added to d_loss
+nms_status backward(nms_surrogate_s* s, const float* T, const int32_t* perm, int B)
+{
+    cudaStream_t st = s->stream;
+    const int H = s->H, O = s->nout, nin = s->nin;
+    float* g = s->d_g;
+    k_mse_grad<<<nb((int64_t)B * O), 256, 0, st>>>(B, O, s->d_Y, T, perm, s->d_ymean, s->d_ystd, s->d_dY, s->d_dYf,
+                                                    s->d_loss);
+    NMS_CUDA_TRY(cudaGetLastError());
+    // layer 3: dW3 = dY^T H2, db3 = colsum dY, dH2 = dY W3
+    NMS_CUDA_TRY(mlp_gemm(true, true, O, H, B, s->d_dY, O, s->d_H2, H, g + off_W3(s), H, st));
+    k_col_sum<<<nb(O), 256, 0, st>>>(B, O, s->d_dYf, g + off_b3(s));
+    NMS_CUDA_TRY(mlp_gemm(false, true, B, H, O, s->d_dY, O, s->d_W3h, H, s->d_dH, H, st));
+    // layer 2
+    k_act_grad<<<nb((int64_t)B * H), 256, 0, st>>>((int64_t)B * H, s->d_dH, s->d_Z2, s->d_dZ, s->d_dZf);
+    NMS_CUDA_TRY(cudaGetLastError());
+    NMS_CUDA_TRY(mlp_gemm(true, true, H, H, B, s->d_dZ, H, s->d_H1, H, g + off_W2(s), H, st));
+    k_col_sum<<<nb(H), 256, 0, st>>>(B, H, s->d_dZf, g + off_b2(s));
+    NMS_CUDA_TRY(mlp_gemm(false, true, B, H, H, s->d_dZ, H, s->d_W2h, H, s->d_dH, H, st));
+    // layer 1 (FP32)
+    k_act_grad<<<nb((int64_t)B * H), 256, 0, st>>>((int64_t)B * H, s->d_dH, s->d_Z1, nullptr, s->d_dZf);
+    k_dw1<<<nb((int64_t)H * nin), 256, 0, st>>>(B, nin, H, s->d_dZf, s->d_Xn, g);
+    k_col_sum<<<nb(H), 256, 0, st>>>(B, H, s->d_dZf, g + off_b1(s));
+    NMS_CUDA_TRY(cudaGetLastError());
+    return NMS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nms_status nms_surrogate_create(nms_surrogate_t* out, int32_t n_in, int32_t n_hidden, int32_t n_out,
+                                const float* x_lo, const float* x_hi, uint64_t seed, void* cuda_stream)
+{
+    set_error("");
+    if (!out) return NMS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_in < 1 || n_in > 64 || n_hidden < 8 || n_hidden > 4096 || n_out < 1 || n_out > 4096 || !x_lo || !x_hi) {
+        set_error("surrogate: need 1 <= n_in <= 64, 8 <= n_hidden <= 4096, 1 <= n_out <= 4096 and input bounds");
+        return NMS_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < n_in; ++i)
+        if (!(x_hi[i] > x_lo[i])) {
+            set_error("surrogate: x_hi must exceed x_lo");
+            return NMS_ERR_INVALID_ARG;
+        }
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) {
+        cudaGetLastError();
+        set_error("no CUDA device available (libnms has no CPU fallback)");
+        return NMS_ERR_CUDA;
+    }
+    nms_surrogate_s* s = new nms_surrogate_s();
+    s->nin = n_in;
+    s->H = n_hidden;
+    s->nout = n_out;
+    s->stream = (cudaStream_t)cuda_stream;
+    s->nparam = (int64_t)n_hidden * n_in + n_hidden + (int64_t)n_hidden * n_hidden + n_hidden +
+                (int64_t)n_out * n_hidden + n_out;
+    // He-style uniform initialisation from a seeded host generator
+    std::vector<float> w(s->nparam, 0.f);
+    std::mt19937_64 rng(seed);
+    auto fill = [&](int64_t off, int64_t n, int fan_in) {
+        const double a = sqrt(6.0 / fan_in);
+        std::uniform_real_distribution<double> u(-a, a);
+        for (int64_t i = 0; i < n; ++i) w[off + i] = (float)u(rng);
+    };
+    fill(0, (int64_t)n_hidden * n_in, n_in);
+    fill(off_W2(s), (int64_t)n_hidden * n_hidden, n_hidden);
+    fill(off_W3(s), (int64_t)n_out * n_hidden, n_hidden);
+    std::vector<float> ones(n_out, 1.f), zeros(n_out, 0.f);
+    auto bail = [&](nms_status st) {
+        nms_surrogate_destroy(s);
+        return st;
+    };
+    if (cudaMalloc(&s->d_w, s->nparam * 4) || cudaMalloc(&s->d_g, s->nparam * 4) ||
+        cudaMalloc(&s->d_m, s->nparam * 4) || cudaMalloc(&s->d_v, s->nparam * 4) ||
+        cudaMalloc(&s->d_W2h, (size_t)n_hidden * n_hidden * 2) || cudaMalloc(&s->d_W3h, (size_t)n_out * n_hidden * 2) ||
+        cudaMalloc(&s->d_xlo, n_in * 4) || cudaMalloc(&s->d_xhi, n_in * 4) || cudaMalloc(&s->d_ymean, n_out * 4) ||
+        cudaMalloc(&s->d_ystd, n_out * 4) || cudaMalloc(&s->d_loss, 8)) {
+        cudaGetLastError();
+        set_error("surrogate: device allocation failed");
+        return bail(NMS_ERR_OUT_OF_MEMORY);
+    }
+    cudaMemcpy(s->d_w, w.data(), s->nparam * 4, cudaMemcpyHostToDevice);
+    cudaMemset(s->d_m, 0, s->nparam * 4);
+    cudaMemset(s->d_v, 0, s->nparam * 4);
+    cudaMemset(s->d_g, 0, s->nparam * 4);
+    cudaMemcpy(s->d_xlo, x_lo, n_in * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(s->d_xhi, x_hi, n_in * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(s->d_ymean, zeros.data(), n_out * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(s->d_ystd, ones.data(), n_out * 4, cudaMemcpyHostToDevice);
+    nms_status st = refresh_bf16(s);
+    if (st) return bail(st);
+    if (cudaDeviceSynchronize() != cudaSuccess) return bail(cuda_fail(cudaGetLastError(), "surrogate init"));
+    *out = s;
+    return NMS_OK;
+}
+
+nms_status nms_surrogate_set_target_stats(nms_surrogate_t s, const float* y_mean, const float* y_std)
+{
+    set_error("");
+    if (!s || !y_mean || !y_std) return NMS_ERR_INVALID_ARG;
+    for (int o = 0; o < s->nout; ++o)
+        if (!(y_std[o] > 0)) {
+            set_error("surrogate: y_std must be > 0");
+            return NMS_ERR_INVALID_ARG;
+        }
+    NMS_CUDA_TRY(cudaMemcpy(s->d_ymean, y_mean, s->nout * 4, cudaMemcpyHostToDevice));
+    NMS_CUDA_TRY(cudaMemcpy(s->d_ystd, y_std, s->nout * 4, cudaMemcpyHostToDevice));
+    s->stats_set = true;
+    return NMS_OK;
+}
+
+nms_status nms_surrogate_train(nms_surrogate_t s, const float* X, const float* Y, int64_t n, int32_t batch,
+                               int32_t epochs, float lr, uint64_t shuffle_seed, float* final_loss)
+{
+    set_error("");
+    if (!s || !X || !Y || n < 1 || batch < 1 || epochs < 0 || !(lr > 0)) {
+        set_error("surrogate train: bad arguments");
+        return NMS_ERR_INVALID_ARG;
+    }
+    if (n > INT32_MAX) {
+        set_error("surrogate train: n too large");
+        return NMS_ERR_INVALID_ARG;
+    }
+    const int B = (int)std::min<int64_t>(batch, n);
+    nms_status st = ensure_batch(s, B);
+    if (st) return st;
+    if (!s->stats_set) {
+        k_target_stats<<<s->nout, 256, 0, s->stream>>>(n, s->nout, Y, s->d_ymean, s->d_ystd);
+        NMS_CUDA_TRY(cudaGetLastError());
+        s->stats_set = true;
+    }
+    if (n > s->perm_cap) {
+        if (s->d_perm) cudaFree(s->d_perm);
+        NMS_CUDA_TRY(cudaMalloc(&s->d_perm, n * sizeof(int32_t)));
+        s->perm_cap = n;
+    }
+    std::vector<int32_t> perm(n);
+    std::mt19937_64 rng(shuffle_seed);
+    double last = 0.0;
+    for (int e = 0; e < epochs; ++e) {
+        for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
+        std::shuffle(perm.begin(), perm.end(), rng);
+        NMS_CUDA_TRY(cudaMemcpyAsync(s->d_perm, perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s->stream));
+        NMS_CUDA_TRY(cudaMemsetAsync(s->d_loss, 0, 8, s->stream));
+        for (int64_t b0 = 0; b0 + B <= n; b0 += B) {
+            if ((st = forward(s, X, s->d_perm + b0, B))) return st;
+            if ((st = backward(s, Y, s->d_perm + b0, B))) return st;
+            ++s->step;
+            const float b1 = 0.9f, b2 = 0.999f;
+            const float c1 = 1.f - powf(b1, (float)s->step), c2 = 1.f - powf(b2, (float)s->step);
+            k_adam<<<nb(s->nparam), 256, 0, s->stream>>>(s->nparam, s->d_w, s->d_g, s->d_m, s->d_v, lr, b1, b2, 1e-8f,
+                                                          c1, c2);
+            NMS_CUDA_TRY(cudaGetLastError());
+            if ((st = refresh_bf16(s))) return st;
+        }
+        double h = 0.0;
+        NMS_CUDA_TRY(cudaMemcpyAsync(&h, s->d_loss, 8, cudaMemcpyDeviceToHost, s->stream));
+        NMS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        last = h / (double)((n / B) * (int64_t)B * s->nout);
+    }
+    if (final_loss) *final_loss = (float)last;
+    return NMS_OK;
+}
+
+nms_status nms_surrogate_gradients(nms_surrogate_t s, const float* X, const float* Y, int32_t n, float* grad,
+                                   double* loss)
+{
+    set_error("");
+    if (!s || !X || !Y || n < 1 || !grad) return NMS_ERR_INVALID_ARG;
+    nms_status st = ensure_batch(s, n);
+    if (st) return st;
+    NMS_CUDA_TRY(cudaMemsetAsync(s->d_loss, 0, 8, s->stream));
+    if ((st = forward(s, X, nullptr, n))) return st;
+    if ((st = backward(s, Y, nullptr, n))) return st;
+    NMS_CUDA_TRY(cudaMemcpyAsync(grad, s->d_g, s->nparam * 4, cudaMemcpyDeviceToHost, s->stream));
+    double h = 0.0;
+    NMS_CUDA_TRY(cudaMemcpyAsync(&h, s->d_loss, 8, cudaMemcpyDeviceToHost, s->stream));
+    NMS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (loss) *loss = h / ((double)n * s->nout);
+    return NMS_OK;
+}
+
+nms_status nms_surrogate_infer(nms_surrogate_t s, const float* X, int64_t n, float* Y)
+{
+    set_error("");
+    if (!s || !X || !Y || n < 0) return NMS_ERR_INVALID_ARG;
+    const int B = 65536;
+    nms_status st = ensure_batch(s, (int)std::min<int64_t>(B, std::max<int64_t>(n, 1)));
+    if (st) return st;
+    for (int64_t b0 = 0; b0 < n; b0 += s->bcap) {
+        const int nb_ = (int)std::min<int64_t>(s->bcap, n - b0);
+        if ((st = forward(s, X + b0 * s->nin, nullptr, nb_))) return st;
+        k_denorm<<<nb((int64_t)nb_ * s->nout), 256, 0, s->stream>>>((int64_t)nb_ * s->nout, s->nout, s->d_Y, s->d_ymean,
+                                                                     s->d_ystd, Y + b0 * s->nout);
+        NMS_CUDA_TRY(cudaGetLastError());
+    }
+    return NMS_OK;
+}
+
+nms_status nms_surrogate_get_params(nms_surrogate_t s, float* host, int64_t* count)
+{
+    set_error("");
+    if (!s) return NMS_ERR_INVALID_ARG;
+    if (count) *count = s->nparam;
+    if (host) {
+        NMS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        NMS_CUDA_TRY(cudaMemcpy(host, s->d_w, s->nparam * 4, cudaMemcpyDeviceToHost));
+    }
+    return NMS_OK;
+}
+
+nms_status nms_surrogate_set_params(nms_surrogate_t s, const float* host, int64_t count)
+{
+    set_error("");
+    if (!s || !host || count != s->nparam) {
+        set_error("surrogate: parameter count mismatch");
+        return NMS_ERR_INVALID_ARG;
+    }
+    NMS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    NMS_CUDA_TRY(cudaMemcpy(s->d_w, host, s->nparam * 4, cudaMemcpyHostToDevice));
+    return refresh_bf16(s);
+}
+
+// Checkpoint: header, master weights, Adam moments, target statistics.
+nms_status nms_surrogate_save(nms_surrogate_t s, const char* path)
+{
+    set_error("");
+    if (!s || !path) return NMS_ERR_INVALID_ARG;
+    std::vector<float> w(s->nparam), m(s->nparam), v(s->nparam), ym(s->nout), ys(s->nout), xl(s->nin), xh(s->nin);
+    NMS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    NMS_CUDA_TRY(cudaMemcpy(w.data(), s->d_w, s->nparam * 4, cudaMemcpyDeviceToHost));
+    NMS_CUDA_TRY(cudaMemcpy(m.data(), s->d_m, s->nparam * 4, cudaMemcpyDeviceToHost));
+    NMS_CUDA_TRY(cudaMemcpy(v.data(), s->d_v, s->nparam * 4, cudaMemcpyDeviceToHost));
+    NMS_CUDA_TRY(cudaMemcpy(ym.data(), s->d_ymean, s->nout * 4, cudaMemcpyDeviceToHost));
+    NMS_CUDA_TRY(cudaMemcpy(ys.data(), s->d_ystd, s->nout * 4, cudaMemcpyDeviceToHost));
+    NMS_CUDA_TRY(cudaMemcpy(xl.data(), s->d_xlo, s->nin * 4, cudaMemcpyDeviceToHost));
+    NMS_CUDA_TRY(cudaMemcpy(xh.data(), s->d_xhi, s->nin * 4, cudaMemcpyDeviceToHost));
+    FILE* f = fopen(path, "wb");
+    if (!f) {
+        set_error(std::string("cannot open ") + path);
+        return NMS_ERR_INVALID_ARG;
+    }
+    const char magic[8] = {'N', 'M', 'S', 'S', 'U', 'R', '0', '1'};
+    int64_t hdr[5] = {s->nin, s->H, s->nout, s->step, s->stats_set ? 1 : 0};
+    bool ok = fwrite(magic, 1, 8, f) == 8 && fwrite(hdr, 8, 5, f) == 5 &&
+              fwrite(w.data(), 4, s->nparam, f) == (size_t)s->nparam && fwrite(m.data(), 4, s->nparam, f) == (size_t)s->nparam &&
+              fwrite(v.data(), 4, s->nparam, f) == (size_t)s->nparam && fwrite(ym.data(), 4, s->nout, f) == (size_t)s->nout &&
+              fwrite(ys.data(), 4, s->nout, f) == (size_t)s->nout && fwrite(xl.data(), 4, s->nin, f) == (size_t)s->nin &&
+              fwrite(xh.data(), 4, s->nin, f) == (size_t)s->nin;
+    fclose(f);
+    if (!ok) {
+        set_error("short write");
+        return NMS_ERR_INVALID_ARG;
+    }
+    return NMS_OK;
+}
+
+nms_status nms_surrogate_load(nms_surrogate_t s, const char* path)
+{
+    set_error("");
+    if (!s || !path) return NMS_ERR_INVALID_ARG;
+    FILE* f = fopen(path, "rb");
+    if (!f) {
+        set_error(std::string("cannot open ") + path);
+        return NMS_ERR_INVALID_ARG;
+    }
+    char magic[8];
+    int64_t hdr[5];
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, "NMSSUR01", 8) == 0 && fread(hdr, 8, 5, f) == 5 &&
+              hdr[0] == s->nin && hdr[1] == s->H && hdr[2] == s->nout;
+    std::vector<float> w(s->nparam), m(s->nparam), v(s->nparam), ym(s->nout), ys(s->nout), xl(s->nin), xh(s->nin);
+    if (ok)
+        ok = fread(w.data(), 4, s->nparam, f) == (size_t)s->nparam && fread(m.data(), 4, s->nparam, f) == (size_t)s->nparam &&
+             fread(v.data(), 4, s->nparam, f) == (size_t)s->nparam && fread(ym.data(), 4, s->nout, f) == (size_t)s->nout &&
+             fread(ys.data(), 4, s->nout, f) == (size_t)s->nout && fread(xl.data(), 4, s->nin, f) == (size_t)s->nin &&
+             fread(xh.data(), 4, s->nin, f) == (size_t)s->nin;
+    fclose(f);
+    if (!ok) {
+        set_error("not a surrogate checkpoint of this shape");
+        return NMS_ERR_INVALID_ARG;
+    }
+    NMS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    NMS_CUDA_TRY(cudaMemcpy(s->d_w, w.data(), s->nparam * 4, cudaMemcpyHostToDevice));
+    NMS_CUDA_TRY(cudaMemcpy(s->d_m, m.data(), s->nparam * 4, cudaMemcpyHostToDevice));
+    NMS_CUDA_TRY(cudaMemcpy(s->d_v, v.data(), s->nparam * 4, cudaMemcpyHostToDevice));
+    NMS_CUDA_TRY(cudaMemcpy(s->d_ymean, ym.data(), s->nout * 4, cudaMemcpyHostToDevice));
+    NMS_CUDA_TRY(cudaMemcpy(s->d_ystd, ys.data(), s->nout * 4, cudaMemcpyHostToDevice));
+    NMS_CUDA_TRY(cudaMemcpy(s->d_xlo, xl.data(), s->nin * 4, cudaMemcpyHostToDevice));
+    NMS_CUDA_TRY(cudaMemcpy(s->d_xhi, xh.data(), s->nin * 4, cudaMemcpyHostToDevice));
+    s->step = hdr[3];
+    s->stats_set = hdr[4] != 0;
+    return refresh_bf16(s);
+}
+
+nms_status nms_surrogate_destroy(nms_surrogate_t s)
+{
+    if (!s) return NMS_OK;
+    cudaStreamSynchronize(s->stream);
+    void* bufs[] = {s->d_w, s->d_g, s->d_m, s->d_v, s->d_W2h, s->d_W3h, s->d_xlo, s->d_xhi, s->d_ymean, s->d_ystd,
+                    s->d_Xn, s->d_Z1, s->d_Z2, s->d_Y, s->d_C, s->d_dYf, s->d_dH, s->d_dZf, s->d_H1, s->d_H2,
+                    s->d_dY, s->d_dZ, s->d_perm, s->d_loss};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete s;
+    return NMS_OK;
+}
+
+}  // extern "C"

@@ -136,6 +136,8 @@ static void free_plan(nms_plan_s* p)
     tc_release(*p);
     if (p->d_cposl && p->d_cposl != p->d_cpos) dfree(p->d_cposl);
     if (p->d_yzl && p->d_yzl != p->d_yz) dfree(p->d_yzl);
+    dfree(p->d_bin_of);
+    dfree(p->d_Iobj);
     p->timer.release();
     delete p;
 }
@@ -412,6 +414,8 @@ nms_status nms_amplitudes(nms_plan_t plan)
     const int64_t np = p.npix;
     NMS_CUDA_TRY(cudaMemsetAsync(p.d_Gtot, 0, 16 * np * 8, s));
     if (p.d_Gdil) NMS_CUDA_TRY(cudaMemsetAsync(p.d_Gdil, 0, 16 * np * 8, s));
+    if (p.d_Iobj)
+        NMS_CUDA_TRY(cudaMemsetAsync(p.d_Iobj, 0, (size_t)tc_object_count(p) * p.oiq_nbins * sizeof(double), s));
     if (p.path == NMS_PREC_TC_F16X3) {
         nms_status st = tc_amplitudes(p, s);
         if (st) return st;
@@ -629,6 +633,75 @@ nms_status nms_correlation(int32_t nq, const double* q, const double* Iq, int32_
         cudaFreeAsync(dp, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "correlation");
+    return NMS_OK;
+}
+
+nms_status nms_plan_object_iq(nms_plan_t plan, int32_t response_id, int32_t nbins, const double* bin_edges)
+{
+    set_error("");
+    if (!plan) return fail(NMS_ERR_INVALID_ARG, "plan is NULL");
+    Plan& p = *plan;
+    if (p.path != NMS_PREC_TC_F16X3) return fail(NMS_ERR_UNSUPPORTED, "per-object averages need the tensor-core path");
+    if (!(response_id == NMS_RESP_N || response_id == NMS_RESP_M || response_id == NMS_RESP_P ||
+          response_id == NMS_RESP_SF || response_id == NMS_RESP_UNPOL))
+        return fail(NMS_ERR_UNSUPPORTED, "per-object averages support N, M, P, SF and UNPOL");
+    if (nbins < 1 || nbins > 8192 || !bin_edges) return fail(NMS_ERR_INVALID_ARG, "need 1 <= nbins <= 8192 and bin_edges");
+    for (int b = 0; b < nbins; ++b)
+        if (!(bin_edges[b + 1] > bin_edges[b])) return fail(NMS_ERR_INVALID_ARG, "bin_edges not increasing");
+    std::vector<int32_t> bin_of(p.npix);
+    p.oiq_counts.assign(nbins, 0);
+    p.oiq_qmean.assign(nbins, 0.0);
+    for (int64_t i = 0; i < p.npix; ++i) {
+        const double x = p.h_qa[i];
+        int b = -1;
+        if (x >= bin_edges[0] && x < bin_edges[nbins])
+            b = (int)(std::upper_bound(bin_edges, bin_edges + nbins + 1, x) - bin_edges) - 1;
+        bin_of[i] = b;
+        if (b >= 0) {
+            p.oiq_counts[b]++;
+            p.oiq_qmean[b] += x;
+        }
+    }
+    for (int b = 0; b < nbins; ++b) p.oiq_qmean[b] = p.oiq_counts[b] ? p.oiq_qmean[b] / p.oiq_counts[b] : NAN;
+    dfree(p.d_bin_of);
+    dfree(p.d_Iobj);
+    p.d_bin_of = nullptr;
+    p.d_Iobj = nullptr;
+    nms_status st;
+    if ((st = dalloc(&p.d_bin_of, p.npix, "bin_of")) ||
+        (st = dalloc(&p.d_Iobj, (size_t)tc_object_count(p) * nbins, "object I(q)")))
+        return st;
+    NMS_CUDA_TRY(cudaMemcpy(p.d_bin_of, bin_of.data(), p.npix * sizeof(int32_t), cudaMemcpyHostToDevice));
+    p.oiq_id = response_id;
+    p.oiq_nbins = nbins;
+    p.have_G = false;
+    return NMS_OK;
+}
+
+nms_status nms_get_object_iq(nms_plan_t plan, double* Iq, int64_t* counts, double* qmean, int32_t out_is_device)
+{
+    set_error("");
+    if (!plan || !Iq) return fail(NMS_ERR_INVALID_ARG, "plan/Iq is NULL");
+    Plan& p = *plan;
+    if (p.oiq_id < 0) return fail(NMS_ERR_BAD_STATE, "nms_plan_object_iq has not been called");
+    if (!p.have_G) return fail(NMS_ERR_BAD_STATE, "nms_amplitudes has not run");
+    nms_status st = check_device_error(p);
+    if (st) return st;
+    const int64_t K = tc_object_count(p);
+    const int nb = p.oiq_nbins;
+    std::vector<double> h((size_t)K * nb);
+    NMS_CUDA_TRY(cudaMemcpyAsync(h.data(), p.d_Iobj, h.size() * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
+    NMS_CUDA_TRY(cudaStreamSynchronize(p.stream));
+    for (int64_t k = 0; k < K; ++k)
+        for (int b = 0; b < nb; ++b) {
+            const int64_t c = p.oiq_counts[b];
+            h[(size_t)k * nb + b] = c ? h[(size_t)k * nb + b] / ((double)c * p.rot_done) : NAN;
+        }
+    cudaMemcpyKind kind = out_is_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    NMS_CUDA_TRY(cudaMemcpyAsync(Iq, h.data(), h.size() * sizeof(double), kind, p.stream));
+    if (counts) NMS_CUDA_TRY(cudaMemcpyAsync(counts, p.oiq_counts.data(), nb * sizeof(int64_t), kind, p.stream));
+    if (qmean) NMS_CUDA_TRY(cudaMemcpyAsync(qmean, p.oiq_qmean.data(), nb * sizeof(double), kind, p.stream));
+    NMS_CUDA_TRY(cudaStreamSynchronize(p.stream));
     return NMS_OK;
 }
 

@@ -96,6 +96,13 @@ struct Plan {
     double* d_wscale = nullptr;   // per-channel power-of-two weight scales [4]
     void* tc_state = nullptr;     // tensor-path state (k_gemm.cu)
     double h_wmax[2] = {0, 0};    // max_j V_j |N_j|, max_j V_j |M_j| (rotation invariant)
+    // per-object azimuthal averages (nms_plan_object_iq)
+    int32_t oiq_id = -1;
+    int oiq_nbins = 0;
+    int32_t* d_bin_of = nullptr;  // bin of each pixel or -1
+    double* d_Iobj = nullptr;     // [objects][nbins] sums of the response
+    std::vector<int64_t> oiq_counts;
+    std::vector<double> oiq_qmean;
     int64_t max_sum_cells = 0;    // largest cell range summed in one call
 
     StageTimer timer;
@@ -133,6 +140,9 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s);
 void tc_release(Plan& p);
 
 int device_sm_count();
+cudaError_t launch_obj_bin(const double* F, int n_out, const int32_t* out_obj, const Plan& p, const int32_t* bin_of,
+                           int nbins, int id, double* Iobj, cudaStream_t s);
+int64_t tc_object_count(const Plan& p);
 
 }  // namespace nms
 

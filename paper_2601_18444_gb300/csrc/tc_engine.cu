@@ -334,6 +334,12 @@ nms_status tc_setup(Plan& p)
     return NMS_OK;
 }
 
+int64_t tc_object_count(const Plan& p)
+{
+    const TcState* t = (const TcState*)p.tc_state;
+    return (t && t->objects) ? p.n_objects : 1;
+}
+
 void tc_release(Plan& p)
 {
     TcState* t = (TcState*)p.tc_state;
@@ -389,19 +395,24 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
             }
             p.timer.begin(ST_GACC);
             int nl = 0;
+            if (p.oiq_id >= 0) {
+                NMS_CUDA_TRY(launch_obj_bin(t.d_Fb, ob.n_out, S.d_out_obj + ob.out0, p, p.d_bin_of, p.oiq_nbins,
+                                            p.oiq_id, p.d_Iobj, s));
+                ++nl;
+            }
             if (t.objects) {
                 NMS_CUDA_TRY(launch_centres(ob.n_out, S.d_out_obj + ob.out0, S.d_out_rot + ob.out0, rb0, t.d_rot, t.d_cen,
                                             t.d_cyz, s));
                 NMS_CUDA_TRY(launch_gacc_batch(t.d_Fb, ob.n_out, np, p.d_Gdil, s));
                 NMS_CUDA_TRY(launch_shift_batch(t.d_Fb, ob.n_out, t.d_cyz, S.d_out_rot + ob.out0, p.d_qturn, np,
                                                 t.d_Ftot_b, s));
-                nl = 3;
+                nl += 3;
             } else {
                 NMS_CUDA_TRY(launch_gacc_batch(t.d_Fb, ob.n_out, np, p.d_Gtot, s));
-                nl = 1;
+                nl += 1;
                 if (p.d_Gdil) {
                     NMS_CUDA_TRY(launch_gacc_batch(t.d_Fb, ob.n_out, np, p.d_Gdil, s));
-                    nl = 2;
+                    nl += 1;
                 }
                 last_F = t.d_Fb + (size_t)(ob.n_out - 1) * 8 * np;
                 if (rb0 + nrl == p.n_rot && &ob == &S.batches.back())

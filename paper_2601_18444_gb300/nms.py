@@ -51,6 +51,7 @@ class nms_options(ctypes.Structure):
 
 
 _D = ctypes.POINTER(ctypes.c_double)
+_F = ctypes.POINTER(ctypes.c_float)
 _I64 = ctypes.POINTER(ctypes.c_int64)
 _V = ctypes.c_void_p
 
@@ -68,6 +69,20 @@ SIGNATURES = {
     "nms_correlation": (ctypes.c_int, [ctypes.c_int32, _V, _V, ctypes.c_int32, _V, ctypes.c_double, _V, _V,
                                        ctypes.c_int32, _V]),
     "nms_plan_stage_ms": (ctypes.c_int, [_V, _D, _I64, ctypes.c_int32]),
+    "nms_plan_object_iq": (ctypes.c_int, [_V, ctypes.c_int32, ctypes.c_int32, _D]),
+    "nms_get_object_iq": (ctypes.c_int, [_V, _V, _V, _V, ctypes.c_int32]),
+    "nms_surrogate_create": (ctypes.c_int, [ctypes.POINTER(_V), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                            _F, _F, ctypes.c_uint64, _V]),
+    "nms_surrogate_set_target_stats": (ctypes.c_int, [_V, _F, _F]),
+    "nms_surrogate_train": (ctypes.c_int, [_V, _V, _V, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                           ctypes.c_uint64, _F]),
+    "nms_surrogate_gradients": (ctypes.c_int, [_V, _V, _V, ctypes.c_int32, _F, _D]),
+    "nms_surrogate_infer": (ctypes.c_int, [_V, _V, ctypes.c_int64, _V]),
+    "nms_surrogate_get_params": (ctypes.c_int, [_V, _F, _I64]),
+    "nms_surrogate_set_params": (ctypes.c_int, [_V, _F, ctypes.c_int64]),
+    "nms_surrogate_save": (ctypes.c_int, [_V, ctypes.c_char_p]),
+    "nms_surrogate_load": (ctypes.c_int, [_V, ctypes.c_char_p]),
+    "nms_surrogate_destroy": (ctypes.c_int, [_V]),
     "nms_dsft_direct_noalloc": (ctypes.c_int, [ctypes.c_int64, _V, _V, _V, ctypes.c_int64, _V, _V, _V, _V]),
     "nms_plan_destroy": (ctypes.c_int, [_V]),
     "nms_last_error": (ctypes.c_char_p, []),
@@ -123,7 +138,20 @@ def _is_dev(t):
 
 
 def _ptr(t):
-    return ctypes.c_void_p(t.data_ptr() if _is_dev(t) else t.ctypes.data)
+    """Raw address of a row-major buffer; strided views are refused (the C ABI
+    takes plain row-major arrays)."""
+    if _is_dev(t):
+        if not t.is_contiguous():
+            raise ValueError("device tensor must be contiguous (row-major)")
+        return ctypes.c_void_p(t.data_ptr())
+    if not t.flags.c_contiguous:
+        raise ValueError("host array must be C-contiguous")
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def _dev_in(t):
+    """Device input as a row-major tensor (copies a strided view)."""
+    return t.contiguous() if _is_dev(t) else t
 
 
 def nms_options_default(**kw):
@@ -238,8 +266,7 @@ def nms_azimuthal_average(plan, img, bin_edges=None, nbins=None):
         p_e = edges.ctypes.data_as(_D)
     else:
         edges, p_e, nb = None, None, int(nbins)
-    if not _is_dev(img):
-        img = np.ascontiguousarray(img, dtype=np.float64)
+    img = _dev_in(img) if _is_dev(img) else np.ascontiguousarray(img, dtype=np.float64)
     I = np.empty(nb, dtype=np.float64)
     c = np.empty(nb, dtype=np.int64)
     qm = np.empty(nb, dtype=np.float64)
@@ -273,9 +300,114 @@ def nms_plan_stage_ms(plan, reset=False):
     return {STAGES[i]: (ms[i], ln[i]) for i in range(8)}
 
 
+class Surrogate:
+    """Owning wrapper of an nms_surrogate_t."""
+
+    def __init__(self, handle, n_in, n_hidden, n_out):
+        self.handle, self.n_in, self.n_hidden, self.n_out = handle, n_in, n_hidden, n_out
+
+    def close(self):
+        if self.handle:
+            load().nms_surrogate_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _fp(a):
+    return a.ctypes.data_as(_F)
+
+
+def nms_surrogate_create(n_in, n_hidden, n_out, x_lo, x_hi, seed=0, stream=None):
+    lo = np.ascontiguousarray(x_lo, dtype=np.float32)
+    hi = np.ascontiguousarray(x_hi, dtype=np.float32)
+    h = ctypes.c_void_p()
+    _check(load().nms_surrogate_create(ctypes.byref(h), n_in, n_hidden, n_out, _fp(lo), _fp(hi), seed,
+                                       ctypes.c_void_p(stream or 0)))
+    return Surrogate(h, n_in, n_hidden, n_out)
+
+
+def nms_surrogate_set_target_stats(s, y_mean, y_std):
+    m = np.ascontiguousarray(y_mean, dtype=np.float32)
+    d = np.ascontiguousarray(y_std, dtype=np.float32)
+    _check(load().nms_surrogate_set_target_stats(s.handle, _fp(m), _fp(d)))
+
+
+def nms_surrogate_train(s, X, Y, batch, epochs, lr, seed=0):
+    """X, Y: float32 CUDA tensors [n, n_in], [n, n_out]; returns the last epoch's loss."""
+    X, Y = _dev_in(X), _dev_in(Y)
+    loss = ctypes.c_float(0.0)
+    _check(load().nms_surrogate_train(s.handle, _ptr(X), _ptr(Y), X.shape[0], batch, epochs, lr, seed,
+                                      ctypes.byref(loss)))
+    return loss.value
+
+
+def nms_surrogate_gradients(s, X, Y):
+    X, Y = _dev_in(X), _dev_in(Y)
+    g = np.empty(nms_surrogate_get_params(s, count_only=True), dtype=np.float32)
+    loss = ctypes.c_double(0.0)
+    _check(load().nms_surrogate_gradients(s.handle, _ptr(X), _ptr(Y), X.shape[0], _fp(g), ctypes.byref(loss)))
+    return g, loss.value
+
+
+def nms_surrogate_infer(s, X, Y):
+    X = _dev_in(X)
+    _check(load().nms_surrogate_infer(s.handle, _ptr(X), X.shape[0], _ptr(Y)))
+    return Y
+
+
+def nms_surrogate_get_params(s, count_only=False):
+    n = ctypes.c_int64(0)
+    _check(load().nms_surrogate_get_params(s.handle, None, ctypes.byref(n)))
+    if count_only:
+        return n.value
+    w = np.empty(n.value, dtype=np.float32)
+    _check(load().nms_surrogate_get_params(s.handle, _fp(w), ctypes.byref(n)))
+    return w
+
+
+def nms_surrogate_set_params(s, w):
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    _check(load().nms_surrogate_set_params(s.handle, _fp(w), w.size))
+
+
+def nms_surrogate_save(s, path):
+    _check(load().nms_surrogate_save(s.handle, str(path).encode()))
+
+
+def nms_surrogate_load(s, path):
+    _check(load().nms_surrogate_load(s.handle, str(path).encode()))
+
+
+def nms_surrogate_destroy(s):
+    s.close()
+
+
+def nms_plan_object_iq(plan, response, bin_edges):
+    rid = RESPONSE_ID[response] if isinstance(response, str) else int(response)
+    edges = np.ascontiguousarray(bin_edges, dtype=np.float64)
+    _check(load().nms_plan_object_iq(plan.handle, rid, len(edges) - 1, edges.ctypes.data_as(_D)))
+    plan._oiq_nbins = len(edges) - 1
+
+
+def nms_get_object_iq(plan, n_objects):
+    """(Iq [n_objects, nbins], counts [nbins], qmean [nbins]) as host arrays."""
+    nb = plan._oiq_nbins
+    I = np.empty((n_objects, nb), dtype=np.float64)
+    c = np.empty(nb, dtype=np.int64)
+    q = np.empty(nb, dtype=np.float64)
+    _check(load().nms_get_object_iq(plan.handle, _ptr(I), _ptr(c), _ptr(q), 0))
+    return I, c, q
+
+
 def nms_dsft_direct_noalloc(Y, Z, w, qy, qz, F, stream=None):
     """Direct sums into a caller-owned device tensor F [4, n_q, 2] without any
     device allocation by the library (all arguments are float64 CUDA tensors)."""
+    Y, Z, w, qy, qz = (_dev_in(t) for t in (Y, Z, w, qy, qz))
     _check(load().nms_dsft_direct_noalloc(Y.numel(), _ptr(Y), _ptr(Z), _ptr(w), qy.numel(), _ptr(qy), _ptr(qz),
                                           _ptr(F), ctypes.c_void_p(stream or 0)))
     return F

@@ -87,3 +87,13 @@ def test_invalid_arguments_are_reported_without_gpu():
         assert e.value.status == 3
         with pytest.raises(nms.NmsError):
             nms.nms_correlation([0.0, 1.0], [1.0, 1.0], [1.0])
+
+
+def test_binding_refuses_strided_buffers():
+    a = np.zeros((4, 6))[:, ::2]
+    with pytest.raises(ValueError):
+        nms._ptr(a)
+    f = np.asfortranarray(np.zeros((3, 5)))
+    with pytest.raises(ValueError):
+        nms._ptr(f)
+    assert nms._ptr(np.zeros((3, 5))).value is not None

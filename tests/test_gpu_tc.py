@@ -188,7 +188,8 @@ def test_tc_amplitudes_capture_in_cuda_graph():
         nms.nms_amplitudes(plan)
         graph.capture_end()
     for _ in range(2):
-        graph.replay()
-        side.synchronize()
+        with torch.cuda.stream(side):
+            graph.replay()                       # replays on the capturing stream
+        torch.cuda.synchronize()
         got = nms.nms_response(plan, "UNPOL", nms.PART_INTERFERENCE)
         assert np.array_equal(got, ref)

@@ -96,7 +96,13 @@ typedef struct {
     int64_t workspace_bytes; /* cap on tensor-path table workspace; 0 -> default */
     int32_t timing;          /* 1: record CUDA events around each stage (see
                                 nms_plan_stage_ms)                               */
-    int32_t reserved[7];
+    int32_t autotune;        /* tensor path: 1 = time candidate kc / work-list
+                                granularities on a probe of the cells at plan
+                                creation and keep the fastest whose amplitude
+                                error (vs the compensated direct sum) is
+                                <= 3e-7 of sum|w|; cached per shape and device
+                                (file $NMS_AUTOTUNE_CACHE if set)              */
+    int32_t reserved[6];
 } nms_options;
 
 /* Fill *opt with the defaults above. */
@@ -308,6 +314,13 @@ nms_status nms_surrogate_destroy(nms_surrogate_t s);
 nms_status nms_dsft_direct_noalloc(int64_t n_cells, const double* Y, const double* Z, const double* w,
                                    int64_t n_q, const double* qy, const double* qz, double* F,
                                    void* cuda_stream);
+
+/* The evaluation the plan settled on: precision = the nms_precision in use
+ * (AUTO resolved), kc_cells = cells per TMEM accumulation chunk and
+ * items_per_sm = work items per SM of each GEMM launch (tensor path; 0
+ * otherwise), after autotuning when it was requested.  Any pointer may be
+ * NULL. */
+nms_status nms_plan_info(nms_plan_t plan, int32_t* precision, int32_t* kc_cells, int32_t* items_per_sm);
 
 /* Release every device resource of the plan.  NULL is accepted. */
 nms_status nms_plan_destroy(nms_plan_t plan);

@@ -221,11 +221,12 @@ static int direct_splits(const Plan& p, int64_t ncell)
 }
 
 // Direct sum of cells [c0, c1) with positions cpos into out [4][npix][2].
-static nms_status direct_sum(Plan& p, const float4* cpos, int64_t c0, int64_t c1, double* out)
+nms_status direct_sum_range(Plan& p, const float4* cpos, int64_t c0, int64_t c1, double* out)
 {
     cudaStream_t s = p.stream;
     int splits = direct_splits(p, c1 - c0);
     p.timer.begin(ST_DIRECT);
+    // the tensor path uses this as its reference (compensated) in the autotuner
     NMS_CUDA_TRY(launch_direct(p, cpos, c0, c1, p.path != NMS_PREC_FP32_NAIVE, splits, s));
     p.timer.end(ST_DIRECT, 1);
     p.timer.begin(ST_REDUCE);
@@ -430,7 +431,7 @@ nms_status nms_amplitudes(nms_plan_t plan)
         NMS_CUDA_TRY(launch_prep(p, R, s));
         p.timer.end(ST_PREP, 1);
         if (!objects) {
-            nms_status st = direct_sum(p, p.d_cpos, 0, p.n_cells, p.d_F);
+            nms_status st = direct_sum_range(p, p.d_cpos, 0, p.n_cells, p.d_F);
             if (st) return st;
             p.timer.begin(ST_GACC);
             NMS_CUDA_TRY(launch_gacc(p, p.d_F, p.d_Gtot, s));
@@ -442,7 +443,7 @@ nms_status nms_amplitudes(nms_plan_t plan)
             for (int64_t k = 0; k < p.n_objects; ++k) {
                 int64_t a = p.h_off[k], b = p.h_off[k + 1];
                 if (b == a) continue;
-                nms_status st = direct_sum(p, p.d_cposl, a, b, p.d_F);
+                nms_status st = direct_sum_range(p, p.d_cposl, a, b, p.d_F);
                 if (st) return st;
                 double cy = 0.0, cz = 0.0;
                 if (!p.h_cen.empty()) {
@@ -719,6 +720,16 @@ nms_status nms_plan_stage_ms(nms_plan_t plan, double ms[8], int64_t launches[8],
     if (reset) {
         for (int i = 0; i < ST_COUNT; ++i) { p.timer.ms[i] = 0; p.timer.launches[i] = 0; }
     }
+    return NMS_OK;
+}
+
+nms_status nms_plan_info(nms_plan_t plan, int32_t* precision, int32_t* kc_cells, int32_t* items_per_sm)
+{
+    set_error("");
+    if (!plan) return fail(NMS_ERR_INVALID_ARG, "plan is NULL");
+    if (precision) *precision = plan->path;
+    if (kc_cells) *kc_cells = tc_tuned_kc_cells(*plan);
+    if (items_per_sm) *items_per_sm = tc_tuned_items_per_sm(*plan);
     return NMS_OK;
 }
 

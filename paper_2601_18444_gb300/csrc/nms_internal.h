@@ -136,10 +136,17 @@ cudaError_t launch_correlation(int nq, const double* q, const double* Iq, int nr
 // Tensor-core path (split-FP16 tcgen05 GEMM): schedule at plan creation,
 // all rotations/objects of one nms_amplitudes call, release.
 nms_status tc_setup(Plan& p);
+struct TcState;
+nms_status tc_autotune(Plan& p, TcState& t);
 nms_status tc_amplitudes(Plan& p, cudaStream_t s);
 void tc_release(Plan& p);
 
 int device_sm_count();
+// Direct sum of cells [c0, c1) (compensated unless the plan asked for the
+// naive phase) into out [4][npix][2] through the split partials.
+nms_status direct_sum_range(Plan& p, const float4* cpos, int64_t c0, int64_t c1, double* out);
+int tc_tuned_kc_cells(const Plan& p);
+int tc_tuned_items_per_sm(const Plan& p);
 cudaError_t launch_obj_bin(const double* F, int n_out, const int32_t* out_obj, const Plan& p, const int32_t* bin_of,
                            int nbins, int id, double* Iobj, cudaStream_t s);
 int64_t tc_object_count(const Plan& p);

@@ -15,9 +15,15 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <stdio.h>
+#include <stdlib.h>
+
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "nms_internal.h"
@@ -88,6 +94,7 @@ struct TcState {
     float2* d_qz = nullptr;
     double W[4] = {1, 1, 1, 1};
     int kcb = 2;
+    int items_per_sm = 8;        // work-list granularity of a GEMM launch
     bool objects = false;        // per-object amplitudes (dilute split) with shifts
     int R_b = 1;                 // rotations prepared per rotation batch
     int64_t tab_kb = 0;          // table capacity in k-blocks
@@ -130,13 +137,14 @@ static void free_schedule(Schedule& s)
     s = Schedule();
 }
 
-// Build the schedule of one rotation batch of n_rl rotations.
-static nms_status build_schedule(const Plan& p, const TcState& t, int n_rl, int out_cap, Schedule& S)
+struct Summand {
+    int rl, obj;        // rotation slot in the stacked arrays, object index
+    int64_t c0, c1;     // cells [c0, c1) of that rotation's arrays
+};
+
+// The summands of one rotation batch of n_rl rotations.
+static std::vector<Summand> plan_summands(const Plan& p, const TcState& t, int n_rl)
 {
-    struct Summand {
-        int rl, obj;
-        int64_t c0, c1;
-    };
     std::vector<Summand> sums;
     for (int rl = 0; rl < n_rl; ++rl) {
         if (t.objects) {
@@ -146,6 +154,13 @@ static nms_status build_schedule(const Plan& p, const TcState& t, int n_rl, int 
             sums.push_back({rl, 0, 0, p.n_cells});
         }
     }
+    return sums;
+}
+
+// Build the schedule of the given summands (n_rl rotation slots).
+static nms_status build_schedule(const Plan& p, const TcState& t, const std::vector<Summand>& sums, int n_rl,
+                                 int out_cap, Schedule& S)
+{
     S.n_rot_local = n_rl;
     S.n_out = (int)sums.size();
     const int sms = device_sm_count();
@@ -194,9 +209,10 @@ static nms_status build_schedule(const Plan& p, const TcState& t, int n_rl, int 
             int64_t nkb_chunk = 0;
             for (const Piece& pc : pieces) nkb_chunk += (pc.n + 31) / 32;
             ch.nkb = nkb_chunk;
-            // work items: about 8 per SM, never shorter than 2 TMEM chunks
+            // work items: about items_per_sm per SM, never shorter than 2 TMEM chunks
+            const int64_t ips = t.items_per_sm;
             const int64_t kb_per_item =
-                std::max<int64_t>(2 * t.kcb, (nkb_chunk * tiles + 8LL * sms - 1) / (8LL * sms));
+                std::max<int64_t>(2 * t.kcb, (nkb_chunk * tiles + ips * sms - 1) / (ips * sms));
             std::vector<HostItem> its;
             ch.red_off = (int64_t)reds.size();
             int slot = 0;
@@ -246,6 +262,226 @@ static nms_status build_schedule(const Plan& p, const TcState& t, int n_rl, int 
         NMS_CUDA_TRY(cudaMemcpy(S.d_reds, reds.data(), reds.size() * sizeof(HostRed), cudaMemcpyHostToDevice));
     }
     return NMS_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+__global__ void k_amp_maxerr(const double2* __restrict__ A, const double2* __restrict__ B, int64_t npix,
+                             unsigned int* __restrict__ err)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const double2 a = A[(int64_t)c * npix + p], b = B[(int64_t)c * npix + p];
+        const float d = (float)hypot(a.x - b.x, a.y - b.y);
+        atomicMax(&err[c], __float_as_uint(d));   // non-negative floats order as integers
+    }
+}
+
+__global__ void k_wabs_sum(const float4* __restrict__ cw, int64_t c0, int64_t c1, double* __restrict__ sums)
+{
+    __shared__ double red[4][256];
+    double a[4] = {0, 0, 0, 0};
+    for (int64_t j = c0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < c1; j += (int64_t)gridDim.x * blockDim.x) {
+        const float4 w = cw[j];
+        a[0] += fabsf(w.x);
+        a[1] += fabsf(w.y);
+        a[2] += fabsf(w.z);
+        a[3] += fabsf(w.w);
+    }
+    for (int c = 0; c < 4; ++c) red[c][threadIdx.x] = a[c];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 4; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 4; ++c) atomicAdd(&sums[c], red[c][0]);
+}
+
+struct TuneChoice {
+    int kcb, ips;
+};
+
+static std::mutex g_tune_mu;
+static std::map<std::string, TuneChoice> g_tune_cache;
+static bool g_tune_file_read = false;
+
+static void tune_file_read()
+{
+    if (g_tune_file_read) return;
+    g_tune_file_read = true;
+    const char* path = getenv("NMS_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    char key[256];
+    int a, b;
+    while (fscanf(f, "%255s %d %d", key, &a, &b) == 3)
+        if (a > 0 && b > 0) g_tune_cache[key] = {a, b};
+    fclose(f);
+}
+
+static void tune_file_append(const std::string& key, TuneChoice c)
+{
+    const char* path = getenv("NMS_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s %d %d\n", key.c_str(), c.kcb, c.ips);
+    fclose(f);
+}
+
+// Time candidate drain intervals and work-list granularities on a probe of
+// the cells and keep the fastest whose error is within the bound.
+nms_status tc_autotune(Plan& p, TcState& t)
+{
+    const int sms = device_sm_count();
+    // probe: up to 131072 cells of the largest summand under the first rotation
+    int64_t c0 = 0, c1 = p.n_cells;
+    if (t.objects) {
+        int64_t best = -1;
+        for (int64_t k = 0; k < p.n_objects; ++k)
+            if (p.h_off[k + 1] - p.h_off[k] > best) {
+                best = p.h_off[k + 1] - p.h_off[k];
+                c0 = p.h_off[k];
+                c1 = p.h_off[k + 1];
+            }
+    }
+    c1 = std::min<int64_t>({c1, c0 + 131072, c0 + t.tab_kb * 32});
+    const int64_t nprobe = c1 - c0;
+    char keybuf[256];
+    snprintf(keybuf, sizeof keybuf, "f16x3:%dx%d:cells%lld:sm%d", t.ny, t.nz, (long long)(64 - __builtin_clzll(nprobe)),
+             sms);
+    const std::string key(keybuf);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        tune_file_read();
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            t.kcb = it->second.kcb;
+            t.items_per_sm = it->second.ips;
+            return NMS_OK;
+        }
+    }
+    cudaStream_t s = p.stream;
+    const int64_t np = p.npix;
+    RotMat R;
+    memcpy(R.m, &p.h_rot[0], sizeof(R.m));
+    const bool timer_was_on = p.timer.on;
+    int64_t launches_before[ST_COUNT];
+    memcpy(launches_before, p.timer.launches, sizeof(launches_before));
+    p.timer.on = false;          // probe launches are not part of the plan's stage counts
+    // reference: the compensated direct sum over the probe cells
+    NMS_CUDA_TRY(launch_prep(p, R.m, s));
+    const float4* ref_pos = t.objects ? p.d_cposl : p.d_cpos;
+    nms_status st = direct_sum_range(p, ref_pos, c0, c1, p.d_F);
+    if (st) return st;
+    NMS_CUDA_TRY(launch_prep_rot(p, R, !t.objects, t.d_cpos_b, t.d_cw_b, s));
+    double* d_sw = nullptr;
+    unsigned int* d_err = nullptr;
+    double* d_Fp = nullptr;
+    NMS_CUDA_TRY(cudaMalloc(&d_sw, 4 * sizeof(double)));
+    NMS_CUDA_TRY(cudaMalloc(&d_err, 4 * sizeof(unsigned int)));
+    NMS_CUDA_TRY(cudaMalloc(&d_Fp, 8 * np * sizeof(double)));
+    NMS_CUDA_TRY(cudaMemsetAsync(d_sw, 0, 4 * sizeof(double), s));
+    k_wabs_sum<<<std::max(1, std::min(4 * sms, (int)((nprobe + 255) / 256))), 256, 0, s>>>(t.d_cw_b, c0, c1, d_sw);
+    NMS_CUDA_TRY(cudaGetLastError());
+    double wsum[4];
+    NMS_CUDA_TRY(cudaMemcpyAsync(wsum, d_sw, sizeof(wsum), cudaMemcpyDeviceToHost, s));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const float sc = tc_operand_scale();
+    const float wscale[4] = {(float)(sc / t.W[0]), (float)(sc / t.W[1]), (float)(sc / t.W[2]), (float)(sc / t.W[3])};
+    double scale[4];
+    for (int c = 0; c < 4; ++c) scale[c] = t.W[c] / ((double)sc * (double)sc);
+    const uint64_t limit = p.opt.max_spin > 0 ? (uint64_t)p.opt.max_spin * 1000ull : 4000000000ull;
+    const std::vector<Summand> probe = {{0, 0, c0, c1}};
+    TuneChoice best{1, 8};
+    float best_ms = 1e30f;
+    const int kcbs[3] = {1, 2, 4};
+    const int ipss[3] = {4, 8, 16};
+    double* saveP = t.d_P;
+    for (int kcb : kcbs)
+        for (int ips : ipss) {
+            t.kcb = kcb;
+            t.items_per_sm = ips;
+            Schedule S;
+            st = build_schedule(p, t, probe, 1, 1, S);
+            if (st) break;
+            double* P = nullptr;
+            cudaError_t ce = cudaMalloc(&P, (size_t)std::max<int64_t>(1, S.max_items) * 128 * 128 * sizeof(double));
+            if (ce != cudaSuccess) { free_schedule(S); st = cuda_fail(ce, "autotune partials"); break; }
+            float ms = 1e30f;
+            const Chunk& ch = S.batches[0].chunks[0];
+            for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {
+                ce = cudaMemsetAsync(d_Fp, 0, 8 * np * sizeof(double), s);
+                if (ce == cudaSuccess)
+                    ce = tc_launch_tables(t.d_cpos_b, t.d_cw_b, S.d_kb_cell0, S.d_kb_ncell, ch.nkb, t.d_qy, t.ny, t.d_qz,
+                                          t.nz, t.mtiles, t.ntiles, wscale, p.d_tab, s);
+                if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+                if (ce == cudaSuccess)
+                    ce = tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles, S.d_items, ch.n_items, ch.grid, kcb, P,
+                                        p.d_err, limit, s);
+                if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+                if (ce == cudaSuccess)
+                    ce = tc_launch_reduce(P, S.d_reds, ch.n_red, t.ny, t.nz, t.ntiles, scale, d_Fp, s);
+                if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+                float m = 0.f;
+                if (ce == cudaSuccess) cudaEventElapsedTime(&m, e0, e1);
+                ms = std::min(ms, m);
+            }
+            unsigned int herr[4] = {0, 0, 0, 0};
+            if (ce == cudaSuccess) ce = cudaMemsetAsync(d_err, 0, sizeof(herr), s);
+            if (ce == cudaSuccess) {
+                k_amp_maxerr<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(reinterpret_cast<const double2*>(d_Fp),
+                                                                        reinterpret_cast<const double2*>(p.d_F), np,
+                                                                        d_err);
+                ce = cudaGetLastError();
+            }
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(herr, d_err, sizeof(herr), cudaMemcpyDeviceToHost, s);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+            cudaFree(P);
+            free_schedule(S);
+            if (ce != cudaSuccess) { st = cuda_fail(ce, "autotune probe"); break; }
+            double err = 0.0;
+            for (int c = 0; c < 4; ++c)
+                if (wsum[c] > 0) err = std::max(err, (double)__builtin_bit_cast(float, herr[c]) / wsum[c]);
+            if (err <= 3e-7 && ms < best_ms) {
+                best_ms = ms;
+                best = {kcb, ips};
+            }
+        }
+    t.d_P = saveP;
+    p.timer.on = timer_was_on;
+    memcpy(p.timer.launches, launches_before, sizeof(launches_before));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_sw);
+    cudaFree(d_err);
+    cudaFree(d_Fp);
+    if (st) return st;
+    NMS_CUDA_TRY(cudaMemsetAsync(p.d_err, 0, sizeof(int32_t), s));
+    t.kcb = best.kcb;
+    t.items_per_sm = best.ips;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = best;
+    tune_file_append(key, best);
+    return NMS_OK;
+}
+
+int tc_tuned_kc_cells(const Plan& p)
+{
+    const TcState* t = (const TcState*)p.tc_state;
+    return t ? 32 * t->kcb : 0;
+}
+
+int tc_tuned_items_per_sm(const Plan& p)
+{
+    const TcState* t = (const TcState*)p.tc_state;
+    return t ? t->items_per_sm : 0;
 }
 
 nms_status tc_setup(Plan& p)
@@ -324,10 +560,13 @@ nms_status tc_setup(Plan& p)
     p.tab_bytes = (size_t)t->tab_kb * per_kb;
     NMS_CUDA_TRY(cudaMalloc(&p.d_tab, p.tab_bytes));
     // schedules: a full rotation batch and the remainder
-    if ((st = build_schedule(p, *t, t->R_b, out_cap, t->full))) return st;
+    if (p.opt.autotune) {
+        if ((st = tc_autotune(p, *t))) return st;
+    }
+    if ((st = build_schedule(p, *t, plan_summands(p, *t, t->R_b), t->R_b, out_cap, t->full))) return st;
     const int rem = p.n_rot % t->R_b;
     if (rem) {
-        if ((st = build_schedule(p, *t, rem, out_cap, t->last))) return st;
+        if ((st = build_schedule(p, *t, plan_summands(p, *t, rem), rem, out_cap, t->last))) return st;
     }
     const int64_t slots = std::max(t->full.max_items, t->last.max_items);
     NMS_CUDA_TRY(cudaMalloc(&t->d_P, (size_t)std::max<int64_t>(1, slots) * 128 * 128 * sizeof(double)));

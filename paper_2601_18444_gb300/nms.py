@@ -47,7 +47,7 @@ class nms_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("want_dilute", ctypes.c_int32), ("volume_V", ctypes.c_double),
                 ("b_H", ctypes.c_double), ("P", ctypes.c_double * 3), ("kc_cells", ctypes.c_int32),
                 ("split_k", ctypes.c_int32), ("max_spin", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
-                ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("timing", ctypes.c_int32), ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -84,6 +84,8 @@ SIGNATURES = {
     "nms_surrogate_load": (ctypes.c_int, [_V, ctypes.c_char_p]),
     "nms_surrogate_destroy": (ctypes.c_int, [_V]),
     "nms_dsft_direct_noalloc": (ctypes.c_int, [ctypes.c_int64, _V, _V, _V, ctypes.c_int64, _V, _V, _V, _V]),
+    "nms_plan_info": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_int32)]),
     "nms_plan_destroy": (ctypes.c_int, [_V]),
     "nms_last_error": (ctypes.c_char_p, []),
     "nms_version": (ctypes.c_char_p, []),
@@ -411,6 +413,13 @@ def nms_dsft_direct_noalloc(Y, Z, w, qy, qz, F, stream=None):
     _check(load().nms_dsft_direct_noalloc(Y.numel(), _ptr(Y), _ptr(Z), _ptr(w), qy.numel(), _ptr(qy), _ptr(qz),
                                           _ptr(F), ctypes.c_void_p(stream or 0)))
     return F
+
+
+def nms_plan_info(plan):
+    """dict(precision, kc_cells, items_per_sm) the plan settled on."""
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().nms_plan_info(plan.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"precision": a.value, "kc_cells": b.value, "items_per_sm": c.value}
 
 
 def nms_plan_destroy(plan):

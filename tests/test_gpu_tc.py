@@ -193,3 +193,19 @@ def test_tc_amplitudes_capture_in_cuda_graph():
         torch.cuda.synchronize()
         got = nms.nms_response(plan, "UNPOL", nms.PART_INTERFERENCE)
         assert np.array_equal(got, ref)
+
+
+def test_tc_autotune_picks_valid_config_and_caches(tmp_path, monkeypatch):
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("NMS_AUTOTUNE_CACHE", str(cache))
+    f = I.box_field(40, 40, 40, a=1.0, n_modes=4, seed=2, pores=False)     # coherent: a hard probe
+    kw = dict(kind="cartesian", n0=36, n1=40, lo0=-0.3, hi0=0.3, lo1=-0.3, hi1=0.3)
+    plan = run(f, kw, autotune=1)
+    info = nms.nms_plan_info(plan)
+    assert info["precision"] == TC and info["kc_cells"] in (32, 64, 128) and info["items_per_sm"] in (4, 8, 16)
+    g = og(kw)
+    F_ref = S.amplitudes(f, np.eye(3), g[0], g[1])
+    assert np.all(amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f)) <= AMP_TOL)
+    # a second plan of the same shape reuses the tuned choice
+    plan2 = run(f, kw, autotune=1)
+    assert nms.nms_plan_info(plan2) == info

@@ -222,6 +222,40 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
         : "memory");
 }
 
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// all threads of both CTAs of the cluster
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// 1D bulk copy delivered to the same shared-memory offset of every CTA in
+// mask, each CTA's mbarrier at the same offset receiving the bytes
+__device__ __forceinline__ void bulk_g2s_mc(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar, uint16_t mask)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+
+// arrive (once MMAs complete) on the mbarrier at this offset in every CTA of mask
+__device__ __forceinline__ void tc_commit_mc(uint64_t* bar, uint16_t mask)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -331,11 +365,18 @@ __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N)
 // TMEM, barriers and the stage ring stay live across items.  An item is one
 // 128 x 128 output tile over a k-block range of the chunk's tables; its
 // unscaled FP64 result goes to P[slot] (128 x 128, row-major).
+//
+// PAIR: CTAs run as clusters of two that share the A operand.  A pair item
+// covers the B tiles 2*nt and 2*nt + 1 of the same A tile and k-range; each
+// CTA copies one half (64 rows) of the A_hi and A_lo blocks and multicasts
+// it into both CTAs' stage, and loads its own B tile, so each SM pulls 48 KB
+// per stage instead of 64 KB.  A stage is refilled only after both CTAs'
+// MMAs consumed it (multicast commit onto both "empty" barriers).
 struct GemmItem {
-    int32_t mt, nt;       // A / B tile rows
+    int32_t mt, nt;       // A / B tile rows (PAIR: nt indexes B tile pairs)
     int32_t kb0, kb1;     // k-block range (within this chunk's tables)
-    int32_t slot;         // output slot in P
-    int32_t pad;
+    int32_t slot;         // output slot in P (PAIR: of cluster rank 0)
+    int32_t slot1;        // PAIR: output slot of cluster rank 1
 };
 
 struct GemmArgs {
@@ -352,6 +393,7 @@ struct GemmArgs {
     uint64_t limit_ns;
 };
 
+template <bool PAIR>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -366,11 +408,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    const int rank = PAIR ? (int)cluster_rank() : 0;
+    const int unit0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;   // first item of this CTA (pair)
+    const int units = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
             mbar_init(&bar_full[s], 1);
-            mbar_init(&bar_empty[s], 1);
+            mbar_init(&bar_empty[s], PAIR ? 2 : 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&bar_acc_full[b], 1);
@@ -388,6 +433,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
     }
     tc_fence_before();
     __syncthreads();
+    if (PAIR) cluster_sync();    // both CTAs' barriers initialised before any remote arrival
     tc_fence_after();
     const uint32_t taddr = s_taddr;
 
@@ -396,7 +442,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
         if (lane == 0) {
             int64_t i = 0;              // stage sequence number across items
             bool ok = true;
-            for (int it = blockIdx.x; it < g.n_items && ok; it += gridDim.x) {
+            for (int it = unit0; it < g.n_items && ok; it += units) {
                 const GemmItem item = g.items[it];
                 for (int kb = item.kb0; kb < item.kb1; ++kb) {
                     const int s = (int)(i % TC_STAGES);
@@ -410,9 +456,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
                     const uint32_t st = sbase + (uint32_t)s * TC_STAGE_BYTES;
                     mbar_arrive_expect_tx(&bar_full[s], TC_STAGE_BYTES);
                     const size_t ao = ((size_t)item.mt * g.nkb + kb) * TC_BLOCK_BYTES;
-                    const size_t bo = ((size_t)item.nt * g.nkb + kb) * TC_BLOCK_BYTES;
-                    bulk_g2s(st, g.A_hi + ao, TC_BLOCK_BYTES, &bar_full[s]);
-                    bulk_g2s(st + TC_BLOCK_BYTES, g.A_lo + ao, TC_BLOCK_BYTES, &bar_full[s]);
+                    const int nt = PAIR ? 2 * item.nt + rank : item.nt;
+                    const size_t bo = ((size_t)nt * g.nkb + kb) * TC_BLOCK_BYTES;
+                    if (PAIR) {
+                        const uint32_t h = (uint32_t)rank * (TC_BLOCK_BYTES / 2);
+                        bulk_g2s_mc(st + h, g.A_hi + ao + h, TC_BLOCK_BYTES / 2, &bar_full[s], (uint16_t)3);
+                        bulk_g2s_mc(st + TC_BLOCK_BYTES + h, g.A_lo + ao + h, TC_BLOCK_BYTES / 2, &bar_full[s],
+                                    (uint16_t)3);
+                    } else {
+                        bulk_g2s(st, g.A_hi + ao, TC_BLOCK_BYTES, &bar_full[s]);
+                        bulk_g2s(st + TC_BLOCK_BYTES, g.A_lo + ao, TC_BLOCK_BYTES, &bar_full[s]);
+                    }
                     bulk_g2s(st + 2 * TC_BLOCK_BYTES, g.B_hi + bo, TC_BLOCK_BYTES, &bar_full[s]);
                     bulk_g2s(st + 3 * TC_BLOCK_BYTES, g.B_lo + bo, TC_BLOCK_BYTES, &bar_full[s]);
                     ++i;
@@ -433,7 +487,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
             int64_t i = 0;              // stage sequence number
             int64_t c = 0;              // TMEM chunk sequence number
             bool ok = true;
-            for (int it = blockIdx.x; it < g.n_items && ok; it += gridDim.x) {
+            for (int it = unit0; it < g.n_items && ok; it += units) {
                 const GemmItem item = g.items[it];
                 for (int k0 = item.kb0; k0 < item.kb1 && ok; k0 += g.kcb, ++c) {
                     const int b = (int)(c & 1);
@@ -468,7 +522,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
                             tc_mma_f16(d1, al, bh, idesc, 1u);
                             first = false;
                         }
-                        tc_commit(&bar_empty[s]);
+                        if (PAIR) tc_commit_mc(&bar_empty[s], (uint16_t)3);
+                        else tc_commit(&bar_empty[s]);
                     }
                     if (!ok) break;
                     tc_commit(&bar_acc_full[b]);
@@ -489,7 +544,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
         const int colh = (e >> 2) * 32;            // column quarter
         int64_t c = 0;
         bool ok = true;
-        for (int it = blockIdx.x; it < g.n_items && ok; it += gridDim.x) {
+        for (int it = unit0; it < g.n_items && ok; it += units) {
             const GemmItem item = g.items[it];
             // two-float running sums, two columns per 64-bit register
             uint64_t hi[16], lo[16];
@@ -536,7 +591,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
             }
             if (!ok) break;
             // this item's tile, unscaled, FP64
-            double* out = g.P + (int64_t)item.slot * (TC_BM * TC_BN) + (int64_t)(quad * 32 + lane) * TC_BN + colh;
+            const int slot = (PAIR && rank) ? item.slot1 : item.slot;
+            double* out = g.P + (int64_t)slot * (TC_BM * TC_BN) + (int64_t)(quad * 32 + lane) * TC_BN + colh;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 double2 v = make_double2((double)f2_lane0(hi[i]) + (double)f2_lane0(lo[i]),
@@ -547,6 +603,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
     }
     tc_fence_before();
     __syncthreads();
+    if (PAIR) cluster_sync();    // no multicast or remote arrival can still target this CTA
     tc_fence_after();
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(512) : "memory");
@@ -612,12 +669,14 @@ cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, const int64_t
 }
 
 cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
-                           int grid, int kcb, double* P, int32_t* err, uint64_t limit_ns, cudaStream_t s)
+                           int grid, int kcb, double* P, int32_t* err, uint64_t limit_ns, bool pair, cudaStream_t s)
 {
     static bool attr = false;
     const int smem = TC_STAGES * TC_STAGE_BYTES + 1024;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_f16x3, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_f16x3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_gemm_f16x3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -633,8 +692,23 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
     ga.P = P;
     ga.err = err;
     ga.limit_ns = limit_ns;
-    k_gemm_f16x3<<<grid, TC_THREADS, smem, s>>>(ga);
-    return cudaGetLastError();
+    if (!pair) {
+        k_gemm_f16x3<false><<<grid, TC_THREADS, smem, s>>>(ga);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_gemm_f16x3<true>, ga);
 }
 
 cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, int ny, int nz, int ntiles,

@@ -35,7 +35,7 @@ cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, const int64_t
                              int64_t nkb, const float2* qy, int ny, const float2* qz, int nz, int mtiles, int ntiles,
                              const float wscale[4], void* tab, cudaStream_t s);
 cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
-                           int grid, int kcb, double* P, int32_t* err, uint64_t limit_ns, cudaStream_t s);
+                           int grid, int kcb, double* P, int32_t* err, uint64_t limit_ns, bool pair, cudaStream_t s);
 cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, int ny, int nz, int ntiles,
                              const double scale[4], double* F, cudaStream_t s);
 size_t tc_item_bytes();
@@ -52,7 +52,7 @@ cudaError_t launch_shift_batch(const double* F, int n_out, const float4* cyz, co
 namespace {
 
 struct HostItem {
-    int32_t mt, nt, kb0, kb1, slot, pad;
+    int32_t mt, nt, kb0, kb1, slot, slot1;   // pair mode: nt = B tile pair, slot1 = rank-1 slot
 };
 struct HostRed {
     int32_t slot_base, splits, out, pad;
@@ -95,6 +95,7 @@ struct TcState {
     double W[4] = {1, 1, 1, 1};
     int kcb = 2;
     int items_per_sm = 8;        // work-list granularity of a GEMM launch
+    bool pair = false;           // 2-CTA clusters sharing the A operand (even ntiles)
     bool objects = false;        // per-object amplitudes (dilute split) with shifts
     int R_b = 1;                 // rotations prepared per rotation batch
     int64_t tab_kb = 0;          // table capacity in k-blocks
@@ -226,12 +227,15 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
                 const int splits = (int)((nkb_p + kb_per_item - 1) / kb_per_item);
                 reds.push_back({slot, splits, pc.out, 0});
                 for (int mt = 0; mt < t.mtiles; ++mt)
-                    for (int nt = 0; nt < t.ntiles; ++nt)
+                    for (int nt = 0; nt < t.ntiles; nt += t.pair ? 2 : 1)
                         for (int sp = 0; sp < splits; ++sp) {
                             const int64_t a = kb + (nkb_p * sp) / splits;
                             const int64_t b = kb + (nkb_p * (sp + 1)) / splits;
-                            its.push_back({mt, nt, (int32_t)a, (int32_t)b, slot + (mt * t.ntiles + nt) * splits + sp,
-                                           0});
+                            const int s0 = slot + (mt * t.ntiles + nt) * splits + sp;
+                            if (t.pair)
+                                its.push_back({mt, nt / 2, (int32_t)a, (int32_t)b, s0, s0 + splits});
+                            else
+                                its.push_back({mt, nt, (int32_t)a, (int32_t)b, s0, 0});
                         }
                 slot += tiles * splits;
                 kb += nkb_p;
@@ -242,7 +246,7 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
                              [](const HostItem& x, const HostItem& y) { return (x.kb1 - x.kb0) > (y.kb1 - y.kb0); });
             ch.item_off = (int64_t)items.size();
             ch.n_items = (int)its.size();
-            ch.grid = std::min(ch.n_items, sms);
+            ch.grid = t.pair ? std::min(2 * ch.n_items, sms & ~1) : std::min(ch.n_items, sms);
             items.insert(items.end(), its.begin(), its.end());
             S.max_items = std::max<int64_t>(S.max_items, slot);
             ob.chunks.push_back(ch);
@@ -424,7 +428,7 @@ nms_status tc_autotune(Plan& p, TcState& t)
                 if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
                 if (ce == cudaSuccess)
                     ce = tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles, S.d_items, ch.n_items, ch.grid, kcb, P,
-                                        p.d_err, limit, s);
+                                        p.d_err, limit, t.pair, s);
                 if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
                 if (ce == cudaSuccess)
                     ce = tc_launch_reduce(P, S.d_reds, ch.n_red, t.ny, t.nz, t.ntiles, scale, d_Fp, s);
@@ -502,6 +506,7 @@ nms_status tc_setup(Plan& p)
     t->ntiles = (2 * t->nz + 127) / 128;
     t->kcb = p.opt.kc_cells > 0 ? std::max(1, p.opt.kc_cells / 32) : 2;
     t->objects = p.n_objects > 1 && p.opt.want_dilute;
+    t->pair = (t->ntiles % 2 == 0) && getenv("NMS_NO_CLUSTER") == nullptr;
     const int64_t n = p.n_cells;
     const int64_t np = p.npix;
 
@@ -625,7 +630,7 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
                 p.timer.begin(ST_GEMM);
                 NMS_CUDA_TRY(tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles,
                                             (const char*)S.d_items + ch.item_off * tc_item_bytes(), ch.n_items, ch.grid,
-                                            t.kcb, t.d_P, p.d_err, limit, s));
+                                            t.kcb, t.d_P, p.d_err, limit, t.pair, s));
                 p.timer.end(ST_GEMM, 1);
                 p.timer.begin(ST_REDUCE);
                 NMS_CUDA_TRY(tc_launch_reduce(t.d_P, (const char*)S.d_reds + ch.red_off * tc_red_bytes(), ch.n_red, t.ny,

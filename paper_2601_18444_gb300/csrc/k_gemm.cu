@@ -17,7 +17,12 @@
 // hi*lo + lo*hi (accumulator D1), a per-product error of ~3 * 2^-22 -- the
 // precision of TF32x3 at the FP16 tensor rate.  FP32 accumulation in TMEM is
 // limited to kc cells at a time: the accumulators are double-buffered and
-// drained by 16 epilogue warps into two-float (hi, lo) registers.
+// drained by 16 epilogue warps into two-float (hi, lo) registers.  Each
+// chunk partial D0 + D1 is added to lo with one FP32 add and (hi, lo) is
+// renormalised by TwoSum every TC_RENORM chunks, so lo holds at most a few
+// chunk partials and its rounding stays far below the TMEM accumulation
+// error (measured on the 4.19M-cell box: 2.0e-7 of sum|w| either way), at
+// less than half the drain arithmetic of a TwoSum per chunk.
 //
 // Phase tables use the two-float phase in turns t = q'.r (q' = q/2 pi) with
 // the exact reduction t - rint(t), then sincospif.  Tables are written in the
@@ -43,6 +48,12 @@ constexpr int TC_STAGES = 3;
 constexpr int TC_STAGE_BYTES = 4 * TC_BLOCK_BYTES;  // A_hi, A_lo, B_hi, B_lo
 constexpr int TC_THREADS = 576;     // warp 0 producer, warp 1 MMA, warps 2..17 epilogue
 constexpr int TC_EPI_WARPS = 16;    // 4 per TMEM lane quadrant, 32 accumulator columns each
+#ifndef TC_RENORM
+#define TC_RENORM 4                 // 0: TwoSum per chunk; G > 0: chunk partials add into lo, TwoSum every G chunks
+#endif
+#ifndef TC_DRAIN_W
+#define TC_DRAIN_W 4                // accumulator columns per tcgen05.ld in the drain (4, 8 or 16)
+#endif
 constexpr float TC_SCALE = 4096.0f; // operand scale 2^12
 
 // ------------------------------------------------------------------ tables
@@ -335,6 +346,14 @@ __device__ __forceinline__ uint64_t f2_pack(float lo_lane, float hi_lane)
 __device__ __forceinline__ float f2_lane0(uint64_t v) { return __uint_as_float((uint32_t)v); }
 __device__ __forceinline__ float f2_lane1(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
 
+template <int W>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v)
+{
+    if constexpr (W == 16) tmem_ld16(taddr, v);
+    else if constexpr (W == 8) tmem_ld8(taddr, v);
+    else tmem_ld4(taddr, v);
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // K-major, 128B-swizzled shared-memory matrix descriptor (tcgen05 format):
@@ -363,8 +382,11 @@ __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N)
 // ------------------------------------------------------------------ GEMM
 // Persistent: gridDim.x CTAs (one per SM) walk the work list round-robin;
 // TMEM, barriers and the stage ring stay live across items.  An item is one
-// 128 x 128 output tile over a k-block range of the chunk's tables; its
-// unscaled FP64 result goes to P[slot] (128 x 128, row-major).
+// 128 x 128 output tile over a k-block range of the chunk's tables.  Its
+// FP64 result either goes, unscaled, to the partial tile P[slot] (128 x 128,
+// row-major) for k_gemm_reduce, or -- when the item covers the whole k-range
+// of its output (slot < 0) -- is scaled and added straight into the
+// amplitudes F[-1 - slot] (no partial tile, no reduction pass).
 //
 // PAIR: CTAs run as clusters of two that share the A operand.  A pair item
 // covers the B tiles 2*nt and 2*nt + 1 of the same A tile and k-range; each
@@ -375,8 +397,8 @@ __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N)
 struct GemmItem {
     int32_t mt, nt;       // A / B tile rows (PAIR: nt indexes B tile pairs)
     int32_t kb0, kb1;     // k-block range (within this chunk's tables)
-    int32_t slot;         // output slot in P (PAIR: of cluster rank 0)
-    int32_t slot1;        // PAIR: output slot of cluster rank 1
+    int32_t slot;         // output slot in P (PAIR: of cluster rank 0); < 0: direct to output -1 - slot
+    int32_t slot1;        // PAIR: output slot of cluster rank 1 (direct: equal to slot)
 };
 
 struct GemmArgs {
@@ -389,6 +411,9 @@ struct GemmArgs {
     int n_items;
     int kcb;              // k-blocks per TMEM chunk (drain interval)
     double* P;            // [slots][128][128]
+    double* F;            // direct outputs: [out][4][ny*nz] complex (re, im)
+    int ny, nz;
+    double scale[4];      // direct outputs: per-channel scale of the unscaled sums
     int32_t* err;
     uint64_t limit_ns;
 };
@@ -567,37 +592,78 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
                 tc_fence_after();
                 const uint32_t base = taddr + ((uint32_t)(quad * 32) << 16) + (uint32_t)b * 256u + (uint32_t)colh;
 #pragma unroll
-                for (int cb = 0; cb < 8; ++cb) {
-                    float v0[4], v1[4];
-                    tmem_ld4(base + cb * 4, v0);
-                    tmem_ld4(base + 128 + cb * 4, v1);
+                for (int cb = 0; cb < 32 / TC_DRAIN_W; ++cb) {
+                    float v0[TC_DRAIN_W], v1[TC_DRAIN_W];
+                    tmem_ld<TC_DRAIN_W>(base + cb * TC_DRAIN_W, v0);
+                    tmem_ld<TC_DRAIN_W>(base + 128 + cb * TC_DRAIN_W, v1);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const int idx = cb * 2 + u;
-                        // x = D0 + D1; TwoSum(hi, x) -> (s, er); hi = s; lo += er
+                    for (int u = 0; u < TC_DRAIN_W / 2; ++u) {
+                        const int idx = cb * (TC_DRAIN_W / 2) + u;
                         const uint64_t x =
                             f2_add(f2_pack(v0[2 * u], v0[2 * u + 1]), f2_pack(v1[2 * u], v1[2 * u + 1]));
+#if TC_RENORM == 0
+                        // TwoSum(hi, x) -> (s, er); hi = s; lo += er
                         const uint64_t sm = f2_add(hi[idx], x);
                         const uint64_t bb = f2_sub(sm, hi[idx]);
                         const uint64_t er = f2_add(f2_sub(hi[idx], f2_sub(sm, bb)), f2_sub(x, bb));
                         hi[idx] = sm;
                         lo[idx] = f2_add(lo[idx], er);
+#else
+                        lo[idx] = f2_add(lo[idx], x);   // chunk partial into the low word
+#endif
                     }
                 }
+#if TC_RENORM > 0
+                // every TC_RENORM chunks: TwoSum(hi, lo) -> (hi, lo), so lo
+                // never holds more than a few chunk partials
+                if (((k0 - item.kb0) / g.kcb + 1) % TC_RENORM == 0) {
+#pragma unroll
+                    for (int idx = 0; idx < 16; ++idx) {
+                        const uint64_t sm = f2_add(hi[idx], lo[idx]);
+                        const uint64_t bb = f2_sub(sm, hi[idx]);
+                        lo[idx] = f2_add(f2_sub(hi[idx], f2_sub(sm, bb)), f2_sub(lo[idx], bb));
+                        hi[idx] = sm;
+                    }
+                }
+#endif
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bar_acc_empty[b]);
             }
             if (!ok) break;
-            // this item's tile, unscaled, FP64
             const int slot = (PAIR && rank) ? item.slot1 : item.slot;
-            double* out = g.P + (int64_t)slot * (TC_BM * TC_BN) + (int64_t)(quad * 32 + lane) * TC_BN + colh;
+            if (slot >= 0) {
+                // this item's tile, unscaled, FP64
+                double* out = g.P + (int64_t)slot * (TC_BM * TC_BN) + (int64_t)(quad * 32 + lane) * TC_BN + colh;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                double2 v = make_double2((double)f2_lane0(hi[i]) + (double)f2_lane0(lo[i]),
-                                         (double)f2_lane1(hi[i]) + (double)f2_lane1(lo[i]));
-                reinterpret_cast<double2*>(out)[i] = v;
+                for (int i = 0; i < 16; ++i) {
+                    double2 v = make_double2((double)f2_lane0(hi[i]) + (double)f2_lane0(lo[i]),
+                                             (double)f2_lane1(hi[i]) + (double)f2_lane1(lo[i]));
+                    reinterpret_cast<double2*>(out)[i] = v;
+                }
+            } else {
+                // the whole k-range of this output: row m = 4a + c, columns
+                // n = 2b + (re, im) for 16 consecutive b, added into F
+                const int m = item.mt * TC_BM + quad * 32 + lane;
+                const int a = m >> 2, ch = m & 3;
+                const int ntile = PAIR ? 2 * item.nt + rank : item.nt;
+                const int b0 = (ntile * TC_BN + colh) >> 1;
+                if (a < g.ny) {
+                    const int64_t npix = (int64_t)g.ny * g.nz;
+                    double2* o = reinterpret_cast<double2*>(g.F) + ((int64_t)(-1 - slot) * 4 + ch) * npix +
+                                 (int64_t)a * g.nz + b0;
+                    const double sc = ch == 0 ? g.scale[0] : ch == 1 ? g.scale[1] : ch == 2 ? g.scale[2] : g.scale[3];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        if (b0 + i < g.nz) {
+                            double2 v = o[i];
+                            v.x += sc * ((double)f2_lane0(hi[i]) + (double)f2_lane0(lo[i]));
+                            v.y += sc * ((double)f2_lane1(hi[i]) + (double)f2_lane1(lo[i]));
+                            o[i] = v;
+                        }
+                    }
+                }
             }
         }
     }
@@ -669,7 +735,8 @@ cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, const int64_t
 }
 
 cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
-                           int grid, int kcb, double* P, int32_t* err, uint64_t limit_ns, bool pair, cudaStream_t s)
+                           int grid, int kcb, double* P, double* F, int ny, int nz, const double scale[4], int32_t* err,
+                           uint64_t limit_ns, bool pair, cudaStream_t s)
 {
     static bool attr = false;
     const int smem = TC_STAGES * TC_STAGE_BYTES + 1024;
@@ -690,6 +757,10 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
     ga.n_items = n_items;
     ga.kcb = kcb;
     ga.P = P;
+    ga.F = F;
+    ga.ny = ny;
+    ga.nz = nz;
+    for (int c = 0; c < 4; ++c) ga.scale[c] = scale[c];
     ga.err = err;
     ga.limit_ns = limit_ns;
     if (!pair) {
@@ -717,6 +788,7 @@ cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, int n
     Scale4 sc;
     for (int c = 0; c < 4; ++c) sc.v[c] = scale[c];
     const int64_t n = (int64_t)n_red * 4 * ny * nz;
+    if (n == 0) return cudaSuccess;   // every item of the chunk wrote its output directly
     k_gemm_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, (const RedDesc*)reds, n_red, ny, nz, ntiles, sc, F);
     return cudaGetLastError();
 }

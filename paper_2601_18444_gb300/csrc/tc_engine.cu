@@ -35,7 +35,8 @@ cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, const int64_t
                              int64_t nkb, const float2* qy, int ny, const float2* qz, int nz, int mtiles, int ntiles,
                              const float wscale[4], void* tab, cudaStream_t s);
 cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
-                           int grid, int kcb, double* P, int32_t* err, uint64_t limit_ns, bool pair, cudaStream_t s);
+                           int grid, int kcb, double* P, double* F, int ny, int nz, const double scale[4], int32_t* err,
+                           uint64_t limit_ns, bool pair, cudaStream_t s);
 cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, int ny, int nz, int ntiles,
                              const double scale[4], double* F, cudaStream_t s);
 size_t tc_item_bytes();
@@ -225,6 +226,15 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
                     kb_ncell.push_back((int32_t)std::min<int64_t>(32, pc.n - 32 * i));
                 }
                 const int splits = (int)((nkb_p + kb_per_item - 1) / kb_per_item);
+                if (splits == 1) {
+                    // one item per tile spans the piece: the GEMM adds it into F directly
+                    const int32_t direct = -1 - pc.out;
+                    for (int mt = 0; mt < t.mtiles; ++mt)
+                        for (int nt = 0; nt < t.ntiles; nt += t.pair ? 2 : 1)
+                            its.push_back({mt, t.pair ? nt / 2 : nt, (int32_t)kb, (int32_t)(kb + nkb_p), direct, direct});
+                    kb += nkb_p;
+                    continue;
+                }
                 reds.push_back({slot, splits, pc.out, 0});
                 for (int mt = 0; mt < t.mtiles; ++mt)
                     for (int nt = 0; nt < t.ntiles; nt += t.pair ? 2 : 1)
@@ -428,7 +438,7 @@ nms_status tc_autotune(Plan& p, TcState& t)
                 if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
                 if (ce == cudaSuccess)
                     ce = tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles, S.d_items, ch.n_items, ch.grid, kcb, P,
-                                        p.d_err, limit, t.pair, s);
+                                        d_Fp, t.ny, t.nz, scale, p.d_err, limit, t.pair, s);
                 if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
                 if (ce == cudaSuccess)
                     ce = tc_launch_reduce(P, S.d_reds, ch.n_red, t.ny, t.nz, t.ntiles, scale, d_Fp, s);
@@ -630,12 +640,12 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
                 p.timer.begin(ST_GEMM);
                 NMS_CUDA_TRY(tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles,
                                             (const char*)S.d_items + ch.item_off * tc_item_bytes(), ch.n_items, ch.grid,
-                                            t.kcb, t.d_P, p.d_err, limit, t.pair, s));
+                                            t.kcb, t.d_P, t.d_Fb, t.ny, t.nz, scale, p.d_err, limit, t.pair, s));
                 p.timer.end(ST_GEMM, 1);
                 p.timer.begin(ST_REDUCE);
                 NMS_CUDA_TRY(tc_launch_reduce(t.d_P, (const char*)S.d_reds + ch.red_off * tc_red_bytes(), ch.n_red, t.ny,
                                               t.nz, t.ntiles, scale, t.d_Fb, s));
-                p.timer.end(ST_REDUCE, 1);
+                p.timer.end(ST_REDUCE, ch.n_red > 0 ? 1 : 0);
             }
             p.timer.begin(ST_GACC);
             int nl = 0;

@@ -155,6 +155,35 @@ def test_tc_ensemble_many_chunks_dilute_interference():
         assert np.max(np.abs(nms.nms_response(plan, k, nms.PART_INTERFERENCE) - parts[k][2])) <= tol + tol_dil, k
 
 
+def test_tc_mixed_object_sizes_direct_and_split_outputs():
+    # one large object (its tiles are split over many work items and reduced)
+    # beside many small ones (one item per tile, written straight into F), in
+    # the same table chunk; plus a two-rotation batch so outputs of both kinds
+    # interleave across rotation slots
+    rng = np.random.default_rng(21)
+    sizes = np.concatenate([[20000], rng.integers(1, 300, size=60)])
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(off[-1])
+    pos = rng.uniform(-6.0, 6.0, size=(n, 3))
+    f = I.Field(pos, rng.uniform(0.5, 1.5, n), rng.normal(size=n), rng.normal(size=(n, 3)), offsets=off,
+                centers=rng.uniform(-40.0, 40.0, size=(len(sizes), 3)), name="mixed_objects")
+    kw = dict(kind="cartesian", n0=40, n1=56, lo0=-1.5, hi0=1.5, lo1=-1.5, hi1=1.5)
+    Rs = I.random_rotations(2, seed=8)
+    plan = run(f, kw, rot=Rs, want_dilute=1)
+    g = og(kw)
+    ids = ("N", "M", "SF", "UNPOL")
+    acc = {k: [0, 0, 0] for k in ids}
+    for R in Rs:
+        parts = S.response_parts(f, R, g, ids=ids)
+        for k in ids:
+            for i in range(3):
+                acc[k][i] = acc[k][i] + parts[k][i] / len(Rs)
+    tol = 2 * resp_tol(f, rotations=Rs)
+    for k in ids:
+        for i, part in enumerate((nms.PART_TOTAL, nms.PART_DILUTE, nms.PART_INTERFERENCE)):
+            assert np.max(np.abs(nms.nms_response(plan, k, part) - acc[k][i])) <= tol, (k, part)
+
+
 def test_tc_rotation_batches_full_and_remainder():
     # 70 rotations: one batch of 64 prepared rotations and a remainder of 6
     f = I.ellipsoid_uniform((8.0, 5.0, 5.0), a=1.0, seed=2)

@@ -132,37 +132,67 @@ cudaError_t launch_gacc_batch(const double* F, int n_out, int64_t npix, double* 
     return cudaGetLastError();
 }
 
-// Ftot[out_rot[o]][c][p] += F_o[c][p] exp(-i (q_y cy_o + q_z cz_o)); the
-// phase is a two-float product in turns reduced exactly (as in the direct
-// sum).  Outputs are ordered by rotation, so each thread flushes its
-// two-float sums to FP64 once per rotation.
-__global__ void k_shift_batch(const double2* __restrict__ F, int n_out, const float4* __restrict__ cyz,
-                              const int32_t* __restrict__ out_rot, const float4* __restrict__ qturn, int64_t npix,
-                              double2* __restrict__ Ftot)
+// One pass over a batch of object amplitudes F_o (FP64 [n_out][4][npix]):
+//   G_dil[16][p]              += F_o F_o^dagger                  (dilute part)
+//   Ftot[out_rot[o]][c][p]    += F_o[c][p] exp(-i (q_y cy_o + q_z cz_o))
+// The shift phase is a two-float product in turns reduced exactly (as in the
+// direct sum).  Outputs are ordered by rotation, so each thread flushes its
+// two-float shifted sums to FP64 once per rotation.  The next output's
+// amplitudes are loaded while the current one is processed, so each thread
+// keeps two outputs' loads in flight.
+__device__ __forceinline__ void load_f(const double2* __restrict__ F, int64_t o, int64_t npix, int64_t p, double2* v)
+{
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[c] = F[(o * 4 + c) * npix + p];
+}
+
+__global__ void __launch_bounds__(128)
+k_dilute_shift_batch(const double2* __restrict__ F, int n_out, const float4* __restrict__ cyz,
+                     const int32_t* __restrict__ out_rot, const float4* __restrict__ qturn, int64_t npix,
+                     double* __restrict__ Gdil, double2* __restrict__ Ftot)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= npix) return;
+    if (p >= npix || n_out <= 0) return;
     const float4 q = qturn[p];
-    float hi[8], lo[8];
+    float gh[16], gl[16], th[8], tl[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) { hi[k] = 0.f; lo[k] = 0.f; }
-    int cur = n_out > 0 ? out_rot[0] : 0;
-    for (int o = 0; o <= n_out; ++o) {
-        const int r = o < n_out ? out_rot[o] : -1;
+    for (int k = 0; k < 16; ++k) { gh[k] = 0.f; gl[k] = 0.f; }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { th[k] = 0.f; tl[k] = 0.f; }
+    double2 nxt[4];
+    load_f(F, 0, npix, p, nxt);
+    int cur = out_rot[0];
+    for (int o = 0; o < n_out; ++o) {
+        float2 f[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) f[c] = make_float2((float)nxt[c].x, (float)nxt[c].y);
+        if (o + 1 < n_out) load_f(F, o + 1, npix, p, nxt);
+        const int r = out_rot[o];
         if (r != cur) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 double2* t = Ftot + ((int64_t)cur * 4 + c) * npix + p;
                 double2 v = *t;
-                v.x += (double)hi[2 * c] + (double)lo[2 * c];
-                v.y += (double)hi[2 * c + 1] + (double)lo[2 * c + 1];
+                v.x += (double)th[2 * c] + (double)tl[2 * c];
+                v.y += (double)th[2 * c + 1] + (double)tl[2 * c + 1];
                 *t = v;
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) { hi[k] = 0.f; lo[k] = 0.f; }
+            for (int k = 0; k < 8; ++k) { th[k] = 0.f; tl[k] = 0.f; }
             cur = r;
         }
-        if (o == n_out) break;
+        // dilute: F_o F_o^dagger
+#pragma unroll
+        for (int a = 0; a < 4; ++a) ts_acc(gh[a], gl[a], fmaf(f[a].x, f[a].x, f[a].y * f[a].y));
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = a + 1; b < 4; ++b) {
+                const int k = pair_idx(a, b);
+                ts_acc(gh[4 + 2 * k], gl[4 + 2 * k], fmaf(f[a].x, f[b].x, f[a].y * f[b].y));
+                ts_acc(gh[5 + 2 * k], gl[5 + 2 * k], fmaf(f[a].y, f[b].x, -f[a].x * f[b].y));
+            }
+        // total: F_o moved to its rotated centre
         const float4 cc = cyz[o];
         const float py = q.x * cc.x;
         const float ey = fmaf(q.x, cc.x, -py) + fmaf(q.x, cc.y, q.y * cc.x);
@@ -176,21 +206,28 @@ __global__ void k_shift_batch(const double2* __restrict__ F, int n_out, const fl
         sincospif(2.0f * t, &sn, &cs);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const double2 v = F[((int64_t)o * 4 + c) * npix + p];
-            const float fr = (float)v.x, fi = (float)v.y;
-            ts_acc(hi[2 * c], lo[2 * c], fmaf(fr, cs, fi * sn));
-            ts_acc(hi[2 * c + 1], lo[2 * c + 1], fmaf(fi, cs, -fr * sn));
+            ts_acc(th[2 * c], tl[2 * c], fmaf(f[c].x, cs, f[c].y * sn));
+            ts_acc(th[2 * c + 1], tl[2 * c + 1], fmaf(f[c].y, cs, -f[c].x * sn));
         }
     }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        double2* t = Ftot + ((int64_t)cur * 4 + c) * npix + p;
+        double2 v = *t;
+        v.x += (double)th[2 * c] + (double)tl[2 * c];
+        v.y += (double)th[2 * c + 1] + (double)tl[2 * c + 1];
+        *t = v;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) Gdil[(int64_t)k * npix + p] += (double)gh[k] + (double)gl[k];
 }
 
-cudaError_t launch_shift_batch(const double* F, int n_out, const float4* cyz, const int32_t* out_rot,
-                               const float4* qturn, int64_t npix, double* Ftot, cudaStream_t s)
+cudaError_t launch_dilute_shift_batch(const double* F, int n_out, const float4* cyz, const int32_t* out_rot,
+                                      const float4* qturn, int64_t npix, double* Gdil, double* Ftot, cudaStream_t s)
 {
     if (n_out <= 0) return cudaSuccess;
-    k_shift_batch<<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(reinterpret_cast<const double2*>(F), n_out, cyz,
-                                                                 out_rot, qturn, npix,
-                                                                 reinterpret_cast<double2*>(Ftot));
+    k_dilute_shift_batch<<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(
+        reinterpret_cast<const double2*>(F), n_out, cyz, out_rot, qturn, npix, Gdil, reinterpret_cast<double2*>(Ftot));
     return cudaGetLastError();
 }
 

@@ -66,12 +66,6 @@ __device__ __forceinline__ uint32_t swz_offset(int row, int k)
     return (uint32_t)row * 128u + ((uint32_t)(((k >> 3) ^ (row & 7))) << 4) + (uint32_t)(k & 7) * 2u;
 }
 
-__device__ __forceinline__ void split_h(float x, __half& h, __half& l)
-{
-    h = __float2half_rn(x);
-    l = __float2half_rn(x - __half2float(h));
-}
-
 __device__ __forceinline__ float turns_reduced(float2 q, float xh, float xl)
 {
     // two-float product q' * coordinate (turns) reduced to [-1/2, 1/2]
@@ -81,10 +75,20 @@ __device__ __forceinline__ float turns_reduced(float2 q, float xh, float xl)
     return (p - n) + e;
 }
 
-union H8 {
-    uint4 v;
-    __half h[8];
-};
+// (x0, x1) -> hi = fp16x2(x0, x1), lo = fp16x2(x0 - hi.x, x1 - hi.y); x0 in
+// the low half (the lower k index)
+__device__ __forceinline__ void split_h2(float x0, float x1, uint32_t& h, uint32_t& l)
+{
+    const __half2 hh = __floats2half2_rn(x0, x1);
+    const float2 f = __half22float2(hh);
+    const __half2 ll = __floats2half2_rn(x0 - f.x, x1 - f.y);
+    h = *reinterpret_cast<const uint32_t*>(&hh);
+    l = *reinterpret_cast<const uint32_t*>(&ll);
+}
+
+// fp16x2 (u, v) -> (v, -u), u in the low half: rounding to nearest is
+// odd-symmetric, so the split of a negated value is the negated split
+__device__ __forceinline__ uint32_t swap_neg_h2(uint32_t w) { return __byte_perm(w, 0, 0x1032) ^ 0x80000000u; }
 
 // A tables: block (mt, kb) holds rows m = mt*128 + 4*a_loc + c, a_loc < 32,
 // and k = 2 j_loc + p.  Thread (a_loc, chunk): 4 cells x 4 channels.
@@ -100,7 +104,9 @@ k_tables_a(const float4* __restrict__ cpos, const float4* __restrict__ cw, const
     const int a = mt * 32 + a_loc;
     const int64_t c0 = kb_cell0[kb];
     const int nc = kb_ncell[kb];
-    H8 hi[4], lo[4];
+    uint4 hi[4], lo[4];
+    uint32_t* hw = reinterpret_cast<uint32_t*>(hi);
+    uint32_t* lw = reinterpret_cast<uint32_t*>(lo);
     const bool arow = a < ny;
     const float2 q = arow ? qy[a] : make_float2(0.f, 0.f);
 #pragma unroll
@@ -116,22 +122,21 @@ k_tables_a(const float4* __restrict__ cpos, const float4* __restrict__ cw, const
         }
         const float wv[4] = {w.x * wscale.x, w.y * wscale.y, w.z * wscale.z, w.w * wscale.w};
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) {
-            split_h(wv[ch] * cs, hi[ch].h[2 * u], lo[ch].h[2 * u]);
-            split_h(wv[ch] * sn, hi[ch].h[2 * u + 1], lo[ch].h[2 * u + 1]);
-        }
+        for (int ch = 0; ch < 4; ++ch) split_h2(wv[ch] * cs, wv[ch] * sn, hw[4 * ch + u], lw[4 * ch + u]);
     }
     const size_t blk = ((size_t)mt * nkb + kb) * TC_BLOCK_BYTES;
 #pragma unroll
     for (int ch = 0; ch < 4; ++ch) {
         const int row = 4 * a_loc + ch;
         const uint32_t off = swz_offset(row, chunk * 8);
-        *reinterpret_cast<uint4*>(A_hi + blk + off) = hi[ch].v;
-        *reinterpret_cast<uint4*>(A_lo + blk + off) = lo[ch].v;
+        *reinterpret_cast<uint4*>(A_hi + blk + off) = hi[ch];
+        *reinterpret_cast<uint4*>(A_lo + blk + off) = lo[ch];
     }
 }
 
 // B tables: block (nt, kb) holds rows n = nt*128 + 2*b_loc + r, b_loc < 64.
+// Re row (cos, -sin), Im row (-sin, -cos): each Im word is the Re word
+// (c, -s) turned into (-s, -c).
 __global__ void __launch_bounds__(512)
 k_tables_b(const float4* __restrict__ cpos, const int64_t* __restrict__ kb_cell0, const int32_t* __restrict__ kb_ncell,
            const float2* __restrict__ qz, int nz, int64_t nkb, uint8_t* __restrict__ B_hi, uint8_t* __restrict__ B_lo)
@@ -145,7 +150,11 @@ k_tables_b(const float4* __restrict__ cpos, const int64_t* __restrict__ kb_cell0
     const int nc = kb_ncell[kb];
     const bool brow = b < nz;
     const float2 q = brow ? qz[b] : make_float2(0.f, 0.f);
-    H8 hr, lr, hi_, li_;
+    uint4 hr, lr, hi_, li_;
+    uint32_t* hrw = reinterpret_cast<uint32_t*>(&hr);
+    uint32_t* lrw = reinterpret_cast<uint32_t*>(&lr);
+    uint32_t* hiw = reinterpret_cast<uint32_t*>(&hi_);
+    uint32_t* liw = reinterpret_cast<uint32_t*>(&li_);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int jl = chunk * 4 + u;
@@ -155,20 +164,17 @@ k_tables_b(const float4* __restrict__ cpos, const int64_t* __restrict__ kb_cell0
             float t = turns_reduced(q, c.z, c.w);
             sincospif(2.0f * t, &sn, &cs);
         }
-        cs *= TC_SCALE;
-        sn *= TC_SCALE;
-        split_h(cs, hr.h[2 * u], lr.h[2 * u]);          // Re row: ( cos, -sin)
-        split_h(-sn, hr.h[2 * u + 1], lr.h[2 * u + 1]);
-        split_h(-sn, hi_.h[2 * u], li_.h[2 * u]);       // Im row: (-sin, -cos)
-        split_h(-cs, hi_.h[2 * u + 1], li_.h[2 * u + 1]);
+        split_h2(cs * TC_SCALE, -sn * TC_SCALE, hrw[u], lrw[u]);   // Re row: ( cos, -sin)
+        hiw[u] = swap_neg_h2(hrw[u]);                              // Im row: (-sin, -cos)
+        liw[u] = swap_neg_h2(lrw[u]);
     }
     const size_t blk = ((size_t)nt * nkb + kb) * TC_BLOCK_BYTES;
     const uint32_t o0 = swz_offset(2 * b_loc, chunk * 8);
     const uint32_t o1 = swz_offset(2 * b_loc + 1, chunk * 8);
-    *reinterpret_cast<uint4*>(B_hi + blk + o0) = hr.v;
-    *reinterpret_cast<uint4*>(B_lo + blk + o0) = lr.v;
-    *reinterpret_cast<uint4*>(B_hi + blk + o1) = hi_.v;
-    *reinterpret_cast<uint4*>(B_lo + blk + o1) = li_.v;
+    *reinterpret_cast<uint4*>(B_hi + blk + o0) = hr;
+    *reinterpret_cast<uint4*>(B_lo + blk + o0) = lr;
+    *reinterpret_cast<uint4*>(B_hi + blk + o1) = hi_;
+    *reinterpret_cast<uint4*>(B_lo + blk + o1) = li_;
 }
 
 // ------------------------------------------------------------------ PTX helpers

@@ -47,8 +47,8 @@ cudaError_t launch_prep_rot(const Plan& p, const RotMat& R, bool global, float4*
 cudaError_t launch_centres(int n_out, const int32_t* out_obj, const int32_t* out_rot, int rot0, const double* rot,
                            const double* cen, float4* cyz, cudaStream_t s);
 cudaError_t launch_gacc_batch(const double* F, int n_out, int64_t npix, double* G, cudaStream_t s);
-cudaError_t launch_shift_batch(const double* F, int n_out, const float4* cyz, const int32_t* out_rot,
-                               const float4* qturn, int64_t npix, double* Ftot, cudaStream_t s);
+cudaError_t launch_dilute_shift_batch(const double* F, int n_out, const float4* cyz, const int32_t* out_rot,
+                                      const float4* qturn, int64_t npix, double* Gdil, double* Ftot, cudaStream_t s);
 
 namespace {
 
@@ -657,10 +657,9 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
             if (t.objects) {
                 NMS_CUDA_TRY(launch_centres(ob.n_out, S.d_out_obj + ob.out0, S.d_out_rot + ob.out0, rb0, t.d_rot, t.d_cen,
                                             t.d_cyz, s));
-                NMS_CUDA_TRY(launch_gacc_batch(t.d_Fb, ob.n_out, np, p.d_Gdil, s));
-                NMS_CUDA_TRY(launch_shift_batch(t.d_Fb, ob.n_out, t.d_cyz, S.d_out_rot + ob.out0, p.d_qturn, np,
-                                                t.d_Ftot_b, s));
-                nl += 3;
+                NMS_CUDA_TRY(launch_dilute_shift_batch(t.d_Fb, ob.n_out, t.d_cyz, S.d_out_rot + ob.out0, p.d_qturn, np,
+                                                       p.d_Gdil, t.d_Ftot_b, s));
+                nl += 2;
             } else {
                 NMS_CUDA_TRY(launch_gacc_batch(t.d_Fb, ob.n_out, np, p.d_Gtot, s));
                 nl += 1;

@@ -109,18 +109,20 @@ k_tables_a(const float4* __restrict__ cpos, const float4* __restrict__ cw, const
     uint32_t* lw = reinterpret_cast<uint32_t*>(lo);
     const bool arow = a < ny;
     const float2 q = arow ? qy[a] : make_float2(0.f, 0.f);
+    // all loads of this thread's 4 cells first, then the arithmetic
+    float4 cp[4], w[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int jl = chunk * 4 + u;
-        float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-        float sn = 0.f, cs = 0.f;
-        if (arow && jl < nc) {
-            const float4 c = cpos[c0 + jl];
-            w = cw[c0 + jl];
-            float t = turns_reduced(q, c.x, c.y);
-            sincospif(2.0f * t, &sn, &cs);
-        }
-        const float wv[4] = {w.x * wscale.x, w.y * wscale.y, w.z * wscale.z, w.w * wscale.w};
+        const bool live = arow && jl < nc;
+        cp[u] = live ? cpos[c0 + jl] : make_float4(0.f, 0.f, 0.f, 0.f);
+        w[u] = live ? cw[c0 + jl] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        float sn, cs;
+        sincospif(2.0f * turns_reduced(q, cp[u].x, cp[u].y), &sn, &cs);
+        const float wv[4] = {w[u].x * wscale.x, w[u].y * wscale.y, w[u].z * wscale.z, w[u].w * wscale.w};
 #pragma unroll
         for (int ch = 0; ch < 4; ++ch) split_h2(wv[ch] * cs, wv[ch] * sn, hw[4 * ch + u], lw[4 * ch + u]);
     }
@@ -155,16 +157,23 @@ k_tables_b(const float4* __restrict__ cpos, const int64_t* __restrict__ kb_cell0
     uint32_t* lrw = reinterpret_cast<uint32_t*>(&lr);
     uint32_t* hiw = reinterpret_cast<uint32_t*>(&hi_);
     uint32_t* liw = reinterpret_cast<uint32_t*>(&li_);
+    // all loads of this thread's 4 cells first, then the arithmetic; padding
+    // cells and rows stay zero
+    float2 cz[4];
+    float live[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int jl = chunk * 4 + u;
-        float sn = 0.f, cs = 0.f;
-        if (brow && jl < nc) {
-            const float4 c = cpos[c0 + jl];
-            float t = turns_reduced(q, c.z, c.w);
-            sincospif(2.0f * t, &sn, &cs);
-        }
-        split_h2(cs * TC_SCALE, -sn * TC_SCALE, hrw[u], lrw[u]);   // Re row: ( cos, -sin)
+        const bool ok = brow && jl < nc;
+        const float4 c = ok ? cpos[c0 + jl] : make_float4(0.f, 0.f, 0.f, 0.f);
+        cz[u] = make_float2(c.z, c.w);
+        live[u] = ok ? TC_SCALE : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        float sn, cs;
+        sincospif(2.0f * turns_reduced(q, cz[u].x, cz[u].y), &sn, &cs);
+        split_h2(cs * live[u], -sn * live[u], hrw[u], lrw[u]);   // Re row: ( cos, -sin)
         hiw[u] = swap_neg_h2(hrw[u]);                              // Im row: (-sin, -cos)
         liw[u] = swap_neg_h2(lrw[u]);
     }

@@ -236,9 +236,12 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
                     continue;
                 }
                 reds.push_back({slot, splits, pc.out, 0});
-                for (int mt = 0; mt < t.mtiles; ++mt)
-                    for (int nt = 0; nt < t.ntiles; nt += t.pair ? 2 : 1)
-                        for (int sp = 0; sp < splits; ++sp) {
+                // k-range major: the CTAs of one wave share each k-range, so
+                // every table block comes from HBM about once and is reused
+                // by all tiles through L2
+                for (int sp = 0; sp < splits; ++sp)
+                    for (int mt = 0; mt < t.mtiles; ++mt)
+                        for (int nt = 0; nt < t.ntiles; nt += t.pair ? 2 : 1) {
                             const int64_t a = kb + (nkb_p * sp) / splits;
                             const int64_t b = kb + (nkb_p * (sp + 1)) / splits;
                             const int s0 = slot + (mt * t.ntiles + nt) * splits + sp;

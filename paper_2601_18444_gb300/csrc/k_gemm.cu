@@ -394,26 +394,132 @@ __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N)
     return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// tcgen05 instructions of a kernel all use one CTA-group size: CG = 2 for
+// the two-SM MMA, 1 otherwise.
+template <int CG>
+__device__ __forceinline__ void tc_alloc(uint32_t dst_smem, uint32_t ncols)
+{
+    if constexpr (CG == 2)
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                     : "memory");
+    else
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                     : "memory");
+}
+
+template <int CG>
+__device__ __forceinline__ void tc_relinquish()
+{
+    if constexpr (CG == 2) asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    else asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+template <int CG>
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    if constexpr (CG == 2)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+    else
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// arrive (once this thread's MMAs complete) on the mbarrier at this offset
+// in every CTA of mask (CG = 2: the CTA pair)
+template <int CG>
+__device__ __forceinline__ void tc_commit_to(uint64_t* bar, uint16_t mask)
+{
+    if constexpr (CG == 2)
+        asm volatile(
+            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                smem_u32(bar)),
+            "h"(mask)
+            : "memory");
+    else
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+                smem_u32(bar)),
+            "h"(mask)
+            : "memory");
+}
+
+__device__ __forceinline__ void tc_mma2_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// arrive on the mbarrier at this offset in CTA `cta` of the cluster
+__device__ __forceinline__ void mbar_arrive_cluster(uint64_t* bar, uint32_t cta)
+{
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(bar)), "r"(cta));
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+}
+
+// try_wait that also acquires what other CTAs of the cluster released
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(200000u)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
+                                                  volatile int* abort_flag)
+{
+    if (mbar_try_wait_cluster(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (true) {
+        if (mbar_try_wait_cluster(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > limit_ns) return false;
+    }
+}
+
 // ------------------------------------------------------------------ GEMM
 // Persistent: gridDim.x CTAs (one per SM) walk the work list round-robin;
 // TMEM, barriers and the stage ring stay live across items.  An item is one
-// 128 x 128 output tile over a k-block range of the chunk's tables.  Its
-// FP64 result either goes, unscaled, to the partial tile P[slot] (128 x 128,
-// row-major) for k_gemm_reduce, or -- when the item covers the whole k-range
-// of its output (slot < 0) -- is scaled and added straight into the
-// amplitudes F[-1 - slot] (no partial tile, no reduction pass).
+// 128 x 128 output tile per CTA over a k-block range of the chunk's tables.
+// Its FP64 result either goes, unscaled, to the partial tile P[slot]
+// (128 x 128, row-major) for k_gemm_reduce, or -- when the item covers the
+// whole k-range of its output (slot < 0) -- is scaled and added straight
+// into the amplitudes F[-1 - slot] (no partial tile, no reduction pass).
 //
-// PAIR: CTAs run as clusters of two that share the A operand.  A pair item
+// MODE 0: one CTA per item, tcgen05.mma.cta_group::1 with M = N = 128.
+//
+// MODE 1: clusters of two CTAs that share the A operand.  A pair item
 // covers the B tiles 2*nt and 2*nt + 1 of the same A tile and k-range; each
 // CTA copies one half (64 rows) of the A_hi and A_lo blocks and multicasts
-// it into both CTAs' stage, and loads its own B tile, so each SM pulls 48 KB
-// per stage instead of 64 KB.  A stage is refilled only after both CTAs'
-// MMAs consumed it (multicast commit onto both "empty" barriers).
+// it into both CTAs' stage, and loads its own B tile.  A stage is refilled
+// only after both CTAs' MMAs consumed it (multicast commit onto both
+// "empty" barriers).
+//
+// MODE 2: the two-SM MMA.  A pair item covers the A tiles 2*mt and 2*mt + 1
+// and one B tile: tcgen05.mma.cta_group::2 with M = 256, N = 128, issued by
+// the even CTA, reads the A tile of each CTA and the B tile split in two
+// 64-row halves, one in each CTA's shared memory, and accumulates each CTA's
+// 128 rows in its own TMEM.  A stage is 48 KB per SM instead of 64 KB and an
+// MMA reads 6 KB of shared memory per 128 x 128 x 16 product instead of 8 KB,
+// which is the resource the single-CTA form runs out of; the 48 KB stages
+// also make room for a fourth stage.  The odd CTA's MMA warp relays "stage
+// full" to the even CTA; the odd CTA's epilogue warps release accumulators
+// on the even CTA's barrier.
 struct GemmItem {
-    int32_t mt, nt;       // A / B tile rows (PAIR: nt indexes B tile pairs)
+    int32_t mt, nt;       // A / B tile rows (MODE 1: nt indexes B tile pairs, MODE 2: mt indexes A tile pairs)
     int32_t kb0, kb1;     // k-block range (within this chunk's tables)
-    int32_t slot;         // output slot in P (PAIR: of cluster rank 0); < 0: direct to output -1 - slot
-    int32_t slot1;        // PAIR: output slot of cluster rank 1 (direct: equal to slot)
+    int32_t slot;         // output slot in P (clusters: of rank 0); < 0: direct to output -1 - slot
+    int32_t slot1;        // clusters: output slot of rank 1 (direct: equal to slot)
 };
 
 struct GemmArgs {
@@ -433,12 +539,24 @@ struct GemmArgs {
     uint64_t limit_ns;
 };
 
-template <bool PAIR>
+template <int MODE>
+struct GemmCfg {
+    static constexpr int STAGES = MODE == 2 ? 4 : TC_STAGES;
+    static constexpr int STAGE_BYTES = MODE == 2 ? 3 * TC_BLOCK_BYTES : TC_STAGE_BYTES;
+    static constexpr int B_BYTES = MODE == 2 ? TC_BLOCK_BYTES / 2 : TC_BLOCK_BYTES;   // B piece per CTA
+    static constexpr int CG = MODE == 2 ? 2 : 1;
+};
+
+template <int MODE>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
 {
+    using C = GemmCfg<MODE>;
+    constexpr bool CLUSTER = MODE != 0;
+    constexpr int STG = C::STAGES;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bar_full[TC_STAGES];
-    __shared__ __align__(8) uint64_t bar_empty[TC_STAGES];
+    __shared__ __align__(8) uint64_t bar_full[STG];
+    __shared__ __align__(8) uint64_t bar_pfull[STG];    // MODE 2, even CTA: the odd CTA's stage is full
+    __shared__ __align__(8) uint64_t bar_empty[STG];
     __shared__ __align__(8) uint64_t bar_acc_full[2];
     __shared__ __align__(8) uint64_t bar_acc_empty[2];
     __shared__ __align__(8) uint64_t bar_final;
@@ -448,57 +566,58 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
-    const int rank = PAIR ? (int)cluster_rank() : 0;
-    const int unit0 = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;   // first item of this CTA (pair)
-    const int units = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+    const int rank = CLUSTER ? (int)cluster_rank() : 0;
+    const int unit0 = CLUSTER ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;   // first item of this CTA (pair)
+    const int units = CLUSTER ? (int)(gridDim.x >> 1) : (int)gridDim.x;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < STG; ++s) {
             mbar_init(&bar_full[s], 1);
-            mbar_init(&bar_empty[s], PAIR ? 2 : 1);
+            mbar_init(&bar_pfull[s], 1);
+            mbar_init(&bar_empty[s], MODE == 1 ? 2 : 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&bar_acc_full[b], 1);
-            mbar_init(&bar_acc_empty[b], TC_EPI_WARPS);
+            mbar_init(&bar_acc_empty[b], MODE == 2 ? 2 * TC_EPI_WARPS : TC_EPI_WARPS);
         }
         mbar_init(&bar_final, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
-                     "r"(512)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tc_alloc<C::CG>(smem_u32(&s_taddr), 512);
+        tc_relinquish<C::CG>();
     }
     tc_fence_before();
     __syncthreads();
-    if (PAIR) cluster_sync();    // both CTAs' barriers initialised before any remote arrival
+    if (CLUSTER) cluster_sync();    // both CTAs' barriers initialised before any remote arrival
     tc_fence_after();
     const uint32_t taddr = s_taddr;
 
     if (warp == 0) {
-        // ---------------- producer: bulk copies of the four operand blocks
+        // ---------------- producer: bulk copies of the operand blocks
         if (lane == 0) {
             int64_t i = 0;              // stage sequence number across items
             bool ok = true;
             for (int it = unit0; it < g.n_items && ok; it += units) {
                 const GemmItem item = g.items[it];
                 for (int kb = item.kb0; kb < item.kb1; ++kb) {
-                    const int s = (int)(i % TC_STAGES);
-                    const uint32_t par = (uint32_t)((i / TC_STAGES) & 1) ^ 1u;
+                    const int s = (int)(i % STG);
+                    const uint32_t par = (uint32_t)((i / STG) & 1) ^ 1u;
                     if (!mbar_wait(&bar_empty[s], par, g.limit_ns, &s_abort)) {
                         s_abort = 1;
                         atomicExch(g.err, 1);
                         ok = false;
                         break;
                     }
-                    const uint32_t st = sbase + (uint32_t)s * TC_STAGE_BYTES;
-                    mbar_arrive_expect_tx(&bar_full[s], TC_STAGE_BYTES);
-                    const size_t ao = ((size_t)item.mt * g.nkb + kb) * TC_BLOCK_BYTES;
-                    const int nt = PAIR ? 2 * item.nt + rank : item.nt;
-                    const size_t bo = ((size_t)nt * g.nkb + kb) * TC_BLOCK_BYTES;
-                    if (PAIR) {
+                    const uint32_t st = sbase + (uint32_t)s * C::STAGE_BYTES;
+                    mbar_arrive_expect_tx(&bar_full[s], C::STAGE_BYTES);
+                    const int mt = MODE == 2 ? 2 * item.mt + rank : item.mt;
+                    const int nt = MODE == 1 ? 2 * item.nt + rank : item.nt;
+                    const size_t ao = ((size_t)mt * g.nkb + kb) * TC_BLOCK_BYTES;
+                    // MODE 2: this CTA's 64-row half of the B block
+                    const size_t bo = ((size_t)nt * g.nkb + kb) * TC_BLOCK_BYTES + (MODE == 2 ? rank * C::B_BYTES : 0);
+                    if (MODE == 1) {
                         const uint32_t h = (uint32_t)rank * (TC_BLOCK_BYTES / 2);
                         bulk_g2s_mc(st + h, g.A_hi + ao + h, TC_BLOCK_BYTES / 2, &bar_full[s], (uint16_t)3);
                         bulk_g2s_mc(st + TC_BLOCK_BYTES + h, g.A_lo + ao + h, TC_BLOCK_BYTES / 2, &bar_full[s],
@@ -507,23 +626,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
                         bulk_g2s(st, g.A_hi + ao, TC_BLOCK_BYTES, &bar_full[s]);
                         bulk_g2s(st + TC_BLOCK_BYTES, g.A_lo + ao, TC_BLOCK_BYTES, &bar_full[s]);
                     }
-                    bulk_g2s(st + 2 * TC_BLOCK_BYTES, g.B_hi + bo, TC_BLOCK_BYTES, &bar_full[s]);
-                    bulk_g2s(st + 3 * TC_BLOCK_BYTES, g.B_lo + bo, TC_BLOCK_BYTES, &bar_full[s]);
+                    bulk_g2s(st + 2 * TC_BLOCK_BYTES, g.B_hi + bo, C::B_BYTES, &bar_full[s]);
+                    bulk_g2s(st + 2 * TC_BLOCK_BYTES + C::B_BYTES, g.B_lo + bo, C::B_BYTES, &bar_full[s]);
                     ++i;
                 }
             }
             // copies in flight must land before the CTA exits (bounded): only
-            // the last TC_STAGES issued stages can still be pending
-            for (int64_t k = (i > TC_STAGES ? i - TC_STAGES : 0); k < i; ++k) {
-                const int s = (int)(k % TC_STAGES);
-                const uint32_t par = (uint32_t)((k / TC_STAGES) & 1);
+            // the last STG issued stages can still be pending
+            for (int64_t k = (i > STG ? i - STG : 0); k < i; ++k) {
+                const int s = (int)(k % STG);
+                const uint32_t par = (uint32_t)((k / STG) & 1);
                 mbar_wait(&bar_full[s], par, g.limit_ns, &s_abort);
             }
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer (one thread)
-        if (lane == 0) {
-            const uint32_t idesc = idesc_f16_f32(TC_BM, TC_BN);
+        if (MODE == 2 && rank == 1) {
+            // ---------------- odd CTA: relay "stage full" to the MMA issuer
+            if (lane == 0) {
+                int64_t i = 0;
+                bool ok = true;
+                for (int it = unit0; it < g.n_items && ok; it += units) {
+                    const GemmItem item = g.items[it];
+                    for (int kb = item.kb0; kb < item.kb1; ++kb, ++i) {
+                        const int s = (int)(i % STG);
+                        const uint32_t par = (uint32_t)((i / STG) & 1);
+                        if (!mbar_wait(&bar_full[s], par, g.limit_ns, &s_abort)) {
+                            s_abort = 1;
+                            atomicExch(g.err, 4);
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_cluster(&bar_pfull[s], 0);
+                    }
+                }
+            }
+        } else if (lane == 0) {
+            // ---------------- MMA issuer (one thread; MODE 2: of the even CTA)
+            constexpr int MM = MODE == 2 ? 2 * TC_BM : TC_BM;
+            const uint32_t idesc = idesc_f16_f32(MM, TC_BN);
+            const uint32_t bofs = 2 * TC_BLOCK_BYTES;             // B_hi in the stage
+            const uint32_t lofs = bofs + C::B_BYTES;              // B_lo in the stage
             int64_t i = 0;              // stage sequence number
             int64_t c = 0;              // TMEM chunk sequence number
             bool ok = true;
@@ -532,7 +674,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
                 for (int k0 = item.kb0; k0 < item.kb1 && ok; k0 += g.kcb, ++c) {
                     const int b = (int)(c & 1);
                     const uint32_t apar = (uint32_t)((c >> 1) & 1) ^ 1u;
-                    if (!mbar_wait(&bar_acc_empty[b], apar, g.limit_ns, &s_abort)) {
+                    const bool oka = MODE == 2 ? mbar_wait_cluster(&bar_acc_empty[b], apar, g.limit_ns, &s_abort)
+                                               : mbar_wait(&bar_acc_empty[b], apar, g.limit_ns, &s_abort);
+                    if (!oka) {
                         ok = false;
                         break;
                     }
@@ -542,31 +686,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
                     const int k1 = min(item.kb1, k0 + g.kcb);
                     bool first = true;
                     for (int kb = k0; kb < k1; ++kb, ++i) {
-                        const int s = (int)(i % TC_STAGES);
-                        const uint32_t par = (uint32_t)((i / TC_STAGES) & 1);
-                        if (!mbar_wait(&bar_full[s], par, g.limit_ns, &s_abort)) {
+                        const int s = (int)(i % STG);
+                        const uint32_t par = (uint32_t)((i / STG) & 1);
+                        bool okf = mbar_wait(&bar_full[s], par, g.limit_ns, &s_abort);
+                        if (MODE == 2 && okf) okf = mbar_wait_cluster(&bar_pfull[s], par, g.limit_ns, &s_abort);
+                        if (!okf) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t st = sbase + (uint32_t)s * TC_STAGE_BYTES;
+                        const uint32_t st = sbase + (uint32_t)s * C::STAGE_BYTES;
 #pragma unroll
                         for (int k16 = 0; k16 < 4; ++k16) {
                             const uint64_t ah = sw128_desc(st + k16 * 32);
                             const uint64_t al = sw128_desc(st + TC_BLOCK_BYTES + k16 * 32);
-                            const uint64_t bh = sw128_desc(st + 2 * TC_BLOCK_BYTES + k16 * 32);
-                            const uint64_t bl = sw128_desc(st + 3 * TC_BLOCK_BYTES + k16 * 32);
+                            const uint64_t bh = sw128_desc(st + bofs + k16 * 32);
+                            const uint64_t bl = sw128_desc(st + lofs + k16 * 32);
                             const uint32_t acc = first ? 0u : 1u;
-                            tc_mma_f16(d0, ah, bh, idesc, acc);
-                            tc_mma_f16(d1, ah, bl, idesc, acc);
-                            tc_mma_f16(d1, al, bh, idesc, 1u);
+                            if (MODE == 2) {
+                                tc_mma2_f16(d0, ah, bh, idesc, acc);
+                                tc_mma2_f16(d1, ah, bl, idesc, acc);
+                                tc_mma2_f16(d1, al, bh, idesc, 1u);
+                            } else {
+                                tc_mma_f16(d0, ah, bh, idesc, acc);
+                                tc_mma_f16(d1, ah, bl, idesc, acc);
+                                tc_mma_f16(d1, al, bh, idesc, 1u);
+                            }
                             first = false;
                         }
-                        if (PAIR) tc_commit_mc(&bar_empty[s], (uint16_t)3);
-                        else tc_commit(&bar_empty[s]);
+                        if (MODE == 0) tc_commit(&bar_empty[s]);
+                        else tc_commit_to<C::CG>(&bar_empty[s], (uint16_t)3);
                     }
                     if (!ok) break;
-                    tc_commit(&bar_acc_full[b]);
+                    if (MODE == 2) tc_commit_to<2>(&bar_acc_full[b], (uint16_t)3);
+                    else tc_commit(&bar_acc_full[b]);
                 }
             }
             if (!ok) {
@@ -574,7 +727,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
                 atomicExch(g.err, 2);
             }
             // every MMA issued by this thread completes before TMEM is freed
-            tc_commit(&bar_final);
+            if (MODE == 2) tc_commit_to<2>(&bar_final, (uint16_t)1);
+            else tc_commit(&bar_final);
             mbar_wait(&bar_final, 0, g.limit_ns, &s_abort);
         }
     } else {
@@ -644,10 +798,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
 #endif
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&bar_acc_empty[b]);
+                if (lane == 0) {
+                    if (MODE == 2) mbar_arrive_cluster(&bar_acc_empty[b], 0);   // the MMA issuer's barrier
+                    else mbar_arrive(&bar_acc_empty[b]);
+                }
             }
             if (!ok) break;
-            const int slot = (PAIR && rank) ? item.slot1 : item.slot;
+            const int slot = (CLUSTER && rank) ? item.slot1 : item.slot;
             if (slot >= 0) {
                 // this item's tile, unscaled, FP64
                 double* out = g.P + (int64_t)slot * (TC_BM * TC_BN) + (int64_t)(quad * 32 + lane) * TC_BN + colh;
@@ -660,9 +817,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
             } else {
                 // the whole k-range of this output: row m = 4a + c, columns
                 // n = 2b + (re, im) for 16 consecutive b, added into F
-                const int m = item.mt * TC_BM + quad * 32 + lane;
+                const int mtile = MODE == 2 ? 2 * item.mt + rank : item.mt;
+                const int ntile = MODE == 1 ? 2 * item.nt + rank : item.nt;
+                const int m = mtile * TC_BM + quad * 32 + lane;
                 const int a = m >> 2, ch = m & 3;
-                const int ntile = PAIR ? 2 * item.nt + rank : item.nt;
                 const int b0 = (ntile * TC_BN + colh) >> 1;
                 if (a < g.ny) {
                     const int64_t npix = (int64_t)g.ny * g.nz;
@@ -684,11 +842,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
     }
     tc_fence_before();
     __syncthreads();
-    if (PAIR) cluster_sync();    // no multicast or remote arrival can still target this CTA
+    if (CLUSTER) cluster_sync();    // no multicast, MMA or remote arrival can still target this CTA
     tc_fence_after();
-    if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(512) : "memory");
-    }
+    if (warp == 1) tc_dealloc<C::CG>(taddr, 512);
 }
 
 // Reduction of item tiles into per-output amplitudes:
@@ -751,17 +907,22 @@ cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, const int64_t
 
 cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
                            int grid, int kcb, double* P, double* F, int ny, int nz, const double scale[4], int32_t* err,
-                           uint64_t limit_ns, bool pair, cudaStream_t s)
+                           uint64_t limit_ns, int mode, cudaStream_t s)
 {
+    static_assert(GemmCfg<0>::STAGES * GemmCfg<0>::STAGE_BYTES == GemmCfg<2>::STAGES * GemmCfg<2>::STAGE_BYTES,
+                  "one dynamic shared-memory size for every mode");
     static bool attr = false;
-    const int smem = TC_STAGES * TC_STAGE_BYTES + 1024;
+    const int smem = GemmCfg<0>::STAGES * GemmCfg<0>::STAGE_BYTES + 1024;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_f16x3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_f16x3<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_gemm_f16x3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            e = cudaFuncSetAttribute(k_gemm_f16x3<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_gemm_f16x3<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    if (mode < 0 || mode > 2 || (mode != 0 && (grid & 1))) return cudaErrorInvalidValue;
     GemmArgs ga;
     ga.A_hi = (const uint8_t*)tab;
     ga.A_lo = ga.A_hi + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
@@ -778,8 +939,8 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
     for (int c = 0; c < 4; ++c) ga.scale[c] = scale[c];
     ga.err = err;
     ga.limit_ns = limit_ns;
-    if (!pair) {
-        k_gemm_f16x3<false><<<grid, TC_THREADS, smem, s>>>(ga);
+    if (mode == 0) {
+        k_gemm_f16x3<0><<<grid, TC_THREADS, smem, s>>>(ga);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
@@ -794,7 +955,7 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_gemm_f16x3<true>, ga);
+    return mode == 1 ? cudaLaunchKernelEx(&cfg, k_gemm_f16x3<1>, ga) : cudaLaunchKernelEx(&cfg, k_gemm_f16x3<2>, ga);
 }
 
 cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, int ny, int nz, int ntiles,

@@ -36,7 +36,7 @@ cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, const int64_t
                              const float wscale[4], void* tab, cudaStream_t s);
 cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
                            int grid, int kcb, double* P, double* F, int ny, int nz, const double scale[4], int32_t* err,
-                           uint64_t limit_ns, bool pair, cudaStream_t s);
+                           uint64_t limit_ns, int mode, cudaStream_t s);
 cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, int ny, int nz, int ntiles,
                              const double scale[4], double* F, cudaStream_t s);
 size_t tc_item_bytes();
@@ -53,7 +53,7 @@ cudaError_t launch_dilute_shift_batch(const double* F, int n_out, const float4* 
 namespace {
 
 struct HostItem {
-    int32_t mt, nt, kb0, kb1, slot, slot1;   // pair mode: nt = B tile pair, slot1 = rank-1 slot
+    int32_t mt, nt, kb0, kb1, slot, slot1;   // clusters: mt (mode 2) or nt (mode 1) indexes a tile pair
 };
 struct HostRed {
     int32_t slot_base, splits, out, pad;
@@ -96,7 +96,7 @@ struct TcState {
     double W[4] = {1, 1, 1, 1};
     int kcb = 2;
     int items_per_sm = 8;        // work-list granularity of a GEMM launch
-    bool pair = false;           // 2-CTA clusters sharing the A operand (even ntiles)
+    int mode = 0;                // GEMM form: 0 one CTA, 1 pairs sharing A (even ntiles), 2 two-SM MMA (even mtiles)
     bool objects = false;        // per-object amplitudes (dilute split) with shifts
     int R_b = 1;                 // rotations prepared per rotation batch
     int64_t tab_kb = 0;          // table capacity in k-blocks
@@ -226,12 +226,14 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
                     kb_ncell.push_back((int32_t)std::min<int64_t>(32, pc.n - 32 * i));
                 }
                 const int splits = (int)((nkb_p + kb_per_item - 1) / kb_per_item);
+                // (mt, nt) of the first tile of a work unit and its step to the partner tile
+                const int mstep = t.mode == 2 ? 2 : 1, nstep = t.mode == 1 ? 2 : 1;
                 if (splits == 1) {
                     // one item per tile spans the piece: the GEMM adds it into F directly
                     const int32_t direct = -1 - pc.out;
-                    for (int mt = 0; mt < t.mtiles; ++mt)
-                        for (int nt = 0; nt < t.ntiles; nt += t.pair ? 2 : 1)
-                            its.push_back({mt, t.pair ? nt / 2 : nt, (int32_t)kb, (int32_t)(kb + nkb_p), direct, direct});
+                    for (int mt = 0; mt < t.mtiles; mt += mstep)
+                        for (int nt = 0; nt < t.ntiles; nt += nstep)
+                            its.push_back({mt / mstep, nt / nstep, (int32_t)kb, (int32_t)(kb + nkb_p), direct, direct});
                     kb += nkb_p;
                     continue;
                 }
@@ -240,15 +242,14 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
                 // every table block comes from HBM about once and is reused
                 // by all tiles through L2
                 for (int sp = 0; sp < splits; ++sp)
-                    for (int mt = 0; mt < t.mtiles; ++mt)
-                        for (int nt = 0; nt < t.ntiles; nt += t.pair ? 2 : 1) {
+                    for (int mt = 0; mt < t.mtiles; mt += mstep)
+                        for (int nt = 0; nt < t.ntiles; nt += nstep) {
                             const int64_t a = kb + (nkb_p * sp) / splits;
                             const int64_t b = kb + (nkb_p * (sp + 1)) / splits;
                             const int s0 = slot + (mt * t.ntiles + nt) * splits + sp;
-                            if (t.pair)
-                                its.push_back({mt, nt / 2, (int32_t)a, (int32_t)b, s0, s0 + splits});
-                            else
-                                its.push_back({mt, nt, (int32_t)a, (int32_t)b, s0, 0});
+                            // slot of the partner tile: next B tile (mode 1) or next A tile (mode 2)
+                            const int s1 = t.mode == 1 ? s0 + splits : t.mode == 2 ? s0 + t.ntiles * splits : 0;
+                            its.push_back({mt / mstep, nt / nstep, (int32_t)a, (int32_t)b, s0, s1});
                         }
                 slot += tiles * splits;
                 kb += nkb_p;
@@ -259,7 +260,7 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
                              [](const HostItem& x, const HostItem& y) { return (x.kb1 - x.kb0) > (y.kb1 - y.kb0); });
             ch.item_off = (int64_t)items.size();
             ch.n_items = (int)its.size();
-            ch.grid = t.pair ? std::min(2 * ch.n_items, sms & ~1) : std::min(ch.n_items, sms);
+            ch.grid = t.mode ? std::min(2 * ch.n_items, sms & ~1) : std::min(ch.n_items, sms);
             items.insert(items.end(), its.begin(), its.end());
             S.max_items = std::max<int64_t>(S.max_items, slot);
             ob.chunks.push_back(ch);
@@ -441,7 +442,7 @@ nms_status tc_autotune(Plan& p, TcState& t)
                 if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
                 if (ce == cudaSuccess)
                     ce = tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles, S.d_items, ch.n_items, ch.grid, kcb, P,
-                                        d_Fp, t.ny, t.nz, scale, p.d_err, limit, t.pair, s);
+                                        d_Fp, t.ny, t.nz, scale, p.d_err, limit, t.mode, s);
                 if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
                 if (ce == cudaSuccess)
                     ce = tc_launch_reduce(P, S.d_reds, ch.n_red, t.ny, t.nz, t.ntiles, scale, d_Fp, s);
@@ -519,7 +520,16 @@ nms_status tc_setup(Plan& p)
     t->ntiles = (2 * t->nz + 127) / 128;
     t->kcb = p.opt.kc_cells > 0 ? std::max(1, p.opt.kc_cells / 32) : 2;
     t->objects = p.n_objects > 1 && p.opt.want_dilute;
-    t->pair = (t->ntiles % 2 == 0) && getenv("NMS_NO_CLUSTER") == nullptr;
+    // CTA pairs sharing A where the B tiles pair up (the fastest form
+    // measured: the two-SM MMA reads less shared memory per product but its
+    // odd CTA's "stage full" relay costs more than that saves), else the
+    // two-SM MMA over A-tile pairs, else one CTA per tile.  NMS_GEMM_MODE = 0,
+    // 1 or 2 forces a form the grid allows (diagnostics, tests).
+    t->mode = (t->ntiles % 2 == 0) ? 1 : (t->mtiles % 2 == 0) ? 2 : 0;
+    if (const char* gm = getenv("NMS_GEMM_MODE")) {
+        const int want = atoi(gm);
+        if (want == 0 || (want == 1 && t->ntiles % 2 == 0) || (want == 2 && t->mtiles % 2 == 0)) t->mode = want;
+    }
     const int64_t n = p.n_cells;
     const int64_t np = p.npix;
 
@@ -643,7 +653,7 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
                 p.timer.begin(ST_GEMM);
                 NMS_CUDA_TRY(tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles,
                                             (const char*)S.d_items + ch.item_off * tc_item_bytes(), ch.n_items, ch.grid,
-                                            t.kcb, t.d_P, t.d_Fb, t.ny, t.nz, scale, p.d_err, limit, t.pair, s));
+                                            t.kcb, t.d_P, t.d_Fb, t.ny, t.nz, scale, p.d_err, limit, t.mode, s));
                 p.timer.end(ST_GEMM, 1);
                 p.timer.begin(ST_REDUCE);
                 NMS_CUDA_TRY(tc_launch_reduce(t.d_P, (const char*)S.d_reds + ch.red_off * tc_red_bytes(), ch.n_red, t.ny,

@@ -184,6 +184,36 @@ def test_tc_mixed_object_sizes_direct_and_split_outputs():
             assert np.max(np.abs(nms.nms_response(plan, k, part) - acc[k][i])) <= tol, (k, part)
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_tc_gemm_forms_agree_with_oracle(mode, monkeypatch):
+    # the three GEMM forms (one CTA; CTA pairs sharing A; the two-SM MMA over
+    # A-tile pairs) on a grid with even tile counts in both dimensions, with
+    # split-and-reduced items (one large object) and direct items (small ones)
+    monkeypatch.setenv("NMS_GEMM_MODE", str(mode))
+    rng = np.random.default_rng(30 + mode)
+    sizes = np.concatenate([[12000], rng.integers(1, 200, size=20)])
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(off[-1])
+    f = I.Field(rng.uniform(-5.0, 5.0, size=(n, 3)), rng.uniform(0.5, 1.5, n), rng.normal(size=n),
+                rng.normal(size=(n, 3)), offsets=off, centers=rng.uniform(-30.0, 30.0, size=(len(sizes), 3)),
+                name="mixed_objects")
+    kw = dict(kind="cartesian", n0=61, n1=117, lo0=-1.5, hi0=1.4, lo1=-1.3, hi1=1.5)   # 2 A tiles, 2 B tiles
+    plan = run(f, kw, want_dilute=1)
+    g = og(kw)
+    ids = ("N", "M", "UNPOL")
+    parts = S.response_parts(f, np.eye(3), g, ids=ids)
+    tol = 2 * resp_tol(f)
+    for k in ids:
+        for i, part in enumerate((nms.PART_TOTAL, nms.PART_DILUTE, nms.PART_INTERFERENCE)):
+            assert np.max(np.abs(nms.nms_response(plan, k, part) - parts[k][i])) <= tol, (k, part)
+    # one object alone: amplitudes against the oracle element by element
+    f1 = I.Field(f.pos[:12000], f.vol[:12000], f.nuc[:12000], f.mag[:12000], name="large_object")
+    plan1 = run(f1, kw)
+    F_ref = S.amplitudes(f1, np.eye(3), g[0], g[1])
+    err = amp_error(nms.nms_get_amplitudes(plan1), F_ref, weight_sums(f1))
+    assert np.all(err <= AMP_TOL), err
+
+
 def test_tc_rotation_batches_full_and_remainder():
     # 70 rotations: one batch of 64 prepared rotations and a remainder of 6
     f = I.ellipsoid_uniform((8.0, 5.0, 5.0), a=1.0, seed=2)

@@ -40,6 +40,11 @@ METRIC = "cell·q-point terms/s of SANS Fourier sum: tensor-core split vs FP32 a
 DIRECT_OPS_PER_TERM = 57
 # Executed tensor flops per term of the split-FP16 GEMM: 3 products x 32 flops.
 TC_FLOPS_PER_TERM = 96
+# DRAM bytes (read + write) the GEMM moves per byte of phase tables it
+# consumes, from an ncu capture of one launch on the 64x64x64 box (512^2
+# detector); the box workloads scale it by their own table bytes per launch.
+TC_DRAM_PER_TABLE_BYTE = 1.311   # 8.446 GB for 6.442 GB of tables
+TC_TRAFFIC_WORKLOADS = ("box", "box64")
 
 
 def load_peaks():
@@ -329,9 +334,12 @@ def main():
         k_ms = stage["gemm"][0] / args.steps
         achieved = terms * TC_FLOPS_PER_TERM / (k_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops", 1900.0)
+        traffic = None
+        if TC_DRAM_PER_TABLE_BYTE and args.workload in TC_TRAFFIC_WORKLOADS:
+            traffic = TC_DRAM_PER_TABLE_BYTE * table_bytes(field, grid_kw, n_rot) / (stage["gemm"][1] / args.steps)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_gemm_f16x3",
-                "peak_source": f"{peak_src} bf16 dense (f16 same rate)"}
+                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+                "kernel": "k_gemm_f16x3", "peak_source": f"{peak_src} bf16 dense (f16 same rate)"}
     else:
         k_ms = stage["direct"][0] / args.steps
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -399,6 +407,18 @@ def main():
                 "clocks": clocks, "amp_err_vs_oracle": err}
         print(json.dumps(line), flush=True)
     return 0
+
+
+def table_bytes(field, grid_kw, n_rot):
+    """Bytes of split-FP16 phase tables one step writes and the GEMM reads:
+    per 32-cell k-block, (A tiles + B tiles) x (hi, lo) x 16 KB."""
+    mt = -(-4 * grid_kw["n0"] // 128)
+    nt = -(-2 * grid_kw["n1"] // 128)
+    if field.offsets is not None and len(field.offsets) > 2:
+        nkb = int(sum(-(-(b - a) // 32) for a, b in zip(field.offsets[:-1], field.offsets[1:])))
+    else:
+        nkb = -(-field.n // 32)
+    return float(nkb * n_rot * (mt + nt) * 2 * 16384)
 
 
 def plan_path_is_tc(stage):

@@ -96,12 +96,14 @@ typedef struct {
     int64_t workspace_bytes; /* cap on tensor-path table workspace; 0 -> default */
     int32_t timing;          /* 1: record CUDA events around each stage (see
                                 nms_plan_stage_ms)                               */
-    int32_t autotune;        /* tensor path: 1 = time candidate kc / work-list
-                                granularities on a probe of the cells at plan
-                                creation and keep the fastest whose amplitude
-                                error (vs the compensated direct sum) is
-                                <= 3e-7 of sum|w|; cached per shape and device
-                                (file $NMS_AUTOTUNE_CACHE if set)              */
+    int32_t autotune;        /* tensor path: 1 = time candidate GEMM forms
+                                (one CTA, CTA pairs sharing A, two-SM MMA),
+                                kc and work-list granularities on a probe of
+                                the cells at plan creation and keep the
+                                fastest whose amplitude error (vs the
+                                compensated direct sum) is <= 3e-7 of sum|w|;
+                                cached per shape and device (file
+                                $NMS_AUTOTUNE_CACHE if set)                    */
     int32_t reserved[6];
 } nms_options;
 

@@ -97,6 +97,7 @@ struct TcState {
     int kcb = 2;
     int items_per_sm = 8;        // work-list granularity of a GEMM launch
     int mode = 0;                // GEMM form: 0 one CTA, 1 pairs sharing A (even ntiles), 2 two-SM MMA (even mtiles)
+    bool mode_forced = false;    // set by NMS_GEMM_MODE: the autotuner keeps it
     bool objects = false;        // per-object amplitudes (dilute split) with shifts
     int R_b = 1;                 // rotations prepared per rotation batch
     int64_t tab_kb = 0;          // table capacity in k-blocks
@@ -319,7 +320,7 @@ __global__ void k_wabs_sum(const float4* __restrict__ cw, int64_t c0, int64_t c1
 }
 
 struct TuneChoice {
-    int kcb, ips;
+    int kcb, ips, mode;
 };
 
 static std::mutex g_tune_mu;
@@ -335,9 +336,9 @@ static void tune_file_read()
     FILE* f = fopen(path, "r");
     if (!f) return;
     char key[256];
-    int a, b;
-    while (fscanf(f, "%255s %d %d", key, &a, &b) == 3)
-        if (a > 0 && b > 0) g_tune_cache[key] = {a, b};
+    int a, b, m;
+    while (fscanf(f, "%255s %d %d %d", key, &a, &b, &m) == 4)
+        if (a > 0 && b > 0 && m >= 0 && m <= 2) g_tune_cache[key] = {a, b, m};
     fclose(f);
 }
 
@@ -347,12 +348,12 @@ static void tune_file_append(const std::string& key, TuneChoice c)
     if (!path) return;
     FILE* f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "%s %d %d\n", key.c_str(), c.kcb, c.ips);
+    fprintf(f, "%s %d %d %d\n", key.c_str(), c.kcb, c.ips, c.mode);
     fclose(f);
 }
 
-// Time candidate drain intervals and work-list granularities on a probe of
-// the cells and keep the fastest whose error is within the bound.
+// Time candidate GEMM forms, drain intervals and work-list granularities on
+// a probe of the cells and keep the fastest whose error is within the bound.
 nms_status tc_autotune(Plan& p, TcState& t)
 {
     const int sms = device_sm_count();
@@ -370,8 +371,8 @@ nms_status tc_autotune(Plan& p, TcState& t)
     c1 = std::min<int64_t>({c1, c0 + 131072, c0 + t.tab_kb * 32});
     const int64_t nprobe = c1 - c0;
     char keybuf[256];
-    snprintf(keybuf, sizeof keybuf, "f16x3:%dx%d:cells%lld:sm%d", t.ny, t.nz, (long long)(64 - __builtin_clzll(nprobe)),
-             sms);
+    snprintf(keybuf, sizeof keybuf, "f16x3:%dx%d:cells%lld:sm%d:forms%d", t.ny, t.nz,
+             (long long)(64 - __builtin_clzll(nprobe)), sms, t.mode_forced ? t.mode : -1);
     const std::string key(keybuf);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -380,6 +381,7 @@ nms_status tc_autotune(Plan& p, TcState& t)
         if (it != g_tune_cache.end()) {
             t.kcb = it->second.kcb;
             t.items_per_sm = it->second.ips;
+            t.mode = it->second.mode;
             return NMS_OK;
         }
     }
@@ -417,61 +419,72 @@ nms_status tc_autotune(Plan& p, TcState& t)
     for (int c = 0; c < 4; ++c) scale[c] = t.W[c] / ((double)sc * (double)sc);
     const uint64_t limit = p.opt.max_spin > 0 ? (uint64_t)p.opt.max_spin * 1000ull : 4000000000ull;
     const std::vector<Summand> probe = {{0, 0, c0, c1}};
-    TuneChoice best{1, 8};
+    const int mode0 = t.mode;
+    TuneChoice best{2, 8, mode0};
     float best_ms = 1e30f;
     const int kcbs[3] = {1, 2, 4};
     const int ipss[3] = {4, 8, 16};
+    std::vector<int> modes;
+    for (int m = 0; m < 3; ++m)
+        if (t.mode_forced ? m == mode0
+                          : (m == 0 || (m == 1 && t.ntiles % 2 == 0) || (m == 2 && t.mtiles % 2 == 0)))
+            modes.push_back(m);
     double* saveP = t.d_P;
-    for (int kcb : kcbs)
-        for (int ips : ipss) {
-            t.kcb = kcb;
-            t.items_per_sm = ips;
-            Schedule S;
-            st = build_schedule(p, t, probe, 1, 1, S);
-            if (st) break;
-            double* P = nullptr;
-            cudaError_t ce = cudaMalloc(&P, (size_t)std::max<int64_t>(1, S.max_items) * 128 * 128 * sizeof(double));
-            if (ce != cudaSuccess) { free_schedule(S); st = cuda_fail(ce, "autotune partials"); break; }
-            float ms = 1e30f;
-            const Chunk& ch = S.batches[0].chunks[0];
-            for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {
-                ce = cudaMemsetAsync(d_Fp, 0, 8 * np * sizeof(double), s);
-                if (ce == cudaSuccess)
-                    ce = tc_launch_tables(t.d_cpos_b, t.d_cw_b, S.d_kb_cell0, S.d_kb_ncell, ch.nkb, t.d_qy, t.ny, t.d_qz,
-                                          t.nz, t.mtiles, t.ntiles, wscale, p.d_tab, s);
-                if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
-                if (ce == cudaSuccess)
-                    ce = tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles, S.d_items, ch.n_items, ch.grid, kcb, P,
-                                        d_Fp, t.ny, t.nz, scale, p.d_err, limit, t.mode, s);
-                if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
-                if (ce == cudaSuccess)
-                    ce = tc_launch_reduce(P, S.d_reds, ch.n_red, t.ny, t.nz, t.ntiles, scale, d_Fp, s);
-                if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
-                float m = 0.f;
-                if (ce == cudaSuccess) cudaEventElapsedTime(&m, e0, e1);
-                ms = std::min(ms, m);
-            }
-            unsigned int herr[4] = {0, 0, 0, 0};
-            if (ce == cudaSuccess) ce = cudaMemsetAsync(d_err, 0, sizeof(herr), s);
-            if (ce == cudaSuccess) {
-                k_amp_maxerr<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(reinterpret_cast<const double2*>(d_Fp),
-                                                                        reinterpret_cast<const double2*>(p.d_F), np,
-                                                                        d_err);
-                ce = cudaGetLastError();
-            }
-            if (ce == cudaSuccess) ce = cudaMemcpyAsync(herr, d_err, sizeof(herr), cudaMemcpyDeviceToHost, s);
-            if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-            cudaFree(P);
-            free_schedule(S);
-            if (ce != cudaSuccess) { st = cuda_fail(ce, "autotune probe"); break; }
-            double err = 0.0;
-            for (int c = 0; c < 4; ++c)
-                if (wsum[c] > 0) err = std::max(err, (double)__builtin_bit_cast(float, herr[c]) / wsum[c]);
-            if (err <= 3e-7 && ms < best_ms) {
-                best_ms = ms;
-                best = {kcb, ips};
-            }
+    std::vector<TuneChoice> cand;
+    for (int mode : modes)
+        for (int kcb : kcbs)
+            for (int ips : ipss) cand.push_back({kcb, ips, mode});
+    for (const TuneChoice& cd : cand) {
+        const int mode = cd.mode, kcb = cd.kcb, ips = cd.ips;
+        t.mode = mode;
+        t.kcb = kcb;
+        t.items_per_sm = ips;
+        Schedule S;
+        st = build_schedule(p, t, probe, 1, 1, S);
+        if (st) break;
+        double* P = nullptr;
+        cudaError_t ce = cudaMalloc(&P, (size_t)std::max<int64_t>(1, S.max_items) * 128 * 128 * sizeof(double));
+        if (ce != cudaSuccess) { free_schedule(S); st = cuda_fail(ce, "autotune partials"); break; }
+        float ms = 1e30f;
+        const Chunk& ch = S.batches[0].chunks[0];
+        for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {
+            ce = cudaMemsetAsync(d_Fp, 0, 8 * np * sizeof(double), s);
+            if (ce == cudaSuccess)
+                ce = tc_launch_tables(t.d_cpos_b, t.d_cw_b, S.d_kb_cell0, S.d_kb_ncell, ch.nkb, t.d_qy, t.ny, t.d_qz,
+                                      t.nz, t.mtiles, t.ntiles, wscale, p.d_tab, s);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
+            if (ce == cudaSuccess)
+                ce = tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles, S.d_items, ch.n_items, ch.grid, kcb, P,
+                                    d_Fp, t.ny, t.nz, scale, p.d_err, limit, t.mode, s);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
+            if (ce == cudaSuccess)
+                ce = tc_launch_reduce(P, S.d_reds, ch.n_red, t.ny, t.nz, t.ntiles, scale, d_Fp, s);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            float m = 0.f;
+            if (ce == cudaSuccess) cudaEventElapsedTime(&m, e0, e1);
+            ms = std::min(ms, m);
         }
+        unsigned int herr[4] = {0, 0, 0, 0};
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(d_err, 0, sizeof(herr), s);
+        if (ce == cudaSuccess) {
+            k_amp_maxerr<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(reinterpret_cast<const double2*>(d_Fp),
+                                                                    reinterpret_cast<const double2*>(p.d_F), np,
+                                                                    d_err);
+            ce = cudaGetLastError();
+        }
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(herr, d_err, sizeof(herr), cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        cudaFree(P);
+        free_schedule(S);
+        if (ce != cudaSuccess) { st = cuda_fail(ce, "autotune probe"); break; }
+        double err = 0.0;
+        for (int c = 0; c < 4; ++c)
+            if (wsum[c] > 0) err = std::max(err, (double)__builtin_bit_cast(float, herr[c]) / wsum[c]);
+        if (err <= 3e-7 && ms < best_ms) {
+            best_ms = ms;
+            best = {kcb, ips, mode};
+        }
+    }
     t.d_P = saveP;
     p.timer.on = timer_was_on;
     memcpy(p.timer.launches, launches_before, sizeof(launches_before));
@@ -484,6 +497,7 @@ nms_status tc_autotune(Plan& p, TcState& t)
     NMS_CUDA_TRY(cudaMemsetAsync(p.d_err, 0, sizeof(int32_t), s));
     t.kcb = best.kcb;
     t.items_per_sm = best.ips;
+    t.mode = best.mode;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune_cache[key] = best;
     tune_file_append(key, best);
@@ -528,7 +542,10 @@ nms_status tc_setup(Plan& p)
     t->mode = (t->ntiles % 2 == 0) ? 1 : (t->mtiles % 2 == 0) ? 2 : 0;
     if (const char* gm = getenv("NMS_GEMM_MODE")) {
         const int want = atoi(gm);
-        if (want == 0 || (want == 1 && t->ntiles % 2 == 0) || (want == 2 && t->mtiles % 2 == 0)) t->mode = want;
+        if (want == 0 || (want == 1 && t->ntiles % 2 == 0) || (want == 2 && t->mtiles % 2 == 0)) {
+            t->mode = want;
+            t->mode_forced = true;
+        }
     }
     const int64_t n = p.n_cells;
     const int64_t np = p.npix;

@@ -26,6 +26,11 @@ Steps and the passages they follow (paper section / equation):
                     decomposition (form factor sum vs full amplitude).
   azimuthal_*       Eq. iqazi (trapezoidal rule; periodic in theta).
   correlation       Eqs. crrad and prrad (trapezoidal rule over the nodes).
+  angular_spectrum_* Eq. CosineSinceIntensities (sine/cosine harmonics of
+                    the 2D image over theta) and modal_amplitudes, Eq.
+                    ModalAmplitudes.
+  correlation_2d_*  Eq. crav2d (inverse 2D transform of the image; trapezoid
+                    rule in q and theta, or in q_y and q_z).
   sphere_*/vortex_* Sec. "Spherical form factor model" and the linear vortex
                     section (analytic amplitudes used as pins).
 """
@@ -321,6 +326,115 @@ def correlation(q, Iq, r, prefactor=1.0 / (2.0 * np.pi ** 2)):
         f = Iq * spherical_j0(q * rm) * q * q
         c[m] = prefactor * np.sum(0.5 * (f[1:] + f[:-1]) * np.diff(q))
     return c, r * r * c
+
+
+# --------------------------------------------------------------------------
+# angular spectrum and 2D correlation function
+# --------------------------------------------------------------------------
+def angular_spectrum_polar(img, n_q, n_theta, kmax):
+    """Eq. CosineSinceIntensities on the polar grid, theta_j = 2 pi j / n_theta.
+
+    The periodic trapezoid turns the theta integral into a mean over j:
+        I_k^{c,s}(q_i) = (2 - delta_k0) / n_theta * sum_j f(q_i, theta_j) {cos, sin}(k theta_j).
+    Returns (Ic, Is), each [kmax + 1][n_q].
+    """
+    f = np.asarray(img, dtype=np.float64).reshape(n_q, n_theta)
+    theta = 2.0 * np.pi * np.arange(n_theta) / n_theta
+    k = np.arange(kmax + 1)
+    pref = (2.0 - (k == 0)) / n_theta
+    Ic = pref[:, None] * (np.cos(np.outer(k, theta)) @ f.T)
+    Is = pref[:, None] * (np.sin(np.outer(k, theta)) @ f.T)
+    return Ic, Is
+
+
+def angular_spectrum_cartesian(img, qy, qz, edges, kmax):
+    """Eq. CosineSinceIntensities on ring bins of a Cartesian or list grid.
+
+    Reading (as for the azimuthal average): the theta integral over the ring
+    edges[b] <= |q| < edges[b+1] is the mean over its pixels, with the pixel
+    angle theta = atan2(q_y, q_z) (qhat = (0, sin theta, cos theta); theta = 0
+    at q = 0).  Returns (Ic, Is, counts, qmean); empty bins give NaN.
+    """
+    f = np.asarray(img, dtype=np.float64).ravel()
+    qy = np.asarray(qy, dtype=np.float64).ravel()
+    qz = np.asarray(qz, dtype=np.float64).ravel()
+    qa = np.hypot(qy, qz)
+    th = np.arctan2(qy, qz)
+    nb = len(edges) - 1
+    Ic = np.full((kmax + 1, nb), np.nan)
+    Is = np.full((kmax + 1, nb), np.nan)
+    qm = np.full(nb, np.nan)
+    cnt = np.zeros(nb, dtype=np.int64)
+    for b in range(nb):
+        sel = (qa >= edges[b]) & (qa < edges[b + 1])
+        cnt[b] = int(sel.sum())
+        if not cnt[b]:
+            continue
+        qm[b] = qa[sel].mean()
+        for k in range(kmax + 1):
+            pref = 1.0 if k == 0 else 2.0
+            Ic[k, b] = pref * np.mean(f[sel] * np.cos(k * th[sel]))
+            Is[k, b] = pref * np.mean(f[sel] * np.sin(k * th[sel]))
+    return Ic, Is, cnt, qm
+
+
+def modal_amplitudes(Ic, Is):
+    """Eq. ModalAmplitudes: a_k = sum_i I_k(q_i) over the finite nodes, and
+    A_k^{s,c} = a_k^{s,c} / sum_{j <= kmax} sqrt(|a_j^s|^2 + |a_j^c|^2).
+    Returns (Ac, As)."""
+    Ic = np.asarray(Ic, dtype=np.float64)
+    Is = np.asarray(Is, dtype=np.float64)
+    ac = np.where(np.isfinite(Ic), Ic, 0.0).sum(axis=1)
+    as_ = np.where(np.isfinite(Is), Is, 0.0).sum(axis=1)
+    den = np.sum(np.sqrt(as_ ** 2 + ac ** 2))
+    return ac / den, as_ / den
+
+
+def trapezoid_weights(x):
+    """Weights of the trapezoidal rule on the nodes x (increasing)."""
+    x = np.asarray(x, dtype=np.float64)
+    w = np.zeros_like(x)
+    if len(x) > 1:
+        d = np.diff(x)
+        w[:-1] += 0.5 * d
+        w[1:] += 0.5 * d
+    return w
+
+
+def correlation_2d_polar(img, q, n_theta, rho, alpha):
+    """Eq. crav2d on the polar grid:
+        C(rho, alpha) = sum_i sum_j wq_i q_i (2 pi / n_theta) f(q_i, theta_j)
+                        exp(i q_i rho cos(theta_j - alpha)),
+    trapezoid weights wq in q, periodic trapezoid in theta.  Returns complex
+    C[len(rho)][len(alpha)]."""
+    q = np.asarray(q, dtype=np.float64)
+    f = np.asarray(img, dtype=np.float64).reshape(len(q), n_theta)
+    theta = 2.0 * np.pi * np.arange(n_theta) / n_theta
+    w = (trapezoid_weights(q) * q)[:, None] * (2.0 * np.pi / n_theta) * f
+    C = np.zeros((len(rho), len(alpha)), dtype=np.complex128)
+    for m, rm in enumerate(rho):
+        for n, an in enumerate(alpha):
+            C[m, n] = np.sum(w * np.exp(1j * np.outer(q, np.cos(theta - an)) * rm))
+    return C
+
+
+def correlation_2d_cartesian(img, qy_nodes, qz_nodes, rho, alpha):
+    """Eq. crav2d on a Cartesian grid: q dq dtheta = dq_y dq_z and
+    q rho cos(theta - alpha) = q_y rho sin(alpha) + q_z rho cos(alpha)
+    (qhat = (0, sin theta, cos theta)), trapezoid weights in q_y and q_z:
+        C(rho, alpha) = sum_{a,b} wy_a wz_b f_ab exp(i (q_y,a rho sin alpha + q_z,b rho cos alpha)).
+    img is [n_y][n_z] (pixel a * n_z + b).  Returns complex C[len(rho)][len(alpha)]."""
+    qy = np.asarray(qy_nodes, dtype=np.float64)
+    qz = np.asarray(qz_nodes, dtype=np.float64)
+    f = np.asarray(img, dtype=np.float64).reshape(len(qy), len(qz))
+    w = trapezoid_weights(qy)[:, None] * trapezoid_weights(qz)[None, :] * f
+    C = np.zeros((len(rho), len(alpha)), dtype=np.complex128)
+    for m, rm in enumerate(rho):
+        for n, an in enumerate(alpha):
+            ey = np.exp(1j * qy * rm * np.sin(an))
+            ez = np.exp(1j * qz * rm * np.cos(an))
+            C[m, n] = ey @ w @ ez
+    return C
 
 
 # --------------------------------------------------------------------------

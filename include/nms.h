@@ -207,6 +207,43 @@ nms_status nms_azimuthal_average(nms_plan_t plan, const double* img, int32_t img
                                  double* Iq, int64_t* counts, double* qmean,
                                  int32_t out_is_device);
 
+/* Angular spectrum of a per-pixel image of this plan's grid (paper, Eq.
+ * CosineSinceIntensities, trapezoidal rule) and its modal amplitudes (Eq.
+ * ModalAmplitudes).
+ *  POLAR grid:  nbins must equal n0 (bin_edges may be NULL) and n1 <= 8533;
+ *               Ic[k][i] = (2 - delta_k0)/n1 sum_j f(q_i, theta_j) cos(k theta_j),
+ *               Is likewise with sin (the periodic trapezoid); counts[i] = n1,
+ *               qmean[i] = q_i.
+ *  CARTESIAN/LIST: ring bins as in nms_azimuthal_average; Ic[k][b] =
+ *               (2 - delta_k0) x the mean over the bin's pixels of
+ *               f cos(k theta), Is with sin, theta = atan2(q_y, q_z) (0 at
+ *               q = 0); NaN for empty bins.
+ * Ac[k], As[k] = a_k / sum_j sqrt(a_j^s^2 + a_j^c^2), a_k = sum of I_k over
+ * the finite nodes.  0 <= kmax <= 1023.  Ic, Is: [kmax+1][nbins]; counts,
+ * qmean: [nbins]; Ac, As: [kmax+1]; counts, qmean, Ac, As may be NULL.
+ * img host or device per img_is_device, outputs per out_is_device.
+ * Synchronous. */
+nms_status nms_angular_spectrum(nms_plan_t plan, const double* img, int32_t img_is_device, int32_t kmax,
+                                int32_t nbins, const double* bin_edges, double* Ic, double* Is,
+                                int64_t* counts, double* qmean, double* Ac, double* As,
+                                int32_t out_is_device);
+
+/* 2D correlation function of a per-pixel image (paper, Eq. crav2d):
+ *   C(rho_m, alpha_n) = sum_p W_p f_p exp(+i q_p . rho_vec),
+ *   rho_vec = rho_m (0, sin alpha_n, cos alpha_n)  (so q.rho_vec = q rho cos(theta - alpha)),
+ * with the trapezoid rule of the grid as W_p: POLAR W = w_i q_i 2 pi/n1
+ * (w_i the trapezoid weights of the q nodes: q dq dtheta), CARTESIAN
+ * W = w_a w_b (trapezoid weights of the q_y and q_z nodes: dq_y dq_z).
+ * LIST grids have no quadrature: UNSUPPORTED.  rho [n_rho] and alpha
+ * [n_alpha] on the host, n_rho * n_alpha <= 2^24.  C: [n_rho][n_alpha][2]
+ * (re, im).  scale (may be NULL) = sum_p |W_p f_p|, the magnitude the
+ * rounding error is relative to (FP32 terms, two-float sums: |error| is of
+ * order 1e-7 scale).  Outputs host or device per out_is_device.
+ * Synchronous. */
+nms_status nms_correlation_2d(nms_plan_t plan, const double* img, int32_t img_is_device, int32_t n_rho,
+                              const double* rho, int32_t n_alpha, const double* alpha, double* C,
+                              double* scale, int32_t out_is_device);
+
 /* Correlation and pair-distance distribution functions (paper, Eqs. crrad
  * and prrad): c(r_m) = prefactor * trapz_i [ I(q_i) j0(q_i r_m) q_i^2 ],
  * p(r_m) = r_m^2 c(r_m), trapezoid over the nodes in the given order with

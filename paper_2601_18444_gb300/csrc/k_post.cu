@@ -1,79 +1,14 @@
-// Azimuthal averages (paper, Eq. iqazi) and correlation functions
-// (Eqs. crrad, prrad).  Both are small, HBM-bound reductions over the
-// detector image; the kernels read each pixel once.
+// Azimuthal average on the polar grid (paper, Eq. iqazi) and correlation
+// functions (Eqs. crrad, prrad).  Both are small, HBM-bound reductions over
+// the detector image; the kernels read each pixel once.  (Ring-binned
+// averages on Cartesian and list grids are the k = 0 mode of the angular
+// spectrum kernels.)
 #include <cuda_runtime.h>
 #include <math.h>
 
 #include "nms_internal.h"
 
 namespace nms {
-
-// ------------------------------------------------------------ cartesian rings
-// Bin b holds pixels with edges[b] <= |q| < edges[b+1].  Each block bins its
-// pixels in shared memory first, then adds its per-bin totals to global
-// memory once (FP64 atomics), so contention scales with blocks, not pixels.
-constexpr int AZI_THREADS = 256;
-constexpr int AZI_SMEM_BINS = 1024;
-
-__device__ __forceinline__ int find_bin(const double* __restrict__ e, int nb, double x)
-{
-    if (!(x >= e[0]) || !(x < e[nb])) return -1;
-    int lo = 0, hi = nb;  // e[lo] <= x < e[hi]
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (x >= e[mid]) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
-__global__ void k_azimuthal_cart(const double* __restrict__ img, const double* __restrict__ qa, int64_t npix,
-                                 const double* __restrict__ edges, int nbins, double* __restrict__ sum,
-                                 unsigned long long* __restrict__ cnt, double* __restrict__ qsum)
-{
-    __shared__ double s_sum[AZI_SMEM_BINS];
-    __shared__ double s_q[AZI_SMEM_BINS];
-    __shared__ unsigned int s_cnt[AZI_SMEM_BINS];
-    const bool local = nbins <= AZI_SMEM_BINS;
-    if (local) {
-        for (int b = threadIdx.x; b < nbins; b += blockDim.x) { s_sum[b] = 0.0; s_q[b] = 0.0; s_cnt[b] = 0u; }
-        __syncthreads();
-    }
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
-        double x = qa[p];
-        int b = find_bin(edges, nbins, x);
-        if (b < 0) continue;
-        if (local) {
-            atomicAdd(&s_sum[b], img[p]);
-            atomicAdd(&s_q[b], x);
-            atomicAdd(&s_cnt[b], 1u);
-        } else {
-            atomicAdd(&sum[b], img[p]);
-            atomicAdd(&qsum[b], x);
-            atomicAdd(&cnt[b], 1ull);
-        }
-    }
-    if (local) {
-        __syncthreads();
-        for (int b = threadIdx.x; b < nbins; b += blockDim.x)
-            if (s_cnt[b]) {
-                atomicAdd(&sum[b], s_sum[b]);
-                atomicAdd(&qsum[b], s_q[b]);
-                atomicAdd(&cnt[b], (unsigned long long)s_cnt[b]);
-            }
-    }
-}
-
-cudaError_t launch_azimuthal_cart(const Plan& p, const double* img, int nbins, const double* d_edges, double* d_sum,
-                                  unsigned long long* d_cnt, double* d_qsum, cudaStream_t s)
-{
-    int64_t blocks = (p.npix + AZI_THREADS * 8 - 1) / (AZI_THREADS * 8);
-    int cap = 4 * device_sm_count();
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    k_azimuthal_cart<<<(unsigned)blocks, AZI_THREADS, 0, s>>>(img, p.d_qa, p.npix, d_edges, nbins, d_sum, d_cnt,
-                                                              d_qsum);
-    return cudaGetLastError();
-}
 
 // ------------------------------------------------------------ polar grid
 // Periodic trapezoid over theta_j = 2 pi j / n_theta equals the mean over j.
@@ -95,6 +30,24 @@ __global__ void k_azimuthal_polar(const double* __restrict__ img, int n0, int n1
 cudaError_t launch_azimuthal_polar(const Plan& p, const double* img, double* Iq, cudaStream_t s)
 {
     k_azimuthal_polar<<<p.grid.n0, 256, 0, s>>>(img, p.grid.n0, p.grid.n1, Iq);
+    return cudaGetLastError();
+}
+
+// Nodes of the polar grid as bins: counts[i] = n_theta, qmean[i] = q_i
+// (linear nodes lo + ((hi - lo) i)/(n - 1), as the grid defines them).
+__global__ void k_polar_nodes(int n0, int n1, double lo, double hi, int64_t* __restrict__ counts,
+                              double* __restrict__ qmean)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n0) return;
+    if (counts) counts[i] = n1;
+    if (qmean) qmean[i] = n0 == 1 ? lo : lo + ((hi - lo) * i) / (double)(n0 - 1);
+}
+
+cudaError_t launch_polar_nodes(const Plan& p, int64_t* counts, double* qmean, cudaStream_t s)
+{
+    k_polar_nodes<<<(p.grid.n0 + 127) / 128, 128, 0, s>>>(p.grid.n0, p.grid.n1, p.grid.lo0, p.grid.hi0, counts,
+                                                          qmean);
     return cudaGetLastError();
 }
 

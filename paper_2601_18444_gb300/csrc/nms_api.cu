@@ -505,6 +505,57 @@ nms_status nms_response(nms_plan_t plan, int32_t id, int32_t part, double* out, 
     return check_device_error(p);
 }
 
+// Device staging of results: kernels write device buffers; results the
+// caller wants on the host are copied back at the end of the call.
+namespace {
+struct Staged {
+    void* user = nullptr;   // caller's buffer (may be NULL: not wanted)
+    void* dev = nullptr;    // what the kernels write
+    size_t bytes = 0;
+    bool copy_back = false;
+};
+
+cudaError_t stage(Staged& st, void* user, size_t bytes, bool user_is_device, cudaStream_t s)
+{
+    st.user = user;
+    st.bytes = bytes;
+    if (user && user_is_device) {
+        st.dev = user;
+        return cudaSuccess;
+    }
+    st.copy_back = user != nullptr;
+    return cudaMallocAsync(&st.dev, bytes > 0 ? bytes : 8, s);
+}
+
+cudaError_t unstage(Staged& st, cudaStream_t s, cudaError_t e)
+{
+    if (e == cudaSuccess && st.copy_back) e = cudaMemcpyAsync(st.user, st.dev, st.bytes, cudaMemcpyDeviceToHost, s);
+    if (st.dev && st.dev != st.user) cudaFreeAsync(st.dev, s);
+    st.dev = nullptr;
+    return e;
+}
+
+// image on the device for the duration of a call
+cudaError_t device_image(const Plan& p, const double* img, bool is_device, const double** d_img, double** tmp)
+{
+    *tmp = nullptr;
+    *d_img = img;
+    if (is_device) return cudaSuccess;
+    cudaError_t e = cudaMallocAsync((void**)tmp, p.npix * 8, p.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(*tmp, img, p.npix * 8, cudaMemcpyHostToDevice, p.stream);
+    *d_img = *tmp;
+    return e;
+}
+
+nms_status check_edges(int nbins, const double* edges)
+{
+    if (nbins < 1 || !edges) return fail(NMS_ERR_INVALID_ARG, "need nbins >= 1 and bin_edges");
+    for (int b = 0; b < nbins; ++b)
+        if (!(edges[b + 1] > edges[b])) return fail(NMS_ERR_INVALID_ARG, "bin_edges not increasing");
+    return NMS_OK;
+}
+}  // namespace
+
 nms_status nms_azimuthal_average(nms_plan_t plan, const double* img, int32_t img_is_device, int32_t nbins,
                                  const double* bin_edges, double* Iq, int64_t* counts, double* qmean,
                                  int32_t out_is_device)
@@ -513,76 +564,157 @@ nms_status nms_azimuthal_average(nms_plan_t plan, const double* img, int32_t img
     if (!plan || !img || !Iq || !counts) return fail(NMS_ERR_INVALID_ARG, "NULL argument");
     Plan& p = *plan;
     cudaStream_t s = p.stream;
-    const int64_t np = p.npix;
-    const double* d_img = img;
+    const bool polar = p.grid.kind == NMS_QGRID_POLAR;
+    if (polar && nbins != p.grid.n0) return fail(NMS_ERR_INVALID_ARG, "POLAR grid: nbins must equal n0");
+    if (!polar) {
+        nms_status st = check_edges(nbins, bin_edges);
+        if (st) return st;
+    }
+    const double* d_img = nullptr;
     double* tmp_img = nullptr;
-    if (!img_is_device) {
-        NMS_CUDA_TRY(cudaMallocAsync((void**)&tmp_img, np * 8, s));
-        NMS_CUDA_TRY(cudaMemcpyAsync(tmp_img, img, np * 8, cudaMemcpyHostToDevice, s));
-        d_img = tmp_img;
-    }
-    std::vector<double> hI(std::max(nbins, 0)), hq(std::max(nbins, 0));
-    std::vector<int64_t> hc(std::max(nbins, 0));
-    nms_status result = NMS_OK;
-    if (p.grid.kind == NMS_QGRID_POLAR) {
-        if (nbins != p.grid.n0) {
-            result = fail(NMS_ERR_INVALID_ARG, "POLAR grid: nbins must equal n0");
-        } else {
-            double* d_I = nullptr;
-            NMS_CUDA_TRY(cudaMallocAsync((void**)&d_I, nbins * 8, s));
-            cudaError_t e = launch_azimuthal_polar(p, d_img, d_I, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(hI.data(), d_I, nbins * 8, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            cudaFreeAsync(d_I, s);
-            if (e != cudaSuccess) result = cuda_fail(e, "azimuthal (polar)");
-            for (int i = 0; i < nbins; ++i) {
-                hc[i] = p.grid.n1;
-                hq[i] = lin_node(i, p.grid.n0, p.grid.lo0, p.grid.hi0);
-            }
-        }
+    NMS_CUDA_TRY(device_image(p, img, img_is_device != 0, &d_img, &tmp_img));
+    Staged sI, sc, sq;
+    cudaError_t e = stage(sI, Iq, (size_t)nbins * 8, out_is_device, s);
+    if (e == cudaSuccess) e = stage(sc, counts, (size_t)nbins * 8, out_is_device, s);
+    if (e == cudaSuccess) e = stage(sq, qmean, (size_t)nbins * 8, out_is_device, s);
+    if (polar) {
+        // the periodic trapezoid over theta (Eq. iqazi) is the mean over j
+        if (e == cudaSuccess) e = launch_azimuthal_polar(p, d_img, (double*)sI.dev, s);
+        if (e == cudaSuccess) e = launch_polar_nodes(p, (int64_t*)sc.dev, (double*)sq.dev, s);
     } else {
-        if (nbins < 1 || !bin_edges) {
-            result = fail(NMS_ERR_INVALID_ARG, "need nbins >= 1 and bin_edges");
-        } else {
-            for (int b = 0; b < nbins; ++b)
-                if (!(bin_edges[b + 1] > bin_edges[b])) { result = fail(NMS_ERR_INVALID_ARG, "bin_edges not increasing"); break; }
-        }
-        if (result == NMS_OK) {
-            double *d_e = nullptr, *d_sum = nullptr, *d_qs = nullptr;
-            unsigned long long* d_cnt = nullptr;
-            NMS_CUDA_TRY(cudaMallocAsync((void**)&d_e, (nbins + 1) * 8, s));
-            NMS_CUDA_TRY(cudaMallocAsync((void**)&d_sum, nbins * 8, s));
-            NMS_CUDA_TRY(cudaMallocAsync((void**)&d_qs, nbins * 8, s));
-            NMS_CUDA_TRY(cudaMallocAsync((void**)&d_cnt, nbins * 8, s));
-            cudaError_t e = cudaMemcpyAsync(d_e, bin_edges, (nbins + 1) * 8, cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) e = cudaMemsetAsync(d_sum, 0, nbins * 8, s);
-            if (e == cudaSuccess) e = cudaMemsetAsync(d_qs, 0, nbins * 8, s);
-            if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, nbins * 8, s);
-            if (e == cudaSuccess) e = launch_azimuthal_cart(p, d_img, nbins, d_e, d_sum, d_cnt, d_qs, s);
-            std::vector<unsigned long long> cnt(nbins);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(hI.data(), d_sum, nbins * 8, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(hq.data(), d_qs, nbins * 8, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), d_cnt, nbins * 8, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            cudaFreeAsync(d_e, s);
-            cudaFreeAsync(d_sum, s);
-            cudaFreeAsync(d_qs, s);
-            cudaFreeAsync(d_cnt, s);
-            if (e != cudaSuccess) result = cuda_fail(e, "azimuthal (cartesian)");
-            for (int b = 0; b < nbins; ++b) {
-                hc[b] = (int64_t)cnt[b];
-                if (cnt[b]) { hI[b] /= (double)cnt[b]; hq[b] /= (double)cnt[b]; }
-                else { hI[b] = NAN; hq[b] = NAN; }
-            }
-        }
+        // ring means: the k = 0 mode of the ring-binned angular spectrum
+        double *d_e = nullptr, *acc = nullptr, *Is0 = nullptr;
+        unsigned long long* cnt = nullptr;
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_e, (nbins + 1) * 8, s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&acc, (size_t)3 * nbins * 8, s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&cnt, (size_t)nbins * 8, s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&Is0, (size_t)nbins * 8, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_e, bin_edges, (nbins + 1) * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, (size_t)3 * nbins * 8, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, (size_t)nbins * 8, s);
+        if (e == cudaSuccess)
+            e = launch_angspec_rings(p, d_img, d_e, nbins, 0, acc, cnt, (double*)sI.dev, Is0, (int64_t*)sc.dev,
+                                     (double*)sq.dev, s);
+        cudaFreeAsync(d_e, s);
+        cudaFreeAsync(acc, s);
+        cudaFreeAsync(cnt, s);
+        cudaFreeAsync(Is0, s);
     }
+    e = unstage(sI, s, e);
+    e = unstage(sc, s, e);
+    e = unstage(sq, s, e);
     if (tmp_img) cudaFreeAsync(tmp_img, s);
-    if (result != NMS_OK) return result;
-    cudaMemcpyKind k = out_is_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
-    NMS_CUDA_TRY(cudaMemcpyAsync(Iq, hI.data(), nbins * 8, k, s));
-    NMS_CUDA_TRY(cudaMemcpyAsync(counts, hc.data(), nbins * 8, k, s));
-    if (qmean) NMS_CUDA_TRY(cudaMemcpyAsync(qmean, hq.data(), nbins * 8, k, s));
-    NMS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "azimuthal average");
+    return NMS_OK;
+}
+
+nms_status nms_angular_spectrum(nms_plan_t plan, const double* img, int32_t img_is_device, int32_t kmax,
+                                int32_t nbins, const double* bin_edges, double* Ic, double* Is, int64_t* counts,
+                                double* qmean, double* Ac, double* As, int32_t out_is_device)
+{
+    set_error("");
+    if (!plan || !img || !Ic || !Is) return fail(NMS_ERR_INVALID_ARG, "NULL argument");
+    if (kmax < 0 || kmax > 1023) return fail(NMS_ERR_INVALID_ARG, "need 0 <= kmax <= 1023");
+    Plan& p = *plan;
+    cudaStream_t s = p.stream;
+    const bool polar = p.grid.kind == NMS_QGRID_POLAR;
+    if (polar) {
+        if (nbins != p.grid.n0) return fail(NMS_ERR_INVALID_ARG, "POLAR grid: nbins must equal n0");
+        if ((size_t)3 * p.grid.n1 * 8 > (200u << 10))
+            return fail(NMS_ERR_UNSUPPORTED, "POLAR grid: n_theta above 8533");
+    } else {
+        nms_status st = check_edges(nbins, bin_edges);
+        if (st) return st;
+    }
+    const int K = kmax + 1;
+    const double* d_img = nullptr;
+    double* tmp_img = nullptr;
+    NMS_CUDA_TRY(device_image(p, img, img_is_device != 0, &d_img, &tmp_img));
+    Staged sIc, sIs, sc, sq, sAc, sAs;
+    const bool od = out_is_device != 0;
+    cudaError_t e = stage(sIc, Ic, (size_t)K * nbins * 8, od, s);
+    if (e == cudaSuccess) e = stage(sIs, Is, (size_t)K * nbins * 8, od, s);
+    if (e == cudaSuccess) e = stage(sc, counts, (size_t)nbins * 8, od, s);
+    if (e == cudaSuccess) e = stage(sq, qmean, (size_t)nbins * 8, od, s);
+    if (e == cudaSuccess) e = stage(sAc, Ac, (size_t)K * 8, od, s);
+    if (e == cudaSuccess) e = stage(sAs, As, (size_t)K * 8, od, s);
+    if (polar) {
+        if (e == cudaSuccess) e = launch_angspec_polar(p, d_img, kmax, (double*)sIc.dev, (double*)sIs.dev, s);
+        if (e == cudaSuccess) e = launch_polar_nodes(p, (int64_t*)sc.dev, (double*)sq.dev, s);
+    } else {
+        double *d_e = nullptr, *acc = nullptr;
+        unsigned long long* cnt = nullptr;
+        const size_t nacc = (size_t)(2 * K + 1) * nbins;
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_e, (nbins + 1) * 8, s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&acc, nacc * 8, s);
+        if (e == cudaSuccess) e = cudaMallocAsync((void**)&cnt, (size_t)nbins * 8, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_e, bin_edges, (nbins + 1) * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, nacc * 8, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, (size_t)nbins * 8, s);
+        if (e == cudaSuccess)
+            e = launch_angspec_rings(p, d_img, d_e, nbins, kmax, acc, cnt, (double*)sIc.dev, (double*)sIs.dev,
+                                     (int64_t*)sc.dev, (double*)sq.dev, s);
+        cudaFreeAsync(d_e, s);
+        cudaFreeAsync(acc, s);
+        cudaFreeAsync(cnt, s);
+    }
+    if (e == cudaSuccess)
+        e = launch_modal_amplitudes((double*)sIc.dev, (double*)sIs.dev, nbins, kmax, (double*)sAc.dev,
+                                    (double*)sAs.dev, s);
+    e = unstage(sIc, s, e);
+    e = unstage(sIs, s, e);
+    e = unstage(sc, s, e);
+    e = unstage(sq, s, e);
+    e = unstage(sAc, s, e);
+    e = unstage(sAs, s, e);
+    if (tmp_img) cudaFreeAsync(tmp_img, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "angular spectrum");
+    return NMS_OK;
+}
+
+nms_status nms_correlation_2d(nms_plan_t plan, const double* img, int32_t img_is_device, int32_t n_rho,
+                              const double* rho, int32_t n_alpha, const double* alpha, double* C, double* scale,
+                              int32_t out_is_device)
+{
+    set_error("");
+    if (!plan || !img || !C || !rho || !alpha) return fail(NMS_ERR_INVALID_ARG, "NULL argument");
+    if (n_rho < 1 || n_alpha < 1 || (int64_t)n_rho * n_alpha > (1 << 24))
+        return fail(NMS_ERR_INVALID_ARG, "need n_rho, n_alpha >= 1 and n_rho * n_alpha <= 2^24");
+    Plan& p = *plan;
+    if (p.grid.kind == NMS_QGRID_LIST) return fail(NMS_ERR_UNSUPPORTED, "LIST grid has no quadrature weights");
+    cudaStream_t s = p.stream;
+    const int n_out = n_rho * n_alpha;
+    const int splits = corr2d_splits(p.npix, n_out);
+    const double* d_img = nullptr;
+    double* tmp_img = nullptr;
+    NMS_CUDA_TRY(device_image(p, img, img_is_device != 0, &d_img, &tmp_img));
+    Staged sC, sS;
+    cudaError_t e = stage(sC, C, (size_t)n_out * 16, out_is_device != 0, s);
+    if (e == cudaSuccess) e = stage(sS, scale, 8, out_is_device != 0, s);
+    double *d_rho = nullptr, *d_alpha = nullptr;
+    float* d_w = nullptr;
+    float4* d_pts = nullptr;
+    double2* d_part = nullptr;
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_rho, (size_t)n_rho * 8, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_alpha, (size_t)n_alpha * 8, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_w, (size_t)p.npix * 4, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_pts, (size_t)n_out * 16, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_part, (size_t)splits * n_out * 16, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_rho, rho, (size_t)n_rho * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_alpha, alpha, (size_t)n_alpha * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sS.dev, 0, 8, s);
+    if (e == cudaSuccess)
+        e = launch_corr2d(p, d_img, d_rho, n_rho, d_alpha, n_alpha, d_w, (double*)sS.dev, d_pts, d_part, splits,
+                          (double2*)sC.dev, s);
+    for (void* x : {(void*)d_rho, (void*)d_alpha, (void*)d_w, (void*)d_pts, (void*)d_part})
+        if (x) cudaFreeAsync(x, s);
+    e = unstage(sC, s, e);
+    e = unstage(sS, s, e);
+    if (tmp_img) cudaFreeAsync(tmp_img, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "2D correlation");
     return NMS_OK;
 }
 

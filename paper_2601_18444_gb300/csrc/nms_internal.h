@@ -125,9 +125,17 @@ cudaError_t launch_shift_add(const Plan& p, const double* Fk, double cy, double 
 cudaError_t launch_response(const Plan& p, int id, const double* Ga, const double* Gb, double norm,
                             double* out, cudaStream_t s);
 // Azimuthal averages.
-cudaError_t launch_azimuthal_cart(const Plan& p, const double* img, int nbins, const double* d_edges,
-                                  double* d_sum, unsigned long long* d_cnt, double* d_qsum,
-                                  cudaStream_t s);
+cudaError_t launch_polar_nodes(const Plan& p, int64_t* counts, double* qmean, cudaStream_t s);
+cudaError_t launch_angspec_polar(const Plan& p, const double* img, int kmax, double* Ic, double* Is, cudaStream_t s);
+cudaError_t launch_angspec_rings(const Plan& p, const double* img, const double* d_edges, int nbins, int kmax,
+                                 double* acc, unsigned long long* cnt, double* Ic, double* Is, int64_t* counts,
+                                 double* qmean, cudaStream_t s);
+cudaError_t launch_modal_amplitudes(const double* Ic, const double* Is, int nb, int kmax, double* Ac, double* As,
+                                    cudaStream_t s);
+cudaError_t launch_corr2d(const Plan& p, const double* img, const double* d_rho, int n_rho, const double* d_alpha,
+                          int n_alpha, float* d_w, double* d_wabs, float4* d_pts, double2* d_part, int splits,
+                          double2* d_C, cudaStream_t s);
+int corr2d_splits(int64_t npix, int n_out);
 cudaError_t launch_azimuthal_polar(const Plan& p, const double* img, double* Iq, cudaStream_t s);
 cudaError_t launch_correlation(int nq, const double* q, const double* Iq, int nr, const double* r,
                                double pref, double* c, double* pr, double* scratch_q, double* scratch_f,
@@ -142,6 +150,20 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s);
 void tc_release(Plan& p);
 
 int device_sm_count();
+
+// Ring bin of |q| = x: b with e[b] <= x < e[b+1] (e increasing, nb bins), or
+// -1 outside [e[0], e[nb]) and for NaN.
+__device__ __forceinline__ int find_bin(const double* __restrict__ e, int nb, double x)
+{
+    if (!(x >= e[0]) || !(x < e[nb])) return -1;
+    int lo = 0, hi = nb;  // e[lo] <= x < e[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (x >= e[mid]) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
 // Direct sum of cells [c0, c1) (compensated unless the plan asked for the
 // naive phase) into out [4][npix][2] through the split partials.
 nms_status direct_sum_range(Plan& p, const float4* cpos, int64_t c0, int64_t c1, double* out);

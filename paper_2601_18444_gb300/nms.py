@@ -66,6 +66,10 @@ SIGNATURES = {
     "nms_response": (ctypes.c_int, [_V, ctypes.c_int32, ctypes.c_int32, _V, ctypes.c_int32]),
     "nms_azimuthal_average": (ctypes.c_int, [_V, _V, ctypes.c_int32, ctypes.c_int32, _D, _V, _V, _V,
                                              ctypes.c_int32]),
+    "nms_angular_spectrum": (ctypes.c_int, [_V, _V, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _D, _V, _V, _V,
+                                            _V, _V, _V, ctypes.c_int32]),
+    "nms_correlation_2d": (ctypes.c_int, [_V, _V, ctypes.c_int32, ctypes.c_int32, _D, ctypes.c_int32, _D, _V, _V,
+                                          ctypes.c_int32]),
     "nms_correlation": (ctypes.c_int, [ctypes.c_int32, _V, _V, ctypes.c_int32, _V, ctypes.c_double, _V, _V,
                                        ctypes.c_int32, _V]),
     "nms_plan_stage_ms": (ctypes.c_int, [_V, _D, _I64, ctypes.c_int32]),
@@ -275,6 +279,50 @@ def nms_azimuthal_average(plan, img, bin_edges=None, nbins=None):
     _check(load().nms_azimuthal_average(plan.handle, _ptr(img), 1 if _is_dev(img) else 0, nb, p_e, _ptr(I),
                                         _ptr(c), _ptr(qm), 0))
     return I, c, qm
+
+
+def nms_angular_spectrum(plan, img, kmax, bin_edges=None, nbins=None):
+    """Returns dict(Ic, Is [kmax+1][nbins], counts, qmean, Ac, As) as host numpy arrays."""
+    if bin_edges is not None:
+        edges = np.ascontiguousarray(bin_edges, dtype=np.float64)
+        nb = len(edges) - 1
+        p_e = edges.ctypes.data_as(_D)
+    else:
+        edges, p_e, nb = None, None, int(nbins)
+    img = _dev_in(img) if _is_dev(img) else np.ascontiguousarray(img, dtype=np.float64)
+    K = int(kmax) + 1
+    Ic = np.empty((K, nb), dtype=np.float64)
+    Is = np.empty((K, nb), dtype=np.float64)
+    c = np.empty(nb, dtype=np.int64)
+    qm = np.empty(nb, dtype=np.float64)
+    Ac = np.empty(K, dtype=np.float64)
+    As = np.empty(K, dtype=np.float64)
+    _check(load().nms_angular_spectrum(plan.handle, _ptr(img), 1 if _is_dev(img) else 0, int(kmax), nb, p_e,
+                                       _ptr(Ic), _ptr(Is), _ptr(c), _ptr(qm), _ptr(Ac), _ptr(As), 0))
+    return {"Ic": Ic, "Is": Is, "counts": c, "qmean": qm, "Ac": Ac, "As": As}
+
+
+def nms_correlation_2d(plan, img, rho, alpha, out=None):
+    """C(rho, alpha) of Eq. crav2d.  Returns (C complex [n_rho][n_alpha] host
+    array, scale = sum |W f|); with out (a device float64 [n_rho][n_alpha][2]
+    tensor) the result stays on the device and (out, scale) is returned."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64).ravel()
+    alpha = np.ascontiguousarray(alpha, dtype=np.float64).ravel()
+    img = _dev_in(img) if _is_dev(img) else np.ascontiguousarray(img, dtype=np.float64)
+    lib = load()
+    if out is not None:
+        import torch
+        sc = torch.empty(1, dtype=torch.float64, device=out.device)
+        _check(lib.nms_correlation_2d(plan.handle, _ptr(img), 1 if _is_dev(img) else 0, len(rho),
+                                      rho.ctypes.data_as(_D), len(alpha), alpha.ctypes.data_as(_D), _ptr(out),
+                                      _ptr(sc), 1))
+        return out, sc
+    C = np.empty((len(rho), len(alpha), 2), dtype=np.float64)
+    sc = np.empty(1, dtype=np.float64)
+    _check(lib.nms_correlation_2d(plan.handle, _ptr(img), 1 if _is_dev(img) else 0, len(rho),
+                                  rho.ctypes.data_as(_D), len(alpha), alpha.ctypes.data_as(_D), _ptr(C), _ptr(sc),
+                                  0))
+    return C[..., 0] + 1j * C[..., 1], float(sc[0])
 
 
 def nms_correlation(q, Iq, r, prefactor=0.0, stream=None):

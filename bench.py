@@ -258,7 +258,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nms", choices=["nms", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "tc", "direct", "naive"])
-    ap.add_argument("--workload", default="box", choices=["box", "box64", "sphere", "ensemble", "rotations"])
+    ap.add_argument("--workload", default="box",
+                    choices=["box", "box64", "sphere", "ensemble", "rotations", "post2d"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kc", type=int, default=0, help="cells per TMEM accumulation chunk (0: library default)")
     ap.add_argument("--workspace-gb", type=float, default=0.0)
@@ -275,6 +276,8 @@ def main():
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     nms.load()
+    if args.workload == "post2d":
+        return run_post2d(args, rank, world, dev)
     field, grid_kw, edges, r, desc, rot, dilute = make_workload(args.workload)
     prec = {"auto": nms.PREC_AUTO, "tc": nms.PREC_TC_F16X3, "direct": nms.PREC_FP32_DIRECT,
             "naive": nms.PREC_FP32_NAIVE}[args.precision]
@@ -419,6 +422,105 @@ def table_bytes(field, grid_kw, n_rot):
     else:
         nkb = -(-field.n // 32)
     return float(nkb * n_rot * (mt + nt) * 2 * 16384)
+
+
+# FP32-pipe operations per (pixel, output point) term of k_corr2d, counted
+# from its source (two-float phase and exact reduction 16, sincospif ~20,
+# 2 FMA, two-float fold of 8-term partials ~2).
+CORR2D_OPS_PER_TERM = 40
+
+
+def run_post2d(args, rank, world, dev):
+    """2D post-processing of the box's unpolarized image: the angular spectrum
+    (kmax 16 on 128 ring bins) and the 2D correlation C(rho, alpha) on a
+    64 x 64 output grid, timed with CUDA events; one step = both calls."""
+    import torch
+    from paper_2601_18444_gb300 import nms
+    field, grid_kw, edges, r, desc, rot, dilute = make_workload("box")
+    stream = torch.cuda.current_stream()
+    plan = nms.plan_from_field(field, nms.make_grid(**grid_kw), nms.nms_options_default(), stream=stream.cuda_stream)
+    nms.nms_amplitudes(plan)
+    npix = plan.npix
+    img = torch.empty(npix, dtype=torch.float64, device="cuda")
+    nms.nms_response(plan, "UNPOL", out=img)
+    rho = np.linspace(0.0, 300.0, 64)
+    alpha = np.linspace(0.0, np.pi, 64, endpoint=False)
+    C = torch.empty((64, 64, 2), dtype=torch.float64, device="cuda")
+    terms = float(npix) * 64 * 64
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        nms.nms_angular_spectrum(plan, img, kmax=16, bin_edges=edges)
+        nms.nms_correlation_2d(plan, img, rho, alpha, out=C)
+
+    def corr_only():
+        nms.nms_correlation_2d(plan, img, rho, alpha, out=C)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    peaks, _ = load_peaks()
+    times, tcorr = [], []
+    barrier(world)
+    with ClockSampler(dev) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            corr_only()
+            e2.record(stream)
+            e2.synchronize()
+            times.append(e0.elapsed_time(e1))
+            tcorr.append(e1.elapsed_time(e2))
+    barrier(world)
+    ms = max_over_ranks(float(np.mean(times)), world)
+    ms_corr = float(np.mean(tcorr))
+    clocks = clk.summary(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    peak = sms * 128 * mhz * 1e6 / 1e12
+    achieved = terms * CORR2D_OPS_PER_TERM / (ms_corr * 1e-3) / 1e12
+    # end to end: host image in, host results out
+    img_h = img.cpu().numpy()
+    t0 = time.perf_counter()
+    for _ in range(2):
+        nms.nms_angular_spectrum(plan, img_h, kmax=16, bin_edges=edges)
+        nms.nms_correlation_2d(plan, img_h, rho, alpha)
+    t_e2e = (time.perf_counter() - t0) / 2
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        # the oracle's 2D correlation on a bounded sample of output points
+        from oracle import sans as S
+        q0 = np.linspace(grid_kw["lo0"], grid_kw["hi0"], grid_kw["n0"])
+        q1 = np.linspace(grid_kw["lo1"], grid_kw["hi1"], grid_kw["n1"])
+        n_s, t0, dt = 0, time.perf_counter(), 0.0
+        while dt < 3.0:
+            S.correlation_2d_cartesian(img_h, q0, q1, rho[n_s % 64:n_s % 64 + 1], alpha[:4])
+            n_s += 4
+            dt = time.perf_counter() - t0
+        cpu = {"value": n_s * npix / dt, "unit": "terms/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n_s} output points x {npix} pixels, {dt:.1f} s (numpy with its BLAS threads)"}
+    if rank == 0:
+        line = {"metric": "pixel x output-point terms/s of the 2D correlation (Eq. crav2d) with the angular spectrum",
+                "value": world * terms / (ms * 1e-3), "unit": "terms/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32(two-float)", "data": "synthetic",
+                "config": {"workload": "UNPOL image of " + desc + "; angular spectrum kmax 16 on 128 ring bins; "
+                                       "C(rho, alpha) on 64 rho in [0, 300] nm x 64 alpha in [0, pi)",
+                           "parallelism": f"replicas x{world}", "l2": "flushed between steps",
+                           "corr2d_ms": ms_corr},
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                             "frac": achieved / peak, "traffic": None, "kernel": "k_corr2d",
+                             "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz"},
+                "cpu_baseline": cpu,
+                "e2e": {"value": world * terms / t_e2e, "unit": "terms/s", "h2d_bytes_per_step": 2 * npix * 8,
+                        "d2h_bytes_per_step": 64 * 64 * 16 + 17 * 128 * 16 + 128 * 16 + 17 * 16},
+                "gpu_launches": args.steps * 7, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
 
 
 def plan_path_is_tc(stage):

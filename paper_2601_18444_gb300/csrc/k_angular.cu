@@ -6,9 +6,9 @@
 // pixel is read once.  On the polar grid a block owns one q row, keeps the row
 // and a table of cos/sin(2 pi m / n_theta) in shared memory, and one warp per
 // harmonic k sums f_j T[(k j) mod n_theta] (the periodic trapezoid).  On ring
-// bins each pixel adds f cos(k theta), f sin(k theta) (angle-addition
-// recurrence from qhat = (0, sin theta, cos theta)) to per-block bins in
-// shared memory, flushed to FP64 global bins once per block.
+// bins the pixels are counting-sorted by bin and one block per bin sums
+// f cos(k theta), f sin(k theta) (angle-addition recurrence from
+// qhat = (0, sin theta, cos theta)) in registers.
 //
 // The 2D correlation is a dense sum over pixels for every output point
 // rho_vec = rho (0, sin alpha, cos alpha):
@@ -31,7 +31,6 @@ namespace nms {
 // ------------------------------------------------------------ polar grid
 constexpr int ANG_THREADS = 256;
 constexpr size_t ANG_POLAR_MAX_SMEM = 200u << 10;   // row + cos/sin tables: n_theta <= 8533
-constexpr size_t ANG_RING_MAX_SMEM = 200u << 10;    // per-block bins; larger requests use global bins
 
 // Ic/Is[k][i] = (2 - delta_k0)/n_theta * sum_j f(q_i, theta_j) {cos, sin}(k theta_j)
 __global__ void __launch_bounds__(ANG_THREADS)
@@ -89,93 +88,226 @@ cudaError_t launch_angspec_polar(const Plan& p, const double* img, int kmax, dou
 }
 
 // ------------------------------------------------------------ ring bins
-// acc layout: [2 * (kmax + 1) + 1][nbins] doubles: cos sums (k = 0..kmax),
-// sin sums (k = 0..kmax), |q| sums; cnt[nbins].
-__global__ void __launch_bounds__(ANG_THREADS)
-k_angspec_rings(const double* __restrict__ img, const double* __restrict__ hy, const double* __restrict__ hz,
-                const double* __restrict__ qa, int64_t npix, const double* __restrict__ edges, int nbins, int kmax,
-                int local, double* __restrict__ acc, unsigned long long* __restrict__ cnt)
+// The pixels are counting-sorted by ring bin (bin of every pixel, bin sizes,
+// offsets, scatter).  Each bin is cut into parts of at most ANG_PART pixels;
+// one block per part sums f cos(k theta) and f sin(k theta) for a chunk of
+// harmonics in registers and writes the part's sums, and a last pass adds
+// the parts of each bin in order: no atomics on the sums, the same result
+// for any pixel order within a part's block reduction.
+constexpr int ANG_KC = 16;          // harmonics per register chunk
+constexpr int ANG_RED_THREADS = 128;
+constexpr int ANG_PART = 256;       // pixels per part
+
+__global__ void k_ang_bins(const double* __restrict__ qa, int64_t npix, const double* __restrict__ edges, int nbins,
+                           int32_t* __restrict__ bin_of, int32_t* __restrict__ count)
 {
-    extern __shared__ double s_acc[];
-    const int K = kmax + 1;
-    const int nrow = 2 * K + 1;
-    unsigned int* s_cnt = reinterpret_cast<unsigned int*>(s_acc + (size_t)nrow * nbins);
-    if (local) {
-        for (int t = threadIdx.x; t < nrow * nbins; t += blockDim.x) s_acc[t] = 0.0;
-        for (int t = threadIdx.x; t < nbins; t += blockDim.x) s_cnt[t] = 0u;
-        __syncthreads();
-    }
-    double* A = local ? s_acc : acc;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
-        const double x = qa[p];
-        const int b = find_bin(edges, nbins, x);
-        if (b < 0) continue;
-        const double f = img[p];
-        const double c1 = hz[p], s1 = hy[p];   // cos(theta), sin(theta)
-        double ck = 1.0, sk = 0.0;
-        for (int k = 0; k < K; ++k) {
-            atomicAdd(&A[(size_t)k * nbins + b], f * ck);
-            atomicAdd(&A[(size_t)(K + k) * nbins + b], f * sk);
-            const double cn = ck * c1 - sk * s1;
-            sk = sk * c1 + ck * s1;
-            ck = cn;
-        }
-        atomicAdd(&A[(size_t)(2 * K) * nbins + b], x);
-        if (local) atomicAdd(&s_cnt[b], 1u);
-        else atomicAdd(&cnt[b], 1ull);
-    }
-    if (local) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < nrow * nbins; t += blockDim.x)
-            if (s_acc[t] != 0.0) atomicAdd(&acc[t], s_acc[t]);
-        for (int t = threadIdx.x; t < nbins; t += blockDim.x)
-            if (s_cnt[t]) atomicAdd(&cnt[t], (unsigned long long)s_cnt[t]);
+        const int b = find_bin(edges, nbins, qa[p]);
+        bin_of[p] = b;
+        if (b >= 0) atomicAdd(&count[b], 1);
     }
 }
 
-// Ic/Is[k][b] = (2 - delta_k0) * sum / count; qmean[b]; NaN for empty bins
-__global__ void k_angspec_rings_finish(const double* __restrict__ acc, const unsigned long long* __restrict__ cnt,
-                                       int nbins, int kmax, double* __restrict__ Ic, double* __restrict__ Is,
-                                       int64_t* __restrict__ counts, double* __restrict__ qmean)
+// exclusive prefixes (one block): start[b] of the pixels, cursor[b] = start[b],
+// pstart[b] of the parts (pstart[nbins] = number of parts)
+__global__ void k_ang_offsets(const int32_t* __restrict__ count, int nbins, int32_t* __restrict__ start,
+                              int32_t* __restrict__ cursor, int32_t* __restrict__ pstart)
 {
-    const int K = kmax + 1;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)K * nbins) return;
-    const int k = (int)(t / nbins), b = (int)(t % nbins);
-    const unsigned long long n = cnt[b];
-    const double pref = k == 0 ? 1.0 : 2.0;
-    Ic[t] = n ? pref * acc[(size_t)k * nbins + b] / (double)n : nan("");
-    Is[t] = n ? pref * acc[(size_t)(K + k) * nbins + b] / (double)n : nan("");
-    if (k == 0) {
-        counts[b] = (int64_t)n;
-        qmean[b] = n ? acc[(size_t)(2 * K) * nbins + b] / (double)n : nan("");
+    __shared__ int32_t s_pix[1024];
+    __shared__ int32_t s_prt[1024];
+    const int per = (nbins + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per, b1 = min(nbins, b0 + per);
+    int32_t sp = 0, sq = 0;
+    for (int b = b0; b < b1; ++b) {
+        sp += count[b];
+        sq += (count[b] + ANG_PART - 1) / ANG_PART;
+    }
+    s_pix[threadIdx.x] = sp;
+    s_prt[threadIdx.x] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t rp = 0, rq = 0;
+        for (int t = 0; t < (int)blockDim.x; ++t) {
+            const int32_t vp = s_pix[t], vq = s_prt[t];
+            s_pix[t] = rp;
+            s_prt[t] = rq;
+            rp += vp;
+            rq += vq;
+        }
+        pstart[nbins] = rq;
+    }
+    __syncthreads();
+    int32_t rp = s_pix[threadIdx.x], rq = s_prt[threadIdx.x];
+    for (int b = b0; b < b1; ++b) {
+        start[b] = rp;
+        cursor[b] = rp;
+        pstart[b] = rq;
+        rp += count[b];
+        rq += (count[b] + ANG_PART - 1) / ANG_PART;
     }
 }
+
+__global__ void k_ang_scatter(const int32_t* __restrict__ bin_of, int64_t npix, int32_t* __restrict__ cursor,
+                              int32_t* __restrict__ perm)
+{
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+        const int b = bin_of[p];
+        if (b >= 0) perm[atomicAdd(&cursor[b], 1)] = (int32_t)p;
+    }
+}
+
+// one block per part: psum[part][r], r < K cos sums, K <= r < 2K sin sums,
+// r = 2K the |q| sum
+__global__ void __launch_bounds__(ANG_RED_THREADS)
+k_ang_parts(const double* __restrict__ img, const double* __restrict__ hy, const double* __restrict__ hz,
+            const double* __restrict__ qa, const int32_t* __restrict__ perm, const int32_t* __restrict__ start,
+            const int32_t* __restrict__ count, const int32_t* __restrict__ pstart, int nbins, int kmax,
+            double* __restrict__ psum)
+{
+    __shared__ double s_red[2 * ANG_KC + 1][ANG_RED_THREADS / 32];
+    const int part = blockIdx.x;
+    if (part >= pstart[nbins]) return;
+    // bin of this part: last b with pstart[b] <= part
+    int lo = 0, hi = nbins;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pstart[mid] <= part) lo = mid;
+        else hi = mid;
+    }
+    const int b = lo;
+    const int i0 = (part - pstart[b]) * ANG_PART;
+    const int n = min(ANG_PART, count[b] - i0);
+    const int32_t* idx = perm + start[b] + i0;
+    const int K = kmax + 1;
+    const int R = 2 * K + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = ANG_RED_THREADS / 32;
+    for (int k0 = 0; k0 < K; k0 += ANG_KC) {
+        double ac[ANG_KC], as[ANG_KC], aq = 0.0;
+#pragma unroll
+        for (int u = 0; u < ANG_KC; ++u) { ac[u] = 0.0; as[u] = 0.0; }
+        for (int i = threadIdx.x; i < n; i += ANG_RED_THREADS) {
+            const int p = idx[i];
+            const double f = img[p];
+            const double c1 = hz[p], s1 = hy[p];   // cos(theta), sin(theta)
+            // (cos, sin)(k0 theta) by binary powering of exp(i theta)
+            double ck = 1.0, sk = 0.0, bc = c1, bs = s1;
+            for (int e = k0; e; e >>= 1) {
+                if (e & 1) {
+                    const double t = ck * bc - sk * bs;
+                    sk = sk * bc + ck * bs;
+                    ck = t;
+                }
+                const double t = bc * bc - bs * bs;
+                bs = 2.0 * bc * bs;
+                bc = t;
+            }
+            const int nk = min(ANG_KC, K - k0);
+#pragma unroll
+            for (int u = 0; u < ANG_KC; ++u) {
+                if (u < nk) {
+                    ac[u] = fma(f, ck, ac[u]);
+                    as[u] = fma(f, sk, as[u]);
+                    const double t = ck * c1 - sk * s1;
+                    sk = sk * c1 + ck * s1;
+                    ck = t;
+                }
+            }
+            if (k0 == 0) aq += qa[p];
+        }
+#pragma unroll
+        for (int u = 0; u < ANG_KC; ++u) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                ac[u] += __shfl_xor_sync(0xffffffffu, ac[u], o);
+                as[u] += __shfl_xor_sync(0xffffffffu, as[u], o);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) aq += __shfl_xor_sync(0xffffffffu, aq, o);
+        __syncthreads();
+        if (lane == 0) {
+#pragma unroll
+            for (int u = 0; u < ANG_KC; ++u) {
+                s_red[u][warp] = ac[u];
+                s_red[ANG_KC + u][warp] = as[u];
+            }
+            s_red[2 * ANG_KC][warp] = aq;
+        }
+        __syncthreads();
+        if (threadIdx.x < 2 * ANG_KC + 1) {
+            double v = 0.0;
+            for (int w = 0; w < nw; ++w) v += s_red[threadIdx.x][w];
+            const int r = threadIdx.x;
+            double* out = psum + (int64_t)part * R;
+            if (r < 2 * ANG_KC) {
+                const int k = k0 + (r % ANG_KC);
+                if (k < K) out[r < ANG_KC ? k : K + k] = v;
+            } else if (k0 == 0) {
+                out[2 * K] = v;
+            }
+        }
+    }
+}
+
+// Ic/Is[k][b] = (2 - delta_k0) * (sum of the bin's parts, in order) / count;
+// counts, qmean; NaN for empty bins
+__global__ void k_ang_finish(const double* __restrict__ psum, const int32_t* __restrict__ count,
+                             const int32_t* __restrict__ pstart, int nbins, int kmax, double* __restrict__ Ic,
+                             double* __restrict__ Is, int64_t* __restrict__ counts, double* __restrict__ qmean)
+{
+    const int K = kmax + 1;
+    const int R = 2 * K + 1;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)R * nbins) return;
+    const int r = (int)(t / nbins), b = (int)(t % nbins);
+    const int n = count[b];
+    double v = 0.0;
+    for (int q = pstart[b]; q < pstart[b + 1]; ++q) v += psum[(int64_t)q * R + r];
+    if (r < 2 * K) {
+        const int k = r < K ? r : r - K;
+        const double out = n ? (k == 0 ? 1.0 : 2.0) * v / (double)n : nan("");
+        if (r < K) Ic[(int64_t)k * nbins + b] = out;
+        else Is[(int64_t)k * nbins + b] = out;
+    } else {
+        counts[b] = n;
+        qmean[b] = n ? v / (double)n : nan("");
+    }
+}
+
+static int64_t ang_max_parts(int64_t npix, int nbins) { return (npix + ANG_PART - 1) / ANG_PART + nbins; }
 
 cudaError_t launch_angspec_rings(const Plan& p, const double* img, const double* d_edges, int nbins, int kmax,
-                                 double* acc, unsigned long long* cnt, double* Ic, double* Is, int64_t* counts,
-                                 double* qmean, cudaStream_t s)
+                                 void* work, double* Ic, double* Is, int64_t* counts, double* qmean, cudaStream_t s)
 {
+    // work: part sums [max parts][2K+1] (FP64), then bin_of, perm [npix],
+    // count, start, cursor [nbins], pstart [nbins+1] (int32)
     const int K = kmax + 1;
-    const size_t smem = (size_t)(2 * K + 1) * nbins * sizeof(double) + (size_t)nbins * sizeof(unsigned int);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_angspec_rings, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)ANG_RING_MAX_SMEM);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    const bool local = smem <= ANG_RING_MAX_SMEM;
-    int64_t blocks = (p.npix + ANG_THREADS * 8 - 1) / (ANG_THREADS * 8);
-    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 2 * device_sm_count()));
-    k_angspec_rings<<<(unsigned)blocks, ANG_THREADS, local ? smem : 0, s>>>(img, p.d_hy, p.d_hz, p.d_qa, p.npix,
-                                                                             d_edges, nbins, kmax, local ? 1 : 0,
-                                                                             acc, cnt);
-    cudaError_t e = cudaGetLastError();
+    const int64_t mp = ang_max_parts(p.npix, nbins);
+    double* psum = (double*)work;
+    int32_t* bin_of = (int32_t*)(psum + mp * (2 * K + 1));
+    int32_t* perm = bin_of + p.npix;
+    int32_t* count = perm + p.npix;
+    int32_t* start = count + nbins;
+    int32_t* cursor = start + nbins;
+    int32_t* pstart = cursor + nbins;
+    cudaError_t e = cudaMemsetAsync(count, 0, (size_t)nbins * sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
-    const int64_t n = (int64_t)K * nbins;
-    k_angspec_rings_finish<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(acc, cnt, nbins, kmax, Ic, Is, counts, qmean);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((p.npix + 255) / 256, 8 * device_sm_count()));
+    k_ang_bins<<<blocks, 256, 0, s>>>(p.d_qa, p.npix, d_edges, nbins, bin_of, count);
+    k_ang_offsets<<<1, 1024, 0, s>>>(count, nbins, start, cursor, pstart);
+    k_ang_scatter<<<blocks, 256, 0, s>>>(bin_of, p.npix, cursor, perm);
+    k_ang_parts<<<(unsigned)mp, ANG_RED_THREADS, 0, s>>>(img, p.d_hy, p.d_hz, p.d_qa, perm, start, count, pstart,
+                                                        nbins, kmax, psum);
+    const int64_t nf = (int64_t)(2 * K + 1) * nbins;
+    k_ang_finish<<<(unsigned)((nf + 255) / 256), 256, 0, s>>>(psum, count, pstart, nbins, kmax, Ic, Is, counts, qmean);
     return cudaGetLastError();
+}
+
+size_t angspec_rings_work_bytes(int64_t npix, int nbins, int kmax)
+{
+    const int64_t mp = ang_max_parts(npix, nbins);
+    return (size_t)mp * (2 * (kmax + 1) + 1) * sizeof(double) + (size_t)(2 * npix + 4 * (int64_t)nbins + 1) * 4;
 }
 
 // ------------------------------------------------------------ modal amplitudes

@@ -12,6 +12,41 @@
 #include "nms.h"
 #include "nms_internal.h"
 
+#include <map>
+#include <mutex>
+
+// Stream-ordered scratch of the host-called helpers comes from a private
+// memory pool per device that keeps its memory on release: the default pool
+// hands freed memory back to the driver at every synchronisation, so each
+// call would map fresh pages again.
+static cudaError_t tmp_alloc(void** ptr, size_t bytes, cudaStream_t s)
+{
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = pools.find(dev);
+        if (it == pools.end()) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            e = cudaMemPoolCreate(&pool, &props);
+            if (e != cudaSuccess) return e;
+            uint64_t keep = 1ull << 30;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            pools[dev] = pool;
+        } else {
+            pool = it->second;
+        }
+    }
+    return cudaMallocFromPoolAsync(ptr, bytes > 0 ? bytes : 8, pool, s);
+}
+
 namespace nms {
 
 static thread_local std::string g_last_error;
@@ -495,7 +530,7 @@ nms_status nms_response(nms_plan_t plan, int32_t id, int32_t part, double* out, 
     double norm = 1.0 / (double)(p.rot_done > 0 ? p.rot_done : 1);
     double* dst = out;
     if (!out_is_device) {
-        NMS_CUDA_TRY(cudaMallocAsync((void**)&dst, p.npix * 8, p.stream));
+        NMS_CUDA_TRY(tmp_alloc((void**)&dst, p.npix * 8, p.stream));
     }
     cudaError_t e = launch_response(p, id, Ga, Gb, norm, dst, p.stream);
     if (e == cudaSuccess && !out_is_device)
@@ -524,7 +559,7 @@ cudaError_t stage(Staged& st, void* user, size_t bytes, bool user_is_device, cud
         return cudaSuccess;
     }
     st.copy_back = user != nullptr;
-    return cudaMallocAsync(&st.dev, bytes > 0 ? bytes : 8, s);
+    return tmp_alloc(&st.dev, bytes > 0 ? bytes : 8, s);
 }
 
 cudaError_t unstage(Staged& st, cudaStream_t s, cudaError_t e)
@@ -541,7 +576,7 @@ cudaError_t device_image(const Plan& p, const double* img, bool is_device, const
     *tmp = nullptr;
     *d_img = img;
     if (is_device) return cudaSuccess;
-    cudaError_t e = cudaMallocAsync((void**)tmp, p.npix * 8, p.stream);
+    cudaError_t e = tmp_alloc((void**)tmp, p.npix * 8, p.stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(*tmp, img, p.npix * 8, cudaMemcpyHostToDevice, p.stream);
     *d_img = *tmp;
     return e;
@@ -569,6 +604,7 @@ nms_status nms_azimuthal_average(nms_plan_t plan, const double* img, int32_t img
     if (!polar) {
         nms_status st = check_edges(nbins, bin_edges);
         if (st) return st;
+        if (p.npix >= (1ll << 31)) return fail(NMS_ERR_UNSUPPORTED, "more than 2^31 pixels");
     }
     const double* d_img = nullptr;
     double* tmp_img = nullptr;
@@ -583,21 +619,17 @@ nms_status nms_azimuthal_average(nms_plan_t plan, const double* img, int32_t img
         if (e == cudaSuccess) e = launch_polar_nodes(p, (int64_t*)sc.dev, (double*)sq.dev, s);
     } else {
         // ring means: the k = 0 mode of the ring-binned angular spectrum
-        double *d_e = nullptr, *acc = nullptr, *Is0 = nullptr;
-        unsigned long long* cnt = nullptr;
-        if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_e, (nbins + 1) * 8, s);
-        if (e == cudaSuccess) e = cudaMallocAsync((void**)&acc, (size_t)3 * nbins * 8, s);
-        if (e == cudaSuccess) e = cudaMallocAsync((void**)&cnt, (size_t)nbins * 8, s);
-        if (e == cudaSuccess) e = cudaMallocAsync((void**)&Is0, (size_t)nbins * 8, s);
+        double *d_e = nullptr, *Is0 = nullptr;
+        void* work = nullptr;
+        if (e == cudaSuccess) e = tmp_alloc((void**)&d_e, (nbins + 1) * 8, s);
+        if (e == cudaSuccess) e = tmp_alloc((void**)&work, angspec_rings_work_bytes(p.npix, nbins, 0), s);
+        if (e == cudaSuccess) e = tmp_alloc((void**)&Is0, (size_t)nbins * 8, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_e, bin_edges, (nbins + 1) * 8, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, (size_t)3 * nbins * 8, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, (size_t)nbins * 8, s);
         if (e == cudaSuccess)
-            e = launch_angspec_rings(p, d_img, d_e, nbins, 0, acc, cnt, (double*)sI.dev, Is0, (int64_t*)sc.dev,
+            e = launch_angspec_rings(p, d_img, d_e, nbins, 0, work, (double*)sI.dev, Is0, (int64_t*)sc.dev,
                                      (double*)sq.dev, s);
         cudaFreeAsync(d_e, s);
-        cudaFreeAsync(acc, s);
-        cudaFreeAsync(cnt, s);
+        cudaFreeAsync(work, s);
         cudaFreeAsync(Is0, s);
     }
     e = unstage(sI, s, e);
@@ -617,6 +649,7 @@ nms_status nms_angular_spectrum(nms_plan_t plan, const double* img, int32_t img_
     if (!plan || !img || !Ic || !Is) return fail(NMS_ERR_INVALID_ARG, "NULL argument");
     if (kmax < 0 || kmax > 1023) return fail(NMS_ERR_INVALID_ARG, "need 0 <= kmax <= 1023");
     Plan& p = *plan;
+    if (p.npix >= (1ll << 31)) return fail(NMS_ERR_UNSUPPORTED, "more than 2^31 pixels");
     cudaStream_t s = p.stream;
     const bool polar = p.grid.kind == NMS_QGRID_POLAR;
     if (polar) {
@@ -643,21 +676,16 @@ nms_status nms_angular_spectrum(nms_plan_t plan, const double* img, int32_t img_
         if (e == cudaSuccess) e = launch_angspec_polar(p, d_img, kmax, (double*)sIc.dev, (double*)sIs.dev, s);
         if (e == cudaSuccess) e = launch_polar_nodes(p, (int64_t*)sc.dev, (double*)sq.dev, s);
     } else {
-        double *d_e = nullptr, *acc = nullptr;
-        unsigned long long* cnt = nullptr;
-        const size_t nacc = (size_t)(2 * K + 1) * nbins;
-        if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_e, (nbins + 1) * 8, s);
-        if (e == cudaSuccess) e = cudaMallocAsync((void**)&acc, nacc * 8, s);
-        if (e == cudaSuccess) e = cudaMallocAsync((void**)&cnt, (size_t)nbins * 8, s);
+        double* d_e = nullptr;
+        void* work = nullptr;
+        if (e == cudaSuccess) e = tmp_alloc((void**)&d_e, (nbins + 1) * 8, s);
+        if (e == cudaSuccess) e = tmp_alloc((void**)&work, angspec_rings_work_bytes(p.npix, nbins, kmax), s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_e, bin_edges, (nbins + 1) * 8, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, nacc * 8, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, (size_t)nbins * 8, s);
         if (e == cudaSuccess)
-            e = launch_angspec_rings(p, d_img, d_e, nbins, kmax, acc, cnt, (double*)sIc.dev, (double*)sIs.dev,
+            e = launch_angspec_rings(p, d_img, d_e, nbins, kmax, work, (double*)sIc.dev, (double*)sIs.dev,
                                      (int64_t*)sc.dev, (double*)sq.dev, s);
         cudaFreeAsync(d_e, s);
-        cudaFreeAsync(acc, s);
-        cudaFreeAsync(cnt, s);
+        cudaFreeAsync(work, s);
     }
     if (e == cudaSuccess)
         e = launch_modal_amplitudes((double*)sIc.dev, (double*)sIs.dev, nbins, kmax, (double*)sAc.dev,
@@ -697,11 +725,11 @@ nms_status nms_correlation_2d(nms_plan_t plan, const double* img, int32_t img_is
     float* d_w = nullptr;
     float4* d_pts = nullptr;
     double2* d_part = nullptr;
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_rho, (size_t)n_rho * 8, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_alpha, (size_t)n_alpha * 8, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_w, (size_t)p.npix * 4, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_pts, (size_t)n_out * 16, s);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_part, (size_t)splits * n_out * 16, s);
+    if (e == cudaSuccess) e = tmp_alloc((void**)&d_rho, (size_t)n_rho * 8, s);
+    if (e == cudaSuccess) e = tmp_alloc((void**)&d_alpha, (size_t)n_alpha * 8, s);
+    if (e == cudaSuccess) e = tmp_alloc((void**)&d_w, (size_t)p.npix * 4, s);
+    if (e == cudaSuccess) e = tmp_alloc((void**)&d_pts, (size_t)n_out * 16, s);
+    if (e == cudaSuccess) e = tmp_alloc((void**)&d_part, (size_t)splits * n_out * 16, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_rho, rho, (size_t)n_rho * 8, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_alpha, alpha, (size_t)n_alpha * 8, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(sS.dev, 0, 8, s);
@@ -734,17 +762,17 @@ nms_status nms_correlation(int32_t nq, const double* q, const double* Iq, int32_
     int nqa = std::max(nq, 1);
     double *dq = nullptr, *dI = nullptr, *dr = nullptr, *dc = nullptr, *dp = nullptr, *sq = nullptr, *sf = nullptr;
     int* sn = nullptr;
-    NMS_CUDA_TRY(cudaMallocAsync((void**)&sq, nqa * 8, s));
-    NMS_CUDA_TRY(cudaMallocAsync((void**)&sf, nqa * 8, s));
-    NMS_CUDA_TRY(cudaMallocAsync((void**)&sn, sizeof(int), s));
+    NMS_CUDA_TRY(tmp_alloc((void**)&sq, nqa * 8, s));
+    NMS_CUDA_TRY(tmp_alloc((void**)&sf, nqa * 8, s));
+    NMS_CUDA_TRY(tmp_alloc((void**)&sn, sizeof(int), s));
     if (is_device) {
         dq = (double*)q; dI = (double*)Iq; dr = (double*)r; dc = c_r; dp = p_r;
     } else {
-        NMS_CUDA_TRY(cudaMallocAsync((void**)&dq, nqa * 8, s));
-        NMS_CUDA_TRY(cudaMallocAsync((void**)&dI, nqa * 8, s));
-        NMS_CUDA_TRY(cudaMallocAsync((void**)&dr, nr * 8, s));
-        NMS_CUDA_TRY(cudaMallocAsync((void**)&dc, nr * 8, s));
-        NMS_CUDA_TRY(cudaMallocAsync((void**)&dp, nr * 8, s));
+        NMS_CUDA_TRY(tmp_alloc((void**)&dq, nqa * 8, s));
+        NMS_CUDA_TRY(tmp_alloc((void**)&dI, nqa * 8, s));
+        NMS_CUDA_TRY(tmp_alloc((void**)&dr, nr * 8, s));
+        NMS_CUDA_TRY(tmp_alloc((void**)&dc, nr * 8, s));
+        NMS_CUDA_TRY(tmp_alloc((void**)&dp, nr * 8, s));
         if (nq) NMS_CUDA_TRY(cudaMemcpyAsync(dq, q, nq * 8, cudaMemcpyHostToDevice, s));
         if (nq) NMS_CUDA_TRY(cudaMemcpyAsync(dI, Iq, nq * 8, cudaMemcpyHostToDevice, s));
         NMS_CUDA_TRY(cudaMemcpyAsync(dr, r, nr * 8, cudaMemcpyHostToDevice, s));

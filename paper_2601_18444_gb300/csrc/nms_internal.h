@@ -128,8 +128,8 @@ cudaError_t launch_response(const Plan& p, int id, const double* Ga, const doubl
 cudaError_t launch_polar_nodes(const Plan& p, int64_t* counts, double* qmean, cudaStream_t s);
 cudaError_t launch_angspec_polar(const Plan& p, const double* img, int kmax, double* Ic, double* Is, cudaStream_t s);
 cudaError_t launch_angspec_rings(const Plan& p, const double* img, const double* d_edges, int nbins, int kmax,
-                                 double* acc, unsigned long long* cnt, double* Ic, double* Is, int64_t* counts,
-                                 double* qmean, cudaStream_t s);
+                                 void* work, double* Ic, double* Is, int64_t* counts, double* qmean, cudaStream_t s);
+size_t angspec_rings_work_bytes(int64_t npix, int nbins, int kmax);
 cudaError_t launch_modal_amplitudes(const double* Ic, const double* Is, int nb, int kmax, double* Ac, double* As,
                                     cudaStream_t s);
 cudaError_t launch_corr2d(const Plan& p, const double* img, const double* d_rho, int n_rho, const double* d_alpha,

@@ -265,6 +265,8 @@ def main():
     ap.add_argument("--workspace-gb", type=float, default=0.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--sets", type=int, default=1,
+                    help="loop mode: S magnetization states of the workload along a field sweep in one plan")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -279,17 +281,24 @@ def main():
     if args.workload == "post2d":
         return run_post2d(args, rank, world, dev)
     field, grid_kw, edges, r, desc, rot, dilute = make_workload(args.workload)
+    field0 = field
+    if args.sets > 1:
+        from paper_2601_18444_gb300 import inputs as I
+        nuc_s, mag_s = I.field_sweep(field, np.linspace(0.0, 2.0, args.sets))
+        field0 = I.Field(field.pos, field.vol, nuc_s[0], mag_s[0], field.offsets, field.centers, field.name)
+        field = I.Field(field.pos, field.vol, nuc_s, mag_s, field.offsets, field.centers, field.name)
+        desc += f"; loop mode: {args.sets} magnetization states (field sweep h = 0..2) in one plan"
     prec = {"auto": nms.PREC_AUTO, "tc": nms.PREC_TC_F16X3, "direct": nms.PREC_FP32_DIRECT,
             "naive": nms.PREC_FP32_NAIVE}[args.precision]
     stream = torch.cuda.current_stream()
     g = nms.make_grid(**grid_kw)
     opt = nms.nms_options_default(precision=prec, timing=1, kc_cells=args.kc, want_dilute=1 if dilute else 0,
-                                  workspace_bytes=int(args.workspace_gb * (1 << 30)))
+                                  workspace_bytes=int(args.workspace_gb * (1 << 30)), n_sets=max(1, args.sets))
     plan = nms.plan_from_field(field, g, opt, rot=rot, stream=stream.cuda_stream)
     npix = plan.npix
     n_rot = 1 if rot is None else len(rot)
     # with the dilute split the per-object form factors are the summed terms
-    terms = float(field.n) * npix * n_rot
+    terms = float(field.n) * npix * n_rot * max(1, args.sets)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     img_u = torch.empty(npix, dtype=torch.float64, device="cuda")
     img_s = torch.empty(npix, dtype=torch.float64, device="cuda")
@@ -338,7 +347,7 @@ def main():
         achieved = terms * TC_FLOPS_PER_TERM / (k_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops", 1900.0)
         traffic = None
-        if TC_DRAM_PER_TABLE_BYTE and args.workload in TC_TRAFFIC_WORKLOADS:
+        if TC_DRAM_PER_TABLE_BYTE and args.workload in TC_TRAFFIC_WORKLOADS and args.sets <= 1:
             traffic = TC_DRAM_PER_TABLE_BYTE * table_bytes(field, grid_kw, n_rot) / (stage["gemm"][1] / args.steps)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
@@ -358,10 +367,10 @@ def main():
     err = None
     if rank == 0 and not args.no_cpu_baseline:
         R_last = np.eye(3) if rot is None else rot[-1]
-        rate, sample, F_ref, idx, cores = oracle_sample_rate(field, grid_kw, args.cpu_seconds, R=R_last)
-        F = nms.nms_get_amplitudes(plan)
+        rate, sample, F_ref, idx, cores = oracle_sample_rate(field0, grid_kw, args.cpu_seconds, R=R_last)
+        F = nms.nms_get_amplitudes(plan)       # weight set 0
         from oracle import sans as S
-        wsum = np.abs(S.cell_weights(field.vol, field.nuc, field.mag, R_last)).sum(1)
+        wsum = np.abs(S.cell_weights(field0.vol, field0.nuc, field0.mag, R_last)).sum(1)
         err = [float(np.max(np.abs(F[c][idx] - F_ref[c])) / wsum[c]) if wsum[c] > 0 else 0.0 for c in range(4)]
         cpu = {"value": rate, "unit": "terms/s", "cores": cores, "kind": "oracle", "sample": sample}
 

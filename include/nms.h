@@ -104,7 +104,14 @@ typedef struct {
                                 compensated direct sum) is <= 3e-7 of sum|w|;
                                 cached per shape and device (file
                                 $NMS_AUTOTUNE_CACHE if set)                    */
-    int32_t reserved[6];
+    int32_t n_sets;          /* weight sets S (loop mode: e.g. one magnetization
+                                state per applied field) over the same cells,
+                                objects and orientations; nuc and mag then hold
+                                S sets ([S][n], [S][n][3]).  0 -> 1.  Tensor
+                                path: S <= 32, stacked along the GEMM rows so
+                                every q_z table block serves all sets; results
+                                per set via nms_select_set.                    */
+    int32_t reserved[5];
 } nms_options;
 
 /* Fill *opt with the defaults above. */
@@ -118,8 +125,10 @@ nms_status nms_options_default(nms_options* opt);
  *   n_cells         W >= 1 total cells.
  *   pos             host [n_cells][3] local cell coordinates x^{kl}.
  *   cell_vol        host [n_cells] cell volumes V_j, or NULL for all 1.
- *   nuc             host [n_cells] nuclear density N_j, or NULL (channel off).
- *   mag             host [n_cells][3] magnetization M_j, or NULL (off).
+ *   nuc             host [n_cells] nuclear density N_j, or NULL (channel off);
+ *                   [S][n_cells] with opt->n_sets = S > 1.
+ *   mag             host [n_cells][3] magnetization M_j, or NULL (off);
+ *                   [S][n_cells][3] with S weight sets.
  *   n_objects       K >= 1.
  *   object_offsets  host [K+1], 0 = off_0 <= ... <= off_K = n_cells (empty
  *                   objects allowed), or NULL when K == 1.
@@ -360,6 +369,13 @@ nms_status nms_dsft_direct_noalloc(int64_t n_cells, const double* Y, const doubl
  * otherwise), after autotuning when it was requested.  Any pointer may be
  * NULL. */
 nms_status nms_plan_info(nms_plan_t plan, int32_t* precision, int32_t* kc_cells, int32_t* items_per_sm);
+
+/* Loop mode (paper, Sec. "Program description": batch runs over field-,
+ * temperature- or time-dependent data sets of one geometry): select which
+ * weight set 0 <= set < n_sets subsequent nms_get_amplitudes and
+ * nms_response calls report.  The default is set 0.  The Fourier sums of
+ * all sets are computed by each nms_amplitudes call. */
+nms_status nms_select_set(nms_plan_t plan, int32_t set);
 
 /* Release every device resource of the plan.  NULL is accepted. */
 nms_status nms_plan_destroy(nms_plan_t plan);

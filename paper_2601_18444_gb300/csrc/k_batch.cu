@@ -27,11 +27,12 @@ __device__ __forceinline__ float4 split_pos(double y, double z)
 }
 
 // Rotated positions (global R(x + r^k) or local R x) and rotated weights of
-// one rotation, written at the given offset of the stacked arrays.
-__global__ void k_prep_rot(int64_t n, const double* __restrict__ pos, const double* __restrict__ vol,
-                           const double* __restrict__ nuc, const double* __restrict__ mag,
-                           const double* __restrict__ cen_cell, RotMat R, float4* __restrict__ cpos,
-                           float4* __restrict__ cw)
+// one rotation, written at the given offset of the stacked arrays; weights
+// of weight set s (nuc [S][n], mag [S][n][3]) go to cw[s * wstride + j].
+__global__ void k_prep_rot(int64_t n, int n_sets, int64_t wstride, const double* __restrict__ pos,
+                           const double* __restrict__ vol, const double* __restrict__ nuc,
+                           const double* __restrict__ mag, const double* __restrict__ cen_cell, RotMat R,
+                           float4* __restrict__ cpos, float4* __restrict__ cw)
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
@@ -44,21 +45,25 @@ __global__ void k_prep_rot(int64_t n, const double* __restrict__ pos, const doub
     const double* r = R.m;
     cpos[j] = split_pos(r[3] * x + r[4] * y + r[5] * z, r[6] * x + r[7] * y + r[8] * z);
     const double v = vol ? vol[j] : 1.0;
-    const double wn = nuc ? v * nuc[j] : 0.0;
-    double wx = 0.0, wy = 0.0, wz = 0.0;
-    if (mag) {
-        const double mx = mag[3 * j], my = mag[3 * j + 1], mz = mag[3 * j + 2];
-        wx = v * (r[0] * mx + r[1] * my + r[2] * mz);
-        wy = v * (r[3] * mx + r[4] * my + r[5] * mz);
-        wz = v * (r[6] * mx + r[7] * my + r[8] * mz);
+    for (int st = 0; st < n_sets; ++st) {
+        const int64_t js = (int64_t)st * n + j;
+        const double wn = nuc ? v * nuc[js] : 0.0;
+        double wx = 0.0, wy = 0.0, wz = 0.0;
+        if (mag) {
+            const double mx = mag[3 * js], my = mag[3 * js + 1], mz = mag[3 * js + 2];
+            wx = v * (r[0] * mx + r[1] * my + r[2] * mz);
+            wy = v * (r[3] * mx + r[4] * my + r[5] * mz);
+            wz = v * (r[6] * mx + r[7] * my + r[8] * mz);
+        }
+        cw[(int64_t)st * wstride + j] = make_float4((float)wn, (float)wx, (float)wy, (float)wz);
     }
-    cw[j] = make_float4((float)wn, (float)wx, (float)wy, (float)wz);
 }
 
-cudaError_t launch_prep_rot(const Plan& p, const RotMat& R, bool global, float4* cpos, float4* cw, cudaStream_t s)
+cudaError_t launch_prep_rot(const Plan& p, const RotMat& R, bool global, float4* cpos, float4* cw, int64_t wstride,
+                            cudaStream_t s)
 {
     const int64_t n = p.n_cells;
-    k_prep_rot<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, p.d_pos, p.d_vol, p.d_nuc, p.d_mag,
+    k_prep_rot<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, p.n_sets, wstride, p.d_pos, p.d_vol, p.d_nuc, p.d_mag,
                                                            global ? p.d_cen_cell : nullptr, R, cpos, cw);
     return cudaGetLastError();
 }
@@ -95,8 +100,10 @@ __device__ __forceinline__ int pair_idx(int a, int b)  // a < b
     return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
 }
 
-// G[16][npix] += sum_o F_o F_o^dagger (F: [n_out][4][npix] complex FP64).
-__global__ void k_gacc_batch(const double2* __restrict__ F, int n_out, int64_t npix, double* __restrict__ G)
+// G[16][npix] += sum_o F_o F_o^dagger (F_o: [4][npix] complex FP64 at
+// F + o * ostride doubles).
+__global__ void k_gacc_batch(const double2* __restrict__ F, int n_out, int64_t ostride2, int64_t npix,
+                             double* __restrict__ G)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npix) return;
@@ -107,7 +114,7 @@ __global__ void k_gacc_batch(const double2* __restrict__ F, int n_out, int64_t n
         float2 f[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const double2 v = F[((int64_t)o * 4 + c) * npix + p];
+            const double2 v = F[(int64_t)o * ostride2 + (int64_t)c * npix + p];
             f[c] = make_float2((float)v.x, (float)v.y);
         }
 #pragma unroll
@@ -125,10 +132,11 @@ __global__ void k_gacc_batch(const double2* __restrict__ F, int n_out, int64_t n
     for (int k = 0; k < 16; ++k) G[(int64_t)k * npix + p] += (double)hi[k] + (double)lo[k];
 }
 
-cudaError_t launch_gacc_batch(const double* F, int n_out, int64_t npix, double* G, cudaStream_t s)
+cudaError_t launch_gacc_batch(const double* F, int n_out, int64_t ostride, int64_t npix, double* G, cudaStream_t s)
 {
     if (n_out <= 0) return cudaSuccess;
-    k_gacc_batch<<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(reinterpret_cast<const double2*>(F), n_out, npix, G);
+    k_gacc_batch<<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(reinterpret_cast<const double2*>(F), n_out,
+                                                                ostride / 2, npix, G);
     return cudaGetLastError();
 }
 
@@ -140,16 +148,17 @@ cudaError_t launch_gacc_batch(const double* F, int n_out, int64_t npix, double* 
 // two-float shifted sums to FP64 once per rotation.  The next output's
 // amplitudes are loaded while the current one is processed, so each thread
 // keeps two outputs' loads in flight.
-__device__ __forceinline__ void load_f(const double2* __restrict__ F, int64_t o, int64_t npix, int64_t p, double2* v)
+__device__ __forceinline__ void load_f(const double2* __restrict__ F, int64_t o, int64_t ostride2, int64_t npix,
+                                       int64_t p, double2* v)
 {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) v[c] = F[(o * 4 + c) * npix + p];
+    for (int c = 0; c < 4; ++c) v[c] = F[o * ostride2 + (int64_t)c * npix + p];
 }
 
 __global__ void __launch_bounds__(128)
-k_dilute_shift_batch(const double2* __restrict__ F, int n_out, const float4* __restrict__ cyz,
+k_dilute_shift_batch(const double2* __restrict__ F, int n_out, int64_t ostride2, const float4* __restrict__ cyz,
                      const int32_t* __restrict__ out_rot, const float4* __restrict__ qturn, int64_t npix,
-                     double* __restrict__ Gdil, double2* __restrict__ Ftot)
+                     double* __restrict__ Gdil, double2* __restrict__ Ftot, int64_t tstride2)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npix || n_out <= 0) return;
@@ -160,18 +169,18 @@ k_dilute_shift_batch(const double2* __restrict__ F, int n_out, const float4* __r
 #pragma unroll
     for (int k = 0; k < 8; ++k) { th[k] = 0.f; tl[k] = 0.f; }
     double2 nxt[4];
-    load_f(F, 0, npix, p, nxt);
+    load_f(F, 0, ostride2, npix, p, nxt);
     int cur = out_rot[0];
     for (int o = 0; o < n_out; ++o) {
         float2 f[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) f[c] = make_float2((float)nxt[c].x, (float)nxt[c].y);
-        if (o + 1 < n_out) load_f(F, o + 1, npix, p, nxt);
+        if (o + 1 < n_out) load_f(F, o + 1, ostride2, npix, p, nxt);
         const int r = out_rot[o];
         if (r != cur) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                double2* t = Ftot + ((int64_t)cur * 4 + c) * npix + p;
+                double2* t = Ftot + (int64_t)cur * tstride2 + (int64_t)c * npix + p;
                 double2 v = *t;
                 v.x += (double)th[2 * c] + (double)tl[2 * c];
                 v.y += (double)th[2 * c + 1] + (double)tl[2 * c + 1];
@@ -212,7 +221,7 @@ k_dilute_shift_batch(const double2* __restrict__ F, int n_out, const float4* __r
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        double2* t = Ftot + ((int64_t)cur * 4 + c) * npix + p;
+        double2* t = Ftot + (int64_t)cur * tstride2 + (int64_t)c * npix + p;
         double2 v = *t;
         v.x += (double)th[2 * c] + (double)tl[2 * c];
         v.y += (double)th[2 * c + 1] + (double)tl[2 * c + 1];
@@ -222,12 +231,14 @@ k_dilute_shift_batch(const double2* __restrict__ F, int n_out, const float4* __r
     for (int k = 0; k < 16; ++k) Gdil[(int64_t)k * npix + p] += (double)gh[k] + (double)gl[k];
 }
 
-cudaError_t launch_dilute_shift_batch(const double* F, int n_out, const float4* cyz, const int32_t* out_rot,
-                                      const float4* qturn, int64_t npix, double* Gdil, double* Ftot, cudaStream_t s)
+cudaError_t launch_dilute_shift_batch(const double* F, int n_out, int64_t ostride, const float4* cyz,
+                                      const int32_t* out_rot, const float4* qturn, int64_t npix, double* Gdil,
+                                      double* Ftot, int64_t tstride, cudaStream_t s)
 {
     if (n_out <= 0) return cudaSuccess;
     k_dilute_shift_batch<<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(
-        reinterpret_cast<const double2*>(F), n_out, cyz, out_rot, qturn, npix, Gdil, reinterpret_cast<double2*>(Ftot));
+        reinterpret_cast<const double2*>(F), n_out, ostride / 2, cyz, out_rot, qturn, npix, Gdil,
+        reinterpret_cast<double2*>(Ftot), tstride / 2);
     return cudaGetLastError();
 }
 

@@ -76,12 +76,15 @@ __global__ void k_prep(int64_t n, const double* __restrict__ pos, const double* 
     }
 }
 
-cudaError_t launch_prep(Plan& p, const double* R, cudaStream_t s)
+cudaError_t launch_prep(Plan& p, const double* R, cudaStream_t s, int set)
 {
     int64_t n = p.n_cells;
     int th = 256;
     int64_t bl = (n + th - 1) / th;
-    k_prep<<<(unsigned)bl, th, 0, s>>>(n, p.d_pos, p.d_vol, p.d_nuc, p.d_mag, p.d_cen_cell, R[0], R[1], R[2],
+    // weight set `set` of nuc [S][n] and mag [S][n][3]
+    const double* nuc = p.d_nuc ? p.d_nuc + (size_t)set * n : nullptr;
+    const double* mag = p.d_mag ? p.d_mag + (size_t)set * 3 * n : nullptr;
+    k_prep<<<(unsigned)bl, th, 0, s>>>(n, p.d_pos, p.d_vol, nuc, mag, p.d_cen_cell, R[0], R[1], R[2],
                                        R[3], R[4], R[5], R[6], R[7], R[8], p.d_cpos,
                                        p.d_cposl != p.d_cpos ? p.d_cposl : nullptr, p.d_cw, p.d_yz,
                                        p.d_yzl != p.d_yz ? p.d_yzl : nullptr, p.d_w64);

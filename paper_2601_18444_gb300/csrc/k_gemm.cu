@@ -90,18 +90,23 @@ __device__ __forceinline__ void split_h2(float x0, float x1, uint32_t& h, uint32
 // odd-symmetric, so the split of a negated value is the negated split
 __device__ __forceinline__ uint32_t swap_neg_h2(uint32_t w) { return __byte_perm(w, 0, 0x1032) ^ 0x80000000u; }
 
-// A tables: block (mt, kb) holds rows m = mt*128 + 4*a_loc + c, a_loc < 32,
-// and k = 2 j_loc + p.  Thread (a_loc, chunk): 4 cells x 4 channels.
+// A tables: block (mt, kb) holds rows m = mt*128 + r, r < 128, with
+// m = a * nch + c (q_y index a, channel c = 4 * set + {N, Mx, My, Mz}) and
+// k = 2 j_loc + p.  Thread (g, chunk): the 4 rows 4g..4g+3 (one set, one a;
+// nch is a multiple of 4) for 4 cells.  Weight set st of cell j is
+// cw[st * wstride + j].
 __global__ void __launch_bounds__(256)
-k_tables_a(const float4* __restrict__ cpos, const float4* __restrict__ cw, const int64_t* __restrict__ kb_cell0,
-           const int32_t* __restrict__ kb_ncell, const float2* __restrict__ qy, int ny, float4 wscale, int64_t nkb,
-           uint8_t* __restrict__ A_hi, uint8_t* __restrict__ A_lo)
+k_tables_a(const float4* __restrict__ cpos, const float4* __restrict__ cw, int64_t wstride, int nch,
+           const int64_t* __restrict__ kb_cell0, const int32_t* __restrict__ kb_ncell, const float2* __restrict__ qy,
+           int ny, float4 wscale, int64_t nkb, uint8_t* __restrict__ A_hi, uint8_t* __restrict__ A_lo)
 {
     const int64_t kb = blockIdx.x;
     const int mt = blockIdx.y;
-    const int a_loc = threadIdx.x >> 3;
+    const int g = threadIdx.x >> 3;
     const int chunk = threadIdx.x & 7;
-    const int a = mt * 32 + a_loc;
+    const int m0 = mt * TC_BM + 4 * g;
+    const int a = m0 / nch;
+    const int st = (m0 % nch) >> 2;
     const int64_t c0 = kb_cell0[kb];
     const int nc = kb_ncell[kb];
     uint4 hi[4], lo[4];
@@ -109,6 +114,7 @@ k_tables_a(const float4* __restrict__ cpos, const float4* __restrict__ cw, const
     uint32_t* lw = reinterpret_cast<uint32_t*>(lo);
     const bool arow = a < ny;
     const float2 q = arow ? qy[a] : make_float2(0.f, 0.f);
+    const float4* wset = cw + (int64_t)st * wstride;
     // all loads of this thread's 4 cells first, then the arithmetic
     float4 cp[4], w[4];
 #pragma unroll
@@ -116,7 +122,7 @@ k_tables_a(const float4* __restrict__ cpos, const float4* __restrict__ cw, const
         const int jl = chunk * 4 + u;
         const bool live = arow && jl < nc;
         cp[u] = live ? cpos[c0 + jl] : make_float4(0.f, 0.f, 0.f, 0.f);
-        w[u] = live ? cw[c0 + jl] : make_float4(0.f, 0.f, 0.f, 0.f);
+        w[u] = live ? wset[c0 + jl] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -129,7 +135,7 @@ k_tables_a(const float4* __restrict__ cpos, const float4* __restrict__ cw, const
     const size_t blk = ((size_t)mt * nkb + kb) * TC_BLOCK_BYTES;
 #pragma unroll
     for (int ch = 0; ch < 4; ++ch) {
-        const int row = 4 * a_loc + ch;
+        const int row = 4 * g + ch;
         const uint32_t off = swz_offset(row, chunk * 8);
         *reinterpret_cast<uint4*>(A_hi + blk + off) = hi[ch];
         *reinterpret_cast<uint4*>(A_lo + blk + off) = lo[ch];
@@ -532,8 +538,9 @@ struct GemmArgs {
     int n_items;
     int kcb;              // k-blocks per TMEM chunk (drain interval)
     double* P;            // [slots][128][128]
-    double* F;            // direct outputs: [out][4][ny*nz] complex (re, im)
+    double* F;            // direct outputs: [out][nch][ny*nz] complex (re, im)
     int ny, nz;
+    int nch;              // channels per output (4 per weight set), a power of two
     double scale[4];      // direct outputs: per-channel scale of the unscaled sums
     int32_t* err;
     uint64_t limit_ns;
@@ -820,13 +827,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
                 const int mtile = MODE == 2 ? 2 * item.mt + rank : item.mt;
                 const int ntile = MODE == 1 ? 2 * item.nt + rank : item.nt;
                 const int m = mtile * TC_BM + quad * 32 + lane;
-                const int a = m >> 2, ch = m & 3;
+                const int a = m / g.nch, ch = m & (g.nch - 1);
                 const int b0 = (ntile * TC_BN + colh) >> 1;
                 if (a < g.ny) {
                     const int64_t npix = (int64_t)g.ny * g.nz;
-                    double2* o = reinterpret_cast<double2*>(g.F) + ((int64_t)(-1 - slot) * 4 + ch) * npix +
+                    double2* o = reinterpret_cast<double2*>(g.F) + ((int64_t)(-1 - slot) * g.nch + ch) * npix +
                                  (int64_t)a * g.nz + b0;
-                    const double sc = ch == 0 ? g.scale[0] : ch == 1 ? g.scale[1] : ch == 2 ? g.scale[2] : g.scale[3];
+                    const int c4 = ch & 3;
+                    const double sc = c4 == 0 ? g.scale[0] : c4 == 1 ? g.scale[1] : c4 == 2 ? g.scale[2] : g.scale[3];
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         if (b0 + i < g.nz) {
@@ -848,8 +856,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
 }
 
 // Reduction of item tiles into per-output amplitudes:
-//   F[out][c][p][r] += scale_c * sum_{s < splits} P[slot_base + (mt*ntiles + nt)*splits + s][row][col]
-// with m = 4a + c = mt*128 + row, n = 2b + r = nt*128 + col, p = a*nz + b.
+//   F[out][c][p][r] += scale_{c mod 4} * sum_{s < splits} P[slot_base + (mt*ntiles + nt)*splits + s][row][col]
+// with m = nch*a + c = mt*128 + row, n = 2b + r = nt*128 + col, p = a*nz + b.
 struct RedDesc {
     int32_t slot_base;
     int32_t splits;
@@ -862,17 +870,17 @@ struct Scale4 {
 };
 
 __global__ void k_gemm_reduce(const double* __restrict__ P, const RedDesc* __restrict__ reds, int n_red, int ny,
-                              int nz, int ntiles, Scale4 scale, double* __restrict__ F)
+                              int nz, int ntiles, int nch, Scale4 scale, double* __restrict__ F)
 {
     const int64_t npix = (int64_t)ny * nz;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)n_red * 4 * npix) return;
-    const int r = (int)(idx / (4 * npix));
-    const int64_t rem = idx % (4 * npix);
+    if (idx >= (int64_t)n_red * nch * npix) return;
+    const int r = (int)(idx / (nch * npix));
+    const int64_t rem = idx % (nch * npix);
     const int c = (int)(rem / npix);
     const int64_t p = rem % npix;
     const int a = (int)(p / nz), b = (int)(p % nz);
-    const int m = 4 * a + c, n = 2 * b;
+    const int m = nch * a + c, n = 2 * b;
     const int mt = m >> 7, row = m & 127, nt = n >> 7, col = n & 127;
     const RedDesc d = reds[r];
     const int64_t base = (int64_t)d.slot_base + (int64_t)(mt * ntiles + nt) * d.splits;
@@ -882,32 +890,33 @@ __global__ void k_gemm_reduce(const double* __restrict__ P, const RedDesc* __res
         re += v.x;
         im += v.y;
     }
-    double2* o = reinterpret_cast<double2*>(F) + ((int64_t)d.out * 4 + c) * npix + p;
+    double2* o = reinterpret_cast<double2*>(F) + ((int64_t)d.out * nch + c) * npix + p;
     double2 t = *o;
-    t.x += scale.v[c] * re;
-    t.y += scale.v[c] * im;
+    t.x += scale.v[c & 3] * re;
+    t.y += scale.v[c & 3] * im;
     *o = t;
 }
 
 // ------------------------------------------------------------------ launchers
-cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, const int64_t* kb_cell0, const int32_t* kb_ncell,
-                             int64_t nkb, const float2* qy, int ny, const float2* qz, int nz, int mtiles, int ntiles,
-                             const float wscale[4], void* tab, cudaStream_t s)
+cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, int64_t wstride, int nch, const int64_t* kb_cell0,
+                             const int32_t* kb_ncell, int64_t nkb, const float2* qy, int ny, const float2* qz, int nz,
+                             int mtiles, int ntiles, const float wscale[4], void* tab, cudaStream_t s)
 {
     uint8_t* A_hi = (uint8_t*)tab;
     uint8_t* A_lo = A_hi + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
     uint8_t* B_hi = A_lo + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
     uint8_t* B_lo = B_hi + (size_t)ntiles * nkb * TC_BLOCK_BYTES;
     k_tables_a<<<dim3((unsigned)nkb, (unsigned)mtiles), 256, 0, s>>>(
-        cpos, cw, kb_cell0, kb_ncell, qy, ny, make_float4(wscale[0], wscale[1], wscale[2], wscale[3]), nkb, A_hi, A_lo);
+        cpos, cw, wstride, nch, kb_cell0, kb_ncell, qy, ny, make_float4(wscale[0], wscale[1], wscale[2], wscale[3]),
+        nkb, A_hi, A_lo);
     k_tables_b<<<dim3((unsigned)nkb, (unsigned)ntiles), 512, 0, s>>>(cpos, kb_cell0, kb_ncell, qz, nz, nkb, B_hi,
                                                                      B_lo);
     return cudaGetLastError();
 }
 
 cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
-                           int grid, int kcb, double* P, double* F, int ny, int nz, const double scale[4], int32_t* err,
-                           uint64_t limit_ns, int mode, cudaStream_t s)
+                           int grid, int kcb, double* P, double* F, int ny, int nz, int nch, const double scale[4],
+                           int32_t* err, uint64_t limit_ns, int mode, cudaStream_t s)
 {
     static_assert(GemmCfg<0>::STAGES * GemmCfg<0>::STAGE_BYTES == GemmCfg<2>::STAGES * GemmCfg<2>::STAGE_BYTES,
                   "one dynamic shared-memory size for every mode");
@@ -936,6 +945,7 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
     ga.F = F;
     ga.ny = ny;
     ga.nz = nz;
+    ga.nch = nch;
     for (int c = 0; c < 4; ++c) ga.scale[c] = scale[c];
     ga.err = err;
     ga.limit_ns = limit_ns;
@@ -958,14 +968,15 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
     return mode == 1 ? cudaLaunchKernelEx(&cfg, k_gemm_f16x3<1>, ga) : cudaLaunchKernelEx(&cfg, k_gemm_f16x3<2>, ga);
 }
 
-cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, int ny, int nz, int ntiles,
+cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, int ny, int nz, int ntiles, int nch,
                              const double scale[4], double* F, cudaStream_t s)
 {
     Scale4 sc;
     for (int c = 0; c < 4; ++c) sc.v[c] = scale[c];
-    const int64_t n = (int64_t)n_red * 4 * ny * nz;
+    const int64_t n = (int64_t)n_red * nch * ny * nz;
     if (n == 0) return cudaSuccess;   // every item of the chunk wrote its output directly
-    k_gemm_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, (const RedDesc*)reds, n_red, ny, nz, ntiles, sc, F);
+    k_gemm_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, (const RedDesc*)reds, n_red, ny, nz, ntiles, nch, sc,
+                                                              F);
     return cudaGetLastError();
 }
 

@@ -335,6 +335,7 @@ nms_status nms_plan_create(nms_plan_t* out, int64_t n_cells, const double* pos, 
     p->n_cells = n_cells;
     p->n_objects = n_objects;
     p->n_rot = n_rot;
+    p->n_sets = p->opt.n_sets > 0 ? p->opt.n_sets : 1;
     p->V = p->opt.volume_V > 0 ? p->opt.volume_V : 1.0;
     p->bH = p->opt.b_H != 0 ? p->opt.b_H : 1.0;
     double pn = sqrt(p->opt.P[0] * p->opt.P[0] + p->opt.P[1] * p->opt.P[1] + p->opt.P[2] * p->opt.P[2]);
@@ -353,6 +354,8 @@ nms_status nms_plan_create(nms_plan_t* out, int64_t n_cells, const double* pos, 
         return bail(fail(NMS_ERR_INVALID_ARG, "the tensor-core path needs a CARTESIAN (separable) grid"));
     if (prec == NMS_PREC_AUTO) prec = grid->kind == NMS_QGRID_CARTESIAN ? NMS_PREC_TC_F16X3 : NMS_PREC_FP32_DIRECT;
     p->path = prec;
+    if (p->n_sets > 4096 || (prec == NMS_PREC_TC_F16X3 && p->n_sets > 32))
+        return bail(fail(NMS_ERR_INVALID_ARG, "n_sets above 32 (tensor path) or 4096"));
 
     // offsets
     p->h_off.resize(n_objects + 1);
@@ -379,6 +382,7 @@ nms_status nms_plan_create(nms_plan_t* out, int64_t n_cells, const double* pos, 
 
     // inputs to the device
     const int64_t n = n_cells;
+    const int64_t nS = p->n_sets;
     if ((st = dalloc(&p->d_pos, 3 * n, "pos"))) return bail(st);
     NMS_CUDA_TRY(cudaMemcpy(p->d_pos, pos, 3 * n * 8, cudaMemcpyHostToDevice));
     if (cell_vol) {
@@ -386,12 +390,12 @@ nms_status nms_plan_create(nms_plan_t* out, int64_t n_cells, const double* pos, 
         NMS_CUDA_TRY(cudaMemcpy(p->d_vol, cell_vol, n * 8, cudaMemcpyHostToDevice));
     }
     if (nuc) {
-        if ((st = dalloc(&p->d_nuc, n, "nuc"))) return bail(st);
-        NMS_CUDA_TRY(cudaMemcpy(p->d_nuc, nuc, n * 8, cudaMemcpyHostToDevice));
+        if ((st = dalloc(&p->d_nuc, nS * n, "nuc"))) return bail(st);
+        NMS_CUDA_TRY(cudaMemcpy(p->d_nuc, nuc, nS * n * 8, cudaMemcpyHostToDevice));
     }
     if (mag) {
-        if ((st = dalloc(&p->d_mag, 3 * n, "mag"))) return bail(st);
-        NMS_CUDA_TRY(cudaMemcpy(p->d_mag, mag, 3 * n * 8, cudaMemcpyHostToDevice));
+        if ((st = dalloc(&p->d_mag, 3 * nS * n, "mag"))) return bail(st);
+        NMS_CUDA_TRY(cudaMemcpy(p->d_mag, mag, 3 * nS * n * 8, cudaMemcpyHostToDevice));
     }
     if (object_centers) {
         std::vector<double> cc((size_t)3 * n);
@@ -411,21 +415,22 @@ nms_status nms_plan_create(nms_plan_t* out, int64_t n_cells, const double* pos, 
     }
     const int64_t np = p->npix;
     p->fpart_splits = std::max<int64_t>(1, std::min<int64_t>(64, (int64_t)(256ll << 20) / (64 * np)));
-    if ((st = dalloc(&p->d_F, 8 * np, "F")) || (st = dalloc(&p->d_Fpart, 8 * np * p->fpart_splits, "Fpart")) ||
-        (st = dalloc(&p->d_Gtot, 16 * np, "Gtot")) || (st = dalloc(&p->d_err, 1, "err")))
+    if ((st = dalloc(&p->d_F, nS * 8 * np, "F")) || (st = dalloc(&p->d_Fpart, 8 * np * p->fpart_splits, "Fpart")) ||
+        (st = dalloc(&p->d_Gtot, nS * 16 * np, "Gtot")) || (st = dalloc(&p->d_err, 1, "err")))
         return bail(st);
     if (p->opt.want_dilute) {
-        if ((st = dalloc(&p->d_Gdil, 16 * np, "Gdil"))) return bail(st);
+        if ((st = dalloc(&p->d_Gdil, nS * 16 * np, "Gdil"))) return bail(st);
     }
     if (n_objects > 1 && p->opt.want_dilute) {
-        if ((st = dalloc(&p->d_Ftot, 8 * np, "Ftot"))) return bail(st);
+        if ((st = dalloc(&p->d_Ftot, nS * 8 * np, "Ftot"))) return bail(st);
     }
     NMS_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int32_t)));
-    for (int64_t j = 0; j < n; ++j) {
+    for (int64_t js = 0; js < nS * n; ++js) {
+        const int64_t j = js % n;
         double v = cell_vol ? fabs(cell_vol[j]) : 1.0;
-        if (nuc) p->h_wmax[0] = std::max(p->h_wmax[0], v * fabs(nuc[j]));
+        if (nuc) p->h_wmax[0] = std::max(p->h_wmax[0], v * fabs(nuc[js]));
         if (mag) {
-            double m2 = mag[3 * j] * mag[3 * j] + mag[3 * j + 1] * mag[3 * j + 1] + mag[3 * j + 2] * mag[3 * j + 2];
+            double m2 = mag[3 * js] * mag[3 * js] + mag[3 * js + 1] * mag[3 * js + 1] + mag[3 * js + 2] * mag[3 * js + 2];
             p->h_wmax[1] = std::max(p->h_wmax[1], v * sqrt(m2));
         }
     }
@@ -448,8 +453,9 @@ nms_status nms_amplitudes(nms_plan_t plan)
     Plan& p = *plan;
     cudaStream_t s = p.stream;
     const int64_t np = p.npix;
-    NMS_CUDA_TRY(cudaMemsetAsync(p.d_Gtot, 0, 16 * np * 8, s));
-    if (p.d_Gdil) NMS_CUDA_TRY(cudaMemsetAsync(p.d_Gdil, 0, 16 * np * 8, s));
+    const int64_t nS = p.n_sets;
+    NMS_CUDA_TRY(cudaMemsetAsync(p.d_Gtot, 0, nS * 16 * np * 8, s));
+    if (p.d_Gdil) NMS_CUDA_TRY(cudaMemsetAsync(p.d_Gdil, 0, nS * 16 * np * 8, s));
     if (p.d_Iobj)
         NMS_CUDA_TRY(cudaMemsetAsync(p.d_Iobj, 0, (size_t)tc_object_count(p) * p.oiq_nbins * sizeof(double), s));
     if (p.path == NMS_PREC_TC_F16X3) {
@@ -460,42 +466,48 @@ nms_status nms_amplitudes(nms_plan_t plan)
         return NMS_OK;
     }
     const bool objects = p.n_objects > 1 && p.opt.want_dilute;
-    for (int32_t r = 0; r < p.n_rot; ++r) {
-        const double* R = &p.h_rot[9 * r];
-        p.timer.begin(ST_PREP);
-        NMS_CUDA_TRY(launch_prep(p, R, s));
-        p.timer.end(ST_PREP, 1);
-        if (!objects) {
-            nms_status st = direct_sum_range(p, p.d_cpos, 0, p.n_cells, p.d_F);
-            if (st) return st;
-            p.timer.begin(ST_GACC);
-            NMS_CUDA_TRY(launch_gacc(p, p.d_F, p.d_Gtot, s));
-            if (p.d_Gdil) NMS_CUDA_TRY(launch_gacc(p, p.d_F, p.d_Gdil, s));
-            p.timer.end(ST_GACC, p.d_Gdil ? 2 : 1);
-        } else {
-            // per object: local amplitude F_k -> G_dil, and shifted into F_tot
-            NMS_CUDA_TRY(cudaMemsetAsync(p.d_Ftot, 0, 8 * np * 8, s));
-            for (int64_t k = 0; k < p.n_objects; ++k) {
-                int64_t a = p.h_off[k], b = p.h_off[k + 1];
-                if (b == a) continue;
-                nms_status st = direct_sum_range(p, p.d_cposl, a, b, p.d_F);
+    // loop mode on the direct path: one pass per weight set
+    for (int32_t r = 0; r < p.n_rot; ++r)
+        for (int32_t set = 0; set < p.n_sets; ++set) {
+            const double* R = &p.h_rot[9 * r];
+            double* F = p.d_F + (size_t)set * 8 * np;
+            double* Gt = p.d_Gtot + (size_t)set * 16 * np;
+            double* Gd = p.d_Gdil ? p.d_Gdil + (size_t)set * 16 * np : nullptr;
+            p.timer.begin(ST_PREP);
+            NMS_CUDA_TRY(launch_prep(p, R, s, set));
+            p.timer.end(ST_PREP, 1);
+            if (!objects) {
+                nms_status st = direct_sum_range(p, p.d_cpos, 0, p.n_cells, F);
                 if (st) return st;
-                double cy = 0.0, cz = 0.0;
-                if (!p.h_cen.empty()) {
-                    const double* c = &p.h_cen[3 * k];
-                    cy = R[3] * c[0] + R[4] * c[1] + R[5] * c[2];
-                    cz = R[6] * c[0] + R[7] * c[1] + R[8] * c[2];
+                p.timer.begin(ST_GACC);
+                NMS_CUDA_TRY(launch_gacc(p, F, Gt, s));
+                if (Gd) NMS_CUDA_TRY(launch_gacc(p, F, Gd, s));
+                p.timer.end(ST_GACC, Gd ? 2 : 1);
+            } else {
+                // per object: local amplitude F_k -> G_dil, and shifted into F_tot
+                double* Ft = p.d_Ftot + (size_t)set * 8 * np;
+                NMS_CUDA_TRY(cudaMemsetAsync(Ft, 0, 8 * np * 8, s));
+                for (int64_t k = 0; k < p.n_objects; ++k) {
+                    int64_t a = p.h_off[k], b = p.h_off[k + 1];
+                    if (b == a) continue;
+                    nms_status st = direct_sum_range(p, p.d_cposl, a, b, F);
+                    if (st) return st;
+                    double cy = 0.0, cz = 0.0;
+                    if (!p.h_cen.empty()) {
+                        const double* c = &p.h_cen[3 * k];
+                        cy = R[3] * c[0] + R[4] * c[1] + R[5] * c[2];
+                        cz = R[6] * c[0] + R[7] * c[1] + R[8] * c[2];
+                    }
+                    p.timer.begin(ST_GACC);
+                    NMS_CUDA_TRY(launch_gacc(p, F, Gd, s));
+                    NMS_CUDA_TRY(launch_shift_add(p, F, cy, cz, Ft, s));
+                    p.timer.end(ST_GACC, 2);
                 }
                 p.timer.begin(ST_GACC);
-                NMS_CUDA_TRY(launch_gacc(p, p.d_F, p.d_Gdil, s));
-                NMS_CUDA_TRY(launch_shift_add(p, p.d_F, cy, cz, p.d_Ftot, s));
-                p.timer.end(ST_GACC, 2);
+                NMS_CUDA_TRY(launch_gacc(p, Ft, Gt, s));
+                p.timer.end(ST_GACC, 1);
             }
-            p.timer.begin(ST_GACC);
-            NMS_CUDA_TRY(launch_gacc(p, p.d_Ftot, p.d_Gtot, s));
-            p.timer.end(ST_GACC, 1);
         }
-    }
     p.rot_done = p.n_rot;
     p.have_G = true;
     return NMS_OK;
@@ -509,7 +521,7 @@ nms_status nms_get_amplitudes(nms_plan_t plan, double* out, int32_t out_is_devic
     if (!p.have_G) return fail(NMS_ERR_BAD_STATE, "nms_amplitudes has not run");
     nms_status st = check_device_error(p);
     if (st) return st;
-    const double* src = (p.n_objects > 1 && p.opt.want_dilute) ? p.d_Ftot : p.d_F;
+    const double* src = ((p.n_objects > 1 && p.opt.want_dilute) ? p.d_Ftot : p.d_F) + (size_t)p.sel_set * 8 * p.npix;
     NMS_CUDA_TRY(cudaMemcpyAsync(out, src, 8 * p.npix * 8,
                                  out_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p.stream));
     NMS_CUDA_TRY(cudaStreamSynchronize(p.stream));
@@ -525,8 +537,9 @@ nms_status nms_response(nms_plan_t plan, int32_t id, int32_t part, double* out, 
     if (part < NMS_PART_TOTAL || part > NMS_PART_INTERFERENCE) return fail(NMS_ERR_INVALID_ARG, "bad part");
     if (!p.have_G) return fail(NMS_ERR_BAD_STATE, "nms_amplitudes has not run");
     if (part != NMS_PART_TOTAL && !p.d_Gdil) return fail(NMS_ERR_UNSUPPORTED, "dilute part needs want_dilute");
-    const double* Ga = part == NMS_PART_DILUTE ? p.d_Gdil : p.d_Gtot;
-    const double* Gb = part == NMS_PART_INTERFERENCE ? p.d_Gdil : nullptr;
+    const size_t gs = (size_t)p.sel_set * 16 * p.npix;   // the selected weight set's G
+    const double* Ga = (part == NMS_PART_DILUTE ? p.d_Gdil : p.d_Gtot) + gs;
+    const double* Gb = part == NMS_PART_INTERFERENCE ? p.d_Gdil + gs : nullptr;
     double norm = 1.0 / (double)(p.rot_done > 0 ? p.rot_done : 1);
     double* dst = out;
     if (!out_is_device) {
@@ -803,6 +816,7 @@ nms_status nms_plan_object_iq(nms_plan_t plan, int32_t response_id, int32_t nbin
     if (!plan) return fail(NMS_ERR_INVALID_ARG, "plan is NULL");
     Plan& p = *plan;
     if (p.path != NMS_PREC_TC_F16X3) return fail(NMS_ERR_UNSUPPORTED, "per-object averages need the tensor-core path");
+    if (p.n_sets > 1) return fail(NMS_ERR_UNSUPPORTED, "per-object averages take one weight set");
     if (!(response_id == NMS_RESP_N || response_id == NMS_RESP_M || response_id == NMS_RESP_P ||
           response_id == NMS_RESP_SF || response_id == NMS_RESP_UNPOL))
         return fail(NMS_ERR_UNSUPPORTED, "per-object averages support N, M, P, SF and UNPOL");
@@ -890,6 +904,15 @@ nms_status nms_plan_info(nms_plan_t plan, int32_t* precision, int32_t* kc_cells,
     if (precision) *precision = plan->path;
     if (kc_cells) *kc_cells = tc_tuned_kc_cells(*plan);
     if (items_per_sm) *items_per_sm = tc_tuned_items_per_sm(*plan);
+    return NMS_OK;
+}
+
+nms_status nms_select_set(nms_plan_t plan, int32_t set)
+{
+    set_error("");
+    if (!plan) return fail(NMS_ERR_INVALID_ARG, "plan is NULL");
+    if (set < 0 || set >= plan->n_sets) return fail(NMS_ERR_INVALID_ARG, "weight set out of range");
+    plan->sel_set = set;
     return NMS_OK;
 }
 

@@ -54,6 +54,8 @@ struct Plan {
     int path = 0;                 // nms_precision actually used
     int64_t n_cells = 0, n_objects = 1, npix = 0;
     int32_t n_rot = 1;
+    int32_t n_sets = 1;           // weight sets (loop mode); nuc/mag [S][n]
+    int32_t sel_set = 0;          // set reported by nms_response / nms_get_amplitudes
     double V = 1.0, bH = 1.0, P[3] = {0, 0, 1};
     bool has_nuc = false, has_mag = false, has_centers = false;
     std::vector<int64_t> h_off;   // [K+1]
@@ -63,8 +65,8 @@ struct Plan {
     // device inputs (FP64)
     double* d_pos = nullptr;      // [n][3]
     double* d_vol = nullptr;      // [n]
-    double* d_nuc = nullptr;      // [n] or null
-    double* d_mag = nullptr;      // [n][3] or null
+    double* d_nuc = nullptr;      // [S][n] or null
+    double* d_mag = nullptr;      // [S][n][3] or null
     double* d_cen_cell = nullptr; // [n][3] object centre of each cell, or null
     // q-grid (FP64) and the turns form used by the kernels
     double* d_qy = nullptr; double* d_qz = nullptr;
@@ -79,12 +81,12 @@ struct Plan {
     double* d_yzl = nullptr;      // FP64 (Y, Z) local
     double* d_w64 = nullptr;      // FP64 weights [4][n]
     // results
-    double* d_F = nullptr;        // [4][npix][2] amplitudes of the current sum
-    double* d_Ftot = nullptr;     // [4][npix][2] total amplitude (object path)
+    double* d_F = nullptr;        // [S][4][npix][2] amplitudes of the last sum
+    double* d_Ftot = nullptr;     // [S][4][npix][2] total amplitude (object path)
     double* d_Fpart = nullptr;    // split partials [splits][4][npix][2]
     int64_t fpart_splits = 0;
-    double* d_Gtot = nullptr;     // [16][npix]
-    double* d_Gdil = nullptr;     // [16][npix] (want_dilute)
+    double* d_Gtot = nullptr;     // [S][16][npix]
+    double* d_Gdil = nullptr;     // [S][16][npix] (want_dilute)
     int32_t* d_err = nullptr;     // device error word (timeouts)
     bool have_G = false;
     int32_t rot_done = 0;
@@ -110,7 +112,7 @@ struct Plan {
 
 // ---------------------------------------------------------------- kernels (launchers)
 // Rotation and weights for cells [0, n): FP64 positions -> two-float, FP32 weights.
-cudaError_t launch_prep(Plan& p, const double* R9, cudaStream_t s);
+cudaError_t launch_prep(Plan& p, const double* R9, cudaStream_t s, int set = 0);
 // Direct sum over cells [c0, c1) of the given position array into split partials.
 cudaError_t launch_direct(const Plan& p, const float4* cpos, int64_t c0, int64_t c1,
                           bool compensated, int splits, cudaStream_t s);

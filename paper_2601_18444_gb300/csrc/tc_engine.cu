@@ -31,24 +31,26 @@
 namespace nms {
 
 // launchers in k_gemm.cu / k_batch.cu
-cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, const int64_t* kb_cell0, const int32_t* kb_ncell,
-                             int64_t nkb, const float2* qy, int ny, const float2* qz, int nz, int mtiles, int ntiles,
-                             const float wscale[4], void* tab, cudaStream_t s);
+cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, int64_t wstride, int nch, const int64_t* kb_cell0,
+                             const int32_t* kb_ncell, int64_t nkb, const float2* qy, int ny, const float2* qz, int nz,
+                             int mtiles, int ntiles, const float wscale[4], void* tab, cudaStream_t s);
 cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
-                           int grid, int kcb, double* P, double* F, int ny, int nz, const double scale[4], int32_t* err,
-                           uint64_t limit_ns, int mode, cudaStream_t s);
-cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, int ny, int nz, int ntiles,
+                           int grid, int kcb, double* P, double* F, int ny, int nz, int nch, const double scale[4],
+                           int32_t* err, uint64_t limit_ns, int mode, cudaStream_t s);
+cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, int ny, int nz, int ntiles, int nch,
                              const double scale[4], double* F, cudaStream_t s);
 size_t tc_item_bytes();
 size_t tc_red_bytes();
 size_t tc_block_bytes();
 float tc_operand_scale();
-cudaError_t launch_prep_rot(const Plan& p, const RotMat& R, bool global, float4* cpos, float4* cw, cudaStream_t s);
+cudaError_t launch_prep_rot(const Plan& p, const RotMat& R, bool global, float4* cpos, float4* cw, int64_t wstride,
+                            cudaStream_t s);
 cudaError_t launch_centres(int n_out, const int32_t* out_obj, const int32_t* out_rot, int rot0, const double* rot,
                            const double* cen, float4* cyz, cudaStream_t s);
-cudaError_t launch_gacc_batch(const double* F, int n_out, int64_t npix, double* G, cudaStream_t s);
-cudaError_t launch_dilute_shift_batch(const double* F, int n_out, const float4* cyz, const int32_t* out_rot,
-                                      const float4* qturn, int64_t npix, double* Gdil, double* Ftot, cudaStream_t s);
+cudaError_t launch_gacc_batch(const double* F, int n_out, int64_t ostride, int64_t npix, double* G, cudaStream_t s);
+cudaError_t launch_dilute_shift_batch(const double* F, int n_out, int64_t ostride, const float4* cyz,
+                                      const int32_t* out_rot, const float4* qturn, int64_t npix, double* Gdil,
+                                      double* Ftot, int64_t tstride, cudaStream_t s);
 
 namespace {
 
@@ -96,6 +98,9 @@ struct TcState {
     double W[4] = {1, 1, 1, 1};
     int kcb = 2;
     int items_per_sm = 8;        // work-list granularity of a GEMM launch
+    int nsets = 1;               // weight sets (loop mode), stacked along the GEMM rows
+    int nch = 4;                 // channels per output: 4 x (weight sets rounded up to a power of two)
+    int64_t wstride = 0;         // cells between weight sets in d_cw_b (= R_b * n)
     int mode = 0;                // GEMM form: 0 one CTA, 1 pairs sharing A (even ntiles), 2 two-SM MMA (even mtiles)
     bool mode_forced = false;    // set by NMS_GEMM_MODE: the autotuner keeps it
     bool objects = false;        // per-object amplitudes (dilute split) with shifts
@@ -398,13 +403,13 @@ nms_status tc_autotune(Plan& p, TcState& t)
     const float4* ref_pos = t.objects ? p.d_cposl : p.d_cpos;
     nms_status st = direct_sum_range(p, ref_pos, c0, c1, p.d_F);
     if (st) return st;
-    NMS_CUDA_TRY(launch_prep_rot(p, R, !t.objects, t.d_cpos_b, t.d_cw_b, s));
+    NMS_CUDA_TRY(launch_prep_rot(p, R, !t.objects, t.d_cpos_b, t.d_cw_b, t.wstride, s));
     double* d_sw = nullptr;
     unsigned int* d_err = nullptr;
     double* d_Fp = nullptr;
     NMS_CUDA_TRY(cudaMalloc(&d_sw, 4 * sizeof(double)));
     NMS_CUDA_TRY(cudaMalloc(&d_err, 4 * sizeof(unsigned int)));
-    NMS_CUDA_TRY(cudaMalloc(&d_Fp, 8 * np * sizeof(double)));
+    NMS_CUDA_TRY(cudaMalloc(&d_Fp, (size_t)t.nch * 2 * np * sizeof(double)));
     NMS_CUDA_TRY(cudaMemsetAsync(d_sw, 0, 4 * sizeof(double), s));
     k_wabs_sum<<<std::max(1, std::min(4 * sms, (int)((nprobe + 255) / 256))), 256, 0, s>>>(t.d_cw_b, c0, c1, d_sw);
     NMS_CUDA_TRY(cudaGetLastError());
@@ -448,17 +453,17 @@ nms_status tc_autotune(Plan& p, TcState& t)
         float ms = 1e30f;
         const Chunk& ch = S.batches[0].chunks[0];
         for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {
-            ce = cudaMemsetAsync(d_Fp, 0, 8 * np * sizeof(double), s);
+            ce = cudaMemsetAsync(d_Fp, 0, (size_t)t.nch * 2 * np * sizeof(double), s);
             if (ce == cudaSuccess)
-                ce = tc_launch_tables(t.d_cpos_b, t.d_cw_b, S.d_kb_cell0, S.d_kb_ncell, ch.nkb, t.d_qy, t.ny, t.d_qz,
-                                      t.nz, t.mtiles, t.ntiles, wscale, p.d_tab, s);
+                ce = tc_launch_tables(t.d_cpos_b, t.d_cw_b, t.wstride, t.nch, S.d_kb_cell0, S.d_kb_ncell, ch.nkb, t.d_qy,
+                                      t.ny, t.d_qz, t.nz, t.mtiles, t.ntiles, wscale, p.d_tab, s);
             if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
             if (ce == cudaSuccess)
                 ce = tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles, S.d_items, ch.n_items, ch.grid, kcb, P,
-                                    d_Fp, t.ny, t.nz, scale, p.d_err, limit, t.mode, s);
+                                    d_Fp, t.ny, t.nz, t.nch, scale, p.d_err, limit, t.mode, s);
             if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
             if (ce == cudaSuccess)
-                ce = tc_launch_reduce(P, S.d_reds, ch.n_red, t.ny, t.nz, t.ntiles, scale, d_Fp, s);
+                ce = tc_launch_reduce(P, S.d_reds, ch.n_red, t.ny, t.nz, t.ntiles, t.nch, scale, d_Fp, s);
             if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
             float m = 0.f;
             if (ce == cudaSuccess) cudaEventElapsedTime(&m, e0, e1);
@@ -530,7 +535,13 @@ nms_status tc_setup(Plan& p)
     p.tc_state = t;
     t->ny = p.grid.n0;
     t->nz = p.grid.n1;
-    t->mtiles = (4 * t->ny + 127) / 128;
+    t->nsets = p.n_sets;
+    {
+        int sp = 1;
+        while (sp < t->nsets) sp <<= 1;
+        t->nch = 4 * sp;
+    }
+    t->mtiles = (t->nch * t->ny + 127) / 128;
     t->ntiles = (2 * t->nz + 127) / 128;
     t->kcb = p.opt.kc_cells > 0 ? std::max(1, p.opt.kc_cells / 32) : 2;
     t->objects = p.n_objects > 1 && p.opt.want_dilute;
@@ -579,17 +590,23 @@ nms_status tc_setup(Plan& p)
 
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
-    // rotations prepared per batch: stacked positions and weights up to 2 GB
-    const int64_t per_rot = n * 32;
+    // rotations prepared per batch: stacked positions and weights (every
+    // weight set, [set][rotation][cell]) up to 2 GB
+    const int64_t per_rot = n * 16 * (1 + t->nch / 4);
     t->R_b = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)p.n_rot, 64, (2ll << 30) / std::max<int64_t>(1, per_rot)}));
+    t->wstride = (int64_t)t->R_b * n;
     NMS_CUDA_TRY(cudaMalloc(&t->d_cpos_b, (size_t)t->R_b * n * sizeof(float4)));
-    NMS_CUDA_TRY(cudaMalloc(&t->d_cw_b, (size_t)t->R_b * n * sizeof(float4)));
-    // output amplitude batch: up to 1 GB
+    NMS_CUDA_TRY(cudaMalloc(&t->d_cw_b, (size_t)(t->nch / 4) * t->wstride * sizeof(float4)));
+    // padding sets (up to the power of two) keep zero weights
+    NMS_CUDA_TRY(cudaMemset(t->d_cw_b, 0, (size_t)(t->nch / 4) * t->wstride * sizeof(float4)));
+    // output amplitude batch: up to 1 GB, nch complex channels per output
+    const int64_t out_bytes = (int64_t)t->nch * np * 16;
     const int64_t outs_per_rb = t->objects ? (int64_t)t->R_b * p.n_objects : t->R_b;
-    const int out_cap = (int)std::max<int64_t>(1, std::min<int64_t>(outs_per_rb, (1ll << 30) / (64 * np)));
-    NMS_CUDA_TRY(cudaMalloc(&t->d_Fb, (size_t)out_cap * 8 * np * sizeof(double)));
+    const int out_cap = (int)std::max<int64_t>(1, std::min<int64_t>(outs_per_rb, (1ll << 30) / out_bytes));
+    NMS_CUDA_TRY(cudaMalloc(&t->d_Fb, (size_t)out_cap * out_bytes));
     NMS_CUDA_TRY(cudaMalloc(&t->d_cyz, (size_t)out_cap * sizeof(float4)));
-    if (t->objects) NMS_CUDA_TRY(cudaMalloc(&t->d_Ftot_b, (size_t)t->R_b * 8 * np * sizeof(double)));
+    // total amplitude per prepared rotation and weight set
+    if (t->objects) NMS_CUDA_TRY(cudaMalloc(&t->d_Ftot_b, (size_t)t->R_b * t->nsets * 8 * np * sizeof(double)));
     // phase tables: as many k-blocks as the workspace allows
     const int64_t per_kb = (int64_t)(t->mtiles + t->ntiles) * 2 * (int64_t)tc_block_bytes();
     const int64_t budget = p.opt.workspace_bytes > 0 ? p.opt.workspace_bytes
@@ -642,12 +659,14 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
     TcState& t = *(TcState*)p.tc_state;
     const int64_t n = p.n_cells;
     const int64_t np = p.npix;
+    const int nS = t.nsets;
+    const int64_t F4 = 8 * np;                   // doubles of one set's amplitudes [4][np] complex
+    const int64_t ostride = (int64_t)t.nch * 2 * np;   // doubles between outputs of a batch
     const float sc = tc_operand_scale();
     const float wscale[4] = {(float)(sc / t.W[0]), (float)(sc / t.W[1]), (float)(sc / t.W[2]), (float)(sc / t.W[3])};
     double scale[4];
     for (int c = 0; c < 4; ++c) scale[c] = t.W[c] / ((double)sc * (double)sc);
     const uint64_t limit = p.opt.max_spin > 0 ? (uint64_t)p.opt.max_spin * 1000ull : 4000000000ull;
-    double* last_F = nullptr;
     for (int rb0 = 0; rb0 < p.n_rot; rb0 += t.R_b) {
         const int nrl = std::min(t.R_b, p.n_rot - rb0);
         const Schedule& S = nrl == t.R_b ? t.full : t.last;
@@ -655,31 +674,32 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
         for (int rl = 0; rl < nrl; ++rl) {
             RotMat R;
             memcpy(R.m, &p.h_rot[9 * (size_t)(rb0 + rl)], sizeof(R.m));
-            NMS_CUDA_TRY(launch_prep_rot(p, R, !t.objects, t.d_cpos_b + (size_t)rl * n, t.d_cw_b + (size_t)rl * n, s));
+            NMS_CUDA_TRY(launch_prep_rot(p, R, !t.objects, t.d_cpos_b + (size_t)rl * n, t.d_cw_b + (size_t)rl * n,
+                                         t.wstride, s));
         }
         p.timer.end(ST_PREP, nrl);
-        if (t.objects) NMS_CUDA_TRY(cudaMemsetAsync(t.d_Ftot_b, 0, (size_t)nrl * 8 * np * sizeof(double), s));
+        if (t.objects) NMS_CUDA_TRY(cudaMemsetAsync(t.d_Ftot_b, 0, (size_t)nrl * nS * F4 * sizeof(double), s));
         for (const OutBatch& ob : S.batches) {
-            NMS_CUDA_TRY(cudaMemsetAsync(t.d_Fb, 0, (size_t)ob.n_out * 8 * np * sizeof(double), s));
+            NMS_CUDA_TRY(cudaMemsetAsync(t.d_Fb, 0, (size_t)ob.n_out * ostride * sizeof(double), s));
             for (const Chunk& ch : ob.chunks) {
                 p.timer.begin(ST_TABLES);
-                NMS_CUDA_TRY(tc_launch_tables(t.d_cpos_b, t.d_cw_b, S.d_kb_cell0 + ch.kb_off, S.d_kb_ncell + ch.kb_off,
-                                              ch.nkb, t.d_qy, t.ny, t.d_qz, t.nz, t.mtiles, t.ntiles, wscale, p.d_tab,
-                                              s));
+                NMS_CUDA_TRY(tc_launch_tables(t.d_cpos_b, t.d_cw_b, t.wstride, t.nch, S.d_kb_cell0 + ch.kb_off,
+                                              S.d_kb_ncell + ch.kb_off, ch.nkb, t.d_qy, t.ny, t.d_qz, t.nz, t.mtiles,
+                                              t.ntiles, wscale, p.d_tab, s));
                 p.timer.end(ST_TABLES, 2);
                 p.timer.begin(ST_GEMM);
                 NMS_CUDA_TRY(tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles,
                                             (const char*)S.d_items + ch.item_off * tc_item_bytes(), ch.n_items, ch.grid,
-                                            t.kcb, t.d_P, t.d_Fb, t.ny, t.nz, scale, p.d_err, limit, t.mode, s));
+                                            t.kcb, t.d_P, t.d_Fb, t.ny, t.nz, t.nch, scale, p.d_err, limit, t.mode, s));
                 p.timer.end(ST_GEMM, 1);
                 p.timer.begin(ST_REDUCE);
                 NMS_CUDA_TRY(tc_launch_reduce(t.d_P, (const char*)S.d_reds + ch.red_off * tc_red_bytes(), ch.n_red, t.ny,
-                                              t.nz, t.ntiles, scale, t.d_Fb, s));
+                                              t.nz, t.ntiles, t.nch, scale, t.d_Fb, s));
                 p.timer.end(ST_REDUCE, ch.n_red > 0 ? 1 : 0);
             }
             p.timer.begin(ST_GACC);
             int nl = 0;
-            if (p.oiq_id >= 0) {
+            if (p.oiq_id >= 0) {   // one weight set (checked when requested)
                 NMS_CUDA_TRY(launch_obj_bin(t.d_Fb, ob.n_out, S.d_out_obj + ob.out0, p, p.d_bin_of, p.oiq_nbins,
                                             p.oiq_id, p.d_Iobj, s));
                 ++nl;
@@ -687,32 +707,41 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
             if (t.objects) {
                 NMS_CUDA_TRY(launch_centres(ob.n_out, S.d_out_obj + ob.out0, S.d_out_rot + ob.out0, rb0, t.d_rot, t.d_cen,
                                             t.d_cyz, s));
-                NMS_CUDA_TRY(launch_dilute_shift_batch(t.d_Fb, ob.n_out, t.d_cyz, S.d_out_rot + ob.out0, p.d_qturn, np,
-                                                       p.d_Gdil, t.d_Ftot_b, s));
-                nl += 2;
-            } else {
-                NMS_CUDA_TRY(launch_gacc_batch(t.d_Fb, ob.n_out, np, p.d_Gtot, s));
-                nl += 1;
-                if (p.d_Gdil) {
-                    NMS_CUDA_TRY(launch_gacc_batch(t.d_Fb, ob.n_out, np, p.d_Gdil, s));
-                    nl += 1;
+                ++nl;
+            }
+            for (int st = 0; st < nS; ++st) {
+                const double* Fs = t.d_Fb + (size_t)st * F4;   // set st of the batch's first output
+                if (t.objects) {
+                    NMS_CUDA_TRY(launch_dilute_shift_batch(Fs, ob.n_out, ostride, t.d_cyz, S.d_out_rot + ob.out0,
+                                                           p.d_qturn, np, p.d_Gdil + (size_t)st * 16 * np,
+                                                           t.d_Ftot_b + (size_t)st * F4, (int64_t)nS * F4, s));
+                    ++nl;
+                } else {
+                    NMS_CUDA_TRY(launch_gacc_batch(Fs, ob.n_out, ostride, np, p.d_Gtot + (size_t)st * 16 * np, s));
+                    ++nl;
+                    if (p.d_Gdil) {
+                        NMS_CUDA_TRY(launch_gacc_batch(Fs, ob.n_out, ostride, np, p.d_Gdil + (size_t)st * 16 * np, s));
+                        ++nl;
+                    }
+                    if (rb0 + nrl == p.n_rot && &ob == &S.batches.back())
+                        NMS_CUDA_TRY(cudaMemcpyAsync(p.d_F + (size_t)st * F4, Fs + (size_t)(ob.n_out - 1) * ostride,
+                                                     F4 * sizeof(double), cudaMemcpyDeviceToDevice, s));
                 }
-                last_F = t.d_Fb + (size_t)(ob.n_out - 1) * 8 * np;
-                if (rb0 + nrl == p.n_rot && &ob == &S.batches.back())
-                    NMS_CUDA_TRY(cudaMemcpyAsync(p.d_F, last_F, 8 * np * sizeof(double), cudaMemcpyDeviceToDevice, s));
             }
             p.timer.end(ST_GACC, nl);
         }
         if (t.objects) {
             p.timer.begin(ST_GACC);
-            NMS_CUDA_TRY(launch_gacc_batch(t.d_Ftot_b, nrl, np, p.d_Gtot, s));
-            p.timer.end(ST_GACC, 1);
-            if (rb0 + nrl == p.n_rot)
-                NMS_CUDA_TRY(cudaMemcpyAsync(p.d_Ftot, t.d_Ftot_b + (size_t)(nrl - 1) * 8 * np, 8 * np * sizeof(double),
-                                             cudaMemcpyDeviceToDevice, s));
+            for (int st = 0; st < nS; ++st) {
+                const double* Ts = t.d_Ftot_b + (size_t)st * F4;
+                NMS_CUDA_TRY(launch_gacc_batch(Ts, nrl, (int64_t)nS * F4, np, p.d_Gtot + (size_t)st * 16 * np, s));
+                if (rb0 + nrl == p.n_rot)
+                    NMS_CUDA_TRY(cudaMemcpyAsync(p.d_Ftot + (size_t)st * F4, Ts + (size_t)(nrl - 1) * nS * F4,
+                                                 F4 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            }
+            p.timer.end(ST_GACC, nS);
         }
     }
-    (void)last_F;
     return NMS_OK;
 }
 

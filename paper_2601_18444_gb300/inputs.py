@@ -344,3 +344,23 @@ def small_random_field(n_cells, seed=7, extent=10.0, n_objects=1):
         off = np.concatenate([[0], cuts, [n_cells]]).astype(np.int64)
         cen = rng.uniform(-3 * extent, 3 * extent, size=(n_objects, 3))
     return Field(pos, vol, nuc, mag, offsets=off, centers=cen, name="small_random")
+
+
+def field_sweep(field, h_values, axis=(0.0, 0.0, 1.0)):
+    """Magnetization states of one geometry along an applied-field sweep (loop
+    mode input): state s is normalise(m + h_s * axis) per cell, with the
+    field's own m as the zero-field state (cells with |m| = 0 stay 0).
+    Returns (nuc [S][n], mag [S][n][3]); N is the same in every state."""
+    m = np.asarray(field.mag, dtype=np.float64)
+    ax = np.asarray(axis, dtype=np.float64)
+    ax = ax / np.linalg.norm(ax)
+    norm0 = np.linalg.norm(m, axis=1, keepdims=True)
+    live = norm0 > 0
+    mags = []
+    for h in h_values:
+        v = m + h * ax[None, :] * live
+        nv = np.linalg.norm(v, axis=1, keepdims=True)
+        mags.append(np.where(nv > 0, v / np.where(nv > 0, nv, 1.0) * norm0, 0.0))
+    S = len(h_values)
+    nuc = np.tile(field.nuc, (S, 1)) if field.nuc is not None else None
+    return nuc, np.ascontiguousarray(np.stack(mags))

@@ -47,7 +47,8 @@ class nms_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("want_dilute", ctypes.c_int32), ("volume_V", ctypes.c_double),
                 ("b_H", ctypes.c_double), ("P", ctypes.c_double * 3), ("kc_cells", ctypes.c_int32),
                 ("split_k", ctypes.c_int32), ("max_spin", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
-                ("timing", ctypes.c_int32), ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("timing", ctypes.c_int32), ("autotune", ctypes.c_int32), ("n_sets", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -90,6 +91,7 @@ SIGNATURES = {
     "nms_dsft_direct_noalloc": (ctypes.c_int, [ctypes.c_int64, _V, _V, _V, ctypes.c_int64, _V, _V, _V, _V]),
     "nms_plan_info": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_int32)]),
+    "nms_select_set": (ctypes.c_int, [_V, ctypes.c_int32]),
     "nms_plan_destroy": (ctypes.c_int, [_V]),
     "nms_last_error": (ctypes.c_char_p, []),
     "nms_version": (ctypes.c_char_p, []),
@@ -220,6 +222,12 @@ def nms_plan_create(pos, cell_vol=None, nuc=None, mag=None, object_offsets=None,
     nuc, p_nuc = _host(nuc)
     mag, p_mag = _host(mag)
     cen, p_cen = _host(object_centers)
+    # loop mode: nuc [S][n] and mag [S][n][3]; the library trusts the sizes
+    S = max(1, int(opt.n_sets)) if opt is not None else 1
+    if nuc is not None and nuc.size != S * n:
+        raise ValueError(f"nuc must hold n_sets x n_cells = {S} x {n} values")
+    if mag is not None and mag.size != 3 * S * n:
+        raise ValueError(f"mag must hold n_sets x n_cells x 3 = {S} x {n} x 3 values")
     off = None
     p_off = None
     K = 1
@@ -472,6 +480,11 @@ def nms_plan_info(plan):
 
 def nms_plan_destroy(plan):
     plan.close()
+
+
+def nms_select_set(plan, s):
+    """Loop mode: later nms_get_amplitudes / nms_response calls report weight set s."""
+    _check(load().nms_select_set(plan.handle, int(s)))
 
 
 def plan_from_field(field, grid, opt=None, rot=None, stream=None):

@@ -377,6 +377,14 @@ nms_status nms_plan_info(nms_plan_t plan, int32_t* precision, int32_t* kc_cells,
  * all sets are computed by each nms_amplitudes call. */
 nms_status nms_select_set(nms_plan_t plan, int32_t set);
 
+/* Failure-path self-test (the paper has no counterpart): one thread waits on
+ * a device mbarrier that nothing arrives on, with the bounded wait every
+ * kernel of the library uses (%globaltimer, limit_us microseconds,
+ * 1 <= limit_us <= 1e7).  The wait runs out, the kernel records an error
+ * code and returns, so this returns NMS_ERR_TIMEOUT and leaves the CUDA
+ * context usable.  Synchronous on cuda_stream. */
+nms_status nms_selftest_bounded_wait(int64_t limit_us, void* cuda_stream);
+
 /* Release every device resource of the plan.  NULL is accepted. */
 nms_status nms_plan_destroy(nms_plan_t plan);
 

@@ -246,6 +246,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
     }
 }
 
+// Teardown wait for this CTA's own asynchronous operations (bulk copies in
+// flight, issued MMAs): it does not give up when another role aborted, only
+// after TC_DRAIN_LIMIT_NS, so an aborting CTA still lets what it started land
+// before it frees TMEM and exits.
+constexpr uint64_t TC_DRAIN_LIMIT_NS = 1000000000ull;
+
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (gtimer() - t0 > TC_DRAIN_LIMIT_NS) return false;
+    }
+}
+
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar)
 {
     asm volatile(
@@ -643,7 +659,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
             for (int64_t k = (i > STG ? i - STG : 0); k < i; ++k) {
                 const int s = (int)(k % STG);
                 const uint32_t par = (uint32_t)((k / STG) & 1);
-                mbar_wait(&bar_full[s], par, g.limit_ns, &s_abort);
+                mbar_wait_drain(&bar_full[s], par);
             }
         }
     } else if (warp == 1) {
@@ -736,7 +752,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
             // every MMA issued by this thread completes before TMEM is freed
             if (MODE == 2) tc_commit_to<2>(&bar_final, (uint16_t)1);
             else tc_commit(&bar_final);
-            mbar_wait(&bar_final, 0, g.limit_ns, &s_abort);
+            mbar_wait_drain(&bar_final, 0);
         }
     } else {
         // ---------------- epilogue: drain TMEM chunks into two-float sums
@@ -895,6 +911,28 @@ __global__ void k_gemm_reduce(const double* __restrict__ P, const RedDesc* __res
     t.x += scale.v[c & 3] * re;
     t.y += scale.v[c & 3] * im;
     *o = t;
+}
+
+// ------------------------------------------------------------------ self-test
+// A bounded wait that runs out: one thread waits on an mbarrier nothing
+// arrives on, with the same wait the GEMM uses; after limit_ns it records
+// code 7 in err and returns.  Nothing is in flight, so the context stays
+// usable.
+__global__ void k_selftest_wait(uint64_t limit_ns, int32_t* err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ volatile int abort_flag;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(&bar, 0, limit_ns, &abort_flag)) atomicExch(err, 7);
+}
+
+cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t* err, cudaStream_t s)
+{
+    k_selftest_wait<<<1, 32, 0, s>>>(limit_ns, err);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ launchers

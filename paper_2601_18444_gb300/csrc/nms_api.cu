@@ -916,6 +916,29 @@ nms_status nms_select_set(nms_plan_t plan, int32_t set)
     return NMS_OK;
 }
 
+nms_status nms_selftest_bounded_wait(int64_t limit_us, void* cuda_stream)
+{
+    set_error("");
+    if (limit_us < 1 || limit_us > 10000000) return fail(NMS_ERR_INVALID_ARG, "need 1 <= limit_us <= 1e7");
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) {
+        cudaGetLastError();
+        return fail(NMS_ERR_CUDA, "no CUDA device available (libnms has no CPU fallback)");
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int32_t* d_err = nullptr;
+    NMS_CUDA_TRY(tmp_alloc((void**)&d_err, sizeof(int32_t), s));
+    int32_t h_err = 0;
+    cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = launch_selftest_wait((uint64_t)limit_us * 1000ull, d_err, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_err, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d_err, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "bounded-wait self-test");
+    if (h_err) return fail(NMS_ERR_TIMEOUT, "device wait gave up after the limit (expected)");
+    return NMS_OK;
+}
+
 nms_status nms_plan_destroy(nms_plan_t plan)
 {
     if (!plan) return NMS_OK;

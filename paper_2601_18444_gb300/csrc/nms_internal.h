@@ -152,6 +152,7 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s);
 void tc_release(Plan& p);
 
 int device_sm_count();
+cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t* err, cudaStream_t s);
 
 // Ring bin of |q| = x: b with e[b] <= x < e[b+1] (e increasing, nb bins), or
 // -1 outside [e[0], e[nb]) and for NaN.

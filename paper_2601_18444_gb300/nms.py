@@ -92,6 +92,7 @@ SIGNATURES = {
     "nms_plan_info": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_int32)]),
     "nms_select_set": (ctypes.c_int, [_V, ctypes.c_int32]),
+    "nms_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int64, _V]),
     "nms_plan_destroy": (ctypes.c_int, [_V]),
     "nms_last_error": (ctypes.c_char_p, []),
     "nms_version": (ctypes.c_char_p, []),
@@ -485,6 +486,12 @@ def nms_plan_destroy(plan):
 def nms_select_set(plan, s):
     """Loop mode: later nms_get_amplitudes / nms_response calls report weight set s."""
     _check(load().nms_select_set(plan.handle, int(s)))
+
+
+def nms_selftest_bounded_wait(limit_us, stream=None):
+    """Run the bounded-wait self-test; raises NmsError (status TIMEOUT) when the
+    device wait gave up, which is the expected outcome."""
+    _check(load().nms_selftest_bounded_wait(int(limit_us), ctypes.c_void_p(stream or 0)))
 
 
 def plan_from_field(field, grid, opt=None, rot=None, stream=None):

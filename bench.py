@@ -58,7 +58,7 @@ def load_peaks():
 
 
 # ----------------------------------------------------------------- workloads
-def make_workload(name):
+def make_workload(name, n_spheres=10000):
     from paper_2601_18444_gb300 import inputs as I
     if name == "box":
         f = I.box_field(256, 256, 64, a=2.0, n_modes=64, kmax=0.2, n_pores=200, seed=1)
@@ -80,11 +80,12 @@ def make_workload(name):
         r = np.linspace(0.0, 40.0, 64)
         desc = "sphere R=16nm a=2nm (2109 cells) seeded vortex; 128x128 detector [-1,1]^2 nm^-1"
     elif name == "ensemble":
-        f = I.sphere_ensemble(n_spheres=10000, median=8.0, sigma=0.35, clip=(5.0, 20.0), a=1.0, cube=2000.0, seed=3)
+        f = I.sphere_ensemble(n_spheres=n_spheres, median=8.0, sigma=0.35, clip=(5.0, 20.0), a=1.0, cube=2000.0,
+                              seed=3)
         grid = dict(kind="cartesian", n0=256, n1=256, lo0=-1.0, hi0=1.0, lo1=-1.0, hi1=1.0)
         edges = np.linspace(0.0, 1.0, 129)
         r = np.linspace(0.0, 60.0, 64)
-        desc = (f"ensemble of 10000 spheres, lognormal R (median 8nm, sigma 0.35, 5-20nm) a=1nm ({f.n} cells), "
+        desc = (f"ensemble of {n_spheres} spheres, lognormal R (median 8nm, sigma 0.35, 5-20nm) a=1nm ({f.n} cells), "
                 "Neel-like canting, 2um cube; 256x256 detector [-1,1]^2 nm^-1; dilute + total + interference")
         return f, grid, edges, r, desc, None, True
     elif name == "rotations":
@@ -259,12 +260,16 @@ def main():
     ap.add_argument("--impl", default="nms", choices=["nms", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "tc", "direct", "naive"])
     ap.add_argument("--workload", default="box",
-                    choices=["box", "box64", "sphere", "ensemble", "rotations", "post2d"])
+                    choices=["box", "box64", "sphere", "ensemble", "rotations", "post2d", "surrogate"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kc", type=int, default=0, help="cells per TMEM accumulation chunk (0: library default)")
     ap.add_argument("--workspace-gb", type=float, default=0.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--spheres", type=int, default=10000, help="ensemble: number of spheres")
+    ap.add_argument("--items-per-sm", type=int, default=0, help="tensor path: GEMM work items per SM (0: library)")
+    ap.add_argument("--single-sum", action="store_true",
+                    help="ensemble: the same cells as one sum (centres applied, no per-object amplitudes)")
     ap.add_argument("--sets", type=int, default=1,
                     help="loop mode: S magnetization states of the workload along a field sweep in one plan")
     args = ap.parse_args()
@@ -280,7 +285,16 @@ def main():
     nms.load()
     if args.workload == "post2d":
         return run_post2d(args, rank, world, dev)
-    field, grid_kw, edges, r, desc, rot, dilute = make_workload(args.workload)
+    if args.workload == "surrogate":
+        return run_surrogate(args, rank, world, dev)
+    field, grid_kw, edges, r, desc, rot, dilute = make_workload(args.workload, args.spheres)
+    if args.single_sum and field.offsets is not None:
+        # batching overhead reference: every cell moved to its object's centre, one summand
+        from paper_2601_18444_gb300 import inputs as I
+        cen = np.repeat(field.centers, np.diff(field.offsets), axis=0) if field.centers is not None else 0.0
+        field = I.Field(field.pos + cen, field.vol, field.nuc, field.mag, name=field.name)
+        dilute = False
+        desc += "; one sum over all cells (no per-object amplitudes)"
     field0 = field
     if args.sets > 1:
         from paper_2601_18444_gb300 import inputs as I
@@ -293,7 +307,8 @@ def main():
     stream = torch.cuda.current_stream()
     g = nms.make_grid(**grid_kw)
     opt = nms.nms_options_default(precision=prec, timing=1, kc_cells=args.kc, want_dilute=1 if dilute else 0,
-                                  workspace_bytes=int(args.workspace_gb * (1 << 30)), n_sets=max(1, args.sets))
+                                  workspace_bytes=int(args.workspace_gb * (1 << 30)), n_sets=max(1, args.sets),
+                                  split_k=args.items_per_sm)
     plan = nms.plan_from_field(field, g, opt, rot=rot, stream=stream.cuda_stream)
     npix = plan.npix
     n_rot = 1 if rot is None else len(rot)
@@ -529,6 +544,81 @@ def run_post2d(args, rank, world, dev):
                 "gpu_launches": args.steps * 7, "clocks": clocks}
         print(json.dumps(line), flush=True)
     plan.close()
+    return 0
+
+
+# Tensor flops of one MLP step per sample, 6 -> H -> H -> n_out: forward
+# 2 (6 H + H^2 + H n_out); training adds about twice that for the backward GEMMs.
+def mlp_flops(n_in, H, n_out):
+    return 2.0 * (n_in * H + H * H + H * n_out)
+
+
+def run_surrogate(args, rank, world, dev):
+    """Learned surrogate (scaled-down vortex family): training curves from the
+    batched transform, then timed training epochs and timed inference on 2^20
+    queries; the MLP GEMMs against the bf16 dense peak."""
+    import torch
+    from paper_2601_18444_gb300 import inputs as I
+    from paper_2601_18444_gb300 import nms
+    from paper_2601_18444_gb300 import surrogate as SG
+    edges = np.geomspace(0.04, 1.2, 65)
+    params = I.vortex_family_params(2048, seed=21)
+    t0 = time.perf_counter()
+    Iq, _, t_tr, terms_tr = SG.generate_curves(params, edges, a=2.5, n_rot=16)
+    ok = np.all(np.isfinite(Iq), axis=0)
+    Y = torch.tensor(SG.log_targets(Iq[:, ok]), device="cuda")
+    X = torch.tensor(params.astype(np.float32), device="cuda")
+    n_out, H = int(ok.sum()), 256
+    lo = I.VORTEX_FAMILY_BOUNDS[:, 0].astype(np.float32)
+    hi = I.VORTEX_FAMILY_BOUNDS[:, 1].astype(np.float32)
+    s = nms.nms_surrogate_create(6, H, n_out, lo, hi, seed=3, stream=torch.cuda.current_stream().cuda_stream)
+    nms.nms_surrogate_train(s, X, Y, batch=128, epochs=max(1, args.warmup), lr=1e-3, seed=4)
+    torch.cuda.synchronize()
+    epochs = 20 * max(1, args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        e0.record()
+        nms.nms_surrogate_train(s, X, Y, batch=128, epochs=epochs, lr=1e-3, seed=5)
+        e1.record()
+        e1.synchronize()
+        ms_train = e0.elapsed_time(e1)
+        nq = 1 << 20
+        q = torch.tensor(I.vortex_family_params(nq, seed=23).astype(np.float32), device="cuda")
+        out = torch.empty((nq, n_out), device="cuda")
+        nms.nms_surrogate_infer(s, q, out)
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(max(1, args.steps)):
+            e0.record()
+            nms.nms_surrogate_infer(s, q, out)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    ms_inf = float(np.mean(times))
+    peaks, peak_src = load_peaks()
+    clocks = clk.summary(peaks.get("sm_max_mhz", 2070.0))
+    f_inf = nq * mlp_flops(6, H, n_out)
+    achieved = f_inf / (ms_inf * 1e-3) / 1e12
+    peak = peaks.get("bf16_tflops", 1900.0)
+    train_samples = epochs * len(params)
+    if rank == 0:
+        line = {"metric": "surrogate inference queries/s (MLP 6->256->256->n_out, bf16 GEMMs)",
+                "value": world * nq / (ms_inf * 1e-3), "unit": "queries/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_inf, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16->f32", "data": "synthetic",
+                "config": {"workload": f"vortex family, {len(params)} training curves from the batched transform "
+                                       f"(a=2.5nm, 16 orientations, 128^2 detector, {n_out} log bins); "
+                                       f"inference on 2^20 queries",
+                           "curves_s": t_tr, "curve_terms_per_s": terms_tr / t_tr,
+                           "train_samples_per_s": train_samples / (ms_train * 1e-3),
+                           "exact_ms_per_curve": 1e3 * t_tr / len(params),
+                           "surrogate_us_per_query": 1e3 * ms_inf / nq},
+                "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "traffic": None, "kernel": "k_mlp_gemm (mma.sync bf16)",
+                             "peak_source": f"{peak_src} bf16 dense"},
+                "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    s.close()
     return 0
 
 

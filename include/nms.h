@@ -90,7 +90,9 @@ typedef struct {
     double b_H;              /* magnetic scattering length b_H; 0 -> 1           */
     double P[3];             /* polarisation unit vector; all 0 -> e_z           */
     int32_t kc_cells;        /* tensor path: cells per FP32 TMEM chunk; 0 -> auto */
-    int32_t split_k;         /* tensor path: K splits across CTAs; 0 -> auto     */
+    int32_t split_k;         /* tensor path: work items per SM of a GEMM launch
+                                (how finely the cells of each output are split
+                                over CTAs); 0 -> 8, or the autotuned value      */
     int64_t max_spin;        /* bounded device waits: poll iterations before the
                                 kernel gives up with NMS_ERR_TIMEOUT; 0 -> default */
     int64_t workspace_bytes; /* cap on tensor-path table workspace; 0 -> default */

@@ -100,9 +100,24 @@ __device__ __forceinline__ int pair_idx(int a, int b)  // a < b
     return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
 }
 
-// G[16][npix] += sum_o F_o F_o^dagger (F_o: [4][npix] complex FP64 at
-// F + o * ostride doubles).
-__global__ void k_gacc_batch(const double2* __restrict__ F, int n_out, int64_t ostride2, int64_t npix,
+// Complex value idx of an amplitude array as FP32: two-float
+// (re hi, re lo, im hi, im lo) when TF, else FP64 (re, im).
+template <bool TF>
+__device__ __forceinline__ float2 load_c(const void* __restrict__ F, int64_t idx)
+{
+    if constexpr (TF) {
+        const float4 v = reinterpret_cast<const float4*>(F)[idx];
+        return make_float2(v.x + v.y, v.z + v.w);
+    } else {
+        const double2 v = reinterpret_cast<const double2*>(F)[idx];
+        return make_float2((float)v.x, (float)v.y);
+    }
+}
+
+// G[16][npix] += sum_o F_o F_o^dagger (F_o: [4][npix] complex at F + o *
+// ostride2 complex values; two-float GEMM outputs or FP64 totals).
+template <bool TF>
+__global__ void k_gacc_batch(const void* __restrict__ F, int n_out, int64_t ostride2, int64_t npix,
                              double* __restrict__ G)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -113,10 +128,7 @@ __global__ void k_gacc_batch(const double2* __restrict__ F, int n_out, int64_t o
     for (int o = 0; o < n_out; ++o) {
         float2 f[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const double2 v = F[(int64_t)o * ostride2 + (int64_t)c * npix + p];
-            f[c] = make_float2((float)v.x, (float)v.y);
-        }
+        for (int c = 0; c < 4; ++c) f[c] = load_c<TF>(F, (int64_t)o * ostride2 + (int64_t)c * npix + p);
 #pragma unroll
         for (int a = 0; a < 4; ++a) ts_acc(hi[a], lo[a], fmaf(f[a].x, f[a].x, f[a].y * f[a].y));
 #pragma unroll
@@ -132,15 +144,33 @@ __global__ void k_gacc_batch(const double2* __restrict__ F, int n_out, int64_t o
     for (int k = 0; k < 16; ++k) G[(int64_t)k * npix + p] += (double)hi[k] + (double)lo[k];
 }
 
-cudaError_t launch_gacc_batch(const double* F, int n_out, int64_t ostride, int64_t npix, double* G, cudaStream_t s)
+cudaError_t launch_gacc_batch(const double* F, int n_out, int64_t ostride, int64_t npix, double* G, bool two_float,
+                              cudaStream_t s)
 {
     if (n_out <= 0) return cudaSuccess;
-    k_gacc_batch<<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(reinterpret_cast<const double2*>(F), n_out,
-                                                                ostride / 2, npix, G);
+    const unsigned blocks = (unsigned)((npix + 127) / 128);
+    if (two_float) k_gacc_batch<true><<<blocks, 128, 0, s>>>(F, n_out, ostride / 2, npix, G);
+    else k_gacc_batch<false><<<blocks, 128, 0, s>>>(F, n_out, ostride / 2, npix, G);
     return cudaGetLastError();
 }
 
-// One pass over a batch of object amplitudes F_o (FP64 [n_out][4][npix]):
+// FP64 amplitudes from two-float ones: (re hi + re lo, im hi + im lo)
+__global__ void k_tf_to_f64(const float4* __restrict__ src, double2* __restrict__ dst, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 v = src[i];
+    dst[i] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
+
+cudaError_t launch_tf_to_f64(const double* src, double* dst, int64_t n_complex, cudaStream_t s)
+{
+    k_tf_to_f64<<<(unsigned)((n_complex + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(src),
+                                                                    reinterpret_cast<double2*>(dst), n_complex);
+    return cudaGetLastError();
+}
+
+// One pass over a batch of object amplitudes F_o (two-float [n_out][4][npix]):
 //   G_dil[16][p]              += F_o F_o^dagger                  (dilute part)
 //   Ftot[out_rot[o]][c][p]    += F_o[c][p] exp(-i (q_y cy_o + q_z cz_o))
 // The shift phase is a two-float product in turns reduced exactly (as in the
@@ -148,15 +178,15 @@ cudaError_t launch_gacc_batch(const double* F, int n_out, int64_t ostride, int64
 // two-float shifted sums to FP64 once per rotation.  The next output's
 // amplitudes are loaded while the current one is processed, so each thread
 // keeps two outputs' loads in flight.
-__device__ __forceinline__ void load_f(const double2* __restrict__ F, int64_t o, int64_t ostride2, int64_t npix,
-                                       int64_t p, double2* v)
+__device__ __forceinline__ void load_f(const float4* __restrict__ F, int64_t o, int64_t ostride2, int64_t npix,
+                                       int64_t p, float4* v)
 {
 #pragma unroll
     for (int c = 0; c < 4; ++c) v[c] = F[o * ostride2 + (int64_t)c * npix + p];
 }
 
 __global__ void __launch_bounds__(128)
-k_dilute_shift_batch(const double2* __restrict__ F, int n_out, int64_t ostride2, const float4* __restrict__ cyz,
+k_dilute_shift_batch(const float4* __restrict__ F, int n_out, int64_t ostride2, const float4* __restrict__ cyz,
                      const int32_t* __restrict__ out_rot, const float4* __restrict__ qturn, int64_t npix,
                      double* __restrict__ Gdil, double2* __restrict__ Ftot, int64_t tstride2)
 {
@@ -168,13 +198,13 @@ k_dilute_shift_batch(const double2* __restrict__ F, int n_out, int64_t ostride2,
     for (int k = 0; k < 16; ++k) { gh[k] = 0.f; gl[k] = 0.f; }
 #pragma unroll
     for (int k = 0; k < 8; ++k) { th[k] = 0.f; tl[k] = 0.f; }
-    double2 nxt[4];
+    float4 nxt[4];
     load_f(F, 0, ostride2, npix, p, nxt);
     int cur = out_rot[0];
     for (int o = 0; o < n_out; ++o) {
         float2 f[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) f[c] = make_float2((float)nxt[c].x, (float)nxt[c].y);
+        for (int c = 0; c < 4; ++c) f[c] = make_float2(nxt[c].x + nxt[c].y, nxt[c].z + nxt[c].w);
         if (o + 1 < n_out) load_f(F, o + 1, ostride2, npix, p, nxt);
         const int r = out_rot[o];
         if (r != cur) {
@@ -237,7 +267,7 @@ cudaError_t launch_dilute_shift_batch(const double* F, int n_out, int64_t ostrid
 {
     if (n_out <= 0) return cudaSuccess;
     k_dilute_shift_batch<<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(
-        reinterpret_cast<const double2*>(F), n_out, ostride / 2, cyz, out_rot, qturn, npix, Gdil,
+        reinterpret_cast<const float4*>(F), n_out, ostride / 2, cyz, out_rot, qturn, npix, Gdil,
         reinterpret_cast<double2*>(Ftot), tstride / 2);
     return cudaGetLastError();
 }
@@ -249,11 +279,11 @@ namespace nms {
 // Per-object azimuthal binning of one response evaluated from a batch of
 // amplitudes: Iobj[obj[o]][bin(p)] += resp(F_o, p) over the pixels of each
 // bin (Eq. iqazi on the ring bins of the detector).  The response is formed
-// in FP32 from the FP64 amplitudes:
+// in FP32 from the two-float amplitudes:
 //   N  = s |F_N|^2,  M = s b^2 (|F_M|^2 - |qhat.F_M|^2)   (|Q|^2, Eq. HJdef)
 //   P  = s b^2 |u.F_M|^2, u = P - qhat (qhat.P)            (Eq. PSANSdef)
 //   SF = M - P,  UNPOL = N + M.
-__global__ void k_obj_bin(const double2* __restrict__ F, int n_out, const int32_t* __restrict__ out_obj,
+__global__ void k_obj_bin(const float4* __restrict__ F, int n_out, const int32_t* __restrict__ out_obj,
                           const double* __restrict__ hy, const double* __restrict__ hz,
                           const int32_t* __restrict__ bin_of, int64_t npix, int nbins, int id, float s, float b,
                           float Px, float Py, float Pz, double* __restrict__ Iobj)
@@ -262,15 +292,15 @@ __global__ void k_obj_bin(const double2* __restrict__ F, int n_out, const int32_
     const int o = blockIdx.y;
     for (int k = threadIdx.x; k < nbins; k += blockDim.x) s_bins[k] = 0.f;
     __syncthreads();
-    const double2* Fo = F + (int64_t)o * 4 * npix;
+    const float4* Fo = F + (int64_t)o * 4 * npix;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
         const int bin = bin_of[p];
         if (bin < 0) continue;
         float2 f[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const double2 v = Fo[(int64_t)c * npix + p];
-            f[c] = make_float2((float)v.x, (float)v.y);
+            const float4 v = Fo[(int64_t)c * npix + p];
+            f[c] = make_float2(v.x + v.y, v.z + v.w);
         }
         const float y = (float)hy[p], z = (float)hz[p];
         const float nn = f[0].x * f[0].x + f[0].y * f[0].y;
@@ -306,7 +336,7 @@ cudaError_t launch_obj_bin(const double* F, int n_out, const int32_t* out_obj, c
     if (n_out <= 0) return cudaSuccess;
     const int64_t pix_blocks = std::min<int64_t>((p.npix + 1023) / 1024, 64);
     dim3 grid((unsigned)pix_blocks, (unsigned)n_out);
-    k_obj_bin<<<grid, 256, nbins * sizeof(float), s>>>(reinterpret_cast<const double2*>(F), n_out, out_obj, p.d_hy,
+    k_obj_bin<<<grid, 256, nbins * sizeof(float), s>>>(reinterpret_cast<const float4*>(F), n_out, out_obj, p.d_hy,
                                                        p.d_hz, bin_of, p.npix, nbins, id, (float)(1.0 / p.V),
                                                        (float)p.bH, (float)p.P[0], (float)p.P[1], (float)p.P[2], Iobj);
     return cudaGetLastError();

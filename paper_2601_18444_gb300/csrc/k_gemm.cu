@@ -381,6 +381,34 @@ __device__ __forceinline__ uint64_t f2_pack(float lo_lane, float hi_lane)
 }
 
 __device__ __forceinline__ float f2_lane0(uint64_t v) { return __uint_as_float((uint32_t)v); }
+
+// Two-float sum (a_hi, a_lo) + (b_hi, b_lo) with TwoSum on both words and
+// renormalisation, so neither low word has to be small (a GEMM partial's low
+// word can hold whole chunk partials); relative error ~2^-44.
+__device__ __forceinline__ float2 tf_add(float ah, float al, float bh, float bl)
+{
+    float s = ah + bh;
+    float bb = s - ah;
+    float e = (ah - (s - bb)) + (bh - bb);
+    const float t = al + bl;
+    bb = t - al;
+    const float f = (al - (t - bb)) + (bl - bb);
+    e += t;
+    float h = s + e;                 // FastTwoSum(s, e)
+    e = e - (h - s);
+    e += f;
+    s = h + e;                       // FastTwoSum(h, e)
+    return make_float2(s, e - (s - h));
+}
+
+// two-float complex (re hi, re lo, im hi, im lo) sum
+__device__ __forceinline__ float4 tf_add4(float4 a, float4 b)
+{
+    const float2 re = tf_add(a.x, a.y, b.x, b.y);
+    const float2 im = tf_add(a.z, a.w, b.z, b.w);
+    return make_float4(re.x, re.y, im.x, im.y);
+}
+
 __device__ __forceinline__ float f2_lane1(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
 
 template <int W>
@@ -542,6 +570,8 @@ struct GemmItem {
     int32_t kb0, kb1;     // k-block range (within this chunk's tables)
     int32_t slot;         // output slot in P (clusters: of rank 0); < 0: direct to output -1 - slot
     int32_t slot1;        // clusters: output slot of rank 1 (direct: equal to slot)
+    int32_t store;        // direct: 1 = first piece of its output (store), 0 = add
+    int32_t pad;
 };
 
 struct GemmArgs {
@@ -553,8 +583,8 @@ struct GemmArgs {
     const GemmItem* items;
     int n_items;
     int kcb;              // k-blocks per TMEM chunk (drain interval)
-    double* P;            // [slots][128][128]
-    double* F;            // direct outputs: [out][nch][ny*nz] complex (re, im)
+    double* P;            // [slots][128][128] two-float (hi, lo) per element
+    double* F;            // direct outputs: [out][nch][ny*nz] complex, two-float (re hi, re lo, im hi, im lo)
     int ny, nz;
     int nch;              // channels per output (4 per weight set), a power of two
     double scale[4];      // direct outputs: per-channel scale of the unscaled sums
@@ -828,18 +858,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
             }
             if (!ok) break;
             const int slot = (CLUSTER && rank) ? item.slot1 : item.slot;
+            // results leave as two-float pairs (no FP64 arithmetic here: GB300
+            // issues few FP64 operations per clock)
             if (slot >= 0) {
-                // this item's tile, unscaled, FP64
-                double* out = g.P + (int64_t)slot * (TC_BM * TC_BN) + (int64_t)(quad * 32 + lane) * TC_BN + colh;
+                // this item's tile, unscaled: (hi, lo) per element
+                float4* out = reinterpret_cast<float4*>(g.P + (int64_t)slot * (TC_BM * TC_BN) +
+                                                        (int64_t)(quad * 32 + lane) * TC_BN + colh);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    double2 v = make_double2((double)f2_lane0(hi[i]) + (double)f2_lane0(lo[i]),
-                                             (double)f2_lane1(hi[i]) + (double)f2_lane1(lo[i]));
-                    reinterpret_cast<double2*>(out)[i] = v;
-                }
+                for (int i = 0; i < 16; ++i)
+                    out[i] = make_float4(f2_lane0(hi[i]), f2_lane0(lo[i]), f2_lane1(hi[i]), f2_lane1(lo[i]));
             } else {
-                // the whole k-range of this output: row m = 4a + c, columns
-                // n = 2b + (re, im) for 16 consecutive b, added into F
+                // the whole k-range of this output: row m = nch a + c, columns
+                // n = 2b + (re, im) for 16 consecutive b, into F
                 const int mtile = MODE == 2 ? 2 * item.mt + rank : item.mt;
                 const int ntile = MODE == 1 ? 2 * item.nt + rank : item.nt;
                 const int m = mtile * TC_BM + quad * 32 + lane;
@@ -847,16 +877,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
                 const int b0 = (ntile * TC_BN + colh) >> 1;
                 if (a < g.ny) {
                     const int64_t npix = (int64_t)g.ny * g.nz;
-                    double2* o = reinterpret_cast<double2*>(g.F) + ((int64_t)(-1 - slot) * g.nch + ch) * npix +
-                                 (int64_t)a * g.nz + b0;
+                    float4* o = reinterpret_cast<float4*>(g.F) + ((int64_t)(-1 - slot) * g.nch + ch) * npix +
+                                (int64_t)a * g.nz + b0;
                     const int c4 = ch & 3;
-                    const double sc = c4 == 0 ? g.scale[0] : c4 == 1 ? g.scale[1] : c4 == 2 ? g.scale[2] : g.scale[3];
+                    // a power of two, exact in FP32 (checked at plan creation)
+                    const float sc =
+                        (float)(c4 == 0 ? g.scale[0] : c4 == 1 ? g.scale[1] : c4 == 2 ? g.scale[2] : g.scale[3]);
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         if (b0 + i < g.nz) {
-                            double2 v = o[i];
-                            v.x += sc * ((double)f2_lane0(hi[i]) + (double)f2_lane0(lo[i]));
-                            v.y += sc * ((double)f2_lane1(hi[i]) + (double)f2_lane1(lo[i]));
+                            float4 v = make_float4(sc * f2_lane0(hi[i]), sc * f2_lane0(lo[i]), sc * f2_lane1(hi[i]),
+                                                   sc * f2_lane1(lo[i]));
+                            if (!item.store) v = tf_add4(v, o[i]);
                             o[i] = v;
                         }
                     }
@@ -871,14 +903,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
     if (warp == 1) tc_dealloc<C::CG>(taddr, 512);
 }
 
-// Reduction of item tiles into per-output amplitudes:
-//   F[out][c][p][r] += scale_{c mod 4} * sum_{s < splits} P[slot_base + (mt*ntiles + nt)*splits + s][row][col]
+// Reduction of item tiles (two-float elements) into per-output amplitudes
+// (two-float complex; stored by an output's first piece, added by later ones):
+//   F[out][c][p][r] (+)= scale_{c mod 4} * sum_{s < splits} P[slot_base + (mt*ntiles + nt)*splits + s][row][col]
 // with m = nch*a + c = mt*128 + row, n = 2b + r = nt*128 + col, p = a*nz + b.
 struct RedDesc {
     int32_t slot_base;
     int32_t splits;
     int32_t out;
-    int32_t pad;
+    int32_t store;        // 1: first piece of its output (store), 0: add
 };
 
 struct Scale4 {
@@ -900,17 +933,16 @@ __global__ void k_gemm_reduce(const double* __restrict__ P, const RedDesc* __res
     const int mt = m >> 7, row = m & 127, nt = n >> 7, col = n & 127;
     const RedDesc d = reds[r];
     const int64_t base = (int64_t)d.slot_base + (int64_t)(mt * ntiles + nt) * d.splits;
-    double re = 0.0, im = 0.0;
-    for (int s = 0; s < d.splits; ++s) {
-        const double2 v = *reinterpret_cast<const double2*>(P + (base + s) * (TC_BM * TC_BN) + row * TC_BN + col);
-        re += v.x;
-        im += v.y;
-    }
-    double2* o = reinterpret_cast<double2*>(F) + ((int64_t)d.out * nch + c) * npix + p;
-    double2 t = *o;
-    t.x += scale.v[c & 3] * re;
-    t.y += scale.v[c & 3] * im;
-    *o = t;
+    // two-float sums in FP32 (FP64 is slow on GB300); the scale is a power
+    // of two, exact in FP32
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int s = 0; s < d.splits; ++s)
+        acc = tf_add4(acc, *reinterpret_cast<const float4*>(P + (base + s) * (TC_BM * TC_BN) + row * TC_BN + col));
+    const float sc = (float)scale.v[c & 3];
+    acc = make_float4(acc.x * sc, acc.y * sc, acc.z * sc, acc.w * sc);
+    float4* o = reinterpret_cast<float4*>(F) + ((int64_t)d.out * nch + c) * npix + p;
+    if (!d.store) acc = tf_add4(acc, *o);
+    *o = acc;
 }
 
 // ------------------------------------------------------------------ self-test

@@ -47,7 +47,9 @@ cudaError_t launch_prep_rot(const Plan& p, const RotMat& R, bool global, float4*
                             cudaStream_t s);
 cudaError_t launch_centres(int n_out, const int32_t* out_obj, const int32_t* out_rot, int rot0, const double* rot,
                            const double* cen, float4* cyz, cudaStream_t s);
-cudaError_t launch_gacc_batch(const double* F, int n_out, int64_t ostride, int64_t npix, double* G, cudaStream_t s);
+cudaError_t launch_gacc_batch(const double* F, int n_out, int64_t ostride, int64_t npix, double* G, bool two_float,
+                              cudaStream_t s);
+cudaError_t launch_tf_to_f64(const double* src, double* dst, int64_t n_complex, cudaStream_t s);
 cudaError_t launch_dilute_shift_batch(const double* F, int n_out, int64_t ostride, const float4* cyz,
                                       const int32_t* out_rot, const float4* qturn, int64_t npix, double* Gdil,
                                       double* Ftot, int64_t tstride, cudaStream_t s);
@@ -56,9 +58,10 @@ namespace {
 
 struct HostItem {
     int32_t mt, nt, kb0, kb1, slot, slot1;   // clusters: mt (mode 2) or nt (mode 1) indexes a tile pair
+    int32_t store, pad;                      // direct items: first piece of the output stores
 };
 struct HostRed {
-    int32_t slot_base, splits, out, pad;
+    int32_t slot_base, splits, out, store;   // store: first piece of the output
 };
 
 struct Chunk {
@@ -108,7 +111,7 @@ struct TcState {
     int64_t tab_kb = 0;          // table capacity in k-blocks
     float4* d_cpos_b = nullptr;  // [R_b][n]
     float4* d_cw_b = nullptr;
-    double* d_Fb = nullptr;      // [out_cap][4][npix][2]
+    double* d_Fb = nullptr;      // [out_cap][nch][npix] two-float complex (16 B each)
     double* d_Ftot_b = nullptr;  // [R_b][4][npix][2] (objects)
     float4* d_cyz = nullptr;     // [out_cap]
     double* d_rot = nullptr;     // [n_rot][9]
@@ -193,6 +196,9 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
             int64_t g0, n;
         };
         std::vector<std::vector<Piece>> chunk_pieces(1);
+        // an output's first piece (in launch order) stores, later pieces add,
+        // so the batch's amplitudes need no clearing
+        std::vector<char> started(ob.n_out, 0);
         int64_t cur_kb = 0;
         for (int o = o0; o < o0 + ob.n_out; ++o) {
             const Summand& sm = sums[o];
@@ -231,19 +237,40 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
                     kb_cell0.push_back(pc.g0 + 32 * i);
                     kb_ncell.push_back((int32_t)std::min<int64_t>(32, pc.n - 32 * i));
                 }
-                const int splits = (int)((nkb_p + kb_per_item - 1) / kb_per_item);
                 // (mt, nt) of the first tile of a work unit and its step to the partner tile
                 const int mstep = t.mode == 2 ? 2 : 1, nstep = t.mode == 1 ? 2 : 1;
+                int splits = (int)((nkb_p + kb_per_item - 1) / kb_per_item);
+                if (splits > 1 && pieces.size() == 1) {
+                    // one output in the chunk: round the split count up so the
+                    // (tile unit x split) items fill whole waves of the
+                    // persistent CTAs (pairs), e.g. 64 pair units x 19 splits
+                    // = 16 waves of 76 clusters
+                    const int units = (t.mtiles / mstep) * (t.ntiles / nstep);
+                    const int conc = t.mode ? sms / 2 : sms;
+                    int gcd = units, rem = conc;
+                    while (rem) {
+                        const int r = gcd % rem;
+                        gcd = rem;
+                        rem = r;
+                    }
+                    const int m = conc / gcd;
+                    const int up = ((splits + m - 1) / m) * m;
+                    if (up <= 2 * splits && up <= nkb_p / std::max(1, 2 * t.kcb)) splits = up;
+                }
                 if (splits == 1) {
                     // one item per tile spans the piece: the GEMM adds it into F directly
                     const int32_t direct = -1 - pc.out;
+                    const int32_t first = started[pc.out] ? 0 : 1;
+                    started[pc.out] = 1;
                     for (int mt = 0; mt < t.mtiles; mt += mstep)
                         for (int nt = 0; nt < t.ntiles; nt += nstep)
-                            its.push_back({mt / mstep, nt / nstep, (int32_t)kb, (int32_t)(kb + nkb_p), direct, direct});
+                            its.push_back({mt / mstep, nt / nstep, (int32_t)kb, (int32_t)(kb + nkb_p), direct, direct,
+                                           first, 0});
                     kb += nkb_p;
                     continue;
                 }
-                reds.push_back({slot, splits, pc.out, 0});
+                reds.push_back({slot, splits, pc.out, started[pc.out] ? 0 : 1});
+                started[pc.out] = 1;
                 // k-range major: the CTAs of one wave share each k-range, so
                 // every table block comes from HBM about once and is reused
                 // by all tiles through L2
@@ -255,7 +282,7 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
                             const int s0 = slot + (mt * t.ntiles + nt) * splits + sp;
                             // slot of the partner tile: next B tile (mode 1) or next A tile (mode 2)
                             const int s1 = t.mode == 1 ? s0 + splits : t.mode == 2 ? s0 + t.ntiles * splits : 0;
-                            its.push_back({mt / mstep, nt / nstep, (int32_t)a, (int32_t)b, s0, s1});
+                            its.push_back({mt / mstep, nt / nstep, (int32_t)a, (int32_t)b, s0, s1, 0, 0});
                         }
                 slot += tiles * splits;
                 kb += nkb_p;
@@ -289,14 +316,18 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
 }
 
 // ------------------------------------------------------------------ autotuner
-__global__ void k_amp_maxerr(const double2* __restrict__ A, const double2* __restrict__ B, int64_t npix,
+// max over pixels of |A - B| per channel; A two-float (the GEMM's output
+// format), B FP64
+__global__ void k_amp_maxerr(const float4* __restrict__ A4, const double2* __restrict__ B, int64_t npix,
                              unsigned int* __restrict__ err)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npix) return;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        const double2 a = A[(int64_t)c * npix + p], b = B[(int64_t)c * npix + p];
+        const float4 a4 = A4[(int64_t)c * npix + p];
+        const double2 a = make_double2((double)a4.x + (double)a4.y, (double)a4.z + (double)a4.w);
+        const double2 b = B[(int64_t)c * npix + p];
         const float d = (float)hypot(a.x - b.x, a.y - b.y);
         atomicMax(&err[c], __float_as_uint(d));   // non-negative floats order as integers
     }
@@ -472,7 +503,7 @@ nms_status tc_autotune(Plan& p, TcState& t)
         unsigned int herr[4] = {0, 0, 0, 0};
         if (ce == cudaSuccess) ce = cudaMemsetAsync(d_err, 0, sizeof(herr), s);
         if (ce == cudaSuccess) {
-            k_amp_maxerr<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(reinterpret_cast<const double2*>(d_Fp),
+            k_amp_maxerr<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(d_Fp),
                                                                     reinterpret_cast<const double2*>(p.d_F), np,
                                                                     d_err);
             ce = cudaGetLastError();
@@ -544,6 +575,7 @@ nms_status tc_setup(Plan& p)
     t->mtiles = (t->nch * t->ny + 127) / 128;
     t->ntiles = (2 * t->nz + 127) / 128;
     t->kcb = p.opt.kc_cells > 0 ? std::max(1, p.opt.kc_cells / 32) : 2;
+    if (p.opt.split_k > 0) t->items_per_sm = std::min(256, p.opt.split_k);
     t->objects = p.n_objects > 1 && p.opt.want_dilute;
     // CTA pairs sharing A where the B tiles pair up (the fastest form
     // measured: the two-SM MMA reads less shared memory per product but its
@@ -580,6 +612,12 @@ nms_status tc_setup(Plan& p)
     if ((st = upload(&t->d_qy, qy)) || (st = upload(&t->d_qz, qz))) return st;
     t->W[0] = pow2_ceil(p.h_wmax[0]);
     t->W[1] = t->W[2] = t->W[3] = pow2_ceil(p.h_wmax[1]);
+    // the GEMM applies W_c / 2^24 in FP32 (a power of two: exact while normal)
+    for (int c = 0; c < 4; ++c)
+        if (!(t->W[c] >= 0x1p-90 && t->W[c] <= 0x1p+100)) {
+            set_error("tensor-core path: cell weights V|N|, V|M| outside [2^-90, 2^100]; rescale the inputs");
+            return NMS_ERR_UNSUPPORTED;
+        }
     if ((st = upload(&t->d_rot, p.h_rot))) return st;
     if (t->objects && !p.h_cen.empty()) {
         if ((st = upload(&t->d_cen, p.h_cen))) return st;
@@ -680,7 +718,6 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
         p.timer.end(ST_PREP, nrl);
         if (t.objects) NMS_CUDA_TRY(cudaMemsetAsync(t.d_Ftot_b, 0, (size_t)nrl * nS * F4 * sizeof(double), s));
         for (const OutBatch& ob : S.batches) {
-            NMS_CUDA_TRY(cudaMemsetAsync(t.d_Fb, 0, (size_t)ob.n_out * ostride * sizeof(double), s));
             for (const Chunk& ch : ob.chunks) {
                 p.timer.begin(ST_TABLES);
                 NMS_CUDA_TRY(tc_launch_tables(t.d_cpos_b, t.d_cw_b, t.wstride, t.nch, S.d_kb_cell0 + ch.kb_off,
@@ -717,15 +754,15 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
                                                            t.d_Ftot_b + (size_t)st * F4, (int64_t)nS * F4, s));
                     ++nl;
                 } else {
-                    NMS_CUDA_TRY(launch_gacc_batch(Fs, ob.n_out, ostride, np, p.d_Gtot + (size_t)st * 16 * np, s));
+                    NMS_CUDA_TRY(launch_gacc_batch(Fs, ob.n_out, ostride, np, p.d_Gtot + (size_t)st * 16 * np, true, s));
                     ++nl;
                     if (p.d_Gdil) {
-                        NMS_CUDA_TRY(launch_gacc_batch(Fs, ob.n_out, ostride, np, p.d_Gdil + (size_t)st * 16 * np, s));
+                        NMS_CUDA_TRY(launch_gacc_batch(Fs, ob.n_out, ostride, np, p.d_Gdil + (size_t)st * 16 * np, true, s));
                         ++nl;
                     }
                     if (rb0 + nrl == p.n_rot && &ob == &S.batches.back())
-                        NMS_CUDA_TRY(cudaMemcpyAsync(p.d_F + (size_t)st * F4, Fs + (size_t)(ob.n_out - 1) * ostride,
-                                                     F4 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                        NMS_CUDA_TRY(launch_tf_to_f64(Fs + (size_t)(ob.n_out - 1) * ostride, p.d_F + (size_t)st * F4,
+                                                      4 * np, s));
                 }
             }
             p.timer.end(ST_GACC, nl);
@@ -734,7 +771,7 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
             p.timer.begin(ST_GACC);
             for (int st = 0; st < nS; ++st) {
                 const double* Ts = t.d_Ftot_b + (size_t)st * F4;
-                NMS_CUDA_TRY(launch_gacc_batch(Ts, nrl, (int64_t)nS * F4, np, p.d_Gtot + (size_t)st * 16 * np, s));
+                NMS_CUDA_TRY(launch_gacc_batch(Ts, nrl, (int64_t)nS * F4, np, p.d_Gtot + (size_t)st * 16 * np, false, s));
                 if (rb0 + nrl == p.n_rot)
                     NMS_CUDA_TRY(cudaMemcpyAsync(p.d_Ftot + (size_t)st * F4, Ts + (size_t)(nrl - 1) * nS * F4,
                                                  F4 * sizeof(double), cudaMemcpyDeviceToDevice, s));

@@ -43,7 +43,7 @@ TC_FLOPS_PER_TERM = 96
 # DRAM bytes (read + write) the GEMM moves per byte of phase tables it
 # consumes, from an ncu capture of one launch on the 64x64x64 box (512^2
 # detector); the box workloads scale it by their own table bytes per launch.
-TC_DRAM_PER_TABLE_BYTE = 1.311   # 8.446 GB for 6.442 GB of tables
+TC_DRAM_PER_TABLE_BYTE = 1.334   # 8.596 GB for 6.442 GB of tables
 TC_TRAFFIC_WORKLOADS = ("box", "box64")
 
 
@@ -389,7 +389,9 @@ def main():
         err = [float(np.max(np.abs(F[c][idx] - F_ref[c])) / wsum[c]) if wsum[c] > 0 else 0.0 for c in range(4)]
         cpu = {"value": rate, "unit": "terms/s", "cores": cores, "kind": "oracle", "sample": sample}
 
-    # end to end through the C ABI from pinned host buffers
+    # end to end through the C ABI from pinned host buffers (the timed plan is
+    # released first: every e2e step creates and destroys its own)
+    plan.close()
     e2e = None
     if args.steps > 0 and not args.no_e2e:
         pin = {}
@@ -401,7 +403,7 @@ def main():
         out_u = torch.empty(npix, dtype=torch.float64, pin_memory=True).numpy()
         out_s = torch.empty(npix, dtype=torch.float64, pin_memory=True).numpy()
         e2e_times = []
-        for _ in range(2):
+        for _ in range(3):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             p2 = nms.nms_plan_create(pin["pos"], pin["vol"], pin["nuc"], pin["mag"], field.offsets, field.centers,

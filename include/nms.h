@@ -95,7 +95,9 @@ typedef struct {
                                 over CTAs); 0 -> 8, or the autotuned value      */
     int64_t max_spin;        /* bounded device waits: poll iterations before the
                                 kernel gives up with NMS_ERR_TIMEOUT; 0 -> default */
-    int64_t workspace_bytes; /* cap on tensor-path table workspace; 0 -> default */
+    int64_t workspace_bytes; /* cap on the tensor-path phase-table workspace
+                                (cells beyond it are processed in chunks);
+                                0 -> min(free / 3, 8 GiB)                      */
     int32_t timing;          /* 1: record CUDA events around each stage (see
                                 nms_plan_stage_ms)                               */
     int32_t autotune;        /* tensor path: 1 = time candidate GEMM forms

@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "nms_internal.h"
 
 namespace nms {
@@ -74,6 +76,54 @@ __global__ void k_prep(int64_t n, const double* __restrict__ pos, const double* 
         w64[2 * n + j] = wy;
         w64[3 * n + j] = wz;
     }
+}
+
+// max over cells and weight sets of V_j |N_j| and V_j |M_j| (the operand
+// scales of the tensor path).  Non-negative doubles order like their bit
+// patterns, so the maxima are integer atomics on those patterns.
+__global__ void k_weight_max(int64_t n, int n_sets, const double* __restrict__ vol, const double* __restrict__ nuc,
+                             const double* __restrict__ mag, unsigned long long* __restrict__ out)
+{
+    double wn = 0.0, wm = 0.0;
+    for (int64_t js = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; js < (int64_t)n_sets * n;
+         js += (int64_t)gridDim.x * blockDim.x) {
+        const double v = vol ? fabs(vol[js % n]) : 1.0;
+        if (nuc) wn = fmax(wn, v * fabs(nuc[js]));
+        if (mag) {
+            const double mx = mag[3 * js], my = mag[3 * js + 1], mz = mag[3 * js + 2];
+            wm = fmax(wm, v * sqrt(mx * mx + my * my + mz * mz));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        wn = fmax(wn, __shfl_xor_sync(0xffffffffu, wn, o));
+        wm = fmax(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&out[0], (unsigned long long)__double_as_longlong(wn));
+        atomicMax(&out[1], (unsigned long long)__double_as_longlong(wm));
+    }
+}
+
+cudaError_t launch_weight_max(const Plan& p, double wmax[2], cudaStream_t s)
+{
+    unsigned long long* d = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&d, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    unsigned long long h[2] = {0, 0};
+    e = cudaMemsetAsync(d, 0, sizeof(h), s);
+    const int64_t total = (int64_t)p.n_sets * p.n_cells;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 8 * device_sm_count()));
+    if (e == cudaSuccess) {
+        k_weight_max<<<blocks, 256, 0, s>>>(p.n_cells, p.n_sets, p.d_vol, p.d_nuc, p.d_mag, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    wmax[0] = __builtin_bit_cast(double, h[0]);
+    wmax[1] = __builtin_bit_cast(double, h[1]);
+    return cudaSuccess;
 }
 
 cudaError_t launch_prep(Plan& p, const double* R, cudaStream_t s, int set)

@@ -19,8 +19,82 @@
 // memory pool per device that keeps its memory on release: the default pool
 // hands freed memory back to the driver at every synchronisation, so each
 // call would map fresh pages again.
+namespace {
+// The memory pools are bypassed (plain cudaMalloc / cudaFree and the default
+// stream-ordered pool) when NMS_NO_POOL is set or a CUDA injection tool such
+// as a profiler is attached: kernel replay with device-memory save and
+// restore is only known to work on ordinary allocations.
+bool pools_enabled()
+{
+    static const bool on = getenv("NMS_NO_POOL") == nullptr && getenv("CUDA_INJECTION64_PATH") == nullptr;
+    return on;
+}
+
+struct PlanPool {
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t stream = nullptr;   // allocation-ordering stream
+};
+std::mutex g_plan_pool_mu;
+std::map<int, PlanPool> g_plan_pools;
+
+cudaError_t plan_pool(PlanPool& out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_plan_pool_mu);
+    auto it = g_plan_pools.find(dev);
+    if (it != g_plan_pools.end()) {
+        out = it->second;
+        return cudaSuccess;
+    }
+    PlanPool pp;
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    e = cudaMemPoolCreate(&pp.pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = 16ull << 30;
+    cudaMemPoolSetAttribute(pp.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    e = cudaStreamCreateWithFlags(&pp.stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    g_plan_pools[dev] = pp;
+    out = pp;
+    return cudaSuccess;
+}
+}  // namespace
+
+namespace nms {
+cudaError_t plan_malloc_raw(void** ptr, size_t bytes)
+{
+    *ptr = nullptr;
+    if (!pools_enabled()) return cudaMalloc(ptr, bytes > 0 ? bytes : 8);
+    PlanPool pp;
+    cudaError_t e = plan_pool(pp);
+    if (e != cudaSuccess) return e;
+    e = cudaMallocFromPoolAsync(ptr, bytes > 0 ? bytes : 8, pp.pool, pp.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pp.stream);
+    return e;
+}
+
+void plan_free(void* ptr)
+{
+    if (!ptr) return;
+    if (!pools_enabled()) {
+        cudaFree(ptr);
+        return;
+    }
+    PlanPool pp;
+    if (plan_pool(pp) != cudaSuccess) return;
+    cudaFreeAsync(ptr, pp.stream);
+    cudaStreamSynchronize(pp.stream);
+}
+}  // namespace nms
+
 static cudaError_t tmp_alloc(void** ptr, size_t bytes, cudaStream_t s)
 {
+    if (!pools_enabled()) return cudaMallocAsync(ptr, bytes > 0 ? bytes : 8, s);
     static std::mutex mu;
     static std::map<int, cudaMemPool_t> pools;
     int dev = 0;
@@ -147,23 +221,22 @@ static nms_status dalloc(T** p, size_t count, const char* what)
 {
     *p = nullptr;
     if (count == 0) return NMS_OK;
-    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    cudaError_t e = plan_malloc(p, count * sizeof(T));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(e == cudaErrorMemoryAllocation ? NMS_ERR_OUT_OF_MEMORY : NMS_ERR_CUDA,
-                    std::string("cudaMalloc failed for ") + what + ": " + cudaGetErrorString(e));
+                    std::string("device allocation failed for ") + what + ": " + cudaGetErrorString(e));
     }
     return NMS_OK;
 }
 
-static void dfree(void* p)
-{
-    if (p) cudaFree(p);
-}
+static void dfree(void* p) { plan_free(p); }
 
 static void free_plan(nms_plan_s* p)
 {
     if (!p) return;
+    cudaStreamSynchronize(p->stream);   // nothing of the plan may still run
+
     void* bufs[] = {p->d_pos, p->d_vol, p->d_nuc, p->d_mag, p->d_cen_cell, p->d_qy, p->d_qz, p->d_hy,
                     p->d_hz, p->d_qa, p->d_qturn, p->d_cpos, p->d_w64, p->d_cw, p->d_yz, p->d_F,
                     p->d_Ftot, p->d_Fpart, p->d_Gtot, p->d_Gdil, p->d_err, p->d_tab, p->d_wscale};
@@ -384,18 +457,20 @@ nms_status nms_plan_create(nms_plan_t* out, int64_t n_cells, const double* pos, 
     const int64_t n = n_cells;
     const int64_t nS = p->n_sets;
     if ((st = dalloc(&p->d_pos, 3 * n, "pos"))) return bail(st);
-    NMS_CUDA_TRY(cudaMemcpy(p->d_pos, pos, 3 * n * 8, cudaMemcpyHostToDevice));
+    // inputs go up on the plan's stream (asynchronous from pinned memory);
+    // the stream is synchronised below, before the call returns
+    NMS_CUDA_TRY(cudaMemcpyAsync(p->d_pos, pos, 3 * n * 8, cudaMemcpyHostToDevice, p->stream));
     if (cell_vol) {
         if ((st = dalloc(&p->d_vol, n, "vol"))) return bail(st);
-        NMS_CUDA_TRY(cudaMemcpy(p->d_vol, cell_vol, n * 8, cudaMemcpyHostToDevice));
+        NMS_CUDA_TRY(cudaMemcpyAsync(p->d_vol, cell_vol, n * 8, cudaMemcpyHostToDevice, p->stream));
     }
     if (nuc) {
         if ((st = dalloc(&p->d_nuc, nS * n, "nuc"))) return bail(st);
-        NMS_CUDA_TRY(cudaMemcpy(p->d_nuc, nuc, nS * n * 8, cudaMemcpyHostToDevice));
+        NMS_CUDA_TRY(cudaMemcpyAsync(p->d_nuc, nuc, nS * n * 8, cudaMemcpyHostToDevice, p->stream));
     }
     if (mag) {
         if ((st = dalloc(&p->d_mag, 3 * nS * n, "mag"))) return bail(st);
-        NMS_CUDA_TRY(cudaMemcpy(p->d_mag, mag, 3 * nS * n * 8, cudaMemcpyHostToDevice));
+        NMS_CUDA_TRY(cudaMemcpyAsync(p->d_mag, mag, 3 * nS * n * 8, cudaMemcpyHostToDevice, p->stream));
     }
     if (object_centers) {
         std::vector<double> cc((size_t)3 * n);
@@ -425,15 +500,8 @@ nms_status nms_plan_create(nms_plan_t* out, int64_t n_cells, const double* pos, 
         if ((st = dalloc(&p->d_Ftot, nS * 8 * np, "Ftot"))) return bail(st);
     }
     NMS_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int32_t)));
-    for (int64_t js = 0; js < nS * n; ++js) {
-        const int64_t j = js % n;
-        double v = cell_vol ? fabs(cell_vol[j]) : 1.0;
-        if (nuc) p->h_wmax[0] = std::max(p->h_wmax[0], v * fabs(nuc[js]));
-        if (mag) {
-            double m2 = mag[3 * js] * mag[3 * js] + mag[3 * js + 1] * mag[3 * js + 1] + mag[3 * js + 2] * mag[3 * js + 2];
-            p->h_wmax[1] = std::max(p->h_wmax[1], v * sqrt(m2));
-        }
-    }
+    // max_j V_j |N_j| and max_j V_j |M_j| over all weight sets, on the device
+    NMS_CUDA_TRY(launch_weight_max(*p, p->h_wmax, p->stream));
     p->max_sum_cells = n_cells;
     if (n_objects > 1 && p->opt.want_dilute) {
         p->max_sum_cells = 0;
@@ -838,6 +906,7 @@ nms_status nms_plan_object_iq(nms_plan_t plan, int32_t response_id, int32_t nbin
         }
     }
     for (int b = 0; b < nbins; ++b) p.oiq_qmean[b] = p.oiq_counts[b] ? p.oiq_qmean[b] / p.oiq_counts[b] : NAN;
+    cudaStreamSynchronize(p.stream);   // earlier amplitude calls may still use the old bins
     dfree(p.d_bin_of);
     dfree(p.d_Iobj);
     p.d_bin_of = nullptr;

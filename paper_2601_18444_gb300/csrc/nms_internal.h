@@ -113,6 +113,7 @@ struct Plan {
 // ---------------------------------------------------------------- kernels (launchers)
 // Rotation and weights for cells [0, n): FP64 positions -> two-float, FP32 weights.
 cudaError_t launch_prep(Plan& p, const double* R9, cudaStream_t s, int set = 0);
+cudaError_t launch_weight_max(const Plan& p, double wmax[2], cudaStream_t s);
 // Direct sum over cells [c0, c1) of the given position array into split partials.
 cudaError_t launch_direct(const Plan& p, const float4* cpos, int64_t c0, int64_t c1,
                           bool compensated, int splits, cudaStream_t s);
@@ -153,6 +154,19 @@ void tc_release(Plan& p);
 
 int device_sm_count();
 cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t* err, cudaStream_t s);
+
+// Device memory of plans: a per-device library memory pool that keeps up to
+// 16 GiB of freed memory for later plans (creating and destroying a plan
+// then maps and unmaps no pages).  Both calls behave like cudaMalloc /
+// cudaFree: the memory is usable on any stream when plan_malloc returns, and
+// plan_free must only see memory no pending work uses.
+cudaError_t plan_malloc_raw(void** ptr, size_t bytes);
+void plan_free(void* ptr);
+template <class T>
+inline cudaError_t plan_malloc(T** ptr, size_t bytes)
+{
+    return plan_malloc_raw(reinterpret_cast<void**>(ptr), bytes);
+}
 
 // Ring bin of |q| = x: b with e[b] <= x < e[b+1] (e increasing, nb bins), or
 // -1 outside [e[0], e[nb]) and for NaN.

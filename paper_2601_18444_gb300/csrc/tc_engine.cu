@@ -135,7 +135,7 @@ static nms_status upload(T** d, const std::vector<T>& h)
 {
     *d = nullptr;
     if (h.empty()) return NMS_OK;
-    NMS_CUDA_TRY(cudaMalloc((void**)d, h.size() * sizeof(T)));
+    NMS_CUDA_TRY(plan_malloc((void**)d, h.size() * sizeof(T)));
     NMS_CUDA_TRY(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
     return NMS_OK;
 }
@@ -144,7 +144,7 @@ static void free_schedule(Schedule& s)
 {
     void* b[] = {s.d_kb_cell0, s.d_kb_ncell, s.d_items, s.d_reds, s.d_out_obj, s.d_out_rot};
     for (void* x : b)
-        if (x) cudaFree(x);
+        if (x) plan_free(x);
     s = Schedule();
 }
 
@@ -305,11 +305,11 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
         (st = upload(&S.d_out_obj, out_obj)) || (st = upload(&S.d_out_rot, out_rot)))
         return st;
     if (!items.empty()) {
-        NMS_CUDA_TRY(cudaMalloc(&S.d_items, items.size() * sizeof(HostItem)));
+        NMS_CUDA_TRY(plan_malloc(&S.d_items, items.size() * sizeof(HostItem)));
         NMS_CUDA_TRY(cudaMemcpy(S.d_items, items.data(), items.size() * sizeof(HostItem), cudaMemcpyHostToDevice));
     }
     if (!reds.empty()) {
-        NMS_CUDA_TRY(cudaMalloc(&S.d_reds, reds.size() * sizeof(HostRed)));
+        NMS_CUDA_TRY(plan_malloc(&S.d_reds, reds.size() * sizeof(HostRed)));
         NMS_CUDA_TRY(cudaMemcpy(S.d_reds, reds.data(), reds.size() * sizeof(HostRed), cudaMemcpyHostToDevice));
     }
     return NMS_OK;
@@ -438,9 +438,9 @@ nms_status tc_autotune(Plan& p, TcState& t)
     double* d_sw = nullptr;
     unsigned int* d_err = nullptr;
     double* d_Fp = nullptr;
-    NMS_CUDA_TRY(cudaMalloc(&d_sw, 4 * sizeof(double)));
-    NMS_CUDA_TRY(cudaMalloc(&d_err, 4 * sizeof(unsigned int)));
-    NMS_CUDA_TRY(cudaMalloc(&d_Fp, (size_t)t.nch * 2 * np * sizeof(double)));
+    NMS_CUDA_TRY(plan_malloc(&d_sw, 4 * sizeof(double)));
+    NMS_CUDA_TRY(plan_malloc(&d_err, 4 * sizeof(unsigned int)));
+    NMS_CUDA_TRY(plan_malloc(&d_Fp, (size_t)t.nch * 2 * np * sizeof(double)));
     NMS_CUDA_TRY(cudaMemsetAsync(d_sw, 0, 4 * sizeof(double), s));
     k_wabs_sum<<<std::max(1, std::min(4 * sms, (int)((nprobe + 255) / 256))), 256, 0, s>>>(t.d_cw_b, c0, c1, d_sw);
     NMS_CUDA_TRY(cudaGetLastError());
@@ -479,7 +479,7 @@ nms_status tc_autotune(Plan& p, TcState& t)
         st = build_schedule(p, t, probe, 1, 1, S);
         if (st) break;
         double* P = nullptr;
-        cudaError_t ce = cudaMalloc(&P, (size_t)std::max<int64_t>(1, S.max_items) * 128 * 128 * sizeof(double));
+        cudaError_t ce = plan_malloc(&P, (size_t)std::max<int64_t>(1, S.max_items) * 128 * 128 * sizeof(double));
         if (ce != cudaSuccess) { free_schedule(S); st = cuda_fail(ce, "autotune partials"); break; }
         float ms = 1e30f;
         const Chunk& ch = S.batches[0].chunks[0];
@@ -510,7 +510,7 @@ nms_status tc_autotune(Plan& p, TcState& t)
         }
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(herr, d_err, sizeof(herr), cudaMemcpyDeviceToHost, s);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-        cudaFree(P);
+        plan_free(P);
         free_schedule(S);
         if (ce != cudaSuccess) { st = cuda_fail(ce, "autotune probe"); break; }
         double err = 0.0;
@@ -526,9 +526,9 @@ nms_status tc_autotune(Plan& p, TcState& t)
     memcpy(p.timer.launches, launches_before, sizeof(launches_before));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(d_sw);
-    cudaFree(d_err);
-    cudaFree(d_Fp);
+    plan_free(d_sw);
+    plan_free(d_err);
+    plan_free(d_Fp);
     if (st) return st;
     NMS_CUDA_TRY(cudaMemsetAsync(p.d_err, 0, sizeof(int32_t), s));
     t.kcb = best.kcb;
@@ -633,22 +633,22 @@ nms_status tc_setup(Plan& p)
     const int64_t per_rot = n * 16 * (1 + t->nch / 4);
     t->R_b = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)p.n_rot, 64, (2ll << 30) / std::max<int64_t>(1, per_rot)}));
     t->wstride = (int64_t)t->R_b * n;
-    NMS_CUDA_TRY(cudaMalloc(&t->d_cpos_b, (size_t)t->R_b * n * sizeof(float4)));
-    NMS_CUDA_TRY(cudaMalloc(&t->d_cw_b, (size_t)(t->nch / 4) * t->wstride * sizeof(float4)));
+    NMS_CUDA_TRY(plan_malloc(&t->d_cpos_b, (size_t)t->R_b * n * sizeof(float4)));
+    NMS_CUDA_TRY(plan_malloc(&t->d_cw_b, (size_t)(t->nch / 4) * t->wstride * sizeof(float4)));
     // padding sets (up to the power of two) keep zero weights
     NMS_CUDA_TRY(cudaMemset(t->d_cw_b, 0, (size_t)(t->nch / 4) * t->wstride * sizeof(float4)));
     // output amplitude batch: up to 1 GB, nch complex channels per output
     const int64_t out_bytes = (int64_t)t->nch * np * 16;
     const int64_t outs_per_rb = t->objects ? (int64_t)t->R_b * p.n_objects : t->R_b;
     const int out_cap = (int)std::max<int64_t>(1, std::min<int64_t>(outs_per_rb, (1ll << 30) / out_bytes));
-    NMS_CUDA_TRY(cudaMalloc(&t->d_Fb, (size_t)out_cap * out_bytes));
-    NMS_CUDA_TRY(cudaMalloc(&t->d_cyz, (size_t)out_cap * sizeof(float4)));
+    NMS_CUDA_TRY(plan_malloc(&t->d_Fb, (size_t)out_cap * out_bytes));
+    NMS_CUDA_TRY(plan_malloc(&t->d_cyz, (size_t)out_cap * sizeof(float4)));
     // total amplitude per prepared rotation and weight set
-    if (t->objects) NMS_CUDA_TRY(cudaMalloc(&t->d_Ftot_b, (size_t)t->R_b * t->nsets * 8 * np * sizeof(double)));
+    if (t->objects) NMS_CUDA_TRY(plan_malloc(&t->d_Ftot_b, (size_t)t->R_b * t->nsets * 8 * np * sizeof(double)));
     // phase tables: as many k-blocks as the workspace allows
     const int64_t per_kb = (int64_t)(t->mtiles + t->ntiles) * 2 * (int64_t)tc_block_bytes();
     const int64_t budget = p.opt.workspace_bytes > 0 ? p.opt.workspace_bytes
-                                                     : (int64_t)std::min<size_t>(free_b / 3, (size_t)48 << 30);
+                                                     : (int64_t)std::min<size_t>(free_b / 3, (size_t)8 << 30);
     int64_t total_kb = 0;
     if (t->objects) {
         for (int64_t k = 0; k < p.n_objects; ++k) total_kb += (p.h_off[k + 1] - p.h_off[k] + 31) / 32;
@@ -658,7 +658,7 @@ nms_status tc_setup(Plan& p)
     total_kb *= t->R_b;
     t->tab_kb = std::max<int64_t>(1, std::min<int64_t>(total_kb, budget / per_kb));
     p.tab_bytes = (size_t)t->tab_kb * per_kb;
-    NMS_CUDA_TRY(cudaMalloc(&p.d_tab, p.tab_bytes));
+    NMS_CUDA_TRY(plan_malloc(&p.d_tab, p.tab_bytes));
     // schedules: a full rotation batch and the remainder
     if (p.opt.autotune) {
         if ((st = tc_autotune(p, *t))) return st;
@@ -669,7 +669,7 @@ nms_status tc_setup(Plan& p)
         if ((st = build_schedule(p, *t, plan_summands(p, *t, rem), rem, out_cap, t->last))) return st;
     }
     const int64_t slots = std::max(t->full.max_items, t->last.max_items);
-    NMS_CUDA_TRY(cudaMalloc(&t->d_P, (size_t)std::max<int64_t>(1, slots) * 128 * 128 * sizeof(double)));
+    NMS_CUDA_TRY(plan_malloc(&t->d_P, (size_t)std::max<int64_t>(1, slots) * 128 * 128 * sizeof(double)));
     return NMS_OK;
 }
 
@@ -685,7 +685,7 @@ void tc_release(Plan& p)
     if (!t) return;
     void* b[] = {t->d_qy, t->d_qz, t->d_cpos_b, t->d_cw_b, t->d_Fb, t->d_Ftot_b, t->d_cyz, t->d_rot, t->d_cen, t->d_P};
     for (void* x : b)
-        if (x) cudaFree(x);
+        if (x) plan_free(x);
     free_schedule(t->full);
     free_schedule(t->last);
     delete t;

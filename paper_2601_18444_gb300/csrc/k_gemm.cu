@@ -90,106 +90,115 @@ __device__ __forceinline__ void split_h2(float x0, float x1, uint32_t& h, uint32
 // odd-symmetric, so the split of a negated value is the negated split
 __device__ __forceinline__ uint32_t swap_neg_h2(uint32_t w) { return __byte_perm(w, 0, 0x1032) ^ 0x80000000u; }
 
+// The tables are written one k-block per block of 128 threads: the cells'
+// positions and weights are loaded once per k-block and every A and B row
+// of that k-block is computed from them, so the load latency is paid once
+// per (A + B tiles) x 32 KB of output.  Thread t holds the cells
+// 4 (t & 7) .. + 3 and takes the row groups t / 8 + 16 i.  Stores are
+// streaming (evict-first): a chunk's tables are read back by the GEMM only
+// after the whole chunk is written.
+constexpr int TAB_THREADS = 128;
+
 // A tables: block (mt, kb) holds rows m = mt*128 + r, r < 128, with
 // m = a * nch + c (q_y index a, channel c = 4 * set + {N, Mx, My, Mz}) and
-// k = 2 j_loc + p.  Thread (g, chunk): the 4 rows 4g..4g+3 (one set, one a;
-// nch is a multiple of 4) for 4 cells.  Weight set st of cell j is
-// cw[st * wstride + j].
-__global__ void __launch_bounds__(256)
-k_tables_a(const float4* __restrict__ cpos, const float4* __restrict__ cw, int64_t wstride, int nch,
-           const int64_t* __restrict__ kb_cell0, const int32_t* __restrict__ kb_ncell, const float2* __restrict__ qy,
-           int ny, float4 wscale, int64_t nkb, uint8_t* __restrict__ A_hi, uint8_t* __restrict__ A_lo)
-{
-    const int64_t kb = blockIdx.x;
-    const int mt = blockIdx.y;
-    const int g = threadIdx.x >> 3;
-    const int chunk = threadIdx.x & 7;
-    const int m0 = mt * TC_BM + 4 * g;
-    const int a = m0 / nch;
-    const int st = (m0 % nch) >> 2;
-    const int64_t c0 = kb_cell0[kb];
-    const int nc = kb_ncell[kb];
-    uint4 hi[4], lo[4];
-    uint32_t* hw = reinterpret_cast<uint32_t*>(hi);
-    uint32_t* lw = reinterpret_cast<uint32_t*>(lo);
-    const bool arow = a < ny;
-    const float2 q = arow ? qy[a] : make_float2(0.f, 0.f);
-    const float4* wset = cw + (int64_t)st * wstride;
-    // all loads of this thread's 4 cells first, then the arithmetic
-    float4 cp[4], w[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int jl = chunk * 4 + u;
-        const bool live = arow && jl < nc;
-        cp[u] = live ? cpos[c0 + jl] : make_float4(0.f, 0.f, 0.f, 0.f);
-        w[u] = live ? wset[c0 + jl] : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        float sn, cs;
-        sincospif(2.0f * turns_reduced(q, cp[u].x, cp[u].y), &sn, &cs);
-        const float wv[4] = {w[u].x * wscale.x, w[u].y * wscale.y, w[u].z * wscale.z, w[u].w * wscale.w};
-#pragma unroll
-        for (int ch = 0; ch < 4; ++ch) split_h2(wv[ch] * cs, wv[ch] * sn, hw[4 * ch + u], lw[4 * ch + u]);
-    }
-    const size_t blk = ((size_t)mt * nkb + kb) * TC_BLOCK_BYTES;
-#pragma unroll
-    for (int ch = 0; ch < 4; ++ch) {
-        const int row = 4 * g + ch;
-        const uint32_t off = swz_offset(row, chunk * 8);
-        *reinterpret_cast<uint4*>(A_hi + blk + off) = hi[ch];
-        *reinterpret_cast<uint4*>(A_lo + blk + off) = lo[ch];
-    }
-}
-
+// k = 2 j_loc + p.  A row group g is the 4 rows 4g..4g+3 (one set, one a;
+// nch is a multiple of 4).  Weight set st of cell j is cw[st * wstride + j].
+//
 // B tables: block (nt, kb) holds rows n = nt*128 + 2*b_loc + r, b_loc < 64.
 // Re row (cos, -sin), Im row (-sin, -cos): each Im word is the Re word
 // (c, -s) turned into (-s, -c).
-__global__ void __launch_bounds__(512)
-k_tables_b(const float4* __restrict__ cpos, const int64_t* __restrict__ kb_cell0, const int32_t* __restrict__ kb_ncell,
-           const float2* __restrict__ qz, int nz, int64_t nkb, uint8_t* __restrict__ B_hi, uint8_t* __restrict__ B_lo)
+__global__ void __launch_bounds__(TAB_THREADS, 7)
+k_tables(const float4* __restrict__ cpos, const float4* __restrict__ cw, int64_t wstride, int nch,
+         const int64_t* __restrict__ kb_cell0, const int32_t* __restrict__ kb_ncell, const float2* __restrict__ qy,
+         int ny, const float2* __restrict__ qz, int nz, float4 wscale, int64_t nkb, int mtiles, int ntiles,
+         uint8_t* __restrict__ A_hi, uint8_t* __restrict__ A_lo, uint8_t* __restrict__ B_hi,
+         uint8_t* __restrict__ B_lo)
 {
-    const int64_t kb = blockIdx.x;
-    const int nt = blockIdx.y;
-    const int b_loc = threadIdx.x >> 3;
+    const int r = threadIdx.x >> 3;
     const int chunk = threadIdx.x & 7;
-    const int b = nt * 64 + b_loc;
-    const int64_t c0 = kb_cell0[kb];
-    const int nc = kb_ncell[kb];
-    const bool brow = b < nz;
-    const float2 q = brow ? qz[b] : make_float2(0.f, 0.f);
-    uint4 hr, lr, hi_, li_;
-    uint32_t* hrw = reinterpret_cast<uint32_t*>(&hr);
-    uint32_t* lrw = reinterpret_cast<uint32_t*>(&lr);
-    uint32_t* hiw = reinterpret_cast<uint32_t*>(&hi_);
-    uint32_t* liw = reinterpret_cast<uint32_t*>(&li_);
-    // all loads of this thread's 4 cells first, then the arithmetic; padding
-    // cells and rows stay zero
-    float2 cz[4];
-    float live[4];
+    const int spad = nch >> 2;                      // weight sets per output (a power of two)
+    // row group g = r + 16 i has weight set g mod spad: one set per thread
+    // when spad <= 16, else spad / 16 passes over i with one set each
+    const int passes = spad > 16 ? spad / 16 : 1;
+    const int ngroups = mtiles * 32;
+    const int nb = ntiles * 64;
+    for (int64_t kb = blockIdx.x; kb < nkb; kb += gridDim.x) {
+        const int64_t c0 = kb_cell0[kb];
+        const int nc = kb_ncell[kb];
+        float4 cp[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int jl = chunk * 4 + u;
-        const bool ok = brow && jl < nc;
-        const float4 c = ok ? cpos[c0 + jl] : make_float4(0.f, 0.f, 0.f, 0.f);
-        cz[u] = make_float2(c.z, c.w);
-        live[u] = ok ? TC_SCALE : 0.f;
-    }
+        for (int u = 0; u < 4; ++u) {
+            const int jl = chunk * 4 + u;
+            cp[u] = jl < nc ? cpos[c0 + jl] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // ---- B rows; padding cells and rows stay zero
+        for (int bi = r; bi < nb; bi += 16) {
+            const int nt = bi >> 6, b_loc = bi & 63;
+            const bool brow = bi < nz;
+            const float2 q = brow ? qz[bi] : make_float2(0.f, 0.f);
+            uint4 hr, lr, hi_, li_;
+            uint32_t* hrw = reinterpret_cast<uint32_t*>(&hr);
+            uint32_t* lrw = reinterpret_cast<uint32_t*>(&lr);
+            uint32_t* hiw = reinterpret_cast<uint32_t*>(&hi_);
+            uint32_t* liw = reinterpret_cast<uint32_t*>(&li_);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        float sn, cs;
-        sincospif(2.0f * turns_reduced(q, cz[u].x, cz[u].y), &sn, &cs);
-        split_h2(cs * live[u], -sn * live[u], hrw[u], lrw[u]);   // Re row: ( cos, -sin)
-        hiw[u] = swap_neg_h2(hrw[u]);                              // Im row: (-sin, -cos)
-        liw[u] = swap_neg_h2(lrw[u]);
+            for (int u = 0; u < 4; ++u) {
+                const float live = (brow && chunk * 4 + u < nc) ? TC_SCALE : 0.f;
+                float sn, cs;
+                sincospif(2.0f * turns_reduced(q, cp[u].z, cp[u].w), &sn, &cs);
+                split_h2(cs * live, -sn * live, hrw[u], lrw[u]);    // Re row: ( cos, -sin)
+                hiw[u] = swap_neg_h2(hrw[u]);                         // Im row: (-sin, -cos)
+                liw[u] = swap_neg_h2(lrw[u]);
+            }
+            const size_t blk = ((size_t)nt * nkb + kb) * TC_BLOCK_BYTES;
+            const uint32_t o0 = swz_offset(2 * b_loc, chunk * 8);
+            const uint32_t o1 = swz_offset(2 * b_loc + 1, chunk * 8);
+            __stcs(reinterpret_cast<uint4*>(B_hi + blk + o0), hr);
+            __stcs(reinterpret_cast<uint4*>(B_lo + blk + o0), lr);
+            __stcs(reinterpret_cast<uint4*>(B_hi + blk + o1), hi_);
+            __stcs(reinterpret_cast<uint4*>(B_lo + blk + o1), li_);
+        }
+        // ---- A rows, one weight set per pass
+        for (int ps = 0; ps < passes; ++ps) {
+            const int st = (r + 16 * ps) & (spad - 1);
+            const float4* wset = cw + (int64_t)st * wstride;
+            float4 w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int jl = chunk * 4 + u;
+                const float4 v = jl < nc ? wset[c0 + jl] : make_float4(0.f, 0.f, 0.f, 0.f);
+                w[u] = make_float4(v.x * wscale.x, v.y * wscale.y, v.z * wscale.z, v.w * wscale.w);
+            }
+            for (int g = r + 16 * ps; g < ngroups; g += 16 * passes) {
+                const int m0 = 4 * g;
+                const int a = m0 / nch;
+                const bool arow = a < ny;
+                const float2 q = arow ? qy[a] : make_float2(0.f, 0.f);
+                const float on = arow ? 1.f : 0.f;
+                uint4 hi[4], lo[4];
+                uint32_t* hw = reinterpret_cast<uint32_t*>(hi);
+                uint32_t* lw = reinterpret_cast<uint32_t*>(lo);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    float sn, cs;
+                    sincospif(2.0f * turns_reduced(q, cp[u].x, cp[u].y), &sn, &cs);
+                    cs *= on;
+                    sn *= on;
+                    const float wv[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
+#pragma unroll
+                    for (int ch = 0; ch < 4; ++ch) split_h2(wv[ch] * cs, wv[ch] * sn, hw[4 * ch + u], lw[4 * ch + u]);
+                }
+                const int mt = m0 >> 7;
+                const size_t blk = ((size_t)mt * nkb + kb) * TC_BLOCK_BYTES;
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch) {
+                    const uint32_t off = swz_offset((m0 & 127) + ch, chunk * 8);
+                    __stcs(reinterpret_cast<uint4*>(A_hi + blk + off), hi[ch]);
+                    __stcs(reinterpret_cast<uint4*>(A_lo + blk + off), lo[ch]);
+                }
+            }
+        }
     }
-    const size_t blk = ((size_t)nt * nkb + kb) * TC_BLOCK_BYTES;
-    const uint32_t o0 = swz_offset(2 * b_loc, chunk * 8);
-    const uint32_t o1 = swz_offset(2 * b_loc + 1, chunk * 8);
-    *reinterpret_cast<uint4*>(B_hi + blk + o0) = hr;
-    *reinterpret_cast<uint4*>(B_lo + blk + o0) = lr;
-    *reinterpret_cast<uint4*>(B_hi + blk + o1) = hi_;
-    *reinterpret_cast<uint4*>(B_lo + blk + o1) = li_;
 }
 
 // ------------------------------------------------------------------ PTX helpers
@@ -976,11 +985,10 @@ cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, int64_t wstri
     uint8_t* A_lo = A_hi + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
     uint8_t* B_hi = A_lo + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
     uint8_t* B_lo = B_hi + (size_t)ntiles * nkb * TC_BLOCK_BYTES;
-    k_tables_a<<<dim3((unsigned)nkb, (unsigned)mtiles), 256, 0, s>>>(
-        cpos, cw, wstride, nch, kb_cell0, kb_ncell, qy, ny, make_float4(wscale[0], wscale[1], wscale[2], wscale[3]),
-        nkb, A_hi, A_lo);
-    k_tables_b<<<dim3((unsigned)nkb, (unsigned)ntiles), 512, 0, s>>>(cpos, kb_cell0, kb_ncell, qz, nz, nkb, B_hi,
-                                                                     B_lo);
+    if (nkb <= 0) return cudaSuccess;
+    k_tables<<<(unsigned)std::min<int64_t>(nkb, 0x7fffffff), TAB_THREADS, 0, s>>>(
+        cpos, cw, wstride, nch, kb_cell0, kb_ncell, qy, ny, qz, nz,
+        make_float4(wscale[0], wscale[1], wscale[2], wscale[3]), nkb, mtiles, ntiles, A_hi, A_lo, B_hi, B_lo);
     return cudaGetLastError();
 }
 

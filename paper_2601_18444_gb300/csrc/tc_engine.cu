@@ -723,7 +723,7 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
                 NMS_CUDA_TRY(tc_launch_tables(t.d_cpos_b, t.d_cw_b, t.wstride, t.nch, S.d_kb_cell0 + ch.kb_off,
                                               S.d_kb_ncell + ch.kb_off, ch.nkb, t.d_qy, t.ny, t.d_qz, t.nz, t.mtiles,
                                               t.ntiles, wscale, p.d_tab, s));
-                p.timer.end(ST_TABLES, 2);
+                p.timer.end(ST_TABLES, 1);
                 p.timer.begin(ST_GEMM);
                 NMS_CUDA_TRY(tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles,
                                             (const char*)S.d_items + ch.item_off * tc_item_bytes(), ch.n_items, ch.grid,

@@ -28,10 +28,12 @@
 // the exact reduction t - rint(t), then sincospif.  Tables are written in the
 // canonical K-major 128-byte-swizzled UMMA layout, 16 KB per (tile, k-block),
 // so the GEMM moves them with plain 1D bulk copies (cp.async.bulk).
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -303,6 +305,28 @@ __device__ __forceinline__ void bulk_g2s_mc(uint32_t dst, const void* src, uint3
         : "memory");
 }
 
+// Tensor copy of one box (row y of a 2D map whose rows are 128-byte table
+// rows; the box is 16 or 8 KB of one table block) into this CTA's shared
+// memory, its bytes completing on an mbarrier of the CTA pair that may be
+// the peer's (cta_group::2: the operands of a two-SM MMA signal the issuing
+// CTA's barrier directly).  The x coordinate is always 0 (16-byte aligned).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* tm, int32_t y, uint32_t bar_cluster)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%2, "
+        "%3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(y), "r"(bar_cluster)
+        : "memory");
+}
+
+// address of the mbarrier at this offset in CTA `cta` of the cluster
+__device__ __forceinline__ uint32_t mbar_cluster_addr(uint64_t* bar, uint32_t cta)
+{
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(bar)), "r"(cta));
+    return remote;
+}
+
 // arrive (once MMAs complete) on the mbarrier at this offset in every CTA of mask
 __device__ __forceinline__ void tc_commit_mc(uint64_t* bar, uint16_t mask)
 {
@@ -571,9 +595,11 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity
 // 128 rows in its own TMEM.  A stage is 48 KB per SM instead of 64 KB and an
 // MMA reads 6 KB of shared memory per 128 x 128 x 16 product instead of 8 KB,
 // which is the resource the single-CTA form runs out of; the 48 KB stages
-// also make room for a fourth stage.  The odd CTA's MMA warp relays "stage
-// full" to the even CTA; the odd CTA's epilogue warps release accumulators
-// on the even CTA's barrier.
+// also make room for a fourth stage.  The even CTA's "stage full" barrier
+// counts the bytes of both CTAs: the odd CTA loads its operands with tensor
+// copies of the CTA pair (cta_group::2) that complete on the even CTA's
+// barrier, so the MMA issuer waits on one barrier.  The odd CTA's epilogue
+// warps release accumulators on the even CTA's barrier.
 struct GemmItem {
     int32_t mt, nt;       // A / B tile rows (MODE 1: nt indexes B tile pairs, MODE 2: mt indexes A tile pairs)
     int32_t kb0, kb1;     // k-block range (within this chunk's tables)
@@ -599,6 +625,7 @@ struct GemmArgs {
     double scale[4];      // direct outputs: per-channel scale of the unscaled sums
     int32_t* err;
     uint64_t limit_ns;
+    int mtiles, ntiles;   // tile rows of A and B (table layout)
 };
 
 template <int MODE>
@@ -609,15 +636,17 @@ struct GemmCfg {
     static constexpr int CG = MODE == 2 ? 2 : 1;
 };
 
+// tmA / tmB (MODE 2): 2D maps over the chunk's tables as 128-byte rows,
+// boxes of 128 rows (an A block) and 64 rows (half a B block)
 template <int MODE>
-__global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_f16x3(const GemmArgs g, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB)
 {
     using C = GemmCfg<MODE>;
     constexpr bool CLUSTER = MODE != 0;
     constexpr int STG = C::STAGES;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t bar_full[STG];
-    __shared__ __align__(8) uint64_t bar_pfull[STG];    // MODE 2, even CTA: the odd CTA's stage is full
+    __shared__ __align__(8) uint64_t bar_full[STG];     // MODE 2, even CTA: both CTAs' stage bytes
     __shared__ __align__(8) uint64_t bar_empty[STG];
     __shared__ __align__(8) uint64_t bar_acc_full[2];
     __shared__ __align__(8) uint64_t bar_acc_empty[2];
@@ -635,7 +664,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STG; ++s) {
             mbar_init(&bar_full[s], 1);
-            mbar_init(&bar_pfull[s], 1);
             mbar_init(&bar_empty[s], MODE == 1 ? 2 : 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -673,9 +701,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
                         break;
                     }
                     const uint32_t st = sbase + (uint32_t)s * C::STAGE_BYTES;
-                    mbar_arrive_expect_tx(&bar_full[s], C::STAGE_BYTES);
                     const int mt = MODE == 2 ? 2 * item.mt + rank : item.mt;
                     const int nt = MODE == 1 ? 2 * item.nt + rank : item.nt;
+                    if (MODE == 2 && rank == 1) {
+                        // table rows (128 B each) of this CTA's A block and B half
+                        const int32_t nk = (int32_t)g.nkb;
+                        const int32_t ra = (mt * nk + kb) * 128;
+                        const int32_t rb = ((2 * g.mtiles + nt) * nk + kb) * 128 + 64;
+                        const uint32_t lead = mbar_cluster_addr(&bar_full[s], 0);
+                        tma_load_2d_pair(st, &tmA, ra, lead);
+                        tma_load_2d_pair(st + TC_BLOCK_BYTES, &tmA, ra + g.mtiles * nk * 128, lead);
+                        tma_load_2d_pair(st + 2 * TC_BLOCK_BYTES, &tmB, rb, lead);
+                        tma_load_2d_pair(st + 2 * TC_BLOCK_BYTES + C::B_BYTES, &tmB, rb + g.ntiles * nk * 128, lead);
+                        ++i;
+                        continue;
+                    }
+                    mbar_arrive_expect_tx(&bar_full[s], MODE == 2 ? 2 * C::STAGE_BYTES : C::STAGE_BYTES);
                     const size_t ao = ((size_t)mt * g.nkb + kb) * TC_BLOCK_BYTES;
                     // MODE 2: this CTA's 64-row half of the B block
                     const size_t bo = ((size_t)nt * g.nkb + kb) * TC_BLOCK_BYTES + (MODE == 2 ? rank * C::B_BYTES : 0);
@@ -694,34 +735,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
                 }
             }
             // copies in flight must land before the CTA exits (bounded): only
-            // the last STG issued stages can still be pending
-            for (int64_t k = (i > STG ? i - STG : 0); k < i; ++k) {
-                const int s = (int)(k % STG);
-                const uint32_t par = (uint32_t)((k / STG) & 1);
-                mbar_wait_drain(&bar_full[s], par);
+            // the last STG issued stages can still be pending.  MODE 2, odd
+            // CTA: its copies complete on the even CTA's barriers; without an
+            // abort the even CTA's MMAs consumed them all before the final
+            // cluster barrier, after an abort it gives them 2 ms to land.
+            if (MODE == 2 && rank == 1) {
+                if (!ok) {
+                    const uint64_t t0 = gtimer();
+                    while (gtimer() - t0 < 2000000ull) __nanosleep(1000);
+                }
+            } else {
+                for (int64_t k = (i > STG ? i - STG : 0); k < i; ++k) {
+                    const int s = (int)(k % STG);
+                    const uint32_t par = (uint32_t)((k / STG) & 1);
+                    mbar_wait_drain(&bar_full[s], par);
+                }
             }
         }
     } else if (warp == 1) {
         if (MODE == 2 && rank == 1) {
-            // ---------------- odd CTA: relay "stage full" to the MMA issuer
-            if (lane == 0) {
-                int64_t i = 0;
-                bool ok = true;
-                for (int it = unit0; it < g.n_items && ok; it += units) {
-                    const GemmItem item = g.items[it];
-                    for (int kb = item.kb0; kb < item.kb1; ++kb, ++i) {
-                        const int s = (int)(i % STG);
-                        const uint32_t par = (uint32_t)((i / STG) & 1);
-                        if (!mbar_wait(&bar_full[s], par, g.limit_ns, &s_abort)) {
-                            s_abort = 1;
-                            atomicExch(g.err, 4);
-                            ok = false;
-                            break;
-                        }
-                        mbar_arrive_cluster(&bar_pfull[s], 0);
-                    }
-                }
-            }
+            // odd CTA: no MMA issuer (its operands and accumulators are
+            // driven by the even CTA)
         } else if (lane == 0) {
             // ---------------- MMA issuer (one thread; MODE 2: of the even CTA)
             constexpr int MM = MODE == 2 ? 2 * TC_BM : TC_BM;
@@ -750,8 +784,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_gemm_f16x3(const GemmArgs g)
                     for (int kb = k0; kb < k1; ++kb, ++i) {
                         const int s = (int)(i % STG);
                         const uint32_t par = (uint32_t)((i / STG) & 1);
-                        bool okf = mbar_wait(&bar_full[s], par, g.limit_ns, &s_abort);
-                        if (MODE == 2 && okf) okf = mbar_wait_cluster(&bar_pfull[s], par, g.limit_ns, &s_abort);
+                        const bool okf = mbar_wait(&bar_full[s], par, g.limit_ns, &s_abort);
                         if (!okf) {
                             ok = false;
                             break;
@@ -992,6 +1025,36 @@ cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, int64_t wstri
     return cudaGetLastError();
 }
 
+// Two 2D maps over `rows` table rows of 128 bytes (64 x 16-bit) at tab:
+// boxes of 128 rows (an A block) and of 64 rows (half a B block).  The data
+// is already in the MMA's swizzled layout, so the copies do not swizzle.
+static cudaError_t encode_row_maps(const void* tab, int64_t rows, CUtensorMap* tm)
+{
+    typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeTiled encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
+        encode = (EncodeTiled)fn;
+    }
+    const cuuint64_t dim[2] = {64, (cuuint64_t)rows};
+    const cuuint64_t stride[1] = {128};
+    const cuuint32_t estr[2] = {1, 1};
+    const cuuint32_t boxA[2] = {64, 128}, boxB[2] = {64, 64};
+    CUresult r = encode(&tm[0], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(tab), dim, stride, boxA, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r == CUDA_SUCCESS)
+        r = encode(&tm[1], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(tab), dim, stride, boxB, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
                            int grid, int kcb, double* P, double* F, int ny, int nz, int nch, const double scale[4],
                            int32_t* err, uint64_t limit_ns, int mode, cudaStream_t s)
@@ -1010,6 +1073,15 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
         attr = true;
     }
     if (mode < 0 || mode > 2 || (mode != 0 && (grid & 1))) return cudaErrorInvalidValue;
+    // MODE 2: tensor maps over the chunk's tables as rows of 128 bytes
+    const int64_t rows = (int64_t)(2 * mtiles + 2 * ntiles) * nkb * (TC_BLOCK_BYTES / 128);
+    CUtensorMap tm[2];
+    memset(tm, 0, sizeof(tm));
+    if (mode == 2) {
+        if (rows > 0x7fffffffll) return cudaErrorInvalidValue;   // row coordinates are 32-bit
+        const cudaError_t e = encode_row_maps(tab, rows, tm);
+        if (e != cudaSuccess) return e;
+    }
     GemmArgs ga;
     ga.A_hi = (const uint8_t*)tab;
     ga.A_lo = ga.A_hi + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
@@ -1027,8 +1099,10 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
     for (int c = 0; c < 4; ++c) ga.scale[c] = scale[c];
     ga.err = err;
     ga.limit_ns = limit_ns;
+    ga.mtiles = mtiles;
+    ga.ntiles = ntiles;
     if (mode == 0) {
-        k_gemm_f16x3<0><<<grid, TC_THREADS, smem, s>>>(ga);
+        k_gemm_f16x3<0><<<grid, TC_THREADS, smem, s>>>(ga, tm[0], tm[1]);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
@@ -1043,7 +1117,8 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return mode == 1 ? cudaLaunchKernelEx(&cfg, k_gemm_f16x3<1>, ga) : cudaLaunchKernelEx(&cfg, k_gemm_f16x3<2>, ga);
+    return mode == 1 ? cudaLaunchKernelEx(&cfg, k_gemm_f16x3<1>, ga, tm[0], tm[1])
+                     : cudaLaunchKernelEx(&cfg, k_gemm_f16x3<2>, ga, tm[0], tm[1]);
 }
 
 cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, int ny, int nz, int ntiles, int nch,

@@ -578,10 +578,11 @@ nms_status tc_setup(Plan& p)
     if (p.opt.split_k > 0) t->items_per_sm = std::min(256, p.opt.split_k);
     t->objects = p.n_objects > 1 && p.opt.want_dilute;
     // CTA pairs sharing A where the B tiles pair up (the fastest form
-    // measured: the two-SM MMA reads less shared memory per product but its
-    // odd CTA's "stage full" relay costs more than that saves), else the
-    // two-SM MMA over A-tile pairs, else one CTA per tile.  NMS_GEMM_MODE = 0,
-    // 1 or 2 forces a form the grid allows (diagnostics, tests).
+    // measured: the two-SM MMA writes fewer operand bytes into shared memory
+    // per stage, but each SM still reads the whole B tile, half of it from
+    // the peer, and it measured 6 % slower), else the two-SM MMA over A-tile
+    // pairs, else one CTA per tile.  NMS_GEMM_MODE = 0, 1 or 2 forces a form
+    // the grid allows (diagnostics, tests).
     t->mode = (t->ntiles % 2 == 0) ? 1 : (t->mtiles % 2 == 0) ? 2 : 0;
     if (const char* gm = getenv("NMS_GEMM_MODE")) {
         const int want = atoi(gm);

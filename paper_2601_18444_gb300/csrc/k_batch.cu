@@ -87,6 +87,39 @@ cudaError_t launch_centres(int n_out, const int32_t* out_obj, const int32_t* out
     return cudaGetLastError();
 }
 
+// Shift factors of each output along each detector axis:
+//   eyz[o][a]      = (cos, sin)(2 pi q'_y,a cy_o)   a < ny
+//   eyz[o][ny + b] = (cos, sin)(2 pi q'_z,b cz_o)   b < nz
+// (q' in turns, two-float; the product is reduced exactly to [-1/2, 1/2]).
+// The phase of pixel (a, b) is the sum of the two (the detector-plane
+// phase separates), so the per-pixel work is one complex product.
+__global__ void k_shift_factors(int n_out, const float4* __restrict__ cyz, const float2* __restrict__ qy, int ny,
+                                const float2* __restrict__ qz, int nz, float2* __restrict__ eyz)
+{
+    const int o = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n_out || i >= ny + nz) return;
+    const float4 c = cyz[o];
+    const bool y = i < ny;
+    const float2 q = y ? qy[i] : qz[i - ny];
+    const float ch = y ? c.x : c.z, cl = y ? c.y : c.w;
+    const float p = q.x * ch;
+    const float e = fmaf(q.x, ch, -p) + fmaf(q.x, cl, q.y * ch);
+    const float t = (p - rintf(p)) + e;
+    float sn, cs;
+    sincospif(2.0f * t, &sn, &cs);
+    eyz[(int64_t)o * (ny + nz) + i] = make_float2(cs, sn);
+}
+
+cudaError_t launch_shift_factors(int n_out, const float4* cyz, const float2* qy, int ny, const float2* qz, int nz,
+                                 float2* eyz, cudaStream_t s)
+{
+    if (n_out <= 0) return cudaSuccess;
+    k_shift_factors<<<dim3((unsigned)((ny + nz + 127) / 128), (unsigned)n_out), 128, 0, s>>>(n_out, cyz, qy, ny, qz, nz,
+                                                                                          eyz);
+    return cudaGetLastError();
+}
+
 __device__ __forceinline__ void ts_acc(float& hi, float& lo, float x)
 {
     const float s = hi + x;
@@ -100,175 +133,223 @@ __device__ __forceinline__ int pair_idx(int a, int b)  // a < b
     return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
 }
 
-// Complex value idx of an amplitude array as FP32: two-float
-// (re hi, re lo, im hi, im lo) when TF, else FP64 (re, im).
+// G[16][npix] += sum_o F_o F_o^dagger.  GEMM outputs (F_b, FbView layout;
+// threads run over q_y fastest so a warp reads contiguous channel rows) or
+// FP64 totals ([4][npix] complex per output at ostride2 complex values,
+// threads over pixels).
 template <bool TF>
-__device__ __forceinline__ float2 load_c(const void* __restrict__ F, int64_t idx)
-{
-    if constexpr (TF) {
-        const float4 v = reinterpret_cast<const float4*>(F)[idx];
-        return make_float2(v.x + v.y, v.z + v.w);
-    } else {
-        const double2 v = reinterpret_cast<const double2*>(F)[idx];
-        return make_float2((float)v.x, (float)v.y);
-    }
-}
-
-// G[16][npix] += sum_o F_o F_o^dagger (F_o: [4][npix] complex at F + o *
-// ostride2 complex values; two-float GEMM outputs or FP64 totals).
-template <bool TF>
-__global__ void k_gacc_batch(const void* __restrict__ F, int n_out, int64_t ostride2, int64_t npix,
+__global__ void k_gacc_batch(FbView V, const double2* __restrict__ T, int n_out, int64_t ostride2, int64_t npix,
                              double* __restrict__ G)
 {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= npix) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npix) return;
+    int64_t p = t;
+    int a = 0, b = 0;
+    if constexpr (TF) {
+        a = (int)(t % V.ny);
+        b = (int)(t / V.ny);
+        p = (int64_t)a * V.nz + b;
+    }
     float hi[16], lo[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) { hi[k] = 0.f; lo[k] = 0.f; }
     for (int o = 0; o < n_out; ++o) {
         float2 f[4];
+        if constexpr (TF) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) f[c] = load_c<TF>(F, (int64_t)o * ostride2 + (int64_t)c * npix + p);
+            for (int c = 0; c < 4; ++c) f[c] = V.load(o, a, b, c);
+        } else {
 #pragma unroll
-        for (int a = 0; a < 4; ++a) ts_acc(hi[a], lo[a], fmaf(f[a].x, f[a].x, f[a].y * f[a].y));
+            for (int c = 0; c < 4; ++c) {
+                const double2 v = T[(int64_t)o * ostride2 + (int64_t)c * npix + p];
+                f[c] = make_float2((float)v.x, (float)v.y);
+            }
+        }
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int i = 0; i < 4; ++i) ts_acc(hi[i], lo[i], fmaf(f[i].x, f[i].x, f[i].y * f[i].y));
 #pragma unroll
-            for (int b = a + 1; b < 4; ++b) {
-                const int k = pair_idx(a, b);
-                ts_acc(hi[4 + 2 * k], lo[4 + 2 * k], fmaf(f[a].x, f[b].x, f[a].y * f[b].y));
-                ts_acc(hi[5 + 2 * k], lo[5 + 2 * k], fmaf(f[a].y, f[b].x, -f[a].x * f[b].y));
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = i + 1; j < 4; ++j) {
+                const int k = pair_idx(i, j);
+                ts_acc(hi[4 + 2 * k], lo[4 + 2 * k], fmaf(f[i].x, f[j].x, f[i].y * f[j].y));
+                ts_acc(hi[5 + 2 * k], lo[5 + 2 * k], fmaf(f[i].y, f[j].x, -f[i].x * f[j].y));
             }
     }
 #pragma unroll
     for (int k = 0; k < 16; ++k) G[(int64_t)k * npix + p] += (double)hi[k] + (double)lo[k];
 }
 
-cudaError_t launch_gacc_batch(const double* F, int n_out, int64_t ostride, int64_t npix, double* G, bool two_float,
-                              cudaStream_t s)
+cudaError_t launch_gacc_batch(const FbView& V, int n_out, double* G, cudaStream_t s)
 {
     if (n_out <= 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((npix + 127) / 128);
-    if (two_float) k_gacc_batch<true><<<blocks, 128, 0, s>>>(F, n_out, ostride / 2, npix, G);
-    else k_gacc_batch<false><<<blocks, 128, 0, s>>>(F, n_out, ostride / 2, npix, G);
+    const int64_t npix = (int64_t)V.ny * V.nz;
+    k_gacc_batch<true><<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(V, nullptr, n_out, 0, npix, G);
     return cudaGetLastError();
 }
 
-// FP64 amplitudes from two-float ones: (re hi + re lo, im hi + im lo)
-__global__ void k_tf_to_f64(const float4* __restrict__ src, double2* __restrict__ dst, int64_t n)
+cudaError_t launch_gacc_totals(const double* T, int n_out, int64_t ostride, int64_t npix, double* G, cudaStream_t s)
 {
+    if (n_out <= 0) return cudaSuccess;
+    FbView none{};
+    k_gacc_batch<false><<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(
+        none, reinterpret_cast<const double2*>(T), n_out, ostride / 2, npix, G);
+    return cudaGetLastError();
+}
+
+// FP64 amplitudes [4][npix] of one output from its F_b value (high word
+// plus, for outputs of several pieces, the low word)
+__global__ void k_tf_to_f64(FbView V, int64_t o, double2* __restrict__ dst)
+{
+    const int64_t npix = (int64_t)V.ny * V.nz;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float4 v = src[i];
-    dst[i] = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+    if (i >= 4 * npix) return;
+    const int c = (int)(i / npix);
+    const int64_t p = i % npix;
+    const int a = (int)(p / V.nz), b = (int)(p % V.nz);
+    const int64_t j = V.idx(o, a, b) + c;
+    const float2 h = V.hi[j];
+    const float2 l = V.two[o] ? V.lo[j] : make_float2(0.f, 0.f);
+    dst[i] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
 }
 
-cudaError_t launch_tf_to_f64(const double* src, double* dst, int64_t n_complex, cudaStream_t s)
+cudaError_t launch_tf_to_f64(const FbView& V, int64_t o, double* dst, cudaStream_t s)
 {
-    k_tf_to_f64<<<(unsigned)((n_complex + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(src),
-                                                                    reinterpret_cast<double2*>(dst), n_complex);
+    const int64_t n = 4 * (int64_t)V.ny * V.nz;
+    k_tf_to_f64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(V, o, reinterpret_cast<double2*>(dst));
     return cudaGetLastError();
 }
 
-// One pass over a batch of object amplitudes F_o (two-float [n_out][4][npix]):
+// One pass over a batch of object amplitudes F_o (FbView layout):
 //   G_dil[16][p]              += F_o F_o^dagger                  (dilute part)
 //   Ftot[out_rot[o]][c][p]    += F_o[c][p] exp(-i (q_y cy_o + q_z cz_o))
-// The shift phase is a two-float product in turns reduced exactly (as in the
-// direct sum).  Outputs are ordered by rotation, so each thread flushes its
-// two-float shifted sums to FP64 once per rotation.  The next output's
-// amplitudes are loaded while the current one is processed, so each thread
-// keeps two outputs' loads in flight.
-__device__ __forceinline__ void load_f(const float4* __restrict__ F, int64_t o, int64_t ostride2, int64_t npix,
-                                       int64_t p, float4* v)
+// The shift factor of pixel (a, b) is the product of the output's factors
+// along q_y and q_z (k_shift_factors).  One thread per pixel; q_y runs
+// fastest, so a warp reads contiguous channel rows of F_b.  Outputs are
+// taken in pairs: the pair's two terms are added in FP32 before they join
+// the two-float sums (one rounding of a two-term sum per pair), and the next
+// pair's values are loaded while the current one is processed.  Outputs are
+// ordered by rotation; the shifted sums are flushed to FP64 at each change
+// of rotation (a pair that straddles one is taken one output at a time).
+struct DsIn {
+    float2 f[4];
+    float2 ey, ez;
+};
+
+__device__ __forceinline__ void ds_load(const FbView& V, const float2* __restrict__ eyz, int ne, int o, int qa, int qb,
+                                        DsIn& d)
 {
+    const float2* src = V.hi + V.idx(o, qa, qb);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) v[c] = F[o * ostride2 + (int64_t)c * npix + p];
+    for (int c = 0; c < 4; ++c) d.f[c] = src[c];
+    d.ey = eyz[(int64_t)o * ne + qa];
+    d.ez = eyz[(int64_t)o * ne + V.ny + qb];
 }
 
-__global__ void __launch_bounds__(128)
-k_dilute_shift_batch(const float4* __restrict__ F, int n_out, int64_t ostride2, const float4* __restrict__ cyz,
-                     const int32_t* __restrict__ out_rot, const float4* __restrict__ qturn, int64_t npix,
+// the 16 Hermitian terms and 8 shifted terms of one output
+__device__ __forceinline__ void ds_terms(const DsIn& d, float* g, float* t)
+{
+    const float2* f = d.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) g[i] = fmaf(f[i].x, f[i].x, f[i].y * f[i].y);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = i + 1; j < 4; ++j) {
+            const int k = pair_idx(i, j);
+            g[4 + 2 * k] = fmaf(f[i].x, f[j].x, f[i].y * f[j].y);
+            g[5 + 2 * k] = fmaf(f[i].y, f[j].x, -f[i].x * f[j].y);
+        }
+    const float cs = fmaf(d.ey.x, d.ez.x, -d.ey.y * d.ez.y);
+    const float sn = fmaf(d.ey.y, d.ez.x, d.ey.x * d.ez.y);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        t[2 * c] = fmaf(f[c].x, cs, f[c].y * sn);
+        t[2 * c + 1] = fmaf(f[c].y, cs, -f[c].x * sn);
+    }
+}
+
+__global__ void __launch_bounds__(128, 4)   // 4 blocks per SM: one wave for a 256 x 256 detector
+k_dilute_shift_batch(FbView V, int n_out, const float2* __restrict__ eyz, const int32_t* __restrict__ out_rot,
                      double* __restrict__ Gdil, double2* __restrict__ Ftot, int64_t tstride2)
 {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= npix || n_out <= 0) return;
-    const float4 q = qturn[p];
+    const int64_t npix = (int64_t)V.ny * V.nz;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= npix || n_out <= 0) return;
+    const int qa = (int)(tid % V.ny), qb = (int)(tid / V.ny);
+    const int64_t p = (int64_t)qa * V.nz + qb;
+    const int ne = V.ny + V.nz;
     float gh[16], gl[16], th[8], tl[8];
 #pragma unroll
     for (int k = 0; k < 16; ++k) { gh[k] = 0.f; gl[k] = 0.f; }
 #pragma unroll
     for (int k = 0; k < 8; ++k) { th[k] = 0.f; tl[k] = 0.f; }
-    float4 nxt[4];
-    load_f(F, 0, ostride2, npix, p, nxt);
-    int cur = out_rot[0];
-    for (int o = 0; o < n_out; ++o) {
-        float2 f[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) f[c] = make_float2(nxt[c].x + nxt[c].y, nxt[c].z + nxt[c].w);
-        if (o + 1 < n_out) load_f(F, o + 1, ostride2, npix, p, nxt);
-        const int r = out_rot[o];
-        if (r != cur) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                double2* t = Ftot + (int64_t)cur * tstride2 + (int64_t)c * npix + p;
-                double2 v = *t;
-                v.x += (double)th[2 * c] + (double)tl[2 * c];
-                v.y += (double)th[2 * c + 1] + (double)tl[2 * c + 1];
-                *t = v;
-            }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) { th[k] = 0.f; tl[k] = 0.f; }
-            cur = r;
-        }
-        // dilute: F_o F_o^dagger
-#pragma unroll
-        for (int a = 0; a < 4; ++a) ts_acc(gh[a], gl[a], fmaf(f[a].x, f[a].x, f[a].y * f[a].y));
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = a + 1; b < 4; ++b) {
-                const int k = pair_idx(a, b);
-                ts_acc(gh[4 + 2 * k], gl[4 + 2 * k], fmaf(f[a].x, f[b].x, f[a].y * f[b].y));
-                ts_acc(gh[5 + 2 * k], gl[5 + 2 * k], fmaf(f[a].y, f[b].x, -f[a].x * f[b].y));
-            }
-        // total: F_o moved to its rotated centre
-        const float4 cc = cyz[o];
-        const float py = q.x * cc.x;
-        const float ey = fmaf(q.x, cc.x, -py) + fmaf(q.x, cc.y, q.y * cc.x);
-        const float pz = q.z * cc.z;
-        const float ez = fmaf(q.z, cc.z, -pz) + fmaf(q.z, cc.w, q.w * cc.z);
-        const float sm = py + pz;
-        const float bb = sm - py;
-        const float es = (py - (sm - bb)) + (pz - bb);
-        const float t = (sm - rintf(sm)) + (es + ey + ez);
-        float sn, cs;
-        sincospif(2.0f * t, &sn, &cs);
+    auto flush = [&](int rot) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            ts_acc(th[2 * c], tl[2 * c], fmaf(f[c].x, cs, f[c].y * sn));
-            ts_acc(th[2 * c + 1], tl[2 * c + 1], fmaf(f[c].y, cs, -f[c].x * sn));
+            double2* t = Ftot + (int64_t)rot * tstride2 + (int64_t)c * npix + p;
+            double2 v = *t;
+            v.x += (double)th[2 * c] + (double)tl[2 * c];
+            v.y += (double)th[2 * c + 1] + (double)tl[2 * c + 1];
+            *t = v;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { th[k] = 0.f; tl[k] = 0.f; }
+    };
+    int cur = out_rot[0];
+    DsIn n0, n1;
+    ds_load(V, eyz, ne, 0, qa, qb, n0);
+    ds_load(V, eyz, ne, min(1, n_out - 1), qa, qb, n1);
+    for (int o = 0; o < n_out; o += 2) {
+        const DsIn d0 = n0, d1 = n1;
+        const bool has1 = o + 1 < n_out;
+        if (o + 2 < n_out) {
+            ds_load(V, eyz, ne, o + 2, qa, qb, n0);
+            ds_load(V, eyz, ne, min(o + 3, n_out - 1), qa, qb, n1);
+        }
+        const int r0 = out_rot[o];
+        const int r1 = has1 ? out_rot[o + 1] : r0;
+        float g0[16], t0[8], g1[16], t1[8];
+        ds_terms(d0, g0, t0);
+        ds_terms(d1, g1, t1);
+        if (!has1) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) g1[k] = 0.f;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) t1[k] = 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) ts_acc(gh[k], gl[k], g0[k] + g1[k]);
+        if (r0 == cur && r1 == cur) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) ts_acc(th[k], tl[k], t0[k] + t1[k]);
+        } else {
+            if (r0 != cur) {
+                flush(cur);
+                cur = r0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) ts_acc(th[k], tl[k], t0[k]);
+            if (r1 != cur) {
+                flush(cur);
+                cur = r1;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) ts_acc(th[k], tl[k], t1[k]);
         }
     }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        double2* t = Ftot + (int64_t)cur * tstride2 + (int64_t)c * npix + p;
-        double2 v = *t;
-        v.x += (double)th[2 * c] + (double)tl[2 * c];
-        v.y += (double)th[2 * c + 1] + (double)tl[2 * c + 1];
-        *t = v;
-    }
+    flush(cur);
 #pragma unroll
     for (int k = 0; k < 16; ++k) Gdil[(int64_t)k * npix + p] += (double)gh[k] + (double)gl[k];
 }
 
-cudaError_t launch_dilute_shift_batch(const double* F, int n_out, int64_t ostride, const float4* cyz,
-                                      const int32_t* out_rot, const float4* qturn, int64_t npix, double* Gdil,
-                                      double* Ftot, int64_t tstride, cudaStream_t s)
+cudaError_t launch_dilute_shift_batch(const FbView& V, int n_out, const float2* eyz, const int32_t* out_rot,
+                                      double* Gdil, double* Ftot, int64_t tstride, cudaStream_t s)
 {
     if (n_out <= 0) return cudaSuccess;
-    k_dilute_shift_batch<<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(
-        reinterpret_cast<const float4*>(F), n_out, ostride / 2, cyz, out_rot, qturn, npix, Gdil,
-        reinterpret_cast<double2*>(Ftot), tstride / 2);
+    const int64_t npix = (int64_t)V.ny * V.nz;
+    k_dilute_shift_batch<<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(V, n_out, eyz, out_rot, Gdil,
+                                                                        reinterpret_cast<double2*>(Ftot), tstride / 2);
     return cudaGetLastError();
 }
 
@@ -283,7 +364,7 @@ namespace nms {
 //   N  = s |F_N|^2,  M = s b^2 (|F_M|^2 - |qhat.F_M|^2)   (|Q|^2, Eq. HJdef)
 //   P  = s b^2 |u.F_M|^2, u = P - qhat (qhat.P)            (Eq. PSANSdef)
 //   SF = M - P,  UNPOL = N + M.
-__global__ void k_obj_bin(const float4* __restrict__ F, int n_out, const int32_t* __restrict__ out_obj,
+__global__ void k_obj_bin(FbView V, int n_out, const int32_t* __restrict__ out_obj,
                           const double* __restrict__ hy, const double* __restrict__ hz,
                           const int32_t* __restrict__ bin_of, int64_t npix, int nbins, int id, float s, float b,
                           float Px, float Py, float Pz, double* __restrict__ Iobj)
@@ -292,16 +373,15 @@ __global__ void k_obj_bin(const float4* __restrict__ F, int n_out, const int32_t
     const int o = blockIdx.y;
     for (int k = threadIdx.x; k < nbins; k += blockDim.x) s_bins[k] = 0.f;
     __syncthreads();
-    const float4* Fo = F + (int64_t)o * 4 * npix;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < npix; t += (int64_t)gridDim.x * blockDim.x) {
+        // q_y fastest: a warp reads contiguous channel rows of F_b
+        const int qa = (int)(t % V.ny), qb = (int)(t / V.ny);
+        const int64_t p = (int64_t)qa * V.nz + qb;
         const int bin = bin_of[p];
         if (bin < 0) continue;
         float2 f[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float4 v = Fo[(int64_t)c * npix + p];
-            f[c] = make_float2(v.x + v.y, v.z + v.w);
-        }
+        for (int c = 0; c < 4; ++c) f[c] = V.load(o, qa, qb, c);
         const float y = (float)hy[p], z = (float)hz[p];
         const float nn = f[0].x * f[0].x + f[0].y * f[0].y;
         const float mm = f[1].x * f[1].x + f[1].y * f[1].y + f[2].x * f[2].x + f[2].y * f[2].y + f[3].x * f[3].x +
@@ -330,13 +410,13 @@ __global__ void k_obj_bin(const float4* __restrict__ F, int n_out, const int32_t
         if (s_bins[k] != 0.f) atomicAdd(&dst[k], (double)s_bins[k]);
 }
 
-cudaError_t launch_obj_bin(const double* F, int n_out, const int32_t* out_obj, const Plan& p, const int32_t* bin_of,
+cudaError_t launch_obj_bin(const FbView& F, int n_out, const int32_t* out_obj, const Plan& p, const int32_t* bin_of,
                            int nbins, int id, double* Iobj, cudaStream_t s)
 {
     if (n_out <= 0) return cudaSuccess;
     const int64_t pix_blocks = std::min<int64_t>((p.npix + 1023) / 1024, 64);
     dim3 grid((unsigned)pix_blocks, (unsigned)n_out);
-    k_obj_bin<<<grid, 256, nbins * sizeof(float), s>>>(reinterpret_cast<const float4*>(F), n_out, out_obj, p.d_hy,
+    k_obj_bin<<<grid, 256, nbins * sizeof(float), s>>>(F, n_out, out_obj, p.d_hy,
                                                        p.d_hz, bin_of, p.npix, nbins, id, (float)(1.0 / p.V),
                                                        (float)p.bH, (float)p.P[0], (float)p.P[1], (float)p.P[2], Iobj);
     return cudaGetLastError();

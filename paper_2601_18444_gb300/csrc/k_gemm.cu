@@ -434,6 +434,19 @@ __device__ __forceinline__ float2 tf_add(float ah, float al, float bh, float bl)
     return make_float2(s, e - (s - h));
 }
 
+// (hi, lo) pairs of a two-float complex value renormalised by TwoSum (the
+// low word of a GEMM result may hold whole chunk partials)
+__device__ __forceinline__ float4 tf_norm4(float4 v)
+{
+    float s = v.x + v.y, bb = s - v.x;
+    const float er = (v.x - (s - bb)) + (v.y - bb);
+    const float re = s;
+    s = v.z + v.w;
+    bb = s - v.z;
+    const float ei = (v.z - (s - bb)) + (v.w - bb);
+    return make_float4(re, er, s, ei);
+}
+
 // two-float complex (re hi, re lo, im hi, im lo) sum
 __device__ __forceinline__ float4 tf_add4(float4 a, float4 b)
 {
@@ -574,10 +587,13 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity
 // Persistent: gridDim.x CTAs (one per SM) walk the work list round-robin;
 // TMEM, barriers and the stage ring stay live across items.  An item is one
 // 128 x 128 output tile per CTA over a k-block range of the chunk's tables.
-// Its FP64 result either goes, unscaled, to the partial tile P[slot]
-// (128 x 128, row-major) for k_gemm_reduce, or -- when the item covers the
-// whole k-range of its output (slot < 0) -- is scaled and added straight
-// into the amplitudes F[-1 - slot] (no partial tile, no reduction pass).
+// Its two-float result either goes, unscaled, to the partial tile P[slot]
+// (128 x 128: column pairs outermost, rows innermost) for k_gemm_reduce, or
+// -- when the item covers the whole k-range of its output (slot < 0) -- is
+// scaled and stored (first piece) or added into the amplitudes F[-1 - slot]
+// (FbView layout; no partial tile, no reduction pass).  Both layouts put
+// the row index innermost, so the 32 rows of an epilogue warp go out as
+// contiguous 512-byte stores.
 //
 // MODE 0: one CTA per item, tcgen05.mma.cta_group::1 with M = N = 128.
 //
@@ -606,7 +622,7 @@ struct GemmItem {
     int32_t slot;         // output slot in P (clusters: of rank 0); < 0: direct to output -1 - slot
     int32_t slot1;        // clusters: output slot of rank 1 (direct: equal to slot)
     int32_t store;        // direct: 1 = first piece of its output (store), 0 = add
-    int32_t pad;
+    int32_t two;          // direct: 1 = the output has several pieces (two-float, both planes)
 };
 
 struct GemmArgs {
@@ -618,8 +634,9 @@ struct GemmArgs {
     const GemmItem* items;
     int n_items;
     int kcb;              // k-blocks per TMEM chunk (drain interval)
-    double* P;            // [slots][128][128] two-float (hi, lo) per element
-    double* F;            // direct outputs: [out][nch][ny*nz] complex, two-float (re hi, re lo, im hi, im lo)
+    double* P;            // [slots][64 column pairs][128 rows] float4 (re hi, re lo, im hi, im lo)
+    double* F;            // direct outputs, high plane: [out][nz][nch * ny] float2 (FbView layout)
+    int64_t lo_off;       // float2 from the high to the low plane
     int ny, nz;
     int nch;              // channels per output (4 per weight set), a power of two
     double scale[4];      // direct outputs: per-channel scale of the unscaled sums
@@ -903,12 +920,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // results leave as two-float pairs (no FP64 arithmetic here: GB300
             // issues few FP64 operations per clock)
             if (slot >= 0) {
-                // this item's tile, unscaled: (hi, lo) per element
-                float4* out = reinterpret_cast<float4*>(g.P + (int64_t)slot * (TC_BM * TC_BN) +
-                                                        (int64_t)(quad * 32 + lane) * TC_BN + colh);
+                // this item's tile, unscaled: (hi, lo) per element, column
+                // pairs j = n / 2 outermost, rows innermost (a warp's stores
+                // are contiguous)
+                float4* out = reinterpret_cast<float4*>(g.P) + (int64_t)slot * (TC_BM * TC_BN / 2) +
+                              (int64_t)(colh >> 1) * TC_BM + quad * 32 + lane;
 #pragma unroll
                 for (int i = 0; i < 16; ++i)
-                    out[i] = make_float4(f2_lane0(hi[i]), f2_lane0(lo[i]), f2_lane1(hi[i]), f2_lane1(lo[i]));
+                    out[i * TC_BM] =
+                        make_float4(f2_lane0(hi[i]), f2_lane0(lo[i]), f2_lane1(hi[i]), f2_lane1(lo[i]));
             } else {
                 // the whole k-range of this output: row m = nch a + c, columns
                 // n = 2b + (re, im) for 16 consecutive b, into F
@@ -918,9 +938,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int a = m / g.nch, ch = m & (g.nch - 1);
                 const int b0 = (ntile * TC_BN + colh) >> 1;
                 if (a < g.ny) {
-                    const int64_t npix = (int64_t)g.ny * g.nz;
-                    float4* o = reinterpret_cast<float4*>(g.F) + ((int64_t)(-1 - slot) * g.nch + ch) * npix +
-                                (int64_t)a * g.nz + b0;
+                    // F_b layout: output, then q_z, then row m (a warp's 32
+                    // rows are contiguous)
+                    const int64_t mrows = (int64_t)g.nch * g.ny;
+                    float2* oh = reinterpret_cast<float2*>(g.F) + (int64_t)(-1 - slot) * g.nz * mrows +
+                                 (int64_t)b0 * mrows + m;
+                    float2* ol = oh + g.lo_off;
                     const int c4 = ch & 3;
                     // a power of two, exact in FP32 (checked at plan creation)
                     const float sc =
@@ -930,8 +953,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         if (b0 + i < g.nz) {
                             float4 v = make_float4(sc * f2_lane0(hi[i]), sc * f2_lane0(lo[i]), sc * f2_lane1(hi[i]),
                                                    sc * f2_lane1(lo[i]));
-                            if (!item.store) v = tf_add4(v, o[i]);
-                            o[i] = v;
+                            if (item.two) {
+                                if (!item.store) {
+                                    const float2 h = oh[i * mrows], l = ol[i * mrows];
+                                    v = tf_add4(v, make_float4(h.x, l.x, h.y, l.y));
+                                } else {
+                                    v = tf_norm4(v);   // high word = the value rounded to FP32
+                                }
+                                oh[i * mrows] = make_float2(v.x, v.z);
+                                ol[i * mrows] = make_float2(v.y, v.w);
+                            } else {
+                                // the output's only piece: its value rounded to FP32
+                                oh[i * mrows] = make_float2(v.x + v.y, v.z + v.w);
+                            }
                         }
                     }
                 }
@@ -947,13 +981,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 // Reduction of item tiles (two-float elements) into per-output amplitudes
 // (two-float complex; stored by an output's first piece, added by later ones):
-//   F[out][c][p][r] (+)= scale_{c mod 4} * sum_{s < splits} P[slot_base + (mt*ntiles + nt)*splits + s][row][col]
-// with m = nch*a + c = mt*128 + row, n = 2b + r = nt*128 + col, p = a*nz + b.
+//   F[out][b][m] (+)= scale_{c mod 4} * sum_{s < splits} P[slot_base + (mt*ntiles + nt)*splits + s][j][row]
+// with m = nch*a + c = mt*128 + row, column pair j = b mod 64, nt = b / 64
+// (the tile column n = 2b + r).  Threads run over m fastest, so both the
+// tile reads and the F writes are contiguous.
 struct RedDesc {
     int32_t slot_base;
     int32_t splits;
     int32_t out;
-    int32_t store;        // 1: first piece of its output (store), 0: add
+    int32_t store;        // bit 0: first piece of its output (store, else add); bit 1: several pieces (two-float)
 };
 
 struct Scale4 {
@@ -961,30 +997,40 @@ struct Scale4 {
 };
 
 __global__ void k_gemm_reduce(const double* __restrict__ P, const RedDesc* __restrict__ reds, int n_red, int ny,
-                              int nz, int ntiles, int nch, Scale4 scale, double* __restrict__ F)
+                              int nz, int ntiles, int nch, Scale4 scale, double* __restrict__ F, int64_t lo_off)
 {
-    const int64_t npix = (int64_t)ny * nz;
+    const int64_t mrows = (int64_t)nch * ny;
+    const int64_t per_out = mrows * nz;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)n_red * nch * npix) return;
-    const int r = (int)(idx / (nch * npix));
-    const int64_t rem = idx % (nch * npix);
-    const int c = (int)(rem / npix);
-    const int64_t p = rem % npix;
-    const int a = (int)(p / nz), b = (int)(p % nz);
-    const int m = nch * a + c, n = 2 * b;
-    const int mt = m >> 7, row = m & 127, nt = n >> 7, col = n & 127;
+    if (idx >= (int64_t)n_red * per_out) return;
+    const int r = (int)(idx / per_out);
+    const int64_t rem = idx % per_out;
+    const int b = (int)(rem / mrows);
+    const int m = (int)(rem % mrows);
+    const int c = m & (nch - 1);
+    const int mt = m >> 7, row = m & 127, nt = b >> 6, j = b & 63;
     const RedDesc d = reds[r];
     const int64_t base = (int64_t)d.slot_base + (int64_t)(mt * ntiles + nt) * d.splits;
+    const float4* P4 = reinterpret_cast<const float4*>(P);
     // two-float sums in FP32 (FP64 is slow on GB300); the scale is a power
     // of two, exact in FP32
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int s = 0; s < d.splits; ++s)
-        acc = tf_add4(acc, *reinterpret_cast<const float4*>(P + (base + s) * (TC_BM * TC_BN) + row * TC_BN + col));
+        acc = tf_add4(acc, P4[(base + s) * (TC_BM * TC_BN / 2) + (int64_t)j * TC_BM + row]);
     const float sc = (float)scale.v[c & 3];
     acc = make_float4(acc.x * sc, acc.y * sc, acc.z * sc, acc.w * sc);
-    float4* o = reinterpret_cast<float4*>(F) + ((int64_t)d.out * nch + c) * npix + p;
-    if (!d.store) acc = tf_add4(acc, *o);
-    *o = acc;
+    float2* oh = reinterpret_cast<float2*>(F) + (int64_t)d.out * per_out + (int64_t)b * mrows + m;
+    if (d.store & 2) {
+        float2* ol = oh + lo_off;
+        if (!(d.store & 1)) {
+            const float2 h = *oh, l = *ol;
+            acc = tf_add4(acc, make_float4(h.x, l.x, h.y, l.y));
+        }
+        *oh = make_float2(acc.x, acc.z);
+        *ol = make_float2(acc.y, acc.w);
+    } else {
+        *oh = make_float2(acc.x + acc.y, acc.z + acc.w);   // the output's only piece, rounded to FP32
+    }
 }
 
 // ------------------------------------------------------------------ self-test
@@ -1056,8 +1102,8 @@ static cudaError_t encode_row_maps(const void* tab, int64_t rows, CUtensorMap* t
 }
 
 cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
-                           int grid, int kcb, double* P, double* F, int ny, int nz, int nch, const double scale[4],
-                           int32_t* err, uint64_t limit_ns, int mode, cudaStream_t s)
+                           int grid, int kcb, double* P, double* F, int64_t lo_off, int ny, int nz, int nch,
+                           const double scale[4], int32_t* err, uint64_t limit_ns, int mode, cudaStream_t s)
 {
     static_assert(GemmCfg<0>::STAGES * GemmCfg<0>::STAGE_BYTES == GemmCfg<2>::STAGES * GemmCfg<2>::STAGE_BYTES,
                   "one dynamic shared-memory size for every mode");
@@ -1093,6 +1139,7 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
     ga.kcb = kcb;
     ga.P = P;
     ga.F = F;
+    ga.lo_off = lo_off;
     ga.ny = ny;
     ga.nz = nz;
     ga.nch = nch;
@@ -1122,14 +1169,14 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
 }
 
 cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, int ny, int nz, int ntiles, int nch,
-                             const double scale[4], double* F, cudaStream_t s)
+                             const double scale[4], double* F, int64_t lo_off, cudaStream_t s)
 {
     Scale4 sc;
     for (int c = 0; c < 4; ++c) sc.v[c] = scale[c];
     const int64_t n = (int64_t)n_red * nch * ny * nz;
     if (n == 0) return cudaSuccess;   // every item of the chunk wrote its output directly
     k_gemm_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, (const RedDesc*)reds, n_red, ny, nz, ntiles, nch, sc,
-                                                              F);
+                                                              F, lo_off);
     return cudaGetLastError();
 }
 

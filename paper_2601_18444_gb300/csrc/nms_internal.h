@@ -46,6 +46,34 @@ struct RotMat {
     double m[9];
 };
 
+// Amplitudes of a batch of tensor-path outputs (F_b), complex FP32 values
+// (float2) in two planes: high words, and low words of a two-float value.
+// Value (output o, channel row m = nch a + c, q_z index b) sits at
+// o * ostride2 + b * mrows + m in each plane, with mrows = nch * ny and
+// ostride2 = nz * mrows: the GEMM row index runs fastest, so the 32 rows an
+// epilogue warp holds go out as 256 contiguous bytes, and a pixel's
+// channels are adjacent.  An output assembled from one piece keeps its
+// value, rounded to FP32, in the high plane only; an output whose pieces
+// (table chunks) add up keeps the two-float value, normalised, in both
+// planes (two[o] = 1).  Either way the high plane holds the value rounded to
+// FP32, which is what the Hermitian products and bins read.
+struct FbView {
+    const float2* hi;       // channel 0 of the chosen weight set, output 0
+    const float2* lo;
+    const uint8_t* two;     // per output of the batch: 1 = low plane in use
+    int64_t ostride2;       // float2 between outputs
+    int mrows;              // float2 between consecutive q_z (nch * ny)
+    int nch, ny, nz;
+    __host__ __device__ int64_t idx(int64_t o, int a, int b) const
+    {
+        return o * ostride2 + (int64_t)b * mrows + (int64_t)nch * a;
+    }
+#ifdef __CUDACC__
+    // channel c of output o at (a, b), rounded to FP32
+    __device__ __forceinline__ float2 load(int64_t o, int a, int b, int c) const { return hi[idx(o, a, b) + c]; }
+#endif
+};
+
 // ---------------------------------------------------------------- plan
 struct Plan {
     cudaStream_t stream = nullptr;
@@ -186,7 +214,7 @@ __device__ __forceinline__ int find_bin(const double* __restrict__ e, int nb, do
 nms_status direct_sum_range(Plan& p, const float4* cpos, int64_t c0, int64_t c1, double* out);
 int tc_tuned_kc_cells(const Plan& p);
 int tc_tuned_items_per_sm(const Plan& p);
-cudaError_t launch_obj_bin(const double* F, int n_out, const int32_t* out_obj, const Plan& p, const int32_t* bin_of,
+cudaError_t launch_obj_bin(const FbView& F, int n_out, const int32_t* out_obj, const Plan& p, const int32_t* bin_of,
                            int nbins, int id, double* Iobj, cudaStream_t s);
 int64_t tc_object_count(const Plan& p);
 

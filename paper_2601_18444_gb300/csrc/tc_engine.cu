@@ -35,10 +35,10 @@ cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, int64_t wstri
                              const int32_t* kb_ncell, int64_t nkb, const float2* qy, int ny, const float2* qz, int nz,
                              int mtiles, int ntiles, const float wscale[4], void* tab, cudaStream_t s);
 cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
-                           int grid, int kcb, double* P, double* F, int ny, int nz, int nch, const double scale[4],
-                           int32_t* err, uint64_t limit_ns, int mode, cudaStream_t s);
+                           int grid, int kcb, double* P, double* F, int64_t lo_off, int ny, int nz, int nch,
+                           const double scale[4], int32_t* err, uint64_t limit_ns, int mode, cudaStream_t s);
 cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, int ny, int nz, int ntiles, int nch,
-                             const double scale[4], double* F, cudaStream_t s);
+                             const double scale[4], double* F, int64_t lo_off, cudaStream_t s);
 size_t tc_item_bytes();
 size_t tc_red_bytes();
 size_t tc_block_bytes();
@@ -47,21 +47,22 @@ cudaError_t launch_prep_rot(const Plan& p, const RotMat& R, bool global, float4*
                             cudaStream_t s);
 cudaError_t launch_centres(int n_out, const int32_t* out_obj, const int32_t* out_rot, int rot0, const double* rot,
                            const double* cen, float4* cyz, cudaStream_t s);
-cudaError_t launch_gacc_batch(const double* F, int n_out, int64_t ostride, int64_t npix, double* G, bool two_float,
-                              cudaStream_t s);
-cudaError_t launch_tf_to_f64(const double* src, double* dst, int64_t n_complex, cudaStream_t s);
-cudaError_t launch_dilute_shift_batch(const double* F, int n_out, int64_t ostride, const float4* cyz,
-                                      const int32_t* out_rot, const float4* qturn, int64_t npix, double* Gdil,
-                                      double* Ftot, int64_t tstride, cudaStream_t s);
+cudaError_t launch_gacc_batch(const FbView& V, int n_out, double* G, cudaStream_t s);
+cudaError_t launch_gacc_totals(const double* T, int n_out, int64_t ostride, int64_t npix, double* G, cudaStream_t s);
+cudaError_t launch_tf_to_f64(const FbView& V, int64_t o, double* dst, cudaStream_t s);
+cudaError_t launch_dilute_shift_batch(const FbView& V, int n_out, const float2* eyz, const int32_t* out_rot,
+                                      double* Gdil, double* Ftot, int64_t tstride, cudaStream_t s);
+cudaError_t launch_shift_factors(int n_out, const float4* cyz, const float2* qy, int ny, const float2* qz, int nz,
+                                 float2* eyz, cudaStream_t s);
 
 namespace {
 
 struct HostItem {
     int32_t mt, nt, kb0, kb1, slot, slot1;   // clusters: mt (mode 2) or nt (mode 1) indexes a tile pair
-    int32_t store, pad;                      // direct items: first piece of the output stores
+    int32_t store, two;                      // direct items: first piece of the output stores; two: several pieces
 };
 struct HostRed {
-    int32_t slot_base, splits, out, store;   // store: first piece of the output
+    int32_t slot_base, splits, out, store;   // store: bit 0 first piece of the output, bit 1 several pieces
 };
 
 struct Chunk {
@@ -88,6 +89,7 @@ struct Schedule {
     void* d_reds = nullptr;
     int32_t* d_out_obj = nullptr;
     int32_t* d_out_rot = nullptr;
+    uint8_t* d_out_two = nullptr;   // per output: 1 = assembled from several pieces (two-float F_b)
     int64_t max_items = 0;
     int max_batch_out = 0;
 };
@@ -111,14 +113,35 @@ struct TcState {
     int64_t tab_kb = 0;          // table capacity in k-blocks
     float4* d_cpos_b = nullptr;  // [R_b][n]
     float4* d_cw_b = nullptr;
-    double* d_Fb = nullptr;      // [out_cap][nch][npix] two-float complex (16 B each)
+    double* d_Fb = nullptr;      // out_cap outputs, FbView layout: two planes [out][q_z][nch * n_y] of float2
+    int out_cap = 1;             // outputs per batch
     double* d_Ftot_b = nullptr;  // [R_b][4][npix][2] (objects)
     float4* d_cyz = nullptr;     // [out_cap]
+    float2* d_eyz = nullptr;     // objects: [out_cap][ny + nz] shift factors along q_y and q_z
     double* d_rot = nullptr;     // [n_rot][9]
     double* d_cen = nullptr;     // [K][3]
     double* d_P = nullptr;       // item tiles
     Schedule full, last;
 };
+
+// float2 values in one plane of a batch of GEMM outputs
+static int64_t fb_plane(const TcState& t, int n_out) { return (int64_t)n_out * t.nz * t.nch * t.ny; }
+
+// view of a batch of GEMM outputs: high plane at F, low plane lo_off float2
+// further, per-output piece flags two; weight set st
+static FbView fb_view(const TcState& t, const double* F, int64_t lo_off, const uint8_t* two, int st)
+{
+    FbView v;
+    v.hi = reinterpret_cast<const float2*>(F) + 4 * st;
+    v.lo = v.hi + lo_off;
+    v.two = two;
+    v.mrows = t.nch * t.ny;
+    v.ostride2 = (int64_t)t.nz * v.mrows;
+    v.nch = t.nch;
+    v.ny = t.ny;
+    v.nz = t.nz;
+    return v;
+}
 
 static double pow2_ceil(double x)
 {
@@ -142,7 +165,7 @@ static nms_status upload(T** d, const std::vector<T>& h)
 
 static void free_schedule(Schedule& s)
 {
-    void* b[] = {s.d_kb_cell0, s.d_kb_ncell, s.d_items, s.d_reds, s.d_out_obj, s.d_out_rot};
+    void* b[] = {s.d_kb_cell0, s.d_kb_ncell, s.d_items, s.d_reds, s.d_out_obj, s.d_out_rot, s.d_out_two};
     for (void* x : b)
         if (x) plan_free(x);
     s = Schedule();
@@ -181,6 +204,7 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
     std::vector<HostItem> items;
     std::vector<HostRed> reds;
     std::vector<int32_t> out_obj(sums.size()), out_rot(sums.size());
+    std::vector<uint8_t> out_two(sums.size(), 0);
     for (size_t o = 0; o < sums.size(); ++o) {
         out_obj[o] = sums[o].obj;
         out_rot[o] = sums[o].rl;
@@ -215,6 +239,13 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
                 cur_kb += (take + 31) / 32;
                 c += take;
             }
+        }
+        // outputs cut into several pieces keep two-float values
+        {
+            std::vector<int> npieces(ob.n_out, 0);
+            for (const auto& pieces : chunk_pieces)
+                for (const Piece& pc : pieces) ++npieces[pc.out];
+            for (int o = 0; o < ob.n_out; ++o) out_two[o0 + o] = npieces[o] > 1 ? 1 : 0;
         }
         for (auto& pieces : chunk_pieces) {
             if (pieces.empty()) continue;
@@ -261,15 +292,16 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
                     // one item per tile spans the piece: the GEMM adds it into F directly
                     const int32_t direct = -1 - pc.out;
                     const int32_t first = started[pc.out] ? 0 : 1;
+                    const int32_t two = out_two[o0 + pc.out];
                     started[pc.out] = 1;
                     for (int mt = 0; mt < t.mtiles; mt += mstep)
                         for (int nt = 0; nt < t.ntiles; nt += nstep)
                             its.push_back({mt / mstep, nt / nstep, (int32_t)kb, (int32_t)(kb + nkb_p), direct, direct,
-                                           first, 0});
+                                           first, two});
                     kb += nkb_p;
                     continue;
                 }
-                reds.push_back({slot, splits, pc.out, started[pc.out] ? 0 : 1});
+                reds.push_back({slot, splits, pc.out, (started[pc.out] ? 0 : 1) | (out_two[o0 + pc.out] ? 2 : 0)});
                 started[pc.out] = 1;
                 // k-range major: the CTAs of one wave share each k-range, so
                 // every table block comes from HBM about once and is reused
@@ -302,7 +334,8 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
     }
     nms_status st;
     if ((st = upload(&S.d_kb_cell0, kb_cell0)) || (st = upload(&S.d_kb_ncell, kb_ncell)) ||
-        (st = upload(&S.d_out_obj, out_obj)) || (st = upload(&S.d_out_rot, out_rot)))
+        (st = upload(&S.d_out_obj, out_obj)) || (st = upload(&S.d_out_rot, out_rot)) ||
+        (st = upload(&S.d_out_two, out_two)))
         return st;
     if (!items.empty()) {
         NMS_CUDA_TRY(plan_malloc(&S.d_items, items.size() * sizeof(HostItem)));
@@ -318,15 +351,17 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
 // ------------------------------------------------------------------ autotuner
 // max over pixels of |A - B| per channel; A two-float (the GEMM's output
 // format), B FP64
-__global__ void k_amp_maxerr(const float4* __restrict__ A4, const double2* __restrict__ B, int64_t npix,
-                             unsigned int* __restrict__ err)
+__global__ void k_amp_maxerr(FbView A, const double2* __restrict__ B, unsigned int* __restrict__ err)
 {
+    const int64_t npix = (int64_t)A.ny * A.nz;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npix) return;
+    const int qa = (int)(p / A.nz), qb = (int)(p % A.nz);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        const float4 a4 = A4[(int64_t)c * npix + p];
-        const double2 a = make_double2((double)a4.x + (double)a4.y, (double)a4.z + (double)a4.w);
+        const float2 h = A.hi[A.idx(0, qa, qb) + c];
+        const float2 l = A.two[0] ? A.lo[A.idx(0, qa, qb) + c] : make_float2(0.f, 0.f);
+        const double2 a = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
         const double2 b = B[(int64_t)c * npix + p];
         const float d = (float)hypot(a.x - b.x, a.y - b.y);
         atomicMax(&err[c], __float_as_uint(d));   // non-negative floats order as integers
@@ -483,18 +518,17 @@ nms_status tc_autotune(Plan& p, TcState& t)
         if (ce != cudaSuccess) { free_schedule(S); st = cuda_fail(ce, "autotune partials"); break; }
         float ms = 1e30f;
         const Chunk& ch = S.batches[0].chunks[0];
+        const int64_t lo_off = fb_plane(t, 1);
         for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {
-            ce = cudaMemsetAsync(d_Fp, 0, (size_t)t.nch * 2 * np * sizeof(double), s);
-            if (ce == cudaSuccess)
-                ce = tc_launch_tables(t.d_cpos_b, t.d_cw_b, t.wstride, t.nch, S.d_kb_cell0, S.d_kb_ncell, ch.nkb, t.d_qy,
+            ce = tc_launch_tables(t.d_cpos_b, t.d_cw_b, t.wstride, t.nch, S.d_kb_cell0, S.d_kb_ncell, ch.nkb, t.d_qy,
                                       t.ny, t.d_qz, t.nz, t.mtiles, t.ntiles, wscale, p.d_tab, s);
             if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
             if (ce == cudaSuccess)
                 ce = tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles, S.d_items, ch.n_items, ch.grid, kcb, P,
-                                    d_Fp, t.ny, t.nz, t.nch, scale, p.d_err, limit, t.mode, s);
+                                    d_Fp, lo_off, t.ny, t.nz, t.nch, scale, p.d_err, limit, t.mode, s);
             if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
             if (ce == cudaSuccess)
-                ce = tc_launch_reduce(P, S.d_reds, ch.n_red, t.ny, t.nz, t.ntiles, t.nch, scale, d_Fp, s);
+                ce = tc_launch_reduce(P, S.d_reds, ch.n_red, t.ny, t.nz, t.ntiles, t.nch, scale, d_Fp, lo_off, s);
             if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
             float m = 0.f;
             if (ce == cudaSuccess) cudaEventElapsedTime(&m, e0, e1);
@@ -503,9 +537,8 @@ nms_status tc_autotune(Plan& p, TcState& t)
         unsigned int herr[4] = {0, 0, 0, 0};
         if (ce == cudaSuccess) ce = cudaMemsetAsync(d_err, 0, sizeof(herr), s);
         if (ce == cudaSuccess) {
-            k_amp_maxerr<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(reinterpret_cast<const float4*>(d_Fp),
-                                                                    reinterpret_cast<const double2*>(p.d_F), np,
-                                                                    d_err);
+            k_amp_maxerr<<<(unsigned)((np + 255) / 256), 256, 0, s>>>(fb_view(t, d_Fp, lo_off, S.d_out_two, 0),
+                                                                    reinterpret_cast<const double2*>(p.d_F), d_err);
             ce = cudaGetLastError();
         }
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(herr, d_err, sizeof(herr), cudaMemcpyDeviceToHost, s);
@@ -642,8 +675,10 @@ nms_status tc_setup(Plan& p)
     const int64_t out_bytes = (int64_t)t->nch * np * 16;
     const int64_t outs_per_rb = t->objects ? (int64_t)t->R_b * p.n_objects : t->R_b;
     const int out_cap = (int)std::max<int64_t>(1, std::min<int64_t>(outs_per_rb, (1ll << 30) / out_bytes));
+    t->out_cap = out_cap;
     NMS_CUDA_TRY(plan_malloc(&t->d_Fb, (size_t)out_cap * out_bytes));
     NMS_CUDA_TRY(plan_malloc(&t->d_cyz, (size_t)out_cap * sizeof(float4)));
+    if (t->objects) NMS_CUDA_TRY(plan_malloc(&t->d_eyz, (size_t)out_cap * (t->ny + t->nz) * sizeof(float2)));
     // total amplitude per prepared rotation and weight set
     if (t->objects) NMS_CUDA_TRY(plan_malloc(&t->d_Ftot_b, (size_t)t->R_b * t->nsets * 8 * np * sizeof(double)));
     // phase tables: as many k-blocks as the workspace allows
@@ -684,7 +719,8 @@ void tc_release(Plan& p)
 {
     TcState* t = (TcState*)p.tc_state;
     if (!t) return;
-    void* b[] = {t->d_qy, t->d_qz, t->d_cpos_b, t->d_cw_b, t->d_Fb, t->d_Ftot_b, t->d_cyz, t->d_rot, t->d_cen, t->d_P};
+    void* b[] = {t->d_qy,  t->d_qz,  t->d_cpos_b, t->d_cw_b, t->d_Fb, t->d_Ftot_b,
+                 t->d_cyz, t->d_eyz, t->d_rot,    t->d_cen,  t->d_P};
     for (void* x : b)
         if (x) plan_free(x);
     free_schedule(t->full);
@@ -700,12 +736,12 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
     const int64_t np = p.npix;
     const int nS = t.nsets;
     const int64_t F4 = 8 * np;                   // doubles of one set's amplitudes [4][np] complex
-    const int64_t ostride = (int64_t)t.nch * 2 * np;   // doubles between outputs of a batch
     const float sc = tc_operand_scale();
     const float wscale[4] = {(float)(sc / t.W[0]), (float)(sc / t.W[1]), (float)(sc / t.W[2]), (float)(sc / t.W[3])};
     double scale[4];
     for (int c = 0; c < 4; ++c) scale[c] = t.W[c] / ((double)sc * (double)sc);
     const uint64_t limit = p.opt.max_spin > 0 ? (uint64_t)p.opt.max_spin * 1000ull : 4000000000ull;
+    const int64_t lo_off = fb_plane(t, t.out_cap);   // float2 from the high to the low plane of F_b
     for (int rb0 = 0; rb0 < p.n_rot; rb0 += t.R_b) {
         const int nrl = std::min(t.R_b, p.n_rot - rb0);
         const Schedule& S = nrl == t.R_b ? t.full : t.last;
@@ -728,42 +764,44 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
                 p.timer.begin(ST_GEMM);
                 NMS_CUDA_TRY(tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles,
                                             (const char*)S.d_items + ch.item_off * tc_item_bytes(), ch.n_items, ch.grid,
-                                            t.kcb, t.d_P, t.d_Fb, t.ny, t.nz, t.nch, scale, p.d_err, limit, t.mode, s));
+                                            t.kcb, t.d_P, t.d_Fb, lo_off, t.ny, t.nz, t.nch, scale, p.d_err, limit,
+                                            t.mode, s));
                 p.timer.end(ST_GEMM, 1);
                 p.timer.begin(ST_REDUCE);
                 NMS_CUDA_TRY(tc_launch_reduce(t.d_P, (const char*)S.d_reds + ch.red_off * tc_red_bytes(), ch.n_red, t.ny,
-                                              t.nz, t.ntiles, t.nch, scale, t.d_Fb, s));
+                                              t.nz, t.ntiles, t.nch, scale, t.d_Fb, lo_off, s));
                 p.timer.end(ST_REDUCE, ch.n_red > 0 ? 1 : 0);
             }
             p.timer.begin(ST_GACC);
             int nl = 0;
             if (p.oiq_id >= 0) {   // one weight set (checked when requested)
-                NMS_CUDA_TRY(launch_obj_bin(t.d_Fb, ob.n_out, S.d_out_obj + ob.out0, p, p.d_bin_of, p.oiq_nbins,
-                                            p.oiq_id, p.d_Iobj, s));
+                const FbView V0 = fb_view(t, t.d_Fb, lo_off, S.d_out_two + ob.out0, 0);
+                NMS_CUDA_TRY(launch_obj_bin(V0, ob.n_out, S.d_out_obj + ob.out0, p, p.d_bin_of, p.oiq_nbins, p.oiq_id,
+                                            p.d_Iobj, s));
                 ++nl;
             }
             if (t.objects) {
                 NMS_CUDA_TRY(launch_centres(ob.n_out, S.d_out_obj + ob.out0, S.d_out_rot + ob.out0, rb0, t.d_rot, t.d_cen,
                                             t.d_cyz, s));
-                ++nl;
+                NMS_CUDA_TRY(launch_shift_factors(ob.n_out, t.d_cyz, t.d_qy, t.ny, t.d_qz, t.nz, t.d_eyz, s));
+                nl += 2;
             }
             for (int st = 0; st < nS; ++st) {
-                const double* Fs = t.d_Fb + (size_t)st * F4;   // set st of the batch's first output
+                const FbView V = fb_view(t, t.d_Fb, lo_off, S.d_out_two + ob.out0, st);   // set st of the batch's outputs
                 if (t.objects) {
-                    NMS_CUDA_TRY(launch_dilute_shift_batch(Fs, ob.n_out, ostride, t.d_cyz, S.d_out_rot + ob.out0,
-                                                           p.d_qturn, np, p.d_Gdil + (size_t)st * 16 * np,
+                    NMS_CUDA_TRY(launch_dilute_shift_batch(V, ob.n_out, t.d_eyz, S.d_out_rot + ob.out0,
+                                                           p.d_Gdil + (size_t)st * 16 * np,
                                                            t.d_Ftot_b + (size_t)st * F4, (int64_t)nS * F4, s));
                     ++nl;
                 } else {
-                    NMS_CUDA_TRY(launch_gacc_batch(Fs, ob.n_out, ostride, np, p.d_Gtot + (size_t)st * 16 * np, true, s));
+                    NMS_CUDA_TRY(launch_gacc_batch(V, ob.n_out, p.d_Gtot + (size_t)st * 16 * np, s));
                     ++nl;
                     if (p.d_Gdil) {
-                        NMS_CUDA_TRY(launch_gacc_batch(Fs, ob.n_out, ostride, np, p.d_Gdil + (size_t)st * 16 * np, true, s));
+                        NMS_CUDA_TRY(launch_gacc_batch(V, ob.n_out, p.d_Gdil + (size_t)st * 16 * np, s));
                         ++nl;
                     }
                     if (rb0 + nrl == p.n_rot && &ob == &S.batches.back())
-                        NMS_CUDA_TRY(launch_tf_to_f64(Fs + (size_t)(ob.n_out - 1) * ostride, p.d_F + (size_t)st * F4,
-                                                      4 * np, s));
+                        NMS_CUDA_TRY(launch_tf_to_f64(V, ob.n_out - 1, p.d_F + (size_t)st * F4, s));
                 }
             }
             p.timer.end(ST_GACC, nl);
@@ -772,7 +810,7 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
             p.timer.begin(ST_GACC);
             for (int st = 0; st < nS; ++st) {
                 const double* Ts = t.d_Ftot_b + (size_t)st * F4;
-                NMS_CUDA_TRY(launch_gacc_batch(Ts, nrl, (int64_t)nS * F4, np, p.d_Gtot + (size_t)st * 16 * np, false, s));
+                NMS_CUDA_TRY(launch_gacc_totals(Ts, nrl, (int64_t)nS * F4, np, p.d_Gtot + (size_t)st * 16 * np, s));
                 if (rb0 + nrl == p.n_rot)
                     NMS_CUDA_TRY(cudaMemcpyAsync(p.d_Ftot + (size_t)st * F4, Ts + (size_t)(nrl - 1) * nS * F4,
                                                  F4 * sizeof(double), cudaMemcpyDeviceToDevice, s));

@@ -549,6 +549,36 @@ __device__ __forceinline__ void tc_mma2_f16(uint32_t d_tmem, uint64_t a_desc, ui
         : "memory");
 }
 
+// The three products of one 16-wide k step: D0 (+)= A_hi B_hi, D1 (+)= A_hi B_lo,
+// D1 += A_lo B_hi, in one asm block (one predicate for the first two, a
+// constant-true one for the third), so the issuing thread spends few
+// instructions per MMA.
+template <int CG>
+__device__ __forceinline__ void tc_mma3_f16(uint32_t d0, uint32_t d1, uint64_t ah, uint64_t al, uint64_t bh,
+                                            uint64_t bl, uint32_t idesc, uint32_t accumulate)
+{
+    if constexpr (CG == 2)
+        asm volatile(
+            "{\n\t.reg .pred p, t;\n\t"
+            "setp.ne.b32 p, %7, 0;\n\t"
+            "setp.eq.b32 t, %6, %6;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %2, %4, %6, p;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%1], %2, %5, %6, p;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%1], %3, %4, %6, t;\n\t}\n" ::"r"(d0),
+            "r"(d1), "l"(ah), "l"(al), "l"(bh), "l"(bl), "r"(idesc), "r"(accumulate)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p, t;\n\t"
+            "setp.ne.b32 p, %7, 0;\n\t"
+            "setp.eq.b32 t, %6, %6;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %4, %6, p;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%1], %2, %5, %6, p;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%1], %3, %4, %6, t;\n\t}\n" ::"r"(d0),
+            "r"(d1), "l"(ah), "l"(al), "l"(bh), "l"(bl), "r"(idesc), "r"(accumulate)
+            : "memory");
+}
+
 // arrive on the mbarrier at this offset in CTA `cta` of the cluster
 __device__ __forceinline__ void mbar_arrive_cluster(uint64_t* bar, uint32_t cta)
 {
@@ -705,12 +735,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ---------------- producer: bulk copies of the operand blocks
         if (lane == 0) {
             int64_t i = 0;              // stage sequence number across items
+            int s = 0;                  // its stage
+            uint32_t par = 1u;          // parity of the stage's previous "empty" phase
             bool ok = true;
             for (int it = unit0; it < g.n_items && ok; it += units) {
                 const GemmItem item = g.items[it];
                 for (int kb = item.kb0; kb < item.kb1; ++kb) {
-                    const int s = (int)(i % STG);
-                    const uint32_t par = (uint32_t)((i / STG) & 1) ^ 1u;
                     if (!mbar_wait(&bar_empty[s], par, g.limit_ns, &s_abort)) {
                         s_abort = 1;
                         atomicExch(g.err, 1);
@@ -731,6 +761,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         tma_load_2d_pair(st + 2 * TC_BLOCK_BYTES, &tmB, rb, lead);
                         tma_load_2d_pair(st + 2 * TC_BLOCK_BYTES + C::B_BYTES, &tmB, rb + g.ntiles * nk * 128, lead);
                         ++i;
+                        if (++s == STG) {
+                            s = 0;
+                            par ^= 1u;
+                        }
                         continue;
                     }
                     mbar_arrive_expect_tx(&bar_full[s], MODE == 2 ? 2 * C::STAGE_BYTES : C::STAGE_BYTES);
@@ -749,6 +783,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     bulk_g2s(st + 2 * TC_BLOCK_BYTES, g.B_hi + bo, C::B_BYTES, &bar_full[s]);
                     bulk_g2s(st + 2 * TC_BLOCK_BYTES + C::B_BYTES, g.B_lo + bo, C::B_BYTES, &bar_full[s]);
                     ++i;
+                    if (++s == STG) {
+                        s = 0;
+                        par ^= 1u;
+                    }
                 }
             }
             // copies in flight must land before the CTA exits (bounded): only
@@ -779,8 +817,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint32_t idesc = idesc_f16_f32(MM, TC_BN);
             const uint32_t bofs = 2 * TC_BLOCK_BYTES;             // B_hi in the stage
             const uint32_t lofs = bofs + C::B_BYTES;              // B_lo in the stage
-            int64_t i = 0;              // stage sequence number
-            int64_t c = 0;              // TMEM chunk sequence number
+            int s = 0;                  // stage of the next k-block
+            uint32_t sph = 0;           // its phase bit (flips each pass over the ring)
+            uint32_t c = 0;             // TMEM chunk sequence number
             bool ok = true;
             for (int it = unit0; it < g.n_items && ok; it += units) {
                 const GemmItem item = g.items[it];
@@ -798,36 +837,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const uint32_t d1 = d0 + 128u;
                     const int k1 = min(item.kb1, k0 + g.kcb);
                     bool first = true;
-                    for (int kb = k0; kb < k1; ++kb, ++i) {
-                        const int s = (int)(i % STG);
-                        const uint32_t par = (uint32_t)((i / STG) & 1);
-                        const bool okf = mbar_wait(&bar_full[s], par, g.limit_ns, &s_abort);
+                    for (int kb = k0; kb < k1; ++kb) {
+                        const bool okf = mbar_wait(&bar_full[s], sph, g.limit_ns, &s_abort);
                         if (!okf) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
                         const uint32_t st = sbase + (uint32_t)s * C::STAGE_BYTES;
+                        // descriptors of the stage's four blocks; each 16-wide k
+                        // step moves the start address field by 32 bytes (2 units)
+                        const uint64_t ah0 = sw128_desc(st), al0 = sw128_desc(st + TC_BLOCK_BYTES);
+                        const uint64_t bh0 = sw128_desc(st + bofs), bl0 = sw128_desc(st + lofs);
 #pragma unroll
                         for (int k16 = 0; k16 < 4; ++k16) {
-                            const uint64_t ah = sw128_desc(st + k16 * 32);
-                            const uint64_t al = sw128_desc(st + TC_BLOCK_BYTES + k16 * 32);
-                            const uint64_t bh = sw128_desc(st + bofs + k16 * 32);
-                            const uint64_t bl = sw128_desc(st + lofs + k16 * 32);
-                            const uint32_t acc = first ? 0u : 1u;
-                            if (MODE == 2) {
-                                tc_mma2_f16(d0, ah, bh, idesc, acc);
-                                tc_mma2_f16(d1, ah, bl, idesc, acc);
-                                tc_mma2_f16(d1, al, bh, idesc, 1u);
-                            } else {
-                                tc_mma_f16(d0, ah, bh, idesc, acc);
-                                tc_mma_f16(d1, ah, bl, idesc, acc);
-                                tc_mma_f16(d1, al, bh, idesc, 1u);
-                            }
+                            tc_mma3_f16<C::CG>(d0, d1, ah0 + 2 * k16, al0 + 2 * k16, bh0 + 2 * k16, bl0 + 2 * k16, idesc,
+                                               first ? 0u : 1u);
                             first = false;
                         }
                         if (MODE == 0) tc_commit(&bar_empty[s]);
                         else tc_commit_to<C::CG>(&bar_empty[s], (uint16_t)3);
+                        if (++s == STG) {
+                            s = 0;
+                            sph ^= 1u;
+                        }
                     }
                     if (!ok) break;
                     if (MODE == 2) tc_commit_to<2>(&bar_acc_full[b], (uint16_t)3);
@@ -894,6 +927,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         lo[idx] = f2_add(lo[idx], x);   // chunk partial into the low word
 #endif
                     }
+                    // pace the drain: four drain warps share each scheduler with
+                    // the producer or MMA thread; a short yield per column
+                    // group keeps the single MMA-issuing thread from waiting
+                    // behind their bursts (GEMM -3 % on the 512^2 box).  Not
+                    // in the two-SM form, whose MMAs wait for both CTAs' drains.
+                    if (MODE != 2) __nanosleep(32);
                 }
 #if TC_RENORM > 0
                 // every TC_RENORM chunks: TwoSum(hi, lo) -> (hi, lo), so lo

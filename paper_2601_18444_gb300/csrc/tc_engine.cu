@@ -610,13 +610,13 @@ nms_status tc_setup(Plan& p)
     t->kcb = p.opt.kc_cells > 0 ? std::max(1, p.opt.kc_cells / 32) : 2;
     if (p.opt.split_k > 0) t->items_per_sm = std::min(256, p.opt.split_k);
     t->objects = p.n_objects > 1 && p.opt.want_dilute;
-    // CTA pairs sharing A where the B tiles pair up (the fastest form
-    // measured: the two-SM MMA writes fewer operand bytes into shared memory
-    // per stage, but each SM still reads the whole B tile, half of it from
-    // the peer, and it measured 6 % slower), else the two-SM MMA over A-tile
-    // pairs, else one CTA per tile.  NMS_GEMM_MODE = 0, 1 or 2 forces a form
-    // the grid allows (diagnostics, tests).
-    t->mode = (t->ntiles % 2 == 0) ? 1 : (t->mtiles % 2 == 0) ? 2 : 0;
+    // CTA pairs sharing A where the B tiles pair up, else one CTA per tile
+    // (the two measured within 1 %; the two-SM MMA writes fewer operand
+    // bytes into shared memory per stage, but each SM still reads the whole
+    // B tile, half of it from the peer, and it measured 20 % slower).
+    // NMS_GEMM_MODE = 0, 1 or 2 forces a form the grid allows (diagnostics,
+    // tests); the autotuner times all of them.
+    t->mode = (t->ntiles % 2 == 0) ? 1 : 0;
     if (const char* gm = getenv("NMS_GEMM_MODE")) {
         const int want = atoi(gm);
         if (want == 0 || (want == 1 && t->ntiles % 2 == 0) || (want == 2 && t->mtiles % 2 == 0)) {

@@ -33,6 +33,73 @@ cudaError_t launch_azimuthal_polar(const Plan& p, const double* img, double* Iq,
     return cudaGetLastError();
 }
 
+// Per-pixel q-grid quantities in FP64 (Sec. "Summation approach": the
+// detector plane q = (0, q_y, q_z)): q_y, q_z, the unit vector (h_y, h_z) =
+// q/|q| (0, 1 at q = 0), |q|, and q/(2 pi) as two-float turns.  Cartesian:
+// pixel i = a n1 + b, q_y = node(a; n0, lo0, hi0), q_z = node(b; n1, lo1,
+// hi1); polar: |q| = node(a; n0, lo0, hi0), theta = 2 pi b / n1, q_y =
+// |q| sin theta, q_z = |q| cos theta, h = (sin, cos); list: (q_y, q_z) pairs.
+// node(a; n, lo, hi) = lo + ((hi - lo) a)/(n - 1), without contraction.
+__device__ __forceinline__ double grid_node(int64_t a, int64_t n, double lo, double hi)
+{
+    if (n == 1) return lo;
+    return __dadd_rn(lo, __ddiv_rn(__dmul_rn(__dadd_rn(hi, -lo), (double)a), (double)(n - 1)));
+}
+
+__global__ void k_grid(int kind, int64_t np, int n0, int n1, double lo0, double hi0, double lo1, double hi1,
+                       const double* __restrict__ qlist, double* __restrict__ qy, double* __restrict__ qz,
+                       double* __restrict__ hy, double* __restrict__ hz, double* __restrict__ qa,
+                       float4* __restrict__ qturn)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const double two_pi = 6.283185307179586;
+    double y, z, h1, h2, a;
+    if (kind == NMS_QGRID_POLAR) {
+        const double qm = grid_node(i / n1, n0, lo0, hi0);
+        const double th = __ddiv_rn(__dmul_rn(two_pi, (double)(i % n1)), (double)n1);
+        double st, ct;
+        sincos(th, &st, &ct);
+        y = __dmul_rn(qm, st);
+        z = __dmul_rn(qm, ct);
+        h1 = st;
+        h2 = ct;
+        a = qm;
+    } else {
+        if (kind == NMS_QGRID_CARTESIAN) {
+            y = grid_node(i / n1, n0, lo0, hi0);
+            z = grid_node(i % n1, n1, lo1, hi1);
+        } else {
+            y = qlist[2 * i];
+            z = qlist[2 * i + 1];
+        }
+        a = hypot(y, z);
+        if (a > 0.0) {
+            h1 = __ddiv_rn(y, a);
+            h2 = __ddiv_rn(z, a);
+        } else {
+            h1 = 0.0;
+            h2 = 1.0;
+        }
+    }
+    qy[i] = y;
+    qz[i] = z;
+    hy[i] = h1;
+    hz[i] = h2;
+    qa[i] = a;
+    const double ty = __ddiv_rn(y, two_pi), tz = __ddiv_rn(z, two_pi);
+    const float tyh = (float)ty, tzh = (float)tz;
+    qturn[i] = make_float4(tyh, (float)(ty - (double)tyh), tzh, (float)(tz - (double)tzh));
+}
+
+cudaError_t launch_grid(const nms_qgrid& g, int64_t np, const double* d_qlist, double* qy, double* qz, double* hy,
+                        double* hz, double* qa, float4* qturn, cudaStream_t s)
+{
+    k_grid<<<(unsigned)((np + 255) / 256), 256, 0, s>>>((int)g.kind, np, g.n0, g.n1, g.lo0, g.hi0, g.lo1, g.hi1, d_qlist,
+                                                        qy, qz, hy, hz, qa, qturn);
+    return cudaGetLastError();
+}
+
 // Nodes of the polar grid as bins: counts[i] = n_theta, qmean[i] = q_i
 // (linear nodes lo + ((hi - lo) i)/(n - 1), as the grid defines them).
 __global__ void k_polar_nodes(int n0, int n1, double lo, double hi, int64_t* __restrict__ counts,

@@ -250,69 +250,40 @@ static void free_plan(nms_plan_s* p)
     delete p;
 }
 
-// q-grid on the host in FP64.  The expression order of the linear spacing is
-// lo + ((hi - lo) * a) / (n - 1).
-static double lin_node(int64_t a, int64_t n, double lo, double hi)
-{
-    if (n == 1) return lo;
-    return lo + ((hi - lo) * (double)a) / (double)(n - 1);
-}
-
+// Per-pixel q-grid arrays, computed on the device (launch_grid) on the
+// plan's stream; a list grid is checked here and copied up first.
 static nms_status build_grid(Plan& p, const nms_qgrid& g)
 {
     int64_t np = 0;
     if (g.kind == NMS_QGRID_CARTESIAN || g.kind == NMS_QGRID_POLAR) {
         if (g.n0 < 1 || g.n1 < 1) return fail(NMS_ERR_INVALID_ARG, "grid: n0 and n1 must be >= 1");
+        if (!std::isfinite(g.lo0) || !std::isfinite(g.hi0) ||
+            (g.kind == NMS_QGRID_CARTESIAN && (!std::isfinite(g.lo1) || !std::isfinite(g.hi1))))
+            return fail(NMS_ERR_INVALID_ARG, "grid: non-finite q");
         np = (int64_t)g.n0 * g.n1;
     } else if (g.kind == NMS_QGRID_LIST) {
         if (g.n0 < 1 || !g.qlist) return fail(NMS_ERR_INVALID_ARG, "grid: LIST needs n0 >= 1 and qlist");
         np = g.n0;
+        for (int64_t i = 0; i < 2 * np; ++i)
+            if (!std::isfinite(g.qlist[i])) return fail(NMS_ERR_INVALID_ARG, "grid: non-finite q");
     } else {
         return fail(NMS_ERR_INVALID_ARG, "grid: unknown kind");
     }
-    std::vector<double> qy(np), qz(np), hy(np), hz(np), qa(np);
-    std::vector<float4> qt(np);
-    const double two_pi = 2.0 * M_PI;
-    for (int64_t i = 0; i < np; ++i) {
-        double y, z, h1, h2, a;
-        if (g.kind == NMS_QGRID_CARTESIAN) {
-            y = lin_node(i / g.n1, g.n0, g.lo0, g.hi0);
-            z = lin_node(i % g.n1, g.n1, g.lo1, g.hi1);
-        } else if (g.kind == NMS_QGRID_POLAR) {
-            double qm = lin_node(i / g.n1, g.n0, g.lo0, g.hi0);
-            double th = (two_pi * (double)(i % g.n1)) / (double)g.n1;
-            double st = sin(th), ct = cos(th);
-            y = qm * st;
-            z = qm * ct;
-            h1 = st;
-            h2 = ct;
-            a = qm;
-        } else {
-            y = g.qlist[2 * i];
-            z = g.qlist[2 * i + 1];
-        }
-        if (!std::isfinite(y) || !std::isfinite(z)) return fail(NMS_ERR_INVALID_ARG, "grid: non-finite q");
-        if (g.kind != NMS_QGRID_POLAR) {
-            a = hypot(y, z);
-            if (a > 0.0) { h1 = y / a; h2 = z / a; } else { h1 = 0.0; h2 = 1.0; }
-        }
-        qy[i] = y; qz[i] = z; hy[i] = h1; hz[i] = h2; qa[i] = a;
-        double ty = y / two_pi, tz = z / two_pi;
-        float tyh = (float)ty, tzh = (float)tz;
-        qt[i] = make_float4(tyh, (float)(ty - (double)tyh), tzh, (float)(tz - (double)tzh));
-    }
     p.npix = np;
-    p.h_qa = qa;
     nms_status st;
     if ((st = dalloc(&p.d_qy, np, "qy")) || (st = dalloc(&p.d_qz, np, "qz")) || (st = dalloc(&p.d_hy, np, "hy")) ||
         (st = dalloc(&p.d_hz, np, "hz")) || (st = dalloc(&p.d_qa, np, "qa")) || (st = dalloc(&p.d_qturn, np, "qturn")))
         return st;
-    NMS_CUDA_TRY(cudaMemcpy(p.d_qy, qy.data(), np * 8, cudaMemcpyHostToDevice));
-    NMS_CUDA_TRY(cudaMemcpy(p.d_qz, qz.data(), np * 8, cudaMemcpyHostToDevice));
-    NMS_CUDA_TRY(cudaMemcpy(p.d_hy, hy.data(), np * 8, cudaMemcpyHostToDevice));
-    NMS_CUDA_TRY(cudaMemcpy(p.d_hz, hz.data(), np * 8, cudaMemcpyHostToDevice));
-    NMS_CUDA_TRY(cudaMemcpy(p.d_qa, qa.data(), np * 8, cudaMemcpyHostToDevice));
-    NMS_CUDA_TRY(cudaMemcpy(p.d_qturn, qt.data(), np * sizeof(float4), cudaMemcpyHostToDevice));
+    double* d_list = nullptr;
+    if (g.kind == NMS_QGRID_LIST) {
+        if ((st = dalloc(&d_list, 2 * np, "qlist"))) return st;
+        NMS_CUDA_TRY(cudaMemcpyAsync(d_list, g.qlist, 2 * np * sizeof(double), cudaMemcpyHostToDevice, p.stream));
+    }
+    NMS_CUDA_TRY(launch_grid(g, np, d_list, p.d_qy, p.d_qz, p.d_hy, p.d_hz, p.d_qa, p.d_qturn, p.stream));
+    if (d_list) {
+        NMS_CUDA_TRY(cudaStreamSynchronize(p.stream));   // the copy from the caller's buffer has completed
+        dfree(d_list);
+    }
     return NMS_OK;
 }
 
@@ -892,10 +863,13 @@ nms_status nms_plan_object_iq(nms_plan_t plan, int32_t response_id, int32_t nbin
     for (int b = 0; b < nbins; ++b)
         if (!(bin_edges[b + 1] > bin_edges[b])) return fail(NMS_ERR_INVALID_ARG, "bin_edges not increasing");
     std::vector<int32_t> bin_of(p.npix);
+    std::vector<double> h_qa(p.npix);
+    NMS_CUDA_TRY(cudaMemcpyAsync(h_qa.data(), p.d_qa, p.npix * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
+    NMS_CUDA_TRY(cudaStreamSynchronize(p.stream));
     p.oiq_counts.assign(nbins, 0);
     p.oiq_qmean.assign(nbins, 0.0);
     for (int64_t i = 0; i < p.npix; ++i) {
-        const double x = p.h_qa[i];
+        const double x = h_qa[i];
         int b = -1;
         if (x >= bin_edges[0] && x < bin_edges[nbins])
             b = (int)(std::upper_bound(bin_edges, bin_edges + nbins + 1, x) - bin_edges) - 1;

@@ -100,7 +100,6 @@ struct Plan {
     double* d_qy = nullptr; double* d_qz = nullptr;
     double* d_hy = nullptr; double* d_hz = nullptr; double* d_qa = nullptr;
     float4* d_qturn = nullptr;    // per pixel (qy/2pi hi, lo, qz/2pi hi, lo)
-    std::vector<double> h_qa;     // |q| per pixel (host copy, binning)
     // per-rotation cell data
     float4* d_cpos = nullptr;     // global positions R(x + r^k): (Yh, Yl, Zh, Zl)
     float4* d_cposl = nullptr;    // local positions R x (dilute), may alias d_cpos
@@ -214,6 +213,8 @@ __device__ __forceinline__ int find_bin(const double* __restrict__ e, int nb, do
 nms_status direct_sum_range(Plan& p, const float4* cpos, int64_t c0, int64_t c1, double* out);
 int tc_tuned_kc_cells(const Plan& p);
 int tc_tuned_items_per_sm(const Plan& p);
+cudaError_t launch_grid(const nms_qgrid& g, int64_t np, const double* d_qlist, double* qy, double* qz, double* hy,
+                        double* hz, double* qa, float4* qturn, cudaStream_t s);
 cudaError_t launch_obj_bin(const FbView& F, int n_out, const int32_t* out_obj, const Plan& p, const int32_t* bin_of,
                            int nbins, int id, double* Iobj, cudaStream_t s);
 int64_t tc_object_count(const Plan& p);

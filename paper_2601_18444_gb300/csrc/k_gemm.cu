@@ -54,7 +54,7 @@ constexpr int TC_EPI_WARPS = 16;    // 4 per TMEM lane quadrant, 32 accumulator 
 #define TC_RENORM 4                 // 0: TwoSum per chunk; G > 0: chunk partials add into lo, TwoSum every G chunks
 #endif
 #ifndef TC_DRAIN_W
-#define TC_DRAIN_W 4                // accumulator columns per tcgen05.ld in the drain (4, 8 or 16)
+#define TC_DRAIN_W 8                // accumulator columns per tcgen05.ld in the drain (4, 8 or 16)
 #endif
 constexpr float TC_SCALE = 4096.0f; // operand scale 2^12
 
@@ -930,9 +930,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     // pace the drain: four drain warps share each scheduler with
                     // the producer or MMA thread; a short yield per column
                     // group keeps the single MMA-issuing thread from waiting
-                    // behind their bursts (GEMM -3 % on the 512^2 box).  Not
+                    // behind their bursts (GEMM -4 % on the 512^2 box).  Not
                     // in the two-SM form, whose MMAs wait for both CTAs' drains.
-                    if (MODE != 2) __nanosleep(32);
+                    if (MODE != 2) __nanosleep(8 * TC_DRAIN_W);
                 }
 #if TC_RENORM > 0
                 // every TC_RENORM chunks: TwoSum(hi, lo) -> (hi, lo), so lo

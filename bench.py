@@ -43,7 +43,7 @@ TC_FLOPS_PER_TERM = 96
 # DRAM bytes (read + write) the GEMM moves per byte of phase tables it
 # consumes, from an ncu capture of one launch on the 64x64x64 box (512^2
 # detector); the box workloads scale it by their own table bytes per launch.
-TC_DRAM_PER_TABLE_BYTE = 1.317   # 8.486 GB for 6.442 GB of tables (ncu, box64)
+TC_DRAM_PER_TABLE_BYTE = 1.329   # 8.559 GB for 6.442 GB of tables (ncu, box64)
 TC_TRAFFIC_WORKLOADS = ("box", "box64")
 
 

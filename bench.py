@@ -616,7 +616,7 @@ def run_surrogate(args, rank, world, dev):
                            "exact_ms_per_curve": 1e3 * t_tr / len(params),
                            "surrogate_us_per_query": 1e3 * ms_inf / nq},
                 "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                             "frac": achieved / peak, "traffic": None, "kernel": "k_mlp_gemm (mma.sync bf16)",
+                             "frac": achieved / peak, "traffic": None, "kernel": "k_mlp_infer (fused tcgen05 bf16)",
                              "peak_source": f"{peak_src} bf16 dense"},
                 "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks}
         print(json.dumps(line), flush=True)

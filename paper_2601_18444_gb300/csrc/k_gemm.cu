@@ -39,6 +39,7 @@
 #include <vector>
 
 #include "nms_internal.h"
+#include "tc_ptx.cuh"
 
 namespace nms {
 
@@ -62,12 +63,6 @@ constexpr float TC_SCALE = 4096.0f; // operand scale 2^12
 // Tables cover a list of k-blocks; k-block kb holds the cells
 // [kb_cell0[kb], kb_cell0[kb] + kb_ncell[kb]) (kb_ncell <= 32) of the stacked
 // per-rotation cell arrays, the rest of the block is zero padding.
-__device__ __forceinline__ uint32_t swz_offset(int row, int k)
-{
-    // byte offset of element (row, k) of a 128 x 64 fp16 block, 128B swizzle
-    return (uint32_t)row * 128u + ((uint32_t)(((k >> 3) ^ (row & 7))) << 4) + (uint32_t)(k & 7) * 2u;
-}
-
 __device__ __forceinline__ float turns_reduced(float2 q, float xh, float xl)
 {
     // two-float product q' * coordinate (turns) reduced to [-1/2, 1/2]
@@ -204,59 +199,6 @@ k_tables(const float4* __restrict__ cpos, const float4* __restrict__ cw, int64_t
 }
 
 // ------------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t gtimer()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
-{
-    // the waiting thread is suspended (up to the hint, in ns) until the phase
-    // completes instead of spinning on the issue slots
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(200000u)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: gives up after limit_ns or when another role aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
-                                          volatile int* abort_flag)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = gtimer();
-    while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (gtimer() - t0 > limit_ns) return false;
-    }
-}
-
 // Teardown wait for this CTA's own asynchronous operations (bulk copies in
 // flight, issued MMAs): it does not give up when another role aborted, only
 // after TC_DRAIN_LIMIT_NS, so an aborting CTA still lets what it started land
@@ -337,62 +279,6 @@ __device__ __forceinline__ void tc_commit_mc(uint64_t* bar, uint16_t mask)
         : "memory");
 }
 
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tc_commit(uint64_t* bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                           uint32_t accumulate)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v)
-{
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr)
-                 : "memory");
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v)
-{
-    uint32_t r[4];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(taddr)
-                 : "memory");
-#pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // Packed FP32x2 arithmetic (sm_100+): two lanes of a 64-bit register, RN.
 __device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b)
 {
@@ -456,68 +342,6 @@ __device__ __forceinline__ float4 tf_add4(float4 a, float4 b)
 }
 
 __device__ __forceinline__ float f2_lane1(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
-
-template <int W>
-__device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v)
-{
-    if constexpr (W == 16) tmem_ld16(taddr, v);
-    else if constexpr (W == 8) tmem_ld8(taddr, v);
-    else tmem_ld4(taddr, v);
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// K-major, 128B-swizzled shared-memory matrix descriptor (tcgen05 format):
-// start >> 4 in [0,14), leading byte offset >> 4 in [16,30) (unused for
-// swizzled K-major), stride byte offset >> 4 in [32,46) = 1024 B between
-// 8-row groups, fixed 0b01 in [46,48), swizzle mode 2 (128B) in [61,64).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1u << 16;
-    d |= (uint64_t)(1024u >> 4) << 32;
-    d |= (uint64_t)1u << 46;
-    d |= (uint64_t)2u << 61;
-    return d;
-}
-
-// Instruction descriptor of kind::f16: D F32 (bits 4-5 = 1), A and B F16
-// (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0), N >> 3 in bits
-// 17-22, M >> 4 in bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N)
-{
-    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// tcgen05 instructions of a kernel all use one CTA-group size: CG = 2 for
-// the two-SM MMA, 1 otherwise.
-template <int CG>
-__device__ __forceinline__ void tc_alloc(uint32_t dst_smem, uint32_t ncols)
-{
-    if constexpr (CG == 2)
-        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
-                     : "memory");
-    else
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
-                     : "memory");
-}
-
-template <int CG>
-__device__ __forceinline__ void tc_relinquish()
-{
-    if constexpr (CG == 2) asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
-    else asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-template <int CG>
-__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols)
-{
-    if constexpr (CG == 2)
-        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-    else
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
 
 // arrive (once this thread's MMAs complete) on the mbarrier at this offset
 // in every CTA of mask (CG = 2: the CTA pair)

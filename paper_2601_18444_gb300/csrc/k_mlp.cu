@@ -25,6 +25,7 @@
 
 #include "nms.h"
 #include "nms_internal.h"
+#include "tc_ptx.cuh"
 
 namespace nms {
 
@@ -125,6 +126,234 @@ static cudaError_t mlp_gemm(bool ta, bool tb, int M, int N, int K, const __nv_bf
 
 // ------------------------------------------------------------------ element-wise
 __device__ __forceinline__ float silu(float z) { return z / (1.0f + expf(-z)); }
+
+// SiLU with the fast exponential and reciprocal (the result is rounded to
+// BF16, 8 significant bits)
+__device__ __forceinline__ float silu_fast(float z) { return z * __frcp_rn(1.0f + __expf(-z)); }
+
+// bf16x2 word of (a, b), a in the low half
+__device__ __forceinline__ uint32_t bf16x2(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// ------------------------------------------------------------------ fused inference
+// Inference for H = 256, n_out <= 64, n_in <= 8 on the 5th-generation tensor
+// cores, one kernel for the whole network.  A persistent CTA keeps W2 and W3
+// (BF16) in shared memory in the 128-byte swizzled K-major layout, and walks
+// tiles of 128 queries:
+//   layer 1 (threads, FP32):  H1 = bf16(silu(b1 + W1 xn))          -> smem
+//   layer 2 (tcgen05.mma):    D2 = H1 W2^T   (128 x 256, FP32 TMEM)
+//   drain:                     H2 = bf16(silu(D2 + b2))            -> smem
+//   layer 3 (tcgen05.mma):    D3 = H2 W3^T   (128 x 64, FP32 TMEM)
+//   drain:                     Y  = (D3 + b3) ystd + ymean         -> global
+// The arithmetic is that of the layer-by-layer path (BF16 operands, FP32
+// accumulation and activations); only the order of the FP32 sums differs.
+constexpr int FI_THREADS = 1024;   // 32 warps: the element-wise work needs many warps in flight
+constexpr int FI_H = 256;
+constexpr int FI_NO = 64;      // W3 rows padded with zeros
+constexpr int FI_TM = 128;     // queries per tile (the MMA's M)
+constexpr int FI_W2_BYTES = 4 * FI_H * 128;   // 4 K-blocks of 256 rows x 128 B
+constexpr int FI_W3_BYTES = 4 * FI_NO * 128;
+constexpr int FI_HB_BYTES = 4 * FI_TM * 128;  // H1 / H2 (A operand)
+constexpr int FI_SMEM = FI_W2_BYTES + FI_W3_BYTES + FI_HB_BYTES + 1024;
+
+__global__ void __launch_bounds__(FI_THREADS, 1)
+k_mlp_infer(int64_t n, int nin, int nout, const float* __restrict__ X, const float* __restrict__ xlo,
+            const float* __restrict__ xhi, const float* __restrict__ W1, const float* __restrict__ b1,
+            const __nv_bfloat16* __restrict__ W2h, const float* __restrict__ b2, const __nv_bfloat16* __restrict__ W3h,
+            const float* __restrict__ b3, const float* __restrict__ ymean, const float* __restrict__ ystd,
+            float* __restrict__ Y, int32_t* __restrict__ err, uint64_t limit_ns)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bar_mma;
+    __shared__ uint32_t s_taddr;
+    __shared__ volatile int s_abort;
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* gW2 = smem_raw + (base - raw);
+    uint8_t* gW3 = gW2 + FI_W2_BYTES;
+    uint8_t* gH = gW3 + FI_W3_BYTES;
+    const uint32_t sW2 = base, sW3 = base + FI_W2_BYTES, sH = sW3 + FI_W3_BYTES;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // W2 [256][256] and W3 [nout][256] (rows = outputs, K = inputs) into the
+    // swizzled layout: K-block kb holds k in [64 kb, 64 kb + 64) of every row
+    for (int u = tid; u < FI_H * 32; u += FI_THREADS) {
+        const int r = u >> 5, j = u & 31, k = 8 * j;
+        const uint4 v = reinterpret_cast<const uint4*>(W2h)[u];
+        *reinterpret_cast<uint4*>(gW2 + (k >> 6) * (FI_H * 128) + swz_offset(r, k & 63)) = v;
+    }
+    for (int u = tid; u < FI_NO * 32; u += FI_THREADS) {
+        const int r = u >> 5, j = u & 31, k = 8 * j;
+        const uint4 v = r < nout ? reinterpret_cast<const uint4*>(W3h)[u] : make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(gW3 + (k >> 6) * (FI_NO * 128) + swz_offset(r, k & 63)) = v;
+    }
+    if (tid == 0) {
+        mbar_init(&bar_mma, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        tc_alloc<1>(smem_u32(&s_taddr), 512);
+        tc_relinquish<1>();
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = s_taddr;
+    const uint32_t id2 = idesc_bf16_f32(FI_TM, FI_H), id3 = idesc_bf16_f32(FI_TM, FI_NO);
+    const int quad = warp & 3, cg = warp >> 2;        // TMEM lane quadrant, column group (0..7)
+    const int row = 32 * quad + lane;                 // this thread's query row in the drains
+    uint32_t phase = 0;
+    bool aborted = false;
+    const int64_t ntiles = (n + FI_TM - 1) / FI_TM;
+    for (int64_t tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
+        const int64_t q0 = tile * FI_TM;
+        // ---- layer 1: thread (row r = tid mod 128) computes the row's
+        // normalised inputs once and 32 of its hidden units, 8 at a time
+        // (the 32 lanes of a warp share each weight: broadcast loads)
+        {
+            const int r = tid & (FI_TM - 1);
+            const int64_t q = q0 + r;
+            float xn[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                xn[i] = 0.f;
+                if (i < nin && q < n) xn[i] = 2.0f * (X[q * nin + i] - xlo[i]) / (xhi[i] - xlo[i]) - 1.0f;
+            }
+            for (int j = tid >> 7; j < FI_H / 8; j += FI_THREADS / FI_TM) {
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float z[2];
+#pragma unroll
+                    for (int t = 0; t < 2; ++t) {
+                        const int h = 8 * j + 2 * e + t;
+                        float acc = b1[h];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            if (i < nin) acc = fmaf(W1[h * nin + i], xn[i], acc);
+                        z[t] = silu_fast(acc);
+                    }
+                    w[e] = bf16x2(z[0], z[1]);
+                }
+                const int k = 8 * j;
+                *reinterpret_cast<uint4*>(gH + (k >> 6) * (FI_TM * 128) + swz_offset(r, k & 63)) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        // ---- layer 2 on the tensor cores
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kb = 0; kb < 4; ++kb)
+#pragma unroll
+                for (int k16 = 0; k16 < 4; ++k16)
+                    tc_mma_f16(taddr, sw128_desc(sH + kb * (FI_TM * 128)) + 2 * k16,
+                               sw128_desc(sW2 + kb * (FI_H * 128)) + 2 * k16, id2, (kb | k16) ? 1u : 0u);
+            tc_commit(&bar_mma);
+        }
+        {
+            const bool ok = mbar_wait(&bar_mma, phase, limit_ns, &s_abort);
+            if (__syncthreads_or(!ok)) {
+                aborted = true;
+                break;
+            }
+        }
+        phase ^= 1u;
+        tc_fence_after();
+        // ---- drain D2: bias, SiLU, BF16 into the A buffer (layer 2's MMAs
+        // have completed, so the buffer is free); this warp's 32 columns
+#pragma unroll
+        for (int c16 = 0; c16 < 2; ++c16) {
+            float v[16];
+            const int c0 = 32 * cg + 16 * c16;
+            tmem_ld16(taddr + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0, v);
+            tmem_wait_ld();
+            float bb[16];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float4 b4 = reinterpret_cast<const float4*>(b2 + c0)[e];
+                bb[4 * e] = b4.x;
+                bb[4 * e + 1] = b4.y;
+                bb[4 * e + 2] = b4.z;
+                bb[4 * e + 3] = b4.w;
+            }
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int u = 8 * half + 2 * e;
+                    w[e] = bf16x2(silu_fast(v[u] + bb[u]), silu_fast(v[u + 1] + bb[u + 1]));
+                }
+                const int k = c0 + 8 * half;
+                *reinterpret_cast<uint4*>(gH + (k >> 6) * (FI_TM * 128) + swz_offset(row, k & 63)) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        // ---- layer 3 on the tensor cores (TMEM columns 256..319)
+        if (tid == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int kb = 0; kb < 4; ++kb)
+#pragma unroll
+                for (int k16 = 0; k16 < 4; ++k16)
+                    tc_mma_f16(taddr + 256u, sw128_desc(sH + kb * (FI_TM * 128)) + 2 * k16,
+                               sw128_desc(sW3 + kb * (FI_NO * 128)) + 2 * k16, id3, (kb | k16) ? 1u : 0u);
+            tc_commit(&bar_mma);
+        }
+        {
+            const bool ok = mbar_wait(&bar_mma, phase, limit_ns, &s_abort);
+            if (__syncthreads_or(!ok)) {
+                aborted = true;
+                break;
+            }
+        }
+        phase ^= 1u;
+        tc_fence_after();
+        // ---- drain D3: 8 columns per warp
+        {
+            float v[8];
+            const int c0 = 8 * cg;
+            tmem_ld8(taddr + ((uint32_t)(32 * quad) << 16) + 256u + (uint32_t)c0, v);
+            tmem_wait_ld();
+            const int64_t q = q0 + row;
+            if (q < n) {
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const int c = c0 + t;
+                    if (c < nout) Y[q * nout + c] = (v[t] + b3[c]) * ystd[c] + ymean[c];
+                }
+            }
+        }
+        // TMEM read and the A buffer free before the next tile
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (aborted) {
+        if (tid == 0) atomicExch(err, 1);
+        // let any MMA still in flight finish (bounded) before TMEM is freed
+        if (tid == 0) {
+            const uint64_t t0 = gtimer();
+            while (!mbar_try_wait(&bar_mma, phase) && gtimer() - t0 < 1000000000ull) {
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tc_dealloc<1>(taddr, 512);
+}
 __device__ __forceinline__ float silu_grad(float z)
 {
     const float s = 1.0f / (1.0f + expf(-z));
@@ -306,6 +535,7 @@ struct nms_surrogate_s {
     int32_t* d_perm = nullptr;
     int64_t perm_cap = 0;
     double* d_loss = nullptr;
+    int32_t* d_err = nullptr;  // fused inference: a bounded wait gave up
     bool stats_set = false;
 };
 
@@ -456,7 +686,7 @@ nms_status nms_surrogate_create(nms_surrogate_t* out, int32_t n_in, int32_t n_hi
         cudaMalloc(&s->d_m, s->nparam * 4) || cudaMalloc(&s->d_v, s->nparam * 4) ||
         cudaMalloc(&s->d_W2h, (size_t)n_hidden * n_hidden * 2) || cudaMalloc(&s->d_W3h, (size_t)n_out * n_hidden * 2) ||
         cudaMalloc(&s->d_xlo, n_in * 4) || cudaMalloc(&s->d_xhi, n_in * 4) || cudaMalloc(&s->d_ymean, n_out * 4) ||
-        cudaMalloc(&s->d_ystd, n_out * 4) || cudaMalloc(&s->d_loss, 8)) {
+        cudaMalloc(&s->d_ystd, n_out * 4) || cudaMalloc(&s->d_loss, 8) || cudaMalloc(&s->d_err, 4)) {
         cudaGetLastError();
         set_error("surrogate: device allocation failed");
         return bail(NMS_ERR_OUT_OF_MEMORY);
@@ -566,6 +796,30 @@ nms_status nms_surrogate_infer(nms_surrogate_t s, const float* X, int64_t n, flo
 {
     set_error("");
     if (!s || !X || !Y || n < 0) return NMS_ERR_INVALID_ARG;
+    if (n == 0) return NMS_OK;
+    if (s->H == FI_H && s->nout <= FI_NO && s->nin <= 8) {
+        // the whole network in one tensor-core kernel
+        static bool attr = false;
+        if (!attr) {
+            NMS_CUDA_TRY(cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, FI_SMEM));
+            attr = true;
+        }
+        NMS_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, 4, s->stream));
+        const int64_t tiles = (n + FI_TM - 1) / FI_TM;
+        const int grid = (int)std::min<int64_t>(tiles, device_sm_count());
+        k_mlp_infer<<<grid, FI_THREADS, FI_SMEM, s->stream>>>(n, s->nin, s->nout, X, s->d_xlo, s->d_xhi, W1p(s),
+                                                              b1p(s), s->d_W2h, b2p(s), s->d_W3h, b3p(s),
+                                                              s->d_ymean, s->d_ystd, Y, s->d_err, 4000000000ull);
+        NMS_CUDA_TRY(cudaGetLastError());
+        int32_t herr = 0;
+        NMS_CUDA_TRY(cudaMemcpyAsync(&herr, s->d_err, 4, cudaMemcpyDeviceToHost, s->stream));
+        NMS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        if (herr) {
+            set_error("surrogate inference: a bounded device wait gave up");
+            return NMS_ERR_TIMEOUT;
+        }
+        return NMS_OK;
+    }
     const int B = 65536;
     nms_status st = ensure_batch(s, (int)std::min<int64_t>(B, std::max<int64_t>(n, 1)));
     if (st) return st;
@@ -680,7 +934,7 @@ nms_status nms_surrogate_destroy(nms_surrogate_t s)
     cudaStreamSynchronize(s->stream);
     void* bufs[] = {s->d_w, s->d_g, s->d_m, s->d_v, s->d_W2h, s->d_W3h, s->d_xlo, s->d_xhi, s->d_ymean, s->d_ystd,
                     s->d_Xn, s->d_Z1, s->d_Z2, s->d_Y, s->d_C, s->d_dYf, s->d_dH, s->d_dZf, s->d_H1, s->d_H2,
-                    s->d_dY, s->d_dZ, s->d_perm, s->d_loss};
+                    s->d_dY, s->d_dZ, s->d_perm, s->d_loss, s->d_err};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete s;

@@ -3,9 +3,8 @@
 // trained on data produced by the batched transform, with hand-written BF16
 // kernels (FP32 accumulation, FP32 master weights, Adam).
 //
-// The paper has no learned component; this follows the surrogate of the
-// build's scope: the exact transform generates the targets and judges the
-// network's error.
+// The paper has no learned component; here the exact transform generates
+// the training targets and is the reference for the network's error.
 //
 // Kernels: a BF16 tensor-core GEMM (mma.sync m16n8k16, FP32 accumulate) with
 // the transposes the forward and backward passes need, plus element-wise

@@ -6,10 +6,12 @@
 // The paper has no learned component; here the exact transform generates
 // the training targets and is the reference for the network's error.
 //
-// Kernels: a BF16 tensor-core GEMM (mma.sync m16n8k16, FP32 accumulate) with
-// the transposes the forward and backward passes need, plus element-wise
-// SiLU / SiLU', MSE gradient, column sums for bias gradients, and Adam.
-// The MLP GEMMs are small (B x 256 x 256); this path is not the Fourier sum.
+// Kernels: for training, a BF16 tensor-core GEMM (mma.sync m16n8k16, FP32
+// accumulate) with the transposes the forward and backward passes need, plus
+// element-wise SiLU / SiLU', MSE gradient, column sums for bias gradients,
+// and Adam (the training GEMMs are small, B x 256 x 256); for inference, one
+// fused tcgen05 kernel that runs the whole network per tile of 128 queries
+// (k_mlp_infer).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>

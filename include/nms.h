@@ -98,8 +98,9 @@ typedef struct {
     int32_t split_k;         /* tensor path: work items per SM of a GEMM launch
                                 (how finely the cells of each output are split
                                 over CTAs); 0 -> 8, or the autotuned value      */
-    int64_t max_spin;        /* bounded device waits: poll iterations before the
-                                kernel gives up with NMS_ERR_TIMEOUT; 0 -> default */
+    int64_t max_spin;        /* bounded device waits: microseconds (%globaltimer)
+                                a wait lasts before the kernel gives up with
+                                NMS_ERR_TIMEOUT; 0 -> 4,000,000 (4 s)          */
     int64_t workspace_bytes; /* cap on the tensor-path phase-table workspace
                                 (cells beyond it are processed in chunks);
                                 0 -> min(free / 3, 8 GiB)                      */

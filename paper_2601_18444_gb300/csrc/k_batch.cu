@@ -17,6 +17,7 @@
 #include <algorithm>
 
 #include "nms_internal.h"
+#include "tc_ptx.cuh"
 
 namespace nms {
 
@@ -225,68 +226,89 @@ cudaError_t launch_tf_to_f64(const FbView& V, int64_t o, double* dst, cudaStream
 //   Ftot[out_rot[o]][c][p]    += F_o[c][p] exp(-i (q_y cy_o + q_z cz_o))
 // The shift factor of pixel (a, b) is the product of the output's factors
 // along q_y and q_z (k_shift_factors).  One thread per pixel; q_y runs
-// fastest, so a warp reads contiguous channel rows of F_b.  Outputs are
-// taken in pairs: the pair's two terms are added in FP32 before they join
-// the two-float sums (one rounding of a two-term sum per pair), and the next
-// pair's values are loaded while the current one is processed.  Outputs are
-// ordered by rotation; the shifted sums are flushed to FP64 at each change
-// of rotation (a pair that straddles one is taken one output at a time).
-struct DsIn {
-    float2 f[4];
-    float2 ey, ez;
-};
+// fastest, so a warp reads contiguous channel rows of F_b.
+//
+// Each thread stages its own inputs of the next DS_DEPTH - 1 outputs (32 B of
+// F, 16 B of shift factors) in shared memory with cp.async, so the loads in
+// flight hold no registers and no thread waits on another.  The terms of
+// DS_RUN consecutive outputs are accumulated by FMA into FP32 partial sums,
+// which are then added into the two-float (hi, lo) totals: one TwoSum per
+// run instead of one per output.  A run's FP32 sum of n terms errs by at most
+// (n - 1) 2^-24 times the sum of their magnitudes.  Outputs are ordered by
+// rotation; the shifted sums are flushed to FP64 at each change of rotation.
+constexpr int DS_DEPTH = 6;   // outputs staged per thread (ring slots)
+constexpr int DS_RUN = 8;     // outputs per FP32 partial sum
 
-__device__ __forceinline__ void ds_load(const FbView& V, const float2* __restrict__ eyz, int ne, int o, int qa, int qb,
-                                        DsIn& d)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
 {
-    const float2* src = V.hi + V.idx(o, qa, qb);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) d.f[c] = src[c];
-    d.ey = eyz[(int64_t)o * ne + qa];
-    d.ez = eyz[(int64_t)o * ne + V.ny + qb];
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
 }
 
-// the 16 Hermitian terms and 8 shifted terms of one output
-__device__ __forceinline__ void ds_terms(const DsIn& d, float* g, float* t)
+__device__ __forceinline__ void cp_async8(void* dst, const void* src)
 {
-    const float2* f = d.f;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) g[i] = fmaf(f[i].x, f[i].x, f[i].y * f[i].y);
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = i + 1; j < 4; ++j) {
-            const int k = pair_idx(i, j);
-            g[4 + 2 * k] = fmaf(f[i].x, f[j].x, f[i].y * f[j].y);
-            g[5 + 2 * k] = fmaf(f[i].y, f[j].x, -f[i].x * f[j].y);
-        }
-    const float cs = fmaf(d.ey.x, d.ez.x, -d.ey.y * d.ez.y);
-    const float sn = fmaf(d.ey.y, d.ez.x, d.ey.x * d.ez.y);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        t[2 * c] = fmaf(f[c].x, cs, f[c].y * sn);
-        t[2 * c + 1] = fmaf(f[c].y, cs, -f[c].x * sn);
-    }
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 __global__ void __launch_bounds__(128, 4)   // 4 blocks per SM: one wave for a 256 x 256 detector
 k_dilute_shift_batch(FbView V, int n_out, const float2* __restrict__ eyz, const int32_t* __restrict__ out_rot,
                      double* __restrict__ Gdil, double2* __restrict__ Ftot, int64_t tstride2)
 {
+    __shared__ float4 ring[DS_DEPTH][3][128];   // per slot: channels 0-1, channels 2-3, (e_y, e_z)
     const int64_t npix = (int64_t)V.ny * V.nz;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= npix || n_out <= 0) return;
+    if (npix <= 0 || n_out <= 0) return;
+    // threads past the last pixel compute on the last one and store nothing,
+    // so every lane of a warp takes part in the shuffles below
+    const int64_t tid0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = tid0 < npix;
+    const int64_t tid = act ? tid0 : npix - 1;
+    const int lt = threadIdx.x;
     const int qa = (int)(tid % V.ny), qb = (int)(tid / V.ny);
     const int64_t p = (int64_t)qa * V.nz + qb;
     const int ne = V.ny + V.nz;
-    float gh[16], gl[16], th[8], tl[8];
+    const float2* fsrc = V.hi + V.idx(0, qa, qb);   // 16-byte aligned: channel groups of 4 complex FP32
+    const float2* eysrc = eyz + qa;
+    const float2* ezsrc = eyz + V.ny + qb;
+    auto stage = [&](int o) {
+        if (o < n_out) {
+            const int sl = o % DS_DEPTH;
+            const float2* f = fsrc + (int64_t)o * V.ostride2;
+            cp_async16(&ring[sl][0][lt], f);
+            cp_async16(&ring[sl][1][lt], f + 2);
+            float2* e = reinterpret_cast<float2*>(&ring[sl][2][lt]);
+            cp_async8(e, eysrc + (int64_t)o * ne);
+            cp_async8(e + 1, ezsrc + (int64_t)o * ne);
+        }
+        cp_async_commit();   // one group per output, empty past the end
+    };
 #pragma unroll
-    for (int k = 0; k < 16; ++k) { gh[k] = 0.f; gl[k] = 0.f; }
+    for (int o = 0; o < DS_DEPTH - 1; ++o) stage(o);
+
+    float gh[16], gl[16], th[8], tl[8], rg[16], rt[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) { th[k] = 0.f; tl[k] = 0.f; }
+    for (int k = 0; k < 16; ++k) { gh[k] = 0.f; gl[k] = 0.f; rg[k] = 0.f; }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { th[k] = 0.f; tl[k] = 0.f; rt[k] = 0.f; }
+    auto fold_t = [&]() {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { ts_acc(th[k], tl[k], rt[k]); rt[k] = 0.f; }
+    };
     auto flush = [&](int rot) {
+        fold_t();
+        if (act)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+            for (int c = 0; c < 4; ++c) {
             double2* t = Ftot + (int64_t)rot * tstride2 + (int64_t)c * npix + p;
             double2 v = *t;
             v.x += (double)th[2 * c] + (double)tl[2 * c];
@@ -296,60 +318,244 @@ k_dilute_shift_batch(FbView V, int n_out, const float2* __restrict__ eyz, const 
 #pragma unroll
         for (int k = 0; k < 8; ++k) { th[k] = 0.f; tl[k] = 0.f; }
     };
+    // rotation of the outputs, 32 at a time: lane l holds out_rot[o32 + l], and
+    // bit l of chg says that output o32 + l starts a new rotation
+    const int lane = lt & 31;
     int cur = out_rot[0];
-    DsIn n0, n1;
-    ds_load(V, eyz, ne, 0, qa, qb, n0);
-    ds_load(V, eyz, ne, min(1, n_out - 1), qa, qb, n1);
-    for (int o = 0; o < n_out; o += 2) {
-        const DsIn d0 = n0, d1 = n1;
-        const bool has1 = o + 1 < n_out;
-        if (o + 2 < n_out) {
-            ds_load(V, eyz, ne, o + 2, qa, qb, n0);
-            ds_load(V, eyz, ne, min(o + 3, n_out - 1), qa, qb, n1);
+    int rw = 0;
+    unsigned chg = 0;
+    int run = 0;
+    for (int o = 0; o < n_out; ++o) {
+        if ((o & 31) == 0) {
+            rw = out_rot[min(o + lane, n_out - 1)];
+            const int prev = __shfl_up_sync(0xffffffffu, rw, 1);
+            chg = __ballot_sync(0xffffffffu, lane == 0 ? rw != cur : rw != prev);
         }
-        const int r0 = out_rot[o];
-        const int r1 = has1 ? out_rot[o + 1] : r0;
-        float g0[16], t0[8], g1[16], t1[8];
-        ds_terms(d0, g0, t0);
-        ds_terms(d1, g1, t1);
-        if (!has1) {
-#pragma unroll
-            for (int k = 0; k < 16; ++k) g1[k] = 0.f;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) t1[k] = 0.f;
+        stage(o + DS_DEPTH - 1);
+        cp_async_wait<DS_DEPTH - 1>();   // this thread's copies of output o have landed
+        const int sl = o % DS_DEPTH;
+        const float4 c01 = ring[sl][0][lt], c23 = ring[sl][1][lt], e = ring[sl][2][lt];
+        const float2 f[4] = {make_float2(c01.x, c01.y), make_float2(c01.z, c01.w), make_float2(c23.x, c23.y),
+                             make_float2(c23.z, c23.w)};
+        if ((chg >> (o & 31)) & 1u) {
+            flush(cur);
+            cur = __shfl_sync(0xffffffffu, rw, o & 31);
         }
 #pragma unroll
-        for (int k = 0; k < 16; ++k) ts_acc(gh[k], gl[k], g0[k] + g1[k]);
-        if (r0 == cur && r1 == cur) {
+        for (int i = 0; i < 4; ++i) rg[i] = fmaf(f[i].x, f[i].x, fmaf(f[i].y, f[i].y, rg[i]));
 #pragma unroll
-            for (int k = 0; k < 8; ++k) ts_acc(th[k], tl[k], t0[k] + t1[k]);
-        } else {
-            if (r0 != cur) {
-                flush(cur);
-                cur = r0;
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = i + 1; j < 4; ++j) {
+                const int k = pair_idx(i, j);
+                rg[4 + 2 * k] = fmaf(f[i].x, f[j].x, fmaf(f[i].y, f[j].y, rg[4 + 2 * k]));
+                rg[5 + 2 * k] = fmaf(f[i].y, f[j].x, fmaf(-f[i].x, f[j].y, rg[5 + 2 * k]));
+            }
+        const float cs = fmaf(e.x, e.z, -e.y * e.w);   // e_y e_z, complex
+        const float sn = fmaf(e.y, e.z, e.x * e.w);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            rt[2 * c] = fmaf(f[c].x, cs, fmaf(f[c].y, sn, rt[2 * c]));
+            rt[2 * c + 1] = fmaf(f[c].y, cs, fmaf(-f[c].x, sn, rt[2 * c + 1]));
+        }
+        if (++run == DS_RUN) {
+            run = 0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) { ts_acc(gh[k], gl[k], rg[k]); rg[k] = 0.f; }
+            fold_t();
+        }
+    }
+    cp_async_wait<0>();
+    flush(cur);
+    if (act)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) Gdil[(int64_t)k * npix + p] += ((double)gh[k] + (double)gl[k]) + (double)rg[k];
+}
+
+// The same pass for detectors whose q_y rows are whole multiples of 128
+// pixels and plans of one weight set (4 channels): the 128 pixels of a block
+// then share q_z, and their 4 channels of output o are one contiguous 4 KB
+// run of F_b.  One thread copies that run, the block's 128 factors e_y and
+// the (16-byte aligned) pair holding its e_z into a ring slot with bulk
+// copies (cp.async.bulk, completion counted on the slot's "full" mbarrier),
+// so no thread spends load instructions on F.  Each warp releases a slot on
+// its "empty" mbarrier after reading it; the copying thread refills the slot
+// of output c with output c + DB_DEPTH once every warp has released c, which
+// it checks DB_LAG outputs later so that it does not wait on slower warps.
+// Every wait is bounded by limit_ns; on expiry the block sets err, stops, and
+// the copying thread waits (bounded) for the copies it has in flight.
+constexpr int DB_DEPTH = 8;
+constexpr int DB_LAG = 2;
+constexpr int DB_F = 128 * 32;              // F bytes per slot
+constexpr int DB_EY = 128 * 8;              // e_y bytes per slot
+constexpr int DB_SLOT = DB_F + DB_EY + 16;  // + the e_z pair
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(128, 4)
+k_dilute_shift_bulk(FbView V, int n_out, const float2* __restrict__ eyz, const int32_t* __restrict__ out_rot,
+                    double* __restrict__ Gdil, double2* __restrict__ Ftot, int64_t tstride2, int32_t* err,
+                    uint64_t limit_ns)
+{
+    __shared__ __align__(128) unsigned char ring[DB_DEPTH][DB_SLOT];
+    __shared__ __align__(8) uint64_t full[DB_DEPTH], empty[DB_DEPTH];
+    __shared__ volatile int abort_flag;
+    const int64_t npix = (int64_t)V.ny * V.nz;
+    const int lt = threadIdx.x, lane = lt & 31;
+    const int64_t t0 = (int64_t)blockIdx.x * 128;
+    const int qa = (int)(t0 % V.ny) + lt, qb = (int)(t0 / V.ny);   // one q_z row per block
+    const int64_t p = (int64_t)qa * V.nz + qb;
+    const int ne = V.ny + V.nz;
+    const float2* fsrc = V.hi + V.idx(0, qa - lt, qb);
+    const float2* eysrc = eyz + (qa - lt);
+    const float2* ezsrc = eyz + V.ny + (qb & ~1);
+    if (lt == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < DB_DEPTH; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 4);
+        }
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+    auto issue = [&](int o) {   // thread 0: output o into slot o % DB_DEPTH
+        const int sl = o % DB_DEPTH;
+        mbar_arrive_expect_tx(&full[sl], DB_SLOT);
+        const uint32_t d = smem_u32(ring[sl]);
+        bulk_copy(d, fsrc + (int64_t)o * V.ostride2, DB_F, &full[sl]);
+        bulk_copy(d + DB_F, eysrc + (int64_t)o * ne, DB_EY, &full[sl]);
+        bulk_copy(d + DB_F + DB_EY, ezsrc + (int64_t)o * ne, 16, &full[sl]);
+    };
+    int issued = 0;   // thread 0: outputs [0, issued) have been copied or are in flight
+    if (lt == 0)
+        for (; issued < min(DB_DEPTH, n_out); ++issued) issue(issued);
+
+    float gh[16], gl[16], th[8], tl[8], rg[16], rt[8];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) { gh[k] = 0.f; gl[k] = 0.f; rg[k] = 0.f; }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { th[k] = 0.f; tl[k] = 0.f; rt[k] = 0.f; }
+    auto fold_t = [&]() {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) { ts_acc(th[k], tl[k], rt[k]); rt[k] = 0.f; }
+    };
+    auto flush = [&](int rot) {
+        fold_t();
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+                double2* t = Ftot + (int64_t)rot * tstride2 + (int64_t)c * npix + p;
+                double2 v = *t;
+                v.x += (double)th[2 * c] + (double)tl[2 * c];
+                v.y += (double)th[2 * c + 1] + (double)tl[2 * c + 1];
+                *t = v;
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) ts_acc(th[k], tl[k], t0[k]);
-            if (r1 != cur) {
-                flush(cur);
-                cur = r1;
-            }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) ts_acc(th[k], tl[k], t1[k]);
+        for (int k = 0; k < 8; ++k) { th[k] = 0.f; tl[k] = 0.f; }
+    };
+    int cur = out_rot[0];
+    int rw = 0;
+    unsigned chg = 0;
+    int run = 0;
+    int o = 0;
+    bool fail = false;
+    for (; o < n_out; ++o) {
+        if ((o & 31) == 0) {
+            rw = out_rot[min(o + lane, n_out - 1)];
+            const int prev = __shfl_up_sync(0xffffffffu, rw, 1);
+            chg = __ballot_sync(0xffffffffu, lane == 0 ? rw != cur : rw != prev);
         }
+        const int sl = o % DB_DEPTH;
+        const bool got = mbar_wait(&full[sl], (uint32_t)(o / DB_DEPTH) & 1u, limit_ns, &abort_flag);
+        if (!__all_sync(0xffffffffu, got)) {   // a warp leaves the loop as a whole
+            fail = true;
+            break;
+        }
+        const unsigned char* slot = ring[sl];
+        const float4 c01 = reinterpret_cast<const float4*>(slot)[2 * lt];
+        const float4 c23 = reinterpret_cast<const float4*>(slot)[2 * lt + 1];
+        const float2 ey = reinterpret_cast<const float2*>(slot + DB_F)[lt];
+        const float2 ez = reinterpret_cast<const float2*>(slot + DB_F + DB_EY)[qb & 1];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[sl]);
+        const float2 f[4] = {make_float2(c01.x, c01.y), make_float2(c01.z, c01.w), make_float2(c23.x, c23.y),
+                             make_float2(c23.z, c23.w)};
+        if ((chg >> (o & 31)) & 1u) {
+            flush(cur);
+            cur = __shfl_sync(0xffffffffu, rw, o & 31);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) rg[i] = fmaf(f[i].x, f[i].x, fmaf(f[i].y, f[i].y, rg[i]));
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = i + 1; j < 4; ++j) {
+                const int k = pair_idx(i, j);
+                rg[4 + 2 * k] = fmaf(f[i].x, f[j].x, fmaf(f[i].y, f[j].y, rg[4 + 2 * k]));
+                rg[5 + 2 * k] = fmaf(f[i].y, f[j].x, fmaf(-f[i].x, f[j].y, rg[5 + 2 * k]));
+            }
+        const float cs = fmaf(ey.x, ez.x, -ey.y * ez.y);
+        const float sn = fmaf(ey.y, ez.x, ey.x * ez.y);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            rt[2 * c] = fmaf(f[c].x, cs, fmaf(f[c].y, sn, rt[2 * c]));
+            rt[2 * c + 1] = fmaf(f[c].y, cs, fmaf(-f[c].x, sn, rt[2 * c + 1]));
+        }
+        if (++run == DS_RUN) {
+            run = 0;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) { ts_acc(gh[k], gl[k], rg[k]); rg[k] = 0.f; }
+            fold_t();
+        }
+        bool stalled = false;
+        if (lt == 0) {   // refill the slot of output o - DB_LAG once every warp has released it
+            const int c = o - DB_LAG;
+            if (c >= 0 && c + DB_DEPTH < n_out) {
+                if (mbar_wait(&empty[c % DB_DEPTH], (uint32_t)(c / DB_DEPTH) & 1u, limit_ns, &abort_flag))
+                    issue(issued++);
+                else
+                    stalled = true;
+            }
+        }
+        if (__any_sync(0xffffffffu, stalled)) {
+            fail = true;
+            ++o;   // output o was read
+            break;
+        }
+    }
+    if (fail) {
+        abort_flag = 1;
+        atomicExch(err, 8);
+        if (lt == 0) {   // let this block's copies land before its shared memory is released
+            volatile int never = 0;
+            for (int x = o; x < issued; ++x)
+                mbar_wait(&full[x % DB_DEPTH], (uint32_t)(x / DB_DEPTH) & 1u, 1000000000ull, &never);
+        }
+        return;
     }
     flush(cur);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) Gdil[(int64_t)k * npix + p] += (double)gh[k] + (double)gl[k];
+    for (int k = 0; k < 16; ++k) Gdil[(int64_t)k * npix + p] += ((double)gh[k] + (double)gl[k]) + (double)rg[k];
 }
 
 cudaError_t launch_dilute_shift_batch(const FbView& V, int n_out, const float2* eyz, const int32_t* out_rot,
-                                      double* Gdil, double* Ftot, int64_t tstride, cudaStream_t s)
+                                      double* Gdil, double* Ftot, int64_t tstride, int32_t* err, uint64_t limit_ns,
+                                      cudaStream_t s)
 {
     if (n_out <= 0) return cudaSuccess;
     const int64_t npix = (int64_t)V.ny * V.nz;
-    k_dilute_shift_batch<<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(V, n_out, eyz, out_rot, Gdil,
-                                                                        reinterpret_cast<double2*>(Ftot), tstride / 2);
+    const bool bulk = V.nch == 4 && V.ny % 128 == 0 && V.nz % 2 == 0 &&
+                      (reinterpret_cast<uintptr_t>(V.hi) & 15) == 0 && (reinterpret_cast<uintptr_t>(eyz) & 15) == 0;
+    if (bulk)
+        k_dilute_shift_bulk<<<(unsigned)(npix / 128), 128, 0, s>>>(
+            V, n_out, eyz, out_rot, Gdil, reinterpret_cast<double2*>(Ftot), tstride / 2, err, limit_ns);
+    else
+        k_dilute_shift_batch<<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(
+            V, n_out, eyz, out_rot, Gdil, reinterpret_cast<double2*>(Ftot), tstride / 2);
     return cudaGetLastError();
 }
 

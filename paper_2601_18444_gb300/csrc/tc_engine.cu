@@ -51,7 +51,8 @@ cudaError_t launch_gacc_batch(const FbView& V, int n_out, double* G, cudaStream_
 cudaError_t launch_gacc_totals(const double* T, int n_out, int64_t ostride, int64_t npix, double* G, cudaStream_t s);
 cudaError_t launch_tf_to_f64(const FbView& V, int64_t o, double* dst, cudaStream_t s);
 cudaError_t launch_dilute_shift_batch(const FbView& V, int n_out, const float2* eyz, const int32_t* out_rot,
-                                      double* Gdil, double* Ftot, int64_t tstride, cudaStream_t s);
+                                      double* Gdil, double* Ftot, int64_t tstride, int32_t* err, uint64_t limit_ns,
+                                      cudaStream_t s);
 cudaError_t launch_shift_factors(int n_out, const float4* cyz, const float2* qy, int ny, const float2* qz, int nz,
                                  float2* eyz, cudaStream_t s);
 
@@ -791,7 +792,8 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
                 if (t.objects) {
                     NMS_CUDA_TRY(launch_dilute_shift_batch(V, ob.n_out, t.d_eyz, S.d_out_rot + ob.out0,
                                                            p.d_Gdil + (size_t)st * 16 * np,
-                                                           t.d_Ftot_b + (size_t)st * F4, (int64_t)nS * F4, s));
+                                                           t.d_Ftot_b + (size_t)st * F4, (int64_t)nS * F4, p.d_err,
+                                                           limit, s));
                     ++nl;
                 } else {
                     NMS_CUDA_TRY(launch_gacc_batch(V, ob.n_out, p.d_Gtot + (size_t)st * 16 * np, s));

@@ -184,6 +184,40 @@ def test_tc_mixed_object_sizes_direct_and_split_outputs():
             assert np.max(np.abs(nms.nms_response(plan, k, part) - acc[k][i])) <= tol, (k, part)
 
 
+@pytest.mark.parametrize("n_obj, n_rot", [(3, 1), (300, 2)])
+def test_tc_dilute_pass_whole_q_y_rows(n_obj, n_rot):
+    # q_y rows of 256 pixels (two blocks of 128) and an even q_z count: the
+    # dilute/shift pass stages each block's slice of F_b with bulk copies.
+    # Fewer outputs than ring slots; several hundred outputs whose rotation
+    # changes inside a batch
+    if n_obj == 3:
+        f = I.small_random_field(900, seed=41, extent=5.0, n_objects=3)
+    else:
+        f = I.sphere_ensemble(n_spheres=n_obj, median=2.5, sigma=0.35, clip=(1.5, 4.0), a=1.0, cube=200.0, seed=43)
+    kw = dict(kind="cartesian", n0=256, n1=14, lo0=-1.5, hi0=1.5, lo1=-1.2, hi1=1.4)
+    Rs = I.random_rotations(n_rot, seed=44)
+    plan = run(f, kw, rot=Rs, want_dilute=1)
+    g = og(kw)
+    ids = ("N", "M", "SF", "UNPOL")
+    acc = {k: [0, 0, 0] for k in ids}
+    for R in Rs:
+        parts = S.response_parts(f, R, g, ids=ids)
+        for k in ids:
+            for i in range(3):
+                acc[k][i] = acc[k][i] + parts[k][i] / len(Rs)
+    tol = 2 * resp_tol(f, rotations=Rs)
+    # the dilute part is bounded by the sum over objects of each one's (sum |w|)^2
+    tol_dil = 0.0
+    for R in Rs:
+        wk = [np.abs(S.cell_weights(f.vol[a:b], f.nuc[a:b], f.mag[a:b], R)).sum(1)
+              for a, b in zip(f.offsets[:-1], f.offsets[1:])]
+        tol_dil = max(tol_dil, 4e-6 * sum((w[0] + w[1] + w[2] + w[3]) ** 2 for w in wk))
+    for k in ids:
+        assert np.max(np.abs(nms.nms_response(plan, k, nms.PART_TOTAL) - acc[k][0])) <= tol, k
+        assert np.max(np.abs(nms.nms_response(plan, k, nms.PART_DILUTE) - acc[k][1])) <= tol_dil, k
+        assert np.max(np.abs(nms.nms_response(plan, k, nms.PART_INTERFERENCE) - acc[k][2])) <= tol + tol_dil, k
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_tc_gemm_forms_agree_with_oracle(mode, monkeypatch):
     # the three GEMM forms (one CTA; CTA pairs sharing A; the two-SM MMA over

@@ -375,20 +375,18 @@ k_dilute_shift_batch(FbView V, int n_out, const float2* __restrict__ eyz, const 
 // The same pass for detectors whose q_y rows are whole multiples of 128
 // pixels and plans of one weight set (4 channels): the 128 pixels of a block
 // then share q_z, and their 4 channels of output o are one contiguous 4 KB
-// run of F_b.  One thread copies that run, the block's 128 factors e_y and
-// the (16-byte aligned) pair holding its e_z into a ring slot with bulk
-// copies (cp.async.bulk, completion counted on the slot's "full" mbarrier),
-// so no thread spends load instructions on F.  Each warp releases a slot on
-// its "empty" mbarrier after reading it; the copying thread refills the slot
-// of output c with output c + DB_DEPTH once every warp has released c, which
-// it checks DB_LAG outputs later so that it does not wait on slower warps.
+// run of F_b.  One thread copies that run into a ring slot with a bulk copy
+// (cp.async.bulk, completion counted on the slot's "full" mbarrier), so no
+// thread spends load instructions on F; each thread loads its own shift
+// factors (L2-resident) two outputs ahead.  Each warp releases a slot on its
+// "empty" mbarrier after reading it; the copying thread refills the slot of
+// output c with output c + DB_DEPTH once every warp has released c, which it
+// checks DB_LAG outputs later so that it does not wait on slower warps.
 // Every wait is bounded by limit_ns; on expiry the block sets err, stops, and
 // the copying thread waits (bounded) for the copies it has in flight.
-constexpr int DB_DEPTH = 8;
+constexpr int DB_DEPTH = 10;
 constexpr int DB_LAG = 2;
-constexpr int DB_F = 128 * 32;              // F bytes per slot
-constexpr int DB_EY = 128 * 8;              // e_y bytes per slot
-constexpr int DB_SLOT = DB_F + DB_EY + 16;  // + the e_z pair
+constexpr int DB_SLOT = 128 * 32;   // F bytes per slot
 
 __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar)
 {
@@ -412,8 +410,8 @@ k_dilute_shift_bulk(FbView V, int n_out, const float2* __restrict__ eyz, const i
     const int64_t p = (int64_t)qa * V.nz + qb;
     const int ne = V.ny + V.nz;
     const float2* fsrc = V.hi + V.idx(0, qa - lt, qb);
-    const float2* eysrc = eyz + (qa - lt);
-    const float2* ezsrc = eyz + V.ny + (qb & ~1);
+    const float2* eysrc = eyz + qa;
+    const float2* ezsrc = eyz + V.ny + qb;
     if (lt == 0) {
         abort_flag = 0;
         for (int s = 0; s < DB_DEPTH; ++s) {
@@ -426,11 +424,15 @@ k_dilute_shift_bulk(FbView V, int n_out, const float2* __restrict__ eyz, const i
     auto issue = [&](int o) {   // thread 0: output o into slot o % DB_DEPTH
         const int sl = o % DB_DEPTH;
         mbar_arrive_expect_tx(&full[sl], DB_SLOT);
-        const uint32_t d = smem_u32(ring[sl]);
-        bulk_copy(d, fsrc + (int64_t)o * V.ostride2, DB_F, &full[sl]);
-        bulk_copy(d + DB_F, eysrc + (int64_t)o * ne, DB_EY, &full[sl]);
-        bulk_copy(d + DB_F + DB_EY, ezsrc + (int64_t)o * ne, 16, &full[sl]);
+        bulk_copy(smem_u32(ring[sl]), fsrc + (int64_t)o * V.ostride2, DB_SLOT, &full[sl]);
     };
+    // shift factors (L2-resident) are loaded two outputs ahead into registers
+    auto load_e = [&](int o) {
+        const int64_t off = (int64_t)min(o, n_out - 1) * ne;
+        const float2 y = __ldg(eysrc + off), z = __ldg(ezsrc + off);
+        return make_float4(y.x, y.y, z.x, z.y);
+    };
+    float4 e0 = load_e(0), e1 = load_e(1);
     int issued = 0;   // thread 0: outputs [0, issued) have been copied or are in flight
     if (lt == 0)
         for (; issued < min(DB_DEPTH, n_out); ++issued) issue(issued);
@@ -478,8 +480,9 @@ k_dilute_shift_bulk(FbView V, int n_out, const float2* __restrict__ eyz, const i
         const unsigned char* slot = ring[sl];
         const float4 c01 = reinterpret_cast<const float4*>(slot)[2 * lt];
         const float4 c23 = reinterpret_cast<const float4*>(slot)[2 * lt + 1];
-        const float2 ey = reinterpret_cast<const float2*>(slot + DB_F)[lt];
-        const float2 ez = reinterpret_cast<const float2*>(slot + DB_F + DB_EY)[qb & 1];
+        const float4 e = e0;
+        e0 = e1;
+        e1 = load_e(o + 2);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[sl]);
         const float2 f[4] = {make_float2(c01.x, c01.y), make_float2(c01.z, c01.w), make_float2(c23.x, c23.y),
@@ -498,8 +501,8 @@ k_dilute_shift_bulk(FbView V, int n_out, const float2* __restrict__ eyz, const i
                 rg[4 + 2 * k] = fmaf(f[i].x, f[j].x, fmaf(f[i].y, f[j].y, rg[4 + 2 * k]));
                 rg[5 + 2 * k] = fmaf(f[i].y, f[j].x, fmaf(-f[i].x, f[j].y, rg[5 + 2 * k]));
             }
-        const float cs = fmaf(ey.x, ez.x, -ey.y * ez.y);
-        const float sn = fmaf(ey.y, ez.x, ey.x * ez.y);
+        const float cs = fmaf(e.x, e.z, -e.y * e.w);
+        const float sn = fmaf(e.y, e.z, e.x * e.w);
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             rt[2 * c] = fmaf(f[c].x, cs, fmaf(f[c].y, sn, rt[2 * c]));
@@ -548,8 +551,7 @@ cudaError_t launch_dilute_shift_batch(const FbView& V, int n_out, const float2* 
 {
     if (n_out <= 0) return cudaSuccess;
     const int64_t npix = (int64_t)V.ny * V.nz;
-    const bool bulk = V.nch == 4 && V.ny % 128 == 0 && V.nz % 2 == 0 &&
-                      (reinterpret_cast<uintptr_t>(V.hi) & 15) == 0 && (reinterpret_cast<uintptr_t>(eyz) & 15) == 0;
+    const bool bulk = V.nch == 4 && V.ny % 128 == 0 && (reinterpret_cast<uintptr_t>(V.hi) & 15) == 0;
     if (bulk)
         k_dilute_shift_bulk<<<(unsigned)(npix / 128), 128, 0, s>>>(
             V, n_out, eyz, out_rot, Gdil, reinterpret_cast<double2*>(Ftot), tstride / 2, err, limit_ns);

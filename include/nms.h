@@ -91,8 +91,8 @@ typedef struct {
     double P[3];             /* polarisation unit vector; all 0 -> e_z           */
     int32_t kc_cells;        /* tensor path: cells per FP32 TMEM chunk; 0 -> 64.
                                 Larger chunks drain less often and run faster
-                                (512^2 box GEMM: 90 ms at 64, 80 at 128, 74
-                                at 512) but the error at fully coherent
+                                (512^2 box GEMM about 11 % faster at 128 and
+                                18 % at 512 than at 64) but the error at fully coherent
                                 pixels grows about linearly with it (2e-7 of
                                 sum |w| at 64, 5e-7 at 128, 1.2e-6 at 256) */
     int32_t split_k;         /* tensor path: work items per SM of a GEMM launch

@@ -373,3 +373,32 @@ def test_interference_split_two_objects():
     np.testing.assert_allclose(dil, 2 * np.abs(F1) ** 2, rtol=1e-12)
     np.testing.assert_allclose(inter, 2 * np.abs(F1) ** 2 * np.cos(g[0] * 9.0 - g[1] * 4.0), rtol=1e-9,
                                atol=1e-9 * np.abs(F1).max() ** 2)
+
+
+def test_interference_split_rotated_sample_moves_centres():
+    # Sec. "Summation approach" with a sample orientation: the centres turn
+    # with the sample, F_tot = F_1 + F_2 exp(-i q.(R d)).  For identical
+    # objects every quadratic response then splits into 2 r_1 (dilute) and
+    # 2 r_1 cos(q.(R d)) (interference), r_1 one rotated object's response;
+    # nuclear, magnetic and spin-flip terms alike (Q is linear in F_M)
+    rng = np.random.default_rng(5)
+    pos = I.lattice_ball(3.0, 1.0)
+    n = len(pos)
+    mag = rng.normal(size=(n, 3))
+    nuc = rng.uniform(0.5, 1.5, n)
+    d = np.array([0.0, 9.0, -4.0]) + np.array([6.0, 0.0, 0.0])
+    R = I.random_rotations(1, seed=12)[0]
+    f = I.Field(np.vstack([pos, pos]), np.ones(2 * n), np.concatenate([nuc, nuc]), np.vstack([mag, mag]),
+                offsets=np.array([0, n, 2 * n]), centers=np.array([[0.0, 0.0, 0.0], d]))
+    g = S.q_grid("cartesian", 7, 9, -1, 1, -1.2, 0.8)
+    ids = ("N", "M", "SF", "UNPOL")
+    parts = S.response_parts(f, R, g, ids=ids)
+    r1 = S.responses(S.amplitudes(I.Field(pos, np.ones(n), nuc, mag), R, g[0], g[1]), g[2], g[3])
+    Rd = R @ d
+    ph = np.cos(g[0] * Rd[1] + g[1] * Rd[2])
+    for k in ids:
+        tot, dil, inter = parts[k]
+        scale = np.abs(r1[k]).max()
+        np.testing.assert_allclose(dil, 2 * r1[k], rtol=1e-12, atol=1e-12 * scale)
+        np.testing.assert_allclose(inter, 2 * r1[k] * ph, rtol=1e-9, atol=1e-9 * scale)
+

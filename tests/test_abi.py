@@ -89,6 +89,34 @@ def test_invalid_arguments_are_reported_without_gpu():
             nms.nms_correlation([0.0, 1.0], [1.0, 1.0], [1.0])
 
 
+def test_plan_create_argument_checks_come_before_the_device():
+    # the host-side checks of nms_plan_create run before any CUDA call, so each
+    # bad argument gives INVALID_ARG (1), not CUDA (3), with or without a GPU
+    lib = nms.load()
+    g = nms.make_grid("cartesian", 4, 4, -1, 1, -1, 1)
+    pos = np.zeros((3, 3))
+    p_pos = pos.ctypes.data_as(nms._D)
+    rot = np.eye(3).reshape(1, 9).repeat(2, axis=0)
+    h = ctypes.c_void_p()
+
+    def create(n, p, K, off, nrot, R, grid=ctypes.byref(g)):
+        h.value = 0x1234                                                     # cleared by every failed create
+        st = lib.nms_plan_create(ctypes.byref(h), n, p, None, None, None, K, off, None, nrot, R, grid, None, None)
+        assert h.value is None
+        return st
+
+    assert create(0, p_pos, 1, None, 1, None) == 1                           # no cells
+    assert create(3, None, 1, None, 1, None) == 1                            # no positions
+    assert create(3, p_pos, 0, None, 1, None) == 1                           # no objects
+    assert create(3, p_pos, 2, None, 1, None) == 1                           # K > 1 without offsets
+    assert create(3, p_pos, 1, None, 0, None) == 1                           # no orientations
+    assert create(3, p_pos, 1, None, 2, None) == 1                           # identity needs n_rot == 1
+    assert create(3, p_pos, 1, None, 2, rot.ctypes.data_as(nms._D), grid=None) == 1   # no grid
+    assert lib.nms_plan_create(None, 3, p_pos, None, None, None, 1, None, None, 1, None, ctypes.byref(g), None,
+                               None) == 1                                     # no output handle
+    assert nms.nms_last_error() == "out is NULL"
+
+
 def test_binding_refuses_strided_buffers():
     a = np.zeros((4, 6))[:, ::2]
     with pytest.raises(ValueError):

@@ -12,11 +12,16 @@ Default workload: the micromagnetic-style box, 256 x 256 x 64 cells at 2 nm
 (4.19M cells, smooth random M from 64 Fourier modes, 200 pores), 512 x 512
 detector on [-2, 2]^2 nm^-1: 1.10e12 terms per step.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nms|reference]
-                  [--precision auto|tc|direct|naive] [--workload box|sphere]
+  python bench.py [--steps K] [--warmup W] [--impl nms|reference]
+                  [--precision auto|tc|direct|naive] [--workload box|...]
 
-With --gpus N > 1 (torchrun) every rank evaluates its own replica of the
-workload (weak scaling, no data-path collective); rank 0 prints one JSON line.
+The library is single-GPU: with --gpus N > 1 (under torchrun) rank 0 prints
+one "unavailable" line and every rank exits 0 without GPU work.  The
+reference arm (--impl reference) times the FP64 CPU oracle on rank 0.
+
+Besides the tensor path, the default line times the FP32 direct sum
+(compensated and naive phase) on a sample of the same detector's pixels with
+all cells: the metric compares the two at the 1e-6 error bar.
 """
 from __future__ import annotations
 
@@ -38,12 +43,14 @@ METRIC = "cell·q-point terms/s of SANS Fourier sum: tensor-core split vs FP32 a
 # FP32-pipe operations per term of the compensated direct-sum kernel counted
 # from its source (phase 22, sincospif ~20, 8 FMA, two-float fold 7).
 DIRECT_OPS_PER_TERM = 57
-# Executed tensor flops per term of the split-FP16 GEMM: 3 products x 32 flops.
-TC_FLOPS_PER_TERM = 96
+# Algorithmic flops per term of the Fourier sum: 4 channels x one complex
+# multiply-add (8 real flops) per (cell, pixel).
+ALGO_FLOPS_PER_TERM = 32
 # DRAM bytes (read + write) the GEMM moves per byte of phase tables it
 # consumes, from an ncu capture of one launch on the 64x64x64 box (512^2
 # detector); the box workloads scale it by their own table bytes per launch.
-TC_DRAM_PER_TABLE_BYTE = 1.329   # 8.559 GB for 6.442 GB of tables (ncu, box64)
+# None until a capture of the current kernel is summarised under profiles/.
+TC_DRAM_PER_TABLE_BYTE = None
 TC_TRAFFIC_WORKLOADS = ("box", "box64")
 
 
@@ -183,48 +190,25 @@ def oracle_sample_rate(field, grid_kw, target_s=12.0, seed=0, R=None):
     return terms / dt, f"{n_s} random pixels x {field.n} cells (seed {seed}), {dt:.1f} s", F, idx, S.oracle_threads()
 
 
-# ----------------------------------------------------------------- dist helpers
-def dist_setup(n_gpus):
-    rank, world = 0, 1
-    if n_gpus > 1 or "RANK" in os.environ:
-        import torch.distributed as dist
-        world = int(os.environ.get("WORLD_SIZE", "1"))
-        rank = int(os.environ.get("RANK", "0"))
-        if world > 1:
-            import torch
-            backend = "nccl" if torch.cuda.is_available() else "gloo"
-            if backend == "nccl":
-                torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-            dist.init_process_group(backend=backend)
-    return rank, world
+# ----------------------------------------------------------------- launch
+def launch_rank():
+    """(rank, world) from torchrun's environment (1 process when absent)."""
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
 
 
-def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
-
-
-def max_over_ranks(x, world):
-    if world <= 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def whole_job(units_per_rank, ms_local, world):
-    """(slowest rank's time in ms, aggregate rate of all ranks' units per s):
-    every rank processes the same units (replicas, weak scaling)."""
-    ms = max_over_ranks(ms_local, world)
-    return ms, world * units_per_rank / (ms * 1e-3)
+def unavailable_multi_gpu(args):
+    """The library drives one GPU; a multi-GPU request prints one line on rank 0."""
+    rank, world = launch_rank()
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "unavailable": f"single-GPU library: --gpus {args.gpus} "
+                          f"(world size {world}) is not supported; run with --gpus 1",
+                          "n_gpus": args.gpus}), flush=True)
+    return 0
 
 
 # ----------------------------------------------------------------- reference arm
 def run_reference(args):
-    rank, world = dist_setup(args.gpus)
+    rank, world = launch_rank()
     if rank != 0:
         return 0
     field, grid_kw, edges, r, desc, rot, dilute = make_workload(args.workload)
@@ -267,11 +251,12 @@ def main():
     ap.add_argument("--impl", default="nms", choices=["nms", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "tc", "direct", "naive"])
     ap.add_argument("--workload", default="box",
-                    choices=["box", "box64", "sphere", "ensemble", "rotations", "post2d", "surrogate"])
+                    choices=["box", "box64", "sphere", "ensemble", "rotations", "post2d", "surrogate", "e4", "paper"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kc", type=int, default=0, help="cells per TMEM accumulation chunk (0: library default)")
     ap.add_argument("--workspace-gb", type=float, default=0.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32-leg", action="store_true", help="skip the FP32 direct-sum comparison")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--spheres", type=int, default=10000, help="ensemble: number of spheres")
     ap.add_argument("--items-per-sm", type=int, default=0, help="tensor path: GEMM work items per SM (0: library)")
@@ -279,21 +264,27 @@ def main():
                     help="ensemble: the same cells as one sum (centres applied, no per-object amplitudes)")
     ap.add_argument("--sets", type=int, default=1,
                     help="loop mode: S magnetization states of the workload along a field sweep in one plan")
+    ap.add_argument("--copies", type=int, default=0, help="e4: number of particle copies (0: the sweep)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.gpus > 1 or launch_rank()[1] > 1:
+        return unavailable_multi_gpu(args)
 
     import torch
     from paper_2601_18444_gb300 import nms
 
-    rank, world = dist_setup(args.gpus)
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     nms.load()
     if args.workload == "post2d":
-        return run_post2d(args, rank, world, dev)
+        return run_post2d(args, dev)
     if args.workload == "surrogate":
-        return run_surrogate(args, rank, world, dev)
+        return run_surrogate(args, dev)
+    if args.workload == "e4":
+        return run_e4(args, dev)
+    if args.workload == "paper":
+        return run_paper_shape(args, dev)
     field, grid_kw, edges, r, desc, rot, dilute = make_workload(args.workload, args.spheres)
     if args.single_sum and field.offsets is not None:
         # batching overhead reference: every cell moved to its object's centre, one summand
@@ -324,7 +315,6 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     img_u = torch.empty(npix, dtype=torch.float64, device="cuda")
     img_s = torch.empty(npix, dtype=torch.float64, device="cuda")
-    r_dev = torch.tensor(r, dtype=torch.float64, device="cuda")
 
     def step():
         nms.nms_amplitudes(plan)
@@ -343,7 +333,6 @@ def main():
     nms.nms_plan_stage_ms(plan, reset=True)
     peaks, peak_src = load_peaks()
     times = []
-    barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(dev) as clk:
         for _ in range(args.steps):
@@ -356,23 +345,33 @@ def main():
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
-    barrier(world)
     stage = nms.nms_plan_stage_ms(plan)
-    ms_step, value = whole_job(terms, float(np.mean(times)), world)
+    ms_step = float(np.mean(times))
+    value = terms / (ms_step * 1e-3)
     launches_per_step = sum(v[1] for v in stage.values()) / args.steps + 2 + 2 + 4
     clocks = clk.summary(peaks.get("sm_max_mhz", 2070.0))
+    is_tc = plan_path_is_tc(stage)
 
     # dominant kernel roofline
-    if plan_path_is_tc(stage):
+    if is_tc:
         k_ms = stage["gemm"][0] / args.steps
-        achieved = terms * TC_FLOPS_PER_TERM / (k_ms * 1e-3) / 1e12
+        info = nms.nms_plan_info(plan)
+        mirror = info.get("mirror", (0, 0))
+        exec_per_term = 3 * ALGO_FLOPS_PER_TERM / ((2 if mirror[0] else 1) * (2 if mirror[1] else 1))
+        achieved = terms * ALGO_FLOPS_PER_TERM / (k_ms * 1e-3) / 1e12
+        executed = terms * exec_per_term / (k_ms * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops", 1900.0)
         traffic = None
         if TC_DRAM_PER_TABLE_BYTE and args.workload in TC_TRAFFIC_WORKLOADS and args.sets <= 1:
             traffic = TC_DRAM_PER_TABLE_BYTE * table_bytes(field, grid_kw, n_rot) / (stage["gemm"][1] / args.steps)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
-                "kernel": "k_gemm_f16x3", "peak_source": f"{peak_src} bf16 dense (f16 same rate)"}
+                "kernel": "k_gemm_f16x3",
+                "flops_per_term": ALGO_FLOPS_PER_TERM,
+                "peak_source": f"{peak_src} bf16 dense (f16 same rate), burst",
+                "executed": {"flops_per_term": exec_per_term, "tflops": executed, "frac": executed / peak,
+                             "note": "3 split-FP16 MMAs per product; symmetric detector axes (q_y, q_z) "
+                                     f"computed on their q >= 0 half: {mirror}"}}
     else:
         k_ms = stage["direct"][0] / args.steps
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -386,7 +385,8 @@ def main():
     # error on a sample of pixels vs the oracle, and the oracle's own rate
     cpu = None
     err = None
-    if rank == 0 and not args.no_cpu_baseline:
+    oracle_sample = None
+    if not args.no_cpu_baseline:
         R_last = np.eye(3) if rot is None else rot[-1]
         rate, sample, F_ref, idx, cores = oracle_sample_rate(field0, grid_kw, args.cpu_seconds, R=R_last)
         F = nms.nms_get_amplitudes(plan)       # weight set 0
@@ -394,10 +394,19 @@ def main():
         wsum = np.abs(S.cell_weights(field0.vol, field0.nuc, field0.mag, R_last)).sum(1)
         err = [float(np.max(np.abs(F[c][idx] - F_ref[c])) / wsum[c]) if wsum[c] > 0 else 0.0 for c in range(4)]
         cpu = {"value": rate, "unit": "terms/s", "cores": cores, "kind": "oracle", "sample": sample}
+        oracle_sample = (idx, F_ref, wsum, R_last)
+    plan.close()
+
+    # the FP32 direct sum on the same box (compensated: the 1e-6 comparison;
+    # naive: throughput and error only), on a sample of the detector's pixels
+    fp32 = None
+    if is_tc and not args.no_fp32_leg and args.sets <= 1 and not dilute and rot is None:
+        fp32 = fp32_leg(nms, field0, grid_kw, stream, peaks, clocks, dev, oracle_sample)
+        if fp32 is not None:
+            fp32["tc_over_fp32_compensated"] = value / fp32["compensated"]["value"]
 
     # end to end through the C ABI from pinned host buffers (the timed plan is
     # released first: every e2e step creates and destroys its own)
-    plan.close()
     e2e = None
     if args.steps > 0 and not args.no_e2e:
         pin = {}
@@ -423,36 +432,95 @@ def main():
             p2.close()
             torch.cuda.synchronize()
             e2e_times.append(time.perf_counter() - t0)
-        t_e2e = max_over_ranks(min(e2e_times), world)
+        t_e2e = min(e2e_times)
         h2d = sum(pin[k].nbytes for k in pin)
         d2h = 2 * npix * 8
-        e2e = {"value": world * terms / t_e2e, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": terms / t_e2e, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "s_per_step": t_e2e}
 
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f16x3->f32(two-float)" if plan_path_is_tc(stage) else "f32(two-float)",
-                "data": "synthetic",
-                "config": {"workload": desc, "parallelism": f"replicas x{world}", "l2": "flushed between steps",
-                           "precision": args.precision, "terms_per_step": terms,
-                           "stage_ms_per_step": {k: v[0] / args.steps for k, v in stage.items() if v[1]}},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(round(launches_per_step
-                                                                                           * args.steps)),
-                "clocks": clocks, "amp_err_vs_oracle": err}
-        print(json.dumps(line), flush=True)
+    stage_ms = {k: v[0] / args.steps for k, v in stage.items() if v[1]}
+    line = {"metric": METRIC, "value": value, "unit": "terms/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16x3->f32(two-float)" if is_tc else "f32(two-float)",
+            "data": "synthetic",
+            "config": {"workload": desc, "parallelism": "1 GPU", "l2": "flushed between steps",
+                       "precision": args.precision, "terms_per_step": terms, "stage_ms_per_step": stage_ms,
+                       "tables_over_gemm": (stage_ms.get("tables", 0.0) / stage_ms["gemm"]) if is_tc else None},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp32_direct": fp32,
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "clocks": clocks, "amp_err_vs_oracle": err}
+    print(json.dumps(line), flush=True)
     return 0
+
+
+def fp32_leg(nms, field, grid_kw, stream, peaks, clocks, dev, oracle_sample, n_pix=8192, reps=3):
+    """Compensated and naive FP32 direct sums of the workload's cells on a
+    random sample of its detector pixels (a LIST grid; the oracle's pixels
+    first, so their error is measured): terms/s, error against the oracle and
+    the compensated kernel's FP32-lane roofline."""
+    import torch
+    from oracle import sans as S
+    kw = dict(grid_kw)
+    kind = kw.pop("kind")
+    qy, qz = S.q_grid(kind, **kw)[:2]
+    npix = qy.shape[0]
+    rng = np.random.default_rng(11)
+    first = oracle_sample[0] if oracle_sample is not None else np.zeros(0, dtype=np.int64)
+    rest = rng.choice(np.setdiff1d(np.arange(npix), first), size=max(0, min(n_pix, npix) - len(first)),
+                      replace=False)
+    idx = np.concatenate([first, rest]).astype(np.int64)
+    ql = np.stack([qy[idx], qz[idx]], axis=1)
+    g = nms.make_grid("list", len(idx), qlist=ql)
+    terms = float(field.n) * len(idx)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    lanes_peak = sms * 128 * mhz * 1e6 / 1e12
+    res = {"sample": f"{len(idx)} random pixels of the same detector x {field.n} cells (LIST grid)"}
+    for name, prec in (("compensated", nms.PREC_FP32_DIRECT), ("naive", nms.PREC_FP32_NAIVE)):
+        plan = nms.plan_from_field(field, g, nms.nms_options_default(precision=prec), stream=stream.cuda_stream)
+        nms.nms_amplitudes(plan)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            nms.nms_amplitudes(plan)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = float(np.mean(ts))
+        r = {"value": terms / (ms * 1e-3), "unit": "terms/s", "ms": ms}
+        if oracle_sample is not None and len(first):
+            F = nms.nms_get_amplitudes(plan)
+            F_ref, wsum = oracle_sample[1], oracle_sample[2]
+            r["amp_err_vs_oracle"] = [float(np.max(np.abs(F[c][:len(first)] - F_ref[c])) / wsum[c])
+                                      if wsum[c] > 0 else 0.0 for c in range(4)]
+        if name == "compensated":
+            achieved = terms * DIRECT_OPS_PER_TERM / (ms * 1e-3) / 1e12
+            r["roofline"] = {"bound": "alu", "achieved": achieved, "peak": lanes_peak, "unit": "Tops/s",
+                             "frac": achieved / lanes_peak, "ops_per_term": DIRECT_OPS_PER_TERM,
+                             "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz"}
+        res[name] = r
+        plan.close()
+    return res
+
+
+def gemm_axis(n, lo, hi):
+    """Nodes of one detector axis the GEMM covers: the q >= 0 half of an axis
+    symmetric about q = 0, else all of them."""
+    return n - n // 2 if (n >= 2 and lo == -hi) else n
 
 
 def table_bytes(field, grid_kw, n_rot):
     """Bytes of split-FP16 phase tables one step writes and the GEMM reads:
-    per 32-cell k-block, (A tiles + B tiles) x (hi, lo) x 16 KB."""
-    mt = -(-4 * grid_kw["n0"] // 128)
-    nt = -(-2 * grid_kw["n1"] // 128)
+    per 64-cell k-block, (A tiles + B tiles) x (hi, lo) x 16 KB, with A rows
+    (q_y node, channel) x (cos, sin) and B rows q_z node x (cos, sin)."""
+    mt = -(-8 * gemm_axis(grid_kw["n0"], grid_kw["lo0"], grid_kw["hi0"]) // 128)
+    nt = -(-2 * gemm_axis(grid_kw["n1"], grid_kw["lo1"], grid_kw["hi1"]) // 128)
     if field.offsets is not None and len(field.offsets) > 2:
-        nkb = int(sum(-(-(b - a) // 32) for a, b in zip(field.offsets[:-1], field.offsets[1:])))
+        nkb = int(sum(-(-(b - a) // 64) for a, b in zip(field.offsets[:-1], field.offsets[1:])))
     else:
-        nkb = -(-field.n // 32)
+        nkb = -(-field.n // 64)
     return float(nkb * n_rot * (mt + nt) * 2 * 16384)
 
 
@@ -462,7 +530,7 @@ def table_bytes(field, grid_kw, n_rot):
 CORR2D_OPS_PER_TERM = 40
 
 
-def run_post2d(args, rank, world, dev):
+def run_post2d(args, dev):
     """2D post-processing of the box's unpolarized image: the angular spectrum
     (kmax 16 on 128 ring bins) and the 2D correlation C(rho, alpha) on a
     64 x 64 output grid, timed with CUDA events; one step = both calls."""
@@ -493,7 +561,6 @@ def run_post2d(args, rank, world, dev):
     torch.cuda.synchronize()
     peaks, _ = load_peaks()
     times, tcorr = [], []
-    barrier(world)
     with ClockSampler(dev) as clk:
         for _ in range(args.steps):
             flush.fill_(1)
@@ -506,8 +573,7 @@ def run_post2d(args, rank, world, dev):
             e2.synchronize()
             times.append(e0.elapsed_time(e1))
             tcorr.append(e1.elapsed_time(e2))
-    barrier(world)
-    ms = max_over_ranks(float(np.mean(times)), world)
+    ms = float(np.mean(times))
     ms_corr = float(np.mean(tcorr))
     clocks = clk.summary(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -522,7 +588,7 @@ def run_post2d(args, rank, world, dev):
         nms.nms_correlation_2d(plan, img_h, rho, alpha)
     t_e2e = (time.perf_counter() - t0) / 2
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if not args.no_cpu_baseline:
         # the oracle's 2D correlation on a bounded sample of output points
         from oracle import sans as S
         q0 = np.linspace(grid_kw["lo0"], grid_kw["hi0"], grid_kw["n0"])
@@ -534,23 +600,22 @@ def run_post2d(args, rank, world, dev):
             dt = time.perf_counter() - t0
         cpu = {"value": n_s * npix / dt, "unit": "terms/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{n_s} output points x {npix} pixels, {dt:.1f} s (numpy with its BLAS threads)"}
-    if rank == 0:
-        line = {"metric": "pixel x output-point terms/s of the 2D correlation (Eq. crav2d) with the angular spectrum",
-                "value": world * terms / (ms * 1e-3), "unit": "terms/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32(two-float)", "data": "synthetic",
-                "config": {"workload": "UNPOL image of " + desc + "; angular spectrum kmax 16 on 128 ring bins; "
-                                       "C(rho, alpha) on 64 rho in [0, 300] nm x 64 alpha in [0, pi)",
-                           "parallelism": f"replicas x{world}", "l2": "flushed between steps",
-                           "corr2d_ms": ms_corr},
-                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                             "frac": achieved / peak, "traffic": None, "kernel": "k_corr2d",
-                             "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz"},
-                "cpu_baseline": cpu,
-                "e2e": {"value": world * terms / t_e2e, "unit": "terms/s", "h2d_bytes_per_step": 2 * npix * 8,
-                        "d2h_bytes_per_step": 64 * 64 * 16 + 17 * 128 * 16 + 128 * 16 + 17 * 16},
-                "gpu_launches": args.steps * 7, "clocks": clocks}
-        print(json.dumps(line), flush=True)
+    line = {"metric": "pixel x output-point terms/s of the 2D correlation (Eq. crav2d) with the angular spectrum",
+            "value": terms / (ms * 1e-3), "unit": "terms/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32(two-float)", "data": "synthetic",
+            "config": {"workload": "UNPOL image of " + desc + "; angular spectrum kmax 16 on 128 ring bins; "
+                                   "C(rho, alpha) on 64 rho in [0, 300] nm x 64 alpha in [0, pi)",
+                       "parallelism": "1 GPU", "l2": "flushed between steps",
+                       "corr2d_ms": ms_corr},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_corr2d",
+                         "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": terms / t_e2e, "unit": "terms/s", "h2d_bytes_per_step": 2 * npix * 8,
+                    "d2h_bytes_per_step": 64 * 64 * 16 + 17 * 128 * 16 + 128 * 16 + 17 * 16},
+            "gpu_launches": args.steps * 7, "clocks": clocks}
+    print(json.dumps(line), flush=True)
     plan.close()
     return 0
 
@@ -561,7 +626,7 @@ def mlp_flops(n_in, H, n_out):
     return 2.0 * (n_in * H + H * H + H * n_out)
 
 
-def run_surrogate(args, rank, world, dev):
+def run_surrogate(args, dev):
     """Learned surrogate (scaled-down vortex family): training curves from the
     batched transform, then timed training epochs and timed inference on 2^20
     queries; the MLP GEMMs against the bf16 dense peak."""
@@ -596,7 +661,6 @@ def run_surrogate(args, rank, world, dev):
         for _ in range(max(3, args.warmup)):
             nms.nms_surrogate_infer(s, q, out)
         torch.cuda.synchronize()
-        barrier(world)
         times = []
         for _ in range(max(1, args.steps)):
             e0.record()
@@ -604,34 +668,189 @@ def run_surrogate(args, rank, world, dev):
             e1.record()
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
-        barrier(world)
-    ms_inf, q_rate = whole_job(nq, float(np.mean(times)), world)
+    ms_inf = float(np.mean(times))
+    q_rate = nq / (ms_inf * 1e-3)
     peaks, peak_src = load_peaks()
     clocks = clk.summary(peaks.get("sm_max_mhz", 2070.0))
     f_inf = nq * mlp_flops(6, H, n_out)
     achieved = f_inf / (ms_inf * 1e-3) / 1e12
     peak = peaks.get("bf16_tflops", 1900.0)
     train_samples = epochs * len(params)
-    if rank == 0:
-        line = {"metric": "surrogate inference queries/s (MLP 6->256->256->n_out, bf16 GEMMs)",
-                "value": q_rate, "unit": "queries/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_inf, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "bf16->f32", "data": "synthetic",
-                "config": {"workload": f"vortex family, {len(params)} training curves from the batched transform "
-                                       f"(a=2.5nm, 16 orientations, 128^2 detector, {n_out} log bins); "
-                                       f"inference on 2^20 queries",
-                           "curves_s": t_tr, "curve_terms_per_s": terms_tr / t_tr,
-                           "train_samples_per_s": train_samples / (ms_train * 1e-3),
-                           "exact_ms_per_curve": 1e3 * t_tr / len(params),
-                           "surrogate_us_per_query": 1e3 * ms_inf / nq},
-                "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                             "frac": achieved / peak, "traffic": None, "kernel": "k_mlp_infer (fused tcgen05 bf16)",
-                             "peak_source": f"{peak_src} bf16 dense"},
-                "cpu_baseline": None, "e2e": None,
-                "gpu_launches": len(times) if (H == 256 and n_out <= 64) else None,   # one fused kernel per call
-                "clocks": clocks}
-        print(json.dumps(line), flush=True)
+    line = {"metric": "surrogate inference queries/s (MLP 6->256->256->n_out, bf16 GEMMs)",
+            "value": q_rate, "unit": "queries/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_inf, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16->f32", "data": "synthetic",
+            "config": {"workload": f"vortex family, {len(params)} training curves from the batched transform "
+                                   f"(a=2.5nm, 16 orientations, 128^2 detector, {n_out} log bins); "
+                                   f"inference on 2^20 queries",
+                       "curves_s": t_tr, "curve_terms_per_s": terms_tr / t_tr,
+                       "train_samples_per_s": train_samples / (ms_train * 1e-3),
+                       "exact_ms_per_curve": 1e3 * t_tr / len(params),
+                       "surrogate_us_per_query": 1e3 * ms_inf / nq},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_mlp_infer (fused tcgen05 bf16)",
+                         "peak_source": f"{peak_src} bf16 dense"},
+            "cpu_baseline": None, "e2e": None,
+            "gpu_launches": len(times) if (H == 256 and n_out <= 64) else None,   # one fused kernel per call
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
     s.close()
+    return 0
+
+
+def lattice_copies(particle, n_copies, spacing=45.0):
+    """n_copies of a particle on the simple-cubic sites (spacing in nm)
+    nearest the origin, as one field (one sum over all cells)."""
+    from paper_2601_18444_gb300 import inputs as I
+    side = int(np.ceil(n_copies ** (1.0 / 3.0))) + 2
+    ax = (np.arange(side) - (side - 1) / 2.0) * spacing
+    sites = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), axis=-1).reshape(-1, 3)
+    sites = sites[np.argsort(np.linalg.norm(sites, axis=1), kind="stable")[:n_copies]]
+    n = particle.n
+    pos = (particle.pos[None, :, :] + sites[:, None, :]).reshape(-1, 3)
+    return I.Field(pos, np.tile(particle.vol, n_copies), np.tile(particle.nuc, n_copies),
+                   np.tile(particle.mag, (n_copies, 1)), name=f"{particle.name}_x{n_copies}")
+
+
+E4_COPIES = (10, 40, 160, 640, 2560, 10240, 25600)
+
+
+def run_e4(args, dev):
+    """Runtime-scaling shape of the paper's runtime experiment: N identical
+    D = 40 nm linear-vortex spheres (a = 2 nm, 4169 cells) on a 45 nm simple
+    cubic lattice, N = 10 ... 25,600 (4.2e4 ... 1.07e8 cells), one sum over
+    all cells on a 256^2 detector [-1.5, 1.5]^2 nm^-1 (tensor path).  One step
+    = amplitudes + the unpolarized image + its azimuthal average; terms/s
+    against the total cell count W."""
+    import torch
+    from paper_2601_18444_gb300 import inputs as I
+    from paper_2601_18444_gb300 import nms
+    particle = I.linear_vortex_sphere(20.0, 2.0, normalised=True)
+    grid_kw = dict(kind="cartesian", n0=256, n1=256, lo0=-1.5, hi0=1.5, lo1=-1.5, hi1=1.5)
+    g = nms.make_grid(**grid_kw)
+    edges = np.linspace(0.0, 1.5, 129)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    peaks, _ = load_peaks()
+    copies = (args.copies,) if args.copies > 0 else E4_COPIES
+    sweep = []
+    with ClockSampler(dev) as clk:
+        for nc in copies:
+            f = lattice_copies(particle, nc)
+            plan = nms.plan_from_field(f, g, nms.nms_options_default(timing=1), stream=stream.cuda_stream)
+            img = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+
+            def step():
+                nms.nms_amplitudes(plan)
+                nms.nms_response(plan, "UNPOL", out=img)
+                nms.nms_azimuthal_average(plan, img, edges)
+
+            for _ in range(max(1, args.warmup)):
+                step()
+            torch.cuda.synchronize()
+            nms.nms_plan_stage_ms(plan, reset=True)
+            ts = []
+            for _ in range(max(1, args.steps)):
+                flush.fill_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            st = nms.nms_plan_stage_ms(plan)
+            ms = float(np.mean(ts))
+            terms = float(f.n) * plan.npix
+            sweep.append({"copies": nc, "cells": int(f.n), "ms_per_step": ms, "terms_per_s": terms / (ms * 1e-3),
+                          "stage_ms": {k: v[0] / max(1, args.steps) for k, v in st.items() if v[1]}})
+            plan.close()
+            del f
+    clocks = clk.summary(peaks.get("sm_max_mhz", 2070.0))
+    last = sweep[-1]
+    line = {"metric": "cell·q-point terms/s of the SANS Fourier sum vs total cells (runtime-experiment shape)",
+            "value": last["terms_per_s"], "unit": "terms/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": last["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16x3->f32(two-float)", "data": "synthetic",
+            "config": {"workload": "N x linear-vortex sphere D=40nm a=2nm (4169 cells) on a 45nm simple-cubic "
+                                   "lattice, one sum; 256x256 detector [-1.5,1.5]^2 nm^-1; value at the largest N",
+                       "l2": "flushed between steps", "sweep": sweep,
+                       "paper_context": "RTX 3090: linear in W from 4.169e4 to 1.067e8 cells (values only in "
+                                        "a figure, not in the text)"},
+            "roofline": None, "cpu_baseline": None, "e2e": None,
+            "gpu_launches": None, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_paper_shape(args, dev):
+    """The paper's interparticle-interference example as a shape: 800 D = 40 nm
+    spheres (4169 cells each, linear vortex) on a 45 nm simple-cubic lattice,
+    one sum over 3.34e6 cells on the paper's polar (q, theta) grid of 1000 x
+    1000 nodes, q in [0, 1.5] nm^-1 -- the direct FP32 path (compensated
+    phase), the only one for a polar grid.  One step = amplitudes, the
+    unpolarized and spin-flip images, their azimuthal averages and c(r)."""
+    import torch
+    from paper_2601_18444_gb300 import inputs as I
+    from paper_2601_18444_gb300 import nms
+    particle = I.linear_vortex_sphere(20.0, 2.0, normalised=True)
+    f = lattice_copies(particle, 800)
+    g = nms.make_grid("polar", 1000, 1000, 0.0, 1.5)
+    stream = torch.cuda.current_stream()
+    plan = nms.plan_from_field(f, g, nms.nms_options_default(timing=1), stream=stream.cuda_stream)
+    npix = plan.npix
+    img_u = torch.empty(npix, dtype=torch.float64, device="cuda")
+    img_s = torch.empty(npix, dtype=torch.float64, device="cuda")
+    r = np.linspace(0.0, 400.0, 200)
+
+    def step():
+        nms.nms_amplitudes(plan)
+        nms.nms_response(plan, "UNPOL", out=img_u)
+        nms.nms_response(plan, "SF", out=img_s)
+        for img in (img_u, img_s):
+            Iq, c, qm = nms.nms_azimuthal_average(plan, img, nbins=1000)
+            nms.nms_correlation(qm, Iq, r, stream=stream.cuda_stream)
+
+    warm, steps = max(1, min(args.warmup, 1)), max(1, min(args.steps, 2))
+    for _ in range(warm):
+        step()
+    torch.cuda.synchronize()
+    nms.nms_plan_stage_ms(plan, reset=True)
+    peaks, _ = load_peaks()
+    ts = []
+    with ClockSampler(dev) as clk:
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    st = nms.nms_plan_stage_ms(plan)
+    ms = float(np.mean(ts))
+    terms = float(f.n) * npix
+    clocks = clk.summary(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    peak = sms * 128 * mhz * 1e6 / 1e12
+    k_ms = st["direct"][0] / steps
+    achieved = terms * DIRECT_OPS_PER_TERM / (k_ms * 1e-3) / 1e12
+    line = {"metric": "cell·q-point terms/s of the SANS Fourier sum, paper's example shape (polar grid, direct path)",
+            "value": terms / (ms * 1e-3), "unit": "terms/s", "n_gpus": 1, "steps": steps, "warmup": warm,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32(two-float)", "data": "synthetic",
+            "config": {"workload": "800 x linear-vortex sphere D=40nm a=2nm (3.34e6 cells) on a 45nm simple-cubic "
+                                   "lattice; polar grid 1000 q in [0,1.5] nm^-1 x 1000 theta; UNPOL + SF, "
+                                   "azimuthal averages, c(r) on 200 r",
+                       "stage_ms_per_step": {k: v[0] / steps for k, v in st.items() if v[1]},
+                       "paper_context": "about 60 s on an RTX 3090 for 3.38e6 cells on a 1000x1000 (q, theta) grid "
+                                        "with all outputs incl. a 1000x1000 2D correlation and 670 MB of CSV "
+                                        "(>= 5.6e10 terms/s)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_direct<compensated>",
+                         "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz"},
+            "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    plan.close()
     return 0
 
 

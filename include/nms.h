@@ -89,12 +89,11 @@ typedef struct {
     double volume_V;         /* scattering volume V of the 1/V prefactor; 0 -> 1 */
     double b_H;              /* magnetic scattering length b_H; 0 -> 1           */
     double P[3];             /* polarisation unit vector; all 0 -> e_z           */
-    int32_t kc_cells;        /* tensor path: cells per FP32 TMEM chunk; 0 -> 64.
-                                Larger chunks drain less often and run faster
-                                (512^2 box GEMM about 11 % faster at 128 and
-                                18 % at 512 than at 64) but the error at fully coherent
-                                pixels grows about linearly with it (2e-7 of
-                                sum |w| at 64, 5e-7 at 128, 1.2e-6 at 256) */
+    int32_t kc_cells;        /* tensor path: cells per FP32 TMEM chunk, rounded
+                                down to a multiple of 64 (at least 64); 0 -> 128.
+                                Larger chunks drain less often and run faster,
+                                but the error at fully coherent pixels grows
+                                about linearly with the chunk                  */
     int32_t split_k;         /* tensor path: work items per SM of a GEMM launch
                                 (how finely the cells of each output are split
                                 over CTAs); 0 -> 8, or the autotuned value      */
@@ -107,7 +106,7 @@ typedef struct {
     int32_t timing;          /* 1: record CUDA events around each stage (see
                                 nms_plan_stage_ms)                               */
     int32_t autotune;        /* tensor path: 1 = time candidate GEMM forms
-                                (one CTA, CTA pairs sharing A, two-SM MMA),
+                                (one CTA per tile, two-SM MMA),
                                 kc and work-list granularities on a probe of
                                 the cells at plan creation and keep the
                                 fastest whose amplitude error (vs the
@@ -379,9 +378,14 @@ nms_status nms_dsft_direct_noalloc(int64_t n_cells, const double* Y, const doubl
 /* The evaluation the plan settled on: precision = the nms_precision in use
  * (AUTO resolved), kc_cells = cells per TMEM accumulation chunk and
  * items_per_sm = work items per SM of each GEMM launch (tensor path; 0
- * otherwise), after autotuning when it was requested.  Any pointer may be
- * NULL. */
-nms_status nms_plan_info(nms_plan_t plan, int32_t* precision, int32_t* kc_cells, int32_t* items_per_sm);
+ * otherwise), after autotuning when it was requested; gemm_form = 0 (one
+ * CTA per 128 x 128 tile) or 2 (two-SM MMA over pairs of A tiles), -1 off
+ * the tensor path; mirror_y / mirror_z = 1 where the detector axis is
+ * symmetric about q = 0 (lo = -hi) and the GEMM evaluates its q >= 0 half,
+ * writing both signs (cos is even and sin odd in q; Sec. "Summation
+ * approach" sum, split by parity).  Any pointer may be NULL. */
+nms_status nms_plan_info(nms_plan_t plan, int32_t* precision, int32_t* kc_cells, int32_t* items_per_sm,
+                         int32_t* gemm_form, int32_t* mirror_y, int32_t* mirror_z);
 
 /* Loop mode (paper, Sec. "Program description": batch runs over field-,
  * temperature- or time-dependent data sets of one geometry): select which

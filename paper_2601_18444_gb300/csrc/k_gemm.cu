@@ -1,15 +1,23 @@
 // Tensor-core path: the Fourier sum on a separable (Cartesian) detector grid
-// as a split-FP16 complex GEMM on tcgen05 (sm_103a).
+// as a split-FP16 real GEMM on tcgen05 (sm_103a).
 //
 // Paper, Sec. "Summation approach": F_c(q) = sum_j w_cj exp(-i q.r_j).  On the
 // detector plane q = (0, q_y, q_z) the phase separates,
 //   exp(-i (q_y Y + q_z Z)) = exp(-i q_y Y) exp(-i q_z Z),
-// so with m = 4a + c (q_y index a, channel c), n = 2b + r (q_z index b,
-// r = Re/Im) and k = 2j + p (cell j, p = cos/sin part)
-//   A[m, 2j]   = w_cj cos(q_y,a Y_j)      A[m, 2j+1]   = w_cj sin(q_y,a Y_j)
-//   B[2b, 2j]  = cos(q_z,b Z_j)           B[2b, 2j+1]  = -sin(q_z,b Z_j)
-//   B[2b+1,2j] = -sin(q_z,b Z_j)          B[2b+1,2j+1] = -cos(q_z,b Z_j)
-//   D = A B^T:  D[4a+c, 2b] = Re F_c(a, b),  D[4a+c, 2b+1] = Im F_c(a, b).
+// and with alpha = q_y Y_j, beta = q_z Z_j the four real sums
+//   cc = sum_j w_cj cos(alpha) cos(beta)     cs = sum_j w_cj cos(alpha) sin(beta)
+//   sc = sum_j w_cj sin(alpha) cos(beta)     ss = sum_j w_cj sin(alpha) sin(beta)
+// give F_c(s_y q_y, s_z q_z) = (cc - s_y s_z ss) - i (s_z cs + s_y sc) for both
+// signs s_y, s_z = +-1: cos is even and sin odd in q.  The GEMM is
+//   D = A B^T,  A[2 (nch a + c) + p, j] = w_cj {cos, sin}_p(q_y,a Y_j),
+//               B[2 b + r, j]           = {cos, sin}_r(q_z,b Z_j),
+// K = cells, so D holds (cc, cs) in row p = 0 and (sc, ss) in row p = 1 of
+// each (a, c).  On a detector axis that is symmetric about q = 0 (lo = -hi)
+// the GEMM covers only the q >= 0 half of that axis and the epilogue writes
+// both signs: a grid symmetric in q_y and q_z costs a quarter of the MMA work
+// and 10 instead of 24 table bytes per cell and pixel pair (512^2 grid),
+// with the same per-term arithmetic.  An asymmetric axis is covered in full
+// and only the s = +1 combination is written.
 //
 // Precision (GB300-specific choice): each operand x (scaled by a power of two
 // to |x| <= 2^12) is split x = hi + lo with hi = fp16(x), lo = fp16(x - hi);
@@ -21,8 +29,7 @@
 // chunk partial D0 + D1 is added to lo with one FP32 add and (hi, lo) is
 // renormalised by TwoSum every TC_RENORM chunks, so lo holds at most a few
 // chunk partials and its rounding stays far below the TMEM accumulation
-// error (measured on the 4.19M-cell box: 2.0e-7 of sum|w| either way), at
-// less than half the drain arithmetic of a TwoSum per chunk.
+// error.
 //
 // Phase tables use the two-float phase in turns t = q'.r (q' = q/2 pi) with
 // the exact reduction t - rint(t), then sincospif.  Tables are written in the
@@ -43,9 +50,9 @@
 
 namespace nms {
 
-constexpr int TC_BM = 128;          // rows of A per tile (32 q_y values x 4 channels)
-constexpr int TC_BN = 128;          // rows of B per tile (64 q_z values x Re/Im)
-constexpr int TC_BK = 64;           // k per block (32 cells), one 128-byte swizzle row
+constexpr int TC_BM = 128;          // rows of A per tile: 64 (q_y, channel) pairs x (cos, sin)
+constexpr int TC_BN = 128;          // rows of B per tile: 64 q_z values x (cos, sin)
+constexpr int TC_BK = 64;           // k per block = cells per block, one 128-byte swizzle row
 constexpr int TC_BLOCK_BYTES = TC_BM * TC_BK * 2;   // 16 KB
 constexpr int TC_STAGES = 3;
 constexpr int TC_STAGE_BYTES = 4 * TC_BLOCK_BYTES;  // A_hi, A_lo, B_hi, B_lo
@@ -61,7 +68,7 @@ constexpr float TC_SCALE = 4096.0f; // operand scale 2^12
 
 // ------------------------------------------------------------------ tables
 // Tables cover a list of k-blocks; k-block kb holds the cells
-// [kb_cell0[kb], kb_cell0[kb] + kb_ncell[kb]) (kb_ncell <= 32) of the stacked
+// [kb_cell0[kb], kb_cell0[kb] + kb_ncell[kb]) (kb_ncell <= 64) of the stacked
 // per-rotation cell arrays, the rest of the block is zero padding.
 __device__ __forceinline__ float turns_reduced(float2 q, float xh, float xl)
 {
@@ -83,77 +90,76 @@ __device__ __forceinline__ void split_h2(float x0, float x1, uint32_t& h, uint32
     l = *reinterpret_cast<const uint32_t*>(&ll);
 }
 
-// fp16x2 (u, v) -> (v, -u), u in the low half: rounding to nearest is
-// odd-symmetric, so the split of a negated value is the negated split
-__device__ __forceinline__ uint32_t swap_neg_h2(uint32_t w) { return __byte_perm(w, 0, 0x1032) ^ 0x80000000u; }
+// four consecutive k of one row: hi and lo halves as 8-byte words
+__device__ __forceinline__ void split4(float x0, float x1, float x2, float x3, uint2& h, uint2& l)
+{
+    split_h2(x0, x1, h.x, l.x);
+    split_h2(x2, x3, h.y, l.y);
+}
 
-// The tables are written one k-block per block of 128 threads: the cells'
-// positions and weights are loaded once per k-block and every A and B row
-// of that k-block is computed from them, so the load latency is paid once
-// per (A + B tiles) x 32 KB of output.  Thread t holds the cells
-// 4 (t & 7) .. + 3 and takes the row groups t / 8 + 16 i.  Stores are
-// streaming (evict-first): a chunk's tables are read back by the GEMM only
-// after the whole chunk is written.
-constexpr int TAB_THREADS = 128;
+// The tables are written one k-block (64 cells) per block of 256 threads:
+// the cells' positions and weights are loaded once per k-block and every A
+// and B row of that k-block is computed from them.  Thread t holds the
+// cells 4 (t & 15) .. + 3 (one 8-byte half of a 16-byte swizzle chunk) and
+// takes the row groups t / 16 + 16 i, so the 16 threads of a half-warp write
+// one whole 128-byte row per store.  Stores are streaming (evict-first): a
+// chunk's tables are read back by the GEMM only after the whole chunk is
+// written.
+constexpr int TAB_THREADS = 256;
 
 // A tables: block (mt, kb) holds rows m = mt*128 + r, r < 128, with
-// m = a * nch + c (q_y index a, channel c = 4 * set + {N, Mx, My, Mz}) and
-// k = 2 j_loc + p.  A row group g is the 4 rows 4g..4g+3 (one set, one a;
-// nch is a multiple of 4).  Weight set st of cell j is cw[st * wstride + j].
+// m = 2 (nch a + c) + p (GEMM q_y index a, channel c = 4 * set + {N, Mx, My,
+// Mz}, p = cos/sin) and k = cell of the block.  A row group g is the 8 rows
+// 8g..8g+7: one q_y node a and one weight set (g = spad a + set, spad =
+// nch / 4).  Weight set st of cell j is cw[st * wstride + j].
 //
-// B tables: block (nt, kb) holds rows n = nt*128 + 2*b_loc + r, b_loc < 64.
-// Re row (cos, -sin), Im row (-sin, -cos): each Im word is the Re word
-// (c, -s) turned into (-s, -c).
-__global__ void __launch_bounds__(TAB_THREADS, 7)
+// B tables: block (nt, kb) holds rows n = nt*128 + 2 b_loc + r, b_loc < 64,
+// r = cos/sin of q_z,b Z_j.
+__global__ void __launch_bounds__(TAB_THREADS, 3)
 k_tables(const float4* __restrict__ cpos, const float4* __restrict__ cw, int64_t wstride, int nch,
          const int64_t* __restrict__ kb_cell0, const int32_t* __restrict__ kb_ncell, const float2* __restrict__ qy,
-         int ny, const float2* __restrict__ qz, int nz, float4 wscale, int64_t nkb, int mtiles, int ntiles,
+         int nyg, const float2* __restrict__ qz, int nzg, float4 wscale, int64_t nkb, int mtiles, int ntiles,
          uint8_t* __restrict__ A_hi, uint8_t* __restrict__ A_lo, uint8_t* __restrict__ B_hi,
          uint8_t* __restrict__ B_lo)
 {
-    const int r = threadIdx.x >> 3;
-    const int chunk = threadIdx.x & 7;
+    const int r = threadIdx.x >> 4;
+    const int q4 = threadIdx.x & 15;
+    const int k0 = 4 * q4;                          // first cell of this thread in the k-block
     const int spad = nch >> 2;                      // weight sets per output (a power of two)
     // row group g = r + 16 i has weight set g mod spad: one set per thread
     // when spad <= 16, else spad / 16 passes over i with one set each
     const int passes = spad > 16 ? spad / 16 : 1;
-    const int ngroups = mtiles * 32;
+    const int ngroups = mtiles * 16;
     const int nb = ntiles * 64;
     for (int64_t kb = blockIdx.x; kb < nkb; kb += gridDim.x) {
         const int64_t c0 = kb_cell0[kb];
         const int nc = kb_ncell[kb];
         float4 cp[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int jl = chunk * 4 + u;
-            cp[u] = jl < nc ? cpos[c0 + jl] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+        for (int u = 0; u < 4; ++u) cp[u] = k0 + u < nc ? cpos[c0 + k0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
         // ---- B rows; padding cells and rows stay zero
         for (int bi = r; bi < nb; bi += 16) {
             const int nt = bi >> 6, b_loc = bi & 63;
-            const bool brow = bi < nz;
+            const bool brow = bi < nzg;
             const float2 q = brow ? qz[bi] : make_float2(0.f, 0.f);
-            uint4 hr, lr, hi_, li_;
-            uint32_t* hrw = reinterpret_cast<uint32_t*>(&hr);
-            uint32_t* lrw = reinterpret_cast<uint32_t*>(&lr);
-            uint32_t* hiw = reinterpret_cast<uint32_t*>(&hi_);
-            uint32_t* liw = reinterpret_cast<uint32_t*>(&li_);
+            float cs[4], sn[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const float live = (brow && chunk * 4 + u < nc) ? TC_SCALE : 0.f;
-                float sn, cs;
-                sincospif(2.0f * turns_reduced(q, cp[u].z, cp[u].w), &sn, &cs);
-                split_h2(cs * live, -sn * live, hrw[u], lrw[u]);    // Re row: ( cos, -sin)
-                hiw[u] = swap_neg_h2(hrw[u]);                         // Im row: (-sin, -cos)
-                liw[u] = swap_neg_h2(lrw[u]);
+                const float live = (brow && k0 + u < nc) ? TC_SCALE : 0.f;
+                sincospif(2.0f * turns_reduced(q, cp[u].z, cp[u].w), &sn[u], &cs[u]);
+                cs[u] *= live;
+                sn[u] *= live;
             }
+            uint2 ch, cl, sh, sl;
+            split4(cs[0], cs[1], cs[2], cs[3], ch, cl);
+            split4(sn[0], sn[1], sn[2], sn[3], sh, sl);
             const size_t blk = ((size_t)nt * nkb + kb) * TC_BLOCK_BYTES;
-            const uint32_t o0 = swz_offset(2 * b_loc, chunk * 8);
-            const uint32_t o1 = swz_offset(2 * b_loc + 1, chunk * 8);
-            __stcs(reinterpret_cast<uint4*>(B_hi + blk + o0), hr);
-            __stcs(reinterpret_cast<uint4*>(B_lo + blk + o0), lr);
-            __stcs(reinterpret_cast<uint4*>(B_hi + blk + o1), hi_);
-            __stcs(reinterpret_cast<uint4*>(B_lo + blk + o1), li_);
+            const uint32_t oc = swz_offset(2 * b_loc, k0);
+            const uint32_t os = swz_offset(2 * b_loc + 1, k0);
+            __stcs(reinterpret_cast<uint2*>(B_hi + blk + oc), ch);
+            __stcs(reinterpret_cast<uint2*>(B_lo + blk + oc), cl);
+            __stcs(reinterpret_cast<uint2*>(B_hi + blk + os), sh);
+            __stcs(reinterpret_cast<uint2*>(B_lo + blk + os), sl);
         }
         // ---- A rows, one weight set per pass
         for (int ps = 0; ps < passes; ++ps) {
@@ -162,36 +168,37 @@ k_tables(const float4* __restrict__ cpos, const float4* __restrict__ cw, int64_t
             float4 w[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int jl = chunk * 4 + u;
-                const float4 v = jl < nc ? wset[c0 + jl] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 v = k0 + u < nc ? wset[c0 + k0 + u] : make_float4(0.f, 0.f, 0.f, 0.f);
                 w[u] = make_float4(v.x * wscale.x, v.y * wscale.y, v.z * wscale.z, v.w * wscale.w);
             }
             for (int g = r + 16 * ps; g < ngroups; g += 16 * passes) {
-                const int m0 = 4 * g;
-                const int a = m0 / nch;
-                const bool arow = a < ny;
+                const int a = g / spad;
+                const bool arow = a < nyg;
                 const float2 q = arow ? qy[a] : make_float2(0.f, 0.f);
                 const float on = arow ? 1.f : 0.f;
-                uint4 hi[4], lo[4];
-                uint32_t* hw = reinterpret_cast<uint32_t*>(hi);
-                uint32_t* lw = reinterpret_cast<uint32_t*>(lo);
+                float cs[4], sn[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    float sn, cs;
-                    sincospif(2.0f * turns_reduced(q, cp[u].x, cp[u].y), &sn, &cs);
-                    cs *= on;
-                    sn *= on;
-                    const float wv[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
-#pragma unroll
-                    for (int ch = 0; ch < 4; ++ch) split_h2(wv[ch] * cs, wv[ch] * sn, hw[4 * ch + u], lw[4 * ch + u]);
+                    sincospif(2.0f * turns_reduced(q, cp[u].x, cp[u].y), &sn[u], &cs[u]);
+                    cs[u] *= on;
+                    sn[u] *= on;
                 }
-                const int mt = m0 >> 7;
-                const size_t blk = ((size_t)mt * nkb + kb) * TC_BLOCK_BYTES;
+                const int m0 = 8 * g;
+                const size_t blk = ((size_t)(m0 >> 7) * nkb + kb) * TC_BLOCK_BYTES;
 #pragma unroll
-                for (int ch = 0; ch < 4; ++ch) {
-                    const uint32_t off = swz_offset((m0 & 127) + ch, chunk * 8);
-                    __stcs(reinterpret_cast<uint4*>(A_hi + blk + off), hi[ch]);
-                    __stcs(reinterpret_cast<uint4*>(A_lo + blk + off), lo[ch]);
+                for (int c = 0; c < 4; ++c) {
+                    float wv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) wv[u] = c == 0 ? w[u].x : c == 1 ? w[u].y : c == 2 ? w[u].z : w[u].w;
+                    uint2 h, l;
+                    const uint32_t oc = swz_offset((m0 & 127) + 2 * c, k0);
+                    split4(wv[0] * cs[0], wv[1] * cs[1], wv[2] * cs[2], wv[3] * cs[3], h, l);
+                    __stcs(reinterpret_cast<uint2*>(A_hi + blk + oc), h);
+                    __stcs(reinterpret_cast<uint2*>(A_lo + blk + oc), l);
+                    const uint32_t os = swz_offset((m0 & 127) + 2 * c + 1, k0);
+                    split4(wv[0] * sn[0], wv[1] * sn[1], wv[2] * sn[2], wv[3] * sn[3], h, l);
+                    __stcs(reinterpret_cast<uint2*>(A_hi + blk + os), h);
+                    __stcs(reinterpret_cast<uint2*>(A_lo + blk + os), l);
                 }
             }
         }
@@ -236,17 +243,6 @@ __device__ __forceinline__ void cluster_sync()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// 1D bulk copy delivered to the same shared-memory offset of every CTA in
-// mask, each CTA's mbarrier at the same offset receiving the bytes
-__device__ __forceinline__ void bulk_g2s_mc(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar, uint16_t mask)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
-        "%4;" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
-        : "memory");
-}
-
 // Tensor copy of one box (row y of a 2D map whose rows are 128-byte table
 // rows; the box is 16 or 8 KB of one table block) into this CTA's shared
 // memory, its bytes completing on an mbarrier of the CTA pair that may be
@@ -267,16 +263,6 @@ __device__ __forceinline__ uint32_t mbar_cluster_addr(uint64_t* bar, uint32_t ct
     uint32_t remote;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(bar)), "r"(cta));
     return remote;
-}
-
-// arrive (once MMAs complete) on the mbarrier at this offset in every CTA of mask
-__device__ __forceinline__ void tc_commit_mc(uint64_t* bar, uint16_t mask)
-{
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(mask)
-        : "memory");
 }
 
 // Packed FP32x2 arithmetic (sm_100+): two lanes of a 64-bit register, RN.
@@ -320,19 +306,6 @@ __device__ __forceinline__ float2 tf_add(float ah, float al, float bh, float bl)
     return make_float2(s, e - (s - h));
 }
 
-// (hi, lo) pairs of a two-float complex value renormalised by TwoSum (the
-// low word of a GEMM result may hold whole chunk partials)
-__device__ __forceinline__ float4 tf_norm4(float4 v)
-{
-    float s = v.x + v.y, bb = s - v.x;
-    const float er = (v.x - (s - bb)) + (v.y - bb);
-    const float re = s;
-    s = v.z + v.w;
-    bb = s - v.z;
-    const float ei = (v.z - (s - bb)) + (v.w - bb);
-    return make_float4(re, er, s, ei);
-}
-
 // two-float complex (re hi, re lo, im hi, im lo) sum
 __device__ __forceinline__ float4 tf_add4(float4 a, float4 b)
 {
@@ -343,33 +316,15 @@ __device__ __forceinline__ float4 tf_add4(float4 a, float4 b)
 
 __device__ __forceinline__ float f2_lane1(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
 
-// arrive (once this thread's MMAs complete) on the mbarrier at this offset
-// in every CTA of mask (CG = 2: the CTA pair)
-template <int CG>
-__device__ __forceinline__ void tc_commit_to(uint64_t* bar, uint16_t mask)
-{
-    if constexpr (CG == 2)
-        asm volatile(
-            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                smem_u32(bar)),
-            "h"(mask)
-            : "memory");
-    else
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-                smem_u32(bar)),
-            "h"(mask)
-            : "memory");
-}
-
-__device__ __forceinline__ void tc_mma2_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                            uint32_t accumulate)
+// two-SM MMA: arrive (once this thread's MMAs complete) on the mbarrier at
+// this offset in the CTAs of the pair named by mask (bit 0 even, bit 1 odd;
+// a barrier signal into each CTA's own shared memory, no data moves)
+__device__ __forceinline__ void tc_commit_pair(uint64_t* bar, uint16_t mask)
 {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
         : "memory");
 }
 
@@ -444,37 +399,27 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity
 // Its two-float result either goes, unscaled, to the partial tile P[slot]
 // (128 x 128: column pairs outermost, rows innermost) for k_gemm_reduce, or
 // -- when the item covers the whole k-range of its output (slot < 0) -- is
-// scaled and stored (first piece) or added into the amplitudes F[-1 - slot]
-// (FbView layout; no partial tile, no reduction pass).  Both layouts put
-// the row index innermost, so the 32 rows of an epilogue warp go out as
-// contiguous 512-byte stores.
+// combined into amplitudes, scaled and stored (first piece) or added into
+// F[-1 - slot] (FbView layout; no partial tile, no reduction pass).
 //
 // MODE 0: one CTA per item, tcgen05.mma.cta_group::1 with M = N = 128.
-//
-// MODE 1: clusters of two CTAs that share the A operand.  A pair item
-// covers the B tiles 2*nt and 2*nt + 1 of the same A tile and k-range; each
-// CTA copies one half (64 rows) of the A_hi and A_lo blocks and multicasts
-// it into both CTAs' stage, and loads its own B tile.  A stage is refilled
-// only after both CTAs' MMAs consumed it (multicast commit onto both
-// "empty" barriers).
 //
 // MODE 2: the two-SM MMA.  A pair item covers the A tiles 2*mt and 2*mt + 1
 // and one B tile: tcgen05.mma.cta_group::2 with M = 256, N = 128, issued by
 // the even CTA, reads the A tile of each CTA and the B tile split in two
 // 64-row halves, one in each CTA's shared memory, and accumulates each CTA's
 // 128 rows in its own TMEM.  A stage is 48 KB per SM instead of 64 KB and an
-// MMA reads 6 KB of shared memory per 128 x 128 x 16 product instead of 8 KB,
-// which is the resource the single-CTA form runs out of; the 48 KB stages
-// also make room for a fourth stage.  The even CTA's "stage full" barrier
-// counts the bytes of both CTAs: the odd CTA loads its operands with tensor
-// copies of the CTA pair (cta_group::2) that complete on the even CTA's
-// barrier, so the MMA issuer waits on one barrier.  The odd CTA's epilogue
-// warps release accumulators on the even CTA's barrier.
+// MMA reads 6 KB of shared memory per 128 x 128 x 16 product instead of 8 KB;
+// the 48 KB stages also make room for a fourth stage.  The even CTA's "stage
+// full" barrier counts the bytes of both CTAs: the odd CTA loads its
+// operands with tensor copies of the CTA pair (cta_group::2) that complete
+// on the even CTA's barrier, so the MMA issuer waits on one barrier.  The odd
+// CTA's epilogue warps release accumulators on the even CTA's barrier.
 struct GemmItem {
-    int32_t mt, nt;       // A / B tile rows (MODE 1: nt indexes B tile pairs, MODE 2: mt indexes A tile pairs)
+    int32_t mt, nt;       // A / B tile rows (MODE 2: mt indexes A tile pairs)
     int32_t kb0, kb1;     // k-block range (within this chunk's tables)
-    int32_t slot;         // output slot in P (clusters: of rank 0); < 0: direct to output -1 - slot
-    int32_t slot1;        // clusters: output slot of rank 1 (direct: equal to slot)
+    int32_t slot;         // output slot in P (pairs: of rank 0); < 0: direct to output -1 - slot
+    int32_t slot1;        // pairs: output slot of rank 1 (direct: equal to slot)
     int32_t store;        // direct: 1 = first piece of its output (store), 0 = add
     int32_t two;          // direct: 1 = the output has several pieces (two-float, both planes)
 };
@@ -488,12 +433,12 @@ struct GemmArgs {
     const GemmItem* items;
     int n_items;
     int kcb;              // k-blocks per TMEM chunk (drain interval)
-    double* P;            // [slots][64 column pairs][128 rows] float4 (re hi, re lo, im hi, im lo)
+    double* P;            // [slots][64 column pairs][128 rows] float4 (col 2j hi, lo, col 2j+1 hi, lo)
     double* F;            // direct outputs, high plane: [out][nz][nch * ny] float2 (FbView layout)
     int64_t lo_off;       // float2 from the high to the low plane
-    int ny, nz;
+    AxisMap ax;
     int nch;              // channels per output (4 per weight set), a power of two
-    double scale[4];      // direct outputs: per-channel scale of the unscaled sums
+    float scale[4];       // direct outputs: per-channel scale of the unscaled sums (powers of two)
     int32_t* err;
     uint64_t limit_ns;
     int mtiles, ntiles;   // tile rows of A and B (table layout)
@@ -507,6 +452,27 @@ struct GemmCfg {
     static constexpr int CG = MODE == 2 ? 2 : 1;
 };
 
+// Amplitudes at (s_y q_y, s_z q_z) from the four real sums (each a two-float
+// (hi, lo) pair): F = (cc - s_y s_z ss) - i (s_z cs + s_y sc).  Rounded to
+// FP32 (re, im); the two differences are taken word by word, so the rounding
+// error is about 2^-23 |F| plus 2^-24 of the low words.
+__device__ __forceinline__ float2 combine_f32(float2 cc, float2 cs, float2 sc, float2 ss, float sy, float sz)
+{
+    const float k = -sy * sz;
+    const float re = fmaf(k, ss.x, cc.x) + fmaf(k, ss.y, cc.y);
+    const float im = -(fmaf(sz, cs.x, sy * sc.x) + fmaf(sz, cs.y, sy * sc.y));
+    return make_float2(re, im);
+}
+
+// The same as a normalised two-float complex value (re hi, re lo, im hi, im lo).
+__device__ __forceinline__ float4 combine_tf(float2 cc, float2 cs, float2 sc, float2 ss, float sy, float sz)
+{
+    const float k = -sy * sz;
+    const float2 re = tf_add(cc.x, cc.y, k * ss.x, k * ss.y);
+    const float2 im = tf_add(-sz * cs.x, -sz * cs.y, -sy * sc.x, -sy * sc.y);
+    return make_float4(re.x, re.y, im.x, im.y);
+}
+
 // tmA / tmB (MODE 2): 2D maps over the chunk's tables as 128-byte rows,
 // boxes of 128 rows (an A block) and 64 rows (half a B block)
 template <int MODE>
@@ -514,7 +480,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_f16x3(const GemmArgs g, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB)
 {
     using C = GemmCfg<MODE>;
-    constexpr bool CLUSTER = MODE != 0;
+    constexpr bool CLUSTER = MODE == 2;
     constexpr int STG = C::STAGES;
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[STG];     // MODE 2, even CTA: both CTAs' stage bytes
@@ -535,7 +501,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STG; ++s) {
             mbar_init(&bar_full[s], 1);
-            mbar_init(&bar_empty[s], MODE == 1 ? 2 : 1);
+            mbar_init(&bar_empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&bar_acc_full[b], 1);
@@ -573,7 +539,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     const uint32_t st = sbase + (uint32_t)s * C::STAGE_BYTES;
                     const int mt = MODE == 2 ? 2 * item.mt + rank : item.mt;
-                    const int nt = MODE == 1 ? 2 * item.nt + rank : item.nt;
+                    const int nt = item.nt;
                     if (MODE == 2 && rank == 1) {
                         // table rows (128 B each) of this CTA's A block and B half
                         const int32_t nk = (int32_t)g.nkb;
@@ -595,15 +561,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const size_t ao = ((size_t)mt * g.nkb + kb) * TC_BLOCK_BYTES;
                     // MODE 2: this CTA's 64-row half of the B block
                     const size_t bo = ((size_t)nt * g.nkb + kb) * TC_BLOCK_BYTES + (MODE == 2 ? rank * C::B_BYTES : 0);
-                    if (MODE == 1) {
-                        const uint32_t h = (uint32_t)rank * (TC_BLOCK_BYTES / 2);
-                        bulk_g2s_mc(st + h, g.A_hi + ao + h, TC_BLOCK_BYTES / 2, &bar_full[s], (uint16_t)3);
-                        bulk_g2s_mc(st + TC_BLOCK_BYTES + h, g.A_lo + ao + h, TC_BLOCK_BYTES / 2, &bar_full[s],
-                                    (uint16_t)3);
-                    } else {
-                        bulk_g2s(st, g.A_hi + ao, TC_BLOCK_BYTES, &bar_full[s]);
-                        bulk_g2s(st + TC_BLOCK_BYTES, g.A_lo + ao, TC_BLOCK_BYTES, &bar_full[s]);
-                    }
+                    bulk_g2s(st, g.A_hi + ao, TC_BLOCK_BYTES, &bar_full[s]);
+                    bulk_g2s(st + TC_BLOCK_BYTES, g.A_lo + ao, TC_BLOCK_BYTES, &bar_full[s]);
                     bulk_g2s(st + 2 * TC_BLOCK_BYTES, g.B_hi + bo, C::B_BYTES, &bar_full[s]);
                     bulk_g2s(st + 2 * TC_BLOCK_BYTES + C::B_BYTES, g.B_lo + bo, C::B_BYTES, &bar_full[s]);
                     ++i;
@@ -679,15 +638,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                                first ? 0u : 1u);
                             first = false;
                         }
-                        if (MODE == 0) tc_commit(&bar_empty[s]);
-                        else tc_commit_to<C::CG>(&bar_empty[s], (uint16_t)3);
+                        if (MODE == 2) tc_commit_pair(&bar_empty[s], (uint16_t)3);
+                        else tc_commit(&bar_empty[s]);
                         if (++s == STG) {
                             s = 0;
                             sph ^= 1u;
                         }
                     }
                     if (!ok) break;
-                    if (MODE == 2) tc_commit_to<2>(&bar_acc_full[b], (uint16_t)3);
+                    if (MODE == 2) tc_commit_pair(&bar_acc_full[b], (uint16_t)3);
                     else tc_commit(&bar_acc_full[b]);
                 }
             }
@@ -696,7 +655,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 atomicExch(g.err, 2);
             }
             // every MMA issued by this thread completes before TMEM is freed
-            if (MODE == 2) tc_commit_to<2>(&bar_final, (uint16_t)1);
+            if (MODE == 2) tc_commit_pair(&bar_final, (uint16_t)1);
             else tc_commit(&bar_final);
             mbar_wait_drain(&bar_final, 0);
         }
@@ -754,8 +713,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     // pace the drain: four drain warps share each scheduler with
                     // the producer or MMA thread; a short yield per column
                     // group keeps the single MMA-issuing thread from waiting
-                    // behind their bursts (GEMM -4 % on the 512^2 box).  Not
-                    // in the two-SM form, whose MMAs wait for both CTAs' drains.
+                    // behind their bursts.  Not in the two-SM form, whose MMAs
+                    // wait for both CTAs' drains.
                     if (MODE != 2) __nanosleep(8 * TC_DRAIN_W);
                 }
 #if TC_RENORM > 0
@@ -793,42 +752,69 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     out[i * TC_BM] =
                         make_float4(f2_lane0(hi[i]), f2_lane0(lo[i]), f2_lane1(hi[i]), f2_lane1(lo[i]));
             } else {
-                // the whole k-range of this output: row m = nch a + c, columns
-                // n = 2b + (re, im) for 16 consecutive b, into F
+                // the whole k-range of this output.  Row mg = 2 (nch a + c) + p:
+                // the lanes 2i, 2i + 1 of a warp hold the cos and sin rows of
+                // one (a, c); columns 2b + r hold cos, sin of q_z,b.  Each lane
+                // takes its partner's pair and writes one or two amplitudes:
+                // on a symmetric q_y axis lane p = 0 writes +q_y and lane 1
+                // the mirrored -q_y node (both q_z signs where q_z is
+                // symmetric); otherwise lane 0 writes +q_z and lane 1 -q_z.
+                const AxisMap& ax = g.ax;
                 const int mtile = MODE == 2 ? 2 * item.mt + rank : item.mt;
-                const int ntile = MODE == 1 ? 2 * item.nt + rank : item.nt;
-                const int m = mtile * TC_BM + quad * 32 + lane;
-                const int a = m / g.nch, ch = m & (g.nch - 1);
-                const int b0 = (ntile * TC_BN + colh) >> 1;
-                if (a < g.ny) {
-                    // F_b layout: output, then q_z, then row m (a warp's 32
-                    // rows are contiguous)
-                    const int64_t mrows = (int64_t)g.nch * g.ny;
-                    float2* oh = reinterpret_cast<float2*>(g.F) + (int64_t)(-1 - slot) * g.nz * mrows +
-                                 (int64_t)b0 * mrows + m;
-                    float2* ol = oh + g.lo_off;
-                    const int c4 = ch & 3;
-                    // a power of two, exact in FP32 (checked at plan creation)
-                    const float sc =
-                        (float)(c4 == 0 ? g.scale[0] : c4 == 1 ? g.scale[1] : c4 == 2 ? g.scale[2] : g.scale[3]);
+                const int mg = mtile * TC_BM + quad * 32 + lane;
+                const int p = mg & 1;
+                const int qi = mg >> 1;
+                const int ag = qi / g.nch, ch = qi & (g.nch - 1);
+                const int b0 = (item.nt * TC_BN + colh) >> 1;       // GEMM q_z index of column pair 0
+                const int64_t mrows = (int64_t)g.nch * ax.ny;
+                float2* Fo = reinterpret_cast<float2*>(g.F) + (int64_t)(-1 - slot) * ax.nz * mrows + ch;
+                // this lane's q_y node and sign, and which q_z signs it writes
+                float sy = 1.f;
+                int a_out = ax.hy + ag;
+                bool act = ag < ax.nyg;
+                int zfirst = 0, zlast = ax.mz ? 1 : 0;          // 0: +q_z, 1: -q_z
+                if (ax.my) {
+                    if (p) {
+                        sy = -1.f;
+                        a_out = ax.ny - 1 - ax.hy - ag;
+                        act = act && a_out != ax.hy + ag;      // q_y = 0 is its own mirror
+                    }
+                } else {
+                    zfirst = zlast = p;
+                    act = act && (p == 0 || ax.mz);
+                }
+                const float sc = g.scale[ch & 3];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        if (b0 + i < g.nz) {
-                            float4 v = make_float4(sc * f2_lane0(hi[i]), sc * f2_lane0(lo[i]), sc * f2_lane1(hi[i]),
-                                                   sc * f2_lane1(lo[i]));
-                            if (item.two) {
-                                if (!item.store) {
-                                    const float2 h = oh[i * mrows], l = ol[i * mrows];
-                                    v = tf_add4(v, make_float4(h.x, l.x, h.y, l.y));
-                                } else {
-                                    v = tf_norm4(v);   // high word = the value rounded to FP32
-                                }
-                                oh[i * mrows] = make_float2(v.x, v.z);
-                                ol[i * mrows] = make_float2(v.y, v.w);
-                            } else {
-                                // the output's only piece: its value rounded to FP32
-                                oh[i * mrows] = make_float2(v.x + v.y, v.z + v.w);
+                for (int i = 0; i < 16; ++i) {
+                    // partner pair: all lanes take part in the exchange
+                    const uint64_t ph = __shfl_xor_sync(0xffffffffu, hi[i], 1);
+                    const uint64_t pl = __shfl_xor_sync(0xffffffffu, lo[i], 1);
+                    const float2 xc = make_float2(f2_lane0(hi[i]), f2_lane0(lo[i]));   // own row x cos(q_z Z)
+                    const float2 xs = make_float2(f2_lane1(hi[i]), f2_lane1(lo[i]));   // own row x sin(q_z Z)
+                    const float2 yc = make_float2(f2_lane0(ph), f2_lane0(pl));
+                    const float2 ys = make_float2(f2_lane1(ph), f2_lane1(pl));
+                    const float2 cc = p ? yc : xc, cs = p ? ys : xs, scs = p ? xc : yc, ss = p ? xs : ys;
+                    const int bg = b0 + i;
+                    if (!act || bg >= ax.nzg) continue;
+                    for (int zs = zfirst; zs <= zlast; ++zs) {
+                        const float sz = zs ? -1.f : 1.f;
+                        const int b_out = zs ? ax.nz - 1 - ax.hz - bg : ax.hz + bg;
+                        if (zs && b_out == ax.hz + bg) continue;     // q_z = 0 is its own mirror
+                        float2* oh = Fo + (int64_t)b_out * mrows + (int64_t)g.nch * a_out;
+                        if (item.two) {
+                            float4 v = combine_tf(cc, cs, scs, ss, sy, sz);
+                            v = make_float4(sc * v.x, sc * v.y, sc * v.z, sc * v.w);
+                            float2* ol = oh + g.lo_off;
+                            if (!item.store) {
+                                const float2 h = *oh, l = *ol;
+                                v = tf_add4(v, make_float4(h.x, l.x, h.y, l.y));
                             }
+                            *oh = make_float2(v.x, v.z);
+                            *ol = make_float2(v.y, v.w);
+                        } else {
+                            // the output's only piece: its value rounded to FP32
+                            const float2 v = combine_f32(cc, cs, scs, ss, sy, sz);
+                            *oh = make_float2(sc * v.x, sc * v.y);
                         }
                     }
                 }
@@ -837,17 +823,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (CLUSTER) cluster_sync();    // no multicast, MMA or remote arrival can still target this CTA
+    if (CLUSTER) cluster_sync();    // no MMA, commit or remote arrival can still target this CTA
     tc_fence_after();
     if (warp == 1) tc_dealloc<C::CG>(taddr, 512);
 }
 
 // Reduction of item tiles (two-float elements) into per-output amplitudes
-// (two-float complex; stored by an output's first piece, added by later ones):
-//   F[out][b][m] (+)= scale_{c mod 4} * sum_{s < splits} P[slot_base + (mt*ntiles + nt)*splits + s][j][row]
-// with m = nch*a + c = mt*128 + row, column pair j = b mod 64, nt = b / 64
-// (the tile column n = 2b + r).  Threads run over m fastest, so both the
-// tile reads and the F writes are contiguous.
+// (two-float complex; stored by an output's first piece, added by later ones).
+// Thread (output r, GEMM q_z index b, pair qi = nch a + c) sums the splits of
+// the tile rows 2 qi (cos q_y Y: cc, cs) and 2 qi + 1 (sin q_y Y: sc, ss) at
+// column pair j = b mod 64 of B tile b / 64, then writes the amplitudes of
+// every sign combination of the symmetric axes:
+//   F[out][b_out][nch a_out + c] (+)= scale_{c mod 4} ((cc - s_y s_z ss) - i (s_z cs + s_y sc)).
+// Threads run over qi fastest, so the tile reads and the F writes are
+// contiguous.
 struct RedDesc {
     int32_t slot_base;
     int32_t splits;
@@ -856,43 +845,60 @@ struct RedDesc {
 };
 
 struct Scale4 {
-    double v[4];
+    float v[4];
 };
 
-__global__ void k_gemm_reduce(const double* __restrict__ P, const RedDesc* __restrict__ reds, int n_red, int ny,
-                              int nz, int ntiles, int nch, Scale4 scale, double* __restrict__ F, int64_t lo_off)
+__global__ void k_gemm_reduce(const double* __restrict__ P, const RedDesc* __restrict__ reds, int n_red, AxisMap ax,
+                              int ntiles, int nch, Scale4 scale, double* __restrict__ F, int64_t lo_off)
 {
-    const int64_t mrows = (int64_t)nch * ny;
-    const int64_t per_out = mrows * nz;
+    const int64_t qrows = (int64_t)nch * ax.nyg;
+    const int64_t per_red = qrows * ax.nzg;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)n_red * per_out) return;
-    const int r = (int)(idx / per_out);
-    const int64_t rem = idx % per_out;
-    const int b = (int)(rem / mrows);
-    const int m = (int)(rem % mrows);
-    const int c = m & (nch - 1);
-    const int mt = m >> 7, row = m & 127, nt = b >> 6, j = b & 63;
+    if (idx >= (int64_t)n_red * per_red) return;
+    const int r = (int)(idx / per_red);
+    const int64_t rem = idx % per_red;
+    const int bg = (int)(rem / qrows);
+    const int qi = (int)(rem % qrows);
+    const int ag = qi / nch, c = qi & (nch - 1);
+    const int mg = 2 * qi;
+    const int mt = mg >> 7, row = mg & 127, nt = bg >> 6, j = bg & 63;
     const RedDesc d = reds[r];
     const int64_t base = (int64_t)d.slot_base + (int64_t)(mt * ntiles + nt) * d.splits;
     const float4* P4 = reinterpret_cast<const float4*>(P);
     // two-float sums in FP32 (FP64 is slow on GB300); the scale is a power
     // of two, exact in FP32
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int s = 0; s < d.splits; ++s)
-        acc = tf_add4(acc, P4[(base + s) * (TC_BM * TC_BN / 2) + (int64_t)j * TC_BM + row]);
-    const float sc = (float)scale.v[c & 3];
-    acc = make_float4(acc.x * sc, acc.y * sc, acc.z * sc, acc.w * sc);
-    float2* oh = reinterpret_cast<float2*>(F) + (int64_t)d.out * per_out + (int64_t)b * mrows + m;
-    if (d.store & 2) {
-        float2* ol = oh + lo_off;
-        if (!(d.store & 1)) {
-            const float2 h = *oh, l = *ol;
-            acc = tf_add4(acc, make_float4(h.x, l.x, h.y, l.y));
+    float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+    for (int s = 0; s < d.splits; ++s) {
+        const float4* t = P4 + (base + s) * (TC_BM * TC_BN / 2) + (int64_t)j * TC_BM + row;
+        a0 = tf_add4(a0, t[0]);
+        a1 = tf_add4(a1, t[1]);
+    }
+    const float2 cc = make_float2(a0.x, a0.y), cs = make_float2(a0.z, a0.w);
+    const float2 sc = make_float2(a1.x, a1.y), ss = make_float2(a1.z, a1.w);
+    const float f = scale.v[c & 3];
+    const int64_t mrows = (int64_t)nch * ax.ny;
+    float2* Fo = reinterpret_cast<float2*>(F) + (int64_t)d.out * ax.nz * mrows + c;
+    for (int ys = 0; ys <= ax.my; ++ys) {
+        const int a_out = ys ? ax.ny - 1 - ax.hy - ag : ax.hy + ag;
+        if (ys && a_out == ax.hy + ag) continue;        // q_y = 0 is its own mirror
+        for (int zs = 0; zs <= ax.mz; ++zs) {
+            const int b_out = zs ? ax.nz - 1 - ax.hz - bg : ax.hz + bg;
+            if (zs && b_out == ax.hz + bg) continue;
+            float4 v = combine_tf(cc, cs, sc, ss, ys ? -1.f : 1.f, zs ? -1.f : 1.f);
+            v = make_float4(f * v.x, f * v.y, f * v.z, f * v.w);
+            float2* oh = Fo + (int64_t)b_out * mrows + (int64_t)nch * a_out;
+            if (d.store & 2) {
+                float2* ol = oh + lo_off;
+                if (!(d.store & 1)) {
+                    const float2 h = *oh, l = *ol;
+                    v = tf_add4(v, make_float4(h.x, l.x, h.y, l.y));
+                }
+                *oh = make_float2(v.x, v.z);
+                *ol = make_float2(v.y, v.w);
+            } else {
+                *oh = make_float2(v.x + v.y, v.z + v.w);   // the output's only piece, rounded to FP32
+            }
         }
-        *oh = make_float2(acc.x, acc.z);
-        *ol = make_float2(acc.y, acc.w);
-    } else {
-        *oh = make_float2(acc.x + acc.y, acc.z + acc.w);   // the output's only piece, rounded to FP32
     }
 }
 
@@ -920,7 +926,7 @@ cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t* err, cudaStream_t s
 
 // ------------------------------------------------------------------ launchers
 cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, int64_t wstride, int nch, const int64_t* kb_cell0,
-                             const int32_t* kb_ncell, int64_t nkb, const float2* qy, int ny, const float2* qz, int nz,
+                             const int32_t* kb_ncell, int64_t nkb, const float2* qy, int nyg, const float2* qz, int nzg,
                              int mtiles, int ntiles, const float wscale[4], void* tab, cudaStream_t s)
 {
     uint8_t* A_hi = (uint8_t*)tab;
@@ -929,7 +935,7 @@ cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, int64_t wstri
     uint8_t* B_lo = B_hi + (size_t)ntiles * nkb * TC_BLOCK_BYTES;
     if (nkb <= 0) return cudaSuccess;
     k_tables<<<(unsigned)std::min<int64_t>(nkb, 0x7fffffff), TAB_THREADS, 0, s>>>(
-        cpos, cw, wstride, nch, kb_cell0, kb_ncell, qy, ny, qz, nz,
+        cpos, cw, wstride, nch, kb_cell0, kb_ncell, qy, nyg, qz, nzg,
         make_float4(wscale[0], wscale[1], wscale[2], wscale[3]), nkb, mtiles, ntiles, A_hi, A_lo, B_hi, B_lo);
     return cudaGetLastError();
 }
@@ -965,7 +971,7 @@ static cudaError_t encode_row_maps(const void* tab, int64_t rows, CUtensorMap* t
 }
 
 cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
-                           int grid, int kcb, double* P, double* F, int64_t lo_off, int ny, int nz, int nch,
+                           int grid, int kcb, double* P, double* F, int64_t lo_off, const AxisMap& ax, int nch,
                            const double scale[4], int32_t* err, uint64_t limit_ns, int mode, cudaStream_t s)
 {
     static_assert(GemmCfg<0>::STAGES * GemmCfg<0>::STAGE_BYTES == GemmCfg<2>::STAGES * GemmCfg<2>::STAGE_BYTES,
@@ -975,13 +981,11 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_gemm_f16x3<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_gemm_f16x3<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_gemm_f16x3<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    if (mode < 0 || mode > 2 || (mode != 0 && (grid & 1))) return cudaErrorInvalidValue;
+    if ((mode != 0 && mode != 2) || (mode == 2 && ((grid & 1) || (mtiles & 1)))) return cudaErrorInvalidValue;
     // MODE 2: tensor maps over the chunk's tables as rows of 128 bytes
     const int64_t rows = (int64_t)(2 * mtiles + 2 * ntiles) * nkb * (TC_BLOCK_BYTES / 128);
     CUtensorMap tm[2];
@@ -1003,10 +1007,9 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
     ga.P = P;
     ga.F = F;
     ga.lo_off = lo_off;
-    ga.ny = ny;
-    ga.nz = nz;
+    ga.ax = ax;
     ga.nch = nch;
-    for (int c = 0; c < 4; ++c) ga.scale[c] = scale[c];
+    for (int c = 0; c < 4; ++c) ga.scale[c] = (float)scale[c];
     ga.err = err;
     ga.limit_ns = limit_ns;
     ga.mtiles = mtiles;
@@ -1027,25 +1030,25 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return mode == 1 ? cudaLaunchKernelEx(&cfg, k_gemm_f16x3<1>, ga, tm[0], tm[1])
-                     : cudaLaunchKernelEx(&cfg, k_gemm_f16x3<2>, ga, tm[0], tm[1]);
+    return cudaLaunchKernelEx(&cfg, k_gemm_f16x3<2>, ga, tm[0], tm[1]);
 }
 
-cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, int ny, int nz, int ntiles, int nch,
+cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, const AxisMap& ax, int ntiles, int nch,
                              const double scale[4], double* F, int64_t lo_off, cudaStream_t s)
 {
     Scale4 sc;
-    for (int c = 0; c < 4; ++c) sc.v[c] = scale[c];
-    const int64_t n = (int64_t)n_red * nch * ny * nz;
+    for (int c = 0; c < 4; ++c) sc.v[c] = (float)scale[c];
+    const int64_t n = (int64_t)n_red * nch * ax.nyg * ax.nzg;
     if (n == 0) return cudaSuccess;   // every item of the chunk wrote its output directly
-    k_gemm_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, (const RedDesc*)reds, n_red, ny, nz, ntiles, nch, sc,
-                                                              F, lo_off);
+    k_gemm_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, (const RedDesc*)reds, n_red, ax, ntiles, nch, sc, F,
+                                                              lo_off);
     return cudaGetLastError();
 }
 
 size_t tc_item_bytes() { return sizeof(GemmItem); }
 size_t tc_red_bytes() { return sizeof(RedDesc); }
 size_t tc_block_bytes() { return TC_BLOCK_BYTES; }
+int tc_block_cells() { return TC_BK; }
 float tc_operand_scale() { return TC_SCALE; }
 
 }  // namespace nms

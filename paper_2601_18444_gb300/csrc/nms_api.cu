@@ -940,13 +940,19 @@ nms_status nms_plan_stage_ms(nms_plan_t plan, double ms[8], int64_t launches[8],
     return NMS_OK;
 }
 
-nms_status nms_plan_info(nms_plan_t plan, int32_t* precision, int32_t* kc_cells, int32_t* items_per_sm)
+nms_status nms_plan_info(nms_plan_t plan, int32_t* precision, int32_t* kc_cells, int32_t* items_per_sm,
+                         int32_t* gemm_form, int32_t* mirror_y, int32_t* mirror_z)
 {
     set_error("");
     if (!plan) return fail(NMS_ERR_INVALID_ARG, "plan is NULL");
     if (precision) *precision = plan->path;
     if (kc_cells) *kc_cells = tc_tuned_kc_cells(*plan);
     if (items_per_sm) *items_per_sm = tc_tuned_items_per_sm(*plan);
+    int32_t form = -1, my = 0, mz = 0;
+    tc_form_info(*plan, &form, &my, &mz);
+    if (gemm_form) *gemm_form = form;
+    if (mirror_y) *mirror_y = my;
+    if (mirror_z) *mirror_z = mz;
     return NMS_OK;
 }
 

@@ -74,6 +74,15 @@ struct FbView {
 #endif
 };
 
+// Detector axes of one tensor-path GEMM: the full grid (ny x nz), the first
+// node of the GEMM's part of each axis (hy, hz: 0, or the first q >= 0 node of
+// an axis symmetric about q = 0) and its length (nyg = ny - hy, nzg = nz - hz);
+// my, mz = 1: the axis is symmetric and the epilogue also writes the mirrored
+// nodes n - 1 - h - i (except a node that is its own mirror, q = 0).
+struct AxisMap {
+    int ny, nz, hy, hz, nyg, nzg, my, mz;
+};
+
 // ---------------------------------------------------------------- plan
 struct Plan {
     cudaStream_t stream = nullptr;
@@ -213,6 +222,9 @@ __device__ __forceinline__ int find_bin(const double* __restrict__ e, int nb, do
 nms_status direct_sum_range(Plan& p, const float4* cpos, int64_t c0, int64_t c1, double* out);
 int tc_tuned_kc_cells(const Plan& p);
 int tc_tuned_items_per_sm(const Plan& p);
+// GEMM form (0 one CTA per tile, 2 two-SM MMA; -1 without a tensor path) and
+// which detector axes the GEMM covers on their q >= 0 half only
+void tc_form_info(const Plan& p, int32_t* form, int32_t* mirror_y, int32_t* mirror_z);
 cudaError_t launch_grid(const nms_qgrid& g, int64_t np, const double* d_qlist, double* qy, double* qz, double* hy,
                         double* hz, double* qa, float4* qturn, cudaStream_t s);
 cudaError_t launch_obj_bin(const FbView& F, int n_out, const int32_t* out_obj, const Plan& p, const int32_t* bin_of,

@@ -32,16 +32,17 @@ namespace nms {
 
 // launchers in k_gemm.cu / k_batch.cu
 cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, int64_t wstride, int nch, const int64_t* kb_cell0,
-                             const int32_t* kb_ncell, int64_t nkb, const float2* qy, int ny, const float2* qz, int nz,
+                             const int32_t* kb_ncell, int64_t nkb, const float2* qy, int nyg, const float2* qz, int nzg,
                              int mtiles, int ntiles, const float wscale[4], void* tab, cudaStream_t s);
 cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
-                           int grid, int kcb, double* P, double* F, int64_t lo_off, int ny, int nz, int nch,
+                           int grid, int kcb, double* P, double* F, int64_t lo_off, const AxisMap& ax, int nch,
                            const double scale[4], int32_t* err, uint64_t limit_ns, int mode, cudaStream_t s);
-cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, int ny, int nz, int ntiles, int nch,
+cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, const AxisMap& ax, int ntiles, int nch,
                              const double scale[4], double* F, int64_t lo_off, cudaStream_t s);
 size_t tc_item_bytes();
 size_t tc_red_bytes();
 size_t tc_block_bytes();
+int tc_block_cells();
 float tc_operand_scale();
 cudaError_t launch_prep_rot(const Plan& p, const RotMat& R, bool global, float4* cpos, float4* cw, int64_t wstride,
                             cudaStream_t s);
@@ -59,7 +60,7 @@ cudaError_t launch_shift_factors(int n_out, const float4* cyz, const float2* qy,
 namespace {
 
 struct HostItem {
-    int32_t mt, nt, kb0, kb1, slot, slot1;   // clusters: mt (mode 2) or nt (mode 1) indexes a tile pair
+    int32_t mt, nt, kb0, kb1, slot, slot1;   // mode 2: mt indexes an A-tile pair
     int32_t store, two;                      // direct items: first piece of the output stores; two: several pieces
 };
 struct HostRed {
@@ -99,7 +100,8 @@ struct Schedule {
 
 struct TcState {
     int ny = 0, nz = 0, mtiles = 0, ntiles = 0;
-    float2* d_qy = nullptr;
+    AxisMap ax{};                // GEMM part of each detector axis (q >= 0 half of a symmetric axis)
+    float2* d_qy = nullptr;      // full grid: q_y / 2 pi two-float [ny]
     float2* d_qz = nullptr;
     double W[4] = {1, 1, 1, 1};
     int kcb = 2;
@@ -107,7 +109,7 @@ struct TcState {
     int nsets = 1;               // weight sets (loop mode), stacked along the GEMM rows
     int nch = 4;                 // channels per output: 4 x (weight sets rounded up to a power of two)
     int64_t wstride = 0;         // cells between weight sets in d_cw_b (= R_b * n)
-    int mode = 0;                // GEMM form: 0 one CTA, 1 pairs sharing A (even ntiles), 2 two-SM MMA (even mtiles)
+    int mode = 0;                // GEMM form: 0 one CTA per tile, 2 two-SM MMA over A-tile pairs (even mtiles)
     bool mode_forced = false;    // set by NMS_GEMM_MODE: the autotuner keeps it
     bool objects = false;        // per-object amplitudes (dilute split) with shifts
     int R_b = 1;                 // rotations prepared per rotation batch
@@ -198,6 +200,7 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
 {
     S.n_rot_local = n_rl;
     S.n_out = (int)sums.size();
+    const int64_t KBC = tc_block_cells();   // cells per k-block
     const int sms = device_sm_count();
     const int tiles = t.mtiles * t.ntiles;
     std::vector<int64_t> kb_cell0;
@@ -229,15 +232,15 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
             const Summand& sm = sums[o];
             int64_t c = sm.c0;
             while (c < sm.c1) {
-                int64_t room = (t.tab_kb - cur_kb) * 32;
+                int64_t room = (t.tab_kb - cur_kb) * KBC;
                 if (room <= 0) {
                     chunk_pieces.emplace_back();
                     cur_kb = 0;
-                    room = t.tab_kb * 32;
+                    room = t.tab_kb * KBC;
                 }
                 const int64_t take = std::min(room, sm.c1 - c);
                 chunk_pieces.back().push_back({o - o0, (int64_t)sm.rl * p.n_cells + c, take});
-                cur_kb += (take + 31) / 32;
+                cur_kb += (take + KBC - 1) / KBC;
                 c += take;
             }
         }
@@ -253,7 +256,7 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
             Chunk ch;
             ch.kb_off = (int64_t)kb_cell0.size();
             int64_t nkb_chunk = 0;
-            for (const Piece& pc : pieces) nkb_chunk += (pc.n + 31) / 32;
+            for (const Piece& pc : pieces) nkb_chunk += (pc.n + KBC - 1) / KBC;
             ch.nkb = nkb_chunk;
             // work items: about items_per_sm per SM, never shorter than 2 TMEM chunks
             const int64_t ips = t.items_per_sm;
@@ -264,19 +267,18 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
             int slot = 0;
             int64_t kb = 0;
             for (const Piece& pc : pieces) {
-                const int64_t nkb_p = (pc.n + 31) / 32;
+                const int64_t nkb_p = (pc.n + KBC - 1) / KBC;
                 for (int64_t i = 0; i < nkb_p; ++i) {
-                    kb_cell0.push_back(pc.g0 + 32 * i);
-                    kb_ncell.push_back((int32_t)std::min<int64_t>(32, pc.n - 32 * i));
+                    kb_cell0.push_back(pc.g0 + KBC * i);
+                    kb_ncell.push_back((int32_t)std::min<int64_t>(KBC, pc.n - KBC * i));
                 }
                 // (mt, nt) of the first tile of a work unit and its step to the partner tile
-                const int mstep = t.mode == 2 ? 2 : 1, nstep = t.mode == 1 ? 2 : 1;
+                const int mstep = t.mode == 2 ? 2 : 1, nstep = 1;
                 int splits = (int)((nkb_p + kb_per_item - 1) / kb_per_item);
                 if (splits > 1 && pieces.size() == 1) {
                     // one output in the chunk: round the split count up so the
                     // (tile unit x split) items fill whole waves of the
-                    // persistent CTAs (pairs), e.g. 64 pair units x 19 splits
-                    // = 16 waves of 76 clusters
+                    // persistent CTAs (pairs)
                     const int units = (t.mtiles / mstep) * (t.ntiles / nstep);
                     const int conc = t.mode ? sms / 2 : sms;
                     int gcd = units, rem = conc;
@@ -313,8 +315,8 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
                             const int64_t a = kb + (nkb_p * sp) / splits;
                             const int64_t b = kb + (nkb_p * (sp + 1)) / splits;
                             const int s0 = slot + (mt * t.ntiles + nt) * splits + sp;
-                            // slot of the partner tile: next B tile (mode 1) or next A tile (mode 2)
-                            const int s1 = t.mode == 1 ? s0 + splits : t.mode == 2 ? s0 + t.ntiles * splits : 0;
+                            // slot of the partner tile (mode 2): the next A tile
+                            const int s1 = t.mode == 2 ? s0 + t.ntiles * splits : 0;
                             its.push_back({mt / mstep, nt / nstep, (int32_t)a, (int32_t)b, s0, s1, 0, 0});
                         }
                 slot += tiles * splits;
@@ -440,10 +442,10 @@ nms_status tc_autotune(Plan& p, TcState& t)
                 c1 = p.h_off[k + 1];
             }
     }
-    c1 = std::min<int64_t>({c1, c0 + 131072, c0 + t.tab_kb * 32});
+    c1 = std::min<int64_t>({c1, c0 + 131072, c0 + t.tab_kb * tc_block_cells()});
     const int64_t nprobe = c1 - c0;
     char keybuf[256];
-    snprintf(keybuf, sizeof keybuf, "f16x3:%dx%d:cells%lld:sm%d:forms%d", t.ny, t.nz,
+    snprintf(keybuf, sizeof keybuf, "f16x3:%dx%d:half%dx%d:cells%lld:sm%d:forms%d", t.ny, t.nz, t.ax.nyg, t.ax.nzg,
              (long long)(64 - __builtin_clzll(nprobe)), sms, t.mode_forced ? t.mode : -1);
     const std::string key(keybuf);
     {
@@ -498,8 +500,7 @@ nms_status tc_autotune(Plan& p, TcState& t)
     const int ipss[3] = {4, 8, 16};
     std::vector<int> modes;
     for (int m = 0; m < 3; ++m)
-        if (t.mode_forced ? m == mode0
-                          : (m == 0 || (m == 1 && t.ntiles % 2 == 0) || (m == 2 && t.mtiles % 2 == 0)))
+        if (t.mode_forced ? m == mode0 : (m == 0 || (m == 2 && t.mtiles % 2 == 0)))
             modes.push_back(m);
     double* saveP = t.d_P;
     std::vector<TuneChoice> cand;
@@ -521,15 +522,16 @@ nms_status tc_autotune(Plan& p, TcState& t)
         const Chunk& ch = S.batches[0].chunks[0];
         const int64_t lo_off = fb_plane(t, 1);
         for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {
-            ce = tc_launch_tables(t.d_cpos_b, t.d_cw_b, t.wstride, t.nch, S.d_kb_cell0, S.d_kb_ncell, ch.nkb, t.d_qy,
-                                      t.ny, t.d_qz, t.nz, t.mtiles, t.ntiles, wscale, p.d_tab, s);
+            ce = tc_launch_tables(t.d_cpos_b, t.d_cw_b, t.wstride, t.nch, S.d_kb_cell0, S.d_kb_ncell, ch.nkb,
+                                  t.d_qy + t.ax.hy, t.ax.nyg, t.d_qz + t.ax.hz, t.ax.nzg, t.mtiles, t.ntiles, wscale,
+                                  p.d_tab, s);
             if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
             if (ce == cudaSuccess)
                 ce = tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles, S.d_items, ch.n_items, ch.grid, kcb, P,
-                                    d_Fp, lo_off, t.ny, t.nz, t.nch, scale, p.d_err, limit, t.mode, s);
+                                    d_Fp, lo_off, t.ax, t.nch, scale, p.d_err, limit, t.mode, s);
             if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
             if (ce == cudaSuccess)
-                ce = tc_launch_reduce(P, S.d_reds, ch.n_red, t.ny, t.nz, t.ntiles, t.nch, scale, d_Fp, lo_off, s);
+                ce = tc_launch_reduce(P, S.d_reds, ch.n_red, t.ax, t.ntiles, t.nch, scale, d_Fp, lo_off, s);
             if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
             float m = 0.f;
             if (ce == cudaSuccess) cudaEventElapsedTime(&m, e0, e1);
@@ -577,13 +579,21 @@ nms_status tc_autotune(Plan& p, TcState& t)
 int tc_tuned_kc_cells(const Plan& p)
 {
     const TcState* t = (const TcState*)p.tc_state;
-    return t ? 32 * t->kcb : 0;
+    return t ? tc_block_cells() * t->kcb : 0;
 }
 
 int tc_tuned_items_per_sm(const Plan& p)
 {
     const TcState* t = (const TcState*)p.tc_state;
     return t ? t->items_per_sm : 0;
+}
+
+void tc_form_info(const Plan& p, int32_t* form, int32_t* mirror_y, int32_t* mirror_z)
+{
+    const TcState* t = (const TcState*)p.tc_state;
+    *form = t ? t->mode : -1;
+    *mirror_y = t ? t->ax.my : 0;
+    *mirror_z = t ? t->ax.mz : 0;
 }
 
 nms_status tc_setup(Plan& p)
@@ -606,21 +616,34 @@ nms_status tc_setup(Plan& p)
         while (sp < t->nsets) sp <<= 1;
         t->nch = 4 * sp;
     }
-    t->mtiles = (t->nch * t->ny + 127) / 128;
-    t->ntiles = (2 * t->nz + 127) / 128;
-    t->kcb = p.opt.kc_cells > 0 ? std::max(1, p.opt.kc_cells / 32) : 2;
+    // an axis symmetric about q = 0 (lo = -hi, two or more nodes): the GEMM
+    // covers its q >= 0 half and the epilogue writes both signs
+    // (NMS_GRID_MIRROR=0 turns this off, for comparisons)
+    const char* mirror_env = getenv("NMS_GRID_MIRROR");
+    const bool mirror_ok = !(mirror_env && atoi(mirror_env) == 0);
+    t->ax.ny = t->ny;
+    t->ax.nz = t->nz;
+    t->ax.my = (mirror_ok && t->ny >= 2 && p.grid.lo0 == -p.grid.hi0) ? 1 : 0;
+    t->ax.mz = (mirror_ok && t->nz >= 2 && p.grid.lo1 == -p.grid.hi1) ? 1 : 0;
+    t->ax.hy = t->ax.my ? t->ny / 2 : 0;
+    t->ax.hz = t->ax.mz ? t->nz / 2 : 0;
+    t->ax.nyg = t->ny - t->ax.hy;
+    t->ax.nzg = t->nz - t->ax.hz;
+    // A rows: (q_y node, channel) x (cos, sin); B rows: q_z node x (cos, sin)
+    t->mtiles = (2 * t->nch * t->ax.nyg + 127) / 128;
+    t->ntiles = (2 * t->ax.nzg + 127) / 128;
+    t->kcb = p.opt.kc_cells > 0 ? std::max(1, p.opt.kc_cells / tc_block_cells()) : 2;
     if (p.opt.split_k > 0) t->items_per_sm = std::min(256, p.opt.split_k);
     t->objects = p.n_objects > 1 && p.opt.want_dilute;
-    // CTA pairs sharing A where the B tiles pair up, else one CTA per tile
-    // (the two measured within 1 %; the two-SM MMA writes fewer operand
-    // bytes into shared memory per stage, but each SM still reads the whole
-    // B tile, half of it from the peer, and it measured 20 % slower).
-    // NMS_GEMM_MODE = 0, 1 or 2 forces a form the grid allows (diagnostics,
-    // tests); the autotuner times all of them.
-    t->mode = (t->ntiles % 2 == 0) ? 1 : 0;
+    // One CTA per tile by default (the two-SM MMA writes fewer operand bytes
+    // into shared memory per stage, but each SM still reads the whole B tile,
+    // half of it from the peer, and it measured slower).  NMS_GEMM_MODE = 0
+    // or 2 forces a form the grid allows (diagnostics, tests); the autotuner
+    // times both.
+    t->mode = 0;
     if (const char* gm = getenv("NMS_GEMM_MODE")) {
         const int want = atoi(gm);
-        if (want == 0 || (want == 1 && t->ntiles % 2 == 0) || (want == 2 && t->mtiles % 2 == 0)) {
+        if (want == 0 || (want == 2 && t->mtiles % 2 == 0)) {
             t->mode = want;
             t->mode_forced = true;
         }
@@ -687,10 +710,11 @@ nms_status tc_setup(Plan& p)
     const int64_t budget = p.opt.workspace_bytes > 0 ? p.opt.workspace_bytes
                                                      : (int64_t)std::min<size_t>(free_b / 3, (size_t)8 << 30);
     int64_t total_kb = 0;
+    const int64_t kbc = tc_block_cells();
     if (t->objects) {
-        for (int64_t k = 0; k < p.n_objects; ++k) total_kb += (p.h_off[k + 1] - p.h_off[k] + 31) / 32;
+        for (int64_t k = 0; k < p.n_objects; ++k) total_kb += (p.h_off[k + 1] - p.h_off[k] + kbc - 1) / kbc;
     } else {
-        total_kb = (n + 31) / 32;
+        total_kb = (n + kbc - 1) / kbc;
     }
     total_kb *= t->R_b;
     t->tab_kb = std::max<int64_t>(1, std::min<int64_t>(total_kb, budget / per_kb));
@@ -759,18 +783,18 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
             for (const Chunk& ch : ob.chunks) {
                 p.timer.begin(ST_TABLES);
                 NMS_CUDA_TRY(tc_launch_tables(t.d_cpos_b, t.d_cw_b, t.wstride, t.nch, S.d_kb_cell0 + ch.kb_off,
-                                              S.d_kb_ncell + ch.kb_off, ch.nkb, t.d_qy, t.ny, t.d_qz, t.nz, t.mtiles,
-                                              t.ntiles, wscale, p.d_tab, s));
+                                              S.d_kb_ncell + ch.kb_off, ch.nkb, t.d_qy + t.ax.hy, t.ax.nyg,
+                                              t.d_qz + t.ax.hz, t.ax.nzg, t.mtiles, t.ntiles, wscale, p.d_tab, s));
                 p.timer.end(ST_TABLES, 1);
                 p.timer.begin(ST_GEMM);
                 NMS_CUDA_TRY(tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles,
                                             (const char*)S.d_items + ch.item_off * tc_item_bytes(), ch.n_items, ch.grid,
-                                            t.kcb, t.d_P, t.d_Fb, lo_off, t.ny, t.nz, t.nch, scale, p.d_err, limit,
-                                            t.mode, s));
+                                            t.kcb, t.d_P, t.d_Fb, lo_off, t.ax, t.nch, scale, p.d_err, limit, t.mode,
+                                            s));
                 p.timer.end(ST_GEMM, 1);
                 p.timer.begin(ST_REDUCE);
-                NMS_CUDA_TRY(tc_launch_reduce(t.d_P, (const char*)S.d_reds + ch.red_off * tc_red_bytes(), ch.n_red, t.ny,
-                                              t.nz, t.ntiles, t.nch, scale, t.d_Fb, lo_off, s));
+                NMS_CUDA_TRY(tc_launch_reduce(t.d_P, (const char*)S.d_reds + ch.red_off * tc_red_bytes(), ch.n_red, t.ax,
+                                              t.ntiles, t.nch, scale, t.d_Fb, lo_off, s));
                 p.timer.end(ST_REDUCE, ch.n_red > 0 ? 1 : 0);
             }
             p.timer.begin(ST_GACC);

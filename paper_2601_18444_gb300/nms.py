@@ -89,8 +89,7 @@ SIGNATURES = {
     "nms_surrogate_load": (ctypes.c_int, [_V, ctypes.c_char_p]),
     "nms_surrogate_destroy": (ctypes.c_int, [_V]),
     "nms_dsft_direct_noalloc": (ctypes.c_int, [ctypes.c_int64, _V, _V, _V, ctypes.c_int64, _V, _V, _V, _V]),
-    "nms_plan_info": (ctypes.c_int, [_V, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
-                                     ctypes.POINTER(ctypes.c_int32)]),
+    "nms_plan_info": (ctypes.c_int, [_V] + [ctypes.POINTER(ctypes.c_int32)] * 6),
     "nms_select_set": (ctypes.c_int, [_V, ctypes.c_int32]),
     "nms_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int64, _V]),
     "nms_plan_destroy": (ctypes.c_int, [_V]),
@@ -473,10 +472,11 @@ def nms_dsft_direct_noalloc(Y, Z, w, qy, qz, F, stream=None):
 
 
 def nms_plan_info(plan):
-    """dict(precision, kc_cells, items_per_sm) the plan settled on."""
-    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-    _check(load().nms_plan_info(plan.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-    return {"precision": a.value, "kc_cells": b.value, "items_per_sm": c.value}
+    """dict(precision, kc_cells, items_per_sm, gemm_form, mirror=(y, z)) the plan settled on."""
+    v = [ctypes.c_int32() for _ in range(6)]
+    _check(load().nms_plan_info(plan.handle, *[ctypes.byref(x) for x in v]))
+    return {"precision": v[0].value, "kc_cells": v[1].value, "items_per_sm": v[2].value, "gemm_form": v[3].value,
+            "mirror": (v[4].value, v[5].value)}
 
 
 def nms_plan_destroy(plan):

@@ -366,9 +366,13 @@ nms_status nms_surrogate_destroy(nms_surrogate_t s);
  * every GPU that loads libnms until the process exits), so n_q is limited to
  * 262144 points (a 512 x 512 detector); larger n_q returns
  * NMS_ERR_INVALID_ARG.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress) and caches it: make that first call
- * before any stream capture.  All calls share the array, so calls whose
- * kernels can overlap on the GPU (different streams without ordering) race.
+ * device address (cudaGetSymbolAddress) and caches it with the device's
+ * current context: make that first call before any stream capture.  The
+ * cached address does not outlive its context: a call that finds a new
+ * context (after cudaDeviceReset) looks it up again, so make the first call
+ * after a reset outside a capture too.  All calls share the array, so calls
+ * whose kernels can overlap on the GPU (different streams without ordering)
+ * race.  n_cells = 0 writes zeros; n_q = 0 does nothing.
  * Asynchronous on cuda_stream; no cudaMalloc, cudaFree or other allocating
  * call is made. */
 nms_status nms_dsft_direct_noalloc(int64_t n_cells, const double* Y, const double* Z, const double* w,

@@ -7,6 +7,11 @@ mean-squared error 0.5 (y - t)^2 averaged over the batch and the outputs on
 standardised targets t = (T - mean) / std, and its exact gradient by the
 chain rule.  Flat parameter layout: W1[H][n_in] b1[H] W2[H][H] b2[H]
 W3[n_out][H] b3[n_out].  Pinned by finite differences and closed forms.
+
+``grad_magnitude`` gives, per parameter, the sum over the batch of the
+absolute values of the terms whose signed sum is that gradient (the same
+chain rule with |.| on every factor): the scale an element-by-element
+comparison of a low-precision gradient is measured against.
 """
 import numpy as np
 
@@ -67,3 +72,22 @@ def loss_and_grad(theta, X, T, x_lo, x_hi, y_mean, y_std, nin, H, nout):
     gb1 = dZ1.sum(0)
     g = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3])
     return loss, g
+
+
+def grad_magnitude(theta, X, T, x_lo, x_hi, y_mean, y_std, nin, H, nout):
+    """Per parameter: sum over samples of |term| of its gradient sum (flat,
+    same layout as the gradient)."""
+    W1, b1, W2, b2, W3, b3 = split(theta, nin, H, nout)
+    f = forward(theta, X, x_lo, x_hi, nin, H, nout)
+    t = (np.asarray(T, np.float64) - y_mean) / y_std
+    B = f["Y"].shape[0]
+    aY = np.abs(f["Y"] - t) / (B * nout)
+    mW3 = aY.T @ np.abs(f["H2"])
+    mb3 = aY.sum(0)
+    aZ2 = (aY @ np.abs(W3)) * np.abs(silu_grad(f["Z2"]))
+    mW2 = aZ2.T @ np.abs(f["H1"])
+    mb2 = aZ2.sum(0)
+    aZ1 = (aZ2 @ np.abs(W2)) * np.abs(silu_grad(f["Z1"]))
+    mW1 = aZ1.T @ np.abs(f["Xn"])
+    mb1 = aZ1.sum(0)
+    return np.concatenate([mW1.ravel(), mb1, mW2.ravel(), mb2, mW3.ravel(), mb3])

@@ -13,7 +13,11 @@
 // (16 MiB).  Every GPU that loads libnms keeps those 16 MiB until the process
 // exits.  Host code cannot use the array's name as a device address, so the
 // first call on each device looks the address up with cudaGetSymbolAddress
-// (with that device current) and caches it; make that first call before any
+// (with that device current) and caches it together with the device's
+// current context; make that first call before any stream capture.  A call
+// that finds another context current on the device (after cudaDeviceReset,
+// or a primary context torn down and created again) looks the address up
+// again instead of using the cached one; that call, too, belongs outside a
 // stream capture.  All calls share the array: two calls whose kernels overlap
 // on the GPU (different streams, no ordering between them) race on it.
 #include <cuda_runtime.h>
@@ -36,9 +40,31 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
 
 static double* g_scratch_addr[NOALLOC_MAX_DEVICES];
+static void* g_scratch_ctx[NOALLOC_MAX_DEVICES];   // context the cached address belongs to
 static std::mutex g_scratch_mu;
 
-// Device address of the scratch array on the current device (looked up once).
+// The driver's current context (cuCtxGetCurrent through the runtime's
+// driver entry point; no link-time dependency on libcuda).
+static void* current_context()
+{
+    typedef int (*GetCurrent)(void**);
+    static GetCurrent fn = nullptr;
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !f) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        fn = (GetCurrent)f;
+    }
+    void* ctx = nullptr;
+    return fn(&ctx) == 0 ? ctx : nullptr;
+}
+
+// Device address of the scratch array on the current device: looked up once
+// per device and context, with that device current.
 static nms_status scratch_address(double** out)
 {
     int dev = 0;
@@ -49,11 +75,15 @@ static nms_status scratch_address(double** out)
         return NMS_ERR_UNSUPPORTED;
     }
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    // before the first runtime call on the device there may be no context
+    // yet (ctx = NULL): cudaGetSymbolAddress creates it
+    void* ctx = current_context();
+    if (!g_scratch_addr[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
         g_scratch_addr[dev] = (double*)p;
+        g_scratch_ctx[dev] = current_context();
     }
     *out = g_scratch_addr[dev];
     return NMS_OK;

@@ -78,17 +78,16 @@ cudaError_t plan_malloc_raw(void** ptr, size_t bytes)
     return e;
 }
 
-void plan_free(void* ptr)
+void plan_free(void* ptr, cudaStream_t used_on)
 {
     if (!ptr) return;
     if (!pools_enabled()) {
-        cudaFree(ptr);
+        cudaFree(ptr);   // waits for the device's outstanding work
         return;
     }
-    PlanPool pp;
-    if (plan_pool(pp) != cudaSuccess) return;
-    cudaFreeAsync(ptr, pp.stream);
-    cudaStreamSynchronize(pp.stream);
+    // stream-ordered after the last work that used the memory: the pool can
+    // hand it out again (or trim it) only once that stream has passed here
+    cudaFreeAsync(ptr, used_on);
 }
 }  // namespace nms
 
@@ -230,7 +229,7 @@ static nms_status dalloc(T** p, size_t count, const char* what)
     return NMS_OK;
 }
 
-static void dfree(void* p) { plan_free(p); }
+static void dfree(void* p, cudaStream_t s) { plan_free(p, s); }
 
 static void free_plan(nms_plan_s* p)
 {
@@ -240,12 +239,13 @@ static void free_plan(nms_plan_s* p)
     void* bufs[] = {p->d_pos, p->d_vol, p->d_nuc, p->d_mag, p->d_cen_cell, p->d_qy, p->d_qz, p->d_hy,
                     p->d_hz, p->d_qa, p->d_qturn, p->d_cpos, p->d_w64, p->d_cw, p->d_yz, p->d_F,
                     p->d_Ftot, p->d_Fpart, p->d_Gtot, p->d_Gdil, p->d_err, p->d_tab, p->d_wscale};
-    for (void* b : bufs) dfree(b);
+    for (void* b : bufs) dfree(b, p->stream);
     tc_release(*p);
-    if (p->d_cposl && p->d_cposl != p->d_cpos) dfree(p->d_cposl);
-    if (p->d_yzl && p->d_yzl != p->d_yz) dfree(p->d_yzl);
-    dfree(p->d_bin_of);
-    dfree(p->d_Iobj);
+    if (p->d_cposl && p->d_cposl != p->d_cpos) dfree(p->d_cposl, p->stream);
+    if (p->d_yzl && p->d_yzl != p->d_yz) dfree(p->d_yzl, p->stream);
+    dfree(p->d_bin_of, p->stream);
+    dfree(p->d_Iobj, p->stream);
+    cudaStreamSynchronize(p->stream);   // the frees are done before the stream can go away
     p->timer.release();
     delete p;
 }
@@ -282,7 +282,7 @@ static nms_status build_grid(Plan& p, const nms_qgrid& g)
     NMS_CUDA_TRY(launch_grid(g, np, d_list, p.d_qy, p.d_qz, p.d_hy, p.d_hz, p.d_qa, p.d_qturn, p.stream));
     if (d_list) {
         NMS_CUDA_TRY(cudaStreamSynchronize(p.stream));   // the copy from the caller's buffer has completed
-        dfree(d_list);
+        dfree(d_list, p.stream);
     }
     return NMS_OK;
 }
@@ -881,8 +881,8 @@ nms_status nms_plan_object_iq(nms_plan_t plan, int32_t response_id, int32_t nbin
     }
     for (int b = 0; b < nbins; ++b) p.oiq_qmean[b] = p.oiq_counts[b] ? p.oiq_qmean[b] / p.oiq_counts[b] : NAN;
     cudaStreamSynchronize(p.stream);   // earlier amplitude calls may still use the old bins
-    dfree(p.d_bin_of);
-    dfree(p.d_Iobj);
+    dfree(p.d_bin_of, p.stream);
+    dfree(p.d_Iobj, p.stream);
     p.d_bin_of = nullptr;
     p.d_Iobj = nullptr;
     nms_status st;

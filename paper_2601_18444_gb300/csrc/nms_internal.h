@@ -193,11 +193,13 @@ cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t* err, cudaStream_t s
 
 // Device memory of plans: a per-device library memory pool that keeps up to
 // 16 GiB of freed memory for later plans (creating and destroying a plan
-// then maps and unmaps no pages).  Both calls behave like cudaMalloc /
-// cudaFree: the memory is usable on any stream when plan_malloc returns, and
-// plan_free must only see memory no pending work uses.
+// then maps and unmaps no pages).  The memory is usable on any stream when
+// plan_malloc returns.  plan_free(ptr, s) releases it stream-ordered after
+// all work issued so far on s, the stream every use of it was issued on (or
+// ordered before): memory a kernel may still read is never handed out again
+// or returned to the driver.
 cudaError_t plan_malloc_raw(void** ptr, size_t bytes);
-void plan_free(void* ptr);
+void plan_free(void* ptr, cudaStream_t used_on);
 template <class T>
 inline cudaError_t plan_malloc(T** ptr, size_t bytes)
 {

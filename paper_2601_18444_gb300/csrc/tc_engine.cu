@@ -166,11 +166,11 @@ static nms_status upload(T** d, const std::vector<T>& h)
     return NMS_OK;
 }
 
-static void free_schedule(Schedule& s)
+static void free_schedule(Schedule& s, cudaStream_t used_on)
 {
     void* b[] = {s.d_kb_cell0, s.d_kb_ncell, s.d_items, s.d_reds, s.d_out_obj, s.d_out_rot, s.d_out_two};
     for (void* x : b)
-        if (x) plan_free(x);
+        if (x) plan_free(x, used_on);
     s = Schedule();
 }
 
@@ -517,7 +517,7 @@ nms_status tc_autotune(Plan& p, TcState& t)
         if (st) break;
         double* P = nullptr;
         cudaError_t ce = plan_malloc(&P, (size_t)std::max<int64_t>(1, S.max_items) * 128 * 128 * sizeof(double));
-        if (ce != cudaSuccess) { free_schedule(S); st = cuda_fail(ce, "autotune partials"); break; }
+        if (ce != cudaSuccess) { free_schedule(S, s); st = cuda_fail(ce, "autotune partials"); break; }
         float ms = 1e30f;
         const Chunk& ch = S.batches[0].chunks[0];
         const int64_t lo_off = fb_plane(t, 1);
@@ -546,8 +546,9 @@ nms_status tc_autotune(Plan& p, TcState& t)
         }
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(herr, d_err, sizeof(herr), cudaMemcpyDeviceToHost, s);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-        plan_free(P);
-        free_schedule(S);
+        // ordered after this candidate's launches on s, also when one failed
+        plan_free(P, s);
+        free_schedule(S, s);
         if (ce != cudaSuccess) { st = cuda_fail(ce, "autotune probe"); break; }
         double err = 0.0;
         for (int c = 0; c < 4; ++c)
@@ -562,9 +563,9 @@ nms_status tc_autotune(Plan& p, TcState& t)
     memcpy(p.timer.launches, launches_before, sizeof(launches_before));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    plan_free(d_sw);
-    plan_free(d_err);
-    plan_free(d_Fp);
+    plan_free(d_sw, s);
+    plan_free(d_err, s);
+    plan_free(d_Fp, s);
     if (st) return st;
     NMS_CUDA_TRY(cudaMemsetAsync(p.d_err, 0, sizeof(int32_t), s));
     t.kcb = best.kcb;
@@ -747,9 +748,9 @@ void tc_release(Plan& p)
     void* b[] = {t->d_qy,  t->d_qz,  t->d_cpos_b, t->d_cw_b, t->d_Fb, t->d_Ftot_b,
                  t->d_cyz, t->d_eyz, t->d_rot,    t->d_cen,  t->d_P};
     for (void* x : b)
-        if (x) plan_free(x);
-    free_schedule(t->full);
-    free_schedule(t->last);
+        if (x) plan_free(x, p.stream);
+    free_schedule(t->full, p.stream);
+    free_schedule(t->last, p.stream);
     delete t;
     p.tc_state = nullptr;
 }

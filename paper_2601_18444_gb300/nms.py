@@ -462,9 +462,42 @@ def nms_get_object_iq(plan, n_objects):
     return I, c, q
 
 
+def _noalloc_args(Y, Z, w, qy, qz, F):
+    """Checks of nms_dsft_direct_noalloc's buffers before any device access:
+    float64 torch tensors, sizes consistent with n_cells = Y.numel() and
+    n_q = qy.numel(), F contiguous, and (last) every tensor on the GPU.
+    Raises ValueError on the first mismatch."""
+    names = ("Y", "Z", "w", "qy", "qz", "F")
+    bufs = (Y, Z, w, qy, qz, F)
+    for nm, t in zip(names, bufs):
+        if not (hasattr(t, "dtype") and hasattr(t, "numel") and hasattr(t, "is_cuda")):
+            raise ValueError(f"{nm} must be a torch tensor")
+        if str(t.dtype) != "torch.float64":
+            raise ValueError(f"{nm} must be float64, got {t.dtype}")
+    n, nq = Y.numel(), qy.numel()
+    if Z.numel() != n:
+        raise ValueError(f"Z has {Z.numel()} elements, Y has {n}")
+    if w.numel() != 4 * n:
+        raise ValueError(f"w must hold [4][n_cells] = {4 * n} weights, has {w.numel()}")
+    if qz.numel() != nq:
+        raise ValueError(f"qz has {qz.numel()} elements, qy has {nq}")
+    if F.numel() < 8 * nq:
+        raise ValueError(f"F must hold [4][n_q][2] = {8 * nq} values, has {F.numel()}")
+    if not F.is_contiguous():
+        raise ValueError("F must be contiguous (it is written in place)")
+    for nm, t in zip(names, bufs):
+        if not t.is_cuda:
+            raise ValueError(f"{nm} must be a CUDA tensor (the entry point reads and writes device memory)")
+    devs = {t.device for t in bufs}
+    if len(devs) != 1:
+        raise ValueError(f"all buffers must be on one device, got {sorted(str(d) for d in devs)}")
+
+
 def nms_dsft_direct_noalloc(Y, Z, w, qy, qz, F, stream=None):
     """Direct sums into a caller-owned device tensor F [4, n_q, 2] without any
-    device allocation by the library (all arguments are float64 CUDA tensors)."""
+    device allocation by the library (all arguments are float64 CUDA tensors
+    on one device; checked here before the call)."""
+    _noalloc_args(Y, Z, w, qy, qz, F)
     Y, Z, w, qy, qz = (_dev_in(t) for t in (Y, Z, w, qy, qz))
     _check(load().nms_dsft_direct_noalloc(Y.numel(), _ptr(Y), _ptr(Z), _ptr(w), qy.numel(), _ptr(qy), _ptr(qz),
                                           _ptr(F), ctypes.c_void_p(stream or 0)))

@@ -125,3 +125,28 @@ def test_binding_refuses_strided_buffers():
     with pytest.raises(ValueError):
         nms._ptr(f)
     assert nms._ptr(np.zeros((3, 5))).value is not None
+
+
+def test_noalloc_binding_checks_buffers_before_the_call():
+    # every malformed buffer is refused by the binding before the library is
+    # called: wrong dtype, inconsistent sizes, a short or strided output, and
+    # host (CPU) tensors; no GPU is needed to see the refusals
+    torch = pytest.importorskip("torch")
+    d = torch.float64
+    n, nq = 10, 7
+    ok = dict(Y=torch.zeros(n, dtype=d), Z=torch.zeros(n, dtype=d), w=torch.zeros(4, n, dtype=d),
+              qy=torch.zeros(nq, dtype=d), qz=torch.zeros(nq, dtype=d), F=torch.zeros(4, nq, 2, dtype=d))
+    bad = [("Y", torch.zeros(n, dtype=torch.float32), "float64"),
+           ("w", torch.zeros(1, n, dtype=d), "[4][n_cells]"),
+           ("Z", torch.zeros(n + 1, dtype=d), "Z has"),
+           ("qz", torch.zeros(nq - 1, dtype=d), "qz has"),
+           ("F", torch.zeros(4, nq, 1, dtype=d), "[4][n_q][2]"),
+           ("F", torch.zeros(4, 2, nq, dtype=d).transpose(1, 2), "contiguous"),
+           ("qy", np.zeros(nq), "torch tensor")]
+    for name, val, msg in bad:
+        kw = dict(ok)
+        kw[name] = val
+        with pytest.raises(ValueError, match=re.escape(msg)):
+            nms.nms_dsft_direct_noalloc(**kw)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        nms.nms_dsft_direct_noalloc(**ok)

@@ -69,6 +69,16 @@ def test_gradients_match_fp64_oracle(H):
                                        hi.astype(np.float64), ym.astype(np.float64), ys.astype(np.float64),
                                        nin, H, nout)
     assert abs(loss - loss_ref) <= 2e-2 * abs(loss_ref)
+    # element by element: each gradient is a sum over the batch of products
+    # formed from BF16-rounded activations (relative 2^-8 each); its error is
+    # bounded by a small multiple of the sum of the terms' magnitudes
+    mag = OM.grad_magnitude(th, X.astype(np.float64), T.astype(np.float64), lo.astype(np.float64),
+                            hi.astype(np.float64), ym.astype(np.float64), ys.astype(np.float64), nin, H, nout)
+    assert np.all(mag >= np.abs(g_ref) * (1 - 1e-12))
+    bound = 3e-2 * mag + 1e-6 * mag.max()
+    bad = np.flatnonzero(np.abs(g - g_ref) > bound)
+    assert bad.size == 0, (bad[:8], g[bad[:8]], g_ref[bad[:8]], mag[bad[:8]])
+    # and block by block in norm, as a second view
     off = [0, H * nin, o2, o2 + H * H, o3, o3 + nout * H, len(theta)]
     for a, b in zip(off[:-1], off[1:]):
         rel = np.linalg.norm(g[a:b] - g_ref[a:b]) / max(np.linalg.norm(g_ref[a:b]), 1e-30)

@@ -55,3 +55,22 @@ def test_input_scaling_maps_bounds_to_unit_interval():
     theta, X, T, lo, hi, ym, ys, nin, H, nout = _setup()
     f = M.forward(theta, np.vstack([lo, hi]), lo, hi, nin, H, nout)
     np.testing.assert_allclose(f["Xn"], [[-1.0] * nin, [1.0] * nin])
+
+
+def test_gradient_magnitude_bounds_and_positive_case():
+    # |g| <= magnitude element by element on a random network; with every
+    # weight, bias and scaled input positive and every output above its
+    # target, no term of any gradient sum is negative, so the two coincide
+    theta, X, T, lo, hi, ym, ys, nin, H, nout = _setup(seed=5)
+    _, g = M.loss_and_grad(theta, X, T, lo, hi, ym, ys, nin, H, nout)
+    mag = M.grad_magnitude(theta, X, T, lo, hi, ym, ys, nin, H, nout)
+    assert np.all(mag >= np.abs(g) - 1e-15)
+    assert np.any(mag > np.abs(g) * (1 + 1e-6))          # cancellation does occur
+    rng = np.random.default_rng(6)
+    theta = rng.uniform(0.1, 1.0, size=theta.size)
+    X = rng.uniform(0.6, 3.0, size=X.shape)              # above the midpoint 0.5 of [-2, 3]: scaled input > 0
+    T = np.full(T.shape, -1e3)
+    _, g = M.loss_and_grad(theta, X, T, lo, hi, ym, ys, nin, H, nout)
+    mag = M.grad_magnitude(theta, X, T, lo, hi, ym, ys, nin, H, nout)
+    assert np.all(g > 0)
+    np.testing.assert_allclose(mag, g, rtol=1e-12)

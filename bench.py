@@ -49,8 +49,7 @@ ALGO_FLOPS_PER_TERM = 32
 # DRAM bytes (read + write) the GEMM moves per byte of phase tables it
 # consumes, from an ncu capture of one launch on the 64x64x64 box (512^2
 # detector); the box workloads scale it by their own table bytes per launch.
-# None until a capture of the current kernel is summarised under profiles/.
-TC_DRAM_PER_TABLE_BYTE = None
+TC_DRAM_PER_TABLE_BYTE = 1.134   # 3.045 GB for 2.684 GB of tables (ncu, box64)
 TC_TRAFFIC_WORKLOADS = ("box", "box64")
 
 

@@ -75,7 +75,11 @@ typedef enum {
     NMS_PREC_AUTO = 0,          /* TC_F16X3 on CARTESIAN grids, FP32_DIRECT otherwise   */
     NMS_PREC_TC_F16X3 = 1,      /* split-FP16 (hi/lo, 3 products) tcgen05 GEMM, FP32
                                    TMEM accumulation promoted to two-float every
-                                   kc_cells cells; CARTESIAN grids only               */
+                                   kc_cells cells; CARTESIAN grids only.  It takes
+                                   the place of TF32x3 (same ~2^-22 per-product
+                                   error, but TF32 runs at half the FP16 rate on
+                                   tcgen05), BF16x3 (2^-17: misses 1e-6) and
+                                   BF16x6 (twice the MMAs for no gain over this) */
     NMS_PREC_FP32_DIRECT = 2,   /* compensated FP32 direct sum (two-float phase in
                                    turns, exact reduction, sincospif)                  */
     NMS_PREC_FP32_NAIVE = 3     /* plain FP32 phase + sincosf: fast, inaccurate at
@@ -409,7 +413,9 @@ nms_status nms_selftest_bounded_wait(int64_t limit_us, void* cuda_stream);
 /* Release every device resource of the plan.  NULL is accepted. */
 nms_status nms_plan_destroy(nms_plan_t plan);
 
-/* Thread-local text of the last failure in this thread ("" if none). */
+/* Thread-local text of the last failure in this thread ("" if none).  It
+ * takes no plan: a failed nms_plan_create has no plan to ask, and with one
+ * plan per host thread the thread's last failure is the plan's. */
 const char* nms_last_error(void);
 
 /* Library version, e.g. "nms 0.1.0 sm_103a". */

@@ -6,8 +6,8 @@
 // The paper has no learned component; here the exact transform generates
 // the training targets and is the reference for the network's error.
 //
-// Kernels: for training, a BF16 tensor-core GEMM (mma.sync m16n8k16, FP32
-// accumulate) with the transposes the forward and backward passes need, plus
+// Kernels: for training, a BF16 tcgen05 GEMM (FP32 accumulation in TMEM)
+// with the transposes the forward and backward passes need, plus
 // element-wise SiLU / SiLU', MSE gradient, column sums for bias gradients,
 // and Adam (the training GEMMs are small, B x 256 x 256); for inference, one
 // fused tcgen05 kernel that runs the whole network per tile of 128 queries
@@ -33,96 +33,165 @@ namespace nms {
 // ------------------------------------------------------------------ GEMM
 // C[m][n] (FP32, ldc) = sum_k A(m,k) B(n,k), A(m,k) = TA ? A[k*lda + m] :
 // A[m*lda + k], B(n,k) = TB ? B[k*ldb + n] : B[n*ldb + k]; BF16 operands.
-constexpr int MG_BM = 64, MG_BN = 64, MG_BK = 32, MG_LD = MG_BK + 8;
+//
+// On the 5th-generation tensor cores: one CTA of 8 warps per 128 x 128 tile
+// of C.  For each 256-wide stretch of K the threads stage A and B into
+// shared memory in the 128-byte-swizzled K-major layout (four k-blocks of 64
+// per operand, 128 KB): every thread gathers 8 consecutive k of one row
+// (one 16-byte load where the row is contiguous and aligned, 8 loads down a
+// column where the operand is stored with K outermost; zero outside the
+// matrix) and writes them as one 16-byte chunk.  One thread issues the
+// tcgen05.mma (M = N = 128, K = 16, FP32 accumulation in 128 TMEM columns)
+// and commits them to an mbarrier every thread waits on (bounded) before
+// the buffers are reused; warp w reads TMEM lanes 32 (w mod 4) .. + 31 (rows
+// of C), columns 64 (w / 4) .. + 63.  The training GEMMs are B x 256 x 256
+// at most: a few CTAs, one or two K stretches.
+constexpr int TG_BM = 128, TG_BN = 128, TG_BK = 64, TG_KB = 4, TG_THREADS = 256;
+constexpr int TG_BLK = TG_BM * TG_BK * 2;              // 16 KB: one k-block of one operand
+constexpr int TG_SMEM = 2 * TG_KB * TG_BLK + 1024;     // A and B, 4 k-blocks each
 
-__device__ __forceinline__ void mma_bf16_16816(float* c, const uint32_t* a, const uint32_t* b)
+// 8 consecutive k (k0 .. k0 + 7) of row `row` as BF16x8, zero outside [0, R) x [0, K)
+template <bool T>
+__device__ __forceinline__ uint4 gather8(const __nv_bfloat16* __restrict__ P, int ld, int row, int R, int k0, int K)
 {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+    uint4 out = make_uint4(0u, 0u, 0u, 0u);
+    if (row >= R) return out;
+    if (!T && k0 + 8 <= K && (ld & 7) == 0 && ((reinterpret_cast<uintptr_t>(P) & 15) == 0))
+        return *reinterpret_cast<const uint4*>(P + (int64_t)row * ld + k0);
+    uint32_t w[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int k = k0 + e;
+        if (k < K) {
+            const __nv_bfloat16 v = T ? P[(int64_t)k * ld + row] : P[(int64_t)row * ld + k];
+            w[e >> 1] |= (uint32_t)__bfloat16_as_ushort(v) << (16 * (e & 1));
+        }
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 template <bool TA, bool TB>
-__global__ void __launch_bounds__(128) k_mlp_gemm(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda,
-                                                  const __nv_bfloat16* __restrict__ B, int ldb, float* __restrict__ C,
-                                                  int ldc)
+__global__ void __launch_bounds__(TG_THREADS)
+    k_mlp_gemm_tc(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda, const __nv_bfloat16* __restrict__ B,
+                  int ldb, float* __restrict__ C, int ldc, int32_t* __restrict__ err, uint64_t limit_ns)
 {
-    __shared__ __align__(16) __nv_bfloat16 As[MG_BM][MG_LD];
-    __shared__ __align__(16) __nv_bfloat16 Bs[MG_BN][MG_LD];
-    const int m0 = blockIdx.y * MG_BM, n0 = blockIdx.x * MG_BN;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-    const int gid = lane >> 2, tig = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-    const __nv_bfloat16 zero = __float2bfloat16(0.f);
-    for (int k0 = 0; k0 < K; k0 += MG_BK) {
-        for (int idx = threadIdx.x; idx < MG_BM * MG_BK; idx += blockDim.x) {
-            int r, kk;
-            if (TA) { kk = idx / MG_BM; r = idx % MG_BM; } else { r = idx / MG_BK; kk = idx % MG_BK; }
-            const int m = m0 + r, k = k0 + kk;
-            As[r][kk] = (m < M && k < K) ? (TA ? A[(int64_t)k * lda + m] : A[(int64_t)m * lda + k]) : zero;
-        }
-        for (int idx = threadIdx.x; idx < MG_BN * MG_BK; idx += blockDim.x) {
-            int r, kk;
-            if (TB) { kk = idx / MG_BN; r = idx % MG_BN; } else { r = idx / MG_BK; kk = idx % MG_BK; }
-            const int n = n0 + r, k = k0 + kk;
-            Bs[r][kk] = (n < N && k < K) ? (TB ? B[(int64_t)k * ldb + n] : B[(int64_t)n * ldb + k]) : zero;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int ks = 0; ks < MG_BK; ks += 16) {
-            uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm + i * 16 + gid;
-                af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][ks + tig * 2]);
-                af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + tig * 2]);
-                af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][ks + tig * 2 + 8]);
-                af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][ks + tig * 2 + 8]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int r = wn + j * 8 + gid;
-                bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[r][ks + tig * 2]);
-                bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[r][ks + tig * 2 + 8]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) mma_bf16_16816(acc[i][j], af[i], bfr[j]);
-        }
-        __syncthreads();
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_taddr;
+    __shared__ volatile int s_abort;
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* gA = smem_raw + (base - raw);
+    uint8_t* gB = gA + TG_KB * TG_BLK;
+    const uint32_t sA = base, sB = base + TG_KB * TG_BLK;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * TG_BM, n0 = blockIdx.x * TG_BN;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int r = m0 + wm + i * 16 + gid;
-            const int c = n0 + wn + j * 8 + tig * 2;
-            if (r < M && c < N) C[(int64_t)r * ldc + c] = acc[i][j][0];
-            if (r < M && c + 1 < N) C[(int64_t)r * ldc + c + 1] = acc[i][j][1];
-            if (r + 8 < M && c < N) C[(int64_t)(r + 8) * ldc + c] = acc[i][j][2];
-            if (r + 8 < M && c + 1 < N) C[(int64_t)(r + 8) * ldc + c + 1] = acc[i][j][3];
+    if (warp == 0) {
+        tc_alloc<1>(smem_u32(&s_taddr), TG_BN);
+        tc_relinquish<1>();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = s_taddr;
+    const uint32_t idesc = idesc_bf16_f32(TG_BM, TG_BN);
+    uint32_t phase = 0;
+    bool aborted = false;
+    for (int k0 = 0; k0 < K; k0 += TG_KB * TG_BK) {
+        const int nkb = min(TG_KB, (K - k0 + TG_BK - 1) / TG_BK);
+        // units: (k-block kb, row r, 8-wide chunk c); consecutive threads take
+        // consecutive addresses of whichever index is contiguous in memory
+        for (int u = tid; u < nkb * TG_BM * 8; u += TG_THREADS) {
+            const int kb = u / (TG_BM * 8), v = u % (TG_BM * 8);
+            const int r = TA ? v % TG_BM : v / 8, c = TA ? v / TG_BM : v % 8;
+            const uint4 x = gather8<TA>(A, lda, m0 + r, M, k0 + kb * TG_BK + 8 * c, K);
+            *reinterpret_cast<uint4*>(gA + kb * TG_BLK + swz_offset(r, 8 * c)) = x;
         }
+        for (int u = tid; u < nkb * TG_BN * 8; u += TG_THREADS) {
+            const int kb = u / (TG_BN * 8), v = u % (TG_BN * 8);
+            const int r = TB ? v % TG_BN : v / 8, c = TB ? v / TG_BN : v % 8;
+            const uint4 x = gather8<TB>(B, ldb, n0 + r, N, k0 + kb * TG_BK + 8 * c, K);
+            *reinterpret_cast<uint4*>(gB + kb * TG_BLK + swz_offset(r, 8 * c)) = x;
+        }
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            for (int kb = 0; kb < nkb; ++kb)
+#pragma unroll
+                for (int k16 = 0; k16 < 4; ++k16)
+                    tc_mma_f16(taddr, sw128_desc(sA + kb * TG_BLK) + 2 * k16, sw128_desc(sB + kb * TG_BLK) + 2 * k16,
+                               idesc, (k0 | kb | k16) ? 1u : 0u);
+            tc_commit(&bar);
+        }
+        const bool ok = mbar_wait(&bar, phase, limit_ns, &s_abort);
+        if (__syncthreads_or(!ok)) {
+            aborted = true;
+            break;
+        }
+        phase ^= 1u;
+        tc_fence_after();
+    }
+    if (!aborted) {
+        const int quad = warp & 3, ch = warp >> 2;
+        const int m = m0 + 32 * quad + lane;
+#pragma unroll
+        for (int c16 = 0; c16 < 4; ++c16) {
+            float v[16];
+            const int c0 = 64 * ch + 16 * c16;
+            tmem_ld16(taddr + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0, v);
+            tmem_wait_ld();
+            if (m < M) {
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const int n = n0 + c0 + t;
+                    if (n < N) C[(int64_t)m * ldc + n] = v[t];
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(err, 2);
+        // let the MMAs in flight finish (bounded) before TMEM is freed
+        const uint64_t t0 = gtimer();
+        while (!mbar_try_wait(&bar, phase) && gtimer() - t0 < 1000000000ull) {
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tc_dealloc<1>(taddr, TG_BN);
+}
+
+template <bool TA, bool TB>
+static cudaError_t launch_gemm_tc(dim3 grid, int M, int N, int K, const __nv_bfloat16* A, int lda,
+                                  const __nv_bfloat16* B, int ldb, float* C, int ldc, int32_t* err, cudaStream_t s)
+{
+    static bool attr = false;   // one-time opt-in to 129 KB of dynamic shared memory
+    if (!attr) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_mlp_gemm_tc<TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, TG_SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_mlp_gemm_tc<TA, TB><<<grid, TG_THREADS, TG_SMEM, s>>>(M, N, K, A, lda, B, ldb, C, ldc, err, 4000000000ull);
+    return cudaGetLastError();
 }
 
 static cudaError_t mlp_gemm(bool ta, bool tb, int M, int N, int K, const __nv_bfloat16* A, int lda,
-                            const __nv_bfloat16* B, int ldb, float* C, int ldc, cudaStream_t s)
+                            const __nv_bfloat16* B, int ldb, float* C, int ldc, int32_t* err, cudaStream_t s)
 {
-    dim3 grid((N + MG_BN - 1) / MG_BN, (M + MG_BM - 1) / MG_BM);
-    if (!ta && !tb) k_mlp_gemm<false, false><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
-    else if (!ta && tb) k_mlp_gemm<false, true><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
-    else if (ta && !tb) k_mlp_gemm<true, false><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
-    else k_mlp_gemm<true, true><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc);
-    return cudaGetLastError();
+    if (M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
+    const dim3 grid((N + TG_BN - 1) / TG_BN, (M + TG_BM - 1) / TG_BM);
+    if (!ta && !tb) return launch_gemm_tc<false, false>(grid, M, N, K, A, lda, B, ldb, C, ldc, err, s);
+    if (!ta && tb) return launch_gemm_tc<false, true>(grid, M, N, K, A, lda, B, ldb, C, ldc, err, s);
+    if (ta && !tb) return launch_gemm_tc<true, false>(grid, M, N, K, A, lda, B, ldb, C, ldc, err, s);
+    return launch_gemm_tc<true, true>(grid, M, N, K, A, lda, B, ldb, C, ldc, err, s);
 }
 
 // ------------------------------------------------------------------ element-wise
@@ -599,10 +668,10 @@ nms_status forward(nms_surrogate_s* s, const float* X, const int32_t* perm, int 
     k_layer1<<<nb((int64_t)B * H), 256, 0, st>>>(B, s->nin, H, X, perm, s->d_xlo, s->d_xhi, W1p(s), b1p(s), s->d_Xn,
                                                  s->d_Z1, s->d_H1);
     NMS_CUDA_TRY(cudaGetLastError());
-    NMS_CUDA_TRY(mlp_gemm(false, false, B, H, H, s->d_H1, H, s->d_W2h, H, s->d_C, H, st));
+    NMS_CUDA_TRY(mlp_gemm(false, false, B, H, H, s->d_H1, H, s->d_W2h, H, s->d_C, H, s->d_err, st));
     k_bias_act<<<nb((int64_t)B * H), 256, 0, st>>>(B, H, s->d_C, b2p(s), 1, s->d_Z2, s->d_H2);
     NMS_CUDA_TRY(cudaGetLastError());
-    NMS_CUDA_TRY(mlp_gemm(false, false, B, O, H, s->d_H2, H, s->d_W3h, H, s->d_C, O, st));
+    NMS_CUDA_TRY(mlp_gemm(false, false, B, O, H, s->d_H2, H, s->d_W3h, H, s->d_C, O, s->d_err, st));
     k_bias_act<<<nb((int64_t)B * O), 256, 0, st>>>(B, O, s->d_C, b3p(s), 0, s->d_Y, nullptr);
     NMS_CUDA_TRY(cudaGetLastError());
     return NMS_OK;
@@ -618,15 +687,15 @@ nms_status backward(nms_surrogate_s* s, const float* T, const int32_t* perm, int
                                                     s->d_loss);
     NMS_CUDA_TRY(cudaGetLastError());
     // layer 3: dW3 = dY^T H2, db3 = colsum dY, dH2 = dY W3
-    NMS_CUDA_TRY(mlp_gemm(true, true, O, H, B, s->d_dY, O, s->d_H2, H, g + off_W3(s), H, st));
+    NMS_CUDA_TRY(mlp_gemm(true, true, O, H, B, s->d_dY, O, s->d_H2, H, g + off_W3(s), H, s->d_err, st));
     k_col_sum<<<nb(O), 256, 0, st>>>(B, O, s->d_dYf, g + off_b3(s));
-    NMS_CUDA_TRY(mlp_gemm(false, true, B, H, O, s->d_dY, O, s->d_W3h, H, s->d_dH, H, st));
+    NMS_CUDA_TRY(mlp_gemm(false, true, B, H, O, s->d_dY, O, s->d_W3h, H, s->d_dH, H, s->d_err, st));
     // layer 2
     k_act_grad<<<nb((int64_t)B * H), 256, 0, st>>>((int64_t)B * H, s->d_dH, s->d_Z2, s->d_dZ, s->d_dZf);
     NMS_CUDA_TRY(cudaGetLastError());
-    NMS_CUDA_TRY(mlp_gemm(true, true, H, H, B, s->d_dZ, H, s->d_H1, H, g + off_W2(s), H, st));
+    NMS_CUDA_TRY(mlp_gemm(true, true, H, H, B, s->d_dZ, H, s->d_H1, H, g + off_W2(s), H, s->d_err, st));
     k_col_sum<<<nb(H), 256, 0, st>>>(B, H, s->d_dZf, g + off_b2(s));
-    NMS_CUDA_TRY(mlp_gemm(false, true, B, H, H, s->d_dZ, H, s->d_W2h, H, s->d_dH, H, st));
+    NMS_CUDA_TRY(mlp_gemm(false, true, B, H, H, s->d_dZ, H, s->d_W2h, H, s->d_dH, H, s->d_err, st));
     // layer 1 (FP32)
     k_act_grad<<<nb((int64_t)B * H), 256, 0, st>>>((int64_t)B * H, s->d_dH, s->d_Z1, nullptr, s->d_dZf);
     k_dw1<<<nb((int64_t)H * nin), 256, 0, st>>>(B, nin, H, s->d_dZf, s->d_Xn, g);
@@ -750,6 +819,7 @@ nms_status nms_surrogate_train(nms_surrogate_t s, const float* X, const float* Y
     std::vector<int32_t> perm(n);
     std::mt19937_64 rng(shuffle_seed);
     double last = 0.0;
+    NMS_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, 4, s->stream));
     for (int e = 0; e < epochs; ++e) {
         for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
         std::shuffle(perm.begin(), perm.end(), rng);
@@ -767,8 +837,14 @@ nms_status nms_surrogate_train(nms_surrogate_t s, const float* X, const float* Y
             if ((st = refresh_bf16(s))) return st;
         }
         double h = 0.0;
+        int32_t herr = 0;
         NMS_CUDA_TRY(cudaMemcpyAsync(&h, s->d_loss, 8, cudaMemcpyDeviceToHost, s->stream));
+        NMS_CUDA_TRY(cudaMemcpyAsync(&herr, s->d_err, 4, cudaMemcpyDeviceToHost, s->stream));
         NMS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        if (herr) {
+            set_error("surrogate train: a tensor-core GEMM's bounded wait gave up");
+            return NMS_ERR_TIMEOUT;
+        }
         last = h / (double)((n / B) * (int64_t)B * s->nout);
     }
     if (final_loss) *final_loss = (float)last;
@@ -783,12 +859,19 @@ nms_status nms_surrogate_gradients(nms_surrogate_t s, const float* X, const floa
     nms_status st = ensure_batch(s, n);
     if (st) return st;
     NMS_CUDA_TRY(cudaMemsetAsync(s->d_loss, 0, 8, s->stream));
+    NMS_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, 4, s->stream));
     if ((st = forward(s, X, nullptr, n))) return st;
     if ((st = backward(s, Y, nullptr, n))) return st;
     NMS_CUDA_TRY(cudaMemcpyAsync(grad, s->d_g, s->nparam * 4, cudaMemcpyDeviceToHost, s->stream));
     double h = 0.0;
+    int32_t herr = 0;
     NMS_CUDA_TRY(cudaMemcpyAsync(&h, s->d_loss, 8, cudaMemcpyDeviceToHost, s->stream));
+    NMS_CUDA_TRY(cudaMemcpyAsync(&herr, s->d_err, 4, cudaMemcpyDeviceToHost, s->stream));
     NMS_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (herr) {
+        set_error("surrogate gradients: a tensor-core GEMM's bounded wait gave up");
+        return NMS_ERR_TIMEOUT;
+    }
     if (loss) *loss = h / ((double)n * s->nout);
     return NMS_OK;
 }

@@ -264,6 +264,12 @@ def main():
     ap.add_argument("--sets", type=int, default=1,
                     help="loop mode: S magnetization states of the workload along a field sweep in one plan")
     ap.add_argument("--copies", type=int, default=0, help="e4: number of particle copies (0: the sweep)")
+    ap.add_argument("--curves", type=int, default=2048, help="surrogate: training curves")
+    ap.add_argument("--orientations", type=int, default=16, help="surrogate: orientations per curve")
+    ap.add_argument("--bins", type=int, default=64, help="surrogate: log |q| bins")
+    ap.add_argument("--qmin", type=float, default=0.04, help="surrogate: lower edge of the log bins (nm^-1)")
+    ap.add_argument("--held-out", type=int, default=256, help="surrogate: held-out curves judged by the transform")
+    ap.add_argument("--epochs", type=int, default=0, help="surrogate: timed training epochs (0: 20 x steps)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -626,19 +632,33 @@ def mlp_flops(n_in, H, n_out):
 
 
 def run_surrogate(args, dev):
-    """Learned surrogate (scaled-down vortex family): training curves from the
-    batched transform, then timed training epochs and timed inference on 2^20
-    queries; the MLP GEMMs against the bf16 dense peak."""
+    """Learned surrogate on the vortex family: training curves from the
+    batched transform (orientation-averaged unpolarized I(q) on log |q| bins),
+    timed training epochs, the held-out error against the transform, and
+    timed inference on 2^20 queries; the MLP GEMMs against the bf16 dense
+    peak.  Default: a scaled-down family (2048 curves x 16 orientations, 64
+    bins); --curves 200000 --orientations 256 --bins 128 runs the stated
+    scale (members built by spawned worker processes, chunks of 8000 per
+    plan)."""
     import torch
     from paper_2601_18444_gb300 import inputs as I
     from paper_2601_18444_gb300 import nms
     from paper_2601_18444_gb300 import surrogate as SG
-    edges = np.geomspace(0.04, 1.2, 65)
-    params = I.vortex_family_params(2048, seed=21)
-    t0 = time.perf_counter()
-    Iq, _, t_tr, terms_tr = SG.generate_curves(params, edges, a=2.5, n_rot=16)
-    ok = np.all(np.isfinite(Iq), axis=0)
-    Y = torch.tensor(SG.log_targets(Iq[:, ok]), device="cuda")
+    edges = np.geomspace(args.qmin, 1.2, args.bins + 1)
+    a_lat = 2.5
+    params = I.vortex_family_params(args.curves, seed=21)
+    p_test = I.vortex_family_params(args.held_out, seed=22)
+    big = args.curves > 4096
+    t_host = 0.0
+    if big:
+        Iq, _, t_tr, terms_tr, t_host = SG.generate_curves_chunked(params, edges, a=a_lat, n_rot=args.orientations)
+        I_te, _, t_te, terms_te, _ = SG.generate_curves_chunked(p_test, edges, a=a_lat, n_rot=args.orientations)
+    else:
+        Iq, _, t_tr, terms_tr = SG.generate_curves(params, edges, a=a_lat, n_rot=args.orientations)
+        I_te, _, t_te, terms_te = SG.generate_curves(p_test, edges, a=a_lat, n_rot=args.orientations)
+    ok = np.all(np.isfinite(Iq), axis=0) & np.all(np.isfinite(I_te), axis=0)
+    Y_tr, Y_te = SG.log_targets(Iq[:, ok]), SG.log_targets(I_te[:, ok])
+    Y = torch.tensor(Y_tr, device="cuda")
     X = torch.tensor(params.astype(np.float32), device="cuda")
     n_out, H = int(ok.sum()), 256
     lo = I.VORTEX_FAMILY_BOUNDS[:, 0].astype(np.float32)
@@ -646,14 +666,21 @@ def run_surrogate(args, dev):
     s = nms.nms_surrogate_create(6, H, n_out, lo, hi, seed=3, stream=torch.cuda.current_stream().cuda_stream)
     nms.nms_surrogate_train(s, X, Y, batch=128, epochs=max(1, args.warmup), lr=1e-3, seed=4)
     torch.cuda.synchronize()
-    epochs = 20 * max(1, args.steps)
+    epochs = args.epochs if args.epochs > 0 else 20 * max(1, args.steps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(dev) as clk:
         e0.record()
-        nms.nms_surrogate_train(s, X, Y, batch=128, epochs=epochs, lr=1e-3, seed=5)
+        loss = nms.nms_surrogate_train(s, X, Y, batch=128, epochs=epochs, lr=1e-3, seed=5)
         e1.record()
         e1.synchronize()
         ms_train = e0.elapsed_time(e1)
+        # held-out error against the exact transform
+        Xt = torch.tensor(p_test.astype(np.float32), device="cuda")
+        pred_t = torch.empty((len(p_test), n_out), device="cuda")
+        nms.nms_surrogate_infer(s, Xt, pred_t)
+        pred = pred_t.cpu().numpy()
+        rms = float(np.sqrt(np.mean((pred - Y_te) ** 2)))
+        rms_mean = float(np.sqrt(np.mean((Y_tr.mean(0) - Y_te) ** 2)))
         nq = 1 << 20
         q = torch.tensor(I.vortex_family_params(nq, seed=23).astype(np.float32), device="cuda")
         out = torch.empty((nq, n_out), device="cuda")   # 2^20 x n_out FP32 outputs: larger than L2
@@ -675,17 +702,21 @@ def run_surrogate(args, dev):
     achieved = f_inf / (ms_inf * 1e-3) / 1e12
     peak = peaks.get("bf16_tflops", 1900.0)
     train_samples = epochs * len(params)
+    exact_ms = 1e3 * t_te / len(p_test)
     line = {"metric": "surrogate inference queries/s (MLP 6->256->256->n_out, bf16 GEMMs)",
             "value": q_rate, "unit": "queries/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_inf, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16->f32", "data": "synthetic",
             "config": {"workload": f"vortex family, {len(params)} training curves from the batched transform "
-                                   f"(a=2.5nm, 16 orientations, 128^2 detector, {n_out} log bins); "
-                                   f"inference on 2^20 queries",
-                       "curves_s": t_tr, "curve_terms_per_s": terms_tr / t_tr,
-                       "train_samples_per_s": train_samples / (ms_train * 1e-3),
-                       "exact_ms_per_curve": 1e3 * t_tr / len(params),
-                       "surrogate_us_per_query": 1e3 * ms_inf / nq},
+                                   f"(a={a_lat}nm, {args.orientations} orientations, 128^2 detector [-1.2,1.2]^2, "
+                                   f"{args.bins} log bins {args.qmin}-1.2 nm^-1, {n_out} non-empty in every curve); "
+                                   f"{len(p_test)} held-out curves; inference on 2^20 queries",
+                       "curves_s": t_tr, "curve_terms_per_s": terms_tr / t_tr, "host_wait_s": t_host,
+                       "train_epochs": epochs, "train_samples_per_s": train_samples / (ms_train * 1e-3),
+                       "train_loss": loss,
+                       "held_out_rms_dex": rms, "mean_curve_rms_dex": rms_mean,
+                       "exact_ms_per_curve": exact_ms, "surrogate_us_per_query": 1e3 * ms_inf / nq,
+                       "speedup_per_query": exact_ms * 1e-3 / (ms_inf * 1e-3 / nq)},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "k_mlp_infer (fused tcgen05 bf16)",
                          "peak_source": f"{peak_src} bf16 dense"},

@@ -230,7 +230,7 @@ constexpr int FI_HB_BYTES = 4 * FI_TM * 128;  // H1 / H2 (A operand)
 constexpr int FI_SMEM = FI_W2_BYTES + FI_W3_BYTES + FI_HB_BYTES + 1024;
 
 __global__ void __launch_bounds__(FI_THREADS, 1)
-k_mlp_infer(int64_t n, int nin, int nout, const float* __restrict__ X, const float* __restrict__ xlo,
+k_mlp_infer(int64_t n, int nin, int nout, int ystride, const float* __restrict__ X, const float* __restrict__ xlo,
             const float* __restrict__ xhi, const float* __restrict__ W1, const float* __restrict__ b1,
             const __nv_bfloat16* __restrict__ W2h, const float* __restrict__ b2, const __nv_bfloat16* __restrict__ W3h,
             const float* __restrict__ b3, const float* __restrict__ ymean, const float* __restrict__ ystd,
@@ -402,7 +402,7 @@ k_mlp_infer(int64_t n, int nin, int nout, const float* __restrict__ X, const flo
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
                     const int c = c0 + t;
-                    if (c < nout) Y[q * nout + c] = (v[t] + b3[c]) * ystd[c] + ymean[c];
+                    if (c < nout) Y[q * ystride + c] = (v[t] + b3[c]) * ystd[c] + ymean[c];
                 }
             }
         }
@@ -881,8 +881,10 @@ nms_status nms_surrogate_infer(nms_surrogate_t s, const float* X, int64_t n, flo
     set_error("");
     if (!s || !X || !Y || n < 0) return NMS_ERR_INVALID_ARG;
     if (n == 0) return NMS_OK;
-    if (s->H == FI_H && s->nout <= FI_NO && s->nin <= 8) {
-        // the whole network in one tensor-core kernel
+    if (s->H == FI_H && s->nout <= 4 * FI_NO && s->nin <= 8) {
+        // the whole network in one tensor-core kernel per 64 outputs (W3 and
+        // the 128-query activation tile fill the shared memory; more
+        // outputs run the hidden layers again for each further 64)
         static bool attr = false;
         if (!attr) {
             NMS_CUDA_TRY(cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, FI_SMEM));
@@ -891,10 +893,14 @@ nms_status nms_surrogate_infer(nms_surrogate_t s, const float* X, int64_t n, flo
         NMS_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, 4, s->stream));
         const int64_t tiles = (n + FI_TM - 1) / FI_TM;
         const int grid = (int)std::min<int64_t>(tiles, device_sm_count());
-        k_mlp_infer<<<grid, FI_THREADS, FI_SMEM, s->stream>>>(n, s->nin, s->nout, X, s->d_xlo, s->d_xhi, W1p(s),
-                                                              b1p(s), s->d_W2h, b2p(s), s->d_W3h, b3p(s),
-                                                              s->d_ymean, s->d_ystd, Y, s->d_err, 4000000000ull);
-        NMS_CUDA_TRY(cudaGetLastError());
+        for (int o0 = 0; o0 < s->nout; o0 += FI_NO) {
+            const int part = std::min(FI_NO, s->nout - o0);
+            k_mlp_infer<<<grid, FI_THREADS, FI_SMEM, s->stream>>>(
+                n, s->nin, part, s->nout, X, s->d_xlo, s->d_xhi, W1p(s), b1p(s), s->d_W2h, b2p(s),
+                s->d_W3h + (int64_t)o0 * FI_H, b3p(s) + o0, s->d_ymean + o0, s->d_ystd + o0, Y + o0, s->d_err,
+                4000000000ull);
+            NMS_CUDA_TRY(cudaGetLastError());
+        }
         int32_t herr = 0;
         NMS_CUDA_TRY(cudaMemcpyAsync(&herr, s->d_err, 4, cudaMemcpyDeviceToHost, s->stream));
         NMS_CUDA_TRY(cudaStreamSynchronize(s->stream));

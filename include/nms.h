@@ -110,8 +110,7 @@ typedef struct {
     int32_t timing;          /* 1: record CUDA events around each stage (see
                                 nms_plan_stage_ms)                               */
     int32_t autotune;        /* tensor path: 1 = time candidate GEMM forms
-                                (one CTA per tile with A from weighted or
-                                trig-only tables, two-SM MMA),
+                                (one CTA per tile, two-SM MMA),
                                 kc and work-list granularities on a probe of
                                 the cells at plan creation and keep the
                                 fastest whose amplitude error (vs the
@@ -388,9 +387,8 @@ nms_status nms_dsft_direct_noalloc(int64_t n_cells, const double* Y, const doubl
  * (AUTO resolved), kc_cells = cells per TMEM accumulation chunk and
  * items_per_sm = work items per SM of each GEMM launch (tensor path; 0
  * otherwise), after autotuning when it was requested; gemm_form = 0 (one
- * CTA per 128 x 128 tile), 1 (the same with the weighted A operand formed in
- * shared memory from trig-only tables; one weight set) or 2 (two-SM MMA over
- * pairs of A tiles), -1 off the tensor path; mirror_y / mirror_z = 1 where the detector axis is
+ * CTA per 128 x 128 tile) or 2 (two-SM MMA over pairs of A tiles), -1 off
+ * the tensor path; mirror_y / mirror_z = 1 where the detector axis is
  * symmetric about q = 0 (lo = -hi) and the GEMM evaluates its q >= 0 half,
  * writing both signs (cos is even and sin odd in q; Sec. "Summation
  * approach" sum, split by parity).  Any pointer may be NULL. */

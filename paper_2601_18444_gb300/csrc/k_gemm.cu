@@ -56,9 +56,7 @@ constexpr int TC_BK = 64;           // k per block = cells per block, one 128-by
 constexpr int TC_BLOCK_BYTES = TC_BM * TC_BK * 2;   // 16 KB
 constexpr int TC_STAGES = 3;
 constexpr int TC_STAGE_BYTES = 4 * TC_BLOCK_BYTES;  // A_hi, A_lo, B_hi, B_lo
-constexpr int TC_THREADS = 576;     // warp 0 producer, warp 1 MMA, warps 2..17 epilogue (+ 18, 19 in MODE 1)
-constexpr int TC_T_BYTES = 32 * TC_BK * 4;   // MODE 1: trig rows of one A tile's 16 q_y nodes, FP32 (8 KB)
-constexpr int TC_W_BYTES = TC_BK * 16;       // MODE 1: one k-block's cell weights, float4 (1 KB)
+constexpr int TC_THREADS = 576;     // warp 0 producer, warp 1 MMA, warps 2..17 epilogue
 constexpr int TC_EPI_WARPS = 16;    // 4 per TMEM lane quadrant, 32 accumulator columns each
 #ifndef TC_RENORM
 #define TC_RENORM 4                 // 0: TwoSum per chunk; G > 0: chunk partials add into lo, TwoSum every G chunks
@@ -117,18 +115,12 @@ constexpr int TAB_THREADS = 256;
 //
 // B tables: block (nt, kb) holds rows n = nt*128 + 2 b_loc + r, b_loc < 64,
 // r = cos/sin of q_z,b Z_j.
-//
-// With T != NULL (one weight set; the GEMM applies the weights itself) the A
-// rows are replaced by the trig table T: block (mt, kb) holds 32 rows of 64
-// FP32 values, row 2 a_loc + p = cos/sin of q_y,a Y_j for the 16 q_y nodes
-// a = 16 mt + a_loc of A tile mt (zero beyond nyg): 8 KB instead of the
-// 32 KB of split, weighted A rows.
 __global__ void __launch_bounds__(TAB_THREADS, 3)
 k_tables(const float4* __restrict__ cpos, const float4* __restrict__ cw, int64_t wstride, int nch,
          const int64_t* __restrict__ kb_cell0, const int32_t* __restrict__ kb_ncell, const float2* __restrict__ qy,
          int nyg, const float2* __restrict__ qz, int nzg, float4 wscale, int64_t nkb, int mtiles, int ntiles,
          uint8_t* __restrict__ A_hi, uint8_t* __restrict__ A_lo, uint8_t* __restrict__ B_hi,
-         uint8_t* __restrict__ B_lo, float* __restrict__ T)
+         uint8_t* __restrict__ B_lo)
 {
     const int r = threadIdx.x >> 4;
     const int q4 = threadIdx.x & 15;
@@ -168,24 +160,6 @@ k_tables(const float4* __restrict__ cpos, const float4* __restrict__ cw, int64_t
             __stcs(reinterpret_cast<uint2*>(B_lo + blk + oc), cl);
             __stcs(reinterpret_cast<uint2*>(B_hi + blk + os), sh);
             __stcs(reinterpret_cast<uint2*>(B_lo + blk + os), sl);
-        }
-        if (T) {
-            // ---- trig rows of the GEMM's q_y nodes (one node per row group)
-            for (int g = r; g < ngroups; g += 16) {
-                const bool arow = g < nyg;
-                const float2 q = arow ? qy[g] : make_float2(0.f, 0.f);
-                float cs[4], sn[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    sincospif(2.0f * turns_reduced(q, cp[u].x, cp[u].y), &sn[u], &cs[u]);
-                    if (!arow) cs[u] = sn[u] = 0.f;
-                }
-                float* blk = T + ((size_t)(g >> 4) * nkb + kb) * (32 * TC_BK);
-                const int row = 2 * (g & 15);
-                __stcs(reinterpret_cast<float4*>(blk + row * TC_BK + k0), make_float4(cs[0], cs[1], cs[2], cs[3]));
-                __stcs(reinterpret_cast<float4*>(blk + (row + 1) * TC_BK + k0), make_float4(sn[0], sn[1], sn[2], sn[3]));
-            }
-            continue;
         }
         // ---- A rows, one weight set per pass
         for (int ps = 0; ps < passes; ++ps) {
@@ -468,26 +442,14 @@ struct GemmArgs {
     int32_t* err;
     uint64_t limit_ns;
     int mtiles, ntiles;   // tile rows of A and B (table layout)
-    // MODE 1: A is formed in shared memory from the trig table T and the weights
-    const float* T;       // [mtiles][nkb][32][64] FP32
-    const float4* cw;     // stacked cell weights (one set)
-    const int64_t* kb_cell0;
-    const int32_t* kb_ncell;
-    float4 wscale;        // per-channel operand scale of the weights
 };
 
-// MODE 1 stage: A_hi, A_lo (written by the generator warps), B_hi, B_lo, the
-// trig rows T and the weights W (bulk copies), rounded to 1 KB
 template <int MODE>
 struct GemmCfg {
     static constexpr int STAGES = MODE == 2 ? 4 : TC_STAGES;
-    static constexpr int STAGE_BYTES = MODE == 2 ? 3 * TC_BLOCK_BYTES
-                                     : MODE == 1 ? ((TC_STAGE_BYTES + TC_T_BYTES + TC_W_BYTES + 1023) / 1024) * 1024
-                                                 : TC_STAGE_BYTES;
+    static constexpr int STAGE_BYTES = MODE == 2 ? 3 * TC_BLOCK_BYTES : TC_STAGE_BYTES;
     static constexpr int B_BYTES = MODE == 2 ? TC_BLOCK_BYTES / 2 : TC_BLOCK_BYTES;   // B piece per CTA
     static constexpr int CG = MODE == 2 ? 2 : 1;
-    static constexpr int THREADS = MODE == 1 ? TC_THREADS + 64 : TC_THREADS;
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
 };
 
 // Amplitudes at (s_y q_y, s_z q_z) from the four real sums (each a two-float
@@ -514,7 +476,7 @@ __device__ __forceinline__ float4 combine_tf(float2 cc, float2 cs, float2 sc, fl
 // tmA / tmB (MODE 2): 2D maps over the chunk's tables as 128-byte rows,
 // boxes of 128 rows (an A block) and 64 rows (half a B block)
 template <int MODE>
-__global__ void __launch_bounds__(GemmCfg<MODE>::THREADS, 1)
+__global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_f16x3(const GemmArgs g, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB)
 {
     using C = GemmCfg<MODE>;
@@ -523,7 +485,6 @@ __global__ void __launch_bounds__(GemmCfg<MODE>::THREADS, 1)
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[STG];     // MODE 2, even CTA: both CTAs' stage bytes
     __shared__ __align__(8) uint64_t bar_empty[STG];
-    __shared__ __align__(8) uint64_t bar_gen[STG];      // MODE 1: the stage's A formed by both generator warps
     __shared__ __align__(8) uint64_t bar_acc_full[2];
     __shared__ __align__(8) uint64_t bar_acc_empty[2];
     __shared__ __align__(8) uint64_t bar_final;
@@ -541,7 +502,6 @@ __global__ void __launch_bounds__(GemmCfg<MODE>::THREADS, 1)
         for (int s = 0; s < STG; ++s) {
             mbar_init(&bar_full[s], 1);
             mbar_init(&bar_empty[s], 1);
-            mbar_init(&bar_gen[s], 2);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&bar_acc_full[b], 1);
@@ -590,24 +550,6 @@ __global__ void __launch_bounds__(GemmCfg<MODE>::THREADS, 1)
                         tma_load_2d_pair(st + TC_BLOCK_BYTES, &tmA, ra + g.mtiles * nk * 128, lead);
                         tma_load_2d_pair(st + 2 * TC_BLOCK_BYTES, &tmB, rb, lead);
                         tma_load_2d_pair(st + 2 * TC_BLOCK_BYTES + C::B_BYTES, &tmB, rb + g.ntiles * nk * 128, lead);
-                        ++i;
-                        if (++s == STG) {
-                            s = 0;
-                            par ^= 1u;
-                        }
-                        continue;
-                    }
-                    if (MODE == 1) {
-                        // B blocks, the A tile's trig rows and the k-block's weights
-                        const int nc = g.kb_ncell[kb];
-                        const uint32_t wbytes = (uint32_t)nc * 16u;
-                        mbar_arrive_expect_tx(&bar_full[s], 2 * TC_BLOCK_BYTES + TC_T_BYTES + wbytes);
-                        const size_t bo = ((size_t)nt * g.nkb + kb) * TC_BLOCK_BYTES;
-                        bulk_g2s(st + 2 * TC_BLOCK_BYTES, g.B_hi + bo, TC_BLOCK_BYTES, &bar_full[s]);
-                        bulk_g2s(st + 3 * TC_BLOCK_BYTES, g.B_lo + bo, TC_BLOCK_BYTES, &bar_full[s]);
-                        bulk_g2s(st + 4 * TC_BLOCK_BYTES, g.T + ((size_t)mt * g.nkb + kb) * (TC_T_BYTES / 4), TC_T_BYTES,
-                                 &bar_full[s]);
-                        bulk_g2s(st + 4 * TC_BLOCK_BYTES + TC_T_BYTES, g.cw + g.kb_cell0[kb], wbytes, &bar_full[s]);
                         ++i;
                         if (++s == STG) {
                             s = 0;
@@ -679,7 +621,7 @@ __global__ void __launch_bounds__(GemmCfg<MODE>::THREADS, 1)
                     const int k1 = min(item.kb1, k0 + g.kcb);
                     bool first = true;
                     for (int kb = k0; kb < k1; ++kb) {
-                        const bool okf = mbar_wait(MODE == 1 ? &bar_gen[s] : &bar_full[s], sph, g.limit_ns, &s_abort);
+                        const bool okf = mbar_wait(&bar_full[s], sph, g.limit_ns, &s_abort);
                         if (!okf) {
                             ok = false;
                             break;
@@ -716,83 +658,6 @@ __global__ void __launch_bounds__(GemmCfg<MODE>::THREADS, 1)
             if (MODE == 2) tc_commit_pair(&bar_final, (uint16_t)1);
             else tc_commit(&bar_final);
             mbar_wait_drain(&bar_final, 0);
-        }
-    } else if (warp >= 2 + TC_EPI_WARPS) {
-        // ---------------- MODE 1 generators (warps 18, 19): A_hi, A_lo of each
-        // stage from the trig rows T and the weights W the producer copied:
-        // A[2 (4 a + c) + p][j] = split(w_cj * T[2 a + p][j]).  Thread t takes
-        // the cells 8 (t & 7) .. + 7 and the q_y nodes 2 (t >> 3), + 1.
-        if (MODE == 1) {
-            const int t = threadIdx.x - 32 * (2 + TC_EPI_WARPS);   // 0..63
-            const int chunk = t & 7, grp = t >> 3;
-            int s = 0;
-            uint32_t sph = 0;
-            bool ok = true;
-            for (int it = unit0; it < g.n_items && ok; it += units) {
-                const GemmItem item = g.items[it];
-                for (int kb = item.kb0; kb < item.kb1; ++kb) {
-                    int okw = 0;
-                    if (lane == 0) okw = mbar_wait(&bar_full[s], sph, g.limit_ns, &s_abort) ? 1 : 0;
-                    okw = __shfl_sync(0xffffffffu, okw, 0);
-                    if (!okw) {
-                        if (lane == 0) {
-                            s_abort = 1;
-                            atomicExch(g.err, 4);
-                        }
-                        ok = false;
-                        break;
-                    }
-                    const int nc = g.kb_ncell[kb];
-                    uint8_t* stg = smem_raw + (sbase - smem_u32(smem_raw)) + (size_t)s * C::STAGE_BYTES;
-                    const float* Ts = reinterpret_cast<const float*>(stg + 4 * TC_BLOCK_BYTES);
-                    const float4* Ws = reinterpret_cast<const float4*>(stg + 4 * TC_BLOCK_BYTES + TC_T_BYTES);
-                    float4 w[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int j = 8 * chunk + u;
-                        const float4 v = j < nc ? Ws[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        w[u] = make_float4(v.x * g.wscale.x, v.y * g.wscale.y, v.z * g.wscale.z, v.w * g.wscale.w);
-                    }
-#pragma unroll
-                    for (int ai = 0; ai < 2; ++ai) {
-                        const int al = 2 * grp + ai;
-                        const float4* tcr = reinterpret_cast<const float4*>(Ts + (2 * al) * TC_BK + 8 * chunk);
-                        const float4* tsr = reinterpret_cast<const float4*>(Ts + (2 * al + 1) * TC_BK + 8 * chunk);
-                        const float4 c0 = tcr[0], c1 = tcr[1], s0 = tsr[0], s1 = tsr[1];
-                        const float tc[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-                        const float ts[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            float wc[8];
-#pragma unroll
-                            for (int u = 0; u < 8; ++u)
-                                wc[u] = c == 0 ? w[u].x : c == 1 ? w[u].y : c == 2 ? w[u].z : w[u].w;
-                            uint4 h, l;
-                            const int m = 2 * (4 * al + c);
-                            split_h2(wc[0] * tc[0], wc[1] * tc[1], h.x, l.x);
-                            split_h2(wc[2] * tc[2], wc[3] * tc[3], h.y, l.y);
-                            split_h2(wc[4] * tc[4], wc[5] * tc[5], h.z, l.z);
-                            split_h2(wc[6] * tc[6], wc[7] * tc[7], h.w, l.w);
-                            *reinterpret_cast<uint4*>(stg + swz_offset(m, 8 * chunk)) = h;
-                            *reinterpret_cast<uint4*>(stg + TC_BLOCK_BYTES + swz_offset(m, 8 * chunk)) = l;
-                            split_h2(wc[0] * ts[0], wc[1] * ts[1], h.x, l.x);
-                            split_h2(wc[2] * ts[2], wc[3] * ts[3], h.y, l.y);
-                            split_h2(wc[4] * ts[4], wc[5] * ts[5], h.z, l.z);
-                            split_h2(wc[6] * ts[6], wc[7] * ts[7], h.w, l.w);
-                            *reinterpret_cast<uint4*>(stg + swz_offset(m + 1, 8 * chunk)) = h;
-                            *reinterpret_cast<uint4*>(stg + TC_BLOCK_BYTES + swz_offset(m + 1, 8 * chunk)) = l;
-                        }
-                    }
-                    // the tensor cores read A through the async proxy
-                    fence_proxy_async_smem();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&bar_gen[s]);
-                    if (++s == STG) {
-                        s = 0;
-                        sph ^= 1u;
-                    }
-                }
-            }
         }
     } else {
         // ---------------- epilogue: drain TMEM chunks into two-float sums
@@ -1060,36 +925,18 @@ cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t* err, cudaStream_t s
 }
 
 // ------------------------------------------------------------------ launchers
-// Table workspace layout of one chunk of nkb k-blocks:
-//   gen = 0: A_hi, A_lo [mtiles][nkb] x 16 KB, then B_hi, B_lo [ntiles][nkb] x 16 KB;
-//   gen = 1: T [mtiles][nkb] x 8 KB (FP32 trig rows), then B_hi, B_lo.
-size_t tc_table_bytes_per_kb(int mtiles, int ntiles, int gen)
-{
-    return gen ? (size_t)mtiles * TC_T_BYTES + (size_t)ntiles * 2 * TC_BLOCK_BYTES
-               : (size_t)(mtiles + ntiles) * 2 * TC_BLOCK_BYTES;
-}
-
 cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, int64_t wstride, int nch, const int64_t* kb_cell0,
                              const int32_t* kb_ncell, int64_t nkb, const float2* qy, int nyg, const float2* qz, int nzg,
-                             int mtiles, int ntiles, const float wscale[4], int gen, void* tab, cudaStream_t s)
+                             int mtiles, int ntiles, const float wscale[4], void* tab, cudaStream_t s)
 {
+    uint8_t* A_hi = (uint8_t*)tab;
+    uint8_t* A_lo = A_hi + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
+    uint8_t* B_hi = A_lo + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
+    uint8_t* B_lo = B_hi + (size_t)ntiles * nkb * TC_BLOCK_BYTES;
     if (nkb <= 0) return cudaSuccess;
-    if (gen && nch != 4) return cudaErrorInvalidValue;
-    uint8_t* base = (uint8_t*)tab;
-    uint8_t *A_hi = nullptr, *A_lo = nullptr, *B_hi, *B_lo;
-    float* T = nullptr;
-    if (gen) {
-        T = (float*)base;
-        B_hi = base + (size_t)mtiles * nkb * TC_T_BYTES;
-    } else {
-        A_hi = base;
-        A_lo = A_hi + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
-        B_hi = A_lo + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
-    }
-    B_lo = B_hi + (size_t)ntiles * nkb * TC_BLOCK_BYTES;
     k_tables<<<(unsigned)std::min<int64_t>(nkb, 0x7fffffff), TAB_THREADS, 0, s>>>(
         cpos, cw, wstride, nch, kb_cell0, kb_ncell, qy, nyg, qz, nzg,
-        make_float4(wscale[0], wscale[1], wscale[2], wscale[3]), nkb, mtiles, ntiles, A_hi, A_lo, B_hi, B_lo, T);
+        make_float4(wscale[0], wscale[1], wscale[2], wscale[3]), nkb, mtiles, ntiles, A_hi, A_lo, B_hi, B_lo);
     return cudaGetLastError();
 }
 
@@ -1123,51 +970,35 @@ static cudaError_t encode_row_maps(const void* tab, int64_t rows, CUtensorMap* t
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <int MODE>
-static cudaError_t gemm_attr()
-{
-    static bool done = false;
-    if (done) return cudaSuccess;
-    const cudaError_t e =
-        cudaFuncSetAttribute(k_gemm_f16x3<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, GemmCfg<MODE>::SMEM);
-    if (e == cudaSuccess) done = true;
-    return e;
-}
-
-// mode 0: one CTA per tile (tables hold A); 1: the same with A formed in
-// shared memory from the trig table and the weights (gen tables); 2: two-SM MMA
 cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
                            int grid, int kcb, double* P, double* F, int64_t lo_off, const AxisMap& ax, int nch,
-                           const double scale[4], int32_t* err, uint64_t limit_ns, int mode, const float4* cw,
-                           const int64_t* kb_cell0, const int32_t* kb_ncell, const float wscale[4], cudaStream_t s)
+                           const double scale[4], int32_t* err, uint64_t limit_ns, int mode, cudaStream_t s)
 {
-    if (mode < 0 || mode > 2 || (mode == 2 && ((grid & 1) || (mtiles & 1))) || (mode == 1 && nch != 4))
-        return cudaErrorInvalidValue;
-    cudaError_t e = mode == 0 ? gemm_attr<0>() : mode == 1 ? gemm_attr<1>() : gemm_attr<2>();
-    if (e != cudaSuccess) return e;
+    static_assert(GemmCfg<0>::STAGES * GemmCfg<0>::STAGE_BYTES == GemmCfg<2>::STAGES * GemmCfg<2>::STAGE_BYTES,
+                  "one dynamic shared-memory size for every mode");
+    static bool attr = false;
+    const int smem = GemmCfg<0>::STAGES * GemmCfg<0>::STAGE_BYTES + 1024;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_f16x3<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_gemm_f16x3<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if ((mode != 0 && mode != 2) || (mode == 2 && ((grid & 1) || (mtiles & 1)))) return cudaErrorInvalidValue;
     // MODE 2: tensor maps over the chunk's tables as rows of 128 bytes
     const int64_t rows = (int64_t)(2 * mtiles + 2 * ntiles) * nkb * (TC_BLOCK_BYTES / 128);
     CUtensorMap tm[2];
     memset(tm, 0, sizeof(tm));
     if (mode == 2) {
         if (rows > 0x7fffffffll) return cudaErrorInvalidValue;   // row coordinates are 32-bit
-        e = encode_row_maps(tab, rows, tm);
+        const cudaError_t e = encode_row_maps(tab, rows, tm);
         if (e != cudaSuccess) return e;
     }
     GemmArgs ga;
-    memset(&ga, 0, sizeof(ga));
-    if (mode == 1) {
-        ga.T = (const float*)tab;
-        ga.B_hi = (const uint8_t*)tab + (size_t)mtiles * nkb * TC_T_BYTES;
-        ga.cw = cw;
-        ga.kb_cell0 = kb_cell0;
-        ga.kb_ncell = kb_ncell;
-        ga.wscale = make_float4(wscale[0], wscale[1], wscale[2], wscale[3]);
-    } else {
-        ga.A_hi = (const uint8_t*)tab;
-        ga.A_lo = ga.A_hi + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
-        ga.B_hi = ga.A_lo + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
-    }
+    ga.A_hi = (const uint8_t*)tab;
+    ga.A_lo = ga.A_hi + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
+    ga.B_hi = ga.A_lo + (size_t)mtiles * nkb * TC_BLOCK_BYTES;
     ga.B_lo = ga.B_hi + (size_t)ntiles * nkb * TC_BLOCK_BYTES;
     ga.nkb = nkb;
     ga.items = (const GemmItem*)items;
@@ -1184,17 +1015,13 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
     ga.mtiles = mtiles;
     ga.ntiles = ntiles;
     if (mode == 0) {
-        k_gemm_f16x3<0><<<grid, GemmCfg<0>::THREADS, GemmCfg<0>::SMEM, s>>>(ga, tm[0], tm[1]);
-        return cudaGetLastError();
-    }
-    if (mode == 1) {
-        k_gemm_f16x3<1><<<grid, GemmCfg<1>::THREADS, GemmCfg<1>::SMEM, s>>>(ga, tm[0], tm[1]);
+        k_gemm_f16x3<0><<<grid, TC_THREADS, smem, s>>>(ga, tm[0], tm[1]);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(GemmCfg<2>::THREADS);
-    cfg.dynamicSmemBytes = GemmCfg<2>::SMEM;
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;

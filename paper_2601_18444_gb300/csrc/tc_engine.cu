@@ -33,12 +33,10 @@ namespace nms {
 // launchers in k_gemm.cu / k_batch.cu
 cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, int64_t wstride, int nch, const int64_t* kb_cell0,
                              const int32_t* kb_ncell, int64_t nkb, const float2* qy, int nyg, const float2* qz, int nzg,
-                             int mtiles, int ntiles, const float wscale[4], int gen, void* tab, cudaStream_t s);
+                             int mtiles, int ntiles, const float wscale[4], void* tab, cudaStream_t s);
 cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
                            int grid, int kcb, double* P, double* F, int64_t lo_off, const AxisMap& ax, int nch,
-                           const double scale[4], int32_t* err, uint64_t limit_ns, int mode, const float4* cw,
-                           const int64_t* kb_cell0, const int32_t* kb_ncell, const float wscale[4], cudaStream_t s);
-size_t tc_table_bytes_per_kb(int mtiles, int ntiles, int gen);
+                           const double scale[4], int32_t* err, uint64_t limit_ns, int mode, cudaStream_t s);
 cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, const AxisMap& ax, int ntiles, int nch,
                              const double scale[4], double* F, int64_t lo_off, cudaStream_t s);
 size_t tc_item_bytes();
@@ -111,8 +109,7 @@ struct TcState {
     int nsets = 1;               // weight sets (loop mode), stacked along the GEMM rows
     int nch = 4;                 // channels per output: 4 x (weight sets rounded up to a power of two)
     int64_t wstride = 0;         // cells between weight sets in d_cw_b (= R_b * n)
-    int mode = 0;                // GEMM form: 0 one CTA per tile, 1 the same with A formed in shared memory
-                                 // (trig tables, one weight set), 2 two-SM MMA over A-tile pairs (even mtiles)
+    int mode = 0;                // GEMM form: 0 one CTA per tile, 2 two-SM MMA over A-tile pairs (even mtiles)
     bool mode_forced = false;    // set by NMS_GEMM_MODE: the autotuner keeps it
     bool objects = false;        // per-object amplitudes (dilute split) with shifts
     int R_b = 1;                 // rotations prepared per rotation batch
@@ -415,7 +412,7 @@ static void tune_file_read()
     char key[256];
     int a, b, m;
     while (fscanf(f, "%255s %d %d %d", key, &a, &b, &m) == 4)
-        if (a > 0 && b > 0 && m >= 0 && m <= 2) g_tune_cache[key] = {a, b, m};   // a form the plan allows is checked on use
+        if (a > 0 && b > 0 && m >= 0 && m <= 2) g_tune_cache[key] = {a, b, m};
     fclose(f);
 }
 
@@ -503,7 +500,7 @@ nms_status tc_autotune(Plan& p, TcState& t)
     const int ipss[3] = {4, 8, 16};
     std::vector<int> modes;
     for (int m = 0; m < 3; ++m)
-        if (t.mode_forced ? m == mode0 : (m == 0 || (m == 1 && t.nch == 4) || (m == 2 && t.mtiles % 2 == 0)))
+        if (t.mode_forced ? m == mode0 : (m == 0 || (m == 2 && t.mtiles % 2 == 0)))
             modes.push_back(m);
     double* saveP = t.d_P;
     std::vector<TuneChoice> cand;
@@ -527,12 +524,11 @@ nms_status tc_autotune(Plan& p, TcState& t)
         for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {
             ce = tc_launch_tables(t.d_cpos_b, t.d_cw_b, t.wstride, t.nch, S.d_kb_cell0, S.d_kb_ncell, ch.nkb,
                                   t.d_qy + t.ax.hy, t.ax.nyg, t.d_qz + t.ax.hz, t.ax.nzg, t.mtiles, t.ntiles, wscale,
-                                  t.mode == 1, p.d_tab, s);
+                                  p.d_tab, s);
             if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
             if (ce == cudaSuccess)
                 ce = tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles, S.d_items, ch.n_items, ch.grid, kcb, P,
-                                    d_Fp, lo_off, t.ax, t.nch, scale, p.d_err, limit, t.mode, t.d_cw_b, S.d_kb_cell0,
-                                    S.d_kb_ncell, wscale, s);
+                                    d_Fp, lo_off, t.ax, t.nch, scale, p.d_err, limit, t.mode, s);
             if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
             if (ce == cudaSuccess)
                 ce = tc_launch_reduce(P, S.d_reds, ch.n_red, t.ax, t.ntiles, t.nch, scale, d_Fp, lo_off, s);
@@ -645,14 +641,10 @@ nms_status tc_setup(Plan& p)
     // half of it from the peer, and it measured slower).  NMS_GEMM_MODE = 0
     // or 2 forces a form the grid allows (diagnostics, tests); the autotuner
     // times both.
-    // Form 0 by default.  Form 1 (one weight set) forms A in shared memory
-    // from trig-only tables and the weights: 8 KB instead of 32 KB of A tables
-    // per A tile and k-block, but its two generator warps hold the MMA back
-    // (box GEMM 39 against 20.5 ms); the autotuner times it.
     t->mode = 0;
     if (const char* gm = getenv("NMS_GEMM_MODE")) {
         const int want = atoi(gm);
-        if (want == 0 || (want == 1 && t->nch == 4) || (want == 2 && t->mtiles % 2 == 0)) {
+        if (want == 0 || (want == 2 && t->mtiles % 2 == 0)) {
             t->mode = want;
             t->mode_forced = true;
         }
@@ -715,9 +707,7 @@ nms_status tc_setup(Plan& p)
     // total amplitude per prepared rotation and weight set
     if (t->objects) NMS_CUDA_TRY(plan_malloc(&t->d_Ftot_b, (size_t)t->R_b * t->nsets * 8 * np * sizeof(double)));
     // phase tables: as many k-blocks as the workspace allows
-    // the autotuner may pick any form: size the chunks for the largest tables
-    const int64_t per_kb =
-        (int64_t)tc_table_bytes_per_kb(t->mtiles, t->ntiles, (p.opt.autotune || t->mode != 1) ? 0 : 1);
+    const int64_t per_kb = (int64_t)(t->mtiles + t->ntiles) * 2 * (int64_t)tc_block_bytes();
     const int64_t budget = p.opt.workspace_bytes > 0 ? p.opt.workspace_bytes
                                                      : (int64_t)std::min<size_t>(free_b / 3, (size_t)8 << 30);
     int64_t total_kb = 0;
@@ -795,14 +785,13 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
                 p.timer.begin(ST_TABLES);
                 NMS_CUDA_TRY(tc_launch_tables(t.d_cpos_b, t.d_cw_b, t.wstride, t.nch, S.d_kb_cell0 + ch.kb_off,
                                               S.d_kb_ncell + ch.kb_off, ch.nkb, t.d_qy + t.ax.hy, t.ax.nyg,
-                                              t.d_qz + t.ax.hz, t.ax.nzg, t.mtiles, t.ntiles, wscale, t.mode == 1,
-                                              p.d_tab, s));
+                                              t.d_qz + t.ax.hz, t.ax.nzg, t.mtiles, t.ntiles, wscale, p.d_tab, s));
                 p.timer.end(ST_TABLES, 1);
                 p.timer.begin(ST_GEMM);
                 NMS_CUDA_TRY(tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles,
                                             (const char*)S.d_items + ch.item_off * tc_item_bytes(), ch.n_items, ch.grid,
                                             t.kcb, t.d_P, t.d_Fb, lo_off, t.ax, t.nch, scale, p.d_err, limit, t.mode,
-                                            t.d_cw_b, S.d_kb_cell0 + ch.kb_off, S.d_kb_ncell + ch.kb_off, wscale, s));
+                                            s));
                 p.timer.end(ST_GEMM, 1);
                 p.timer.begin(ST_REDUCE);
                 NMS_CUDA_TRY(tc_launch_reduce(t.d_P, (const char*)S.d_reds + ch.red_off * tc_red_bytes(), ch.n_red, t.ax,

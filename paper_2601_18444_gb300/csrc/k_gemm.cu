@@ -784,6 +784,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     act = act && (p == 0 || ax.mz);
                 }
                 const float sc = g.scale[ch & 3];
+                if (!item.two) {
+                    // the output's only piece, rounded to FP32: the two-float
+                    // sums are rounded first (one word per column to exchange),
+                    // then combined; error <= 2^-24 (|cc| + |ss| + |F|)
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const uint64_t x = f2_add(hi[i], lo[i]);
+                        const uint64_t y = __shfl_xor_sync(0xffffffffu, x, 1);
+                        const float xc = f2_lane0(x), xs = f2_lane1(x), yc = f2_lane0(y), ys = f2_lane1(y);
+                        const float cc = p ? yc : xc, cs = p ? ys : xs, scs = p ? xc : yc, ss = p ? xs : ys;
+                        const int bg = b0 + i;
+                        if (!act || bg >= ax.nzg) continue;
+                        for (int zs = zfirst; zs <= zlast; ++zs) {
+                            const float sz = zs ? -1.f : 1.f;
+                            const int b_out = zs ? ax.nz - 1 - ax.hz - bg : ax.hz + bg;
+                            if (zs && b_out == ax.hz + bg) continue;     // q_z = 0 is its own mirror
+                            const float re = fmaf(-sy * sz, ss, cc);
+                            const float im = -fmaf(sz, cs, sy * scs);
+                            Fo[(int64_t)b_out * mrows + (int64_t)g.nch * a_out] = make_float2(sc * re, sc * im);
+                        }
+                    }
+                } else
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
                     // partner pair: all lanes take part in the exchange

@@ -60,6 +60,52 @@ __global__ void k_prep_rot(int64_t n, int n_sets, int64_t wstride, const double*
     }
 }
 
+// The same for nrl rotations in one launch: rotation rot0 + y of the device
+// array rot [n_rot][9] (row-major) into the slot at y * n of the stacked arrays.
+__global__ void k_prep_rot_batch(int64_t n, int n_sets, int64_t wstride, const double* __restrict__ pos,
+                                 const double* __restrict__ vol, const double* __restrict__ nuc,
+                                 const double* __restrict__ mag, const double* __restrict__ cen_cell,
+                                 const double* __restrict__ rot, int rot0, float4* __restrict__ cpos,
+                                 float4* __restrict__ cw)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int rl = blockIdx.y;
+    const double* r = rot + 9 * (int64_t)(rot0 + rl);
+    double x = pos[3 * j], y = pos[3 * j + 1], z = pos[3 * j + 2];
+    if (cen_cell) {
+        x += cen_cell[3 * j];
+        y += cen_cell[3 * j + 1];
+        z += cen_cell[3 * j + 2];
+    }
+    const int64_t o = (int64_t)rl * n + j;
+    cpos[o] = split_pos(r[3] * x + r[4] * y + r[5] * z, r[6] * x + r[7] * y + r[8] * z);
+    const double v = vol ? vol[j] : 1.0;
+    for (int st = 0; st < n_sets; ++st) {
+        const int64_t js = (int64_t)st * n + j;
+        const double wn = nuc ? v * nuc[js] : 0.0;
+        double wx = 0.0, wy = 0.0, wz = 0.0;
+        if (mag) {
+            const double mx = mag[3 * js], my = mag[3 * js + 1], mz = mag[3 * js + 2];
+            wx = v * (r[0] * mx + r[1] * my + r[2] * mz);
+            wy = v * (r[3] * mx + r[4] * my + r[5] * mz);
+            wz = v * (r[6] * mx + r[7] * my + r[8] * mz);
+        }
+        cw[(int64_t)st * wstride + o] = make_float4((float)wn, (float)wx, (float)wy, (float)wz);
+    }
+}
+
+cudaError_t launch_prep_rot_batch(const Plan& p, const double* d_rot, int rot0, int nrl, bool global, float4* cpos,
+                                  float4* cw, int64_t wstride, cudaStream_t s)
+{
+    const int64_t n = p.n_cells;
+    if (n <= 0 || nrl <= 0) return cudaSuccess;
+    k_prep_rot_batch<<<dim3((unsigned)((n + 255) / 256), (unsigned)nrl), 256, 0, s>>>(
+        n, p.n_sets, wstride, p.d_pos, p.d_vol, p.d_nuc, p.d_mag, global ? p.d_cen_cell : nullptr, d_rot, rot0, cpos,
+        cw);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_prep_rot(const Plan& p, const RotMat& R, bool global, float4* cpos, float4* cw, int64_t wstride,
                             cudaStream_t s)
 {

@@ -452,19 +452,9 @@ struct GemmCfg {
     static constexpr int CG = MODE == 2 ? 2 : 1;
 };
 
-// Amplitudes at (s_y q_y, s_z q_z) from the four real sums (each a two-float
-// (hi, lo) pair): F = (cc - s_y s_z ss) - i (s_z cs + s_y sc).  Rounded to
-// FP32 (re, im); the two differences are taken word by word, so the rounding
-// error is about 2^-23 |F| plus 2^-24 of the low words.
-__device__ __forceinline__ float2 combine_f32(float2 cc, float2 cs, float2 sc, float2 ss, float sy, float sz)
-{
-    const float k = -sy * sz;
-    const float re = fmaf(k, ss.x, cc.x) + fmaf(k, ss.y, cc.y);
-    const float im = -(fmaf(sz, cs.x, sy * sc.x) + fmaf(sz, cs.y, sy * sc.y));
-    return make_float2(re, im);
-}
-
-// The same as a normalised two-float complex value (re hi, re lo, im hi, im lo).
+// Amplitudes at (s_y q_y, s_z q_z) from the four real sums cc, cs, sc, ss
+// (each a two-float (hi, lo) pair): F = (cc - s_y s_z ss) - i (s_z cs + s_y sc),
+// as a normalised two-float complex value (re hi, re lo, im hi, im lo).
 __device__ __forceinline__ float4 combine_tf(float2 cc, float2 cs, float2 sc, float2 ss, float sy, float sz)
 {
     const float k = -sy * sz;
@@ -822,22 +812,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const float sz = zs ? -1.f : 1.f;
                         const int b_out = zs ? ax.nz - 1 - ax.hz - bg : ax.hz + bg;
                         if (zs && b_out == ax.hz + bg) continue;     // q_z = 0 is its own mirror
+                        // an output of several pieces: two-float, stored by its
+                        // first piece and added by the later ones
                         float2* oh = Fo + (int64_t)b_out * mrows + (int64_t)g.nch * a_out;
-                        if (item.two) {
-                            float4 v = combine_tf(cc, cs, scs, ss, sy, sz);
-                            v = make_float4(sc * v.x, sc * v.y, sc * v.z, sc * v.w);
-                            float2* ol = oh + g.lo_off;
-                            if (!item.store) {
-                                const float2 h = *oh, l = *ol;
-                                v = tf_add4(v, make_float4(h.x, l.x, h.y, l.y));
-                            }
-                            *oh = make_float2(v.x, v.z);
-                            *ol = make_float2(v.y, v.w);
-                        } else {
-                            // the output's only piece: its value rounded to FP32
-                            const float2 v = combine_f32(cc, cs, scs, ss, sy, sz);
-                            *oh = make_float2(sc * v.x, sc * v.y);
+                        float4 v = combine_tf(cc, cs, scs, ss, sy, sz);
+                        v = make_float4(sc * v.x, sc * v.y, sc * v.z, sc * v.w);
+                        float2* ol = oh + g.lo_off;
+                        if (!item.store) {
+                            const float2 h = *oh, l = *ol;
+                            v = tf_add4(v, make_float4(h.x, l.x, h.y, l.y));
                         }
+                        *oh = make_float2(v.x, v.z);
+                        *ol = make_float2(v.y, v.w);
                     }
                 }
             }

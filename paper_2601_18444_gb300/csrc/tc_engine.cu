@@ -46,6 +46,8 @@ int tc_block_cells();
 float tc_operand_scale();
 cudaError_t launch_prep_rot(const Plan& p, const RotMat& R, bool global, float4* cpos, float4* cw, int64_t wstride,
                             cudaStream_t s);
+cudaError_t launch_prep_rot_batch(const Plan& p, const double* d_rot, int rot0, int nrl, bool global, float4* cpos,
+                                  float4* cw, int64_t wstride, cudaStream_t s);
 cudaError_t launch_centres(int n_out, const int32_t* out_obj, const int32_t* out_rot, int rot0, const double* rot,
                            const double* cen, float4* cyz, cudaStream_t s);
 cudaError_t launch_gacc_batch(const FbView& V, int n_out, double* G, cudaStream_t s);
@@ -772,13 +774,9 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
         const int nrl = std::min(t.R_b, p.n_rot - rb0);
         const Schedule& S = nrl == t.R_b ? t.full : t.last;
         p.timer.begin(ST_PREP);
-        for (int rl = 0; rl < nrl; ++rl) {
-            RotMat R;
-            memcpy(R.m, &p.h_rot[9 * (size_t)(rb0 + rl)], sizeof(R.m));
-            NMS_CUDA_TRY(launch_prep_rot(p, R, !t.objects, t.d_cpos_b + (size_t)rl * n, t.d_cw_b + (size_t)rl * n,
-                                         t.wstride, s));
-        }
-        p.timer.end(ST_PREP, nrl);
+        // the batch's rotations in one launch (rotation rb0 + rl into slot rl)
+        NMS_CUDA_TRY(launch_prep_rot_batch(p, t.d_rot, rb0, nrl, !t.objects, t.d_cpos_b, t.d_cw_b, t.wstride, s));
+        p.timer.end(ST_PREP, 1);
         if (t.objects) NMS_CUDA_TRY(cudaMemsetAsync(t.d_Ftot_b, 0, (size_t)nrl * nS * F4 * sizeof(double), s));
         for (const OutBatch& ob : S.batches) {
             for (const Chunk& ch : ob.chunks) {

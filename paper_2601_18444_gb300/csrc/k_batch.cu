@@ -180,21 +180,28 @@ __device__ __forceinline__ int pair_idx(int a, int b)  // a < b
     return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5);
 }
 
+// A Hermitian product set G of one pixel holds |F_c|^2 at k = c < 4 and
+// Re, Im of F_i conj(F_j) at k = 4 + 2 m, 5 + 2 m for the pair m =
+// pair_idx(i, j).  Its conjugate (the set at the mirror pixel -q) changes
+// the sign of the imaginary parts.
+__device__ __forceinline__ double g_conj_sign(int k) { return (k >= 5 && (k & 1)) ? -1.0 : 1.0; }
+
 // G[16][npix] += sum_o F_o F_o^dagger.  GEMM outputs (F_b, FbView layout;
-// threads run over q_y fastest so a warp reads contiguous channel rows) or
-// FP64 totals ([4][npix] complex per output at ostride2 complex values,
-// threads over pixels).
+// threads over the stored pixels, q_y fastest, so a warp reads contiguous
+// channel rows; a pixel whose point mirror is not stored also adds the
+// conjugate products there) or FP64 totals ([4][npix] complex per output at
+// ostride2 complex values, threads over pixels).
 template <bool TF>
 __global__ void k_gacc_batch(FbView V, const double2* __restrict__ T, int n_out, int64_t ostride2, int64_t npix,
                              double* __restrict__ G)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= npix) return;
+    if (t >= (TF ? V.stored_pixels() : npix)) return;
     int64_t p = t;
     int a = 0, b = 0;
     if constexpr (TF) {
         a = (int)(t % V.ny);
-        b = (int)(t / V.ny);
+        b = V.zs0 + (int)(t / V.ny);
         p = (int64_t)a * V.nz + b;
     }
     float hi[16], lo[16];
@@ -225,13 +232,19 @@ __global__ void k_gacc_batch(FbView V, const double2* __restrict__ T, int n_out,
     }
 #pragma unroll
     for (int k = 0; k < 16; ++k) G[(int64_t)k * npix + p] += (double)hi[k] + (double)lo[k];
+    if (TF && V.mirror_unstored(b)) {
+        const int64_t pm = (int64_t)(V.ny - 1 - a) * V.nz + (V.nz - 1 - b);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) G[(int64_t)k * npix + pm] += g_conj_sign(k) * ((double)hi[k] + (double)lo[k]);
+    }
 }
 
 cudaError_t launch_gacc_batch(const FbView& V, int n_out, double* G, cudaStream_t s)
 {
     if (n_out <= 0) return cudaSuccess;
     const int64_t npix = (int64_t)V.ny * V.nz;
-    k_gacc_batch<true><<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(V, nullptr, n_out, 0, npix, G);
+    const int64_t nt = V.stored_pixels();
+    k_gacc_batch<true><<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(V, nullptr, n_out, 0, npix, G);
     return cudaGetLastError();
 }
 
@@ -254,10 +267,7 @@ __global__ void k_tf_to_f64(FbView V, int64_t o, double2* __restrict__ dst)
     const int c = (int)(i / npix);
     const int64_t p = i % npix;
     const int a = (int)(p / V.nz), b = (int)(p % V.nz);
-    const int64_t j = V.idx(o, a, b) + c;
-    const float2 h = V.hi[j];
-    const float2 l = V.two[o] ? V.lo[j] : make_float2(0.f, 0.f);
-    dst[i] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+    dst[i] = V.load_f64(o, a, b, c);
 }
 
 cudaError_t launch_tf_to_f64(const FbView& V, int64_t o, double* dst, cudaStream_t s)
@@ -271,8 +281,11 @@ cudaError_t launch_tf_to_f64(const FbView& V, int64_t o, double* dst, cudaStream
 //   G_dil[16][p]              += F_o F_o^dagger                  (dilute part)
 //   Ftot[out_rot[o]][c][p]    += F_o[c][p] exp(-i (q_y cy_o + q_z cz_o))
 // The shift factor of pixel (a, b) is the product of the output's factors
-// along q_y and q_z (k_shift_factors).  One thread per pixel; q_y runs
-// fastest, so a warp reads contiguous channel rows of F_b.
+// along q_y and q_z (k_shift_factors).  One thread per stored pixel; q_y
+// runs fastest, so a warp reads contiguous channel rows of F_b.  When only
+// the q_z >= 0 half is stored (FbView.zs0 > 0) each thread also adds the
+// conjugates of its two sums at the mirror pixel -q: the product set and the
+// shifted sum of -q are the conjugates of those at q.
 //
 // Each thread stages its own inputs of the next DS_DEPTH - 1 outputs (32 B of
 // F, 16 B of shift factors) in shared memory with cp.async, so the loads in
@@ -313,15 +326,19 @@ k_dilute_shift_batch(FbView V, int n_out, const float2* __restrict__ eyz, const 
 {
     __shared__ float4 ring[DS_DEPTH][3][128];   // per slot: channels 0-1, channels 2-3, (e_y, e_z)
     const int64_t npix = (int64_t)V.ny * V.nz;
-    if (npix <= 0 || n_out <= 0) return;
-    // threads past the last pixel compute on the last one and store nothing,
-    // so every lane of a warp takes part in the shuffles below
+    const int64_t nst = V.stored_pixels();
+    if (nst <= 0 || n_out <= 0) return;
+    // threads past the last stored pixel compute on the last one and store
+    // nothing, so every lane of a warp takes part in the shuffles below
     const int64_t tid0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool act = tid0 < npix;
-    const int64_t tid = act ? tid0 : npix - 1;
+    const bool act = tid0 < nst;
+    const int64_t tid = act ? tid0 : nst - 1;
     const int lt = threadIdx.x;
-    const int qa = (int)(tid % V.ny), qb = (int)(tid / V.ny);
+    const int qa = (int)(tid % V.ny), qb = V.zs0 + (int)(tid / V.ny);
     const int64_t p = (int64_t)qa * V.nz + qb;
+    // the point mirror -q, written here when it is not stored (conjugates)
+    const bool mir = act && V.mirror_unstored(qb);
+    const int64_t pm = (int64_t)(V.ny - 1 - qa) * V.nz + (V.nz - 1 - qb);
     const int ne = V.ny + V.nz;
     const float2* fsrc = V.hi + V.idx(0, qa, qb);   // 16-byte aligned: channel groups of 4 complex FP32
     const float2* eysrc = eyz + qa;
@@ -355,12 +372,20 @@ k_dilute_shift_batch(FbView V, int n_out, const float2* __restrict__ eyz, const 
         if (act)
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-            double2* t = Ftot + (int64_t)rot * tstride2 + (int64_t)c * npix + p;
-            double2 v = *t;
-            v.x += (double)th[2 * c] + (double)tl[2 * c];
-            v.y += (double)th[2 * c + 1] + (double)tl[2 * c + 1];
-            *t = v;
-        }
+                const double re = (double)th[2 * c] + (double)tl[2 * c];
+                const double im = (double)th[2 * c + 1] + (double)tl[2 * c + 1];
+                double2* t = Ftot + (int64_t)rot * tstride2 + (int64_t)c * npix;
+                double2 v = t[p];
+                v.x += re;
+                v.y += im;
+                t[p] = v;
+                if (mir) {
+                    v = t[pm];
+                    v.x += re;
+                    v.y -= im;
+                    t[pm] = v;
+                }
+            }
 #pragma unroll
         for (int k = 0; k < 8; ++k) { th[k] = 0.f; tl[k] = 0.f; }
     };
@@ -415,7 +440,11 @@ k_dilute_shift_batch(FbView V, int n_out, const float2* __restrict__ eyz, const 
     flush(cur);
     if (act)
 #pragma unroll
-        for (int k = 0; k < 16; ++k) Gdil[(int64_t)k * npix + p] += ((double)gh[k] + (double)gl[k]) + (double)rg[k];
+        for (int k = 0; k < 16; ++k) {
+            const double g = ((double)gh[k] + (double)gl[k]) + (double)rg[k];
+            Gdil[(int64_t)k * npix + p] += g;
+            if (mir) Gdil[(int64_t)k * npix + pm] += g_conj_sign(k) * g;
+        }
 }
 
 // The same pass for detectors whose q_y rows are whole multiples of 128
@@ -451,9 +480,12 @@ k_dilute_shift_bulk(FbView V, int n_out, const float2* __restrict__ eyz, const i
     __shared__ volatile int abort_flag;
     const int64_t npix = (int64_t)V.ny * V.nz;
     const int lt = threadIdx.x, lane = lt & 31;
-    const int64_t t0 = (int64_t)blockIdx.x * 128;
-    const int qa = (int)(t0 % V.ny) + lt, qb = (int)(t0 / V.ny);   // one q_z row per block
+    const int64_t t0 = (int64_t)blockIdx.x * 128;   // stored pixels, q_y fastest
+    const int qa = (int)(t0 % V.ny) + lt, qb = V.zs0 + (int)(t0 / V.ny);   // one q_z row per block
     const int64_t p = (int64_t)qa * V.nz + qb;
+    // the point mirror -q, written here when it is not stored (conjugates)
+    const bool mir = V.mirror_unstored(qb);
+    const int64_t pm = (int64_t)(V.ny - 1 - qa) * V.nz + (V.nz - 1 - qb);
     const int ne = V.ny + V.nz;
     const float2* fsrc = V.hi + V.idx(0, qa - lt, qb);
     const float2* eysrc = eyz + qa;
@@ -496,12 +528,20 @@ k_dilute_shift_bulk(FbView V, int n_out, const float2* __restrict__ eyz, const i
         fold_t();
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-                double2* t = Ftot + (int64_t)rot * tstride2 + (int64_t)c * npix + p;
-                double2 v = *t;
-                v.x += (double)th[2 * c] + (double)tl[2 * c];
-                v.y += (double)th[2 * c + 1] + (double)tl[2 * c + 1];
-                *t = v;
+            const double re = (double)th[2 * c] + (double)tl[2 * c];
+            const double im = (double)th[2 * c + 1] + (double)tl[2 * c + 1];
+            double2* t = Ftot + (int64_t)rot * tstride2 + (int64_t)c * npix;
+            double2 v = t[p];
+            v.x += re;
+            v.y += im;
+            t[p] = v;
+            if (mir) {
+                v = t[pm];
+                v.x += re;
+                v.y -= im;
+                t[pm] = v;
             }
+        }
 #pragma unroll
         for (int k = 0; k < 8; ++k) { th[k] = 0.f; tl[k] = 0.f; }
     };
@@ -588,7 +628,11 @@ k_dilute_shift_bulk(FbView V, int n_out, const float2* __restrict__ eyz, const i
     }
     flush(cur);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) Gdil[(int64_t)k * npix + p] += ((double)gh[k] + (double)gl[k]) + (double)rg[k];
+    for (int k = 0; k < 16; ++k) {
+        const double g = ((double)gh[k] + (double)gl[k]) + (double)rg[k];
+        Gdil[(int64_t)k * npix + p] += g;
+        if (mir) Gdil[(int64_t)k * npix + pm] += g_conj_sign(k) * g;
+    }
 }
 
 cudaError_t launch_dilute_shift_batch(const FbView& V, int n_out, const float2* eyz, const int32_t* out_rot,
@@ -596,13 +640,13 @@ cudaError_t launch_dilute_shift_batch(const FbView& V, int n_out, const float2* 
                                       cudaStream_t s)
 {
     if (n_out <= 0) return cudaSuccess;
-    const int64_t npix = (int64_t)V.ny * V.nz;
+    const int64_t nst = V.stored_pixels();
     const bool bulk = V.nch == 4 && V.ny % 128 == 0 && (reinterpret_cast<uintptr_t>(V.hi) & 15) == 0;
     if (bulk)
-        k_dilute_shift_bulk<<<(unsigned)(npix / 128), 128, 0, s>>>(
+        k_dilute_shift_bulk<<<(unsigned)(nst / 128), 128, 0, s>>>(
             V, n_out, eyz, out_rot, Gdil, reinterpret_cast<double2*>(Ftot), tstride / 2, err, limit_ns);
     else
-        k_dilute_shift_batch<<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(
+        k_dilute_shift_batch<<<(unsigned)((nst + 127) / 128), 128, 0, s>>>(
             V, n_out, eyz, out_rot, Gdil, reinterpret_cast<double2*>(Ftot), tstride / 2);
     return cudaGetLastError();
 }

@@ -17,7 +17,9 @@
 // both signs: a grid symmetric in q_y and q_z costs a quarter of the MMA work
 // and 10 instead of 24 table bytes per cell and pixel pair (512^2 grid),
 // with the same per-term arithmetic.  An asymmetric axis is covered in full
-// and only the s = +1 combination is written.
+// and only the s = +1 combination is written.  When both axes are symmetric
+// the -q_z half is not written at all: with real weights F(-q) = conj F(q),
+// and the readers of the amplitudes take it from the q_z >= 0 half.
 //
 // Precision (GB300-specific choice): each operand x (scaled by a power of two
 // to |x| <= 2^12) is split x = hi + lo with hi = fp16(x), lo = fp16(x - hi);
@@ -393,8 +395,10 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity
 }
 
 // ------------------------------------------------------------------ GEMM
-// Persistent: gridDim.x CTAs (one per SM) walk the work list round-robin;
-// TMEM, barriers and the stage ring stay live across items.  An item is one
+// Persistent: gridDim.x CTAs (one per SM) each walk their own run of the
+// work list (unit u, a CTA or a CTA pair, takes the items
+// [unit_item0[u], unit_item0[u + 1]); the host balances the runs); TMEM,
+// barriers and the stage ring stay live across items.  An item is one
 // 128 x 128 output tile per CTA over a k-block range of the chunk's tables.
 // Its two-float result either goes, unscaled, to the partial tile P[slot]
 // (128 x 128: column pairs outermost, rows innermost) for k_gemm_reduce, or
@@ -431,7 +435,7 @@ struct GemmArgs {
     const uint8_t* B_lo;
     int64_t nkb;          // k-blocks in the tables of this launch (block stride)
     const GemmItem* items;
-    int n_items;
+    const int32_t* unit_item0;   // [units + 1]: first item of each unit (CTA, or CTA pair in MODE 2)
     int kcb;              // k-blocks per TMEM chunk (drain interval)
     double* P;            // [slots][64 column pairs][128 rows] float4 (col 2j hi, lo, col 2j+1 hi, lo)
     double* F;            // direct outputs, high plane: [out][nz][nch * ny] float2 (FbView layout)
@@ -485,8 +489,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int lane = threadIdx.x & 31;
     const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const int rank = CLUSTER ? (int)cluster_rank() : 0;
-    const int unit0 = CLUSTER ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;   // first item of this CTA (pair)
-    const int units = CLUSTER ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+    const int unit = CLUSTER ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;   // this CTA's (pair's) run of items
+    const int it_begin = g.unit_item0[unit], it_end = g.unit_item0[unit + 1];
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STG; ++s) {
@@ -518,7 +522,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int s = 0;                  // its stage
             uint32_t par = 1u;          // parity of the stage's previous "empty" phase
             bool ok = true;
-            for (int it = unit0; it < g.n_items && ok; it += units) {
+            for (int it = it_begin; it < it_end && ok; ++it) {
                 const GemmItem item = g.items[it];
                 for (int kb = item.kb0; kb < item.kb1; ++kb) {
                     if (!mbar_wait(&bar_empty[s], par, g.limit_ns, &s_abort)) {
@@ -594,7 +598,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint32_t sph = 0;           // its phase bit (flips each pass over the ring)
             uint32_t c = 0;             // TMEM chunk sequence number
             bool ok = true;
-            for (int it = unit0; it < g.n_items && ok; it += units) {
+            for (int it = it_begin; it < it_end && ok; ++it) {
                 const GemmItem item = g.items[it];
                 for (int k0 = item.kb0; k0 < item.kb1 && ok; k0 += g.kcb, ++c) {
                     const int b = (int)(c & 1);
@@ -656,7 +660,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int colh = (e >> 2) * 32;            // column quarter
         int64_t c = 0;
         bool ok = true;
-        for (int it = unit0; it < g.n_items && ok; it += units) {
+        for (int it = it_begin; it < it_end && ok; ++it) {
             const GemmItem item = g.items[it];
             // two-float running sums, two columns per 64-bit register
             uint64_t hi[16], lo[16];
@@ -757,12 +761,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int ag = qi / g.nch, ch = qi & (g.nch - 1);
                 const int b0 = (item.nt * TC_BN + colh) >> 1;       // GEMM q_z index of column pair 0
                 const int64_t mrows = (int64_t)g.nch * ax.ny;
-                float2* Fo = reinterpret_cast<float2*>(g.F) + (int64_t)(-1 - slot) * ax.nz * mrows + ch;
+                float2* Fo = reinterpret_cast<float2*>(g.F) + (int64_t)(-1 - slot) * (ax.nz - ax.zs0) * mrows + ch;
                 // this lane's q_y node and sign, and which q_z signs it writes
+                // (-q_z only where the q_z < 0 rows are stored)
                 float sy = 1.f;
                 int a_out = ax.hy + ag;
                 bool act = ag < ax.nyg;
-                int zfirst = 0, zlast = ax.mz ? 1 : 0;          // 0: +q_z, 1: -q_z
+                int zfirst = 0, zlast = (ax.mz && ax.zs0 == 0) ? 1 : 0;   // 0: +q_z, 1: -q_z
                 if (ax.my) {
                     if (p) {
                         sy = -1.f;
@@ -792,7 +797,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             if (zs && b_out == ax.hz + bg) continue;     // q_z = 0 is its own mirror
                             const float re = fmaf(-sy * sz, ss, cc);
                             const float im = -fmaf(sz, cs, sy * scs);
-                            Fo[(int64_t)b_out * mrows + (int64_t)g.nch * a_out] = make_float2(sc * re, sc * im);
+                            Fo[(int64_t)(b_out - ax.zs0) * mrows + (int64_t)g.nch * a_out] = make_float2(sc * re, sc * im);
                         }
                     }
                 } else
@@ -814,7 +819,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         if (zs && b_out == ax.hz + bg) continue;     // q_z = 0 is its own mirror
                         // an output of several pieces: two-float, stored by its
                         // first piece and added by the later ones
-                        float2* oh = Fo + (int64_t)b_out * mrows + (int64_t)g.nch * a_out;
+                        float2* oh = Fo + (int64_t)(b_out - ax.zs0) * mrows + (int64_t)g.nch * a_out;
                         float4 v = combine_tf(cc, cs, scs, ss, sy, sz);
                         v = make_float4(sc * v.x, sc * v.y, sc * v.z, sc * v.w);
                         float2* ol = oh + g.lo_off;
@@ -841,8 +846,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // Thread (output r, GEMM q_z index b, pair qi = nch a + c) sums the splits of
 // the tile rows 2 qi (cos q_y Y: cc, cs) and 2 qi + 1 (sin q_y Y: sc, ss) at
 // column pair j = b mod 64 of B tile b / 64, then writes the amplitudes of
-// every sign combination of the symmetric axes:
-//   F[out][b_out][nch a_out + c] (+)= scale_{c mod 4} ((cc - s_y s_z ss) - i (s_z cs + s_y sc)).
+// every sign combination of the symmetric axes whose q_z row is stored
+// (s_z = +1 only when both axes are symmetric, FbView):
+//   F[out][b_out - zs0][nch a_out + c] (+)= scale_{c mod 4} ((cc - s_y s_z ss) - i (s_z cs + s_y sc)).
 // Threads run over qi fastest, so the tile reads and the F writes are
 // contiguous.
 struct RedDesc {
@@ -885,16 +891,17 @@ __global__ void k_gemm_reduce(const double* __restrict__ P, const RedDesc* __res
     const float2 sc = make_float2(a1.x, a1.y), ss = make_float2(a1.z, a1.w);
     const float f = scale.v[c & 3];
     const int64_t mrows = (int64_t)nch * ax.ny;
-    float2* Fo = reinterpret_cast<float2*>(F) + (int64_t)d.out * ax.nz * mrows + c;
+    float2* Fo = reinterpret_cast<float2*>(F) + (int64_t)d.out * (ax.nz - ax.zs0) * mrows + c;
+    const int zlast = (ax.mz && ax.zs0 == 0) ? 1 : 0;   // -q_z only where those rows are stored
     for (int ys = 0; ys <= ax.my; ++ys) {
         const int a_out = ys ? ax.ny - 1 - ax.hy - ag : ax.hy + ag;
         if (ys && a_out == ax.hy + ag) continue;        // q_y = 0 is its own mirror
-        for (int zs = 0; zs <= ax.mz; ++zs) {
+        for (int zs = 0; zs <= zlast; ++zs) {
             const int b_out = zs ? ax.nz - 1 - ax.hz - bg : ax.hz + bg;
             if (zs && b_out == ax.hz + bg) continue;
             float4 v = combine_tf(cc, cs, sc, ss, ys ? -1.f : 1.f, zs ? -1.f : 1.f);
             v = make_float4(f * v.x, f * v.y, f * v.z, f * v.w);
-            float2* oh = Fo + (int64_t)b_out * mrows + (int64_t)nch * a_out;
+            float2* oh = Fo + (int64_t)(b_out - ax.zs0) * mrows + (int64_t)nch * a_out;
             if (d.store & 2) {
                 float2* ol = oh + lo_off;
                 if (!(d.store & 1)) {
@@ -978,9 +985,10 @@ static cudaError_t encode_row_maps(const void* tab, int64_t rows, CUtensorMap* t
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
-                           int grid, int kcb, double* P, double* F, int64_t lo_off, const AxisMap& ax, int nch,
-                           const double scale[4], int32_t* err, uint64_t limit_ns, int mode, cudaStream_t s)
+cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items,
+                           const int32_t* unit_item0, int grid, int kcb, double* P, double* F, int64_t lo_off,
+                           const AxisMap& ax, int nch, const double scale[4], int32_t* err, uint64_t limit_ns, int mode,
+                           cudaStream_t s)
 {
     static_assert(GemmCfg<0>::STAGES * GemmCfg<0>::STAGE_BYTES == GemmCfg<2>::STAGES * GemmCfg<2>::STAGE_BYTES,
                   "one dynamic shared-memory size for every mode");
@@ -1010,7 +1018,7 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
     ga.B_lo = ga.B_hi + (size_t)ntiles * nkb * TC_BLOCK_BYTES;
     ga.nkb = nkb;
     ga.items = (const GemmItem*)items;
-    ga.n_items = n_items;
+    ga.unit_item0 = unit_item0;
     ga.kcb = kcb;
     ga.P = P;
     ga.F = F;

@@ -49,14 +49,21 @@ struct RotMat {
 // Amplitudes of a batch of tensor-path outputs (F_b), complex FP32 values
 // (float2) in two planes: high words, and low words of a two-float value.
 // Value (output o, channel row m = nch a + c, q_z index b) sits at
-// o * ostride2 + b * mrows + m in each plane, with mrows = nch * ny and
-// ostride2 = nz * mrows: the GEMM row index runs fastest, so the 32 rows an
-// epilogue warp holds go out as 256 contiguous bytes, and a pixel's
-// channels are adjacent.  An output assembled from one piece keeps its
-// value, rounded to FP32, in the high plane only; an output whose pieces
+// o * ostride2 + (b - zs0) * mrows + m in each plane, with mrows = nch * ny
+// and ostride2 = (nz - zs0) * mrows: the GEMM row index runs fastest, so the
+// 32 rows an epilogue warp holds go out as 256 contiguous bytes, and a
+// pixel's channels are adjacent.  An output assembled from one piece keeps
+// its value, rounded to FP32, in the high plane only; an output whose pieces
 // (table chunks) add up keeps the two-float value, normalised, in both
 // planes (two[o] = 1).  Either way the high plane holds the value rounded to
 // FP32, which is what the Hermitian products and bins read.
+//
+// zs0 > 0: the detector is point-symmetric (both axes symmetric about
+// q = 0), and only the q_z rows b >= zs0 (q_z >= 0) are stored.  The weights
+// are real, so F(-q) = conj F(q): the value at (a, b < zs0) is the conjugate
+// of the stored value at the mirror pixel (ny - 1 - a, nz - 1 - b).  The
+// products F F^dagger at -q are the conjugates of those at q, and so is a
+// sum of shifted amplitudes (its phase factors conjugate as well).
 struct FbView {
     const float2* hi;       // channel 0 of the chosen weight set, output 0
     const float2* lo;
@@ -64,13 +71,34 @@ struct FbView {
     int64_t ostride2;       // float2 between outputs
     int mrows;              // float2 between consecutive q_z (nch * ny)
     int nch, ny, nz;
+    int zs0;                // first stored q_z row (0: all rows stored)
     __host__ __device__ int64_t idx(int64_t o, int a, int b) const
     {
-        return o * ostride2 + (int64_t)b * mrows + (int64_t)nch * a;
+        return o * ostride2 + (int64_t)(b - zs0) * mrows + (int64_t)nch * a;
     }
+    // pixels held in the planes: ny * (nz - zs0)
+    __host__ __device__ int64_t stored_pixels() const { return (int64_t)ny * (nz - zs0); }
+    // a stored pixel at q_z row b >= zs0 whose point mirror is not stored
+    // (every stored row but the q_z = 0 row of an odd node count)
+    __host__ __device__ bool mirror_unstored(int b) const { return zs0 > 0 && nz - 1 - b < zs0; }
 #ifdef __CUDACC__
     // channel c of output o at (a, b), rounded to FP32
-    __device__ __forceinline__ float2 load(int64_t o, int a, int b, int c) const { return hi[idx(o, a, b) + c]; }
+    __device__ __forceinline__ float2 load(int64_t o, int a, int b, int c) const
+    {
+        if (b >= zs0) return hi[idx(o, a, b) + c];
+        const float2 v = hi[idx(o, ny - 1 - a, nz - 1 - b) + c];
+        return make_float2(v.x, -v.y);
+    }
+    // the same in FP64 with the low word, where the output has one
+    __device__ __forceinline__ double2 load_f64(int64_t o, int a, int b, int c) const
+    {
+        const bool m = b < zs0;
+        const int64_t j = m ? idx(o, ny - 1 - a, nz - 1 - b) + c : idx(o, a, b) + c;
+        const float2 h = hi[j];
+        const float2 l = two[o] ? lo[j] : make_float2(0.f, 0.f);
+        const double re = (double)h.x + (double)l.x, im = (double)h.y + (double)l.y;
+        return make_double2(re, m ? -im : im);
+    }
 #endif
 };
 
@@ -78,9 +106,11 @@ struct FbView {
 // node of the GEMM's part of each axis (hy, hz: 0, or the first q >= 0 node of
 // an axis symmetric about q = 0) and its length (nyg = ny - hy, nzg = nz - hz);
 // my, mz = 1: the axis is symmetric and the epilogue also writes the mirrored
-// nodes n - 1 - h - i (except a node that is its own mirror, q = 0).
+// nodes n - 1 - h - i (except a node that is its own mirror, q = 0).  zs0:
+// first q_z row of the stored amplitudes (FbView); zs0 = hz > 0 when both
+// axes are symmetric, and then the -q_z writes are left out.
 struct AxisMap {
-    int ny, nz, hy, hz, nyg, nzg, my, mz;
+    int ny, nz, hy, hz, nyg, nzg, my, mz, zs0;
 };
 
 // ---------------------------------------------------------------- plan

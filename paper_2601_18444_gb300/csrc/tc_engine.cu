@@ -20,10 +20,13 @@
 
 #include <algorithm>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <numeric>
+#include <queue>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "nms_internal.h"
@@ -34,9 +37,10 @@ namespace nms {
 cudaError_t tc_launch_tables(const float4* cpos, const float4* cw, int64_t wstride, int nch, const int64_t* kb_cell0,
                              const int32_t* kb_ncell, int64_t nkb, const float2* qy, int nyg, const float2* qz, int nzg,
                              int mtiles, int ntiles, const float wscale[4], void* tab, cudaStream_t s);
-cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items, int n_items,
-                           int grid, int kcb, double* P, double* F, int64_t lo_off, const AxisMap& ax, int nch,
-                           const double scale[4], int32_t* err, uint64_t limit_ns, int mode, cudaStream_t s);
+cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles, const void* items,
+                           const int32_t* unit_item0, int grid, int kcb, double* P, double* F, int64_t lo_off,
+                           const AxisMap& ax, int nch, const double scale[4], int32_t* err, uint64_t limit_ns, int mode,
+                           cudaStream_t s);
 cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, const AxisMap& ax, int ntiles, int nch,
                              const double scale[4], double* F, int64_t lo_off, cudaStream_t s);
 size_t tc_item_bytes();
@@ -72,6 +76,7 @@ struct HostRed {
 struct Chunk {
     int64_t kb_off = 0, nkb = 0;    // into the k-block arrays
     int64_t item_off = 0;
+    int64_t unit_off = 0;           // into the unit runs: units + 1 first-item indices (chunk-relative)
     int n_items = 0, grid = 0;
     int64_t red_off = 0;
     int n_red = 0;
@@ -90,6 +95,7 @@ struct Schedule {
     int64_t* d_kb_cell0 = nullptr;
     int32_t* d_kb_ncell = nullptr;
     void* d_items = nullptr;
+    int32_t* d_units = nullptr;
     void* d_reds = nullptr;
     int32_t* d_out_obj = nullptr;
     int32_t* d_out_rot = nullptr;
@@ -118,7 +124,7 @@ struct TcState {
     int64_t tab_kb = 0;          // table capacity in k-blocks
     float4* d_cpos_b = nullptr;  // [R_b][n]
     float4* d_cw_b = nullptr;
-    double* d_Fb = nullptr;      // out_cap outputs, FbView layout: two planes [out][q_z][nch * n_y] of float2
+    double* d_Fb = nullptr;      // out_cap outputs, FbView layout: two planes [out][stored q_z][nch * n_y] of float2
     int out_cap = 1;             // outputs per batch
     double* d_Ftot_b = nullptr;  // [R_b][4][npix][2] (objects)
     float4* d_cyz = nullptr;     // [out_cap]
@@ -129,8 +135,8 @@ struct TcState {
     Schedule full, last;
 };
 
-// float2 values in one plane of a batch of GEMM outputs
-static int64_t fb_plane(const TcState& t, int n_out) { return (int64_t)n_out * t.nz * t.nch * t.ny; }
+// float2 values in one plane of a batch of GEMM outputs (stored q_z rows)
+static int64_t fb_plane(const TcState& t, int n_out) { return (int64_t)n_out * (t.nz - t.ax.zs0) * t.nch * t.ny; }
 
 // view of a batch of GEMM outputs: high plane at F, low plane lo_off float2
 // further, per-output piece flags two; weight set st
@@ -141,10 +147,11 @@ static FbView fb_view(const TcState& t, const double* F, int64_t lo_off, const u
     v.lo = v.hi + lo_off;
     v.two = two;
     v.mrows = t.nch * t.ny;
-    v.ostride2 = (int64_t)t.nz * v.mrows;
+    v.ostride2 = (int64_t)(t.nz - t.ax.zs0) * v.mrows;
     v.nch = t.nch;
     v.ny = t.ny;
     v.nz = t.nz;
+    v.zs0 = t.ax.zs0;
     return v;
 }
 
@@ -170,7 +177,7 @@ static nms_status upload(T** d, const std::vector<T>& h)
 
 static void free_schedule(Schedule& s, cudaStream_t used_on)
 {
-    void* b[] = {s.d_kb_cell0, s.d_kb_ncell, s.d_items, s.d_reds, s.d_out_obj, s.d_out_rot, s.d_out_two};
+    void* b[] = {s.d_kb_cell0, s.d_kb_ncell, s.d_items, s.d_units, s.d_reds, s.d_out_obj, s.d_out_rot, s.d_out_two};
     for (void* x : b)
         if (x) plan_free(x, used_on);
     s = Schedule();
@@ -208,6 +215,7 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
     std::vector<int64_t> kb_cell0;
     std::vector<int32_t> kb_ncell;
     std::vector<HostItem> items;
+    std::vector<int32_t> unit_item0;
     std::vector<HostRed> reds;
     std::vector<int32_t> out_obj(sums.size()), out_rot(sums.size());
     std::vector<uint8_t> out_two(sums.size(), 0);
@@ -325,13 +333,38 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
                 kb += nkb_p;
             }
             ch.n_red = (int)(reds.size() - ch.red_off);
-            // longest items first, dealt round-robin to the persistent CTAs
+            // longest items first, each to the unit (CTA or CTA pair) with the
+            // least work so far (longest-processing-time rule; an item costs
+            // its k-blocks plus one for its output).  Items of equal length
+            // (the tiles of one k-range) stay adjacent in the list, so they
+            // run at about the same time on different units and share the
+            // k-range's table blocks through L2.
             std::stable_sort(its.begin(), its.end(),
                              [](const HostItem& x, const HostItem& y) { return (x.kb1 - x.kb0) > (y.kb1 - y.kb0); });
             ch.item_off = (int64_t)items.size();
             ch.n_items = (int)its.size();
             ch.grid = t.mode ? std::min(2 * ch.n_items, sms & ~1) : std::min(ch.n_items, sms);
-            items.insert(items.end(), its.begin(), its.end());
+            const int units = t.mode ? ch.grid / 2 : ch.grid;
+            std::vector<std::vector<int>> run(units);
+            {
+                using Load = std::pair<int64_t, int>;   // (work so far, unit): the lowest unit wins a tie
+                std::priority_queue<Load, std::vector<Load>, std::greater<Load>> least;
+                for (int u = 0; u < units; ++u) least.push({0, u});
+                for (int i = 0; i < ch.n_items; ++i) {
+                    const Load l = least.top();
+                    least.pop();
+                    run[l.second].push_back(i);
+                    least.push({l.first + (its[i].kb1 - its[i].kb0) + 1, l.second});
+                }
+            }
+            ch.unit_off = (int64_t)unit_item0.size();
+            int32_t first = 0;
+            for (int u = 0; u < units; ++u) {
+                unit_item0.push_back(first);
+                for (int i : run[u]) items.push_back(its[i]);
+                first += (int32_t)run[u].size();
+            }
+            unit_item0.push_back(first);
             S.max_items = std::max<int64_t>(S.max_items, slot);
             ob.chunks.push_back(ch);
         }
@@ -339,6 +372,7 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
     }
     nms_status st;
     if ((st = upload(&S.d_kb_cell0, kb_cell0)) || (st = upload(&S.d_kb_ncell, kb_ncell)) ||
+        (st = upload(&S.d_units, unit_item0)) ||
         (st = upload(&S.d_out_obj, out_obj)) || (st = upload(&S.d_out_rot, out_rot)) ||
         (st = upload(&S.d_out_two, out_two)))
         return st;
@@ -364,9 +398,7 @@ __global__ void k_amp_maxerr(FbView A, const double2* __restrict__ B, unsigned i
     const int qa = (int)(p / A.nz), qb = (int)(p % A.nz);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        const float2 h = A.hi[A.idx(0, qa, qb) + c];
-        const float2 l = A.two[0] ? A.lo[A.idx(0, qa, qb) + c] : make_float2(0.f, 0.f);
-        const double2 a = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+        const double2 a = A.load_f64(0, qa, qb, c);
         const double2 b = B[(int64_t)c * npix + p];
         const float d = (float)hypot(a.x - b.x, a.y - b.y);
         atomicMax(&err[c], __float_as_uint(d));   // non-negative floats order as integers
@@ -529,8 +561,8 @@ nms_status tc_autotune(Plan& p, TcState& t)
                                   p.d_tab, s);
             if (ce == cudaSuccess) ce = cudaEventRecord(e0, s);
             if (ce == cudaSuccess)
-                ce = tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles, S.d_items, ch.n_items, ch.grid, kcb, P,
-                                    d_Fp, lo_off, t.ax, t.nch, scale, p.d_err, limit, t.mode, s);
+                ce = tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles, S.d_items, S.d_units + ch.unit_off, ch.grid,
+                                    kcb, P, d_Fp, lo_off, t.ax, t.nch, scale, p.d_err, limit, t.mode, s);
             if (ce == cudaSuccess) ce = cudaEventRecord(e1, s);
             if (ce == cudaSuccess)
                 ce = tc_launch_reduce(P, S.d_reds, ch.n_red, t.ax, t.ntiles, t.nch, scale, d_Fp, lo_off, s);
@@ -632,6 +664,8 @@ nms_status tc_setup(Plan& p)
     t->ax.hz = t->ax.mz ? t->nz / 2 : 0;
     t->ax.nyg = t->ny - t->ax.hy;
     t->ax.nzg = t->nz - t->ax.hz;
+    // point-symmetric detector: amplitudes stored for q_z >= 0 only
+    t->ax.zs0 = (t->ax.my && t->ax.mz) ? t->ax.hz : 0;
     // A rows: (q_y node, channel) x (cos, sin); B rows: q_z node x (cos, sin)
     t->mtiles = (2 * t->nch * t->ax.nyg + 127) / 128;
     t->ntiles = (2 * t->ax.nzg + 127) / 128;
@@ -699,7 +733,7 @@ nms_status tc_setup(Plan& p)
     // padding sets (up to the power of two) keep zero weights
     NMS_CUDA_TRY(cudaMemset(t->d_cw_b, 0, (size_t)(t->nch / 4) * t->wstride * sizeof(float4)));
     // output amplitude batch: up to 1 GB, nch complex channels per output
-    const int64_t out_bytes = (int64_t)t->nch * np * 16;
+    const int64_t out_bytes = (int64_t)t->nch * t->ny * (t->nz - t->ax.zs0) * 16;
     const int64_t outs_per_rb = t->objects ? (int64_t)t->R_b * p.n_objects : t->R_b;
     const int out_cap = (int)std::max<int64_t>(1, std::min<int64_t>(outs_per_rb, (1ll << 30) / out_bytes));
     t->out_cap = out_cap;
@@ -760,7 +794,6 @@ void tc_release(Plan& p)
 nms_status tc_amplitudes(Plan& p, cudaStream_t s)
 {
     TcState& t = *(TcState*)p.tc_state;
-    const int64_t n = p.n_cells;
     const int64_t np = p.npix;
     const int nS = t.nsets;
     const int64_t F4 = 8 * np;                   // doubles of one set's amplitudes [4][np] complex
@@ -787,9 +820,9 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
                 p.timer.end(ST_TABLES, 1);
                 p.timer.begin(ST_GEMM);
                 NMS_CUDA_TRY(tc_launch_gemm(p.d_tab, ch.nkb, t.mtiles, t.ntiles,
-                                            (const char*)S.d_items + ch.item_off * tc_item_bytes(), ch.n_items, ch.grid,
-                                            t.kcb, t.d_P, t.d_Fb, lo_off, t.ax, t.nch, scale, p.d_err, limit, t.mode,
-                                            s));
+                                            (const char*)S.d_items + ch.item_off * tc_item_bytes(),
+                                            S.d_units + ch.unit_off, ch.grid, t.kcb, t.d_P, t.d_Fb, lo_off, t.ax,
+                                            t.nch, scale, p.d_err, limit, t.mode, s));
                 p.timer.end(ST_GEMM, 1);
                 p.timer.begin(ST_REDUCE);
                 NMS_CUDA_TRY(tc_launch_reduce(t.d_P, (const char*)S.d_reds + ch.red_off * tc_red_bytes(), ch.n_red, t.ax,

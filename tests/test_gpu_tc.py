@@ -311,6 +311,10 @@ def test_tc_autotune_picks_valid_config_and_caches(tmp_path, monkeypatch):
 # element by element, and the dilute / total / interference parts of objects
 # whose outputs are written straight from the GEMM (one piece), assembled
 # from several pieces (small table workspace) and reduced from split items.
+# On a grid symmetric in both axes only the q_z >= 0 half of the per-object
+# amplitudes is stored and the dilute pass writes the other half by
+# conjugation; the last grid takes the pass that copies whole 128-pixel q_y
+# rows, with an odd q_z count (a q_z = 0 row that is its own mirror).
 SYM_GRIDS = [
     dict(n0=64, n1=48, lo0=-1.2, hi0=1.2, lo1=-0.9, hi1=0.9),     # both symmetric, even
     dict(n0=63, n1=49, lo0=-1.2, hi0=1.2, lo1=-0.9, hi1=0.9),     # both symmetric, odd (q = 0 nodes)
@@ -318,6 +322,7 @@ SYM_GRIDS = [
     dict(n0=52, n1=41, lo0=-0.8, hi0=1.1, lo1=-1.4, hi1=1.4),     # q_z symmetric (odd), q_y not
     dict(n0=200, n1=2, lo0=-2.0, hi0=2.0, lo1=-0.5, hi1=0.5),     # several A tiles; two q_z nodes
     dict(n0=3, n1=300, lo0=-0.3, hi0=0.3, lo1=-2.0, hi1=2.0),     # three q_y nodes; several B tiles
+    dict(n0=128, n1=33, lo0=-1.0, hi0=1.0, lo1=-0.8, hi1=0.8),    # both symmetric; q_y rows of 128 pixels
 ]
 
 
@@ -332,7 +337,7 @@ def test_tc_symmetric_axes_amplitudes(gi):
     assert np.all(err <= AMP_TOL), err
 
 
-@pytest.mark.parametrize("gi", [0, 1, 2, 3])
+@pytest.mark.parametrize("gi", [0, 1, 2, 3, 6])
 @pytest.mark.parametrize("ws", [0, 4 << 20])
 def test_tc_symmetric_axes_objects(gi, ws):
     kw = dict(kind="cartesian", **SYM_GRIDS[gi])

@@ -320,9 +320,83 @@ __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Output slices.  A batch's outputs are split into gridDim.y contiguous
+// slices, one per blockIdx.y, so that a detector with few stored pixels
+// still keeps enough threads in flight.  Slice 0 adds its sums into G_dil
+// and Ftot; slice s >= 1 stores its G_dil sums into a scratch plane, and
+// its shifted sums into G_dil's rotation-by-rotation totals directly for
+// every rotation but its first, whose outputs may continue those of slice
+// s - 1: that one goes to a scratch plane too.  Only one slice writes a
+// rotation directly, so no two blocks update one value, and
+// k_dilute_combine then adds the scratch planes in slice order (the result
+// does not depend on timing).
+struct DiluteOut {
+    double* Gdil;         // [16][npix]
+    double2* Ftot;        // [rotation][4][npix] at tstride2 complex values per rotation
+    int64_t tstride2;
+    double* Gscr;         // [slices - 1][16][npix]
+    double2* Fscr;        // [slices - 1][4][npix]
+};
+
+__device__ __forceinline__ void dil_put_f(const DiluteOut& D, int slice, int rot, int rot_first, int64_t npix,
+                                          int64_t p, int64_t pm, bool mir, int c, double re, double im)
+{
+    if (slice > 0 && rot == rot_first) {
+        double2* t = D.Fscr + ((int64_t)(slice - 1) * 4 + c) * npix;
+        t[p] = make_double2(re, im);
+        if (mir) t[pm] = make_double2(re, -im);
+    } else {
+        double2* t = D.Ftot + (int64_t)rot * D.tstride2 + (int64_t)c * npix;
+        double2 v = t[p];
+        v.x += re;
+        v.y += im;
+        t[p] = v;
+        if (mir) {
+            v = t[pm];
+            v.x += re;
+            v.y -= im;
+            t[pm] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ void dil_put_g(const DiluteOut& D, int slice, int64_t npix, int64_t p, int64_t pm,
+                                          bool mir, int k, double g)
+{
+    if (slice > 0) {
+        double* t = D.Gscr + ((int64_t)(slice - 1) * 16 + k) * npix;
+        t[p] = g;
+        if (mir) t[pm] = g_conj_sign(k) * g;
+    } else {
+        double* t = D.Gdil + (int64_t)k * npix;
+        t[p] += g;
+        if (mir) t[pm] += g_conj_sign(k) * g;
+    }
+}
+
+__global__ void k_dilute_combine(DiluteOut D, int n_out, int slices, const int32_t* __restrict__ out_rot, int64_t npix)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    for (int sl = 1; sl < slices; ++sl) {
+        const int rot = out_rot[(int64_t)n_out * sl / slices];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) D.Gdil[(int64_t)k * npix + p] += D.Gscr[((int64_t)(sl - 1) * 16 + k) * npix + p];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const double2 a = D.Fscr[((int64_t)(sl - 1) * 4 + c) * npix + p];
+            double2* t = D.Ftot + (int64_t)rot * D.tstride2 + (int64_t)c * npix + p;
+            double2 v = *t;
+            v.x += a.x;
+            v.y += a.y;
+            *t = v;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(128, 4)   // 4 blocks per SM: one wave for a 256 x 256 detector
 k_dilute_shift_batch(FbView V, int n_out, const float2* __restrict__ eyz, const int32_t* __restrict__ out_rot,
-                     double* __restrict__ Gdil, double2* __restrict__ Ftot, int64_t tstride2)
+                     DiluteOut D)
 {
     __shared__ float4 ring[DS_DEPTH][3][128];   // per slot: channels 0-1, channels 2-3, (e_y, e_z)
     const int64_t npix = (int64_t)V.ny * V.nz;
@@ -340,9 +414,16 @@ k_dilute_shift_batch(FbView V, int n_out, const float2* __restrict__ eyz, const 
     const bool mir = act && V.mirror_unstored(qb);
     const int64_t pm = (int64_t)(V.ny - 1 - qa) * V.nz + (V.nz - 1 - qb);
     const int ne = V.ny + V.nz;
-    const float2* fsrc = V.hi + V.idx(0, qa, qb);   // 16-byte aligned: channel groups of 4 complex FP32
-    const float2* eysrc = eyz + qa;
-    const float2* ezsrc = eyz + V.ny + qb;
+    // this block's slice of the outputs; o below counts within it
+    const int slice = blockIdx.y;
+    const int o_lo = (int)((int64_t)n_out * slice / gridDim.y);
+    n_out = (int)((int64_t)n_out * (slice + 1) / gridDim.y) - o_lo;
+    out_rot += o_lo;
+    const int rot_first = out_rot[0];
+    // 16-byte aligned: channel groups of 4 complex FP32
+    const float2* fsrc = V.hi + V.idx(0, qa, qb) + (int64_t)o_lo * V.ostride2;
+    const float2* eysrc = eyz + (int64_t)o_lo * ne + qa;
+    const float2* ezsrc = eyz + (int64_t)o_lo * ne + V.ny + qb;
     auto stage = [&](int o) {
         if (o < n_out) {
             const int sl = o % DS_DEPTH;
@@ -371,21 +452,9 @@ k_dilute_shift_batch(FbView V, int n_out, const float2* __restrict__ eyz, const 
         fold_t();
         if (act)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const double re = (double)th[2 * c] + (double)tl[2 * c];
-                const double im = (double)th[2 * c + 1] + (double)tl[2 * c + 1];
-                double2* t = Ftot + (int64_t)rot * tstride2 + (int64_t)c * npix;
-                double2 v = t[p];
-                v.x += re;
-                v.y += im;
-                t[p] = v;
-                if (mir) {
-                    v = t[pm];
-                    v.x += re;
-                    v.y -= im;
-                    t[pm] = v;
-                }
-            }
+            for (int c = 0; c < 4; ++c)
+                dil_put_f(D, slice, rot, rot_first, npix, p, pm, mir, c, (double)th[2 * c] + (double)tl[2 * c],
+                          (double)th[2 * c + 1] + (double)tl[2 * c + 1]);
 #pragma unroll
         for (int k = 0; k < 8; ++k) { th[k] = 0.f; tl[k] = 0.f; }
     };
@@ -440,11 +509,8 @@ k_dilute_shift_batch(FbView V, int n_out, const float2* __restrict__ eyz, const 
     flush(cur);
     if (act)
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const double g = ((double)gh[k] + (double)gl[k]) + (double)rg[k];
-            Gdil[(int64_t)k * npix + p] += g;
-            if (mir) Gdil[(int64_t)k * npix + pm] += g_conj_sign(k) * g;
-        }
+        for (int k = 0; k < 16; ++k)
+            dil_put_g(D, slice, npix, p, pm, mir, k, ((double)gh[k] + (double)gl[k]) + (double)rg[k]);
 }
 
 // The same pass for detectors whose q_y rows are whole multiples of 128
@@ -472,8 +538,7 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
 
 __global__ void __launch_bounds__(128, 4)
 k_dilute_shift_bulk(FbView V, int n_out, const float2* __restrict__ eyz, const int32_t* __restrict__ out_rot,
-                    double* __restrict__ Gdil, double2* __restrict__ Ftot, int64_t tstride2, int32_t* err,
-                    uint64_t limit_ns)
+                    DiluteOut D, int32_t* err, uint64_t limit_ns)
 {
     __shared__ __align__(128) unsigned char ring[DB_DEPTH][DB_SLOT];
     __shared__ __align__(8) uint64_t full[DB_DEPTH], empty[DB_DEPTH];
@@ -487,9 +552,15 @@ k_dilute_shift_bulk(FbView V, int n_out, const float2* __restrict__ eyz, const i
     const bool mir = V.mirror_unstored(qb);
     const int64_t pm = (int64_t)(V.ny - 1 - qa) * V.nz + (V.nz - 1 - qb);
     const int ne = V.ny + V.nz;
-    const float2* fsrc = V.hi + V.idx(0, qa - lt, qb);
-    const float2* eysrc = eyz + qa;
-    const float2* ezsrc = eyz + V.ny + qb;
+    // this block's slice of the outputs; o below counts within it
+    const int slice = blockIdx.y;
+    const int o_lo = (int)((int64_t)n_out * slice / gridDim.y);
+    n_out = (int)((int64_t)n_out * (slice + 1) / gridDim.y) - o_lo;
+    out_rot += o_lo;
+    const int rot_first = out_rot[0];
+    const float2* fsrc = V.hi + V.idx(0, qa - lt, qb) + (int64_t)o_lo * V.ostride2;
+    const float2* eysrc = eyz + (int64_t)o_lo * ne + qa;
+    const float2* ezsrc = eyz + (int64_t)o_lo * ne + V.ny + qb;
     if (lt == 0) {
         abort_flag = 0;
         for (int s = 0; s < DB_DEPTH; ++s) {
@@ -527,21 +598,9 @@ k_dilute_shift_bulk(FbView V, int n_out, const float2* __restrict__ eyz, const i
     auto flush = [&](int rot) {
         fold_t();
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const double re = (double)th[2 * c] + (double)tl[2 * c];
-            const double im = (double)th[2 * c + 1] + (double)tl[2 * c + 1];
-            double2* t = Ftot + (int64_t)rot * tstride2 + (int64_t)c * npix;
-            double2 v = t[p];
-            v.x += re;
-            v.y += im;
-            t[p] = v;
-            if (mir) {
-                v = t[pm];
-                v.x += re;
-                v.y -= im;
-                t[pm] = v;
-            }
-        }
+        for (int c = 0; c < 4; ++c)
+            dil_put_f(D, slice, rot, rot_first, npix, p, pm, mir, c, (double)th[2 * c] + (double)tl[2 * c],
+                      (double)th[2 * c + 1] + (double)tl[2 * c + 1]);
 #pragma unroll
         for (int k = 0; k < 8; ++k) { th[k] = 0.f; tl[k] = 0.f; }
     };
@@ -628,26 +687,46 @@ k_dilute_shift_bulk(FbView V, int n_out, const float2* __restrict__ eyz, const i
     }
     flush(cur);
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        const double g = ((double)gh[k] + (double)gl[k]) + (double)rg[k];
-        Gdil[(int64_t)k * npix + p] += g;
-        if (mir) Gdil[(int64_t)k * npix + pm] += g_conj_sign(k) * g;
-    }
+    for (int k = 0; k < 16; ++k) dil_put_g(D, slice, npix, p, pm, mir, k, ((double)gh[k] + (double)gl[k]) + (double)rg[k]);
 }
 
+// Output slices of one dilute pass: as many as keep every block resident
+// at once (four per SM; a second, partial wave would double the pass), at
+// most 8 (the scratch planes are sized by this count).
+int dilute_slices(int64_t stored_pixels)
+{
+    const int64_t bx = std::max<int64_t>(1, (stored_pixels + 127) / 128);
+    const int64_t fit = 4 * (int64_t)device_sm_count() / bx;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(8, fit));
+}
+
+// scratch: (dilute_slices(V.stored_pixels()) - 1) x 24 x npix doubles, or
+// null when that count is 1
 cudaError_t launch_dilute_shift_batch(const FbView& V, int n_out, const float2* eyz, const int32_t* out_rot,
-                                      double* Gdil, double* Ftot, int64_t tstride, int32_t* err, uint64_t limit_ns,
-                                      cudaStream_t s)
+                                      double* Gdil, double* Ftot, int64_t tstride, double* scratch, int32_t* err,
+                                      uint64_t limit_ns, cudaStream_t s)
 {
     if (n_out <= 0) return cudaSuccess;
+    const int64_t npix = (int64_t)V.ny * V.nz;
     const int64_t nst = V.stored_pixels();
+    const int max_slices = scratch ? dilute_slices(nst) : 1;
+    const int slices = std::min(max_slices, n_out);
+    DiluteOut D;
+    D.Gdil = Gdil;
+    D.Ftot = reinterpret_cast<double2*>(Ftot);
+    D.tstride2 = tstride / 2;
+    D.Gscr = scratch;
+    D.Fscr = scratch ? reinterpret_cast<double2*>(scratch + (int64_t)(max_slices - 1) * 16 * npix) : nullptr;
     const bool bulk = V.nch == 4 && V.ny % 128 == 0 && (reinterpret_cast<uintptr_t>(V.hi) & 15) == 0;
     if (bulk)
-        k_dilute_shift_bulk<<<(unsigned)(nst / 128), 128, 0, s>>>(
-            V, n_out, eyz, out_rot, Gdil, reinterpret_cast<double2*>(Ftot), tstride / 2, err, limit_ns);
+        k_dilute_shift_bulk<<<dim3((unsigned)(nst / 128), (unsigned)slices), 128, 0, s>>>(V, n_out, eyz, out_rot, D,
+                                                                                          err, limit_ns);
     else
-        k_dilute_shift_batch<<<(unsigned)((nst + 127) / 128), 128, 0, s>>>(
-            V, n_out, eyz, out_rot, Gdil, reinterpret_cast<double2*>(Ftot), tstride / 2);
+        k_dilute_shift_batch<<<dim3((unsigned)((nst + 127) / 128), (unsigned)slices), 128, 0, s>>>(V, n_out, eyz,
+                                                                                                  out_rot, D);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || slices == 1) return e;
+    k_dilute_combine<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(D, n_out, slices, out_rot, npix);
     return cudaGetLastError();
 }
 

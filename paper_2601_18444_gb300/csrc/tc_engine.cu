@@ -58,8 +58,9 @@ cudaError_t launch_gacc_batch(const FbView& V, int n_out, double* G, cudaStream_
 cudaError_t launch_gacc_totals(const double* T, int n_out, int64_t ostride, int64_t npix, double* G, cudaStream_t s);
 cudaError_t launch_tf_to_f64(const FbView& V, int64_t o, double* dst, cudaStream_t s);
 cudaError_t launch_dilute_shift_batch(const FbView& V, int n_out, const float2* eyz, const int32_t* out_rot,
-                                      double* Gdil, double* Ftot, int64_t tstride, int32_t* err, uint64_t limit_ns,
-                                      cudaStream_t s);
+                                      double* Gdil, double* Ftot, int64_t tstride, double* scratch, int32_t* err,
+                                      uint64_t limit_ns, cudaStream_t s);
+int dilute_slices(int64_t stored_pixels);
 cudaError_t launch_shift_factors(int n_out, const float4* cyz, const float2* qy, int ny, const float2* qz, int nz,
                                  float2* eyz, cudaStream_t s);
 
@@ -129,6 +130,7 @@ struct TcState {
     double* d_Ftot_b = nullptr;  // [R_b][4][npix][2] (objects)
     float4* d_cyz = nullptr;     // [out_cap]
     float2* d_eyz = nullptr;     // objects: [out_cap][ny + nz] shift factors along q_y and q_z
+    double* d_dscr = nullptr;    // objects: dilute-pass scratch planes of output slices 1.. (or null)
     double* d_rot = nullptr;     // [n_rot][9]
     double* d_cen = nullptr;     // [K][3]
     double* d_P = nullptr;       // item tiles
@@ -740,6 +742,9 @@ nms_status tc_setup(Plan& p)
     NMS_CUDA_TRY(plan_malloc(&t->d_Fb, (size_t)out_cap * out_bytes));
     NMS_CUDA_TRY(plan_malloc(&t->d_cyz, (size_t)out_cap * sizeof(float4)));
     if (t->objects) NMS_CUDA_TRY(plan_malloc(&t->d_eyz, (size_t)out_cap * (t->ny + t->nz) * sizeof(float2)));
+    // dilute pass: G_dil (16) and shifted-sum (4 complex) planes per extra output slice
+    const int dsl = dilute_slices((int64_t)t->ny * (t->nz - t->ax.zs0));
+    if (t->objects && dsl > 1) NMS_CUDA_TRY(plan_malloc(&t->d_dscr, (size_t)(dsl - 1) * 24 * np * sizeof(double)));
     // total amplitude per prepared rotation and weight set
     if (t->objects) NMS_CUDA_TRY(plan_malloc(&t->d_Ftot_b, (size_t)t->R_b * t->nsets * 8 * np * sizeof(double)));
     // phase tables: as many k-blocks as the workspace allows
@@ -782,7 +787,7 @@ void tc_release(Plan& p)
     TcState* t = (TcState*)p.tc_state;
     if (!t) return;
     void* b[] = {t->d_qy,  t->d_qz,  t->d_cpos_b, t->d_cw_b, t->d_Fb, t->d_Ftot_b,
-                 t->d_cyz, t->d_eyz, t->d_rot,    t->d_cen,  t->d_P};
+                 t->d_cyz, t->d_eyz, t->d_dscr,   t->d_rot,  t->d_cen, t->d_P};
     for (void* x : b)
         if (x) plan_free(x, p.stream);
     free_schedule(t->full, p.stream);
@@ -848,9 +853,9 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
                 if (t.objects) {
                     NMS_CUDA_TRY(launch_dilute_shift_batch(V, ob.n_out, t.d_eyz, S.d_out_rot + ob.out0,
                                                            p.d_Gdil + (size_t)st * 16 * np,
-                                                           t.d_Ftot_b + (size_t)st * F4, (int64_t)nS * F4, p.d_err,
-                                                           limit, s));
-                    ++nl;
+                                                           t.d_Ftot_b + (size_t)st * F4, (int64_t)nS * F4, t.d_dscr,
+                                                           p.d_err, limit, s));
+                    nl += std::min(dilute_slices(V.stored_pixels()), ob.n_out) > 1 && t.d_dscr ? 2 : 1;
                 } else {
                     NMS_CUDA_TRY(launch_gacc_batch(V, ob.n_out, p.d_Gtot + (size_t)st * 16 * np, s));
                     ++nl;

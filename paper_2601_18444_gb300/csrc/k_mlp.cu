@@ -197,9 +197,11 @@ static cudaError_t mlp_gemm(bool ta, bool tb, int M, int N, int K, const __nv_bf
 // ------------------------------------------------------------------ element-wise
 __device__ __forceinline__ float silu(float z) { return z / (1.0f + expf(-z)); }
 
-// SiLU with the fast exponential and reciprocal (the result is rounded to
-// BF16, 8 significant bits)
-__device__ __forceinline__ float silu_fast(float z) { return z * __frcp_rn(1.0f + __expf(-z)); }
+// SiLU with the fast exponential and the approximate division (two
+// special-function operations; relative error a few FP32 ulp, and the
+// result is rounded to BF16, 8 significant bits).  For z below about -88
+// the denominator is infinite and the result is -0.
+__device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 
 // bf16x2 word of (a, b), a in the low half
 __device__ __forceinline__ uint32_t bf16x2(float a, float b)
@@ -209,25 +211,70 @@ __device__ __forceinline__ uint32_t bf16x2(float a, float b)
 }
 
 // ------------------------------------------------------------------ fused inference
-// Inference for H = 256, n_out <= 64, n_in <= 8 on the 5th-generation tensor
-// cores, one kernel for the whole network.  A persistent CTA keeps W2 and W3
-// (BF16) in shared memory in the 128-byte swizzled K-major layout, and walks
-// tiles of 128 queries:
-//   layer 1 (threads, FP32):  H1 = bf16(silu(b1 + W1 xn))          -> smem
-//   layer 2 (tcgen05.mma):    D2 = H1 W2^T   (128 x 256, FP32 TMEM)
-//   drain:                     H2 = bf16(silu(D2 + b2))            -> smem
-//   layer 3 (tcgen05.mma):    D3 = H2 W3^T   (128 x 64, FP32 TMEM)
-//   drain:                     Y  = (D3 + b3) ystd + ymean         -> global
-// The arithmetic is that of the layer-by-layer path (BF16 operands, FP32
-// accumulation and activations); only the order of the FP32 sums differs.
+// Inference for H = 256, n_out <= 128 per launch, n_in <= 8 on the
+// 5th-generation tensor cores, one kernel for the whole network.  A
+// persistent CTA keeps W2 and W3 (BF16) in shared memory in the 128-byte
+// swizzled K-major layout (192 KB) and the activations in tensor memory,
+// where the MMA reads them as its A operand (row m in lane m, two BF16 per
+// 32-bit column).  Per tile of 128 queries:
+//   layer 1 (threads, FP32):  H1 = bf16(silu(b1 + W1 xn))      -> TMEM Hb
+//   layer 2 (tcgen05.mma):    D  = H1 W2^T   (128 x 256, FP32)  TMEM D
+//   drain:                     H2 = bf16(silu(D + b2))          -> TMEM Hb
+//   layer 3 (tcgen05.mma):    D  = H2 W3^T   (128 x n_out, FP32, D reused)
+//   drain:                     Y  = (D + b3) ystd + ymean       -> global
+// TMEM: D in columns 0-255, two activation buffers Hb[0], Hb[1] in 256-383
+// and 384-511.  While the layer-2 MMAs of tile i run, the threads compute
+// layer 1 of tile i + 1 into the other buffer.  Warp w handles the rows
+// 32 (w mod 4) .. + 31 (its TMEM lane quadrant) and the hidden units
+// 32 (w / 4) .. + 31.  The arithmetic is that of the layer-by-layer path
+// (BF16 operands, FP32 accumulation and activations); only the order of the
+// FP32 sums differs.
 constexpr int FI_THREADS = 1024;   // 32 warps: the element-wise work needs many warps in flight
 constexpr int FI_H = 256;
-constexpr int FI_NO = 64;      // W3 rows padded with zeros
+constexpr int FI_NO = 128;     // outputs per launch; W3 rows padded with zeros
 constexpr int FI_TM = 128;     // queries per tile (the MMA's M)
 constexpr int FI_W2_BYTES = 4 * FI_H * 128;   // 4 K-blocks of 256 rows x 128 B
 constexpr int FI_W3_BYTES = 4 * FI_NO * 128;
-constexpr int FI_HB_BYTES = 4 * FI_TM * 128;  // H1 / H2 (A operand)
-constexpr int FI_SMEM = FI_W2_BYTES + FI_W3_BYTES + FI_HB_BYTES + 1024;
+constexpr int FI_SMEM = FI_W2_BYTES + FI_W3_BYTES + 1024;
+constexpr uint32_t FI_HB = 256;               // TMEM column of activation buffer 0 (buffer 1: + 128)
+constexpr int FI_STG = FI_NO + 1;             // row stride of the output staging buffer (odd: no bank conflicts)
+
+// Small per-launch tables in shared memory (read as warp-wide broadcasts):
+// layer-1 weights padded to 8 inputs (with n_in < 8 the bias takes input
+// slot 7, whose normalised input is 1), biases, the input normalisation
+// xn = x * in_a + in_c, and the output map y = d * out_a + out_c.
+struct FiSmall {
+    float4 w1[FI_H][2];
+    float b1[FI_H], b2[FI_H];
+    float in_a[8], in_c[8];
+    float out_a[FI_NO], out_c[FI_NO];
+};
+
+// layer 1 of one row for hidden units h0 .. h0 + 31, as 16 BF16 pairs
+// (full8: n_in = 8, the bias is read separately)
+__device__ __forceinline__ void fi_layer1(const float* xn, const FiSmall& sm, int h0, bool full8, uint32_t* w)
+{
+#pragma unroll 4
+    for (int e = 0; e < 16; ++e) {
+        float z[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int h = h0 + 2 * e + t;
+            const float4 u = sm.w1[h][0], v = sm.w1[h][1];
+            float a0 = full8 ? sm.b1[h] : 0.f, a1 = 0.f;   // two chains of four
+            a0 = fmaf(u.x, xn[0], a0);
+            a1 = fmaf(v.x, xn[4], a1);
+            a0 = fmaf(u.y, xn[1], a0);
+            a1 = fmaf(v.y, xn[5], a1);
+            a0 = fmaf(u.z, xn[2], a0);
+            a1 = fmaf(v.z, xn[6], a1);
+            a0 = fmaf(u.w, xn[3], a0);
+            a1 = fmaf(v.w, xn[7], a1);
+            z[t] = silu_fast(a0 + a1);
+        }
+        w[e] = bf16x2(z[0], z[1]);
+    }
+}
 
 __global__ void __launch_bounds__(FI_THREADS, 1)
 k_mlp_infer(int64_t n, int nin, int nout, int ystride, const float* __restrict__ X, const float* __restrict__ xlo,
@@ -240,13 +287,37 @@ k_mlp_infer(int64_t n, int nin, int nout, int ystride, const float* __restrict__
     __shared__ __align__(8) uint64_t bar_mma;
     __shared__ uint32_t s_taddr;
     __shared__ volatile int s_abort;
+    __shared__ __align__(16) FiSmall sm;
+    __shared__ float stag[32 * FI_STG];   // 32 rows of the output tile
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* gW2 = smem_raw + (base - raw);
     uint8_t* gW3 = gW2 + FI_W2_BYTES;
-    uint8_t* gH = gW3 + FI_W3_BYTES;
-    const uint32_t sW2 = base, sW3 = base + FI_W2_BYTES, sH = sW3 + FI_W3_BYTES;
+    const uint32_t sW2 = base, sW3 = base + FI_W2_BYTES;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    for (int h = tid; h < FI_H; h += FI_THREADS) {
+        float w[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w[i] = i < nin ? W1[h * nin + i] : 0.f;
+        if (nin < 8) w[7] = b1[h];
+        sm.w1[h][0] = make_float4(w[0], w[1], w[2], w[3]);
+        sm.w1[h][1] = make_float4(w[4], w[5], w[6], w[7]);
+        sm.b1[h] = b1[h];
+        sm.b2[h] = b2[h];
+    }
+    if (tid < 8) {
+        // xn = 2 (x - lo) / (hi - lo) - 1 as one FMA; inputs past n_in are
+        // 0, except slot 7 (the bias) when n_in < 8
+        const float a = tid < nin ? 2.0f / (xhi[tid] - xlo[tid]) : 0.f;
+        sm.in_a[tid] = a;
+        sm.in_c[tid] = tid < nin ? -fmaf(a, xlo[tid], 1.0f) : (tid == 7 ? 1.0f : 0.f);
+    }
+    for (int c = tid; c < FI_NO; c += FI_THREADS) {
+        // y = (d + b3) ystd + ymean = d ystd + (b3 ystd + ymean)
+        sm.out_a[c] = c < nout ? ystd[c] : 0.f;
+        sm.out_c[c] = c < nout ? fmaf(b3[c], ystd[c], ymean[c]) : 0.f;
+    }
 
     // W2 [256][256] and W3 [nout][256] (rows = outputs, K = inputs) into the
     // swizzled layout: K-block kb holds k in [64 kb, 64 kb + 64) of every row
@@ -274,145 +345,130 @@ k_mlp_infer(int64_t n, int nin, int nout, int ystride, const float* __restrict__
     __syncthreads();
     tc_fence_after();
     const uint32_t taddr = s_taddr;
-    const uint32_t id2 = idesc_bf16_f32(FI_TM, FI_H), id3 = idesc_bf16_f32(FI_TM, FI_NO);
+    // layer 3 covers the outputs rounded up to the MMA's N granularity of 16
+    const uint32_t id2 = idesc_bf16_f32(FI_TM, FI_H), id3 = idesc_bf16_f32(FI_TM, (nout + 15) & ~15);
     const int quad = warp & 3, cg = warp >> 2;        // TMEM lane quadrant, column group (0..7)
-    const int row = 32 * quad + lane;                 // this thread's query row in the drains
+    const int row = 32 * quad + lane;                 // this thread's query row in the tile
+    const uint32_t lanes = (uint32_t)(32 * quad) << 16;
+    const int64_t ntiles = (n + FI_TM - 1) / FI_TM;
+    // this thread's share of layer 1 for tile `tile` into buffer hb
+    auto layer1 = [&](int64_t tile, uint32_t hb) {
+        const int64_t q = tile * FI_TM + row;
+        float xn[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            xn[i] = (i < nin && q < n) ? fmaf(X[q * nin + i], sm.in_a[i], sm.in_c[i]) : sm.in_c[i];
+        uint32_t w[16];
+        fi_layer1(xn, sm, 32 * cg, nin == 8, w);
+        tmem_st16(taddr + lanes + hb + 16u * (uint32_t)cg, w);
+        tmem_wait_st();
+    };
+    // one thread issues the 16 K steps of a layer: D (+)= Hb x B^T
+    auto mma_layer = [&](uint32_t hb, uint32_t sB, int brows, uint32_t idesc) {
+        tc_fence_after();
+#pragma unroll
+        for (int kb = 0; kb < 4; ++kb)
+#pragma unroll
+            for (int k16 = 0; k16 < 4; ++k16)
+                tc_mma_f16_ts(taddr, taddr + hb + (uint32_t)(8 * (4 * kb + k16)),
+                              sw128_desc(sB + kb * (brows * 128)) + 2 * k16, idesc, (kb | k16) ? 1u : 0u);
+        tc_commit(&bar_mma);
+    };
     uint32_t phase = 0;
     bool aborted = false;
-    const int64_t ntiles = (n + FI_TM - 1) / FI_TM;
-    for (int64_t tile = blockIdx.x; tile < ntiles && !aborted; tile += gridDim.x) {
-        const int64_t q0 = tile * FI_TM;
-        // ---- layer 1: thread (row r = tid mod 128) computes the row's
-        // normalised inputs once and 32 of its hidden units, 8 at a time
-        // (the 32 lanes of a warp share each weight: broadcast loads)
-        {
-            const int r = tid & (FI_TM - 1);
-            const int64_t q = q0 + r;
-            float xn[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                xn[i] = 0.f;
-                if (i < nin && q < n) xn[i] = 2.0f * (X[q * nin + i] - xlo[i]) / (xhi[i] - xlo[i]) - 1.0f;
-            }
-            for (int j = tid >> 7; j < FI_H / 8; j += FI_THREADS / FI_TM) {
-                uint32_t w[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    float z[2];
-#pragma unroll
-                    for (int t = 0; t < 2; ++t) {
-                        const int h = 8 * j + 2 * e + t;
-                        float acc = b1[h];
-#pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            if (i < nin) acc = fmaf(W1[h * nin + i], xn[i], acc);
-                        z[t] = silu_fast(acc);
-                    }
-                    w[e] = bf16x2(z[0], z[1]);
-                }
-                const int k = 8 * j;
-                *reinterpret_cast<uint4*>(gH + (k >> 6) * (FI_TM * 128) + swz_offset(r, k & 63)) =
-                    make_uint4(w[0], w[1], w[2], w[3]);
-            }
-        }
-        fence_proxy_async_smem();
+    // every thread waits for the MMAs committed last (bounded); false when
+    // any thread of the block gave up
+    auto wait_mma = [&]() {
+        const bool ok = mbar_wait(&bar_mma, phase, limit_ns, &s_abort);
+        const bool all = !__syncthreads_or(!ok);
+        if (all) phase ^= 1u;
+        return all;
+    };
+    int64_t tile = blockIdx.x;
+    int buf = 0;
+    if (tile < ntiles) {
+        layer1(tile, FI_HB);
         tc_fence_before();
         __syncthreads();
-        // ---- layer 2 on the tensor cores
-        if (tid == 0) {
-            tc_fence_after();
-#pragma unroll
-            for (int kb = 0; kb < 4; ++kb)
-#pragma unroll
-                for (int k16 = 0; k16 < 4; ++k16)
-                    tc_mma_f16(taddr, sw128_desc(sH + kb * (FI_TM * 128)) + 2 * k16,
-                               sw128_desc(sW2 + kb * (FI_H * 128)) + 2 * k16, id2, (kb | k16) ? 1u : 0u);
-            tc_commit(&bar_mma);
+        if (tid == 0) mma_layer(FI_HB, sW2, FI_H, id2);
+    }
+    for (; tile < ntiles; tile += gridDim.x, buf ^= 1) {
+        const uint32_t hb = FI_HB + 128u * (uint32_t)buf, hn = FI_HB + 128u * (uint32_t)(buf ^ 1);
+        const int64_t next = tile + gridDim.x;
+        // layer 1 of the next tile into the other buffer, beside this tile's
+        // layer-2 MMAs (that buffer's last reader, the previous tile's
+        // layer-3 MMAs, has completed)
+        if (next < ntiles) layer1(next, hn);
+        if (!wait_mma()) {
+            aborted = true;
+            break;
         }
-        {
-            const bool ok = mbar_wait(&bar_mma, phase, limit_ns, &s_abort);
-            if (__syncthreads_or(!ok)) {
-                aborted = true;
-                break;
-            }
-        }
-        phase ^= 1u;
         tc_fence_after();
-        // ---- drain D2: bias, SiLU, BF16 into the A buffer (layer 2's MMAs
-        // have completed, so the buffer is free); this warp's 32 columns
+        // ---- drain D: bias, SiLU, BF16 into this tile's buffer (its
+        // layer-2 MMAs, the buffer's readers, have completed)
+        {
+            float v[32];
+            tmem_ld16(taddr + lanes + 32u * (uint32_t)cg, v);
+            tmem_ld16(taddr + lanes + 32u * (uint32_t)cg + 16u, v + 16);
+            tmem_wait_ld();
+            uint32_t w[16];
+            const float4* bb = reinterpret_cast<const float4*>(sm.b2 + 32 * cg);
 #pragma unroll
-        for (int c16 = 0; c16 < 2; ++c16) {
+            for (int e4 = 0; e4 < 8; ++e4) {
+                const float4 b = bb[e4];
+                w[2 * e4] = bf16x2(silu_fast(v[4 * e4] + b.x), silu_fast(v[4 * e4 + 1] + b.y));
+                w[2 * e4 + 1] = bf16x2(silu_fast(v[4 * e4 + 2] + b.z), silu_fast(v[4 * e4 + 3] + b.w));
+            }
+            tmem_st16(taddr + lanes + hb + 16u * (uint32_t)cg, w);
+            tmem_wait_st();
+        }
+        tc_fence_before();
+        __syncthreads();
+        // ---- layer 3 into D (columns 0 .. FI_NO - 1)
+        if (tid == 0) mma_layer(hb, sW3, FI_NO, id3);
+        if (!wait_mma()) {
+            aborted = true;
+            break;
+        }
+        tc_fence_after();
+        // ---- drain D: 16 output columns per warp, written out 32 rows at a
+        // time through shared memory so that consecutive threads store
+        // consecutive columns of a row (a warp's own values are 32 rows apart
+        // in Y)
+        {
+            const int c0 = 16 * cg;
+            const bool have = c0 < nout;   // the same for the whole warp
             float v[16];
-            const int c0 = 32 * cg + 16 * c16;
-            tmem_ld16(taddr + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0, v);
-            tmem_wait_ld();
-            float bb[16];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float4 b4 = reinterpret_cast<const float4*>(b2 + c0)[e];
-                bb[4 * e] = b4.x;
-                bb[4 * e + 1] = b4.y;
-                bb[4 * e + 2] = b4.z;
-                bb[4 * e + 3] = b4.w;
+            if (have) {
+                tmem_ld16(taddr + lanes + (uint32_t)c0, v);
+                tmem_wait_ld();
             }
+            for (int qd = 0; qd < 4; ++qd) {
+                if (quad == qd && have) {
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                uint32_t w[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int u = 8 * half + 2 * e;
-                    w[e] = bf16x2(silu_fast(v[u] + bb[u]), silu_fast(v[u + 1] + bb[u + 1]));
+                    for (int t = 0; t < 16; ++t) {
+                        const int c = c0 + t;
+                        if (c < nout) stag[lane * FI_STG + c] = fmaf(v[t], sm.out_a[c], sm.out_c[c]);
+                    }
                 }
-                const int k = c0 + 8 * half;
-                *reinterpret_cast<uint4*>(gH + (k >> 6) * (FI_TM * 128) + swz_offset(row, k & 63)) =
-                    make_uint4(w[0], w[1], w[2], w[3]);
+                __syncthreads();
+                const int64_t r0 = tile * FI_TM + 32 * qd;
+                const int rows = (int)min((int64_t)32, n - r0);
+                for (int e = tid; e < rows * nout; e += FI_THREADS) {
+                    const int r = e / nout, c = e - r * nout;
+                    Y[(r0 + r) * ystride + c] = stag[r * FI_STG + c];
+                }
+                __syncthreads();
             }
         }
-        fence_proxy_async_smem();
+        // D read before the next tile's layer-2 MMAs overwrite it
         tc_fence_before();
         __syncthreads();
-        // ---- layer 3 on the tensor cores (TMEM columns 256..319)
-        if (tid == 0) {
-            tc_fence_after();
-#pragma unroll
-            for (int kb = 0; kb < 4; ++kb)
-#pragma unroll
-                for (int k16 = 0; k16 < 4; ++k16)
-                    tc_mma_f16(taddr + 256u, sw128_desc(sH + kb * (FI_TM * 128)) + 2 * k16,
-                               sw128_desc(sW3 + kb * (FI_NO * 128)) + 2 * k16, id3, (kb | k16) ? 1u : 0u);
-            tc_commit(&bar_mma);
-        }
-        {
-            const bool ok = mbar_wait(&bar_mma, phase, limit_ns, &s_abort);
-            if (__syncthreads_or(!ok)) {
-                aborted = true;
-                break;
-            }
-        }
-        phase ^= 1u;
-        tc_fence_after();
-        // ---- drain D3: 8 columns per warp
-        {
-            float v[8];
-            const int c0 = 8 * cg;
-            tmem_ld8(taddr + ((uint32_t)(32 * quad) << 16) + 256u + (uint32_t)c0, v);
-            tmem_wait_ld();
-            const int64_t q = q0 + row;
-            if (q < n) {
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const int c = c0 + t;
-                    if (c < nout) Y[q * ystride + c] = (v[t] + b3[c]) * ystd[c] + ymean[c];
-                }
-            }
-        }
-        // TMEM read and the A buffer free before the next tile
-        tc_fence_before();
-        __syncthreads();
+        if (next < ntiles && tid == 0) mma_layer(hn, sW2, FI_H, id2);
     }
     if (aborted) {
         if (tid == 0) atomicExch(err, 1);
-        // let any MMA still in flight finish (bounded) before TMEM is freed
+        // let the MMAs still in flight finish (bounded) before TMEM is freed
         if (tid == 0) {
             const uint64_t t0 = gtimer();
             while (!mbar_try_wait(&bar_mma, phase) && gtimer() - t0 < 1000000000ull) {
@@ -881,10 +937,10 @@ nms_status nms_surrogate_infer(nms_surrogate_t s, const float* X, int64_t n, flo
     set_error("");
     if (!s || !X || !Y || n < 0) return NMS_ERR_INVALID_ARG;
     if (n == 0) return NMS_OK;
-    if (s->H == FI_H && s->nout <= 4 * FI_NO && s->nin <= 8) {
-        // the whole network in one tensor-core kernel per 64 outputs (W3 and
-        // the 128-query activation tile fill the shared memory; more
-        // outputs run the hidden layers again for each further 64)
+    if (s->H == FI_H && s->nout <= 2 * FI_NO && s->nin <= 8) {
+        // the whole network in one tensor-core kernel per 128 outputs (W2 and
+        // W3 fill the shared memory; more outputs run the hidden layers
+        // again for the further 128)
         static bool attr = false;
         if (!attr) {
             NMS_CUDA_TRY(cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, FI_SMEM));

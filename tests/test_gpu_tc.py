@@ -288,6 +288,48 @@ def test_tc_amplitudes_capture_in_cuda_graph():
         assert np.array_equal(got, ref)
 
 
+def test_tc_ensemble_graph_replay_matches_oracle():
+    # An ensemble of 1500 small spheres captured once in a CUDA graph and
+    # replayed: a point-symmetric detector with 128-pixel q_y rows (half-plane
+    # amplitudes, the bulk-copy dilute pass split into output slices), a
+    # table workspace small enough for many chunks.  Every replay must give
+    # the eager result bit for bit, and the eager result must match the
+    # oracle's total, dilute and interference parts.
+    torch = pytest.importorskip("torch")
+    f = I.sphere_ensemble(n_spheres=1500, median=2.5, sigma=0.35, clip=(1.5, 4.0), a=1.0, cube=300.0, seed=17)
+    kw = dict(kind="cartesian", n0=128, n1=64, lo0=-1.5, hi0=1.5, lo1=-1.2, hi1=1.2)
+    side = torch.cuda.Stream()
+    opt = nms.nms_options_default(precision=TC, want_dilute=1, workspace_bytes=8 << 20)
+    plan = nms.plan_from_field(f, nms.make_grid(**kw), opt, stream=side.cuda_stream)
+    assert nms.nms_plan_info(plan)["mirror"] == (1, 1)
+    ids = ("N", "M", "SF", "UNPOL")
+    parts_of = (nms.PART_TOTAL, nms.PART_DILUTE, nms.PART_INTERFERENCE)
+    nms.nms_amplitudes(plan)                     # eager, outside capture
+    eager = {(k, pt): nms.nms_response(plan, k, pt).copy() for k in ids for pt in parts_of}
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        graph.capture_begin()
+        nms.nms_amplitudes(plan)
+        graph.capture_end()
+    for _ in range(2):
+        with torch.cuda.stream(side):
+            graph.replay()
+        torch.cuda.synchronize()
+        for k in ids:
+            for pt in parts_of:
+                assert np.array_equal(nms.nms_response(plan, k, pt), eager[(k, pt)]), (k, pt)
+    g = og(kw)
+    ref = S.response_parts(f, np.eye(3), g, ids=ids)
+    tol = 2 * resp_tol(f)
+    wk = [np.abs(S.cell_weights(f.vol[a:b], f.nuc[a:b], f.mag[a:b], np.eye(3))).sum(1)
+          for a, b in zip(f.offsets[:-1], f.offsets[1:])]
+    tol_dil = 4e-6 * sum((w[0] + w[1] + w[2] + w[3]) ** 2 for w in wk)
+    for k in ids:
+        assert np.max(np.abs(eager[(k, nms.PART_TOTAL)] - ref[k][0])) <= tol, k
+        assert np.max(np.abs(eager[(k, nms.PART_DILUTE)] - ref[k][1])) <= tol_dil, k
+        assert np.max(np.abs(eager[(k, nms.PART_INTERFERENCE)] - ref[k][2])) <= tol + tol_dil, k
+
+
 def test_tc_autotune_picks_valid_config_and_caches(tmp_path, monkeypatch):
     cache = tmp_path / "tune.txt"
     monkeypatch.setenv("NMS_AUTOTUNE_CACHE", str(cache))

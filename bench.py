@@ -721,8 +721,8 @@ def run_surrogate(args, dev):
                          "frac": achieved / peak, "traffic": None, "kernel": "k_mlp_infer (fused tcgen05 bf16)",
                          "peak_source": f"{peak_src} bf16 dense"},
             "cpu_baseline": None, "e2e": None,
-            # the fused kernel runs once per 64 outputs of each call
-            "gpu_launches": len(times) * -(-n_out // 64) if (H == 256 and n_out <= 256) else None,
+            # the fused kernel runs once per 128 outputs of each call
+            "gpu_launches": len(times) * -(-n_out // 128) if (H == 256 and n_out <= 256) else None,
             "clocks": clocks}
     print(json.dumps(line), flush=True)
     s.close()

@@ -337,10 +337,10 @@ nms_status nms_surrogate_gradients(nms_surrogate_t s, const float* X, const floa
                                    double* loss);
 
 /* Y [n][n_out] (device, FP32, de-standardised log10 I) for device X [n][n_in].
- * With H = 256, n_out <= 64 and n_in <= 8 the whole network runs as one
- * tensor-core kernel and the call synchronises the surrogate's stream to read
- * that kernel's error word (TIMEOUT if a bounded wait gave up); otherwise it
- * is asynchronous on the surrogate's stream. */
+ * With H = 256, n_out <= 256 and n_in <= 8 the whole network runs as one
+ * tensor-core kernel per 128 outputs and the call synchronises the
+ * surrogate's stream to read that kernel's error word (TIMEOUT if a bounded
+ * wait gave up); otherwise it is asynchronous on the surrogate's stream. */
 nms_status nms_surrogate_infer(nms_surrogate_t s, const float* X, int64_t n, float* Y);
 
 /* Master parameters to/from host (count = number of parameters). */

@@ -102,11 +102,13 @@ def test_gradients_match_fp64_oracle(H):
     s.close()
 
 
-@pytest.mark.parametrize("H,nout,n", [(256, 55, 1000), (256, 64, 128), (256, 7, 37), (256, 128, 333), (64, 55, 300)])
+@pytest.mark.parametrize("H,nout,n", [(256, 55, 1000), (256, 64, 128), (256, 7, 37), (256, 128, 333),
+                                      (256, 200, 301), (64, 55, 300)])
 def test_inference_matches_fp64_oracle(H, nout, n):
-    # H = 256 runs the fused tensor-core kernel, once per 64 outputs (ragged
-    # last tile, a single tile, fewer rows than a tile, two output parts);
-    # H = 64 the layer-by-layer path.  Against the FP64 forward at the same parameters, with the GEMM
+    # H = 256 runs the fused tensor-core kernel, once per 128 outputs (ragged
+    # last tile, a single tile, fewer rows than a tile, a full pass of 128,
+    # two passes whose outputs are a part of each row); H = 64 the
+    # layer-by-layer path.  Against the FP64 forward at the same parameters, with the GEMM
     # weights rounded to BF16 as the kernels use them; the remaining gap is
     # the BF16 rounding of the hidden activations.
     nin = 6

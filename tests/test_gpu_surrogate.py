@@ -138,6 +138,38 @@ def test_inference_matches_fp64_oracle(H, nout, n):
     s.close()
 
 
+@pytest.mark.parametrize("nout,n", [(55, 4096), (128, 2048), (200, 1000)])
+def test_inference_matches_bf16_activation_forward(nout, n):
+    # The fused kernel against the FP64 network with its GEMM weights and
+    # hidden activations rounded to BF16 where the kernel rounds them (after
+    # each SiLU): what remains is the order of the FP32 sums, layer 1 in FP32
+    # and the fast exponential and division in SiLU, which now and then move
+    # a BF16 rounding decision of an activation by one unit.
+    nin, H = 6, 256
+    lo = I.VORTEX_FAMILY_BOUNDS[:, 0].astype(np.float32)
+    hi = I.VORTEX_FAMILY_BOUNDS[:, 1].astype(np.float32)
+    s = nms.nms_surrogate_create(nin, H, nout, lo, hi, seed=5)
+    rng = np.random.default_rng(6)
+    ym, ys = rng.normal(size=nout).astype(np.float32), rng.uniform(0.5, 2, size=nout).astype(np.float32)
+    nms.nms_surrogate_set_target_stats(s, ym, ys)
+    X = I.vortex_family_params(n, seed=7).astype(np.float32)
+    out = torch.full((n, nout), float("nan"), device="cuda")
+    nms.nms_surrogate_infer(s, torch.tensor(X, device="cuda"), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    bf = lambda v: torch.tensor(v, dtype=torch.float64).to(torch.bfloat16).to(torch.float64).numpy()
+    W1, b1, W2, b2, W3, b3 = OM.split(nms.nms_surrogate_get_params(s).astype(np.float64), nin, H, nout)
+    Xn = 2.0 * (X.astype(np.float64) - lo) / (hi.astype(np.float64) - lo) - 1.0
+    H1 = bf(OM.silu(Xn @ W1.T + b1))
+    H2 = bf(OM.silu(H1 @ bf(W2).T + b2))
+    ref = (H2 @ bf(W3).T + b3) * ys.astype(np.float64) + ym.astype(np.float64)
+    err = np.abs(got - ref) / ys.astype(np.float64)
+    rms = np.sqrt(np.mean(err ** 2))
+    # measured on GB300: max 3.7e-3 .. 4.1e-3 (rounding flips), RMS 4.1e-5 .. 5.7e-5
+    assert err.max() <= 1e-2 and rms <= 2e-4, (err.max(), rms)
+    s.close()
+
+
 def test_training_learns_and_checkpoint_resumes(tmp_path):
     nin, H, nout, n = 6, 64, 16, 4096
     lo = np.zeros(nin, np.float32)

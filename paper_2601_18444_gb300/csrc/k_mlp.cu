@@ -229,7 +229,7 @@ __device__ __forceinline__ uint32_t bf16x2(float a, float b)
 // 32 (w / 4) .. + 31.  The arithmetic is that of the layer-by-layer path
 // (BF16 operands, FP32 accumulation and activations); only the order of the
 // FP32 sums differs.
-constexpr int FI_THREADS = 1024;   // 32 warps: the element-wise work needs many warps in flight
+constexpr int FI_THREADS = 1024;   // 32 warps (one per row of a 32-row output stage): the element-wise work needs many warps in flight
 constexpr int FI_H = 256;
 constexpr int FI_NO = 128;     // outputs per launch; W3 rows padded with zeros
 constexpr int FI_TM = 128;     // queries per tile (the MMA's M)
@@ -238,6 +238,7 @@ constexpr int FI_W3_BYTES = 4 * FI_NO * 128;
 constexpr int FI_SMEM = FI_W2_BYTES + FI_W3_BYTES + 1024;
 constexpr uint32_t FI_HB = 256;               // TMEM column of activation buffer 0 (buffer 1: + 128)
 constexpr int FI_STG = FI_NO + 1;             // row stride of the output staging buffer (odd: no bank conflicts)
+static_assert(FI_THREADS == 32 * 32, "the output stage maps one warp to each of its 32 rows");
 
 // Small per-launch tables in shared memory (read as warp-wide broadcasts):
 // layer-1 weights padded to 8 inputs (with n_in < 8 the bias takes input
@@ -452,12 +453,10 @@ k_mlp_infer(int64_t n, int nin, int nout, int ystride, const float* __restrict__
                     }
                 }
                 __syncthreads();
-                const int64_t r0 = tile * FI_TM + 32 * qd;
-                const int rows = (int)min((int64_t)32, n - r0);
-                for (int e = tid; e < rows * nout; e += FI_THREADS) {
-                    const int r = e / nout, c = e - r * nout;
-                    Y[(r0 + r) * ystride + c] = stag[r * FI_STG + c];
-                }
+                // warp w writes staged row w, its lanes consecutive columns
+                const int64_t q = tile * FI_TM + 32 * qd + warp;
+                if (q < n)
+                    for (int c = lane; c < nout; c += 32) Y[q * ystride + c] = stag[warp * FI_STG + c];
                 __syncthreads();
             }
         }

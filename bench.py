@@ -817,9 +817,12 @@ def run_paper_shape(args, dev):
     """The paper's interparticle-interference example as a shape: 800 D = 40 nm
     spheres (4169 cells each, linear vortex) on a 45 nm simple-cubic lattice,
     one sum over 3.34e6 cells on the paper's polar (q, theta) grid of 1000 x
-    1000 nodes, q in [0, 1.5] nm^-1 -- the direct FP32 path (compensated
-    phase), the only one for a polar grid.  One step = amplitudes, the
-    unpolarized and spin-flip images, their azimuthal averages and c(r)."""
+    1000 nodes, q in [0, 1.5] nm^-1.  The library's default path there is the
+    tensor path, one GEMM per ray (--precision direct: the compensated FP32
+    direct sum).  One step = amplitudes, the unpolarized and spin-flip images,
+    their azimuthal averages and c(r).  With the tensor path the line also
+    times one step of the direct sum on the same plan inputs and gives the
+    largest difference of the two unpolarized images."""
     import torch
     from paper_2601_18444_gb300 import inputs as I
     from paper_2601_18444_gb300 import nms
@@ -827,48 +830,98 @@ def run_paper_shape(args, dev):
     f = lattice_copies(particle, 800)
     g = nms.make_grid("polar", 1000, 1000, 0.0, 1.5)
     stream = torch.cuda.current_stream()
-    plan = nms.plan_from_field(f, g, nms.nms_options_default(timing=1), stream=stream.cuda_stream)
-    npix = plan.npix
-    img_u = torch.empty(npix, dtype=torch.float64, device="cuda")
-    img_s = torch.empty(npix, dtype=torch.float64, device="cuda")
+    prec = {"auto": nms.PREC_AUTO, "tc": nms.PREC_TC_F16X3, "direct": nms.PREC_FP32_DIRECT,
+            "naive": nms.PREC_FP32_NAIVE}[args.precision]
     r = np.linspace(0.0, 400.0, 200)
 
-    def step():
-        nms.nms_amplitudes(plan)
-        nms.nms_response(plan, "UNPOL", out=img_u)
-        nms.nms_response(plan, "SF", out=img_s)
-        for img in (img_u, img_s):
-            Iq, c, qm = nms.nms_azimuthal_average(plan, img, nbins=1000)
-            nms.nms_correlation(qm, Iq, r, stream=stream.cuda_stream)
+    def make(pr):
+        plan = nms.plan_from_field(f, g, nms.nms_options_default(timing=1, precision=pr), stream=stream.cuda_stream)
+        img_u = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
+        img_s = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
 
-    warm, steps = max(1, min(args.warmup, 1)), max(1, min(args.steps, 2))
-    for _ in range(warm):
-        step()
-    torch.cuda.synchronize()
-    nms.nms_plan_stage_ms(plan, reset=True)
-    peaks, _ = load_peaks()
-    ts = []
-    with ClockSampler(dev) as clk:
-        for _ in range(steps):
+        def step():
+            nms.nms_amplitudes(plan)
+            nms.nms_response(plan, "UNPOL", out=img_u)
+            nms.nms_response(plan, "SF", out=img_s)
+            for img in (img_u, img_s):
+                Iq, c, qm = nms.nms_azimuthal_average(plan, img, nbins=1000)
+                nms.nms_correlation(qm, Iq, r, stream=stream.cuda_stream)
+        return plan, step, img_u
+
+    def timed(step, n):
+        ts = []
+        for _ in range(n):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             step()
             e1.record(stream)
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
+        return float(np.mean(ts))
+
+    plan, step, img_u = make(prec)
+    path = nms.nms_plan_info(plan)["precision"]
+    if path == nms.PREC_TC_F16X3:
+        warm, steps = max(3, args.warmup), max(1, args.steps)
+    else:   # seconds per step: a short run
+        warm, steps = max(1, min(args.warmup, 1)), max(1, min(args.steps, 2))
+    for _ in range(warm):
+        step()
+    torch.cuda.synchronize()
+    nms.nms_plan_stage_ms(plan, reset=True)
+    peaks, peak_src = load_peaks()
+    with ClockSampler(dev) as clk:
+        ms = timed(step, steps)
     st = nms.nms_plan_stage_ms(plan)
-    ms = float(np.mean(ts))
-    terms = float(f.n) * npix
+    terms = float(f.n) * plan.npix
     clocks = clk.summary(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-    peak = sms * 128 * mhz * 1e6 / 1e12
-    k_ms = st["direct"][0] / steps
-    achieved = terms * DIRECT_OPS_PER_TERM / (k_ms * 1e-3) / 1e12
-    line = {"metric": "cell·q-point terms/s of the SANS Fourier sum, paper's example shape (polar grid, direct path)",
+    extra = {}
+    if path == nms.PREC_TC_F16X3:
+        # one GEMM per ray: |q| nodes as k1 x k2 (k2 = 64), one 128 x 128 output
+        # tile per ray, so each table block (32 KB per tile and 64 cells) feeds
+        # one tile and the GEMM streams its tables from HBM: HBM roofline
+        k_ms = st["gemm"][0] / steps
+        n0, n1 = 1000, 1000
+        k2 = min(64, n0)
+        k1 = -(-n0 // k2)
+        tiles = -(-(2 * 4 * k1) // 128) + -(-(2 * k2) // 128)
+        n_rays = n1 // 2 if n1 % 2 == 0 else n1
+        table_bytes = n_rays * (-(-f.n // 64)) * tiles * 32768.0
+        achieved = table_bytes / (k_ms * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        tflops = terms * ALGO_FLOPS_PER_TERM / (k_ms * 1e-3) / 1e12
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_gemm_f16x3", "algorithmic_bytes_per_launch": "table bytes read",
+                "table_bytes_per_step": table_bytes, "peak_source": f"{peak_src} HBM copy",
+                "tensor": {"tflops_algorithmic": tflops, "flops_per_term": ALGO_FLOPS_PER_TERM,
+                           "frac_of_bf16_burst": tflops / peaks.get("bf16_tflops", 1900.0)},
+                "note": f"one GEMM per ray: {n0} |q| nodes as {k1} x {k2} (padded to {k1 * k2}), the ray "
+                        "theta + pi taken as the conjugate"}
+        if not args.no_fp32_leg:
+            ref_u = img_u.cpu().numpy()
+            dplan, dstep, dimg = make(nms.PREC_FP32_DIRECT)
+            dstep()
+            torch.cuda.synchronize()
+            d_ms = timed(dstep, 1)
+            du = dimg.cpu().numpy()
+            extra["fp32_direct"] = {"value": terms / (d_ms * 1e-3), "unit": "terms/s", "ms_per_step": d_ms,
+                                    "tc_over_fp32": d_ms / ms,
+                                    "unpol_max_abs_diff_over_max": float(np.max(np.abs(ref_u - du)) / np.max(np.abs(du)))}
+            dplan.close()
+    else:
+        peak = sms * 128 * mhz * 1e6 / 1e12
+        k_ms = st["direct"][0] / steps
+        achieved = terms * DIRECT_OPS_PER_TERM / (k_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_direct<compensated>",
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz"}
+    pname = "tensor path, one GEMM per ray" if path == nms.PREC_TC_F16X3 else "direct path"
+    line = {"metric": f"cell·q-point terms/s of the SANS Fourier sum, paper's example shape (polar grid, {pname})",
             "value": terms / (ms * 1e-3), "unit": "terms/s", "n_gpus": 1, "steps": steps, "warmup": warm,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32(two-float)", "data": "synthetic",
+            "dtype": "f16x3->f32(two-float)" if path == nms.PREC_TC_F16X3 else "f32(two-float)", "data": "synthetic",
             "config": {"workload": "800 x linear-vortex sphere D=40nm a=2nm (3.34e6 cells) on a 45nm simple-cubic "
                                    "lattice; polar grid 1000 q in [0,1.5] nm^-1 x 1000 theta; UNPOL + SF, "
                                    "azimuthal averages, c(r) on 200 r",
@@ -876,10 +929,8 @@ def run_paper_shape(args, dev):
                        "paper_context": "about 60 s on an RTX 3090 for 3.38e6 cells on a 1000x1000 (q, theta) grid "
                                         "with all outputs incl. a 1000x1000 2D correlation and 670 MB of CSV "
                                         "(>= 5.6e10 terms/s)"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_direct<compensated>",
-                         "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz"},
-            "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks}
+            "roofline": roof, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks}
+    line.update(extra)
     print(json.dumps(line), flush=True)
     plan.close()
     return 0

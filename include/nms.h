@@ -72,10 +72,16 @@ typedef struct {
 
 /* How the Fourier sums are evaluated. */
 typedef enum {
-    NMS_PREC_AUTO = 0,          /* TC_F16X3 on CARTESIAN grids, FP32_DIRECT otherwise   */
+    NMS_PREC_AUTO = 0,          /* TC_F16X3 on CARTESIAN grids and on POLAR grids
+                                   without per-object parts, FP32_DIRECT otherwise */
     NMS_PREC_TC_F16X3 = 1,      /* split-FP16 (hi/lo, 3 products) tcgen05 GEMM, FP32
                                    TMEM accumulation promoted to two-float every
-                                   kc_cells cells; CARTESIAN grids only.  It takes
+                                   kc_cells cells; CARTESIAN grids, and POLAR grids
+                                   as one GEMM per ray (the phase |q| u with u the
+                                   cell's projection on the ray splits over two
+                                   axes |q| = lo + 64 i1 dq + i2 dq; the ray at
+                                   theta + pi is the conjugate; no per-object
+                                   parts, no per-object averages).  It takes
                                    the place of TF32x3 (same ~2^-22 per-product
                                    error, but TF32 runs at half the FP16 rate on
                                    tcgen05), BF16x3 (2^-17: misses 1e-6) and
@@ -154,8 +160,9 @@ nms_status nms_options_default(nms_options* opt);
  *   opt             options (copied), or NULL for defaults.
  *   cuda_stream     cudaStream_t every launch of this plan goes to (NULL: the
  *                   legacy default stream).
- * Errors: INVALID_ARG (sizes, offsets not monotone, TC precision on a
- * non-CARTESIAN grid), OUT_OF_MEMORY, CUDA. */
+ * Errors: INVALID_ARG (sizes, offsets not monotone, TC precision on a LIST
+ * grid), UNSUPPORTED (TC precision on a POLAR grid with want_dilute and
+ * several objects), OUT_OF_MEMORY, CUDA. */
 nms_status nms_plan_create(nms_plan_t* out, int64_t n_cells, const double* pos,
                            const double* cell_vol, const double* nuc, const double* mag,
                            int64_t n_objects, const int64_t* object_offsets,
@@ -286,7 +293,8 @@ nms_status nms_correlation(int32_t nq, const double* q, const double* Iq, int32_
  * response_id (N, M, P, SF or UNPOL) of its own amplitude F_k over the ring
  * bins edges[b] <= |q| < edges[b+1] (bin_edges host [nbins+1], increasing,
  * nbins <= 8192).  This is how surrogate training data are generated in one
- * batched pass.  Tensor-core path only (UNSUPPORTED otherwise). */
+ * batched pass.  Tensor-core path on a CARTESIAN grid only (UNSUPPORTED
+ * otherwise). */
 nms_status nms_plan_object_iq(nms_plan_t plan, int32_t response_id, int32_t nbins, const double* bin_edges);
 
 /* Results of nms_plan_object_iq after nms_amplitudes: Iq[k][b] = mean over

@@ -106,6 +106,109 @@ cudaError_t launch_prep_rot_batch(const Plan& p, const double* d_rot, int rot0, 
     return cudaGetLastError();
 }
 
+// Polar detector on the tensor path (rays).  On the ray at angle theta the
+// pixel q = |q| (sin theta, cos theta) (the POLAR grid's q_y, q_z) has the
+// phase q.r = |q| u with u = Y sin theta + Z cos theta, so every ray is a
+// one-dimensional sum over the projections u.  Slot s of a batch (rotation
+// s / n_rays, ray s mod n_rays) gets the projection of its rotated position
+// in both coordinates, (u, u), and the rotated weights as in
+// k_prep_rot_batch (the weights do not depend on the ray).
+__global__ void k_prep_ray_batch(int64_t n, int n_sets, int64_t wstride, const double* __restrict__ pos,
+                                 const double* __restrict__ vol, const double* __restrict__ nuc,
+                                 const double* __restrict__ mag, const double* __restrict__ cen_cell,
+                                 const double* __restrict__ rot, const double2* __restrict__ ray_sc, int n_rays,
+                                 int slot0, float4* __restrict__ cpos, float4* __restrict__ cw)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int rl = blockIdx.y;
+    const int slot = slot0 + rl;
+    const double* r = rot + 9 * (int64_t)(slot / n_rays);
+    const double2 sc = ray_sc[slot % n_rays];   // (sin theta, cos theta)
+    double x = pos[3 * j], y = pos[3 * j + 1], z = pos[3 * j + 2];
+    if (cen_cell) {
+        x += cen_cell[3 * j];
+        y += cen_cell[3 * j + 1];
+        z += cen_cell[3 * j + 2];
+    }
+    const double u = sc.x * (r[3] * x + r[4] * y + r[5] * z) + sc.y * (r[6] * x + r[7] * y + r[8] * z);
+    const int64_t o = (int64_t)rl * n + j;
+    cpos[o] = split_pos(u, u);
+    const double v = vol ? vol[j] : 1.0;
+    for (int st = 0; st < n_sets; ++st) {
+        const int64_t js = (int64_t)st * n + j;
+        const double wn = nuc ? v * nuc[js] : 0.0;
+        double wx = 0.0, wy = 0.0, wz = 0.0;
+        if (mag) {
+            const double mx = mag[3 * js], my = mag[3 * js + 1], mz = mag[3 * js + 2];
+            wx = v * (r[0] * mx + r[1] * my + r[2] * mz);
+            wy = v * (r[3] * mx + r[4] * my + r[5] * mz);
+            wz = v * (r[6] * mx + r[7] * my + r[8] * mz);
+        }
+        cw[(int64_t)st * wstride + o] = make_float4((float)wn, (float)wx, (float)wy, (float)wz);
+    }
+}
+
+// The same slots from inputs rotated once per rotation: rpos [n_rot][n]
+// holds the rotated (Y, Z) of every cell as two-float and rw
+// [set][n_rot][n] its weights (k_prep_rot_batch over all rotations).  The
+// projection u = Y sin theta + Z cos theta is formed in two-float FP32
+// arithmetic (products made exact by FMA, sums by TwoSum; relative error
+// about 2^-44 of |Y| + |Z|, far below what the phase tables resolve), so the
+// per-ray work has no FP64; the weights are copied.
+__device__ __forceinline__ void ray_two_prod(float a_h, float a_l, float b_h, float b_l, float& p, float& e)
+{
+    p = a_h * b_h;
+    e = fmaf(a_h, b_h, -p) + fmaf(a_h, b_l, a_l * b_h);
+}
+
+__global__ void k_prep_ray_from_rot(int64_t n, int n_sets, int64_t wstride, int64_t rwstride,
+                                    const float4* __restrict__ rpos, const float4* __restrict__ rw,
+                                    const float4* __restrict__ ray_sc_tf, int n_rays, int slot0,
+                                    float4* __restrict__ cpos, float4* __restrict__ cw)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int rl = blockIdx.y;
+    const int slot = slot0 + rl;
+    const int64_t src = (int64_t)(slot / n_rays) * n + j;
+    const float4 sc = ray_sc_tf[slot % n_rays];   // sin theta (hi, lo), cos theta (hi, lo)
+    const float4 yz = rpos[src];                  // Y (hi, lo), Z (hi, lo)
+    float p1, e1, p2, e2;
+    ray_two_prod(sc.x, sc.y, yz.x, yz.y, p1, e1);
+    ray_two_prod(sc.z, sc.w, yz.z, yz.w, p2, e2);
+    const float s = p1 + p2;
+    const float bb = s - p1;
+    const float e = ((p1 - (s - bb)) + (p2 - bb)) + (e1 + e2);
+    const float uh = s + e;
+    const float ul = e - (uh - s);
+    const int64_t o = (int64_t)rl * n + j;
+    cpos[o] = make_float4(uh, ul, uh, ul);
+    for (int st = 0; st < n_sets; ++st) cw[(int64_t)st * wstride + o] = rw[(int64_t)st * rwstride + src];
+}
+
+cudaError_t launch_prep_ray_from_rot(const Plan& p, const float4* rpos, const float4* rw, int64_t rwstride,
+                                     const float4* ray_sc_tf, int n_rays, int slot0, int nrl, float4* cpos, float4* cw,
+                                     int64_t wstride, cudaStream_t s)
+{
+    const int64_t n = p.n_cells;
+    if (n <= 0 || nrl <= 0) return cudaSuccess;
+    k_prep_ray_from_rot<<<dim3((unsigned)((n + 255) / 256), (unsigned)nrl), 256, 0, s>>>(
+        n, p.n_sets, wstride, rwstride, rpos, rw, ray_sc_tf, n_rays, slot0, cpos, cw);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_ray_batch(const Plan& p, const double* d_rot, const double2* ray_sc, int n_rays, int slot0,
+                                  int nrl, float4* cpos, float4* cw, int64_t wstride, cudaStream_t s)
+{
+    const int64_t n = p.n_cells;
+    if (n <= 0 || nrl <= 0) return cudaSuccess;
+    k_prep_ray_batch<<<dim3((unsigned)((n + 255) / 256), (unsigned)nrl), 256, 0, s>>>(
+        n, p.n_sets, wstride, p.d_pos, p.d_vol, p.d_nuc, p.d_mag, p.d_cen_cell, d_rot, ray_sc, n_rays, slot0, cpos,
+        cw);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_prep_rot(const Plan& p, const RotMat& R, bool global, float4* cpos, float4* cw, int64_t wstride,
                             cudaStream_t s)
 {
@@ -254,6 +357,75 @@ cudaError_t launch_gacc_totals(const double* T, int n_out, int64_t ostride, int6
     FbView none{};
     k_gacc_batch<false><<<(unsigned)((npix + 127) / 128), 128, 0, s>>>(
         none, reinterpret_cast<const double2*>(T), n_out, ostride / 2, npix, G);
+    return cudaGetLastError();
+}
+
+// Rays (polar detector, see k_prep_ray_batch): the outputs of a batch are
+// the slots slot0 .. slot0 + n_out - 1 (rotation slot / n_rays, ray slot mod
+// n_rays); output o holds its ray's amplitudes at |q|_i, i = k2 i1 + i2, in
+// GEMM cell (a = i1, b = i2).  One thread per (ray, |q| node) adds F F^dagger
+// of every output of the batch on that ray (one rotation after another, so
+// no two threads update one value) into G at the POLAR pixel i n1 + ray and,
+// when n1 is even (mirror), the conjugate products at the ray theta + pi,
+// pixel i n1 + ray + n1 / 2: there q is negated and F(-q) = conj F(q) for
+// real weights.  The amplitudes of rotation last_rot also go to F (FP64).
+// G is accumulated in FP64 from the two-float amplitudes (a few values per
+// pixel and rotation).
+__global__ void k_ray_gacc(FbView V, int n_out, int slot0, int n_rays, int mirror, int n0, int n1, int k2,
+                           int last_rot, double* __restrict__ G, double* __restrict__ Gd, double2* __restrict__ F)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n_rays * n0) return;
+    const int ray = (int)(t % n_rays), i = (int)(t / n_rays);
+    const int a = i / k2, b = i % k2;
+    const int64_t npix = (int64_t)n0 * n1;
+    const int64_t p = (int64_t)i * n1 + ray;
+    const int64_t pm = p + n1 / 2;
+    double g[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) g[k] = 0.0;
+    bool any = false;
+    for (int o = (ray - slot0 % n_rays + n_rays) % n_rays; o < n_out; o += n_rays) {
+        double2 f[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) f[c] = V.load_f64(o, a, b, c);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) g[c] += f[c].x * f[c].x + f[c].y * f[c].y;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int d = c + 1; d < 4; ++d) {
+                const int k = pair_idx(c, d);
+                g[4 + 2 * k] += f[c].x * f[d].x + f[c].y * f[d].y;
+                g[5 + 2 * k] += f[c].y * f[d].x - f[c].x * f[d].y;
+            }
+        if ((slot0 + o) / n_rays == last_rot)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                F[(int64_t)c * npix + p] = f[c];
+                if (mirror) F[(int64_t)c * npix + pm] = make_double2(f[c].x, -f[c].y);
+            }
+        any = true;
+    }
+    if (!any) return;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        G[(int64_t)k * npix + p] += g[k];
+        if (mirror) G[(int64_t)k * npix + pm] += g_conj_sign(k) * g[k];
+        if (Gd) {
+            Gd[(int64_t)k * npix + p] += g[k];
+            if (mirror) Gd[(int64_t)k * npix + pm] += g_conj_sign(k) * g[k];
+        }
+    }
+}
+
+cudaError_t launch_ray_gacc(const FbView& V, int n_out, int slot0, int n_rays, int mirror, int n0, int n1, int k2,
+                            int last_rot, double* G, double* Gd, double* F, cudaStream_t s)
+{
+    if (n_out <= 0) return cudaSuccess;
+    const int64_t nt = (int64_t)n_rays * n0;
+    k_ray_gacc<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(V, n_out, slot0, n_rays, mirror, n0, n1, k2, last_rot, G,
+                                                            Gd, reinterpret_cast<double2*>(F));
     return cudaGetLastError();
 }
 

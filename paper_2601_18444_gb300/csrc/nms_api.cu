@@ -394,9 +394,15 @@ nms_status nms_plan_create(nms_plan_t* out, int64_t n_cells, const double* pos, 
     // precision / path
     int prec = p->opt.precision;
     if (prec < NMS_PREC_AUTO || prec > NMS_PREC_FP32_NAIVE) return bail(fail(NMS_ERR_INVALID_ARG, "bad precision"));
-    if (prec == NMS_PREC_TC_F16X3 && grid->kind != NMS_QGRID_CARTESIAN)
-        return bail(fail(NMS_ERR_INVALID_ARG, "the tensor-core path needs a CARTESIAN (separable) grid"));
-    if (prec == NMS_PREC_AUTO) prec = grid->kind == NMS_QGRID_CARTESIAN ? NMS_PREC_TC_F16X3 : NMS_PREC_FP32_DIRECT;
+    if (prec == NMS_PREC_TC_F16X3 && grid->kind == NMS_QGRID_LIST)
+        return bail(fail(NMS_ERR_INVALID_ARG, "the tensor-core path needs a CARTESIAN or POLAR grid"));
+    // auto: the tensor path on CARTESIAN grids, and on POLAR grids (one GEMM
+    // per ray) unless per-object parts are wanted; the direct sum otherwise
+    if (prec == NMS_PREC_AUTO)
+        prec = (grid->kind == NMS_QGRID_CARTESIAN ||
+                (grid->kind == NMS_QGRID_POLAR && !(n_objects > 1 && p->opt.want_dilute)))
+                   ? NMS_PREC_TC_F16X3
+                   : NMS_PREC_FP32_DIRECT;
     p->path = prec;
     if (p->n_sets > 4096 || (prec == NMS_PREC_TC_F16X3 && p->n_sets > 32))
         return bail(fail(NMS_ERR_INVALID_ARG, "n_sets above 32 (tensor path) or 4096"));
@@ -854,7 +860,8 @@ nms_status nms_plan_object_iq(nms_plan_t plan, int32_t response_id, int32_t nbin
     set_error("");
     if (!plan) return fail(NMS_ERR_INVALID_ARG, "plan is NULL");
     Plan& p = *plan;
-    if (p.path != NMS_PREC_TC_F16X3) return fail(NMS_ERR_UNSUPPORTED, "per-object averages need the tensor-core path");
+    if (p.path != NMS_PREC_TC_F16X3 || p.grid.kind != NMS_QGRID_CARTESIAN)
+        return fail(NMS_ERR_UNSUPPORTED, "per-object averages need the tensor-core path on a CARTESIAN grid");
     if (p.n_sets > 1) return fail(NMS_ERR_UNSUPPORTED, "per-object averages take one weight set");
     if (!(response_id == NMS_RESP_N || response_id == NMS_RESP_M || response_id == NMS_RESP_P ||
           response_id == NMS_RESP_SF || response_id == NMS_RESP_UNPOL))

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -61,6 +62,13 @@ cudaError_t launch_dilute_shift_batch(const FbView& V, int n_out, const float2* 
                                       double* Gdil, double* Ftot, int64_t tstride, double* scratch, int32_t* err,
                                       uint64_t limit_ns, cudaStream_t s);
 int dilute_slices(int64_t stored_pixels);
+cudaError_t launch_prep_ray_batch(const Plan& p, const double* d_rot, const double2* ray_sc, int n_rays, int slot0,
+                                  int nrl, float4* cpos, float4* cw, int64_t wstride, cudaStream_t s);
+cudaError_t launch_ray_gacc(const FbView& V, int n_out, int slot0, int n_rays, int mirror, int n0, int n1, int k2,
+                            int last_rot, double* G, double* Gd, double* F, cudaStream_t s);
+cudaError_t launch_prep_ray_from_rot(const Plan& p, const float4* rpos, const float4* rw, int64_t rwstride,
+                                     const float4* ray_sc_tf, int n_rays, int slot0, int nrl, float4* cpos, float4* cw,
+                                     int64_t wstride, cudaStream_t s);
 cudaError_t launch_shift_factors(int n_out, const float4* cyz, const float2* qy, int ny, const float2* qz, int nz,
                                  float2* eyz, cudaStream_t s);
 
@@ -121,7 +129,18 @@ struct TcState {
     int mode = 0;                // GEMM form: 0 one CTA per tile, 2 two-SM MMA over A-tile pairs (even mtiles)
     bool mode_forced = false;    // set by NMS_GEMM_MODE: the autotuner keeps it
     bool objects = false;        // per-object amplitudes (dilute split) with shifts
-    int R_b = 1;                 // rotations prepared per rotation batch
+    int R_b = 1;                 // slots (rotations, or rotation x ray pairs) prepared per batch
+    int n_slots = 1;             // n_rot, or n_rot x n_rays
+    // POLAR grid (rays): slot s = ray s mod n_rays of rotation s / n_rays; the
+    // GEMM's q_y axis is |q| = lo + k2 i1 dq (i1 < ny), its q_z axis i2 dq
+    // (i2 < nz = k2), and both coordinates are the projection u of a cell on
+    // the ray; with n_theta even only the rays theta < pi are computed
+    bool rays = false;
+    int n_rays = 0, ray_mirror = 0;
+    double2* d_ray_sc = nullptr; // [n_rays] (sin theta, cos theta)
+    float4* d_ray_sc_tf = nullptr;   // the same as two-float (sin hi, lo, cos hi, lo)
+    float4* d_rpos = nullptr;    // rays: rotated (Y, Z) two-float [n_rot][n], or null (FP64 per slot)
+    float4* d_rw = nullptr;      // rays: rotated weights [set][n_rot][n]
     int64_t tab_kb = 0;          // table capacity in k-blocks
     float4* d_cpos_b = nullptr;  // [R_b][n]
     float4* d_cw_b = nullptr;
@@ -270,10 +289,16 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
             int64_t nkb_chunk = 0;
             for (const Piece& pc : pieces) nkb_chunk += (pc.n + KBC - 1) / KBC;
             ch.nkb = nkb_chunk;
-            // work items: about items_per_sm per SM, never shorter than 2 TMEM chunks
+            // work items: about items_per_sm per SM, never shorter than 2 TMEM
+            // chunks.  Each piece's split count is rounded up, which adds up to
+            // one item per piece and tile; when a few pieces share the chunk
+            // those extra items are kept inside the items_per_sm x SMs slots
+            // (beyond them the launch would take a second, mostly idle round)
             const int64_t ips = t.items_per_sm;
-            const int64_t kb_per_item =
-                std::max<int64_t>(2 * t.kcb, (nkb_chunk * tiles + ips * sms - 1) / (ips * sms));
+            const int64_t places = ips * sms;
+            const int64_t extra = (int64_t)pieces.size() * tiles;
+            const int64_t denom = (pieces.size() > 1 && 2 * extra <= places) ? places - extra : places;
+            const int64_t kb_per_item = std::max<int64_t>(2 * t.kcb, (nkb_chunk * tiles + denom - 1) / denom);
             std::vector<HostItem> its;
             ch.red_off = (int64_t)reds.size();
             int slot = 0;
@@ -635,9 +660,13 @@ void tc_form_info(const Plan& p, int32_t* form, int32_t* mirror_y, int32_t* mirr
 
 nms_status tc_setup(Plan& p)
 {
-    if (p.grid.kind != NMS_QGRID_CARTESIAN) {
-        set_error("tensor-core path needs a CARTESIAN grid");
+    if (p.grid.kind != NMS_QGRID_CARTESIAN && p.grid.kind != NMS_QGRID_POLAR) {
+        set_error("tensor-core path needs a CARTESIAN or POLAR grid");
         return NMS_ERR_INVALID_ARG;
+    }
+    if (p.grid.kind == NMS_QGRID_POLAR && p.n_objects > 1 && p.opt.want_dilute) {
+        set_error("tensor-core path on a POLAR grid: per-object parts (want_dilute) need the direct path");
+        return NMS_ERR_UNSUPPORTED;
     }
     if (tc_item_bytes() != sizeof(HostItem) || tc_red_bytes() != sizeof(HostRed)) {
         set_error("internal: work-list record size mismatch");
@@ -645,8 +674,11 @@ nms_status tc_setup(Plan& p)
     }
     TcState* t = new TcState();
     p.tc_state = t;
-    t->ny = p.grid.n0;
-    t->nz = p.grid.n1;
+    t->rays = p.grid.kind == NMS_QGRID_POLAR;
+    // rays: |q|_i = lo + i dq, i = k2 i1 + i2, split over the GEMM's two axes
+    const int k2 = t->rays ? std::min(64, p.grid.n0) : 0;
+    t->ny = t->rays ? (p.grid.n0 + k2 - 1) / k2 : p.grid.n0;
+    t->nz = t->rays ? k2 : p.grid.n1;
     t->nsets = p.n_sets;
     {
         int sp = 1;
@@ -660,8 +692,8 @@ nms_status tc_setup(Plan& p)
     const bool mirror_ok = !(mirror_env && atoi(mirror_env) == 0);
     t->ax.ny = t->ny;
     t->ax.nz = t->nz;
-    t->ax.my = (mirror_ok && t->ny >= 2 && p.grid.lo0 == -p.grid.hi0) ? 1 : 0;
-    t->ax.mz = (mirror_ok && t->nz >= 2 && p.grid.lo1 == -p.grid.hi1) ? 1 : 0;
+    t->ax.my = (!t->rays && mirror_ok && t->ny >= 2 && p.grid.lo0 == -p.grid.hi0) ? 1 : 0;
+    t->ax.mz = (!t->rays && mirror_ok && t->nz >= 2 && p.grid.lo1 == -p.grid.hi1) ? 1 : 0;
     t->ax.hy = t->ax.my ? t->ny / 2 : 0;
     t->ax.hz = t->ax.mz ? t->nz / 2 : 0;
     t->ax.nyg = t->ny - t->ax.hy;
@@ -672,6 +704,10 @@ nms_status tc_setup(Plan& p)
     t->mtiles = (2 * t->nch * t->ax.nyg + 127) / 128;
     t->ntiles = (2 * t->ax.nzg + 127) / 128;
     t->kcb = p.opt.kc_cells > 0 ? std::max(1, p.opt.kc_cells / tc_block_cells()) : 2;
+    // rays: one output tile per slot, so a chunk's few outputs are split
+    // over the CTAs and reduced; one item per SM keeps the splits (and the
+    // serial sums of the reduction) few
+    if (t->rays) t->items_per_sm = 1;
     if (p.opt.split_k > 0) t->items_per_sm = std::min(256, p.opt.split_k);
     t->objects = p.n_objects > 1 && p.opt.want_dilute;
     // One CTA per tile by default (the two-SM MMA writes fewer operand bytes
@@ -695,18 +731,50 @@ nms_status tc_setup(Plan& p)
     auto lin = [](int64_t a, int64_t nn, double lo, double hi) {
         return nn == 1 ? lo : lo + ((hi - lo) * (double)a) / (double)(nn - 1);
     };
+    // rays: the q_y axis holds lo + k2 i1 dq, the q_z axis i2 dq, so that
+    // node (i1, i2) is |q|_{k2 i1 + i2} (nodes past n0 are computed and not read)
+    const double dq = (t->rays && p.grid.n0 > 1) ? (p.grid.hi0 - p.grid.lo0) / (double)(p.grid.n0 - 1) : 0.0;
     for (int a = 0; a < t->ny; ++a) {
-        double v = lin(a, t->ny, p.grid.lo0, p.grid.hi0) / two_pi;
+        double v = (t->rays ? p.grid.lo0 + (double)k2 * a * dq : lin(a, t->ny, p.grid.lo0, p.grid.hi0)) / two_pi;
         float h = (float)v;
         qy[a] = make_float2(h, (float)(v - (double)h));
     }
     for (int b = 0; b < t->nz; ++b) {
-        double v = lin(b, t->nz, p.grid.lo1, p.grid.hi1) / two_pi;
+        double v = (t->rays ? (double)b * dq : lin(b, t->nz, p.grid.lo1, p.grid.hi1)) / two_pi;
         float h = (float)v;
         qz[b] = make_float2(h, (float)(v - (double)h));
     }
     nms_status st;
     if ((st = upload(&t->d_qy, qy)) || (st = upload(&t->d_qz, qz))) return st;
+    t->n_slots = p.n_rot;
+    if (t->rays) {
+        // theta_j = 2 pi j / n1; with n1 even the ray theta + pi is the
+        // conjugate of the ray theta (q negated), so only j < n1 / 2 is computed
+        const int n1 = p.grid.n1;
+        t->ray_mirror = (n1 % 2 == 0 && mirror_ok) ? 1 : 0;
+        t->n_rays = t->ray_mirror ? n1 / 2 : n1;
+        if ((int64_t)p.n_rot * t->n_rays > (int64_t)INT32_MAX / 2) {
+            set_error("tensor-core path on a POLAR grid: n_rot x n_theta too large");
+            return NMS_ERR_UNSUPPORTED;
+        }
+        t->n_slots = p.n_rot * t->n_rays;
+        std::vector<double2> sc(t->n_rays);
+        std::vector<float4> sct(t->n_rays);
+        for (int j = 0; j < t->n_rays; ++j) {
+            const double th = two_pi * (double)j / (double)n1;
+            sc[j] = make_double2(sin(th), cos(th));
+            const float sh = (float)sc[j].x, ch = (float)sc[j].y;
+            sct[j] = make_float4(sh, (float)(sc[j].x - (double)sh), ch, (float)(sc[j].y - (double)ch));
+        }
+        if ((st = upload(&t->d_ray_sc, sc)) || (st = upload(&t->d_ray_sc_tf, sct))) return st;
+        // the cells rotated once per rotation (positions and weights, up to
+        // 1 GB), so that each ray only projects them
+        const int64_t rbytes = (int64_t)p.n_rot * p.n_cells * 16 * (1 + p.n_sets);
+        if (p.n_rot <= 65535 && rbytes <= (1ll << 30)) {
+            NMS_CUDA_TRY(plan_malloc(&t->d_rpos, (size_t)p.n_rot * p.n_cells * sizeof(float4)));
+            NMS_CUDA_TRY(plan_malloc(&t->d_rw, (size_t)p.n_sets * p.n_rot * p.n_cells * sizeof(float4)));
+        }
+    }
     t->W[0] = pow2_ceil(p.h_wmax[0]);
     t->W[1] = t->W[2] = t->W[3] = pow2_ceil(p.h_wmax[1]);
     // the GEMM applies W_c / 2^24 in FP32 (a power of two: exact while normal)
@@ -728,7 +796,7 @@ nms_status tc_setup(Plan& p)
     // rotations prepared per batch: stacked positions and weights (every
     // weight set, [set][rotation][cell]) up to 2 GB
     const int64_t per_rot = n * 16 * (1 + t->nch / 4);
-    t->R_b = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)p.n_rot, 64, (2ll << 30) / std::max<int64_t>(1, per_rot)}));
+    t->R_b = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)t->n_slots, 64, (2ll << 30) / std::max<int64_t>(1, per_rot)}));
     t->wstride = (int64_t)t->R_b * n;
     NMS_CUDA_TRY(plan_malloc(&t->d_cpos_b, (size_t)t->R_b * n * sizeof(float4)));
     NMS_CUDA_TRY(plan_malloc(&t->d_cw_b, (size_t)(t->nch / 4) * t->wstride * sizeof(float4)));
@@ -763,11 +831,11 @@ nms_status tc_setup(Plan& p)
     p.tab_bytes = (size_t)t->tab_kb * per_kb;
     NMS_CUDA_TRY(plan_malloc(&p.d_tab, p.tab_bytes));
     // schedules: a full rotation batch and the remainder
-    if (p.opt.autotune) {
+    if (p.opt.autotune && !t->rays) {   // the tuner's error check reads the Cartesian pixel layout
         if ((st = tc_autotune(p, *t))) return st;
     }
     if ((st = build_schedule(p, *t, plan_summands(p, *t, t->R_b), t->R_b, out_cap, t->full))) return st;
-    const int rem = p.n_rot % t->R_b;
+    const int rem = t->n_slots % t->R_b;
     if (rem) {
         if ((st = build_schedule(p, *t, plan_summands(p, *t, rem), rem, out_cap, t->last))) return st;
     }
@@ -787,7 +855,8 @@ void tc_release(Plan& p)
     TcState* t = (TcState*)p.tc_state;
     if (!t) return;
     void* b[] = {t->d_qy,  t->d_qz,  t->d_cpos_b, t->d_cw_b, t->d_Fb, t->d_Ftot_b,
-                 t->d_cyz, t->d_eyz, t->d_dscr,   t->d_rot,  t->d_cen, t->d_P};
+                 t->d_cyz, t->d_eyz, t->d_dscr,   t->d_rot,  t->d_cen, t->d_P, t->d_ray_sc,
+                 t->d_ray_sc_tf, t->d_rpos, t->d_rw};
     for (void* x : b)
         if (x) plan_free(x, p.stream);
     free_schedule(t->full, p.stream);
@@ -808,12 +877,26 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
     for (int c = 0; c < 4; ++c) scale[c] = t.W[c] / ((double)sc * (double)sc);
     const uint64_t limit = p.opt.max_spin > 0 ? (uint64_t)p.opt.max_spin * 1000ull : 4000000000ull;
     const int64_t lo_off = fb_plane(t, t.out_cap);   // float2 from the high to the low plane of F_b
-    for (int rb0 = 0; rb0 < p.n_rot; rb0 += t.R_b) {
-        const int nrl = std::min(t.R_b, p.n_rot - rb0);
+    if (t.rays && t.d_rpos) {
+        // every rotation's cells once (global positions), for the rays to project
+        p.timer.begin(ST_PREP);
+        NMS_CUDA_TRY(launch_prep_rot_batch(p, t.d_rot, 0, p.n_rot, true, t.d_rpos, t.d_rw,
+                                           (int64_t)p.n_rot * p.n_cells, s));
+        p.timer.end(ST_PREP, 1);
+    }
+    for (int rb0 = 0; rb0 < t.n_slots; rb0 += t.R_b) {
+        const int nrl = std::min(t.R_b, t.n_slots - rb0);
         const Schedule& S = nrl == t.R_b ? t.full : t.last;
         p.timer.begin(ST_PREP);
-        // the batch's rotations in one launch (rotation rb0 + rl into slot rl)
-        NMS_CUDA_TRY(launch_prep_rot_batch(p, t.d_rot, rb0, nrl, !t.objects, t.d_cpos_b, t.d_cw_b, t.wstride, s));
+        // the batch's slots in one launch (rotation, or rotation x ray, rb0 + rl into slot rl)
+        if (t.rays && t.d_rpos)
+            NMS_CUDA_TRY(launch_prep_ray_from_rot(p, t.d_rpos, t.d_rw, (int64_t)p.n_rot * p.n_cells, t.d_ray_sc_tf,
+                                                  t.n_rays, rb0, nrl, t.d_cpos_b, t.d_cw_b, t.wstride, s));
+        else if (t.rays)
+            NMS_CUDA_TRY(launch_prep_ray_batch(p, t.d_rot, t.d_ray_sc, t.n_rays, rb0, nrl, t.d_cpos_b, t.d_cw_b,
+                                               t.wstride, s));
+        else
+            NMS_CUDA_TRY(launch_prep_rot_batch(p, t.d_rot, rb0, nrl, !t.objects, t.d_cpos_b, t.d_cw_b, t.wstride, s));
         p.timer.end(ST_PREP, 1);
         if (t.objects) NMS_CUDA_TRY(cudaMemsetAsync(t.d_Ftot_b, 0, (size_t)nrl * nS * F4 * sizeof(double), s));
         for (const OutBatch& ob : S.batches) {
@@ -856,6 +939,13 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
                                                            t.d_Ftot_b + (size_t)st * F4, (int64_t)nS * F4, t.d_dscr,
                                                            p.d_err, limit, s));
                     nl += std::min(dilute_slices(V.stored_pixels()), ob.n_out) > 1 && t.d_dscr ? 2 : 1;
+                } else if (t.rays) {
+                    // each ray's amplitudes into its POLAR pixels (and the mirror rays)
+                    NMS_CUDA_TRY(launch_ray_gacc(V, ob.n_out, rb0 + ob.out0, t.n_rays, t.ray_mirror, p.grid.n0,
+                                                 p.grid.n1, t.nz, p.n_rot - 1, p.d_Gtot + (size_t)st * 16 * np,
+                                                 p.d_Gdil ? p.d_Gdil + (size_t)st * 16 * np : nullptr,
+                                                 p.d_F + (size_t)st * F4, s));
+                    ++nl;
                 } else {
                     NMS_CUDA_TRY(launch_gacc_batch(V, ob.n_out, p.d_Gtot + (size_t)st * 16 * np, s));
                     ++nl;
@@ -863,7 +953,7 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
                         NMS_CUDA_TRY(launch_gacc_batch(V, ob.n_out, p.d_Gdil + (size_t)st * 16 * np, s));
                         ++nl;
                     }
-                    if (rb0 + nrl == p.n_rot && &ob == &S.batches.back())
+                    if (rb0 + nrl == t.n_slots && &ob == &S.batches.back())
                         NMS_CUDA_TRY(launch_tf_to_f64(V, ob.n_out - 1, p.d_F + (size_t)st * F4, s));
                 }
             }
@@ -874,7 +964,7 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
             for (int st = 0; st < nS; ++st) {
                 const double* Ts = t.d_Ftot_b + (size_t)st * F4;
                 NMS_CUDA_TRY(launch_gacc_totals(Ts, nrl, (int64_t)nS * F4, np, p.d_Gtot + (size_t)st * 16 * np, s));
-                if (rb0 + nrl == p.n_rot)
+                if (rb0 + nrl == t.n_slots)
                     NMS_CUDA_TRY(cudaMemcpyAsync(p.d_Ftot + (size_t)st * F4, Ts + (size_t)(nrl - 1) * nS * F4,
                                                  F4 * sizeof(double), cudaMemcpyDeviceToDevice, s));
             }

@@ -1,0 +1,149 @@
+"""POLAR grids on the tensor path (one GEMM per ray) against the FP64 oracle.
+
+On the ray at angle theta the pixel q = |q| (sin theta, cos theta) has the
+phase |q| u, u = Y sin theta + Z cos theta (paper, Eq. qdef and Sec.
+"Summation approach"); |q|_i = lo + i dq splits as lo + 64 i1 dq + i2 dq,
+so each ray is the Cartesian GEMM with both coordinates equal to u.  With an
+even number of angles the ray theta + pi is the conjugate of the ray theta.
+Covered: even and odd angle counts (mirrored rays or not), |q| counts below,
+at and above 64 (one or several i1 nodes, ragged), a single |q| node,
+rotation averages, many slots in several batches with a remainder batch, a
+small table workspace (many chunks), several objects summed as one (their
+centres applied), weight sets (loop mode), and the responses and azimuthal
+average of the polar image.
+"""
+import numpy as np
+import pytest
+
+from oracle import sans as S
+from paper_2601_18444_gb300 import inputs as I
+from paper_2601_18444_gb300 import nms
+from parity_util import AMP_TOL, IQ_TOL, amp_error, iq_rel_error, resp_tol, weight_sums
+
+pytestmark = pytest.mark.gpu
+TC = nms.PREC_TC_F16X3
+
+
+def run(field, grid_kw, rot=None, **optkw):
+    g = nms.make_grid(**grid_kw)
+    opt = nms.nms_options_default(precision=TC, **optkw)
+    plan = nms.plan_from_field(field, g, opt, rot=rot)
+    nms.nms_amplitudes(plan)
+    assert nms.nms_plan_info(plan)["precision"] == TC
+    return plan
+
+
+def og(grid_kw):
+    kw = dict(grid_kw)
+    kind = kw.pop("kind")
+    return S.q_grid(kind, **kw)
+
+
+POLAR_GRIDS = [
+    dict(n0=33, n1=48, lo0=0.0, hi0=1.2),      # even angles (mirrored rays), one i1 node
+    dict(n0=100, n1=37, lo0=0.0, hi0=1.5),     # odd angles (every ray computed), ragged second i1 node
+    dict(n0=64, n1=10, lo0=0.1, hi0=2.0),      # exactly one full i1 node
+    dict(n0=130, n1=20, lo0=0.05, hi0=2.5),    # three i1 nodes, the last ragged
+    dict(n0=1, n1=8, lo0=0.7, hi0=0.7),        # a single |q| node
+]
+
+
+@pytest.mark.parametrize("gi", range(len(POLAR_GRIDS)))
+def test_polar_tc_amplitudes(gi):
+    kw = dict(kind="polar", **POLAR_GRIDS[gi])
+    f = I.small_random_field(4000, seed=80 + gi, extent=12.0)
+    plan = run(f, kw)
+    g = og(kw)
+    F_ref = S.amplitudes(f, np.eye(3), g[0], g[1])
+    err = amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f))
+    assert np.all(err <= AMP_TOL), err
+
+
+def test_polar_tc_responses_and_average():
+    f = I.linear_vortex_sphere(10.0, 1.0, M0=1.0, N0=0.7)
+    kw = dict(kind="polar", n0=33, n1=48, lo0=0.0, hi0=1.2)
+    plan = run(f, kw)
+    g = og(kw)
+    F_ref = S.amplitudes(f, np.eye(3), g[0], g[1])
+    assert np.all(amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f)) <= AMP_TOL)
+    ref = S.responses(F_ref, g[2], g[3])
+    for name in ("N", "M", "CHI", "NM", "SANSPOL_P", "UNPOL"):
+        img = nms.nms_response(plan, name)
+        assert np.max(np.abs(img - ref[name])) <= resp_tol(f), name
+        Ig, cg, qg = nms.nms_azimuthal_average(plan, img, nbins=33)
+        Ir = S.azimuthal_average_polar(ref[name], 33, 48)
+        assert np.all(cg == 48)
+        if name != "CHI":
+            assert iq_rel_error(Ig, Ir) <= IQ_TOL, name
+        else:
+            assert np.max(np.abs(Ig)) <= resp_tol(f)
+
+
+def test_polar_tc_rotations_many_slots_small_workspace():
+    # 3 rotations x 100 mirrored rays = 300 slots: several batches of at most
+    # 64 slots and a remainder batch; an 8 MB table workspace cuts each batch
+    # into many chunks
+    f = I.small_random_field(3000, seed=91, extent=10.0)
+    kw = dict(kind="polar", n0=70, n1=200, lo0=0.0, hi0=1.4)
+    Rs = I.random_rotations(3, seed=92)
+    plan = run(f, kw, rot=Rs, workspace_bytes=8 << 20)
+    g = og(kw)
+    acc = None
+    for R in Rs:
+        r = S.responses(S.amplitudes(f, R, g[0], g[1]), g[2], g[3])
+        acc = r if acc is None else {k: acc[k] + r[k] for k in acc}
+    for name in ("UNPOL", "SF", "M", "CHI"):
+        assert np.max(np.abs(nms.nms_response(plan, name) - acc[name] / len(Rs))) <= resp_tol(f, rotations=Rs), name
+    F_ref = S.amplitudes(f, Rs[-1], g[0], g[1])
+    assert np.all(amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f, Rs[-1])) <= AMP_TOL)
+
+
+def test_polar_tc_objects_summed_as_one():
+    # several objects with centres and want_dilute = 0: one sum over the cells
+    # at their global positions (the default path on a POLAR grid)
+    rng = np.random.default_rng(95)
+    sizes = rng.integers(50, 400, size=12)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(off[-1])
+    f = I.Field(rng.uniform(-4.0, 4.0, size=(n, 3)), rng.uniform(0.5, 1.5, n), rng.normal(size=n),
+                rng.normal(size=(n, 3)), offsets=off, centers=rng.uniform(-30.0, 30.0, size=(len(sizes), 3)),
+                name="objects")
+    kw = dict(kind="polar", n0=50, n1=64, lo0=0.0, hi0=1.0)
+    plan = nms.plan_from_field(f, nms.make_grid(**kw), nms.nms_options_default())
+    nms.nms_amplitudes(plan)
+    assert nms.nms_plan_info(plan)["precision"] == TC
+    g = og(kw)
+    F_ref = S.amplitudes(f, np.eye(3), g[0], g[1])
+    assert np.all(amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f)) <= AMP_TOL)
+
+
+def test_polar_tc_weight_sets():
+    # two weight sets (loop mode) on one ray GEMM: each set against the oracle
+    f = I.box_field(16, 14, 12, a=2.0, n_modes=6, n_pores=3, seed=97)
+    nuc2, mag2 = I.field_sweep(f, [0.0, 1.5])
+    kw = dict(kind="polar", n0=40, n1=30, lo0=0.0, hi0=1.1)
+    g = nms.make_grid(**kw)
+    opt = nms.nms_options_default(precision=TC, n_sets=2)
+    plan = nms.nms_plan_create(f.pos, f.vol, nuc2, mag2, grid=g, opt=opt)
+    nms.nms_amplitudes(plan)
+    go = og(kw)
+    for st in range(2):
+        fs = I.Field(f.pos, f.vol, nuc2[st], mag2[st], name="set")
+        nms.nms_select_set(plan, st)
+        F_ref = S.amplitudes(fs, np.eye(3), go[0], go[1])
+        assert np.all(amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(fs)) <= AMP_TOL), st
+
+
+def test_polar_tc_refuses_per_object_parts_and_bins():
+    f = I.sphere_ensemble(n_spheres=3, median=2.0, sigma=0.1, clip=(1.5, 2.5), a=1.0, cube=20.0, seed=1)
+    g = nms.make_grid("polar", 4, 4, 0, 1)
+    with pytest.raises(nms.NmsError) as e:
+        nms.plan_from_field(f, g, nms.nms_options_default(precision=TC, want_dilute=1))
+    assert e.value.status == 4
+    # with per-object parts wanted the default path on a POLAR grid is the direct sum
+    plan = nms.plan_from_field(f, g, nms.nms_options_default(want_dilute=1))
+    assert nms.nms_plan_info(plan)["precision"] == nms.PREC_FP32_DIRECT
+    plan = nms.plan_from_field(f, g, nms.nms_options_default(precision=TC))
+    with pytest.raises(nms.NmsError) as e:
+        nms.nms_plan_object_iq(plan, "UNPOL", np.linspace(0.0, 1.0, 5))
+    assert e.value.status == 4

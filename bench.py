@@ -259,6 +259,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--spheres", type=int, default=10000, help="ensemble: number of spheres")
     ap.add_argument("--items-per-sm", type=int, default=0, help="tensor path: GEMM work items per SM (0: library)")
+    ap.add_argument("--objects", action="store_true",
+                    help="paper: the 800 particles as objects (dilute, total and interference parts)")
     ap.add_argument("--single-sum", action="store_true",
                     help="ensemble: the same cells as one sum (centres applied, no per-object amplitudes)")
     ap.add_argument("--sets", type=int, default=1,
@@ -729,15 +731,21 @@ def run_surrogate(args, dev):
     return 0
 
 
-def lattice_copies(particle, n_copies, spacing=45.0):
+def lattice_copies(particle, n_copies, spacing=45.0, objects=False):
     """n_copies of a particle on the simple-cubic sites (spacing in nm)
-    nearest the origin, as one field (one sum over all cells)."""
+    nearest the origin, as one field (one sum over all cells), or with
+    objects=True as n_copies objects (local positions, the sites as centres)."""
     from paper_2601_18444_gb300 import inputs as I
     side = int(np.ceil(n_copies ** (1.0 / 3.0))) + 2
     ax = (np.arange(side) - (side - 1) / 2.0) * spacing
     sites = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), axis=-1).reshape(-1, 3)
     sites = sites[np.argsort(np.linalg.norm(sites, axis=1), kind="stable")[:n_copies]]
     n = particle.n
+    if objects:
+        return I.Field(np.tile(particle.pos, (n_copies, 1)), np.tile(particle.vol, n_copies),
+                       np.tile(particle.nuc, n_copies), np.tile(particle.mag, (n_copies, 1)),
+                       offsets=np.arange(n_copies + 1, dtype=np.int64) * n, centers=sites,
+                       name=f"{particle.name}_x{n_copies}_objects")
     pos = (particle.pos[None, :, :] + sites[:, None, :]).reshape(-1, 3)
     return I.Field(pos, np.tile(particle.vol, n_copies), np.tile(particle.nuc, n_copies),
                    np.tile(particle.mag, (n_copies, 1)), name=f"{particle.name}_x{n_copies}")
@@ -827,7 +835,7 @@ def run_paper_shape(args, dev):
     from paper_2601_18444_gb300 import inputs as I
     from paper_2601_18444_gb300 import nms
     particle = I.linear_vortex_sphere(20.0, 2.0, normalised=True)
-    f = lattice_copies(particle, 800)
+    f = lattice_copies(particle, 800, objects=args.objects)
     g = nms.make_grid("polar", 1000, 1000, 0.0, 1.5)
     stream = torch.cuda.current_stream()
     prec = {"auto": nms.PREC_AUTO, "tc": nms.PREC_TC_F16X3, "direct": nms.PREC_FP32_DIRECT,
@@ -835,7 +843,9 @@ def run_paper_shape(args, dev):
     r = np.linspace(0.0, 400.0, 200)
 
     def make(pr):
-        plan = nms.plan_from_field(f, g, nms.nms_options_default(timing=1, precision=pr), stream=stream.cuda_stream)
+        plan = nms.plan_from_field(f, g, nms.nms_options_default(timing=1, precision=pr,
+                                                                 want_dilute=1 if args.objects else 0),
+                                   stream=stream.cuda_stream)
         img_u = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
         img_s = torch.empty(plan.npix, dtype=torch.float64, device="cuda")
 
@@ -843,6 +853,9 @@ def run_paper_shape(args, dev):
             nms.nms_amplitudes(plan)
             nms.nms_response(plan, "UNPOL", out=img_u)
             nms.nms_response(plan, "SF", out=img_s)
+            if args.objects:   # the interparticle split of the unpolarized image
+                nms.nms_response(plan, "UNPOL", nms.PART_DILUTE, out=img_s)
+                nms.nms_response(plan, "UNPOL", nms.PART_INTERFERENCE, out=img_s)
             for img in (img_u, img_s):
                 Iq, c, qm = nms.nms_azimuthal_average(plan, img, nbins=1000)
                 nms.nms_correlation(qm, Iq, r, stream=stream.cuda_stream)
@@ -923,7 +936,9 @@ def run_paper_shape(args, dev):
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f16x3->f32(two-float)" if path == nms.PREC_TC_F16X3 else "f32(two-float)", "data": "synthetic",
             "config": {"workload": "800 x linear-vortex sphere D=40nm a=2nm (3.34e6 cells) on a 45nm simple-cubic "
-                                   "lattice; polar grid 1000 q in [0,1.5] nm^-1 x 1000 theta; UNPOL + SF, "
+                                   "lattice" + (" as 800 objects (dilute, total and interference parts)"
+                                                if args.objects else "") +
+                                   "; polar grid 1000 q in [0,1.5] nm^-1 x 1000 theta; UNPOL + SF, "
                                    "azimuthal averages, c(r) on 200 r",
                        "stage_ms_per_step": {k: v[0] / steps for k, v in st.items() if v[1]},
                        "paper_context": "about 60 s on an RTX 3090 for 3.38e6 cells on a 1000x1000 (q, theta) grid "

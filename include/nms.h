@@ -72,8 +72,8 @@ typedef struct {
 
 /* How the Fourier sums are evaluated. */
 typedef enum {
-    NMS_PREC_AUTO = 0,          /* TC_F16X3 on CARTESIAN grids and on POLAR grids
-                                   without per-object parts, FP32_DIRECT otherwise */
+    NMS_PREC_AUTO = 0,          /* TC_F16X3 on CARTESIAN and POLAR grids,
+                                   FP32_DIRECT on LIST grids                      */
     NMS_PREC_TC_F16X3 = 1,      /* split-FP16 (hi/lo, 3 products) tcgen05 GEMM, FP32
                                    TMEM accumulation promoted to two-float every
                                    kc_cells cells; CARTESIAN grids, and POLAR grids
@@ -81,7 +81,7 @@ typedef enum {
                                    cell's projection on the ray splits over two
                                    axes |q| = lo + 64 i1 dq + i2 dq; the ray at
                                    theta + pi is the conjugate; no per-object
-                                   parts, no per-object averages).  It takes
+                                   averages).  It takes
                                    the place of TF32x3 (same ~2^-22 per-product
                                    error, but TF32 runs at half the FP16 rate on
                                    tcgen05), BF16x3 (2^-17: misses 1e-6) and
@@ -161,8 +161,7 @@ nms_status nms_options_default(nms_options* opt);
  *   cuda_stream     cudaStream_t every launch of this plan goes to (NULL: the
  *                   legacy default stream).
  * Errors: INVALID_ARG (sizes, offsets not monotone, TC precision on a LIST
- * grid), UNSUPPORTED (TC precision on a POLAR grid with want_dilute and
- * several objects), OUT_OF_MEMORY, CUDA. */
+ * grid), OUT_OF_MEMORY, CUDA. */
 nms_status nms_plan_create(nms_plan_t* out, int64_t n_cells, const double* pos,
                            const double* cell_vol, const double* nuc, const double* mag,
                            int64_t n_objects, const int64_t* object_offsets,

@@ -199,13 +199,13 @@ cudaError_t launch_prep_ray_from_rot(const Plan& p, const float4* rpos, const fl
 }
 
 cudaError_t launch_prep_ray_batch(const Plan& p, const double* d_rot, const double2* ray_sc, int n_rays, int slot0,
-                                  int nrl, float4* cpos, float4* cw, int64_t wstride, cudaStream_t s)
+                                  int nrl, bool global, float4* cpos, float4* cw, int64_t wstride, cudaStream_t s)
 {
     const int64_t n = p.n_cells;
     if (n <= 0 || nrl <= 0) return cudaSuccess;
     k_prep_ray_batch<<<dim3((unsigned)((n + 255) / 256), (unsigned)nrl), 256, 0, s>>>(
-        n, p.n_sets, wstride, p.d_pos, p.d_vol, p.d_nuc, p.d_mag, p.d_cen_cell, d_rot, ray_sc, n_rays, slot0, cpos,
-        cw);
+        n, p.n_sets, wstride, p.d_pos, p.d_vol, p.d_nuc, p.d_mag, global ? p.d_cen_cell : nullptr, d_rot, ray_sc,
+        n_rays, slot0, cpos, cw);
     return cudaGetLastError();
 }
 
@@ -228,6 +228,33 @@ __global__ void k_centres(int n_out, const int32_t* __restrict__ out_obj, const 
     const double* r = rot + 9 * (int64_t)(rot0 + out_rot[o]);
     const double* c = cen + 3 * (int64_t)out_obj[o];
     cyz[o] = split_pos(r[3] * c[0] + r[4] * c[1] + r[5] * c[2], r[6] * c[0] + r[7] * c[1] + r[8] * c[2]);
+}
+
+// Rays: the projection v = Cy sin theta + Cz cos theta of each output's
+// rotated centre on its ray (slot slot0 + out_rot[o]: rotation slot / n_rays,
+// ray slot mod n_rays), as two-float in both coordinates, so that the shift
+// factor e^{-i |q| v} separates over the ray GEMM's two axes like
+// e^{-i (q_y cy + q_z cz)} on a Cartesian detector.
+__global__ void k_ray_centres(int n_out, const int32_t* __restrict__ out_obj, const int32_t* __restrict__ out_rot,
+                              int slot0, const double* __restrict__ rot, const double2* __restrict__ ray_sc,
+                              int n_rays, const double* __restrict__ cen, float4* __restrict__ cyz)
+{
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n_out) return;
+    const int slot = slot0 + out_rot[o];
+    const double* r = rot + 9 * (int64_t)(slot / n_rays);
+    const double2 sc = ray_sc[slot % n_rays];
+    const double* c = cen + 3 * (int64_t)out_obj[o];
+    const double v = sc.x * (r[3] * c[0] + r[4] * c[1] + r[5] * c[2]) + sc.y * (r[6] * c[0] + r[7] * c[1] + r[8] * c[2]);
+    cyz[o] = split_pos(v, v);
+}
+
+cudaError_t launch_ray_centres(int n_out, const int32_t* out_obj, const int32_t* out_rot, int slot0, const double* rot,
+                               const double2* ray_sc, int n_rays, const double* cen, float4* cyz, cudaStream_t s)
+{
+    if (n_out <= 0) return cudaSuccess;
+    k_ray_centres<<<(n_out + 127) / 128, 128, 0, s>>>(n_out, out_obj, out_rot, slot0, rot, ray_sc, n_rays, cen, cyz);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_centres(int n_out, const int32_t* out_obj, const int32_t* out_rot, int rot0, const double* rot,
@@ -426,6 +453,77 @@ cudaError_t launch_ray_gacc(const FbView& V, int n_out, int slot0, int n_rays, i
     const int64_t nt = (int64_t)n_rays * n0;
     k_ray_gacc<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(V, n_out, slot0, n_rays, mirror, n0, n1, k2, last_rot, G,
                                                             Gd, reinterpret_cast<double2*>(F));
+    return cudaGetLastError();
+}
+
+// Rays with objects: after the dilute pass of a batch of nrl slots, slot
+// rl holds the dilute products Gdil_b[rl] [16][npr] and the shifted total
+// Ftot_b[rl] [4][npr] (complex) on its ray grid, node i = k2 i1 + i2 at
+// ray-grid pixel i.  One thread per (ray, |q| node) adds, for every slot of
+// the batch on that ray (rotation after rotation), the dilute products into
+// G_dil and F_tot F_tot^dagger into G_tot at the POLAR pixel i n1 + ray (and
+// the conjugates at the ray theta + pi when mirror), and writes F_tot of
+// rotation last_rot into Ftot (FP64).
+__global__ void k_ray_totals(int nrl, int slot0, int n_rays, int mirror, int n0, int n1, int64_t npr,
+                             const double2* __restrict__ Ftot_b, int64_t fstride2, const double* __restrict__ Gdil_b,
+                             int64_t gstride, int last_rot, double* __restrict__ Gtot, double* __restrict__ Gdil,
+                             double2* __restrict__ Ftot)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n_rays * n0) return;
+    const int ray = (int)(t % n_rays), i = (int)(t / n_rays);
+    const int64_t npix = (int64_t)n0 * n1;
+    const int64_t p = (int64_t)i * n1 + ray;
+    const int64_t pm = p + n1 / 2;
+    double gt[16], gd[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) { gt[k] = 0.0; gd[k] = 0.0; }
+    bool any = false;
+    for (int rl = (ray - slot0 % n_rays + n_rays) % n_rays; rl < nrl; rl += n_rays) {
+        double2 f[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) f[c] = Ftot_b[(int64_t)rl * fstride2 + (int64_t)c * npr + i];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) gt[c] += f[c].x * f[c].x + f[c].y * f[c].y;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int d = c + 1; d < 4; ++d) {
+                const int k = pair_idx(c, d);
+                gt[4 + 2 * k] += f[c].x * f[d].x + f[c].y * f[d].y;
+                gt[5 + 2 * k] += f[c].y * f[d].x - f[c].x * f[d].y;
+            }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) gd[k] += Gdil_b[(int64_t)rl * gstride + (int64_t)k * npr + i];
+        if ((slot0 + rl) / n_rays == last_rot)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                Ftot[(int64_t)c * npix + p] = f[c];
+                if (mirror) Ftot[(int64_t)c * npix + pm] = make_double2(f[c].x, -f[c].y);
+            }
+        any = true;
+    }
+    if (!any) return;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        Gtot[(int64_t)k * npix + p] += gt[k];
+        Gdil[(int64_t)k * npix + p] += gd[k];
+        if (mirror) {
+            Gtot[(int64_t)k * npix + pm] += g_conj_sign(k) * gt[k];
+            Gdil[(int64_t)k * npix + pm] += g_conj_sign(k) * gd[k];
+        }
+    }
+}
+
+cudaError_t launch_ray_totals(int nrl, int slot0, int n_rays, int mirror, int n0, int n1, int64_t npr,
+                              const double* Ftot_b, int64_t fstride, const double* Gdil_b, int64_t gstride,
+                              int last_rot, double* Gtot, double* Gdil, double* Ftot, cudaStream_t s)
+{
+    if (nrl <= 0) return cudaSuccess;
+    const int64_t nt = (int64_t)n_rays * n0;
+    k_ray_totals<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(
+        nrl, slot0, n_rays, mirror, n0, n1, npr, reinterpret_cast<const double2*>(Ftot_b), fstride / 2, Gdil_b,
+        gstride, last_rot, Gtot, Gdil, reinterpret_cast<double2*>(Ftot));
     return cudaGetLastError();
 }
 

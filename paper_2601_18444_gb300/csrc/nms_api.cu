@@ -396,13 +396,9 @@ nms_status nms_plan_create(nms_plan_t* out, int64_t n_cells, const double* pos, 
     if (prec < NMS_PREC_AUTO || prec > NMS_PREC_FP32_NAIVE) return bail(fail(NMS_ERR_INVALID_ARG, "bad precision"));
     if (prec == NMS_PREC_TC_F16X3 && grid->kind == NMS_QGRID_LIST)
         return bail(fail(NMS_ERR_INVALID_ARG, "the tensor-core path needs a CARTESIAN or POLAR grid"));
-    // auto: the tensor path on CARTESIAN grids, and on POLAR grids (one GEMM
-    // per ray) unless per-object parts are wanted; the direct sum otherwise
-    if (prec == NMS_PREC_AUTO)
-        prec = (grid->kind == NMS_QGRID_CARTESIAN ||
-                (grid->kind == NMS_QGRID_POLAR && !(n_objects > 1 && p->opt.want_dilute)))
-                   ? NMS_PREC_TC_F16X3
-                   : NMS_PREC_FP32_DIRECT;
+    // auto: the tensor path on CARTESIAN and POLAR grids (there one GEMM per
+    // ray), the direct sum on point lists
+    if (prec == NMS_PREC_AUTO) prec = grid->kind == NMS_QGRID_LIST ? NMS_PREC_FP32_DIRECT : NMS_PREC_TC_F16X3;
     p->path = prec;
     if (p->n_sets > 4096 || (prec == NMS_PREC_TC_F16X3 && p->n_sets > 32))
         return bail(fail(NMS_ERR_INVALID_ARG, "n_sets above 32 (tensor path) or 4096"));

@@ -63,7 +63,12 @@ cudaError_t launch_dilute_shift_batch(const FbView& V, int n_out, const float2* 
                                       uint64_t limit_ns, cudaStream_t s);
 int dilute_slices(int64_t stored_pixels);
 cudaError_t launch_prep_ray_batch(const Plan& p, const double* d_rot, const double2* ray_sc, int n_rays, int slot0,
-                                  int nrl, float4* cpos, float4* cw, int64_t wstride, cudaStream_t s);
+                                  int nrl, bool global, float4* cpos, float4* cw, int64_t wstride, cudaStream_t s);
+cudaError_t launch_ray_centres(int n_out, const int32_t* out_obj, const int32_t* out_rot, int slot0, const double* rot,
+                               const double2* ray_sc, int n_rays, const double* cen, float4* cyz, cudaStream_t s);
+cudaError_t launch_ray_totals(int nrl, int slot0, int n_rays, int mirror, int n0, int n1, int64_t npr,
+                              const double* Ftot_b, int64_t fstride, const double* Gdil_b, int64_t gstride,
+                              int last_rot, double* Gtot, double* Gdil, double* Ftot, cudaStream_t s);
 cudaError_t launch_ray_gacc(const FbView& V, int n_out, int slot0, int n_rays, int mirror, int n0, int n1, int k2,
                             int last_rot, double* G, double* Gd, double* F, cudaStream_t s);
 cudaError_t launch_prep_ray_from_rot(const Plan& p, const float4* rpos, const float4* rw, int64_t rwstride,
@@ -109,6 +114,7 @@ struct Schedule {
     int32_t* d_out_obj = nullptr;
     int32_t* d_out_rot = nullptr;
     uint8_t* d_out_two = nullptr;   // per output: 1 = assembled from several pieces (two-float F_b)
+    std::vector<int32_t> h_out_rot; // per output: its slot in the batch (host copy)
     int64_t max_items = 0;
     int max_batch_out = 0;
 };
@@ -141,6 +147,7 @@ struct TcState {
     float4* d_ray_sc_tf = nullptr;   // the same as two-float (sin hi, lo, cos hi, lo)
     float4* d_rpos = nullptr;    // rays: rotated (Y, Z) two-float [n_rot][n], or null (FP64 per slot)
     float4* d_rw = nullptr;      // rays: rotated weights [set][n_rot][n]
+    double* d_Gdil_b = nullptr;  // rays with objects: dilute products per slot [R_b][set][16][ny nz]
     int64_t tab_kb = 0;          // table capacity in k-blocks
     float4* d_cpos_b = nullptr;  // [R_b][n]
     float4* d_cw_b = nullptr;
@@ -398,6 +405,7 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
         S.batches.push_back(ob);
     }
     nms_status st;
+    S.h_out_rot = out_rot;
     if ((st = upload(&S.d_kb_cell0, kb_cell0)) || (st = upload(&S.d_kb_ncell, kb_ncell)) ||
         (st = upload(&S.d_units, unit_item0)) ||
         (st = upload(&S.d_out_obj, out_obj)) || (st = upload(&S.d_out_rot, out_rot)) ||
@@ -664,10 +672,6 @@ nms_status tc_setup(Plan& p)
         set_error("tensor-core path needs a CARTESIAN or POLAR grid");
         return NMS_ERR_INVALID_ARG;
     }
-    if (p.grid.kind == NMS_QGRID_POLAR && p.n_objects > 1 && p.opt.want_dilute) {
-        set_error("tensor-core path on a POLAR grid: per-object parts (want_dilute) need the direct path");
-        return NMS_ERR_UNSUPPORTED;
-    }
     if (tc_item_bytes() != sizeof(HostItem) || tc_red_bytes() != sizeof(HostRed)) {
         set_error("internal: work-list record size mismatch");
         return NMS_ERR_UNSUPPORTED;
@@ -811,10 +815,15 @@ nms_status tc_setup(Plan& p)
     NMS_CUDA_TRY(plan_malloc(&t->d_cyz, (size_t)out_cap * sizeof(float4)));
     if (t->objects) NMS_CUDA_TRY(plan_malloc(&t->d_eyz, (size_t)out_cap * (t->ny + t->nz) * sizeof(float2)));
     // dilute pass: G_dil (16) and shifted-sum (4 complex) planes per extra output slice
+    // pixels of one output's image: the detector, or (rays) the ray's node grid
+    const int64_t npg = t->rays ? (int64_t)t->ny * t->nz : np;
     const int dsl = dilute_slices((int64_t)t->ny * (t->nz - t->ax.zs0));
-    if (t->objects && dsl > 1) NMS_CUDA_TRY(plan_malloc(&t->d_dscr, (size_t)(dsl - 1) * 24 * np * sizeof(double)));
+    if (t->objects && dsl > 1) NMS_CUDA_TRY(plan_malloc(&t->d_dscr, (size_t)(dsl - 1) * 24 * npg * sizeof(double)));
     // total amplitude per prepared rotation and weight set
-    if (t->objects) NMS_CUDA_TRY(plan_malloc(&t->d_Ftot_b, (size_t)t->R_b * t->nsets * 8 * np * sizeof(double)));
+    if (t->objects) NMS_CUDA_TRY(plan_malloc(&t->d_Ftot_b, (size_t)t->R_b * t->nsets * 8 * npg * sizeof(double)));
+    // rays: each slot's dilute products on its ray grid, scattered after the batch
+    if (t->objects && t->rays)
+        NMS_CUDA_TRY(plan_malloc(&t->d_Gdil_b, (size_t)t->R_b * t->nsets * 16 * npg * sizeof(double)));
     // phase tables: as many k-blocks as the workspace allows
     const int64_t per_kb = (int64_t)(t->mtiles + t->ntiles) * 2 * (int64_t)tc_block_bytes();
     const int64_t budget = p.opt.workspace_bytes > 0 ? p.opt.workspace_bytes
@@ -856,7 +865,7 @@ void tc_release(Plan& p)
     if (!t) return;
     void* b[] = {t->d_qy,  t->d_qz,  t->d_cpos_b, t->d_cw_b, t->d_Fb, t->d_Ftot_b,
                  t->d_cyz, t->d_eyz, t->d_dscr,   t->d_rot,  t->d_cen, t->d_P, t->d_ray_sc,
-                 t->d_ray_sc_tf, t->d_rpos, t->d_rw};
+                 t->d_ray_sc_tf, t->d_rpos, t->d_rw, t->d_Gdil_b};
     for (void* x : b)
         if (x) plan_free(x, p.stream);
     free_schedule(t->full, p.stream);
@@ -871,6 +880,8 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
     const int64_t np = p.npix;
     const int nS = t.nsets;
     const int64_t F4 = 8 * np;                   // doubles of one set's amplitudes [4][np] complex
+    const int64_t npg = t.rays ? (int64_t)t.ny * t.nz : np;   // pixels of one output's image
+    const int64_t F4g = 8 * npg;
     const float sc = tc_operand_scale();
     const float wscale[4] = {(float)(sc / t.W[0]), (float)(sc / t.W[1]), (float)(sc / t.W[2]), (float)(sc / t.W[3])};
     double scale[4];
@@ -880,7 +891,7 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
     if (t.rays && t.d_rpos) {
         // every rotation's cells once (global positions), for the rays to project
         p.timer.begin(ST_PREP);
-        NMS_CUDA_TRY(launch_prep_rot_batch(p, t.d_rot, 0, p.n_rot, true, t.d_rpos, t.d_rw,
+        NMS_CUDA_TRY(launch_prep_rot_batch(p, t.d_rot, 0, p.n_rot, !t.objects, t.d_rpos, t.d_rw,
                                            (int64_t)p.n_rot * p.n_cells, s));
         p.timer.end(ST_PREP, 1);
     }
@@ -893,12 +904,13 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
             NMS_CUDA_TRY(launch_prep_ray_from_rot(p, t.d_rpos, t.d_rw, (int64_t)p.n_rot * p.n_cells, t.d_ray_sc_tf,
                                                   t.n_rays, rb0, nrl, t.d_cpos_b, t.d_cw_b, t.wstride, s));
         else if (t.rays)
-            NMS_CUDA_TRY(launch_prep_ray_batch(p, t.d_rot, t.d_ray_sc, t.n_rays, rb0, nrl, t.d_cpos_b, t.d_cw_b,
-                                               t.wstride, s));
+            NMS_CUDA_TRY(launch_prep_ray_batch(p, t.d_rot, t.d_ray_sc, t.n_rays, rb0, nrl, !t.objects, t.d_cpos_b,
+                                               t.d_cw_b, t.wstride, s));
         else
             NMS_CUDA_TRY(launch_prep_rot_batch(p, t.d_rot, rb0, nrl, !t.objects, t.d_cpos_b, t.d_cw_b, t.wstride, s));
         p.timer.end(ST_PREP, 1);
-        if (t.objects) NMS_CUDA_TRY(cudaMemsetAsync(t.d_Ftot_b, 0, (size_t)nrl * nS * F4 * sizeof(double), s));
+        if (t.objects) NMS_CUDA_TRY(cudaMemsetAsync(t.d_Ftot_b, 0, (size_t)nrl * nS * F4g * sizeof(double), s));
+        if (t.d_Gdil_b) NMS_CUDA_TRY(cudaMemsetAsync(t.d_Gdil_b, 0, (size_t)nrl * nS * 16 * npg * sizeof(double), s));
         for (const OutBatch& ob : S.batches) {
             for (const Chunk& ch : ob.chunks) {
                 p.timer.begin(ST_TABLES);
@@ -926,14 +938,37 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
                 ++nl;
             }
             if (t.objects) {
-                NMS_CUDA_TRY(launch_centres(ob.n_out, S.d_out_obj + ob.out0, S.d_out_rot + ob.out0, rb0, t.d_rot, t.d_cen,
-                                            t.d_cyz, s));
+                if (t.rays)
+                    NMS_CUDA_TRY(launch_ray_centres(ob.n_out, S.d_out_obj + ob.out0, S.d_out_rot + ob.out0, rb0, t.d_rot,
+                                                    t.d_ray_sc, t.n_rays, t.d_cen, t.d_cyz, s));
+                else
+                    NMS_CUDA_TRY(launch_centres(ob.n_out, S.d_out_obj + ob.out0, S.d_out_rot + ob.out0, rb0, t.d_rot,
+                                                t.d_cen, t.d_cyz, s));
                 NMS_CUDA_TRY(launch_shift_factors(ob.n_out, t.d_cyz, t.d_qy, t.ny, t.d_qz, t.nz, t.d_eyz, s));
                 nl += 2;
             }
             for (int st = 0; st < nS; ++st) {
                 const FbView V = fb_view(t, t.d_Fb, lo_off, S.d_out_two + ob.out0, st);   // set st of the batch's outputs
-                if (t.objects) {
+                if (t.objects && t.rays) {
+                    // one dilute pass per slot: each ray's outputs have their own
+                    // pixels, accumulated on its node grid and scattered later
+                    for (int o = 0; o < ob.n_out;) {
+                        const int rl = S.h_out_rot[ob.out0 + o];
+                        int e = o + 1;
+                        while (e < ob.n_out && S.h_out_rot[ob.out0 + e] == rl) ++e;
+                        FbView Vs = V;
+                        Vs.hi += (int64_t)o * V.ostride2;
+                        Vs.lo += (int64_t)o * V.ostride2;
+                        Vs.two += o;
+                        NMS_CUDA_TRY(launch_dilute_shift_batch(Vs, e - o, t.d_eyz + (size_t)o * (t.ny + t.nz),
+                                                               S.d_out_rot + ob.out0 + o,
+                                                               t.d_Gdil_b + ((size_t)rl * nS + st) * 16 * npg,
+                                                               t.d_Ftot_b + (size_t)st * F4g, (int64_t)nS * F4g,
+                                                               t.d_dscr, p.d_err, limit, s));
+                        nl += std::min(dilute_slices(Vs.stored_pixels()), e - o) > 1 && t.d_dscr ? 2 : 1;
+                        o = e;
+                    }
+                } else if (t.objects) {
                     NMS_CUDA_TRY(launch_dilute_shift_batch(V, ob.n_out, t.d_eyz, S.d_out_rot + ob.out0,
                                                            p.d_Gdil + (size_t)st * 16 * np,
                                                            t.d_Ftot_b + (size_t)st * F4, (int64_t)nS * F4, t.d_dscr,
@@ -959,7 +994,17 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
             }
             p.timer.end(ST_GACC, nl);
         }
-        if (t.objects) {
+        if (t.objects && t.rays) {
+            // each slot's dilute products and total amplitude into the POLAR pixels
+            p.timer.begin(ST_GACC);
+            for (int st = 0; st < nS; ++st)
+                NMS_CUDA_TRY(launch_ray_totals(nrl, rb0, t.n_rays, t.ray_mirror, p.grid.n0, p.grid.n1, npg,
+                                               t.d_Ftot_b + (size_t)st * F4g, (int64_t)nS * F4g,
+                                               t.d_Gdil_b + (size_t)st * 16 * npg, (int64_t)nS * 16 * npg, p.n_rot - 1,
+                                               p.d_Gtot + (size_t)st * 16 * np, p.d_Gdil + (size_t)st * 16 * np,
+                                               p.d_Ftot + (size_t)st * F4, s));
+            p.timer.end(ST_GACC, nS);
+        } else if (t.objects) {
             p.timer.begin(ST_GACC);
             for (int st = 0; st < nS; ++st) {
                 const double* Ts = t.d_Ftot_b + (size_t)st * F4;

@@ -229,11 +229,6 @@ def test_errors_reported_on_bad_calls():
         nms.nms_plan_create(f.pos, grid=nms.make_grid("list", 3, qlist=np.zeros((3, 2))),
                             opt=nms.nms_options_default(precision=nms.PREC_TC_F16X3))
     assert e.value.status == 1
-    with pytest.raises(nms.NmsError) as e:      # per-object parts on a POLAR grid: the direct path
-        fo = I.sphere_ensemble(n_spheres=3, median=2.0, sigma=0.1, clip=(1.5, 2.5), a=1.0, cube=20.0, seed=1)
-        nms.plan_from_field(fo, nms.make_grid("polar", 4, 4, 0, 1),
-                            nms.nms_options_default(precision=nms.PREC_TC_F16X3, want_dilute=1))
-    assert e.value.status == 4
 
 
 def test_stage_timing_counts_launches():

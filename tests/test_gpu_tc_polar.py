@@ -9,8 +9,9 @@ Covered: even and odd angle counts (mirrored rays or not), |q| counts below,
 at and above 64 (one or several i1 nodes, ragged), a single |q| node,
 rotation averages, many slots in several batches with a remainder batch, a
 small table workspace (many chunks), several objects summed as one (their
-centres applied), weight sets (loop mode), and the responses and azimuthal
-average of the polar image.
+centres applied), the dilute, total and interference parts of objects,
+weight sets (loop mode), and the responses and azimuthal average of the
+polar image.
 """
 import numpy as np
 import pytest
@@ -134,16 +135,44 @@ def test_polar_tc_weight_sets():
         assert np.all(amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(fs)) <= AMP_TOL), st
 
 
-def test_polar_tc_refuses_per_object_parts_and_bins():
+@pytest.mark.parametrize("n1,ws", [(48, 0), (37, 0), (64, 4 << 20)])
+def test_polar_tc_objects_dilute_total_interference(n1, ws):
+    # per-object parts on the polar grid: each (rotation, ray) slot's objects
+    # go through the dilute pass on the ray's node grid, whose products and
+    # total amplitude are then scattered into the polar pixels; even and odd
+    # angle counts, two rotations, one run with a small table workspace (a
+    # large object cut into pieces across chunks)
+    rng = np.random.default_rng(70 + n1)
+    sizes = np.concatenate([[6000], rng.integers(1, 300, size=25)])
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(off[-1])
+    f = I.Field(rng.uniform(-5.0, 5.0, size=(n, 3)), rng.uniform(0.5, 1.5, n), rng.normal(size=n),
+                rng.normal(size=(n, 3)), offsets=off, centers=rng.uniform(-30.0, 30.0, size=(len(sizes), 3)),
+                name="mixed_objects")
+    kw = dict(kind="polar", n0=70, n1=n1, lo0=0.0, hi0=1.3)
+    Rs = I.random_rotations(2, seed=71)
+    plan = run(f, kw, rot=Rs, want_dilute=1, workspace_bytes=ws)
+    g = og(kw)
+    ids = ("N", "M", "SF", "CHI", "UNPOL")
+    acc = {k: [0, 0, 0] for k in ids}
+    for R in Rs:
+        parts = S.response_parts(f, R, g, ids=ids)
+        for k in ids:
+            for i in range(3):
+                acc[k][i] = acc[k][i] + parts[k][i] / len(Rs)
+    tol = 2 * resp_tol(f, rotations=Rs)
+    for k in ids:
+        for i, part in enumerate((nms.PART_TOTAL, nms.PART_DILUTE, nms.PART_INTERFERENCE)):
+            assert np.max(np.abs(nms.nms_response(plan, k, part) - acc[k][i])) <= tol, (k, part)
+    F_ref = S.amplitudes(f, Rs[-1], g[0], g[1])   # the total amplitude of the last orientation
+    assert np.all(amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f, Rs[-1])) <= AMP_TOL)
+
+
+def test_polar_tc_refuses_per_object_bins():
     f = I.sphere_ensemble(n_spheres=3, median=2.0, sigma=0.1, clip=(1.5, 2.5), a=1.0, cube=20.0, seed=1)
     g = nms.make_grid("polar", 4, 4, 0, 1)
-    with pytest.raises(nms.NmsError) as e:
-        nms.plan_from_field(f, g, nms.nms_options_default(precision=TC, want_dilute=1))
-    assert e.value.status == 4
-    # with per-object parts wanted the default path on a POLAR grid is the direct sum
     plan = nms.plan_from_field(f, g, nms.nms_options_default(want_dilute=1))
-    assert nms.nms_plan_info(plan)["precision"] == nms.PREC_FP32_DIRECT
-    plan = nms.plan_from_field(f, g, nms.nms_options_default(precision=TC))
+    assert nms.nms_plan_info(plan)["precision"] == TC
     with pytest.raises(nms.NmsError) as e:
         nms.nms_plan_object_iq(plan, "UNPOL", np.linspace(0.0, 1.0, 5))
     assert e.value.status == 4

@@ -100,10 +100,11 @@ typedef struct {
     double b_H;              /* magnetic scattering length b_H; 0 -> 1           */
     double P[3];             /* polarisation unit vector; all 0 -> e_z           */
     int32_t kc_cells;        /* tensor path: cells per FP32 TMEM chunk, rounded
-                                down to a multiple of 64 (at least 64); 0 -> 128.
+                                down to a multiple of 64 (at least 64); 0 -> 192.
                                 Larger chunks drain less often and run faster,
                                 but the error at fully coherent pixels grows
-                                about linearly with the chunk                  */
+                                about linearly with the chunk: at most 8.9e-7
+                                of sum |w| at 192, 5.2e-7 at 128, 1.1e-6 at 256 */
     int32_t split_k;         /* tensor path: work items per SM of a GEMM launch
                                 (how finely the cells of each output are split
                                 over CTAs); 0 -> 8, or the autotuned value      */

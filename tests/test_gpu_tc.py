@@ -74,7 +74,7 @@ def test_tc_ragged_shapes(ny, nz, n):
     assert np.all(err <= AMP_TOL), err
 
 
-@pytest.mark.parametrize("kc", [0, 64, 128])
+@pytest.mark.parametrize("kc", [0, 64, 128, 192])
 def test_tc_coherent_q0_pixel(kc):
     # all-positive constant weights, pixels at and near q = 0: the partial sums
     # in the FP32 tensor accumulators are as coherent as they can be
@@ -337,7 +337,7 @@ def test_tc_autotune_picks_valid_config_and_caches(tmp_path, monkeypatch):
     kw = dict(kind="cartesian", n0=36, n1=40, lo0=-0.3, hi0=0.3, lo1=-0.3, hi1=0.3)
     plan = run(f, kw, autotune=1)
     info = nms.nms_plan_info(plan)
-    assert info["precision"] == TC and info["kc_cells"] in (64, 128, 256) and info["items_per_sm"] in (4, 8, 16)
+    assert info["precision"] == TC and info["kc_cells"] in (64, 128, 192, 256) and info["items_per_sm"] in (4, 8, 16)
     g = og(kw)
     F_ref = S.amplitudes(f, np.eye(3), g[0], g[1])
     assert np.all(amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f)) <= AMP_TOL)

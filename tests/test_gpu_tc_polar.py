@@ -176,3 +176,42 @@ def test_polar_tc_refuses_per_object_bins():
     with pytest.raises(nms.NmsError) as e:
         nms.nms_plan_object_iq(plan, "UNPOL", np.linspace(0.0, 1.0, 5))
     assert e.value.status == 4
+
+
+def test_polar_tc_objects_capture_in_cuda_graph():
+    # the ray path with per-object parts (one dilute pass per slot, issued
+    # from the host) captured once and replayed: bit for bit the eager result
+    torch = pytest.importorskip("torch")
+    f = I.small_random_field(2000, seed=61, extent=6.0, n_objects=7)
+    kw = dict(kind="polar", n0=40, n1=24, lo0=0.0, hi0=1.2)
+    side = torch.cuda.Stream()
+    opt = nms.nms_options_default(precision=TC, want_dilute=1)
+    plan = nms.plan_from_field(f, nms.make_grid(**kw), opt, rot=I.random_rotations(2, seed=62),
+                               stream=side.cuda_stream)
+    nms.nms_amplitudes(plan)
+    ref = {pt: nms.nms_response(plan, "UNPOL", pt).copy()
+           for pt in (nms.PART_TOTAL, nms.PART_DILUTE, nms.PART_INTERFERENCE)}
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        graph.capture_begin()
+        nms.nms_amplitudes(plan)
+        graph.capture_end()
+    for _ in range(2):
+        with torch.cuda.stream(side):
+            graph.replay()
+        torch.cuda.synchronize()
+        for pt, r in ref.items():
+            assert np.array_equal(nms.nms_response(plan, "UNPOL", pt), r), pt
+
+
+def test_polar_tc_autotune_request_keeps_defaults():
+    # the autotuner's error probe reads the Cartesian pixel layout, so a
+    # POLAR plan keeps the default GEMM configuration and still matches
+    f = I.small_random_field(3000, seed=63, extent=8.0)
+    kw = dict(kind="polar", n0=30, n1=16, lo0=0.0, hi0=1.0)
+    plan = run(f, kw, autotune=1)
+    info = nms.nms_plan_info(plan)
+    assert info["kc_cells"] == 192 and info["items_per_sm"] == 1
+    g = og(kw)
+    F_ref = S.amplitudes(f, np.eye(3), g[0], g[1])
+    assert np.all(amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f)) <= AMP_TOL)

@@ -46,6 +46,9 @@ POLAR_GRIDS = [
     dict(n0=64, n1=10, lo0=0.1, hi0=2.0),      # exactly one full i1 node
     dict(n0=130, n1=20, lo0=0.05, hi0=2.5),    # three i1 nodes, the last ragged
     dict(n0=1, n1=8, lo0=0.7, hi0=0.7),        # a single |q| node
+    dict(n0=1, n1=1, lo0=0.4, hi0=0.4),        # a single pixel
+    dict(n0=50, n1=2, lo0=0.0, hi0=1.0),       # two angles: one ray and its mirror
+    dict(n0=3000, n1=6, lo0=0.0, hi0=3.0),     # 47 i1 nodes: three A tiles, the last ragged
 ]
 
 

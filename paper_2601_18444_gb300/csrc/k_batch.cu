@@ -109,10 +109,11 @@ cudaError_t launch_prep_rot_batch(const Plan& p, const double* d_rot, int rot0, 
 // Polar detector on the tensor path (rays).  On the ray at angle theta the
 // pixel q = |q| (sin theta, cos theta) (the POLAR grid's q_y, q_z) has the
 // phase q.r = |q| u with u = Y sin theta + Z cos theta, so every ray is a
-// one-dimensional sum over the projections u.  Slot s of a batch (rotation
-// s / n_rays, ray s mod n_rays) gets the projection of its rotated position
-// in both coordinates, (u, u), and the rotated weights as in
-// k_prep_rot_batch (the weights do not depend on the ray).
+// one-dimensional sum over the projections u.  Slot s = slot0 + blockIdx.y
+// (rotation s / n_rays, ray s mod n_rays) gets the projection of each rotated
+// position in both coordinates, (u, u), and the rotated weights as in
+// k_prep_rot_batch (the weights do not depend on the ray); with cen_cell
+// (plans without per-object parts) the object centres are added first.
 __global__ void k_prep_ray_batch(int64_t n, int n_sets, int64_t wstride, const double* __restrict__ pos,
                                  const double* __restrict__ vol, const double* __restrict__ nuc,
                                  const double* __restrict__ mag, const double* __restrict__ cen_cell,

@@ -43,3 +43,20 @@ def test_gemm_axis_rule():
     assert bench.gemm_axis(63, -1.0, 1.0) == 32       # q = 0 node and the 31 nodes above it
     assert bench.gemm_axis(40, -0.7, 1.3) == 40
     assert bench.gemm_axis(1, 0.0, 0.0) == 1
+
+
+def test_paper_shape_objects_place_the_same_cells():
+    # --workload paper --objects: the same lattice of particles as objects
+    # (local positions, sites as centres) puts every cell where the single
+    # sum puts it, with the same weights
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    from paper_2601_18444_gb300 import inputs as I
+    particle = I.linear_vortex_sphere(6.0, 2.0, normalised=True)
+    one = bench.lattice_copies(particle, 27)
+    objs = bench.lattice_copies(particle, 27, objects=True)
+    assert objs.offsets[-1] == one.n and len(objs.offsets) == 28
+    centres = np.repeat(objs.centers, np.diff(objs.offsets), axis=0)
+    assert np.array_equal(objs.pos + centres, one.pos)
+    assert np.array_equal(objs.vol, one.vol) and np.array_equal(objs.nuc, one.nuc) and np.array_equal(objs.mag, one.mag)

@@ -214,7 +214,8 @@ __device__ __forceinline__ uint32_t bf16x2(float a, float b)
 // Inference for H = 256, n_out <= 128 per launch, n_in <= 8 on the
 // 5th-generation tensor cores, one kernel for the whole network.  A
 // persistent CTA keeps W2 and W3 (BF16) in shared memory in the 128-byte
-// swizzled K-major layout (192 KB) and the activations in tensor memory,
+// swizzled K-major layout (160 or 192 KB: W3 for 64 or 128 outputs) and the
+// activations in tensor memory,
 // where the MMA reads them as its A operand (row m in lane m, two BF16 per
 // 32-bit column).  Per tile of 128 queries:
 //   layer 1 (threads, FP32):  H1 = bf16(silu(b1 + W1 xn))      -> TMEM Hb
@@ -234,11 +235,18 @@ constexpr int FI_H = 256;
 constexpr int FI_NO = 128;     // outputs per launch; W3 rows padded with zeros
 constexpr int FI_TM = 128;     // queries per tile (the MMA's M)
 constexpr int FI_W2_BYTES = 4 * FI_H * 128;   // 4 K-blocks of 256 rows x 128 B
-constexpr int FI_W3_BYTES = 4 * FI_NO * 128;
-constexpr int FI_SMEM = FI_W2_BYTES + FI_W3_BYTES + 1024;
 constexpr uint32_t FI_HB = 256;               // TMEM column of activation buffer 0 (buffer 1: + 128)
-constexpr int FI_STG = FI_NO + 1;             // row stride of the output staging buffer (odd: no bank conflicts)
-static_assert(FI_THREADS == 32 * 32, "the output stage maps one warp to each of its 32 rows");
+// Dynamic shared memory after W2: W3 for 64 or 128 output rows, then the
+// output stage (row stride odd: no bank conflicts).  With at most 64
+// outputs the halved W3 leaves room to stage all 128 rows of a tile at once
+// (one block barrier); otherwise 32 rows at a time.
+__host__ __device__ constexpr int fi_w3_rows(int nout) { return nout <= 64 ? 64 : 128; }
+__host__ __device__ constexpr int fi_stage_rows(int nout) { return nout <= 64 ? 128 : 32; }
+__host__ __device__ constexpr int fi_smem(int nout)
+{
+    return FI_W2_BYTES + 4 * fi_w3_rows(nout) * 128 + fi_stage_rows(nout) * (fi_w3_rows(nout) + 1) * 4 + 1024;
+}
+static_assert(FI_THREADS == 32 * 32, "the 32-row output stage maps one warp to each row");
 
 // Small per-launch tables in shared memory (read as warp-wide broadcasts):
 // layer-1 weights padded to 8 inputs (with n_in < 8 the bias takes input
@@ -289,12 +297,13 @@ k_mlp_infer(int64_t n, int nin, int nout, int ystride, const float* __restrict__
     __shared__ uint32_t s_taddr;
     __shared__ volatile int s_abort;
     __shared__ __align__(16) FiSmall sm;
-    __shared__ float stag[32 * FI_STG];   // 32 rows of the output tile
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* gW2 = smem_raw + (base - raw);
     uint8_t* gW3 = gW2 + FI_W2_BYTES;
     const uint32_t sW2 = base, sW3 = base + FI_W2_BYTES;
+    const int w3rows = fi_w3_rows(nout), srows = fi_stage_rows(nout), sstride = w3rows + 1;
+    float* stag = reinterpret_cast<float*>(gW3 + 4 * w3rows * 128);   // srows x sstride
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     for (int h = tid; h < FI_H; h += FI_THREADS) {
@@ -327,10 +336,10 @@ k_mlp_infer(int64_t n, int nin, int nout, int ystride, const float* __restrict__
         const uint4 v = reinterpret_cast<const uint4*>(W2h)[u];
         *reinterpret_cast<uint4*>(gW2 + (k >> 6) * (FI_H * 128) + swz_offset(r, k & 63)) = v;
     }
-    for (int u = tid; u < FI_NO * 32; u += FI_THREADS) {
+    for (int u = tid; u < w3rows * 32; u += FI_THREADS) {
         const int r = u >> 5, j = u & 31, k = 8 * j;
         const uint4 v = r < nout ? reinterpret_cast<const uint4*>(W3h)[u] : make_uint4(0u, 0u, 0u, 0u);
-        *reinterpret_cast<uint4*>(gW3 + (k >> 6) * (FI_NO * 128) + swz_offset(r, k & 63)) = v;
+        *reinterpret_cast<uint4*>(gW3 + (k >> 6) * (w3rows * 128) + swz_offset(r, k & 63)) = v;
     }
     if (tid == 0) {
         mbar_init(&bar_mma, 1);
@@ -426,7 +435,7 @@ k_mlp_infer(int64_t n, int nin, int nout, int ystride, const float* __restrict__
         tc_fence_before();
         __syncthreads();
         // ---- layer 3 into D (columns 0 .. FI_NO - 1)
-        if (tid == 0) mma_layer(hb, sW3, FI_NO, id3);
+        if (tid == 0) mma_layer(hb, sW3, w3rows, id3);
         if (!wait_mma()) {
             aborted = true;
             break;
@@ -444,20 +453,37 @@ k_mlp_infer(int64_t n, int nin, int nout, int ystride, const float* __restrict__
                 tmem_ld16(taddr + lanes + (uint32_t)c0, v);
                 tmem_wait_ld();
             }
-            for (int qd = 0; qd < 4; ++qd) {
-                if (quad == qd && have) {
+            if (srows == FI_TM) {
+                // the whole tile at once; the stage is read again only after
+                // the barrier that ends this tile
+                if (have)
 #pragma unroll
                     for (int t = 0; t < 16; ++t) {
                         const int c = c0 + t;
-                        if (c < nout) stag[lane * FI_STG + c] = fmaf(v[t], sm.out_a[c], sm.out_c[c]);
+                        if (c < nout) stag[row * sstride + c] = fmaf(v[t], sm.out_a[c], sm.out_c[c]);
                     }
+                __syncthreads();
+                for (int rr = warp; rr < FI_TM; rr += 32) {   // warp w writes rows w, w + 32, ...
+                    const int64_t q = tile * FI_TM + rr;
+                    if (q < n)
+                        for (int c = lane; c < nout; c += 32) Y[q * ystride + c] = stag[rr * sstride + c];
                 }
-                __syncthreads();
-                // warp w writes staged row w, its lanes consecutive columns
-                const int64_t q = tile * FI_TM + 32 * qd + warp;
-                if (q < n)
-                    for (int c = lane; c < nout; c += 32) Y[q * ystride + c] = stag[warp * FI_STG + c];
-                __syncthreads();
+            } else {
+                for (int qd = 0; qd < 4; ++qd) {
+                    if (quad == qd && have) {
+#pragma unroll
+                        for (int t = 0; t < 16; ++t) {
+                            const int c = c0 + t;
+                            if (c < nout) stag[lane * sstride + c] = fmaf(v[t], sm.out_a[c], sm.out_c[c]);
+                        }
+                    }
+                    __syncthreads();
+                    // warp w writes staged row w, its lanes consecutive columns
+                    const int64_t q = tile * FI_TM + 32 * qd + warp;
+                    if (q < n)
+                        for (int c = lane; c < nout; c += 32) Y[q * ystride + c] = stag[warp * sstride + c];
+                    __syncthreads();
+                }
             }
         }
         // D read before the next tile's layer-2 MMAs overwrite it
@@ -942,7 +968,7 @@ nms_status nms_surrogate_infer(nms_surrogate_t s, const float* X, int64_t n, flo
         // again for the further 128)
         static bool attr = false;
         if (!attr) {
-            NMS_CUDA_TRY(cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, FI_SMEM));
+            NMS_CUDA_TRY(cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, fi_smem(FI_NO)));
             attr = true;
         }
         NMS_CUDA_TRY(cudaMemsetAsync(s->d_err, 0, 4, s->stream));
@@ -950,7 +976,7 @@ nms_status nms_surrogate_infer(nms_surrogate_t s, const float* X, int64_t n, flo
         const int grid = (int)std::min<int64_t>(tiles, device_sm_count());
         for (int o0 = 0; o0 < s->nout; o0 += FI_NO) {
             const int part = std::min(FI_NO, s->nout - o0);
-            k_mlp_infer<<<grid, FI_THREADS, FI_SMEM, s->stream>>>(
+            k_mlp_infer<<<grid, FI_THREADS, fi_smem(part), s->stream>>>(
                 n, s->nin, part, s->nout, X, s->d_xlo, s->d_xhi, W1p(s), b1p(s), s->d_W2h, b2p(s),
                 s->d_W3h + (int64_t)o0 * FI_H, b3p(s) + o0, s->d_ymean + o0, s->d_ystd + o0, Y + o0, s->d_err,
                 4000000000ull);

@@ -224,8 +224,10 @@ __device__ __forceinline__ uint32_t bf16x2(float a, float b)
 //   layer 3 (tcgen05.mma):    D  = H2 W3^T   (128 x n_out, FP32, D reused)
 //   drain:                     Y  = (D + b3) ystd + ymean       -> global
 // TMEM: D in columns 0-255, two activation buffers Hb[0], Hb[1] in 256-383
-// and 384-511.  While the layer-2 MMAs of tile i run, the threads compute
-// layer 1 of tile i + 1 into the other buffer.  Warp w handles the rows
+// and 384-511.  The layer-2 MMAs of tile i start as soon as tile i - 1's
+// layer-3 accumulator has been read, and run under that tile's output
+// stores and under layer 1 of tile i + 1, which the threads compute into the
+// other buffer.  Warp w handles the rows
 // 32 (w mod 4) .. + 31 (its TMEM lane quadrant) and the hidden units
 // 32 (w / 4) .. + 31.  The arithmetic is that of the layer-by-layer path
 // (BF16 operands, FP32 accumulation and activations); only the order of the
@@ -453,9 +455,14 @@ k_mlp_infer(int64_t n, int nin, int nout, int ystride, const float* __restrict__
                 tmem_ld16(taddr + lanes + (uint32_t)c0, v);
                 tmem_wait_ld();
             }
+            // D has been read: the next tile's layer-2 MMAs start now and run
+            // under the output stores
+            tc_fence_before();
+            __syncthreads();
+            if (next < ntiles && tid == 0) mma_layer(hn, sW2, FI_H, id2);
             if (srows == FI_TM) {
-                // the whole tile at once; the stage is read again only after
-                // the barrier that ends this tile
+                // the whole tile at once; the stage is written again only
+                // after the next tile's block barriers
                 if (have)
 #pragma unroll
                     for (int t = 0; t < 16; ++t) {
@@ -486,10 +493,6 @@ k_mlp_infer(int64_t n, int nin, int nout, int ystride, const float* __restrict__
                 }
             }
         }
-        // D read before the next tile's layer-2 MMAs overwrite it
-        tc_fence_before();
-        __syncthreads();
-        if (next < ntiles && tid == 0) mma_layer(hn, sW2, FI_H, id2);
     }
     if (aborted) {
         if (tid == 0) atomicExch(err, 1);

@@ -776,8 +776,12 @@ nms_status tc_setup(Plan& p)
         if ((st = upload(&t->d_ray_sc, sc)) || (st = upload(&t->d_ray_sc_tf, sct))) return st;
         // the cells rotated once per rotation (positions and weights, up to
         // 1 GB), so that each ray only projects them
+        // (NMS_RAY_PREP_FP64=1 takes the FP64 rotation per slot regardless,
+        // for comparisons)
         const int64_t rbytes = (int64_t)p.n_rot * p.n_cells * 16 * (1 + p.n_sets);
-        if (p.n_rot <= 65535 && rbytes <= (1ll << 30)) {
+        const char* fp64_env = getenv("NMS_RAY_PREP_FP64");
+        const bool per_slot = fp64_env && atoi(fp64_env) != 0;
+        if (!per_slot && p.n_rot <= 65535 && rbytes <= (1ll << 30)) {
             NMS_CUDA_TRY(plan_malloc(&t->d_rpos, (size_t)p.n_rot * p.n_cells * sizeof(float4)));
             NMS_CUDA_TRY(plan_malloc(&t->d_rw, (size_t)p.n_sets * p.n_rot * p.n_cells * sizeof(float4)));
         }

@@ -218,3 +218,26 @@ def test_polar_tc_autotune_request_keeps_defaults():
     g = og(kw)
     F_ref = S.amplitudes(f, np.eye(3), g[0], g[1])
     assert np.all(amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f)) <= AMP_TOL)
+
+
+@pytest.mark.parametrize("objects", [False, True])
+def test_polar_tc_fp64_ray_preparation_path(objects, monkeypatch):
+    # the FP64 rotation per (rotation, ray) slot, taken when the cells
+    # rotated once per rotation would not fit their 1 GB buffer, forced here
+    monkeypatch.setenv("NMS_RAY_PREP_FP64", "1")
+    f = I.small_random_field(2500, seed=66, extent=7.0, n_objects=5 if objects else 1)
+    kw = dict(kind="polar", n0=45, n1=20, lo0=0.0, hi0=1.2)
+    Rs = I.random_rotations(2, seed=67)
+    plan = run(f, kw, rot=Rs, want_dilute=1 if objects else 0)
+    g = og(kw)
+    F_ref = S.amplitudes(f, Rs[-1], g[0], g[1])
+    assert np.all(amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f, Rs[-1])) <= AMP_TOL)
+    if objects:
+        acc = [0, 0, 0]
+        for R in Rs:
+            parts = S.response_parts(f, R, g, ids=("UNPOL",))
+            for i in range(3):
+                acc[i] = acc[i] + parts["UNPOL"][i] / len(Rs)
+        tol = 2 * resp_tol(f, rotations=Rs)
+        for i, part in enumerate((nms.PART_TOTAL, nms.PART_DILUTE, nms.PART_INTERFERENCE)):
+            assert np.max(np.abs(nms.nms_response(plan, "UNPOL", part) - acc[i])) <= tol, part

@@ -241,3 +241,29 @@ def test_polar_tc_fp64_ray_preparation_path(objects, monkeypatch):
         tol = 2 * resp_tol(f, rotations=Rs)
         for i, part in enumerate((nms.PART_TOTAL, nms.PART_DILUTE, nms.PART_INTERFERENCE)):
             assert np.max(np.abs(nms.nms_response(plan, "UNPOL", part) - acc[i])) <= tol, part
+
+
+def test_polar_tc_weight_sets_with_objects_and_rotations():
+    # 3 states x 6 objects (dilute, total, interference) x 2 orientations on
+    # the ray path: the per-slot buffers hold every set
+    f = I.small_random_field(1500, seed=5, extent=5.0, n_objects=6)
+    nuc, mag = I.field_sweep(f, [0.0, 0.7, 4.0])
+    kw = dict(kind="polar", n0=36, n1=28, lo0=0.0, hi0=1.2)
+    Rs = I.random_rotations(2, seed=4)
+    opt = nms.nms_options_default(precision=TC, want_dilute=1, n_sets=3)
+    plan = nms.nms_plan_create(f.pos, f.vol, nuc, mag, f.offsets, f.centers, Rs, grid=nms.make_grid(**kw), opt=opt)
+    nms.nms_amplitudes(plan)
+    q = og(kw)
+    for s in range(3):
+        fs = I.Field(f.pos, f.vol, nuc[s], mag[s], offsets=f.offsets, centers=f.centers, name=f"state{s}")
+        nms.nms_select_set(plan, s)
+        acc = {k: [0, 0, 0] for k in ("UNPOL", "SF")}
+        for R in Rs:
+            parts = S.response_parts(fs, R, q, ids=("UNPOL", "SF"))
+            for k in acc:
+                for i in range(3):
+                    acc[k][i] = acc[k][i] + parts[k][i] / len(Rs)
+        tol = 2 * resp_tol(fs, rotations=Rs)
+        for k in acc:
+            for i, part in enumerate((nms.PART_TOTAL, nms.PART_DILUTE, nms.PART_INTERFERENCE)):
+                assert np.max(np.abs(nms.nms_response(plan, k, part) - acc[k][i])) <= tol, (s, k, part)

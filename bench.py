@@ -891,7 +891,24 @@ def run_paper_shape(args, dev):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
     extra = {}
-    if path == nms.PREC_TC_F16X3:
+    if path == nms.PREC_TC_F16X3 and nms.nms_plan_info(plan)["gemm_form"] == 3:
+        # one GEMM per ray with its operands generated in shared memory: no
+        # tables; the kernel reads 32 B per cell and ray and is paced by the
+        # generation (instruction issue), so the tensor roofline of the
+        # algorithmic flops is reported with that limit stated
+        k_ms = st["gemm"][0] / steps
+        n0, n1 = 1000, 1000
+        n_rays = n1 // 2 if n1 % 2 == 0 else n1
+        tflops = terms * ALGO_FLOPS_PER_TERM / (k_ms * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops", 1900.0)
+        roof = {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                "traffic": None, "kernel": "k_gemm_ray_fused", "flops_per_term": ALGO_FLOPS_PER_TERM,
+                "peak_source": f"{peak_src} bf16 dense (f16 same rate), burst",
+                "cell_bytes_per_step": n_rays * f.n * 32.0,
+                "limit": "operand generation in shared memory (instruction issue), not the tensor pipe",
+                "note": f"one GEMM per ray: {n0} |q| nodes as 16 x 64 (padded to 1024), operands built in shared "
+                        "memory from the cells' projections; the ray theta + pi taken as the conjugate"}
+    elif path == nms.PREC_TC_F16X3:
         # one GEMM per ray: |q| nodes as k1 x k2 (k2 = 64), one 128 x 128 output
         # tile per ray, so each table block (32 KB per tile and 64 cells) feeds
         # one tile and the GEMM streams its tables from HBM: HBM roofline
@@ -912,17 +929,6 @@ def run_paper_shape(args, dev):
                            "frac_of_bf16_burst": tflops / peaks.get("bf16_tflops", 1900.0)},
                 "note": f"one GEMM per ray: {n0} |q| nodes as {k1} x {k2} (padded to {k1 * k2}), the ray "
                         "theta + pi taken as the conjugate"}
-        if not args.no_fp32_leg:
-            ref_u = img_u.cpu().numpy()
-            dplan, dstep, dimg = make(nms.PREC_FP32_DIRECT)
-            dstep()
-            torch.cuda.synchronize()
-            d_ms = timed(dstep, 1)
-            du = dimg.cpu().numpy()
-            extra["fp32_direct"] = {"value": terms / (d_ms * 1e-3), "unit": "terms/s", "ms_per_step": d_ms,
-                                    "tc_over_fp32": d_ms / ms,
-                                    "unpol_max_abs_diff_over_max": float(np.max(np.abs(ref_u - du)) / np.max(np.abs(du)))}
-            dplan.close()
     else:
         peak = sms * 128 * mhz * 1e6 / 1e12
         k_ms = st["direct"][0] / steps
@@ -930,6 +936,17 @@ def run_paper_shape(args, dev):
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                 "traffic": None, "kernel": "k_direct<compensated>",
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz"}
+    if path == nms.PREC_TC_F16X3 and not args.no_fp32_leg:
+        ref_u = img_u.cpu().numpy()
+        dplan, dstep, dimg = make(nms.PREC_FP32_DIRECT)
+        dstep()
+        torch.cuda.synchronize()
+        d_ms = timed(dstep, 1)
+        du = dimg.cpu().numpy()
+        extra["fp32_direct"] = {"value": terms / (d_ms * 1e-3), "unit": "terms/s", "ms_per_step": d_ms,
+                                "tc_over_fp32": d_ms / ms,
+                                "unpol_max_abs_diff_over_max": float(np.max(np.abs(ref_u - du)) / np.max(np.abs(du)))}
+        dplan.close()
     pname = "tensor path, one GEMM per ray" if path == nms.PREC_TC_F16X3 else "direct path"
     line = {"metric": f"cell·q-point terms/s of the SANS Fourier sum, paper's example shape (polar grid, {pname})",
             "value": terms / (ms * 1e-3), "unit": "terms/s", "n_gpus": 1, "steps": steps, "warmup": warm,
@@ -944,7 +961,9 @@ def run_paper_shape(args, dev):
                        "paper_context": "about 60 s on an RTX 3090 for 3.38e6 cells on a 1000x1000 (q, theta) grid "
                                         "with all outputs incl. a 1000x1000 2D correlation and 670 MB of CSV "
                                         "(>= 5.6e10 terms/s)"},
-            "roofline": roof, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clocks}
+            "roofline": roof, "cpu_baseline": None, "e2e": None,
+            "gpu_launches": int(sum(v[1] for v in st.values()) + steps * (2 + (2 if args.objects else 0) + 2 + 4)),
+            "clocks": clocks}
     line.update(extra)
     print(json.dumps(line), flush=True)
     plan.close()

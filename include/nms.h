@@ -395,8 +395,11 @@ nms_status nms_dsft_direct_noalloc(int64_t n_cells, const double* Y, const doubl
  * (AUTO resolved), kc_cells = cells per TMEM accumulation chunk and
  * items_per_sm = work items per SM of each GEMM launch (tensor path; 0
  * otherwise), after autotuning when it was requested; gemm_form = 0 (one
- * CTA per 128 x 128 tile) or 2 (two-SM MMA over pairs of A tiles), -1 off
- * the tensor path; mirror_y / mirror_z = 1 where the detector axis is
+ * CTA per 128 x 128 tile), 2 (two-SM MMA over pairs of A tiles) or 3 (POLAR
+ * grid whose ray GEMM is one tile, at most 16 x 64 |q| nodes and one weight
+ * set: the operands are generated in the GEMM's shared memory, no phase
+ * tables; environment NMS_RAY_FUSED=0 keeps the tables), -1 off the tensor
+ * path; mirror_y / mirror_z = 1 where the detector axis is
  * symmetric about q = 0 (lo = -hi) and the GEMM evaluates its q >= 0 half,
  * writing both signs (cos is even and sin odd in q; Sec. "Summation
  * approach" sum, split by parity).  Any pointer may be NULL. */
@@ -417,6 +420,17 @@ nms_status nms_select_set(nms_plan_t plan, int32_t set);
  * code and returns, so this returns NMS_ERR_TIMEOUT and leaves the CUDA
  * context usable.  Synchronous on cuda_stream. */
 nms_status nms_selftest_bounded_wait(int64_t limit_us, void* cuda_stream);
+
+/* Self-test of the sine and cosine that the fused ray GEMM form generates
+ * its operands with (the phase 2 pi t of Eq. qdef's exponential, t in turns,
+ * already reduced to |t| <= 1/2; quarter-turn reduction and Taylor series,
+ * the paper has no counterpart): for each of the n host values t[i],
+ * out[4i], out[4i + 1] = sin, cos of 2 pi t[i] by that routine and
+ * out[4i + 2], out[4i + 3] = the same by CUDA's sincospif, for comparison
+ * with each other and with exact values.  out (host) holds 4n floats.
+ * n = 0 does nothing; n < 0 or a NULL array with n > 0 is
+ * NMS_ERR_INVALID_ARG.  Synchronous on cuda_stream. */
+nms_status nms_selftest_sincos(int64_t n, const float* t, float* out, void* cuda_stream);
 
 /* Release every device resource of the plan.  NULL is accepted. */
 nms_status nms_plan_destroy(nms_plan_t plan);

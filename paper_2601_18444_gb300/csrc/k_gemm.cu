@@ -81,6 +81,48 @@ __device__ __forceinline__ float turns_reduced(float2 q, float xh, float xl)
     return (p - n) + e;
 }
 
+// sin(2 pi t) and cos(2 pi t) of a phase in turns, |t| <= 1/2 (the reduced
+// phase above), for the fused ray form, where these values set the pace:
+// the nearest quarter turn n/4 is split off exactly (r = t - n/4, |r| <= 1/8,
+// Sterbenz), sin and cos of 2 pi r come from their Taylor series about 0
+// (odd terms to r^9, even terms to r^10: truncation below 2e-9 for
+// |2 pi r| <= pi/4), and the quadrant n mod 4 swaps and negates them.
+// Coefficients are (2 pi)^k / k! rounded once to FP32.  Error about one
+// unit in the last place (checked against exact values and sincospif).
+__device__ __forceinline__ void sincos_turns(float t, float& sn, float& cs)
+{
+    constexpr double TP = 6.283185307179586476925286766559;
+    constexpr float S1 = (float)TP;
+    constexpr float S3 = (float)(-TP * TP * TP / 6.0);
+    constexpr float S5 = (float)(TP * TP * TP * TP * TP / 120.0);
+    constexpr float S7 = (float)(-TP * TP * TP * TP * TP * TP * TP / 5040.0);
+    constexpr float S9 = (float)(TP * TP * TP * TP * TP * TP * TP * TP * TP / 362880.0);
+    constexpr float C2 = (float)(-TP * TP / 2.0);
+    constexpr float C4 = (float)(TP * TP * TP * TP / 24.0);
+    constexpr float C6 = (float)(-TP * TP * TP * TP * TP * TP / 720.0);
+    constexpr float C8 = (float)(TP * TP * TP * TP * TP * TP * TP * TP / 40320.0);
+    constexpr float C10 = (float)(-TP * TP * TP * TP * TP * TP * TP * TP * TP * TP / 3628800.0);
+    const float qn = rintf(4.0f * t);
+    const float r = fmaf(qn, -0.25f, t);
+    const int n = (int)qn;
+    const float r2 = r * r;
+    float ps = fmaf(S9, r2, S7);
+    ps = fmaf(ps, r2, S5);
+    ps = fmaf(ps, r2, S3);
+    ps = fmaf(ps, r2, S1);
+    const float sr = ps * r;
+    float pc = fmaf(C10, r2, C8);
+    pc = fmaf(pc, r2, C6);
+    pc = fmaf(pc, r2, C4);
+    pc = fmaf(pc, r2, C2);
+    const float cr = fmaf(pc, r2, 1.0f);
+    // quadrant n: (sin, cos) = (s, c), (c, -s), (-s, -c), (-c, s)
+    const bool swap = n & 1;
+    const float a = swap ? cr : sr, b = swap ? sr : cr;
+    sn = (n & 2) ? -a : a;
+    cs = ((n + 1) & 2) ? -b : b;
+}
+
 // (x0, x1) -> hi = fp16x2(x0, x1), lo = fp16x2(x0 - hi.x, x1 - hi.y); x0 in
 // the low half (the lower k index)
 __device__ __forceinline__ void split_h2(float x0, float x1, uint32_t& h, uint32_t& l)
@@ -467,6 +509,113 @@ __device__ __forceinline__ float4 combine_tf(float2 cc, float2 cs, float2 sc, fl
     return make_float4(re.x, re.y, im.x, im.y);
 }
 
+// The end of an item: its two-float column sums (hi[i], lo[i]: columns
+// colh + 2i and colh + 2i + 1 of TMEM lane 32 quad + lane, row of A tile
+// mtile) go to the partial tile P[slot] or, for an item that covers its
+// output's whole k-range (slot < 0), into the amplitudes.
+__device__ __forceinline__ void store_item(const GemmArgs& g, const GemmItem& item, int slot, int mtile, int quad,
+                                           int lane, int colh, const uint64_t* hi, const uint64_t* lo)
+{
+    // results leave as two-float pairs (no FP64 arithmetic here: GB300
+    // issues few FP64 operations per clock)
+    if (slot >= 0) {
+        // this item's tile, unscaled: (hi, lo) per element, column
+        // pairs j = n / 2 outermost, rows innermost (a warp's stores
+        // are contiguous)
+        float4* out = reinterpret_cast<float4*>(g.P) + (int64_t)slot * (TC_BM * TC_BN / 2) +
+                      (int64_t)(colh >> 1) * TC_BM + quad * 32 + lane;
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            out[i * TC_BM] =
+                make_float4(f2_lane0(hi[i]), f2_lane0(lo[i]), f2_lane1(hi[i]), f2_lane1(lo[i]));
+    } else {
+        // the whole k-range of this output.  Row mg = 2 (nch a + c) + p:
+        // the lanes 2i, 2i + 1 of a warp hold the cos and sin rows of
+        // one (a, c); columns 2b + r hold cos, sin of q_z,b.  Each lane
+        // takes its partner's pair and writes one or two amplitudes:
+        // on a symmetric q_y axis lane p = 0 writes +q_y and lane 1
+        // the mirrored -q_y node (both q_z signs where q_z is
+        // symmetric); otherwise lane 0 writes +q_z and lane 1 -q_z.
+        const AxisMap& ax = g.ax;
+        const int mg = mtile * TC_BM + quad * 32 + lane;
+        const int p = mg & 1;
+        const int qi = mg >> 1;
+        const int ag = qi / g.nch, ch = qi & (g.nch - 1);
+        const int b0 = (item.nt * TC_BN + colh) >> 1;       // GEMM q_z index of column pair 0
+        const int64_t mrows = (int64_t)g.nch * ax.ny;
+        float2* Fo = reinterpret_cast<float2*>(g.F) + (int64_t)(-1 - slot) * (ax.nz - ax.zs0) * mrows + ch;
+        // this lane's q_y node and sign, and which q_z signs it writes
+        // (-q_z only where the q_z < 0 rows are stored)
+        float sy = 1.f;
+        int a_out = ax.hy + ag;
+        bool act = ag < ax.nyg;
+        int zfirst = 0, zlast = (ax.mz && ax.zs0 == 0) ? 1 : 0;   // 0: +q_z, 1: -q_z
+        if (ax.my) {
+            if (p) {
+                sy = -1.f;
+                a_out = ax.ny - 1 - ax.hy - ag;
+                act = act && a_out != ax.hy + ag;      // q_y = 0 is its own mirror
+            }
+        } else {
+            zfirst = zlast = p;
+            act = act && (p == 0 || ax.mz);
+        }
+        const float sc = g.scale[ch & 3];
+        if (!item.two) {
+            // the output's only piece, rounded to FP32: the two-float
+            // sums are rounded first (one word per column to exchange),
+            // then combined; error <= 2^-24 (|cc| + |ss| + |F|)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const uint64_t x = f2_add(hi[i], lo[i]);
+                const uint64_t y = __shfl_xor_sync(0xffffffffu, x, 1);
+                const float xc = f2_lane0(x), xs = f2_lane1(x), yc = f2_lane0(y), ys = f2_lane1(y);
+                const float cc = p ? yc : xc, cs = p ? ys : xs, scs = p ? xc : yc, ss = p ? xs : ys;
+                const int bg = b0 + i;
+                if (!act || bg >= ax.nzg) continue;
+                for (int zs = zfirst; zs <= zlast; ++zs) {
+                    const float sz = zs ? -1.f : 1.f;
+                    const int b_out = zs ? ax.nz - 1 - ax.hz - bg : ax.hz + bg;
+                    if (zs && b_out == ax.hz + bg) continue;     // q_z = 0 is its own mirror
+                    const float re = fmaf(-sy * sz, ss, cc);
+                    const float im = -fmaf(sz, cs, sy * scs);
+                    Fo[(int64_t)(b_out - ax.zs0) * mrows + (int64_t)g.nch * a_out] = make_float2(sc * re, sc * im);
+                }
+            }
+        } else
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            // partner pair: all lanes take part in the exchange
+            const uint64_t ph = __shfl_xor_sync(0xffffffffu, hi[i], 1);
+            const uint64_t pl = __shfl_xor_sync(0xffffffffu, lo[i], 1);
+            const float2 xc = make_float2(f2_lane0(hi[i]), f2_lane0(lo[i]));   // own row x cos(q_z Z)
+            const float2 xs = make_float2(f2_lane1(hi[i]), f2_lane1(lo[i]));   // own row x sin(q_z Z)
+            const float2 yc = make_float2(f2_lane0(ph), f2_lane0(pl));
+            const float2 ys = make_float2(f2_lane1(ph), f2_lane1(pl));
+            const float2 cc = p ? yc : xc, cs = p ? ys : xs, scs = p ? xc : yc, ss = p ? xs : ys;
+            const int bg = b0 + i;
+            if (!act || bg >= ax.nzg) continue;
+            for (int zs = zfirst; zs <= zlast; ++zs) {
+                const float sz = zs ? -1.f : 1.f;
+                const int b_out = zs ? ax.nz - 1 - ax.hz - bg : ax.hz + bg;
+                if (zs && b_out == ax.hz + bg) continue;     // q_z = 0 is its own mirror
+                // an output of several pieces: two-float, stored by its
+                // first piece and added by the later ones
+                float2* oh = Fo + (int64_t)(b_out - ax.zs0) * mrows + (int64_t)g.nch * a_out;
+                float4 v = combine_tf(cc, cs, scs, ss, sy, sz);
+                v = make_float4(sc * v.x, sc * v.y, sc * v.z, sc * v.w);
+                float2* ol = oh + g.lo_off;
+                if (!item.store) {
+                    const float2 h = *oh, l = *ol;
+                    v = tf_add4(v, make_float4(h.x, l.x, h.y, l.y));
+                }
+                *oh = make_float2(v.x, v.z);
+                *ol = make_float2(v.y, v.w);
+            }
+        }
+    }
+}
+
 // tmA / tmB (MODE 2): 2D maps over the chunk's tables as 128-byte rows,
 // boxes of 128 rows (an A block) and 64 rows (half a B block)
 template <int MODE>
@@ -732,106 +881,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
             }
             if (!ok) break;
-            const int slot = (CLUSTER && rank) ? item.slot1 : item.slot;
-            // results leave as two-float pairs (no FP64 arithmetic here: GB300
-            // issues few FP64 operations per clock)
-            if (slot >= 0) {
-                // this item's tile, unscaled: (hi, lo) per element, column
-                // pairs j = n / 2 outermost, rows innermost (a warp's stores
-                // are contiguous)
-                float4* out = reinterpret_cast<float4*>(g.P) + (int64_t)slot * (TC_BM * TC_BN / 2) +
-                              (int64_t)(colh >> 1) * TC_BM + quad * 32 + lane;
-#pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    out[i * TC_BM] =
-                        make_float4(f2_lane0(hi[i]), f2_lane0(lo[i]), f2_lane1(hi[i]), f2_lane1(lo[i]));
-            } else {
-                // the whole k-range of this output.  Row mg = 2 (nch a + c) + p:
-                // the lanes 2i, 2i + 1 of a warp hold the cos and sin rows of
-                // one (a, c); columns 2b + r hold cos, sin of q_z,b.  Each lane
-                // takes its partner's pair and writes one or two amplitudes:
-                // on a symmetric q_y axis lane p = 0 writes +q_y and lane 1
-                // the mirrored -q_y node (both q_z signs where q_z is
-                // symmetric); otherwise lane 0 writes +q_z and lane 1 -q_z.
-                const AxisMap& ax = g.ax;
-                const int mtile = MODE == 2 ? 2 * item.mt + rank : item.mt;
-                const int mg = mtile * TC_BM + quad * 32 + lane;
-                const int p = mg & 1;
-                const int qi = mg >> 1;
-                const int ag = qi / g.nch, ch = qi & (g.nch - 1);
-                const int b0 = (item.nt * TC_BN + colh) >> 1;       // GEMM q_z index of column pair 0
-                const int64_t mrows = (int64_t)g.nch * ax.ny;
-                float2* Fo = reinterpret_cast<float2*>(g.F) + (int64_t)(-1 - slot) * (ax.nz - ax.zs0) * mrows + ch;
-                // this lane's q_y node and sign, and which q_z signs it writes
-                // (-q_z only where the q_z < 0 rows are stored)
-                float sy = 1.f;
-                int a_out = ax.hy + ag;
-                bool act = ag < ax.nyg;
-                int zfirst = 0, zlast = (ax.mz && ax.zs0 == 0) ? 1 : 0;   // 0: +q_z, 1: -q_z
-                if (ax.my) {
-                    if (p) {
-                        sy = -1.f;
-                        a_out = ax.ny - 1 - ax.hy - ag;
-                        act = act && a_out != ax.hy + ag;      // q_y = 0 is its own mirror
-                    }
-                } else {
-                    zfirst = zlast = p;
-                    act = act && (p == 0 || ax.mz);
-                }
-                const float sc = g.scale[ch & 3];
-                if (!item.two) {
-                    // the output's only piece, rounded to FP32: the two-float
-                    // sums are rounded first (one word per column to exchange),
-                    // then combined; error <= 2^-24 (|cc| + |ss| + |F|)
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const uint64_t x = f2_add(hi[i], lo[i]);
-                        const uint64_t y = __shfl_xor_sync(0xffffffffu, x, 1);
-                        const float xc = f2_lane0(x), xs = f2_lane1(x), yc = f2_lane0(y), ys = f2_lane1(y);
-                        const float cc = p ? yc : xc, cs = p ? ys : xs, scs = p ? xc : yc, ss = p ? xs : ys;
-                        const int bg = b0 + i;
-                        if (!act || bg >= ax.nzg) continue;
-                        for (int zs = zfirst; zs <= zlast; ++zs) {
-                            const float sz = zs ? -1.f : 1.f;
-                            const int b_out = zs ? ax.nz - 1 - ax.hz - bg : ax.hz + bg;
-                            if (zs && b_out == ax.hz + bg) continue;     // q_z = 0 is its own mirror
-                            const float re = fmaf(-sy * sz, ss, cc);
-                            const float im = -fmaf(sz, cs, sy * scs);
-                            Fo[(int64_t)(b_out - ax.zs0) * mrows + (int64_t)g.nch * a_out] = make_float2(sc * re, sc * im);
-                        }
-                    }
-                } else
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    // partner pair: all lanes take part in the exchange
-                    const uint64_t ph = __shfl_xor_sync(0xffffffffu, hi[i], 1);
-                    const uint64_t pl = __shfl_xor_sync(0xffffffffu, lo[i], 1);
-                    const float2 xc = make_float2(f2_lane0(hi[i]), f2_lane0(lo[i]));   // own row x cos(q_z Z)
-                    const float2 xs = make_float2(f2_lane1(hi[i]), f2_lane1(lo[i]));   // own row x sin(q_z Z)
-                    const float2 yc = make_float2(f2_lane0(ph), f2_lane0(pl));
-                    const float2 ys = make_float2(f2_lane1(ph), f2_lane1(pl));
-                    const float2 cc = p ? yc : xc, cs = p ? ys : xs, scs = p ? xc : yc, ss = p ? xs : ys;
-                    const int bg = b0 + i;
-                    if (!act || bg >= ax.nzg) continue;
-                    for (int zs = zfirst; zs <= zlast; ++zs) {
-                        const float sz = zs ? -1.f : 1.f;
-                        const int b_out = zs ? ax.nz - 1 - ax.hz - bg : ax.hz + bg;
-                        if (zs && b_out == ax.hz + bg) continue;     // q_z = 0 is its own mirror
-                        // an output of several pieces: two-float, stored by its
-                        // first piece and added by the later ones
-                        float2* oh = Fo + (int64_t)(b_out - ax.zs0) * mrows + (int64_t)g.nch * a_out;
-                        float4 v = combine_tf(cc, cs, scs, ss, sy, sz);
-                        v = make_float4(sc * v.x, sc * v.y, sc * v.z, sc * v.w);
-                        float2* ol = oh + g.lo_off;
-                        if (!item.store) {
-                            const float2 h = *oh, l = *ol;
-                            v = tf_add4(v, make_float4(h.x, l.x, h.y, l.y));
-                        }
-                        *oh = make_float2(v.x, v.z);
-                        *ol = make_float2(v.y, v.w);
-                    }
-                }
-            }
+            store_item(g, item, (CLUSTER && rank) ? item.slot1 : item.slot, MODE == 2 ? 2 * item.mt + rank : item.mt,
+                       quad, lane, colh, hi, lo);
         }
     }
     tc_fence_before();
@@ -839,6 +890,484 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (CLUSTER) cluster_sync();    // no MMA, commit or remote arrival can still target this CTA
     tc_fence_after();
     if (warp == 1) tc_dealloc<C::CG>(taddr, 512);
+}
+
+// ------------------------------------------------------------------ fused ray GEMM
+// Polar grid (rays, reading of Eq. qdef on the paper's polar detector) with
+// one weight set and one A and one B tile (at most 16 x 64 |q| nodes): each
+// slot is one 128 x 128 output tile, so with tables every table block is
+// written to HBM once and read back once by a single tile.  This form builds
+// each k-block's four operand blocks in shared memory instead, from the cells'
+// ray projections u and weights, with the arithmetic of k_tables (two-float
+// phase in turns, exact reduction, scaled FP16 hi/lo split) except that sin
+// and cos come from sincos_turns instead of sincospif: generation, not the
+// MMAs, sets this form's pace.
+//
+// Roles (576 threads):
+//   warp 0           copies each k-block's cell data (64 positions, then 64
+//                    weights, float4) into a ring of RF_CELL_SLOTS slots;
+//   warp 1, lane 0   issues the MMAs (as in k_gemm_f16x3);
+//   warps 2..17      generate the operand stages and drain the accumulator.
+// The drain's two-float running sums live in tensor memory (columns 256..383
+// hi, 384..511 lo) instead of registers, which leaves the generating warps
+// their registers for the phase arithmetic; the accumulator (D0 columns
+// 0..127, D1 128..255) is single-buffered.  The workers drain chunk c - 1 just
+// after generating the first k-block of chunk c: the MMAs of chunk c wait for
+// that drain, and generation, slower per k-block than the MMAs, keeps them
+// waiting anyway, so the accumulator is free again before it is needed.
+constexpr int RF_CELL_SLOTS = 4;
+constexpr int RF_CELL_BYTES = 64 * 32;   // per slot: 64 float4 positions, then 64 float4 weights
+constexpr int RF_WORKERS = 16 * 32;
+constexpr int RF_SMEM = TC_STAGES * TC_STAGE_BYTES + RF_CELL_SLOTS * RF_CELL_BYTES + 1024;
+
+struct RayFusedArgs {
+    const float4* cpos;           // (u hi, u lo, u hi, u lo) per cell of the stacked slot arrays
+    const float4* cw;             // weights (N, Mx, My, Mz) per cell (one set)
+    const int64_t* kb_cell0;      // first cell of each k-block of the launch
+    const int32_t* kb_ncell;      // its cells (<= 64)
+    float4 wscale;                // per-channel weight scale (as in k_tables)
+    int nyg, nzg;                 // live nodes: coarse (A rows, <= 16), fine (B rows, <= 64)
+    float2 qy[16];                // coarse nodes lo + 64 i1 dq in turns (two-float)
+    float2 qz[64];                // fine offsets i2 dq in turns (two-float)
+};
+
+// all lanes wait (bounded); the warp continues only if every lane saw the phase
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns, volatile int* abort_flag)
+{
+    const bool ok = mbar_wait(bar, parity, limit_ns, abort_flag);
+    return __all_sync(0xffffffffu, ok) != 0;
+}
+
+// One k-block of operands into the stage at st (generic pointer): thread
+// (r, q4) of the 512 workers writes B rows 2b, 2b + 1 (b = r, r + 32) for the
+// cells 4 q4 .. + 3 (8-byte stores: a half-warp fills a 128-byte row) and the
+// eight A rows of coarse node a = r / 2 (four channels x cos, sin) for the
+// cells 4 q4 + 2h, + 1 (h = r mod 2; 4-byte stores: a warp fills a row).
+__device__ __forceinline__ void ray_gen_block(uint8_t* st, const float* uh, const float* ul, float4 w0, float4 w1,
+                                              int nc, int q4, int r, float2 qb0, float2 qb1, float2 qa, float onb0,
+                                              float onb1, float ona)
+{
+#pragma unroll
+    for (int jb = 0; jb < 2; ++jb) {
+        const float2 q = jb ? qb1 : qb0;
+        const float on = jb ? onb1 : onb0;
+        const int b = r + 32 * jb;
+        float cs[4], sn[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float live = 4 * q4 + u < nc ? on : 0.f;
+            sincos_turns(turns_reduced(q, uh[u], ul[u]), sn[u], cs[u]);
+            cs[u] *= live;
+            sn[u] *= live;
+        }
+        uint2 ch, cl, sh, sl;
+        split4(cs[0], cs[1], cs[2], cs[3], ch, cl);
+        split4(sn[0], sn[1], sn[2], sn[3], sh, sl);
+        const uint32_t oc = swz_offset(2 * b, 4 * q4), os = swz_offset(2 * b + 1, 4 * q4);
+        *reinterpret_cast<uint2*>(st + 2 * TC_BLOCK_BYTES + oc) = ch;
+        *reinterpret_cast<uint2*>(st + 3 * TC_BLOCK_BYTES + oc) = cl;
+        *reinterpret_cast<uint2*>(st + 2 * TC_BLOCK_BYTES + os) = sh;
+        *reinterpret_cast<uint2*>(st + 3 * TC_BLOCK_BYTES + os) = sl;
+    }
+    const int h = r & 1, a = r >> 1;
+    const int k = 4 * q4 + 2 * h;
+    const float u0h = h ? uh[2] : uh[0], u0l = h ? ul[2] : ul[0];
+    const float u1h = h ? uh[3] : uh[1], u1l = h ? ul[3] : ul[1];
+    float s0, c0, s1, c1;
+    sincos_turns(turns_reduced(qa, u0h, u0l), s0, c0);
+    sincos_turns(turns_reduced(qa, u1h, u1l), s1, c1);
+    c0 *= ona;
+    s0 *= ona;
+    c1 *= ona;
+    s1 *= ona;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float x0 = c == 0 ? w0.x : c == 1 ? w0.y : c == 2 ? w0.z : w0.w;
+        const float x1 = c == 0 ? w1.x : c == 1 ? w1.y : c == 2 ? w1.z : w1.w;
+        const int row = 2 * (4 * a + c);
+        uint32_t hh, ll;
+        split_h2(x0 * c0, x1 * c1, hh, ll);
+        const uint32_t oc = swz_offset(row, k), os = swz_offset(row + 1, k);
+        *reinterpret_cast<uint32_t*>(st + oc) = hh;
+        *reinterpret_cast<uint32_t*>(st + TC_BLOCK_BYTES + oc) = ll;
+        split_h2(x0 * s0, x1 * s1, hh, ll);
+        *reinterpret_cast<uint32_t*>(st + os) = hh;
+        *reinterpret_cast<uint32_t*>(st + TC_BLOCK_BYTES + os) = ll;
+    }
+}
+
+// Drain one chunk into the tensor-memory running sums of this warp's 32
+// columns (tb: its D0 address; D1 +128, hi +256, lo +384): lo += D0 + D1
+// (first chunk of an item: hi = 0, lo = D0 + D1), then, when renorm, a
+// second pass TwoSum(hi, lo) -> (hi, lo).  The MMAs of the next chunk wait
+// for this drain, so it works in four 8-column groups (one TMEM load round
+// trip each) and reads hi only in the renormalising pass, which keeps its
+// registers few beside the generation state.
+__device__ __forceinline__ void ray_drain_chunk(uint32_t tb, bool first, bool renorm)
+{
+#pragma unroll
+    for (int cb = 0; cb < 4; ++cb) {
+        float d0[8], d1[8], sl[8];
+        tmem_ld8(tb + 8 * cb, d0);
+        tmem_ld8(tb + 128 + 8 * cb, d1);
+        if (!first) tmem_ld8(tb + 384 + 8 * cb, sl);
+        tmem_wait_ld();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t x = f2_add(f2_pack(d0[2 * u], d0[2 * u + 1]), f2_pack(d1[2 * u], d1[2 * u + 1]));
+            const uint64_t lo = first ? x : f2_add(f2_pack(sl[2 * u], sl[2 * u + 1]), x);
+            sl[2 * u] = f2_lane0(lo);
+            sl[2 * u + 1] = f2_lane1(lo);
+        }
+#pragma unroll
+        for (int z = 0; z < 8; z += 4) tmem_st4(tb + 384 + 8 * cb + z, sl + z);
+        if (first) {
+#pragma unroll
+            for (int z = 0; z < 8; ++z) d0[z] = 0.f;
+#pragma unroll
+            for (int z = 0; z < 8; z += 4) tmem_st4(tb + 256 + 8 * cb + z, d0 + z);
+        }
+    }
+    if (renorm) {
+        tmem_wait_st();
+#pragma unroll
+        for (int cb = 0; cb < 4; ++cb) {
+            float sh[8], sl[8];
+            tmem_ld8(tb + 256 + 8 * cb, sh);
+            tmem_ld8(tb + 384 + 8 * cb, sl);
+            tmem_wait_ld();
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t hi = f2_pack(sh[2 * u], sh[2 * u + 1]);
+                const uint64_t lo = f2_pack(sl[2 * u], sl[2 * u + 1]);
+                const uint64_t sm = f2_add(hi, lo);
+                const uint64_t bb = f2_sub(sm, hi);
+                const uint64_t er = f2_add(f2_sub(hi, f2_sub(sm, bb)), f2_sub(lo, bb));
+                sh[2 * u] = f2_lane0(sm);
+                sh[2 * u + 1] = f2_lane1(sm);
+                sl[2 * u] = f2_lane0(er);
+                sl[2 * u + 1] = f2_lane1(er);
+            }
+#pragma unroll
+            for (int z = 0; z < 8; z += 4) {
+                tmem_st4(tb + 256 + 8 * cb + z, sh + z);
+                tmem_st4(tb + 384 + 8 * cb + z, sl + z);
+            }
+        }
+    }
+    tmem_wait_st();
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_ray_fused(const GemmArgs g, const __grid_constant__ RayFusedArgs ra)
+{
+    constexpr int STG = TC_STAGES;
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t bar_full[STG];       // RF_WORKERS arrivals: a stage is generated
+    __shared__ __align__(8) uint64_t bar_empty[STG];      // MMA commit: a stage is consumed
+    __shared__ __align__(8) uint64_t bar_cell_full[RF_CELL_SLOTS];
+    __shared__ __align__(8) uint64_t bar_cell_empty[RF_CELL_SLOTS];
+    __shared__ __align__(8) uint64_t bar_acc_full;
+    __shared__ __align__(8) uint64_t bar_acc_empty;
+    __shared__ __align__(8) uint64_t bar_final;
+    __shared__ int s_nc[RF_CELL_SLOTS];
+    __shared__ uint32_t s_taddr;
+    __shared__ volatile int s_abort;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    uint8_t* const sgen = smem_raw + (sbase - smem_u32(smem_raw));      // the same address, generic
+    uint8_t* const cells = sgen + STG * TC_STAGE_BYTES;
+    const int it_begin = g.unit_item0[blockIdx.x], it_end = g.unit_item0[blockIdx.x + 1];
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STG; ++s) {
+            mbar_init(&bar_full[s], RF_WORKERS);
+            mbar_init(&bar_empty[s], 1);
+        }
+        for (int s = 0; s < RF_CELL_SLOTS; ++s) {
+            mbar_init(&bar_cell_full[s], 1);
+            mbar_init(&bar_cell_empty[s], RF_WORKERS);
+        }
+        mbar_init(&bar_acc_full, 1);
+        mbar_init(&bar_acc_empty, TC_EPI_WARPS);
+        mbar_init(&bar_final, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tc_alloc<1>(smem_u32(&s_taddr), 512);
+        tc_relinquish<1>();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = s_taddr;
+
+    if (warp == 0) {
+        // ---------------- cell loader: bulk copies of each k-block's cells.
+        // The warp reads the k-block descriptors 32 at a time (lane l holds
+        // block kb0 + 32 i + l), so the copies never wait on those loads;
+        // every lane follows the ring, lane 0 issues.
+        int64_t i = 0;                      // k-block sequence number
+        int cs = 0;                         // its cell slot
+        uint32_t par = 1u;                  // parity of the slot's previous "empty" phase
+        bool ok = true;
+        for (int it = it_begin; it < it_end && ok; ++it) {
+            const GemmItem item = g.items[it];
+            for (int base = item.kb0; base < item.kb1 && ok; base += 32) {
+                const int my = base + lane;
+                const int64_t my_c0 = my < item.kb1 ? ra.kb_cell0[my] : 0;
+                const int my_nc = my < item.kb1 ? ra.kb_ncell[my] : 0;
+                const int cnt = min(32, item.kb1 - base);
+                for (int j = 0; j < cnt; ++j) {
+                    const int64_t c0 = __shfl_sync(0xffffffffu, my_c0, j);
+                    const int nc = __shfl_sync(0xffffffffu, my_nc, j);
+                    if (!warp_wait(&bar_cell_empty[cs], par, g.limit_ns, &s_abort)) {
+                        if (lane == 0) {
+                            s_abort = 1;
+                            atomicExch(g.err, 1);
+                        }
+                        ok = false;
+                        break;
+                    }
+                    if (lane == 0) {
+                        s_nc[cs] = nc;
+                        uint8_t* dst = cells + cs * RF_CELL_BYTES;
+                        if (nc > 0) {
+                            mbar_arrive_expect_tx(&bar_cell_full[cs], (uint32_t)nc * 32u);
+                            bulk_g2s(smem_u32(dst), ra.cpos + c0, (uint32_t)nc * 16u, &bar_cell_full[cs]);
+                            bulk_g2s(smem_u32(dst + RF_CELL_BYTES / 2), ra.cw + c0, (uint32_t)nc * 16u,
+                                     &bar_cell_full[cs]);
+                        } else {
+                            mbar_arrive(&bar_cell_full[cs]);
+                        }
+                    }
+                    __syncwarp();
+                    ++i;
+                    if (++cs == RF_CELL_SLOTS) {
+                        cs = 0;
+                        par ^= 1u;
+                    }
+                }
+            }
+        }
+        // copies in flight land before the CTA exits (bounded)
+        if (lane == 0)
+            for (int64_t k = (i > RF_CELL_SLOTS ? i - RF_CELL_SLOTS : 0); k < i; ++k)
+                mbar_wait_drain(&bar_cell_full[(int)(k % RF_CELL_SLOTS)], (uint32_t)((k / RF_CELL_SLOTS) & 1));
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer: one accumulator pair (D0, D1)
+            const uint32_t idesc = idesc_f16_f32(TC_BM, TC_BN);
+            int s = 0;
+            uint32_t sph = 0;
+            uint32_t c = 0;                 // chunk sequence number
+            bool ok = true;
+            for (int it = it_begin; it < it_end && ok; ++it) {
+                const GemmItem item = g.items[it];
+                for (int k0 = item.kb0; k0 < item.kb1 && ok; k0 += g.kcb, ++c) {
+                    // the drain of chunk c - 1 has read the accumulator
+                    if (!mbar_wait(&bar_acc_empty, (c & 1u) ^ 1u, g.limit_ns, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const int k1 = min(item.kb1, k0 + g.kcb);
+                    bool first = true;
+                    for (int kb = k0; kb < k1; ++kb) {
+                        if (!mbar_wait(&bar_full[s], sph, g.limit_ns, &s_abort)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t st = sbase + (uint32_t)s * TC_STAGE_BYTES;
+                        const uint64_t ah0 = sw128_desc(st), al0 = sw128_desc(st + TC_BLOCK_BYTES);
+                        const uint64_t bh0 = sw128_desc(st + 2 * TC_BLOCK_BYTES);
+                        const uint64_t bl0 = sw128_desc(st + 3 * TC_BLOCK_BYTES);
+#pragma unroll
+                        for (int k16 = 0; k16 < 4; ++k16) {
+                            tc_mma3_f16<1>(taddr, taddr + 128u, ah0 + 2 * k16, al0 + 2 * k16, bh0 + 2 * k16,
+                                           bl0 + 2 * k16, idesc, first ? 0u : 1u);
+                            first = false;
+                        }
+                        tc_commit(&bar_empty[s]);
+                        if (++s == STG) {
+                            s = 0;
+                            sph ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    tc_commit(&bar_acc_full);
+                }
+            }
+            if (!ok) {
+                s_abort = 1;
+                atomicExch(g.err, 2);
+            }
+            tc_commit(&bar_final);
+            mbar_wait_drain(&bar_final, 0);
+        }
+    } else {
+        // ---------------- workers: operand generation and the drain
+        const int e = warp - 2;
+        const int quad = warp & 3;                  // TMEM lane quadrant of this warp
+        const int colh = (e >> 2) * 32;             // its 32 accumulator columns
+        const int t = threadIdx.x - 64;
+        const int q4 = t & 15;                      // cells 4 q4 .. + 3 of each k-block
+        const int r = t >> 4;                       // B nodes r, r + 32; A node r / 2
+        const int h = r & 1;                        // A cells 4 q4 + 2h, + 1
+        const int m = (q4 >> 1) & 3;                // rotation of the cell reads (spreads banks)
+        const float2 zero2 = make_float2(0.f, 0.f);
+        const float2 qb0 = r < ra.nzg ? ra.qz[r] : zero2;
+        const float2 qb1 = r + 32 < ra.nzg ? ra.qz[r + 32] : zero2;
+        const float2 qa = (r >> 1) < ra.nyg ? ra.qy[r >> 1] : zero2;
+        const float onb0 = r < ra.nzg ? TC_SCALE : 0.f;
+        const float onb1 = r + 32 < ra.nzg ? TC_SCALE : 0.f;
+        const float ona = (r >> 1) < ra.nyg ? 1.f : 0.f;
+        const uint32_t tb = taddr + ((uint32_t)(quad * 32) << 16) + (uint32_t)colh;
+        int s = 0;
+        uint32_t epar = 1u;                         // parity of the stage's previous "empty" phase
+        int cs = 0;
+        uint32_t cpar = 0u;                         // parity of the cell slot's next "full" phase
+        uint32_t c = 0;                             // chunk sequence number (drains)
+        bool ok = true;
+        for (int it = it_begin; it < it_end && ok; ++it) {
+            const GemmItem item = g.items[it];
+            int pend = -1;                          // first k-block of the chunk awaiting its drain
+            bool any = false;
+            for (int k0 = item.kb0; k0 < item.kb1 && ok; k0 += g.kcb) {
+                const int k1 = min(item.kb1, k0 + g.kcb);
+                for (int kb = k0; kb < k1; ++kb) {
+                    // this k-block's cells
+                    if (!warp_wait(&bar_cell_full[cs], cpar, g.limit_ns, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint8_t* cl = cells + cs * RF_CELL_BYTES;
+                    const int nc = s_nc[cs];
+                    float2 v[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) v[j] = *reinterpret_cast<const float2*>(cl + 16 * (4 * q4 + ((j + m) & 3)));
+                    float4 wv[2];
+#pragma unroll
+                    for (int j = 0; j < 2; ++j)
+                        wv[j] = *reinterpret_cast<const float4*>(cl + RF_CELL_BYTES / 2 +
+                                                                 16 * (4 * q4 + 2 * h + ((j + m) & 1)));
+                    // the slot's next contents arrive by bulk copy (async proxy):
+                    // order these generic reads before it, then release the slot
+                    fence_proxy_async_smem();
+                    mbar_arrive(&bar_cell_empty[cs]);
+                    if (++cs == RF_CELL_SLOTS) {
+                        cs = 0;
+                        cpar ^= 1u;
+                    }
+                    // cell 4 q4 + u was read into v[(u - m) mod 4]; cells past nc are zero
+                    float uh[4], ul[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int j = (u - m) & 3;
+                        const float2 x = j == 0 ? v[0] : j == 1 ? v[1] : j == 2 ? v[2] : v[3];
+                        const bool live = 4 * q4 + u < nc;
+                        uh[u] = live ? x.x : 0.f;
+                        ul[u] = live ? x.y : 0.f;
+                    }
+                    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 wa = (m & 1) ? wv[1] : wv[0], wb = (m & 1) ? wv[0] : wv[1];
+                    const float4 W = ra.wscale;
+                    const float4 w0 = 4 * q4 + 2 * h < nc
+                                          ? make_float4(wa.x * W.x, wa.y * W.y, wa.z * W.z, wa.w * W.w) : z4;
+                    const float4 w1 = 4 * q4 + 2 * h + 1 < nc
+                                          ? make_float4(wb.x * W.x, wb.y * W.y, wb.z * W.z, wb.w * W.w) : z4;
+                    // the stage, once the MMAs have read its previous contents
+                    if (!warp_wait(&bar_empty[s], epar, g.limit_ns, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    ray_gen_block(sgen + s * TC_STAGE_BYTES, uh, ul, w0, w1, nc, q4, r, qb0, qb1, qa, onb0, onb1, ona);
+                    fence_proxy_async_smem();
+                    mbar_arrive(&bar_full[s]);
+                    if (++s == STG) {
+                        s = 0;
+                        epar ^= 1u;
+                    }
+                    if (kb == k0 && pend >= 0) {
+                        // drain the previous chunk while the MMAs wait for this one
+                        int okw = 0;
+                        if (lane == 0) okw = mbar_wait(&bar_acc_full, c & 1u, g.limit_ns, &s_abort) ? 1 : 0;
+                        okw = __shfl_sync(0xffffffffu, okw, 0);
+                        if (!okw) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const int ci = (pend - item.kb0) / g.kcb;
+                        ray_drain_chunk(tb, ci == 0, TC_RENORM <= 1 || (ci + 1) % TC_RENORM == 0);
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&bar_acc_empty);
+                        ++c;
+                        pend = -1;
+                        any = true;
+                    }
+                }
+                if (ok) pend = k0;
+            }
+            if (ok && pend >= 0) {
+                int okw = 0;
+                if (lane == 0) okw = mbar_wait(&bar_acc_full, c & 1u, g.limit_ns, &s_abort) ? 1 : 0;
+                okw = __shfl_sync(0xffffffffu, okw, 0);
+                if (okw) {
+                    tc_fence_after();
+                    const int ci = (pend - item.kb0) / g.kcb;
+                    ray_drain_chunk(tb, ci == 0, TC_RENORM <= 1 || (ci + 1) % TC_RENORM == 0);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bar_acc_empty);
+                    ++c;
+                    any = true;
+                } else {
+                    ok = false;
+                }
+            }
+            if (!ok) {
+                if (lane == 0) {
+                    s_abort = 1;
+                    atomicExch(g.err, 3);
+                }
+                break;
+            }
+            // the item's tile, unscaled, to its partial slot P[slot] (this
+            // form's schedule gives every item one; k_gemm_reduce combines
+            // them): each 8-column group of the sums straight from TMEM
+            if (item.slot < 0) {
+                if (lane == 0) atomicExch(g.err, 4);
+                continue;
+            }
+            float4* out = reinterpret_cast<float4*>(g.P) + (int64_t)item.slot * (TC_BM * TC_BN / 2) +
+                          (int64_t)(colh >> 1) * TC_BM + quad * 32 + lane;
+#pragma unroll
+            for (int cb = 0; cb < 4; ++cb) {
+                float xh[8], xl[8];
+                if (any) {
+                    tmem_ld8(tb + 256 + 8 * cb, xh);
+                    tmem_ld8(tb + 384 + 8 * cb, xl);
+                    tmem_wait_ld();
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) xh[i] = xl[i] = 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    out[(4 * cb + u) * TC_BM] = make_float4(xh[2 * u], xl[2 * u], xh[2 * u + 1], xl[2 * u + 1]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tc_dealloc<1>(taddr, 512);
 }
 
 // Reduction of item tiles (two-float elements) into per-output amplitudes
@@ -936,6 +1465,28 @@ __global__ void k_selftest_wait(uint64_t limit_ns, int32_t* err)
 cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t* err, cudaStream_t s)
 {
     k_selftest_wait<<<1, 32, 0, s>>>(limit_ns, err);
+    return cudaGetLastError();
+}
+
+// Self-test of sincos_turns: for each t, sin and cos of 2 pi t by
+// sincos_turns (out[4i], out[4i + 1]) and by sincospif (out[4i + 2], + 3).
+__global__ void k_selftest_sincos(const float* __restrict__ t, int64_t n, float* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s, c, s2, c2;
+    sincos_turns(t[i], s, c);
+    sincospif(2.0f * t[i], &s2, &c2);
+    out[4 * i] = s;
+    out[4 * i + 1] = c;
+    out[4 * i + 2] = s2;
+    out[4 * i + 3] = c2;
+}
+
+cudaError_t launch_selftest_sincos(const float* t, int64_t n, float* out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_selftest_sincos<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(t, n, out);
     return cudaGetLastError();
 }
 
@@ -1047,6 +1598,50 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_gemm_f16x3<2>, ga, tm[0], tm[1]);
+}
+
+cudaError_t tc_launch_gemm_rays(const float4* cpos, const float4* cw, const int64_t* kb_cell0, const int32_t* kb_ncell,
+                                const float2* qy, int nyg, const float2* qz, int nzg, const float wscale[4],
+                                const void* items, const int32_t* unit_item0, int grid, int kcb, double* P, double* F,
+                                int64_t lo_off, const AxisMap& ax, int nch, const double scale[4], int32_t* err,
+                                uint64_t limit_ns, cudaStream_t s)
+{
+    if (nyg < 0 || nyg > 16 || nzg < 0 || nzg > 64 || nch != 4 || kcb < 1) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(k_gemm_ray_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, RF_SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    GemmArgs ga;
+    memset(&ga, 0, sizeof(ga));
+    ga.items = (const GemmItem*)items;
+    ga.unit_item0 = unit_item0;
+    ga.kcb = kcb;
+    ga.P = P;
+    ga.F = F;
+    ga.lo_off = lo_off;
+    ga.ax = ax;
+    ga.nch = nch;
+    for (int c = 0; c < 4; ++c) ga.scale[c] = (float)scale[c];
+    ga.err = err;
+    ga.limit_ns = limit_ns;
+    ga.mtiles = 1;
+    ga.ntiles = 1;
+    RayFusedArgs ra;
+    memset(&ra, 0, sizeof(ra));
+    ra.cpos = cpos;
+    ra.cw = cw;
+    ra.kb_cell0 = kb_cell0;
+    ra.kb_ncell = kb_ncell;
+    ra.wscale = make_float4(wscale[0], wscale[1], wscale[2], wscale[3]);
+    ra.nyg = nyg;
+    ra.nzg = nzg;
+    for (int a = 0; a < nyg; ++a) ra.qy[a] = qy[a];
+    for (int b = 0; b < nzg; ++b) ra.qz[b] = qz[b];
+    if (grid <= 0) return cudaSuccess;
+    k_gemm_ray_fused<<<grid, TC_THREADS, RF_SMEM, s>>>(ga, ra);
+    return cudaGetLastError();
 }
 
 cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, const AxisMap& ax, int ntiles, int nch,

@@ -991,6 +991,28 @@ nms_status nms_selftest_bounded_wait(int64_t limit_us, void* cuda_stream)
     return NMS_OK;
 }
 
+nms_status nms_selftest_sincos(int64_t n, const float* t, float* out, void* cuda_stream)
+{
+    set_error("");
+    if (n < 0 || (n > 0 && (!t || !out))) return fail(NMS_ERR_INVALID_ARG, "need n >= 0 and host arrays t, out");
+    if (n == 0) return NMS_OK;
+    int dev_count = 0;
+    if (cudaGetDeviceCount(&dev_count) != cudaSuccess || dev_count < 1) {
+        cudaGetLastError();
+        return fail(NMS_ERR_CUDA, "no CUDA device available (libnms has no CPU fallback)");
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    float* d = nullptr;
+    NMS_CUDA_TRY(tmp_alloc((void**)&d, (size_t)n * 5 * sizeof(float), s));
+    cudaError_t e = cudaMemcpyAsync(d, t, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_selftest_sincos(d, n, d + n, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d + n, (size_t)n * 4 * sizeof(float), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "sincos self-test");
+    return NMS_OK;
+}
+
 nms_status nms_plan_destroy(nms_plan_t plan)
 {
     if (!plan) return NMS_OK;

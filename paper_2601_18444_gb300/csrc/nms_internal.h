@@ -220,6 +220,7 @@ void tc_release(Plan& p);
 
 int device_sm_count();
 cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t* err, cudaStream_t s);
+cudaError_t launch_selftest_sincos(const float* t, int64_t n, float* out, cudaStream_t s);
 
 // Device memory of plans: a per-device library memory pool that keeps up to
 // 16 GiB of freed memory for later plans (creating and destroying a plan

@@ -42,6 +42,11 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
                            const int32_t* unit_item0, int grid, int kcb, double* P, double* F, int64_t lo_off,
                            const AxisMap& ax, int nch, const double scale[4], int32_t* err, uint64_t limit_ns, int mode,
                            cudaStream_t s);
+cudaError_t tc_launch_gemm_rays(const float4* cpos, const float4* cw, const int64_t* kb_cell0, const int32_t* kb_ncell,
+                                const float2* qy, int nyg, const float2* qz, int nzg, const float wscale[4],
+                                const void* items, const int32_t* unit_item0, int grid, int kcb, double* P, double* F,
+                                int64_t lo_off, const AxisMap& ax, int nch, const double scale[4], int32_t* err,
+                                uint64_t limit_ns, cudaStream_t s);
 cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, const AxisMap& ax, int ntiles, int nch,
                              const double scale[4], double* F, int64_t lo_off, cudaStream_t s);
 size_t tc_item_bytes();
@@ -142,6 +147,10 @@ struct TcState {
     // (i2 < nz = k2), and both coordinates are the projection u of a cell on
     // the ray; with n_theta even only the rays theta < pi are computed
     bool rays = false;
+    // rays with one weight set and one A and one B tile: the operands are
+    // generated in the GEMM's shared memory (k_gemm_ray_fused), no tables
+    bool fused = false;
+    std::vector<float2> h_qy, h_qz;   // fused: the GEMM nodes in turns, passed as kernel parameters
     int n_rays = 0, ray_mirror = 0;
     double2* d_ray_sc = nullptr; // [n_rays] (sin theta, cos theta)
     float4* d_ray_sc_tf = nullptr;   // the same as two-float (sin hi, lo, cos hi, lo)
@@ -335,7 +344,7 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
                     const int up = ((splits + m - 1) / m) * m;
                     if (up <= 2 * splits && up <= nkb_p / std::max(1, 2 * t.kcb)) splits = up;
                 }
-                if (splits == 1) {
+                if (splits == 1 && !t.fused) {
                     // one item per tile spans the piece: the GEMM adds it into F directly
                     const int32_t direct = -1 - pc.out;
                     const int32_t first = started[pc.out] ? 0 : 1;
@@ -661,7 +670,7 @@ int tc_tuned_items_per_sm(const Plan& p)
 void tc_form_info(const Plan& p, int32_t* form, int32_t* mirror_y, int32_t* mirror_z)
 {
     const TcState* t = (const TcState*)p.tc_state;
-    *form = t ? t->mode : -1;
+    *form = t ? (t->fused ? 3 : t->mode) : -1;
     *mirror_y = t ? t->ax.my : 0;
     *mirror_z = t ? t->ax.mz : 0;
 }
@@ -753,6 +762,20 @@ nms_status tc_setup(Plan& p)
     }
     nms_status st;
     if ((st = upload(&t->d_qy, qy)) || (st = upload(&t->d_qz, qz))) return st;
+    // rays whose GEMM is one 128 x 128 tile per slot (one weight set, at
+    // most 16 x 64 |q| nodes): operands generated in shared memory, with
+    // eight work items per SM so the many equal splits balance
+    // (NMS_RAY_FUSED=0 keeps the tables, for comparisons)
+    {
+        const char* fe = getenv("NMS_RAY_FUSED");
+        t->fused = t->rays && t->nch == 4 && t->mtiles == 1 && t->ntiles == 1 && t->mode == 0 &&
+                   !(fe && atoi(fe) == 0);
+        if (t->fused) {
+            t->h_qy = qy;
+            t->h_qz = qz;
+            if (p.opt.split_k <= 0) t->items_per_sm = 8;
+        }
+    }
     t->n_slots = p.n_rot;
     if (t->rays) {
         // theta_j = 2 pi j / n1; with n1 even the ray theta + pi is the
@@ -843,9 +866,15 @@ nms_status tc_setup(Plan& p)
         total_kb = (n + kbc - 1) / kbc;
     }
     total_kb *= t->R_b;
-    t->tab_kb = std::max<int64_t>(1, std::min<int64_t>(total_kb, budget / per_kb));
-    p.tab_bytes = (size_t)t->tab_kb * per_kb;
-    NMS_CUDA_TRY(plan_malloc(&p.d_tab, p.tab_bytes));
+    if (t->fused) {
+        // no tables: a batch's slots form one chunk (one GEMM launch)
+        t->tab_kb = std::max<int64_t>(1, std::min<int64_t>(total_kb, (int64_t)1 << 30));
+        p.tab_bytes = 0;
+    } else {
+        t->tab_kb = std::max<int64_t>(1, std::min<int64_t>(total_kb, budget / per_kb));
+        p.tab_bytes = (size_t)t->tab_kb * per_kb;
+        NMS_CUDA_TRY(plan_malloc(&p.d_tab, p.tab_bytes));
+    }
     // schedules: a full rotation batch and the remainder
     if (p.opt.autotune && !t->rays) {   // the tuner's error check reads the Cartesian pixel layout
         if ((st = tc_autotune(p, *t))) return st;
@@ -920,6 +949,20 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
         if (t.d_Gdil_b) NMS_CUDA_TRY(cudaMemsetAsync(t.d_Gdil_b, 0, (size_t)nrl * nS * 16 * npg * sizeof(double), s));
         for (const OutBatch& ob : S.batches) {
             for (const Chunk& ch : ob.chunks) {
+                if (t.fused) {
+                    p.timer.begin(ST_GEMM);
+                    NMS_CUDA_TRY(tc_launch_gemm_rays(t.d_cpos_b, t.d_cw_b, S.d_kb_cell0 + ch.kb_off,
+                                                     S.d_kb_ncell + ch.kb_off, t.h_qy.data(), t.ax.nyg, t.h_qz.data(),
+                                                     t.ax.nzg, wscale, (const char*)S.d_items + ch.item_off * tc_item_bytes(),
+                                                     S.d_units + ch.unit_off, ch.grid, t.kcb, t.d_P, t.d_Fb, lo_off,
+                                                     t.ax, t.nch, scale, p.d_err, limit, s));
+                    p.timer.end(ST_GEMM, 1);
+                    p.timer.begin(ST_REDUCE);
+                    NMS_CUDA_TRY(tc_launch_reduce(t.d_P, (const char*)S.d_reds + ch.red_off * tc_red_bytes(), ch.n_red,
+                                                  t.ax, t.ntiles, t.nch, scale, t.d_Fb, lo_off, s));
+                    p.timer.end(ST_REDUCE, ch.n_red > 0 ? 1 : 0);
+                    continue;
+                }
                 p.timer.begin(ST_TABLES);
                 NMS_CUDA_TRY(tc_launch_tables(t.d_cpos_b, t.d_cw_b, t.wstride, t.nch, S.d_kb_cell0 + ch.kb_off,
                                               S.d_kb_ncell + ch.kb_off, ch.nkb, t.d_qy + t.ax.hy, t.ax.nyg,

@@ -118,6 +118,15 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r)
         : "memory");
 }
 
+// 4 consecutive 32-bit columns of this thread's lane
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const float* v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3]))
+                 : "memory");
+}
+
 // this thread's tensor-memory stores have completed
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 

@@ -92,6 +92,7 @@ SIGNATURES = {
     "nms_plan_info": (ctypes.c_int, [_V] + [ctypes.POINTER(ctypes.c_int32)] * 6),
     "nms_select_set": (ctypes.c_int, [_V, ctypes.c_int32]),
     "nms_selftest_bounded_wait": (ctypes.c_int, [ctypes.c_int64, _V]),
+    "nms_selftest_sincos": (ctypes.c_int, [ctypes.c_int64, _V, _V, _V]),
     "nms_plan_destroy": (ctypes.c_int, [_V]),
     "nms_last_error": (ctypes.c_char_p, []),
     "nms_version": (ctypes.c_char_p, []),
@@ -525,6 +526,15 @@ def nms_selftest_bounded_wait(limit_us, stream=None):
     """Run the bounded-wait self-test; raises NmsError (status TIMEOUT) when the
     device wait gave up, which is the expected outcome."""
     _check(load().nms_selftest_bounded_wait(int(limit_us), ctypes.c_void_p(stream or 0)))
+
+
+def nms_selftest_sincos(t, stream=None):
+    """(n, 4) float32: sin, cos of 2 pi t by the fused ray form's routine, then by sincospif."""
+    t = np.ascontiguousarray(t, dtype=np.float32).ravel()
+    out = np.empty((t.size, 4), dtype=np.float32)
+    _check(load().nms_selftest_sincos(t.size, t.ctypes.data_as(_V), out.ctypes.data_as(_V),
+                                      ctypes.c_void_p(stream or 0)))
+    return out
 
 
 def plan_from_field(field, grid, opt=None, rot=None, stream=None):

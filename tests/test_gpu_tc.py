@@ -5,7 +5,7 @@ responses within the bound that implies, I(q) within 1e-5.  Shapes cover
 several tiles with ragged tails in every GEMM dimension (q_y rows, q_z
 columns, cells), a single cell, objects with the dilute/interference split,
 rotation averages, the coherent q = 0 pixel, and the full-size box workload
-on sampled pixels.
+on sampled pixels and on whole bins of its I(q).
 """
 import numpy as np
 import pytest
@@ -133,6 +133,36 @@ def test_tc_full_box_sampled_pixels():
     F_ref = S.dsft(f.pos[:, 1], f.pos[:, 2], w, g[0][idx], g[1][idx])
     err = amp_error(F[:, idx], F_ref, np.abs(w).sum(1))
     assert np.all(err <= AMP_TOL), err
+
+
+def test_tc_full_box_iq_bins():
+    # the same full-size workload through the unpolarized and spin-flip images
+    # and their 128-bin I(q) (bins of width 2/128 up to |q| = 2): pixel counts
+    # and mean |q| of every bin against the oracle's binning, and I(q) of
+    # seven whole bins -- the four innermost (most coherent), 16, 63 and the
+    # outermost (largest phases) -- from the oracle's amplitudes of every
+    # pixel in them (5,352 of 262,144)
+    f = I.box_field(256, 256, 64, a=2.0, n_modes=64, kmax=0.2, n_pores=200, seed=1)
+    kw = dict(kind="cartesian", n0=512, n1=512, lo0=-2.0, hi0=2.0, lo1=-2.0, hi1=2.0)
+    plan = run(f, kw)
+    edges = np.linspace(0.0, 2.0, 129)
+    g = og(kw)
+    _, cr, qr = S.azimuthal_average_cartesian(np.zeros(512 * 512), g[4], edges)
+    bins = np.array([0, 1, 2, 3, 16, 63, 127])
+    sel = np.flatnonzero(np.isin(np.searchsorted(edges, g[4], side="right") - 1, bins))
+    assert sel.size == cr[bins].sum() == 5352
+    w = S.cell_weights(f.vol, f.nuc, f.mag, np.eye(3))
+    F_ref = S.dsft(f.pos[:, 1], f.pos[:, 2], w, g[0][sel], g[1][sel])
+    ref = S.responses(F_ref, g[2][sel], g[3][sel])
+    for name in ("UNPOL", "SF"):
+        Ig, cg, qg = nms.nms_azimuthal_average(plan, nms.nms_response(plan, name), edges)
+        assert np.array_equal(cg, cr)
+        np.testing.assert_allclose(qg[cg > 0], qr[cr > 0], rtol=1e-13)
+        Ir, cs, _ = S.azimuthal_average_cartesian(ref[name], g[4][sel], edges)
+        assert np.array_equal(cs[bins], cr[bins])
+        assert np.all(Ir[bins] > 1e-8 * Ir[0])           # every chosen bin is under the 1e-5 bar
+        rel = np.abs(Ig[bins] - Ir[bins]) / np.abs(Ir[bins])
+        assert np.all(rel <= IQ_TOL), (name, rel)
 
 
 def test_tc_ensemble_many_chunks_dilute_interference():

@@ -11,7 +11,11 @@ rotation averages, many slots in several batches with a remainder batch, a
 small table workspace (many chunks), several objects summed as one (their
 centres applied), the dilute, total and interference parts of objects,
 weight sets (loop mode), and the responses and azimuthal average of the
-polar image.
+polar image.  A ray whose GEMM is one 128 x 128 tile (one weight set, at
+most 16 x 64 |q| nodes) runs the fused form (operands generated in shared
+memory): it is checked against the oracle and against the table form, at
+every TMEM chunk length, with long work items (renormalised running sums)
+and at the coherent |q| = 0 node.
 """
 import numpy as np
 import pytest
@@ -83,14 +87,17 @@ def test_polar_tc_responses_and_average():
             assert np.max(np.abs(Ig)) <= resp_tol(f)
 
 
-def test_polar_tc_rotations_many_slots_small_workspace():
+@pytest.mark.parametrize("fused", ["1", "0"])
+def test_polar_tc_rotations_many_slots_small_workspace(fused, monkeypatch):
     # 3 rotations x 100 mirrored rays = 300 slots: several batches of at most
-    # 64 slots and a remainder batch; an 8 MB table workspace cuts each batch
-    # into many chunks
+    # 64 slots and a remainder batch; with tables (NMS_RAY_FUSED=0) an 8 MB
+    # workspace cuts each batch into many chunks
+    monkeypatch.setenv("NMS_RAY_FUSED", fused)
     f = I.small_random_field(3000, seed=91, extent=10.0)
     kw = dict(kind="polar", n0=70, n1=200, lo0=0.0, hi0=1.4)
     Rs = I.random_rotations(3, seed=92)
     plan = run(f, kw, rot=Rs, workspace_bytes=8 << 20)
+    assert nms.nms_plan_info(plan)["gemm_form"] == (3 if fused == "1" else 0)
     g = og(kw)
     acc = None
     for R in Rs:
@@ -214,7 +221,7 @@ def test_polar_tc_autotune_request_keeps_defaults():
     kw = dict(kind="polar", n0=30, n1=16, lo0=0.0, hi0=1.0)
     plan = run(f, kw, autotune=1)
     info = nms.nms_plan_info(plan)
-    assert info["kc_cells"] == 192 and info["items_per_sm"] == 1
+    assert info["kc_cells"] == 192 and info["items_per_sm"] == 8 and info["gemm_form"] == 3
     g = og(kw)
     F_ref = S.amplitudes(f, np.eye(3), g[0], g[1])
     assert np.all(amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f)) <= AMP_TOL)
@@ -267,3 +274,71 @@ def test_polar_tc_weight_sets_with_objects_and_rotations():
         for k in acc:
             for i, part in enumerate((nms.PART_TOTAL, nms.PART_DILUTE, nms.PART_INTERFERENCE)):
                 assert np.max(np.abs(nms.nms_response(plan, k, part) - acc[k][i])) <= tol, (s, k, part)
+
+
+def test_polar_tc_fused_matches_tables_and_oracle(monkeypatch):
+    # 1000 |q| nodes (15 full i1 nodes and a ragged 16th: the fused form's
+    # largest grid), 12 angles; the fused form and the table form each
+    # against the oracle, and against each other
+    f = I.small_random_field(5001, seed=71, extent=9.0)
+    kw = dict(kind="polar", n0=1000, n1=12, lo0=0.0, hi0=2.0)
+    g = og(kw)
+    F_ref = S.amplitudes(f, np.eye(3), g[0], g[1])
+    out = {}
+    for fused in ("1", "0"):
+        monkeypatch.setenv("NMS_RAY_FUSED", fused)
+        plan = run(f, kw)
+        assert nms.nms_plan_info(plan)["gemm_form"] == (3 if fused == "1" else 0)
+        out[fused] = nms.nms_get_amplitudes(plan)
+        assert np.all(amp_error(out[fused], F_ref, weight_sums(f)) <= AMP_TOL), fused
+    assert np.all(amp_error(out["1"], out["0"], weight_sums(f)) <= 2 * AMP_TOL)
+
+
+@pytest.mark.parametrize("kc", [64, 128, 192, 256])
+def test_polar_tc_fused_chunk_lengths_long_items(kc):
+    # one work item per SM (split_k = 1): ~15 k-blocks per item, so the
+    # running sums in tensor memory pass several renormalisations; every
+    # drain interval from one to four k-blocks
+    f = I.small_random_field(150000, seed=72, extent=20.0)
+    kw = dict(kind="polar", n0=64, n1=6, lo0=0.02, hi0=1.5)
+    plan = run(f, kw, kc_cells=kc, split_k=1)
+    info = nms.nms_plan_info(plan)
+    assert info["gemm_form"] == 3 and info["kc_cells"] == kc
+    g = og(kw)
+    F_ref = S.amplitudes(f, np.eye(3), g[0], g[1])
+    assert np.all(amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f)) <= AMP_TOL)
+
+
+@pytest.mark.parametrize("kc", [128, 192])
+def test_polar_tc_fused_coherent_q0(kc):
+    # all-positive constant weights and |q| from 0: the partial sums in the
+    # FP32 accumulator are as coherent as they can be
+    f = I.box_field(40, 40, 40, a=1.0, n_modes=4, seed=2, pores=False)
+    kw = dict(kind="polar", n0=9, n1=8, lo0=0.0, hi0=0.02)
+    plan = run(f, kw, kc_cells=kc)
+    assert nms.nms_plan_info(plan)["gemm_form"] == 3
+    g = og(kw)
+    F_ref = S.amplitudes(f, np.eye(3), g[0], g[1])
+    assert np.all(amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f)) <= AMP_TOL)
+
+
+def test_fused_form_sincos_against_exact_and_sincospif():
+    # the fused form's sine and cosine of 2 pi t (quarter-turn reduction and
+    # Taylor series) on reduced phases |t| <= 1/2: random and evenly spaced
+    # values, the quarter-turn boundaries and their neighbours, and tiny t
+    rng = np.random.default_rng(11)
+    edges = np.array([-0.5, -0.375, -0.25, -0.125, 0.0, 0.125, 0.25, 0.375, 0.5], dtype=np.float32)
+    near = np.concatenate([np.nextafter(edges, np.float32(1)), np.nextafter(edges, np.float32(-1))])
+    t = np.concatenate([rng.uniform(-0.5, 0.5, 400000), np.linspace(-0.5, 0.5, 40001), edges, near,
+                        [1e-30, -1e-30, 1e-8, -3e-6]]).astype(np.float32)
+    t = t[np.abs(t) <= 0.5]
+    out = nms.nms_selftest_sincos(t)
+    x = 2.0 * np.pi * t.astype(np.float64)
+    err = np.maximum(np.abs(out[:, 0] - np.sin(x)), np.abs(out[:, 1] - np.cos(x)))
+    err_ref = np.maximum(np.abs(out[:, 2] - np.sin(x)), np.abs(out[:, 3] - np.cos(x)))
+    assert err.max() <= 1.0e-7, err.max()                  # under one unit in the last place at 1
+    assert err.max() <= err_ref.max() + 6e-8, (err.max(), err_ref.max())
+    # exact at the quarter turns
+    q = nms.nms_selftest_sincos(np.array([0.0, 0.25, -0.25, 0.5, -0.5], dtype=np.float32))
+    np.testing.assert_array_equal(q[:, 0], [0.0, 1.0, -1.0, 0.0, 0.0])
+    np.testing.assert_array_equal(q[:, 1], [1.0, 0.0, 0.0, -1.0, -1.0])

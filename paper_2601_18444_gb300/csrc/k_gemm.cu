@@ -87,21 +87,26 @@ __device__ __forceinline__ float turns_reduced(float2 q, float xh, float xl)
 // Sterbenz), sin and cos of 2 pi r come from their Taylor series about 0
 // (odd terms to r^9, even terms to r^10: truncation below 2e-9 for
 // |2 pi r| <= pi/4), and the quadrant n mod 4 swaps and negates them.
-// Coefficients are (2 pi)^k / k! rounded once to FP32.  Error about one
-// unit in the last place (checked against exact values and sincospif).
+// Coefficients are (2 pi)^k / k! rounded once to FP32, times the power of
+// two SCALE (exact: the results come out scaled by SCALE at no cost).  Error
+// about one unit in the last place (checked against exact values and
+// sincospif).
+template <int SCALE = 1>
 __device__ __forceinline__ void sincos_turns(float t, float& sn, float& cs)
 {
+    static_assert(SCALE > 0 && (SCALE & (SCALE - 1)) == 0, "SCALE must be a power of two");
     constexpr double TP = 6.283185307179586476925286766559;
-    constexpr float S1 = (float)TP;
-    constexpr float S3 = (float)(-TP * TP * TP / 6.0);
-    constexpr float S5 = (float)(TP * TP * TP * TP * TP / 120.0);
-    constexpr float S7 = (float)(-TP * TP * TP * TP * TP * TP * TP / 5040.0);
-    constexpr float S9 = (float)(TP * TP * TP * TP * TP * TP * TP * TP * TP / 362880.0);
-    constexpr float C2 = (float)(-TP * TP / 2.0);
-    constexpr float C4 = (float)(TP * TP * TP * TP / 24.0);
-    constexpr float C6 = (float)(-TP * TP * TP * TP * TP * TP / 720.0);
-    constexpr float C8 = (float)(TP * TP * TP * TP * TP * TP * TP * TP / 40320.0);
-    constexpr float C10 = (float)(-TP * TP * TP * TP * TP * TP * TP * TP * TP * TP / 3628800.0);
+    constexpr float K = (float)SCALE;
+    constexpr float S1 = K * (float)TP;
+    constexpr float S3 = K * (float)(-TP * TP * TP / 6.0);
+    constexpr float S5 = K * (float)(TP * TP * TP * TP * TP / 120.0);
+    constexpr float S7 = K * (float)(-TP * TP * TP * TP * TP * TP * TP / 5040.0);
+    constexpr float S9 = K * (float)(TP * TP * TP * TP * TP * TP * TP * TP * TP / 362880.0);
+    constexpr float C2 = K * (float)(-TP * TP / 2.0);
+    constexpr float C4 = K * (float)(TP * TP * TP * TP / 24.0);
+    constexpr float C6 = K * (float)(-TP * TP * TP * TP * TP * TP / 720.0);
+    constexpr float C8 = K * (float)(TP * TP * TP * TP * TP * TP * TP * TP / 40320.0);
+    constexpr float C10 = K * (float)(-TP * TP * TP * TP * TP * TP * TP * TP * TP * TP / 3628800.0);
     const float qn = rintf(4.0f * t);
     const float r = fmaf(qn, -0.25f, t);
     const int n = (int)qn;
@@ -115,7 +120,7 @@ __device__ __forceinline__ void sincos_turns(float t, float& sn, float& cs)
     pc = fmaf(pc, r2, C6);
     pc = fmaf(pc, r2, C4);
     pc = fmaf(pc, r2, C2);
-    const float cr = fmaf(pc, r2, 1.0f);
+    const float cr = fmaf(pc, r2, K);
     // quadrant n: (sin, cos) = (s, c), (c, -s), (-s, -c), (-c, s)
     const bool swap = n & 1;
     const float a = swap ? cr : sr, b = swap ? sr : cr;
@@ -943,23 +948,20 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint64
 // cells 4 q4 .. + 3 (8-byte stores: a half-warp fills a 128-byte row) and the
 // eight A rows of coarse node a = r / 2 (four channels x cos, sin) for the
 // cells 4 q4 + 2h, + 1 (h = r mod 2; 4-byte stores: a warp fills a row).
+// Unlike the tables, B is not masked: a cell past the k-block's end has zero
+// weights in A, so its products vanish, and rows past the live nodes
+// (b >= nzg, a >= nyg) only feed output rows and columns nothing reads.
 __device__ __forceinline__ void ray_gen_block(uint8_t* st, const float* uh, const float* ul, float4 w0, float4 w1,
-                                              int nc, int q4, int r, float2 qb0, float2 qb1, float2 qa, float onb0,
-                                              float onb1, float ona)
+                                              int q4, int r, float2 qb0, float2 qb1, float2 qa)
 {
 #pragma unroll
     for (int jb = 0; jb < 2; ++jb) {
         const float2 q = jb ? qb1 : qb0;
-        const float on = jb ? onb1 : onb0;
         const int b = r + 32 * jb;
         float cs[4], sn[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const float live = 4 * q4 + u < nc ? on : 0.f;
-            sincos_turns(turns_reduced(q, uh[u], ul[u]), sn[u], cs[u]);
-            cs[u] *= live;
-            sn[u] *= live;
-        }
+        for (int u = 0; u < 4; ++u)
+            sincos_turns<(int)TC_SCALE>(turns_reduced(q, uh[u], ul[u]), sn[u], cs[u]);
         uint2 ch, cl, sh, sl;
         split4(cs[0], cs[1], cs[2], cs[3], ch, cl);
         split4(sn[0], sn[1], sn[2], sn[3], sh, sl);
@@ -976,10 +978,6 @@ __device__ __forceinline__ void ray_gen_block(uint8_t* st, const float* uh, cons
     float s0, c0, s1, c1;
     sincos_turns(turns_reduced(qa, u0h, u0l), s0, c0);
     sincos_turns(turns_reduced(qa, u1h, u1l), s1, c1);
-    c0 *= ona;
-    s0 *= ona;
-    c1 *= ona;
-    s1 *= ona;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const float x0 = c == 0 ? w0.x : c == 1 ? w0.y : c == 2 ? w0.z : w0.w;
@@ -1223,9 +1221,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const float2 qb0 = r < ra.nzg ? ra.qz[r] : zero2;
         const float2 qb1 = r + 32 < ra.nzg ? ra.qz[r + 32] : zero2;
         const float2 qa = (r >> 1) < ra.nyg ? ra.qy[r >> 1] : zero2;
-        const float onb0 = r < ra.nzg ? TC_SCALE : 0.f;
-        const float onb1 = r + 32 < ra.nzg ? TC_SCALE : 0.f;
-        const float ona = (r >> 1) < ra.nyg ? 1.f : 0.f;
         const uint32_t tb = taddr + ((uint32_t)(quad * 32) << 16) + (uint32_t)colh;
         int s = 0;
         uint32_t epar = 1u;                         // parity of the stage's previous "empty" phase
@@ -1285,7 +1280,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         ok = false;
                         break;
                     }
-                    ray_gen_block(sgen + s * TC_STAGE_BYTES, uh, ul, w0, w1, nc, q4, r, qb0, qb1, qa, onb0, onb1, ona);
+                    ray_gen_block(sgen + s * TC_STAGE_BYTES, uh, ul, w0, w1, q4, r, qb0, qb1, qa);
                     fence_proxy_async_smem();
                     mbar_arrive(&bar_full[s]);
                     if (++s == STG) {

@@ -1333,13 +1333,53 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 break;
             }
-            // the item's tile, unscaled, to its partial slot P[slot] (this
-            // form's schedule gives every item one; k_gemm_reduce combines
-            // them): each 8-column group of the sums straight from TMEM
             if (item.slot < 0) {
-                if (lane == 0) atomicExch(g.err, 4);
+                // an output of one piece: its amplitudes, rounded to FP32, go
+                // straight into F (FbView layout).  Rays mirror no axis, so
+                // lane p = 0 of each (cos, sin) row pair writes
+                // F = (cc - ss) - i (cs + sc), its partner lane holding sc, ss.
+                // This form's schedule sends outputs of several pieces through
+                // partial slots.
+                if (item.two) {
+                    if (lane == 0) atomicExch(g.err, 4);
+                    continue;
+                }
+                const AxisMap& ax = g.ax;
+                const int mg = quad * 32 + lane;
+                const int p = mg & 1, qi = mg >> 1;
+                const int ag = qi / g.nch, ch = qi & (g.nch - 1);
+                const int64_t mrows = (int64_t)g.nch * ax.ny;
+                float2* Fo = reinterpret_cast<float2*>(g.F) + (int64_t)(-1 - item.slot) * (ax.nz - ax.zs0) * mrows +
+                             ch + (int64_t)g.nch * (ax.hy + ag);
+                const bool act = p == 0 && ag < ax.nyg;
+                const float sc = g.scale[ch & 3];
+#pragma unroll
+                for (int cb = 0; cb < 4; ++cb) {
+                    float xh[8], xl[8];
+                    if (any) {
+                        tmem_ld8(tb + 256 + 8 * cb, xh);
+                        tmem_ld8(tb + 384 + 8 * cb, xl);
+                        tmem_wait_ld();
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) xh[i] = xl[i] = 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const uint64_t x = f2_add(f2_pack(xh[2 * u], xh[2 * u + 1]), f2_pack(xl[2 * u], xl[2 * u + 1]));
+                        const uint64_t y = __shfl_xor_sync(0xffffffffu, x, 1);
+                        const int bg = ((colh + 8 * cb) >> 1) + u;
+                        if (act && bg < ax.nzg) {
+                            const float cc = f2_lane0(x), cs = f2_lane1(x), scs = f2_lane0(y), ss = f2_lane1(y);
+                            Fo[(int64_t)(ax.hz + bg - ax.zs0) * mrows] = make_float2(sc * (cc - ss), -sc * (cs + scs));
+                        }
+                    }
+                }
                 continue;
             }
+            // the item's tile, unscaled, to its partial slot P[slot]
+            // (k_gemm_reduce combines them): each 8-column group of the sums
+            // straight from TMEM
             float4* out = reinterpret_cast<float4*>(g.P) + (int64_t)item.slot * (TC_BM * TC_BN / 2) +
                           (int64_t)(colh >> 1) * TC_BM + quad * 32 + lane;
 #pragma unroll

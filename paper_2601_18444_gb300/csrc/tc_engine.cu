@@ -344,7 +344,7 @@ static nms_status build_schedule(const Plan& p, const TcState& t, const std::vec
                     const int up = ((splits + m - 1) / m) * m;
                     if (up <= 2 * splits && up <= nkb_p / std::max(1, 2 * t.kcb)) splits = up;
                 }
-                if (splits == 1 && !t.fused) {
+                if (splits == 1 && !(t.fused && out_two[o0 + pc.out])) {
                     // one item per tile spans the piece: the GEMM adds it into F directly
                     const int32_t direct = -1 - pc.out;
                     const int32_t first = started[pc.out] ? 0 : 1;

@@ -89,6 +89,22 @@ def test_invalid_arguments_are_reported_without_gpu():
             nms.nms_correlation([0.0, 1.0], [1.0, 1.0], [1.0])
 
 
+def test_sincos_selftest_checks_arguments_before_the_device():
+    lib = nms.load()
+    assert lib.nms_selftest_sincos(-1, None, None, None) == 1            # INVALID_ARG
+    assert lib.nms_selftest_sincos(3, None, None, None) == 1             # NULL arrays with n > 0
+    assert lib.nms_selftest_sincos(0, None, None, None) == 0             # nothing to do
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if not has_gpu:   # valid arguments, no device: refused, no CPU fallback
+        with pytest.raises(nms.NmsError) as e:
+            nms.nms_selftest_sincos(np.zeros(4, dtype=np.float32))
+        assert e.value.status == 3
+
+
 def test_plan_create_argument_checks_come_before_the_device():
     # the host-side checks of nms_plan_create run before any CUDA call, so each
     # bad argument gives INVALID_ARG (1), not CUDA (3), with or without a GPU

@@ -342,3 +342,16 @@ def test_fused_form_sincos_against_exact_and_sincospif():
     q = nms.nms_selftest_sincos(np.array([0.0, 0.25, -0.25, 0.5, -0.5], dtype=np.float32))
     np.testing.assert_array_equal(q[:, 0], [0.0, 1.0, -1.0, 0.0, 0.0])
     np.testing.assert_array_equal(q[:, 1], [1.0, 0.0, 0.0, -1.0, -1.0])
+
+
+@pytest.mark.parametrize("n0,form", [(1024, 3), (1025, 0)])
+def test_polar_tc_fused_form_boundary(n0, form):
+    # 1024 |q| nodes (16 x 64) is the largest ray that is one tile (fused
+    # form); one node more needs a second A tile and takes the tables
+    f = I.small_random_field(3001, seed=73, extent=8.0)
+    kw = dict(kind="polar", n0=n0, n1=4, lo0=0.0, hi0=2.5)
+    plan = run(f, kw)
+    assert nms.nms_plan_info(plan)["gemm_form"] == form
+    g = og(kw)
+    F_ref = S.amplitudes(f, np.eye(3), g[0], g[1])
+    assert np.all(amp_error(nms.nms_get_amplitudes(plan), F_ref, weight_sums(f)) <= AMP_TOL)

@@ -925,11 +925,24 @@ constexpr int RF_CELL_BYTES = 64 * 32;   // per slot: 64 float4 positions, then 
 constexpr int RF_WORKERS = 16 * 32;
 constexpr int RF_SMEM = TC_STAGES * TC_STAGE_BYTES + RF_CELL_SLOTS * RF_CELL_BYTES + 1024;
 
+constexpr int RF_MAX_SLOTS = 64;     // slots per launch when the loader projects
+constexpr int RF_PROJ_LAG = 2;       // k-blocks between a slot's copy and its projection
+
 struct RayFusedArgs {
-    const float4* cpos;           // (u hi, u lo, u hi, u lo) per cell of the stacked slot arrays
-    const float4* cw;             // weights (N, Mx, My, Mz) per cell (one set)
+    // project = 0: cpos holds (u hi, u lo, u hi, u lo) and cw the weights per
+    // cell of the stacked slot arrays, indexed by kb_cell0.  project = 1: cpos
+    // holds the rotated two-float (Y hi, Y lo, Z hi, Z lo) and cw the rotated
+    // weights once per rotation ([n_rot][n_cells]); k-block cell c0 = rl
+    // n_cells + c of slot slot0 + rl (rotation slot / n_rays, ray slot mod
+    // n_rays) is read at rotation row c, and the loader warp projects it,
+    // u = Y sin theta + Z cos theta in two-float (ray_sc: sin hi, lo, cos hi, lo).
+    const float4* cpos;
+    const float4* cw;
     const int64_t* kb_cell0;      // first cell of each k-block of the launch
     const int32_t* kb_ncell;      // its cells (<= 64)
+    const float4* ray_sc;         // project: [n_rays]
+    int64_t n_cells;
+    int project, slot0, n_rays, n_rl;
     float4 wscale;                // per-channel weight scale (as in k_tables)
     int nyg, nzg;                 // live nodes: coarse (A rows, <= 16), fine (B rows, <= 64)
     float2 qy[16];                // coarse nodes lo + 64 i1 dq in turns (two-float)
@@ -1068,7 +1081,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __shared__ __align__(8) uint64_t bar_acc_full;
     __shared__ __align__(8) uint64_t bar_acc_empty;
     __shared__ __align__(8) uint64_t bar_final;
+    __shared__ __align__(8) uint64_t bar_raw_full[RF_CELL_SLOTS];   // project: a slot's copy landed
     __shared__ int s_nc[RF_CELL_SLOTS];
+    __shared__ int s_rl[RF_CELL_SLOTS];
+    __shared__ float4 s_sc[RF_MAX_SLOTS];
     __shared__ uint32_t s_taddr;
     __shared__ volatile int s_abort;
 
@@ -1087,6 +1103,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int s = 0; s < RF_CELL_SLOTS; ++s) {
             mbar_init(&bar_cell_full[s], 1);
             mbar_init(&bar_cell_empty[s], RF_WORKERS);
+            mbar_init(&bar_raw_full[s], 1);
         }
         mbar_init(&bar_acc_full, 1);
         mbar_init(&bar_acc_empty, TC_EPI_WARPS);
@@ -1094,6 +1111,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (ra.project && threadIdx.x < ra.n_rl) s_sc[threadIdx.x] = ra.ray_sc[(ra.slot0 + threadIdx.x) % ra.n_rays];
     if (warp == 1) {
         tc_alloc<1>(smem_u32(&s_taddr), 512);
         tc_relinquish<1>();
@@ -1107,11 +1125,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ---------------- cell loader: bulk copies of each k-block's cells.
         // The warp reads the k-block descriptors 32 at a time (lane l holds
         // block kb0 + 32 i + l), so the copies never wait on those loads;
-        // every lane follows the ring, lane 0 issues.
-        int64_t i = 0;                      // k-block sequence number
+        // every lane follows the ring, lane 0 issues.  With project = 1 the
+        // copy brings the rotated (Y, Z) and the warp replaces them by the
+        // projection u on the slot's ray RF_PROJ_LAG k-blocks later, then
+        // releases the slot to the workers.
+        int64_t i = 0;                      // k-block sequence number (copies issued)
         int cs = 0;                         // its cell slot
         uint32_t par = 1u;                  // parity of the slot's previous "empty" phase
+        int64_t jp = 0;                     // project: k-blocks projected
+        int csp = 0;
+        uint32_t ppar = 0u;
         bool ok = true;
+        auto project_next = [&]() -> bool {
+            if (!warp_wait(&bar_raw_full[csp], ppar, g.limit_ns, &s_abort)) return false;
+            const int nc = s_nc[csp];
+            const float4 sc = s_sc[s_rl[csp]];
+            uint8_t* cl = cells + csp * RF_CELL_BYTES;
+            for (int k = lane; k < nc; k += 32) {
+                const float4 yz = *reinterpret_cast<const float4*>(cl + 16 * k);
+                // u = Y sin theta + Z cos theta: two two-float products and a TwoSum
+                const float p1 = sc.x * yz.x, p2 = sc.z * yz.z;
+                const float e1 = fmaf(sc.x, yz.x, -p1) + fmaf(sc.x, yz.y, sc.y * yz.x);
+                const float e2 = fmaf(sc.z, yz.z, -p2) + fmaf(sc.z, yz.w, sc.w * yz.z);
+                const float sm = p1 + p2;
+                const float bb = sm - p1;
+                const float e = ((p1 - (sm - bb)) + (p2 - bb)) + (e1 + e2);
+                const float uh = sm + e;
+                *reinterpret_cast<float2*>(cl + 16 * k) = make_float2(uh, e - (uh - sm));
+            }
+            fence_proxy_async_smem();       // these writes precede the slot's next bulk copy
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_cell_full[csp]);
+            ++jp;
+            if (++csp == RF_CELL_SLOTS) {
+                csp = 0;
+                ppar ^= 1u;
+            }
+            return true;
+        };
         for (int it = it_begin; it < it_end && ok; ++it) {
             const GemmItem item = g.items[it];
             for (int base = item.kb0; base < item.kb1 && ok; base += 32) {
@@ -1123,23 +1174,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const int64_t c0 = __shfl_sync(0xffffffffu, my_c0, j);
                     const int nc = __shfl_sync(0xffffffffu, my_nc, j);
                     if (!warp_wait(&bar_cell_empty[cs], par, g.limit_ns, &s_abort)) {
-                        if (lane == 0) {
-                            s_abort = 1;
-                            atomicExch(g.err, 1);
-                        }
                         ok = false;
                         break;
                     }
                     if (lane == 0) {
                         s_nc[cs] = nc;
+                        int64_t src = c0;
+                        uint64_t* landed = &bar_cell_full[cs];
+                        if (ra.project) {
+                            const int64_t rl = c0 / ra.n_cells;
+                            const int slot = ra.slot0 + (int)rl;
+                            src = (int64_t)(slot / ra.n_rays) * ra.n_cells + (c0 - rl * ra.n_cells);
+                            s_rl[cs] = (int)rl;
+                            landed = &bar_raw_full[cs];
+                        }
                         uint8_t* dst = cells + cs * RF_CELL_BYTES;
                         if (nc > 0) {
-                            mbar_arrive_expect_tx(&bar_cell_full[cs], (uint32_t)nc * 32u);
-                            bulk_g2s(smem_u32(dst), ra.cpos + c0, (uint32_t)nc * 16u, &bar_cell_full[cs]);
-                            bulk_g2s(smem_u32(dst + RF_CELL_BYTES / 2), ra.cw + c0, (uint32_t)nc * 16u,
-                                     &bar_cell_full[cs]);
+                            mbar_arrive_expect_tx(landed, (uint32_t)nc * 32u);
+                            bulk_g2s(smem_u32(dst), ra.cpos + src, (uint32_t)nc * 16u, landed);
+                            bulk_g2s(smem_u32(dst + RF_CELL_BYTES / 2), ra.cw + src, (uint32_t)nc * 16u, landed);
                         } else {
-                            mbar_arrive(&bar_cell_full[cs]);
+                            mbar_arrive(landed);
                         }
                     }
                     __syncwarp();
@@ -1148,13 +1203,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         cs = 0;
                         par ^= 1u;
                     }
+                    if (ra.project && i - jp > RF_PROJ_LAG && !project_next()) {
+                        ok = false;
+                        break;
+                    }
                 }
             }
         }
-        // copies in flight land before the CTA exits (bounded)
+        while (ok && ra.project && jp < i)
+            if (!project_next()) ok = false;
+        if (!ok && lane == 0) {
+            s_abort = 1;
+            atomicExch(g.err, 1);
+        }
+        // copies in flight land before the CTA exits (bounded): the last
+        // RF_CELL_SLOTS issued; with project only those not yet projected
         if (lane == 0)
-            for (int64_t k = (i > RF_CELL_SLOTS ? i - RF_CELL_SLOTS : 0); k < i; ++k)
-                mbar_wait_drain(&bar_cell_full[(int)(k % RF_CELL_SLOTS)], (uint32_t)((k / RF_CELL_SLOTS) & 1));
+            for (int64_t k = (i > RF_CELL_SLOTS ? i - RF_CELL_SLOTS : 0); k < i; ++k) {
+                if (ra.project && k < jp) continue;
+                uint64_t* bar = ra.project ? &bar_raw_full[(int)(k % RF_CELL_SLOTS)] : &bar_cell_full[(int)(k % RF_CELL_SLOTS)];
+                mbar_wait_drain(bar, (uint32_t)((k / RF_CELL_SLOTS) & 1));
+            }
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer: one accumulator pair (D0, D1)
@@ -1636,12 +1705,14 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
 }
 
 cudaError_t tc_launch_gemm_rays(const float4* cpos, const float4* cw, const int64_t* kb_cell0, const int32_t* kb_ncell,
-                                const float2* qy, int nyg, const float2* qz, int nzg, const float wscale[4],
-                                const void* items, const int32_t* unit_item0, int grid, int kcb, double* P, double* F,
-                                int64_t lo_off, const AxisMap& ax, int nch, const double scale[4], int32_t* err,
-                                uint64_t limit_ns, cudaStream_t s)
+                                const RayProjection& pr, const float2* qy, int nyg, const float2* qz, int nzg,
+                                const float wscale[4], const void* items, const int32_t* unit_item0, int grid, int kcb,
+                                double* P, double* F, int64_t lo_off, const AxisMap& ax, int nch,
+                                const double scale[4], int32_t* err, uint64_t limit_ns, cudaStream_t s)
 {
     if (nyg < 0 || nyg > 16 || nzg < 0 || nzg > 64 || nch != 4 || kcb < 1) return cudaErrorInvalidValue;
+    if (pr.ray_sc && (pr.n_rl < 1 || pr.n_rl > RF_MAX_SLOTS || pr.n_rays < 1 || pr.n_cells < 1))
+        return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
         const cudaError_t e = cudaFuncSetAttribute(k_gemm_ray_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, RF_SMEM);
@@ -1669,6 +1740,12 @@ cudaError_t tc_launch_gemm_rays(const float4* cpos, const float4* cw, const int6
     ra.cw = cw;
     ra.kb_cell0 = kb_cell0;
     ra.kb_ncell = kb_ncell;
+    ra.project = pr.ray_sc ? 1 : 0;
+    ra.ray_sc = pr.ray_sc;
+    ra.n_cells = pr.n_cells;
+    ra.slot0 = pr.slot0;
+    ra.n_rays = pr.n_rays;
+    ra.n_rl = pr.n_rl;
     ra.wscale = make_float4(wscale[0], wscale[1], wscale[2], wscale[3]);
     ra.nyg = nyg;
     ra.nzg = nzg;

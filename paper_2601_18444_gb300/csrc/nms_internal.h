@@ -219,6 +219,15 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s);
 void tc_release(Plan& p);
 
 int device_sm_count();
+// Fused ray GEMM: with ray_sc set, cpos / cw are the cells rotated once per
+// rotation ([n_rot][n_cells]) and the kernel projects them on the rays of
+// slots slot0 .. slot0 + n_rl - 1 (n_rl <= 64); ray_sc = null: cpos / cw are
+// the per-slot projections of the batch.
+struct RayProjection {
+    const float4* ray_sc = nullptr;   // [n_rays] (sin hi, lo, cos hi, lo)
+    int64_t n_cells = 0;
+    int slot0 = 0, n_rays = 0, n_rl = 0;
+};
 cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t* err, cudaStream_t s);
 cudaError_t launch_selftest_sincos(const float* t, int64_t n, float* out, cudaStream_t s);
 

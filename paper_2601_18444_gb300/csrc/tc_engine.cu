@@ -43,10 +43,10 @@ cudaError_t tc_launch_gemm(const void* tab, int64_t nkb, int mtiles, int ntiles,
                            const AxisMap& ax, int nch, const double scale[4], int32_t* err, uint64_t limit_ns, int mode,
                            cudaStream_t s);
 cudaError_t tc_launch_gemm_rays(const float4* cpos, const float4* cw, const int64_t* kb_cell0, const int32_t* kb_ncell,
-                                const float2* qy, int nyg, const float2* qz, int nzg, const float wscale[4],
-                                const void* items, const int32_t* unit_item0, int grid, int kcb, double* P, double* F,
-                                int64_t lo_off, const AxisMap& ax, int nch, const double scale[4], int32_t* err,
-                                uint64_t limit_ns, cudaStream_t s);
+                                const RayProjection& pr, const float2* qy, int nyg, const float2* qz, int nzg,
+                                const float wscale[4], const void* items, const int32_t* unit_item0, int grid, int kcb,
+                                double* P, double* F, int64_t lo_off, const AxisMap& ax, int nch,
+                                const double scale[4], int32_t* err, uint64_t limit_ns, cudaStream_t s);
 cudaError_t tc_launch_reduce(const double* P, const void* reds, int n_red, const AxisMap& ax, int ntiles, int nch,
                              const double scale[4], double* F, int64_t lo_off, cudaStream_t s);
 size_t tc_item_bytes();
@@ -934,25 +934,41 @@ nms_status tc_amplitudes(Plan& p, cudaStream_t s)
     for (int rb0 = 0; rb0 < t.n_slots; rb0 += t.R_b) {
         const int nrl = std::min(t.R_b, t.n_slots - rb0);
         const Schedule& S = nrl == t.R_b ? t.full : t.last;
-        p.timer.begin(ST_PREP);
-        // the batch's slots in one launch (rotation, or rotation x ray, rb0 + rl into slot rl)
-        if (t.rays && t.d_rpos)
-            NMS_CUDA_TRY(launch_prep_ray_from_rot(p, t.d_rpos, t.d_rw, (int64_t)p.n_rot * p.n_cells, t.d_ray_sc_tf,
-                                                  t.n_rays, rb0, nrl, t.d_cpos_b, t.d_cw_b, t.wstride, s));
-        else if (t.rays)
-            NMS_CUDA_TRY(launch_prep_ray_batch(p, t.d_rot, t.d_ray_sc, t.n_rays, rb0, nrl, !t.objects, t.d_cpos_b,
-                                               t.d_cw_b, t.wstride, s));
-        else
-            NMS_CUDA_TRY(launch_prep_rot_batch(p, t.d_rot, rb0, nrl, !t.objects, t.d_cpos_b, t.d_cw_b, t.wstride, s));
-        p.timer.end(ST_PREP, 1);
+        // fused rays with the cells rotated once per rotation: the GEMM projects
+        // them itself, so the batch needs no per-slot arrays
+        const bool project = t.fused && t.d_rpos && nrl <= 64;
+        if (!project) {
+            p.timer.begin(ST_PREP);
+            // the batch's slots in one launch (rotation, or rotation x ray, rb0 + rl into slot rl)
+            if (t.rays && t.d_rpos)
+                NMS_CUDA_TRY(launch_prep_ray_from_rot(p, t.d_rpos, t.d_rw, (int64_t)p.n_rot * p.n_cells,
+                                                      t.d_ray_sc_tf, t.n_rays, rb0, nrl, t.d_cpos_b, t.d_cw_b,
+                                                      t.wstride, s));
+            else if (t.rays)
+                NMS_CUDA_TRY(launch_prep_ray_batch(p, t.d_rot, t.d_ray_sc, t.n_rays, rb0, nrl, !t.objects, t.d_cpos_b,
+                                                   t.d_cw_b, t.wstride, s));
+            else
+                NMS_CUDA_TRY(launch_prep_rot_batch(p, t.d_rot, rb0, nrl, !t.objects, t.d_cpos_b, t.d_cw_b, t.wstride,
+                                                   s));
+            p.timer.end(ST_PREP, 1);
+        }
         if (t.objects) NMS_CUDA_TRY(cudaMemsetAsync(t.d_Ftot_b, 0, (size_t)nrl * nS * F4g * sizeof(double), s));
         if (t.d_Gdil_b) NMS_CUDA_TRY(cudaMemsetAsync(t.d_Gdil_b, 0, (size_t)nrl * nS * 16 * npg * sizeof(double), s));
         for (const OutBatch& ob : S.batches) {
             for (const Chunk& ch : ob.chunks) {
                 if (t.fused) {
                     p.timer.begin(ST_GEMM);
-                    NMS_CUDA_TRY(tc_launch_gemm_rays(t.d_cpos_b, t.d_cw_b, S.d_kb_cell0 + ch.kb_off,
-                                                     S.d_kb_ncell + ch.kb_off, t.h_qy.data(), t.ax.nyg, t.h_qz.data(),
+                    RayProjection pr;
+                    if (project) {
+                        pr.ray_sc = t.d_ray_sc_tf;
+                        pr.n_cells = p.n_cells;
+                        pr.slot0 = rb0;
+                        pr.n_rays = t.n_rays;
+                        pr.n_rl = nrl;
+                    }
+                    NMS_CUDA_TRY(tc_launch_gemm_rays(project ? t.d_rpos : t.d_cpos_b, project ? t.d_rw : t.d_cw_b,
+                                                     S.d_kb_cell0 + ch.kb_off, S.d_kb_ncell + ch.kb_off, pr,
+                                                     t.h_qy.data(), t.ax.nyg, t.h_qz.data(),
                                                      t.ax.nzg, wscale, (const char*)S.d_items + ch.item_off * tc_item_bytes(),
                                                      S.d_units + ch.unit_off, ch.grid, t.kcb, t.d_P, t.d_Fb, lo_off,
                                                      t.ax, t.nch, scale, p.d_err, limit, s));

@@ -910,9 +910,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 //
 // Roles (576 threads):
 //   warp 0           copies each k-block's cell data (64 positions, then 64
-//                    weights, float4) into a ring of RF_CELL_SLOTS slots;
+//                    weights, float4) into a ring of RF_CELL_SLOTS slots
+//                    and, given the cells rotated once per rotation,
+//                    replaces their (Y, Z) by the projection u on the slot's
+//                    ray before releasing the slot;
 //   warp 1, lane 0   issues the MMAs (as in k_gemm_f16x3);
 //   warps 2..17      generate the operand stages and drain the accumulator.
+// Shared memory written by threads and read by the tensor cores, or read by
+// threads and then refilled by a bulk copy, is ordered across the two
+// proxies by fence.proxy.async before the mbarrier arrival that hands it on.
 // The drain's two-float running sums live in tensor memory (columns 256..383
 // hi, 384..511 lo) instead of registers, which leaves the generating warps
 // their registers for the phase arithmetic; the accumulator (D0 columns
@@ -932,10 +938,11 @@ struct RayFusedArgs {
     // project = 0: cpos holds (u hi, u lo, u hi, u lo) and cw the weights per
     // cell of the stacked slot arrays, indexed by kb_cell0.  project = 1: cpos
     // holds the rotated two-float (Y hi, Y lo, Z hi, Z lo) and cw the rotated
-    // weights once per rotation ([n_rot][n_cells]); k-block cell c0 = rl
-    // n_cells + c of slot slot0 + rl (rotation slot / n_rays, ray slot mod
-    // n_rays) is read at rotation row c, and the loader warp projects it,
-    // u = Y sin theta + Z cos theta in two-float (ray_sc: sin hi, lo, cos hi, lo).
+    // weights once per rotation ([n_rot][n_cells]); a k-block's first cell
+    // c0 = rl n_cells + c belongs to slot s = slot0 + rl, that is rotation
+    // s / n_rays and ray s mod n_rays, and is read at (s / n_rays) n_cells + c;
+    // the loader warp then projects it, u = Y sin theta + Z cos theta in
+    // two-float (ray_sc: sin hi, lo, cos hi, lo per ray).
     const float4* cpos;
     const float4* cw;
     const int64_t* kb_cell0;      // first cell of each k-block of the launch

@@ -908,27 +908,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // and cos come from sincos_turns instead of sincospif: generation, not the
 // MMAs, sets this form's pace.
 //
-// Roles (576 threads):
+// Roles (704 threads):
 //   warp 0           copies each k-block's cell data (64 positions, then 64
 //                    weights, float4) into a ring of RF_CELL_SLOTS slots
 //                    and, given the cells rotated once per rotation,
 //                    replaces their (Y, Z) by the projection u on the slot's
 //                    ray before releasing the slot;
 //   warp 1, lane 0   issues the MMAs (as in k_gemm_f16x3);
-//   warps 2..17      generate the operand stages and drain the accumulator.
+//   warps 2..17      generate the operand stages;
+//   warps 18..21     drain the accumulator (one warp per TMEM lane quadrant,
+//                    all 128 columns) and write each item's result.
 // Shared memory written by threads and read by the tensor cores, or read by
 // threads and then refilled by a bulk copy, is ordered across the two
 // proxies by fence.proxy.async before the mbarrier arrival that hands it on.
 // The drain's two-float running sums live in tensor memory (columns 256..383
-// hi, 384..511 lo) instead of registers, which leaves the generating warps
-// their registers for the phase arithmetic; the accumulator (D0 columns
-// 0..127, D1 128..255) is single-buffered.  The workers drain chunk c - 1 just
-// after generating the first k-block of chunk c: the MMAs of chunk c wait for
-// that drain, and generation, slower per k-block than the MMAs, keeps them
-// waiting anyway, so the accumulator is free again before it is needed.
+// hi, 384..511 lo), since a drain thread covers 128 columns; the accumulator
+// (D0 columns 0..127, D1 128..255) is single-buffered, so the MMAs of chunk c
+// wait for the drain of chunk c - 1, which runs beside the generation of
+// chunk c's operands (generation is the slower of the two).
 constexpr int RF_CELL_SLOTS = 4;
 constexpr int RF_CELL_BYTES = 64 * 32;   // per slot: 64 float4 positions, then 64 float4 weights
-constexpr int RF_WORKERS = 16 * 32;
+constexpr int RF_GEN_WARPS = 16;
+constexpr int RF_WORKERS = RF_GEN_WARPS * 32;   // generating threads
+constexpr int RF_DRAIN_WARPS = 4;               // one per TMEM lane quadrant
+constexpr int RF_THREADS = (2 + RF_GEN_WARPS + RF_DRAIN_WARPS) * 32;
 constexpr int RF_SMEM = TC_STAGES * TC_STAGE_BYTES + RF_CELL_SLOTS * RF_CELL_BYTES + 1024;
 
 constexpr int RF_MAX_SLOTS = 64;     // slots per launch when the loader projects
@@ -1014,48 +1017,55 @@ __device__ __forceinline__ void ray_gen_block(uint8_t* st, const float* uh, cons
     }
 }
 
-// Drain one chunk into the tensor-memory running sums of this warp's 32
-// columns (tb: its D0 address; D1 +128, hi +256, lo +384): lo += D0 + D1
-// (first chunk of an item: hi = 0, lo = D0 + D1), then, when renorm, a
-// second pass TwoSum(hi, lo) -> (hi, lo).  The MMAs of the next chunk wait
-// for this drain, so it works in four 8-column groups (one TMEM load round
-// trip each) and reads hi only in the renormalising pass, which keeps its
-// registers few beside the generation state.
+// Drain one chunk into the tensor-memory running sums of this warp's lane
+// quadrant, all 128 columns (tb: column 0 of D0; D1 +128, hi +256, lo +384):
+// lo += D0 + D1 (first chunk of an item: hi = 0, lo = D0 + D1), then, when
+// renorm, a second pass TwoSum(hi, lo) -> (hi, lo).  The MMAs of the next
+// chunk wait for this drain, so each TMEM load round trip covers two
+// 8-column groups.
+__device__ __forceinline__ void ray_drain_pair(uint32_t tb, int cb, bool first)
+{
+    float d0[16], d1[16], sl[16];
+    tmem_ld8(tb + 8 * cb, d0);
+    tmem_ld8(tb + 8 * cb + 8, d0 + 8);
+    tmem_ld8(tb + 128 + 8 * cb, d1);
+    tmem_ld8(tb + 128 + 8 * cb + 8, d1 + 8);
+    if (!first) {
+        tmem_ld8(tb + 384 + 8 * cb, sl);
+        tmem_ld8(tb + 384 + 8 * cb + 8, sl + 8);
+    }
+    tmem_wait_ld();
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const uint64_t x = f2_add(f2_pack(d0[2 * u], d0[2 * u + 1]), f2_pack(d1[2 * u], d1[2 * u + 1]));
+        const uint64_t lo = first ? x : f2_add(f2_pack(sl[2 * u], sl[2 * u + 1]), x);
+        sl[2 * u] = f2_lane0(lo);
+        sl[2 * u + 1] = f2_lane1(lo);
+    }
+#pragma unroll
+    for (int z = 0; z < 16; z += 4) tmem_st4(tb + 384 + 8 * cb + z, sl + z);
+    if (first) {
+#pragma unroll
+        for (int z = 0; z < 16; ++z) d0[z] = 0.f;
+#pragma unroll
+        for (int z = 0; z < 16; z += 4) tmem_st4(tb + 256 + 8 * cb + z, d0 + z);
+    }
+}
+
 __device__ __forceinline__ void ray_drain_chunk(uint32_t tb, bool first, bool renorm)
 {
-#pragma unroll
-    for (int cb = 0; cb < 4; ++cb) {
-        float d0[8], d1[8], sl[8];
-        tmem_ld8(tb + 8 * cb, d0);
-        tmem_ld8(tb + 128 + 8 * cb, d1);
-        if (!first) tmem_ld8(tb + 384 + 8 * cb, sl);
-        tmem_wait_ld();
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const uint64_t x = f2_add(f2_pack(d0[2 * u], d0[2 * u + 1]), f2_pack(d1[2 * u], d1[2 * u + 1]));
-            const uint64_t lo = first ? x : f2_add(f2_pack(sl[2 * u], sl[2 * u + 1]), x);
-            sl[2 * u] = f2_lane0(lo);
-            sl[2 * u + 1] = f2_lane1(lo);
-        }
-#pragma unroll
-        for (int z = 0; z < 8; z += 4) tmem_st4(tb + 384 + 8 * cb + z, sl + z);
-        if (first) {
-#pragma unroll
-            for (int z = 0; z < 8; ++z) d0[z] = 0.f;
-#pragma unroll
-            for (int z = 0; z < 8; z += 4) tmem_st4(tb + 256 + 8 * cb + z, d0 + z);
-        }
-    }
+    for (int cb = 0; cb < 16; cb += 2) ray_drain_pair(tb, cb, first);
     if (renorm) {
         tmem_wait_st();
-#pragma unroll
-        for (int cb = 0; cb < 4; ++cb) {
-            float sh[8], sl[8];
+        for (int cb = 0; cb < 16; cb += 2) {
+            float sh[16], sl[16];
             tmem_ld8(tb + 256 + 8 * cb, sh);
+            tmem_ld8(tb + 256 + 8 * cb + 8, sh + 8);
             tmem_ld8(tb + 384 + 8 * cb, sl);
+            tmem_ld8(tb + 384 + 8 * cb + 8, sl + 8);
             tmem_wait_ld();
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 const uint64_t hi = f2_pack(sh[2 * u], sh[2 * u + 1]);
                 const uint64_t lo = f2_pack(sl[2 * u], sl[2 * u + 1]);
                 const uint64_t sm = f2_add(hi, lo);
@@ -1067,7 +1077,7 @@ __device__ __forceinline__ void ray_drain_chunk(uint32_t tb, bool first, bool re
                 sl[2 * u + 1] = f2_lane1(er);
             }
 #pragma unroll
-            for (int z = 0; z < 8; z += 4) {
+            for (int z = 0; z < 16; z += 4) {
                 tmem_st4(tb + 256 + 8 * cb + z, sh + z);
                 tmem_st4(tb + 384 + 8 * cb + z, sl + z);
             }
@@ -1076,7 +1086,7 @@ __device__ __forceinline__ void ray_drain_chunk(uint32_t tb, bool first, bool re
     tmem_wait_st();
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(RF_THREADS, 1)
     k_gemm_ray_fused(const GemmArgs g, const __grid_constant__ RayFusedArgs ra)
 {
     constexpr int STG = TC_STAGES;
@@ -1113,7 +1123,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(&bar_raw_full[s], 1);
         }
         mbar_init(&bar_acc_full, 1);
-        mbar_init(&bar_acc_empty, TC_EPI_WARPS);
+        mbar_init(&bar_acc_empty, RF_DRAIN_WARPS);
         mbar_init(&bar_final, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1283,11 +1293,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_commit(&bar_final);
             mbar_wait_drain(&bar_final, 0);
         }
-    } else {
-        // ---------------- workers: operand generation and the drain
-        const int e = warp - 2;
-        const int quad = warp & 3;                  // TMEM lane quadrant of this warp
-        const int colh = (e >> 2) * 32;             // its 32 accumulator columns
+    } else if (warp < 2 + RF_GEN_WARPS) {
+        // ---------------- generating warps: the operand stages
         const int t = threadIdx.x - 64;
         const int q4 = t & 15;                      // cells 4 q4 .. + 3 of each k-block
         const int r = t >> 4;                       // B nodes r, r + 32; A node r / 2
@@ -1297,110 +1304,96 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const float2 qb0 = r < ra.nzg ? ra.qz[r] : zero2;
         const float2 qb1 = r + 32 < ra.nzg ? ra.qz[r + 32] : zero2;
         const float2 qa = (r >> 1) < ra.nyg ? ra.qy[r >> 1] : zero2;
-        const uint32_t tb = taddr + ((uint32_t)(quad * 32) << 16) + (uint32_t)colh;
         int s = 0;
         uint32_t epar = 1u;                         // parity of the stage's previous "empty" phase
         int cs = 0;
         uint32_t cpar = 0u;                         // parity of the cell slot's next "full" phase
-        uint32_t c = 0;                             // chunk sequence number (drains)
         bool ok = true;
         for (int it = it_begin; it < it_end && ok; ++it) {
             const GemmItem item = g.items[it];
-            int pend = -1;                          // first k-block of the chunk awaiting its drain
-            bool any = false;
-            for (int k0 = item.kb0; k0 < item.kb1 && ok; k0 += g.kcb) {
-                const int k1 = min(item.kb1, k0 + g.kcb);
-                for (int kb = k0; kb < k1; ++kb) {
-                    // this k-block's cells
-                    if (!warp_wait(&bar_cell_full[cs], cpar, g.limit_ns, &s_abort)) {
-                        ok = false;
-                        break;
-                    }
-                    const uint8_t* cl = cells + cs * RF_CELL_BYTES;
-                    const int nc = s_nc[cs];
-                    float2 v[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) v[j] = *reinterpret_cast<const float2*>(cl + 16 * (4 * q4 + ((j + m) & 3)));
-                    float4 wv[2];
-#pragma unroll
-                    for (int j = 0; j < 2; ++j)
-                        wv[j] = *reinterpret_cast<const float4*>(cl + RF_CELL_BYTES / 2 +
-                                                                 16 * (4 * q4 + 2 * h + ((j + m) & 1)));
-                    // the slot's next contents arrive by bulk copy (async proxy):
-                    // order these generic reads before it, then release the slot
-                    fence_proxy_async_smem();
-                    mbar_arrive(&bar_cell_empty[cs]);
-                    if (++cs == RF_CELL_SLOTS) {
-                        cs = 0;
-                        cpar ^= 1u;
-                    }
-                    // cell 4 q4 + u was read into v[(u - m) mod 4]; cells past nc are zero
-                    float uh[4], ul[4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int j = (u - m) & 3;
-                        const float2 x = j == 0 ? v[0] : j == 1 ? v[1] : j == 2 ? v[2] : v[3];
-                        const bool live = 4 * q4 + u < nc;
-                        uh[u] = live ? x.x : 0.f;
-                        ul[u] = live ? x.y : 0.f;
-                    }
-                    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                    const float4 wa = (m & 1) ? wv[1] : wv[0], wb = (m & 1) ? wv[0] : wv[1];
-                    const float4 W = ra.wscale;
-                    const float4 w0 = 4 * q4 + 2 * h < nc
-                                          ? make_float4(wa.x * W.x, wa.y * W.y, wa.z * W.z, wa.w * W.w) : z4;
-                    const float4 w1 = 4 * q4 + 2 * h + 1 < nc
-                                          ? make_float4(wb.x * W.x, wb.y * W.y, wb.z * W.z, wb.w * W.w) : z4;
-                    // the stage, once the MMAs have read its previous contents
-                    if (!warp_wait(&bar_empty[s], epar, g.limit_ns, &s_abort)) {
-                        ok = false;
-                        break;
-                    }
-                    ray_gen_block(sgen + s * TC_STAGE_BYTES, uh, ul, w0, w1, q4, r, qb0, qb1, qa);
-                    fence_proxy_async_smem();
-                    mbar_arrive(&bar_full[s]);
-                    if (++s == STG) {
-                        s = 0;
-                        epar ^= 1u;
-                    }
-                    if (kb == k0 && pend >= 0) {
-                        // drain the previous chunk while the MMAs wait for this one
-                        int okw = 0;
-                        if (lane == 0) okw = mbar_wait(&bar_acc_full, c & 1u, g.limit_ns, &s_abort) ? 1 : 0;
-                        okw = __shfl_sync(0xffffffffu, okw, 0);
-                        if (!okw) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const int ci = (pend - item.kb0) / g.kcb;
-                        ray_drain_chunk(tb, ci == 0, TC_RENORM <= 1 || (ci + 1) % TC_RENORM == 0);
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&bar_acc_empty);
-                        ++c;
-                        pend = -1;
-                        any = true;
-                    }
+            for (int kb = item.kb0; kb < item.kb1; ++kb) {
+                // this k-block's cells
+                if (!warp_wait(&bar_cell_full[cs], cpar, g.limit_ns, &s_abort)) {
+                    ok = false;
+                    break;
                 }
-                if (ok) pend = k0;
+                const uint8_t* cl = cells + cs * RF_CELL_BYTES;
+                const int nc = s_nc[cs];
+                float2 v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[j] = *reinterpret_cast<const float2*>(cl + 16 * (4 * q4 + ((j + m) & 3)));
+                float4 wv[2];
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+                    wv[j] = *reinterpret_cast<const float4*>(cl + RF_CELL_BYTES / 2 +
+                                                             16 * (4 * q4 + 2 * h + ((j + m) & 1)));
+                // the slot's next contents arrive by bulk copy (async proxy):
+                // order these generic reads before it, then release the slot
+                fence_proxy_async_smem();
+                mbar_arrive(&bar_cell_empty[cs]);
+                if (++cs == RF_CELL_SLOTS) {
+                    cs = 0;
+                    cpar ^= 1u;
+                }
+                // cell 4 q4 + u was read into v[(u - m) mod 4]; cells past nc are zero
+                float uh[4], ul[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = (u - m) & 3;
+                    const float2 x = j == 0 ? v[0] : j == 1 ? v[1] : j == 2 ? v[2] : v[3];
+                    const bool live = 4 * q4 + u < nc;
+                    uh[u] = live ? x.x : 0.f;
+                    ul[u] = live ? x.y : 0.f;
+                }
+                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 wa = (m & 1) ? wv[1] : wv[0], wb = (m & 1) ? wv[0] : wv[1];
+                const float4 W = ra.wscale;
+                const float4 w0 = 4 * q4 + 2 * h < nc
+                                      ? make_float4(wa.x * W.x, wa.y * W.y, wa.z * W.z, wa.w * W.w) : z4;
+                const float4 w1 = 4 * q4 + 2 * h + 1 < nc
+                                      ? make_float4(wb.x * W.x, wb.y * W.y, wb.z * W.z, wb.w * W.w) : z4;
+                // the stage, once the MMAs have read its previous contents
+                if (!warp_wait(&bar_empty[s], epar, g.limit_ns, &s_abort)) {
+                    ok = false;
+                    break;
+                }
+                ray_gen_block(sgen + s * TC_STAGE_BYTES, uh, ul, w0, w1, q4, r, qb0, qb1, qa);
+                fence_proxy_async_smem();
+                mbar_arrive(&bar_full[s]);
+                if (++s == STG) {
+                    s = 0;
+                    epar ^= 1u;
+                }
             }
-            if (ok && pend >= 0) {
+        }
+        if (!ok && lane == 0) {
+            s_abort = 1;
+            atomicExch(g.err, 3);
+        }
+    } else {
+        // ---------------- drain warps: one per TMEM lane quadrant, all 128
+        // columns: each chunk into the running sums, each item's sums out
+        const int quad = warp & 3;
+        const uint32_t tb = taddr + ((uint32_t)(quad * 32) << 16);
+        uint32_t c = 0;                             // chunk sequence number
+        bool ok = true;
+        for (int it = it_begin; it < it_end && ok; ++it) {
+            const GemmItem item = g.items[it];
+            bool any = false;
+            for (int k0 = item.kb0, ci = 0; k0 < item.kb1; k0 += g.kcb, ++ci, ++c) {
                 int okw = 0;
                 if (lane == 0) okw = mbar_wait(&bar_acc_full, c & 1u, g.limit_ns, &s_abort) ? 1 : 0;
                 okw = __shfl_sync(0xffffffffu, okw, 0);
-                if (okw) {
-                    tc_fence_after();
-                    const int ci = (pend - item.kb0) / g.kcb;
-                    ray_drain_chunk(tb, ci == 0, TC_RENORM <= 1 || (ci + 1) % TC_RENORM == 0);
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&bar_acc_empty);
-                    ++c;
-                    any = true;
-                } else {
+                if (!okw) {
                     ok = false;
+                    break;
                 }
+                tc_fence_after();
+                ray_drain_chunk(tb, ci == 0, TC_RENORM <= 1 || (ci + 1) % TC_RENORM == 0);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar_acc_empty);
+                any = true;
             }
             if (!ok) {
                 if (lane == 0) {
@@ -1409,6 +1402,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 break;
             }
+            const int row = quad * 32 + lane;       // this lane's accumulator row
             if (item.slot < 0) {
                 // an output of one piece: its amplitudes, rounded to FP32, go
                 // straight into F (FbView layout).  Rays mirror no axis, so
@@ -1421,16 +1415,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     continue;
                 }
                 const AxisMap& ax = g.ax;
-                const int mg = quad * 32 + lane;
-                const int p = mg & 1, qi = mg >> 1;
+                const int p = row & 1, qi = row >> 1;
                 const int ag = qi / g.nch, ch = qi & (g.nch - 1);
                 const int64_t mrows = (int64_t)g.nch * ax.ny;
                 float2* Fo = reinterpret_cast<float2*>(g.F) + (int64_t)(-1 - item.slot) * (ax.nz - ax.zs0) * mrows +
                              ch + (int64_t)g.nch * (ax.hy + ag);
                 const bool act = p == 0 && ag < ax.nyg;
                 const float sc = g.scale[ch & 3];
-#pragma unroll
-                for (int cb = 0; cb < 4; ++cb) {
+                for (int cb = 0; cb < 16; ++cb) {
                     float xh[8], xl[8];
                     if (any) {
                         tmem_ld8(tb + 256 + 8 * cb, xh);
@@ -1444,7 +1436,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     for (int u = 0; u < 4; ++u) {
                         const uint64_t x = f2_add(f2_pack(xh[2 * u], xh[2 * u + 1]), f2_pack(xl[2 * u], xl[2 * u + 1]));
                         const uint64_t y = __shfl_xor_sync(0xffffffffu, x, 1);
-                        const int bg = ((colh + 8 * cb) >> 1) + u;
+                        const int bg = 4 * cb + u;
                         if (act && bg < ax.nzg) {
                             const float cc = f2_lane0(x), cs = f2_lane1(x), scs = f2_lane0(y), ss = f2_lane1(y);
                             Fo[(int64_t)(ax.hz + bg - ax.zs0) * mrows] = make_float2(sc * (cc - ss), -sc * (cs + scs));
@@ -1454,12 +1446,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 continue;
             }
             // the item's tile, unscaled, to its partial slot P[slot]
-            // (k_gemm_reduce combines them): each 8-column group of the sums
-            // straight from TMEM
-            float4* out = reinterpret_cast<float4*>(g.P) + (int64_t)item.slot * (TC_BM * TC_BN / 2) +
-                          (int64_t)(colh >> 1) * TC_BM + quad * 32 + lane;
-#pragma unroll
-            for (int cb = 0; cb < 4; ++cb) {
+            // (k_gemm_reduce combines them), 8 columns at a time from TMEM
+            float4* out = reinterpret_cast<float4*>(g.P) + (int64_t)item.slot * (TC_BM * TC_BN / 2) + row;
+            for (int cb = 0; cb < 16; ++cb) {
                 float xh[8], xl[8];
                 if (any) {
                     tmem_ld8(tb + 256 + 8 * cb, xh);
@@ -1759,7 +1748,7 @@ cudaError_t tc_launch_gemm_rays(const float4* cpos, const float4* cw, const int6
     for (int a = 0; a < nyg; ++a) ra.qy[a] = qy[a];
     for (int b = 0; b < nzg; ++b) ra.qz[b] = qz[b];
     if (grid <= 0) return cudaSuccess;
-    k_gemm_ray_fused<<<grid, TC_THREADS, RF_SMEM, s>>>(ga, ra);
+    k_gemm_ray_fused<<<grid, RF_THREADS, RF_SMEM, s>>>(ga, ra);
     return cudaGetLastError();
 }
 

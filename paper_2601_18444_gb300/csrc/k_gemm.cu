@@ -911,9 +911,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // Roles (704 threads):
 //   warp 0           copies each k-block's cell data (64 positions, then 64
 //                    weights, float4) into a ring of RF_CELL_SLOTS slots
-//                    and, given the cells rotated once per rotation,
-//                    replaces their (Y, Z) by the projection u on the slot's
-//                    ray before releasing the slot;
+//                    and lays each slot out for the generating threads (u
+//                    as two float arrays, projected on the slot's ray when
+//                    given the cells rotated once per rotation; weights
+//                    scaled, even and odd cells apart; cells past the
+//                    k-block's end zero) before releasing it;
 //   warp 1, lane 0   issues the MMAs (as in k_gemm_f16x3);
 //   warps 2..17      generate the operand stages;
 //   warps 18..21     drain the accumulator (one warp per TMEM lane quadrant,
@@ -935,7 +937,7 @@ constexpr int RF_THREADS = (2 + RF_GEN_WARPS + RF_DRAIN_WARPS) * 32;
 constexpr int RF_SMEM = TC_STAGES * TC_STAGE_BYTES + RF_CELL_SLOTS * RF_CELL_BYTES + 1024;
 
 constexpr int RF_MAX_SLOTS = 64;     // slots per launch when the loader projects
-constexpr int RF_PROJ_LAG = 2;       // k-blocks between a slot's copy and its projection
+constexpr int RF_PROJ_LAG = 2;       // k-blocks between a slot's copy and its final layout
 
 struct RayFusedArgs {
     // project = 0: cpos holds (u hi, u lo, u hi, u lo) and cw the weights per
@@ -1142,10 +1144,10 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
         // ---------------- cell loader: bulk copies of each k-block's cells.
         // The warp reads the k-block descriptors 32 at a time (lane l holds
         // block kb0 + 32 i + l), so the copies never wait on those loads;
-        // every lane follows the ring, lane 0 issues.  With project = 1 the
-        // copy brings the rotated (Y, Z) and the warp replaces them by the
-        // projection u on the slot's ray RF_PROJ_LAG k-blocks later, then
-        // releases the slot to the workers.
+        // every lane follows the ring, lane 0 issues.  RF_PROJ_LAG k-blocks
+        // after a slot's copy the warp rewrites it in the generating threads'
+        // layout (with project = 1 projecting (Y, Z) on the slot's ray), then
+        // releases it to them.
         int64_t i = 0;                      // k-block sequence number (copies issued)
         int cs = 0;                         // its cell slot
         uint32_t par = 1u;                  // parity of the slot's previous "empty" phase
@@ -1153,22 +1155,50 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
         int csp = 0;
         uint32_t ppar = 0u;
         bool ok = true;
-        auto project_next = [&]() -> bool {
+        // a slot's copy has landed: turn it into the layout the generating
+        // threads read (u hi at 0, u lo at 256 bytes, 64 floats each; the
+        // weights times the channel scale, cells 0, 2, .. at 1024 and 1, 3, ..
+        // at 1536 bytes), every one of the 64 cells written, past nc zero
+        auto finalize_next = [&]() -> bool {
             if (!warp_wait(&bar_raw_full[csp], ppar, g.limit_ns, &s_abort)) return false;
             const int nc = s_nc[csp];
-            const float4 sc = s_sc[s_rl[csp]];
             uint8_t* cl = cells + csp * RF_CELL_BYTES;
-            for (int k = lane; k < nc; k += 32) {
-                const float4 yz = *reinterpret_cast<const float4*>(cl + 16 * k);
-                // u = Y sin theta + Z cos theta: two two-float products and a TwoSum
-                const float p1 = sc.x * yz.x, p2 = sc.z * yz.z;
-                const float e1 = fmaf(sc.x, yz.x, -p1) + fmaf(sc.x, yz.y, sc.y * yz.x);
-                const float e2 = fmaf(sc.z, yz.z, -p2) + fmaf(sc.z, yz.w, sc.w * yz.z);
-                const float sm = p1 + p2;
-                const float bb = sm - p1;
-                const float e = ((p1 - (sm - bb)) + (p2 - bb)) + (e1 + e2);
-                const float uh = sm + e;
-                *reinterpret_cast<float2*>(cl + 16 * k) = make_float2(uh, e - (uh - sm));
+            const float4 W = ra.wscale;
+            float uh[2], ul[2];
+            float4 w[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int k = lane + 32 * q;
+                uh[q] = ul[q] = 0.f;
+                w[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (k < nc) {
+                    const float4 x = *reinterpret_cast<const float4*>(cl + 16 * k);
+                    if (ra.project) {
+                        // u = Y sin theta + Z cos theta: two two-float products and a TwoSum
+                        const float4 sc = s_sc[s_rl[csp]];
+                        const float p1 = sc.x * x.x, p2 = sc.z * x.z;
+                        const float e1 = fmaf(sc.x, x.x, -p1) + fmaf(sc.x, x.y, sc.y * x.x);
+                        const float e2 = fmaf(sc.z, x.z, -p2) + fmaf(sc.z, x.w, sc.w * x.z);
+                        const float sm = p1 + p2;
+                        const float bb = sm - p1;
+                        const float e = ((p1 - (sm - bb)) + (p2 - bb)) + (e1 + e2);
+                        uh[q] = sm + e;
+                        ul[q] = e - (uh[q] - sm);
+                    } else {
+                        uh[q] = x.x;
+                        ul[q] = x.y;
+                    }
+                    const float4 v = *reinterpret_cast<const float4*>(cl + RF_CELL_BYTES / 2 + 16 * k);
+                    w[q] = make_float4(v.x * W.x, v.y * W.y, v.z * W.z, v.w * W.w);
+                }
+            }
+            __syncwarp();   // every lane has read its cells before any is overwritten
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int k = lane + 32 * q;
+                reinterpret_cast<float*>(cl)[k] = uh[q];
+                reinterpret_cast<float*>(cl + 256)[k] = ul[q];
+                *reinterpret_cast<float4*>(cl + RF_CELL_BYTES / 2 + 512 * (k & 1) + 16 * (k >> 1)) = w[q];
             }
             fence_proxy_async_smem();       // these writes precede the slot's next bulk copy
             __syncwarp();
@@ -1197,13 +1227,12 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
                     if (lane == 0) {
                         s_nc[cs] = nc;
                         int64_t src = c0;
-                        uint64_t* landed = &bar_cell_full[cs];
+                        uint64_t* landed = &bar_raw_full[cs];
                         if (ra.project) {
                             const int64_t rl = c0 / ra.n_cells;
                             const int slot = ra.slot0 + (int)rl;
                             src = (int64_t)(slot / ra.n_rays) * ra.n_cells + (c0 - rl * ra.n_cells);
                             s_rl[cs] = (int)rl;
-                            landed = &bar_raw_full[cs];
                         }
                         uint8_t* dst = cells + cs * RF_CELL_BYTES;
                         if (nc > 0) {
@@ -1220,27 +1249,24 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
                         cs = 0;
                         par ^= 1u;
                     }
-                    if (ra.project && i - jp > RF_PROJ_LAG && !project_next()) {
+                    if (i - jp > RF_PROJ_LAG && !finalize_next()) {
                         ok = false;
                         break;
                     }
                 }
             }
         }
-        while (ok && ra.project && jp < i)
-            if (!project_next()) ok = false;
+        while (ok && jp < i)
+            if (!finalize_next()) ok = false;
         if (!ok && lane == 0) {
             s_abort = 1;
             atomicExch(g.err, 1);
         }
-        // copies in flight land before the CTA exits (bounded): the last
-        // RF_CELL_SLOTS issued; with project only those not yet projected
+        // copies in flight land before the CTA exits (bounded): those issued
+        // and not yet finalised (none, unless the block aborted)
         if (lane == 0)
-            for (int64_t k = (i > RF_CELL_SLOTS ? i - RF_CELL_SLOTS : 0); k < i; ++k) {
-                if (ra.project && k < jp) continue;
-                uint64_t* bar = ra.project ? &bar_raw_full[(int)(k % RF_CELL_SLOTS)] : &bar_cell_full[(int)(k % RF_CELL_SLOTS)];
-                mbar_wait_drain(bar, (uint32_t)((k / RF_CELL_SLOTS) & 1));
-            }
+            for (int64_t k = (jp > i - RF_CELL_SLOTS ? jp : i - RF_CELL_SLOTS); k < i; ++k)
+                mbar_wait_drain(&bar_raw_full[(int)(k % RF_CELL_SLOTS)], (uint32_t)((k / RF_CELL_SLOTS) & 1));
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer: one accumulator pair (D0, D1)
@@ -1299,7 +1325,6 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
         const int q4 = t & 15;                      // cells 4 q4 .. + 3 of each k-block
         const int r = t >> 4;                       // B nodes r, r + 32; A node r / 2
         const int h = r & 1;                        // A cells 4 q4 + 2h, + 1
-        const int m = (q4 >> 1) & 3;                // rotation of the cell reads (spreads banks)
         const float2 zero2 = make_float2(0.f, 0.f);
         const float2 qb0 = r < ra.nzg ? ra.qz[r] : zero2;
         const float2 qb1 = r + 32 < ra.nzg ? ra.qz[r + 32] : zero2;
@@ -1317,16 +1342,13 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
                     ok = false;
                     break;
                 }
+                // the slot as the loader warp laid it out: u of cells 4 q4 .. + 3,
+                // scaled weights of cells 4 q4 + 2h (even) and + 1 (odd)
                 const uint8_t* cl = cells + cs * RF_CELL_BYTES;
-                const int nc = s_nc[cs];
-                float2 v[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) v[j] = *reinterpret_cast<const float2*>(cl + 16 * (4 * q4 + ((j + m) & 3)));
-                float4 wv[2];
-#pragma unroll
-                for (int j = 0; j < 2; ++j)
-                    wv[j] = *reinterpret_cast<const float4*>(cl + RF_CELL_BYTES / 2 +
-                                                             16 * (4 * q4 + 2 * h + ((j + m) & 1)));
+                const float4 uh4 = *reinterpret_cast<const float4*>(cl + 16 * q4);
+                const float4 ul4 = *reinterpret_cast<const float4*>(cl + 256 + 16 * q4);
+                const float4 w0 = *reinterpret_cast<const float4*>(cl + RF_CELL_BYTES / 2 + 16 * (2 * q4 + h));
+                const float4 w1 = *reinterpret_cast<const float4*>(cl + RF_CELL_BYTES / 2 + 512 + 16 * (2 * q4 + h));
                 // the slot's next contents arrive by bulk copy (async proxy):
                 // order these generic reads before it, then release the slot
                 fence_proxy_async_smem();
@@ -1335,23 +1357,8 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
                     cs = 0;
                     cpar ^= 1u;
                 }
-                // cell 4 q4 + u was read into v[(u - m) mod 4]; cells past nc are zero
-                float uh[4], ul[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = (u - m) & 3;
-                    const float2 x = j == 0 ? v[0] : j == 1 ? v[1] : j == 2 ? v[2] : v[3];
-                    const bool live = 4 * q4 + u < nc;
-                    uh[u] = live ? x.x : 0.f;
-                    ul[u] = live ? x.y : 0.f;
-                }
-                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 wa = (m & 1) ? wv[1] : wv[0], wb = (m & 1) ? wv[0] : wv[1];
-                const float4 W = ra.wscale;
-                const float4 w0 = 4 * q4 + 2 * h < nc
-                                      ? make_float4(wa.x * W.x, wa.y * W.y, wa.z * W.z, wa.w * W.w) : z4;
-                const float4 w1 = 4 * q4 + 2 * h + 1 < nc
-                                      ? make_float4(wb.x * W.x, wb.y * W.y, wb.z * W.z, wb.w * W.w) : z4;
+                const float uh[4] = {uh4.x, uh4.y, uh4.z, uh4.w};
+                const float ul[4] = {ul4.x, ul4.y, ul4.z, ul4.w};
                 // the stage, once the MMAs have read its previous contents
                 if (!warp_wait(&bar_empty[s], epar, g.limit_ns, &s_abort)) {
                     ok = false;

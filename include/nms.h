@@ -423,8 +423,9 @@ nms_status nms_selftest_bounded_wait(int64_t limit_us, void* cuda_stream);
 
 /* Self-test of the sine and cosine that the fused ray GEMM form generates
  * its operands with (the phase 2 pi t of Eq. qdef's exponential, t in turns,
- * already reduced to |t| <= 1/2; quarter-turn reduction and Taylor series,
- * the paper has no counterpart): for each of the n host values t[i],
+ * |t| <= 1/2, taken in quarter turns, split at the nearest one, Taylor series
+ * of the remainder; the paper has no counterpart): for each of the n host
+ * values t[i],
  * out[4i], out[4i + 1] = sin, cos of 2 pi t[i] by that routine and
  * out[4i + 2], out[4i + 3] = the same by CUDA's sincospif, for comparison
  * with each other and with exact values.  out (host) holds 4n floats.

@@ -81,34 +81,38 @@ __device__ __forceinline__ float turns_reduced(float2 q, float xh, float xl)
     return (p - n) + e;
 }
 
-// sin(2 pi t) and cos(2 pi t) of a phase in turns, |t| <= 1/2 (the reduced
-// phase above), for the fused ray form, where these values set the pace:
-// the nearest quarter turn n/4 is split off exactly (r = t - n/4, |r| <= 1/8,
-// Sterbenz), sin and cos of 2 pi r come from their Taylor series about 0
-// (odd terms to r^9, even terms to r^10: truncation below 2e-9 for
-// |2 pi r| <= pi/4), and the quadrant n mod 4 swaps and negates them.
-// Coefficients are (2 pi)^k / k! rounded once to FP32, times the power of
-// two SCALE (exact: the results come out scaled by SCALE at no cost).  Error
-// about one unit in the last place (checked against exact values and
-// sincospif).
+// sin and cos of the phase 2 pi q x of a two-float node q (turns per unit
+// length, passed as q4 = 4 q: scaling by 4 is exact) and a two-float
+// coordinate x, for the fused ray form, where these values set the pace.
+// The product in quarter turns p + e = q4 x (p = fl(q4.x x.h), e its error
+// and the low parts) is split at the nearest quarter turn n = rint(p), the
+// remainder r = (p - n) + e (p - n exact, Sterbenz; |r| <= 1/2 up to |e|)
+// gives sin and cos of (pi/2) r by their Taylor series about 0 (odd terms
+// to r^9, even terms to r^10: truncation below 2e-9 for |(pi/2) r| <= pi/4),
+// and the quadrant n mod 4 swaps and negates them.  Coefficients are
+// (pi/2)^k / k! rounded once to FP32, times the power of two SCALE (exact:
+// the results come out scaled by SCALE at no cost).  Error about one unit in
+// the last place (checked against exact values and sincospif).
 template <int SCALE = 1>
-__device__ __forceinline__ void sincos_turns(float t, float& sn, float& cs)
+__device__ __forceinline__ void sincos_node(float2 q4, float xh, float xl, float& sn, float& cs)
 {
     static_assert(SCALE > 0 && (SCALE & (SCALE - 1)) == 0, "SCALE must be a power of two");
-    constexpr double TP = 6.283185307179586476925286766559;
+    constexpr double H = 1.5707963267948966192313216916398;   // pi / 2
     constexpr float K = (float)SCALE;
-    constexpr float S1 = K * (float)TP;
-    constexpr float S3 = K * (float)(-TP * TP * TP / 6.0);
-    constexpr float S5 = K * (float)(TP * TP * TP * TP * TP / 120.0);
-    constexpr float S7 = K * (float)(-TP * TP * TP * TP * TP * TP * TP / 5040.0);
-    constexpr float S9 = K * (float)(TP * TP * TP * TP * TP * TP * TP * TP * TP / 362880.0);
-    constexpr float C2 = K * (float)(-TP * TP / 2.0);
-    constexpr float C4 = K * (float)(TP * TP * TP * TP / 24.0);
-    constexpr float C6 = K * (float)(-TP * TP * TP * TP * TP * TP / 720.0);
-    constexpr float C8 = K * (float)(TP * TP * TP * TP * TP * TP * TP * TP / 40320.0);
-    constexpr float C10 = K * (float)(-TP * TP * TP * TP * TP * TP * TP * TP * TP * TP / 3628800.0);
-    const float qn = rintf(4.0f * t);
-    const float r = fmaf(qn, -0.25f, t);
+    constexpr float S1 = K * (float)H;
+    constexpr float S3 = K * (float)(-H * H * H / 6.0);
+    constexpr float S5 = K * (float)(H * H * H * H * H / 120.0);
+    constexpr float S7 = K * (float)(-H * H * H * H * H * H * H / 5040.0);
+    constexpr float S9 = K * (float)(H * H * H * H * H * H * H * H * H / 362880.0);
+    constexpr float C2 = K * (float)(-H * H / 2.0);
+    constexpr float C4 = K * (float)(H * H * H * H / 24.0);
+    constexpr float C6 = K * (float)(-H * H * H * H * H * H / 720.0);
+    constexpr float C8 = K * (float)(H * H * H * H * H * H * H * H / 40320.0);
+    constexpr float C10 = K * (float)(-H * H * H * H * H * H * H * H * H * H / 3628800.0);
+    const float p = q4.x * xh;
+    const float e = fmaf(q4.x, xh, -p) + fmaf(q4.x, xl, q4.y * xh);
+    const float qn = rintf(p);
+    const float r = (p - qn) + e;
     const int n = (int)qn;
     const float r2 = r * r;
     float ps = fmaf(S9, r2, S7);
@@ -904,9 +908,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // written to HBM once and read back once by a single tile.  This form builds
 // each k-block's four operand blocks in shared memory instead, from the cells'
 // ray projections u and weights, with the arithmetic of k_tables (two-float
-// phase in turns, exact reduction, scaled FP16 hi/lo split) except that sin
-// and cos come from sincos_turns instead of sincospif: generation, not the
-// MMAs, sets this form's pace.
+// phase, exact reduction, scaled FP16 hi/lo split) except that the phase is
+// taken in quarter turns and its sine and cosine come from sincos_node
+// instead of sincospif: generation, not the MMAs, sets this form's pace.
 //
 // Roles (704 threads):
 //   warp 0           copies each k-block's cell data (64 positions, then 64
@@ -969,7 +973,8 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint64
 }
 
 // One k-block of operands into the stage at st (generic pointer): thread
-// (r, q4) of the 512 workers writes B rows 2b, 2b + 1 (b = r, r + 32) for the
+// (r, q4) of the 512 workers (nodes qb0, qb1, qa times 4, as sincos_node
+// takes them) writes B rows 2b, 2b + 1 (b = r, r + 32) for the
 // cells 4 q4 .. + 3 (8-byte stores: a half-warp fills a 128-byte row) and the
 // eight A rows of coarse node a = r / 2 (four channels x cos, sin) for the
 // cells 4 q4 + 2h, + 1 (h = r mod 2; 4-byte stores: a warp fills a row).
@@ -986,7 +991,7 @@ __device__ __forceinline__ void ray_gen_block(uint8_t* st, const float* uh, cons
         float cs[4], sn[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-            sincos_turns<(int)TC_SCALE>(turns_reduced(q, uh[u], ul[u]), sn[u], cs[u]);
+            sincos_node<(int)TC_SCALE>(q, uh[u], ul[u], sn[u], cs[u]);
         uint2 ch, cl, sh, sl;
         split4(cs[0], cs[1], cs[2], cs[3], ch, cl);
         split4(sn[0], sn[1], sn[2], sn[3], sh, sl);
@@ -1001,8 +1006,8 @@ __device__ __forceinline__ void ray_gen_block(uint8_t* st, const float* uh, cons
     const float u0h = h ? uh[2] : uh[0], u0l = h ? ul[2] : ul[0];
     const float u1h = h ? uh[3] : uh[1], u1l = h ? ul[3] : ul[1];
     float s0, c0, s1, c1;
-    sincos_turns(turns_reduced(qa, u0h, u0l), s0, c0);
-    sincos_turns(turns_reduced(qa, u1h, u1l), s1, c1);
+    sincos_node(qa, u0h, u0l, s0, c0);
+    sincos_node(qa, u1h, u1l, s1, c1);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const float x0 = c == 0 ? w0.x : c == 1 ? w0.y : c == 2 ? w0.z : w0.w;
@@ -1326,9 +1331,11 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
         const int r = t >> 4;                       // B nodes r, r + 32; A node r / 2
         const int h = r & 1;                        // A cells 4 q4 + 2h, + 1
         const float2 zero2 = make_float2(0.f, 0.f);
-        const float2 qb0 = r < ra.nzg ? ra.qz[r] : zero2;
-        const float2 qb1 = r + 32 < ra.nzg ? ra.qz[r + 32] : zero2;
-        const float2 qa = (r >> 1) < ra.nyg ? ra.qy[r >> 1] : zero2;
+        // this thread's nodes times 4 (phases in quarter turns; exact)
+        auto x4 = [](float2 v) { return make_float2(4.0f * v.x, 4.0f * v.y); };
+        const float2 qb0 = r < ra.nzg ? x4(ra.qz[r]) : zero2;
+        const float2 qb1 = r + 32 < ra.nzg ? x4(ra.qz[r + 32]) : zero2;
+        const float2 qa = (r >> 1) < ra.nyg ? x4(ra.qy[r >> 1]) : zero2;
         int s = 0;
         uint32_t epar = 1u;                         // parity of the stage's previous "empty" phase
         int cs = 0;
@@ -1575,14 +1582,15 @@ cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t* err, cudaStream_t s
     return cudaGetLastError();
 }
 
-// Self-test of sincos_turns: for each t, sin and cos of 2 pi t by
-// sincos_turns (out[4i], out[4i + 1]) and by sincospif (out[4i + 2], + 3).
+// Self-test of sincos_node: for each t, sin and cos of 2 pi t by
+// sincos_node (node 1, coordinate t: out[4i], out[4i + 1]) and by sincospif
+// (out[4i + 2], + 3).
 __global__ void k_selftest_sincos(const float* __restrict__ t, int64_t n, float* __restrict__ out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float s, c, s2, c2;
-    sincos_turns(t[i], s, c);
+    sincos_node(make_float2(4.0f, 0.0f), t[i], 0.0f, s, c);
     sincospif(2.0f * t[i], &s2, &c2);
     out[4 * i] = s;
     out[4 * i + 1] = c;

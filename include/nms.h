@@ -396,10 +396,10 @@ nms_status nms_dsft_direct_noalloc(int64_t n_cells, const double* Y, const doubl
  * items_per_sm = work items per SM of each GEMM launch (tensor path; 0
  * otherwise), after autotuning when it was requested; gemm_form = 0 (one
  * CTA per 128 x 128 tile), 2 (two-SM MMA over pairs of A tiles) or 3 (POLAR
- * grid whose ray GEMM is one tile, at most 16 x 64 |q| nodes and one weight
- * set: the operands are generated in the GEMM's shared memory, no phase
- * tables; environment NMS_RAY_FUSED=0 keeps the tables), -1 off the tensor
- * path; mirror_y / mirror_z = 1 where the detector axis is
+ * grid whose ray GEMM has one B tile and at most three A tiles, at most
+ * 48 x 64 |q| nodes and one weight set: the operands are generated in the
+ * GEMM's shared memory, no phase tables; environment NMS_RAY_FUSED=0 keeps
+ * the tables), -1 off the tensor path; mirror_y / mirror_z = 1 where the detector axis is
  * symmetric about q = 0 (lo = -hi) and the GEMM evaluates its q >= 0 half,
  * writing both signs (cos is even and sin odd in q; Sec. "Summation
  * approach" sum, split by parity).  Any pointer may be NULL. */

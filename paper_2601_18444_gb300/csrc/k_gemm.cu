@@ -903,9 +903,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 // ------------------------------------------------------------------ fused ray GEMM
 // Polar grid (rays, reading of Eq. qdef on the paper's polar detector) with
-// one weight set and one A and one B tile (at most 16 x 64 |q| nodes): each
-// slot is one 128 x 128 output tile, so with tables every table block is
-// written to HBM once and read back once by a single tile.  This form builds
+// one weight set, one B tile and up to three A tiles (at most 48 x 64 |q|
+// nodes): each slot is one to three 128 x 128 output tiles, so with tables
+// every table block is written to HBM once and read back once by one to
+// three tiles.  Each work item covers one A tile (item.mt: coarse nodes
+// 16 mt ..) and generates that tile and the B tile; since B is generated
+// again for every A tile, a fourth tile would make the tables the faster
+// form.  This form builds
 // each k-block's four operand blocks in shared memory instead, from the cells'
 // ray projections u and weights, with the arithmetic of k_tables (two-float
 // phase, exact reduction, scaled FP16 hi/lo split) except that the phase is
@@ -941,6 +945,7 @@ constexpr int RF_THREADS = (2 + RF_GEN_WARPS + RF_DRAIN_WARPS) * 32;
 constexpr int RF_SMEM = TC_STAGES * TC_STAGE_BYTES + RF_CELL_SLOTS * RF_CELL_BYTES + 1024;
 
 constexpr int RF_MAX_SLOTS = 64;     // slots per launch when the loader projects
+constexpr int RF_MAX_COARSE = 48;    // coarse |q| nodes: up to 3 A tiles of 16
 constexpr int RF_PROJ_LAG = 2;       // k-blocks between a slot's copy and its final layout
 
 struct RayFusedArgs {
@@ -960,8 +965,8 @@ struct RayFusedArgs {
     int64_t n_cells;
     int project, slot0, n_rays, n_rl;
     float4 wscale;                // per-channel weight scale (as in k_tables)
-    int nyg, nzg;                 // live nodes: coarse (A rows, <= 16), fine (B rows, <= 64)
-    float2 qy[16];                // coarse nodes lo + 64 i1 dq in turns (two-float)
+    int nyg, nzg;                 // live nodes: coarse (A rows, <= 48: A tile mt holds 16 mt ..), fine (B rows, <= 64)
+    float2 qy[RF_MAX_COARSE];     // coarse nodes lo + 64 i1 dq in turns (two-float)
     float2 qz[64];                // fine offsets i2 dq in turns (two-float)
 };
 
@@ -1335,7 +1340,6 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
         auto x4 = [](float2 v) { return make_float2(4.0f * v.x, 4.0f * v.y); };
         const float2 qb0 = r < ra.nzg ? x4(ra.qz[r]) : zero2;
         const float2 qb1 = r + 32 < ra.nzg ? x4(ra.qz[r + 32]) : zero2;
-        const float2 qa = (r >> 1) < ra.nyg ? x4(ra.qy[r >> 1]) : zero2;
         int s = 0;
         uint32_t epar = 1u;                         // parity of the stage's previous "empty" phase
         int cs = 0;
@@ -1343,6 +1347,9 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
         bool ok = true;
         for (int it = it_begin; it < it_end && ok; ++it) {
             const GemmItem item = g.items[it];
+            // the coarse node of this thread's A rows in the item's A tile
+            const int a_node = 16 * item.mt + (r >> 1);
+            const float2 qa = a_node < ra.nyg ? x4(ra.qy[a_node]) : zero2;
             for (int kb = item.kb0; kb < item.kb1; ++kb) {
                 // this k-block's cells
                 if (!warp_wait(&bar_cell_full[cs], cpar, g.limit_ns, &s_abort)) {
@@ -1416,7 +1423,7 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
                 }
                 break;
             }
-            const int row = quad * 32 + lane;       // this lane's accumulator row
+            const int row = quad * 32 + lane;       // this lane's accumulator row (of A tile item.mt)
             if (item.slot < 0) {
                 // an output of one piece: its amplitudes, rounded to FP32, go
                 // straight into F (FbView layout).  Rays mirror no axis, so
@@ -1429,7 +1436,8 @@ __global__ void __launch_bounds__(RF_THREADS, 1)
                     continue;
                 }
                 const AxisMap& ax = g.ax;
-                const int p = row & 1, qi = row >> 1;
+                const int mg = item.mt * TC_BM + row;
+                const int p = mg & 1, qi = mg >> 1;
                 const int ag = qi / g.nch, ch = qi & (g.nch - 1);
                 const int64_t mrows = (int64_t)g.nch * ax.ny;
                 float2* Fo = reinterpret_cast<float2*>(g.F) + (int64_t)(-1 - item.slot) * (ax.nz - ax.zs0) * mrows +
@@ -1721,7 +1729,7 @@ cudaError_t tc_launch_gemm_rays(const float4* cpos, const float4* cw, const int6
                                 double* P, double* F, int64_t lo_off, const AxisMap& ax, int nch,
                                 const double scale[4], int32_t* err, uint64_t limit_ns, cudaStream_t s)
 {
-    if (nyg < 0 || nyg > 16 || nzg < 0 || nzg > 64 || nch != 4 || kcb < 1) return cudaErrorInvalidValue;
+    if (nyg < 0 || nyg > RF_MAX_COARSE || nzg < 0 || nzg > 64 || nch != 4 || kcb < 1) return cudaErrorInvalidValue;
     if (pr.ray_sc && (pr.n_rl < 1 || pr.n_rl > RF_MAX_SLOTS || pr.n_rays < 1 || pr.n_cells < 1))
         return cudaErrorInvalidValue;
     static bool attr = false;

@@ -762,13 +762,14 @@ nms_status tc_setup(Plan& p)
     }
     nms_status st;
     if ((st = upload(&t->d_qy, qy)) || (st = upload(&t->d_qz, qz))) return st;
-    // rays whose GEMM is one 128 x 128 tile per slot (one weight set, at
-    // most 16 x 64 |q| nodes): operands generated in shared memory, with
+    // rays whose GEMM has one B tile and at most three A tiles per slot (one
+    // weight set, at most 48 x 64 |q| nodes): operands generated in shared
+    // memory, each CTA building the A tile of its item and the B tile, with
     // eight work items per SM so the many equal splits balance
     // (NMS_RAY_FUSED=0 keeps the tables, for comparisons)
     {
         const char* fe = getenv("NMS_RAY_FUSED");
-        t->fused = t->rays && t->nch == 4 && t->mtiles == 1 && t->ntiles == 1 && t->mode == 0 &&
+        t->fused = t->rays && t->nch == 4 && t->mtiles <= 3 && t->ntiles == 1 && t->mode == 0 &&
                    !(fe && atoi(fe) == 0);
         if (t->fused) {
             t->h_qy = qy;

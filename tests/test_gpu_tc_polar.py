@@ -11,8 +11,8 @@ rotation averages, many slots in several batches with a remainder batch, a
 small table workspace (many chunks), several objects summed as one (their
 centres applied), the dilute, total and interference parts of objects,
 weight sets (loop mode), and the responses and azimuthal average of the
-polar image.  A ray whose GEMM is one 128 x 128 tile (one weight set, at
-most 16 x 64 |q| nodes) runs the fused form (operands generated in shared
+polar image.  A ray whose GEMM has one B tile and at most three A tiles (one
+weight set, at most 48 x 64 |q| nodes) runs the fused form (operands generated in shared
 memory): it is checked against the oracle and against the table form, at
 every TMEM chunk length, with long work items (renormalised running sums)
 and at the coherent |q| = 0 node.
@@ -277,8 +277,8 @@ def test_polar_tc_weight_sets_with_objects_and_rotations():
 
 
 def test_polar_tc_fused_matches_tables_and_oracle(monkeypatch):
-    # 1000 |q| nodes (15 full i1 nodes and a ragged 16th: the fused form's
-    # largest grid), 12 angles; the fused form and the table form each
+    # 1000 |q| nodes (15 full i1 nodes and a ragged 16th: one A tile),
+    # 12 angles; the fused form and the table form each
     # against the oracle, and against each other
     f = I.small_random_field(5001, seed=71, extent=9.0)
     kw = dict(kind="polar", n0=1000, n1=12, lo0=0.0, hi0=2.0)
@@ -344,10 +344,11 @@ def test_fused_form_sincos_against_exact_and_sincospif():
     np.testing.assert_array_equal(q[:, 1], [1.0, 0.0, 0.0, -1.0, -1.0])
 
 
-@pytest.mark.parametrize("n0,form", [(1024, 3), (1025, 0)])
+@pytest.mark.parametrize("n0,form", [(1024, 3), (1025, 3), (3072, 3), (3073, 0)])
 def test_polar_tc_fused_form_boundary(n0, form):
-    # 1024 |q| nodes (16 x 64) is the largest ray that is one tile (fused
-    # form); one node more needs a second A tile and takes the tables
+    # 1024 |q| nodes (16 x 64) fill one A tile, 1025 start a second; 3072
+    # (48 x 64, three A tiles) is the largest ray of the fused form, one node
+    # more takes the tables
     f = I.small_random_field(3001, seed=73, extent=8.0)
     kw = dict(kind="polar", n0=n0, n1=4, lo0=0.0, hi0=2.5)
     plan = run(f, kw)
